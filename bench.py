@@ -1,0 +1,404 @@
+"""Benchmark: FP64-accurate GEMM TFLOP/s (2mnk/t) on one GB300, native vs emulated.
+
+Workload (default): square FP64 product C := A*B + C, m = n = k = 8192,
+column-major, entries uniform[-1, 1] from the seeded generator; each operand
+(512 MB) is larger than L2, so no L2 flush is needed between steps.
+
+A step is one call of the public C ABI (momms_gemm_ex in AUTO mode: the plan
+picks the emulated path, whose slice count comes from the data).  The JSON line
+carries the device-resident throughput (`value`), the end-to-end throughput with
+host buffers (`e2e`), the roofline of the dominant kernel (the tcgen05 slice
+product, timed per launch with CUDA events), the native DMMA path measured in
+the same run, SM clocks sampled during the timed region, and the CPU oracle
+timed on a bounded sample (`cpu_baseline`).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--size 8192] [--impl reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(replicas; no collective on the data path); value = all ranks' flops / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64-accurate GEMM TFLOP/s (2mnk/t) & % roofline, native vs emulated"
+UNIT = "TFLOP/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--size", type=int, default=8192)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--native-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def workload_name(n):
+    return (f"square FP64 GEMM C := A*B + C, m=n=k={n}, column-major (ld = rows), "
+            f"A, B, C uniform[-1,1] (seeded SplitMix64)")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(mx)
+            out["samples"] = len(sm)
+        out["reasons"] = sorted(reasons)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return out
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def cpu_oracle_sample(n, seconds_budget, reference_arm=False):
+    """Time the oracle (as it stands) on a column sample of the n^3 workload.
+
+    Returns (TFLOP/s, cores, description).  Column j of C needs all of A and column j
+    of B, so a block of c columns is an n x c x n product of the same workload."""
+    import oracle
+    from paper_1904_05717_gb300 import synthetic as syn
+    cores = oracle.max_threads()
+    A = syn.matrix("uniform", n, n, syn.workload_seed(1, "A"))
+    Bfull_cols = None
+    # calibrate on a small block, then size the sample to the budget
+    c = max(cores, 8)
+    B = syn.matrix("uniform", n, c, syn.workload_seed(1, "B"))
+    C = syn.matrix("uniform", n, c, syn.workload_seed(1, "C"))
+    t0 = time.perf_counter()
+    oracle.dgemm(A, B, C, 1.0, 1.0)
+    t1 = time.perf_counter() - t0
+    per_col = t1 / c
+    cols = int(max(c, min(n, seconds_budget / max(per_col, 1e-9))))
+    cols = max(cores, cols - cols % cores)
+    B = syn.matrix("uniform", n, cols, syn.workload_seed(1, "B"))
+    C = syn.matrix("uniform", n, cols, syn.workload_seed(1, "C"))
+    t0 = time.perf_counter()
+    oracle.dgemm(A, B, C, 1.0, 1.0)
+    dt = time.perf_counter() - t0
+    del Bfull_cols
+    tflops = 2.0 * n * n * cols / dt / 1e12
+    desc = (f"oracle triple loop (p ascending, no FMA, OpenMP over columns) on {cols} of {n} columns "
+            f"of the m=n=k={n} product ({2.0 * n * n * cols:.3g} flops, {dt:.1f} s)")
+    return tflops, cores, desc, dt
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    n = args.size
+    # each step: a bounded sample, the whole run within a few minutes
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    desc = ""
+    cores = 1
+    for i in range(args.warmup + args.steps):
+        v, cores, desc, _ = cpu_oracle_sample(n, per_step)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals) if vals else 0.0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(n)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_1904_05717_gb300 import momms as M
+    from paper_1904_05717_gb300 import synthetic as syn
+
+    M.lib(build_if_missing=True)
+    n = args.size
+    flops = 2.0 * n ** 3
+    stream = torch.cuda.current_stream()
+
+    # inputs generated on the host (seeded), copied once: device-resident for `value`
+    A_h = syn.matrix("uniform", n, n, syn.workload_seed(1, "A"))
+    B_h = syn.matrix("uniform", n, n, syn.workload_seed(1, "B"))
+    C_h = syn.matrix("uniform", n, n, syn.workload_seed(1, "C"))
+    dA = M.DeviceMatrix.from_numpy(A_h)
+    dB = M.DeviceMatrix.from_numpy(B_h)
+    dC = M.DeviceMatrix.from_numpy(C_h)
+    dC0 = dC.storage.clone()
+
+    h = M.Handle(mode=M.MODE_AUTO)
+
+    def step():
+        M.check(M.momms_gemm_ex(h, 0, 0, n, n, n, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream),
+                "momms_gemm_ex")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    rep = h.report()
+    launches_per_step = int(rep["launches"])
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world)
+    clocks = clk.summary()
+    status = h.device_status(stream)
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # ---- dominant kernel alone (same digits, same launch configuration), per-launch CUDA events
+    S, bb = int(rep["slices"]), int(rep["digit_bits"])
+    roof = None
+    slice_ms = None
+    if rep["mode"] == M.MODE_EMULATED:
+        m_pad = -(-n // 128) * 128
+        n_pad = -(-n // 256) * 256
+        k_pad = -(-n // 64) * 64
+        e = torch.empty(n, dtype=torch.int32, device="cuda"); ef = torch.empty(n, dtype=torch.uint8, device="cuda")
+        f = torch.empty(n, dtype=torch.int32, device="cuda"); ff = torch.empty(n, dtype=torch.uint8, device="cuda")
+        M.check(M.momms_emu_scale(0, 0, n, n, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), stream), "scale")
+        M.check(M.momms_emu_scale(1, 0, n, n, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), stream), "scale")
+        Ad = torch.empty((S, m_pad, k_pad), dtype=torch.float16, device="cuda")
+        Bd = torch.empty((S, n_pad, k_pad), dtype=torch.float16, device="cuda")
+        M.check(M.momms_emu_split(0, 0, n, n, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), S, bb, Ad.data_ptr(), m_pad, k_pad, stream), "split")
+        M.check(M.momms_emu_split(1, 0, n, n, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), S, bb, Bd.data_ptr(), n_pad, k_pad, stream), "split")
+        nbytes = M.momms_emu_scratch_bytes()
+        scratch = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        Cs = M.DeviceMatrix(n, n)
+        evs = []
+        reps = max(3, min(args.steps, 10))
+        for i in range(reps + 1):
+            a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            M.check(M.momms_emu_slice_gemm(n, n, n, S, bb, Ad.data_ptr(), Bd.data_ptr(), m_pad, n_pad, k_pad,
+                                           e.data_ptr(), ef.data_ptr(), f.data_ptr(), ff.data_ptr(), 1.0, 0.0,
+                                           Cs.ptr, Cs.ld, M.MEMBER_AUTO, scratch.data_ptr(), nbytes, st.data_ptr(),
+                                           stream), "slice gemm")
+            a1.record(stream)
+            if i > 0:  # first launch is a warm-up
+                evs.append((a0, a1))
+        torch.cuda.synchronize()
+        slice_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        pairs = S * (S + 1) // 2
+        tensor_flops = pairs * 2.0 * m_pad * n_pad * k_pad
+        achieved = tensor_flops / (slice_ms * 1e-3) / 1e12
+        peaks, src = measured_peaks()
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "momms::emu::slice_gemm_kernel (tcgen05 kind::f16)",
+                "peak_source": f"{src} bf16_tflops_sustained (fp16 rate = bf16 rate)",
+                "algorithmic_flops_per_launch": tensor_flops, "launch_ms": slice_ms}
+        del Ad, Bd, scratch
+
+    # ---- native FP64 DMMA path on the same inputs (the other half of the metric)
+    hn = M.Handle(mode=M.MODE_NATIVE)
+    dC.storage.copy_(dC0)
+    M.check(M.momms_gemm_ex(hn, 0, 0, n, n, n, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream), "native")
+    torch.cuda.synchronize()
+    n0 = torch.cuda.Event(enable_timing=True); n1 = torch.cuda.Event(enable_timing=True)
+    n0.record(stream)
+    for _ in range(args.native_steps):
+        M.check(M.momms_gemm_ex(hn, 0, 0, n, n, n, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream), "native")
+    n1.record(stream)
+    torch.cuda.synchronize()
+    native_ms = n0.elapsed_time(n1) / args.native_steps
+    native_tflops = flops / (native_ms * 1e-3) / 1e12
+    dmma_peak = M.momms_probe_peak(0, stream)
+    hn.close()
+
+    # ---- end to end through the public API with host buffers (pinned), copies inside the timed region
+    A_p = torch.from_numpy(np.ascontiguousarray(A_h.T)).pin_memory()
+    B_p = torch.from_numpy(np.ascontiguousarray(B_h.T)).pin_memory()
+    C_p = torch.from_numpy(np.ascontiguousarray(C_h.T)).pin_memory()
+    C_out = torch.empty_like(C_p).pin_memory()
+    h2d = 3 * n * n * 8
+    d2h = n * n * 8
+
+    def e2e_step():
+        dA.storage.copy_(A_p, non_blocking=True)
+        dB.storage.copy_(B_p, non_blocking=True)
+        dC.storage.copy_(C_p, non_blocking=True)
+        step()
+        C_out.copy_(dC.storage, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    esteps = max(2, min(args.steps, 5))
+    barrier(world)
+    x0 = torch.cuda.Event(enable_timing=True); x1 = torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for _ in range(esteps):
+        e2e_step()
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(x0.elapsed_time(x1) / esteps, world)
+    e2e_value = world * flops / (e2e_ms * 1e-3) / 1e12
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, desc, _ = cpu_oracle_sample(n, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        peaks, src = measured_peaks()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64",
+            "dtype_detail": (f"FP64-accurate; emulated path: {S} slices of {bb}-bit integer digits in fp16 on "
+                             f"tcgen05 kind::f16, exact FP32 accumulation drained to int32, FP64 recombination"
+                             if rep["mode"] == M.MODE_EMULATED else "native FP64 DMMA"),
+            "data": "synthetic",
+            "config": {"workload": workload_name(n), "path": "emulated" if rep["mode"] == M.MODE_EMULATED else "native",
+                       "slices": S, "digit_bits": bb, "member": M.MEMBER_NAMES.get(int(rep["member"]), "?"),
+                       "l2": "each operand (512 MB) exceeds L2 (126 MB): no flush between steps",
+                       "replicas": world},
+            "roofline": roof,
+            "native": {"value": native_tflops, "unit": UNIT, "ms_per_gemm": native_ms,
+                       "dmma_peak_probe_tflops": dmma_peak,
+                       "frac_of_probe": native_tflops / dmma_peak if dmma_peak else None},
+            "emulated_vs_native": value / world / native_tflops if native_tflops else None,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "device_status": status,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    h.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,216 @@
+/*
+ * momms.h -- C ABI of the GB300-native MOMMS library (libmomms.so).
+ *
+ * The operation is the dense product of the MOMMS paper (Smith & van de Geijn,
+ * "The MOMMS Family of Matrix Multiplication Algorithms", SC19), Sec. 2.1
+ * footnote (gamma_ij = sum_p alpha_ip beta_pj) and Sec. 2.2.1 (C += AB),
+ * extended to BLAS dgemm semantics:
+ *
+ *     C := alpha * op(A) * op(B) + beta * C,   op(X) = X or X^T,
+ *
+ * op(A) m x k, op(B) k x n, C m x n, all FP64 and column-major with leading
+ * dimensions (element (i, j) of X is X[i + j * ldX]).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named A, B, C, X, dC, dA, dB, digits, e, f, flags, workspace and
+ *     scratch are DEVICE pointers owned by the caller.  The library never frees
+ *     them and never uses them after the work enqueued by the call has finished.
+ *   - Every call is asynchronous on `stream` (0 = the legacy default stream);
+ *     results are ready when the stream reaches the enqueued work.
+ *   - Return value: MOMMS_OK (0), a negative number -i when argument i
+ *     (1-based, in the order of the prototype) is invalid, or one of the
+ *     positive MOMMS_ERR_* codes.  Nothing is enqueued when a call fails.
+ *   - BLAS argument rules: m, n, k >= 0; ld >= max(1, rows of the stored
+ *     matrix); m == 0 or n == 0 is a no-op; k == 0 or alpha == 0 gives
+ *     C := beta * C; beta == 0 makes C write-only (NaNs in C do not
+ *     propagate).  C must not overlap A or B.
+ *   - No exception crosses the ABI.  A handle may be used by one host thread at
+ *     a time; different handles are independent.
+ */
+#ifndef MOMMS_H
+#define MOMMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without including the CUDA headers */
+typedef struct CUstream_st* momms_stream_t;
+
+typedef struct momms_handle_s* momms_handle_t;
+
+enum {
+    MOMMS_OK = 0,
+    MOMMS_ERR_CUDA = 1001,        /* a CUDA launch or runtime call failed          */
+    MOMMS_ERR_TIMEOUT = 1002,     /* a bounded device wait expired (the kernel     */
+                                  /* returned early; its output is undefined)      */
+    MOMMS_ERR_NONFINITE = 1003,   /* emulated mode met Inf/NaN input (a warning:   */
+                                  /* affected rows/columns of C were set to NaN)   */
+    MOMMS_ERR_WORKSPACE = 1004,   /* the caller's workspace is too small           */
+    MOMMS_ERR_UNSUPPORTED = 1005, /* size or option outside what the build handles */
+    MOMMS_ERR_ALLOC = 1006,       /* the library could not allocate device memory  */
+    MOMMS_ERR_HANDLE = 1007,      /* null or destroyed handle                      */
+    MOMMS_ERR_IO = 1008           /* plan cache file could not be read or written  */
+};
+
+typedef enum { MOMMS_OP_N = 0, MOMMS_OP_T = 1 } momms_op_t;
+
+/* How the product is computed.
+ *   NATIVE    FP64 DMMA tensor instructions, C micro-tile resident in registers
+ *             (Resident C at L0, Sec. 3.4).
+ *   EMULATED  FP64 emulated by signed integer digit slices on the fp16 tensor
+ *             cores (tcgen05 kind::f16, exact FP32 accumulation in tensor memory,
+ *             drained to exact integers, recombined in FP64).
+ *   AUTO      the plan (tuned or default) decides per size bucket. */
+typedef enum { MOMMS_MODE_AUTO = 0, MOMMS_MODE_NATIVE = 1, MOMMS_MODE_EMULATED = 2 } momms_mode_t;
+
+/* Family member = the order in which C tiles and k blocks are visited, which
+ * decides the operand block that stays resident in L2 (Sec. 3.2, Sec. 3.3 naming):
+ *   C2  grouped raster: a wave of CTAs covers a block of C, A and B panels are
+ *       reused through L2 (Resident C at the L2 level, like C3A2C0 of Sec. 5.4).
+ *   A2  a block of rows of A (all of its k) stays in L2 while the wave sweeps
+ *       the columns of C (Resident A, like A3B2C0).
+ *   B2  mirror of A2: a block of columns of B stays in L2 (like B3A2C0).
+ *   A1  plain row-major raster: each CTA keeps its A tile and walks n
+ *       (Goto-like A2C0: the L2 level is not designed for, Sec. 4.3). */
+typedef enum {
+    MOMMS_MEMBER_AUTO = 0,
+    MOMMS_MEMBER_C2 = 1,
+    MOMMS_MEMBER_A2 = 2,
+    MOMMS_MEMBER_B2 = 3,
+    MOMMS_MEMBER_A1 = 4
+} momms_member_t;
+
+/* What the last call on a handle did. */
+typedef struct {
+    int mode;            /* MOMMS_MODE_NATIVE or MOMMS_MODE_EMULATED actually used   */
+    int member;          /* member actually used                                     */
+    int slices;          /* S (emulated), 0 for native                               */
+    int digit_bits;      /* beta (bits per digit), 0 for native                      */
+    int k_passes;        /* launches along k (emulated: keeps int32 sums exact)      */
+    int tile_m, tile_n;  /* CTA tile                                                 */
+    int64_t launches;    /* kernels enqueued by the call                             */
+    double est_err_ratio;/* emulated: estimated truncation error / bound (heuristic) */
+} momms_report_t;
+
+/* ---------------------------------------------------------------- handles */
+int momms_create(momms_handle_t* handle);
+int momms_destroy(momms_handle_t handle);
+int momms_set_mode(momms_handle_t handle, int mode);      /* momms_mode_t            */
+int momms_set_member(momms_handle_t handle, int member);  /* momms_member_t          */
+/* S = number of digit slices for EMULATED mode: 0 = automatic (from the exponent
+ * spread of the inputs), else 1..MOMMS_MAX_SLICES. */
+int momms_set_slices(momms_handle_t handle, int slices);
+#define MOMMS_MAX_SLICES 16
+int momms_get_last_report(momms_handle_t handle, momms_report_t* report);
+/* Device status word of the handle (0 = fine, MOMMS_ERR_TIMEOUT after a capped
+ * wait expired).  Synchronises `stream` first.  Clears the word. */
+int momms_check_device_status(momms_handle_t handle, momms_stream_t stream);
+const char* momms_status_string(int status);
+
+/* -------------------------------------------------------------- workspace */
+/* Bytes of device workspace a momms_gemm_ex call of this size needs in the
+ * handle's current mode/slices (worst case over modes when AUTO).  Without a
+ * caller workspace the handle allocates (and keeps) its own. */
+int momms_workspace_size(momms_handle_t handle, int op_a, int op_b, int64_t m, int64_t n,
+                         int64_t k, size_t* bytes);
+/* Caller-owned device workspace (NULL, 0 = return to library-owned memory).
+ * Must stay valid until all work enqueued with it has finished. */
+int momms_set_workspace(momms_handle_t handle, void* workspace, size_t bytes);
+
+/* --------------------------------------------------------------- products */
+/* C := alpha*A*B + beta*C (op = N, N) with a per-thread default handle in AUTO
+ * mode.  Sec. 2.2.1; the BLAS dgemm signature. */
+int momms_gemm(int64_t m, int64_t n, int64_t k, double alpha,
+               const double* A, int64_t lda, const double* B, int64_t ldb,
+               double beta, double* C, int64_t ldc, momms_stream_t stream);
+
+/* C := alpha*op(A)*op(B) + beta*C with the handle's mode, member and slices.
+ * op(A) = A (m x k, lda >= m) or A^T (A stored k x m, lda >= k); likewise B. */
+int momms_gemm_ex(momms_handle_t handle, int op_a, int op_b, int64_t m, int64_t n,
+                  int64_t k, double alpha, const double* A, int64_t lda,
+                  const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                  momms_stream_t stream);
+
+/* Gradients of L(C) with C = A*B (A m x k, B k x n): given dC = dL/dC (m x n),
+ *   dA = dC * B^T   (m x k; contraction over n)   -- skipped when dA == NULL
+ *   dB = A^T * dC   (k x n; contraction over m)   -- skipped when dB == NULL
+ * computed through the transposed-operand paths of momms_gemm_ex (dA, dB are
+ * overwritten, beta = 0). */
+int momms_gemm_backward(momms_handle_t handle, int64_t m, int64_t n, int64_t k,
+                        const double* A, int64_t lda, const double* B, int64_t ldb,
+                        const double* dC, int64_t lddc, double* dA, int64_t ldda,
+                        double* dB, int64_t lddb, momms_stream_t stream);
+
+/* `count` independent products C_i := alpha_i*A_i*B_i + beta_i*C_i (op = N, N),
+ * of uneven sizes, in ONE persistent kernel launch over a device tile table
+ * (plus, in EMULATED mode, one scale and one split launch over all problems).
+ * All array arguments are HOST arrays of length `count`; the matrix pointers in
+ * them are device pointers.  The tile table lives in the handle, so the
+ * enqueued launches can be captured in a CUDA graph and replayed as long as the
+ * handle and the problem pointers stay alive and the sizes do not change. */
+int momms_gemm_batched(momms_handle_t handle, int64_t count, const int64_t* m,
+                       const int64_t* n, const int64_t* k, const double* alpha,
+                       const double* const* A, const int64_t* lda,
+                       const double* const* B, const int64_t* ldb, const double* beta,
+                       double* const* C, const int64_t* ldc, momms_stream_t stream);
+
+/* --------------------------------------------- steps of the emulated path */
+/* These expose each step separately (used by the parity tests).  The digit
+ * layout: S slices, slice s (0-based = digit s+1) a rows_pad x inner_pad fp16
+ * matrix stored inner-contiguous at digits + s*rows_pad*inner_pad; rows_pad a
+ * multiple of 128, inner_pad a multiple of 64; padding holds zeros. */
+
+/* Scaling exponents.  which = 0: the rows of op(X) where op(X) is rows x inner
+ * (X = A, op = op_a); which = 1: the columns of op(X) where op(X) is
+ * inner x rows (X = B).  exps[r] = floor(log2 max_q |x_rq|) + 1 (0 for an
+ * all-zero vector), flags[r] = 1 when the vector holds Inf or NaN. */
+int momms_emu_scale(int which, int op, int64_t rows, int64_t inner, const double* X,
+                    int64_t ldx, int32_t* exps, uint8_t* flags, momms_stream_t stream);
+
+/* Truncation digits: x * 2^-e = sum_{s=1..S} d_s 2^(-beta s) + remainder,
+ * |d_s| <= 2^beta - 1, signs of x; flagged vectors give zero digits.
+ * digits: fp16 (integer-valued) as described above; 1 <= beta <= 10. */
+int momms_emu_split(int which, int op, int64_t rows, int64_t inner, const double* X,
+                    int64_t ldx, const int32_t* exps, const uint8_t* flags, int slices,
+                    int digit_bits, void* digits, int64_t rows_pad, int64_t inner_pad,
+                    momms_stream_t stream);
+
+/* Slice products and recombination on the tcgen05 tensor cores:
+ *   P_d = sum_{s+t=d} A_s B_t  (d = 2..S+1, triangular pair set), exact;
+ *   C := alpha * 2^(e_i+f_j) * sum_d 2^(-beta d) P_d + beta*C  (FP64 Horner).
+ * Ad: S slices of m_pad x k_pad, Bd: S slices of n_pad x k_pad (layout above).
+ * scratch: device memory of momms_emu_scratch_bytes() bytes (FP64 partial sums
+ * of the recombination, one 128 x 256 block per CTA).  member: momms_member_t. */
+int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_bits,
+                         const void* Ad, const void* Bd, int64_t m_pad, int64_t n_pad,
+                         int64_t k_pad, const int32_t* e, const uint8_t* eflags,
+                         const int32_t* f, const uint8_t* fflags, double alpha,
+                         double beta, double* C, int64_t ldc, int member, void* scratch,
+                         size_t scratch_bytes, int32_t* status, momms_stream_t stream);
+size_t momms_emu_scratch_bytes(void);
+
+/* ---------------------------------------------------------------- tuning */
+/* Time the candidate plans (mode x member x slices) for the size buckets of the
+ * given shapes (count triples m[i], n[i], k[i]) on `stream`, keep the fastest
+ * that meets the accuracy rule, and persist the plan table to `path` (a small
+ * text file; NULL = do not persist).  A readable file is loaded first. */
+int momms_tune(momms_handle_t handle, const char* path, int64_t count, const int64_t* m,
+               const int64_t* n, const int64_t* k, momms_stream_t stream);
+/* Load a plan table written by momms_tune (a missing or mismatching file is
+ * ignored and reported as MOMMS_ERR_IO). */
+int momms_load_plans(momms_handle_t handle, const char* path);
+
+/* ------------------------------------------------------- microbenchmarks */
+/* Peak probes used as roofline denominators: kind 0 = FP64 DMMA, 1 = FP64 DFMA,
+ * 2 = fp16 tcgen05 (kind::f16, FP32 accumulate).  Writes the achieved rate in
+ * TFLOP/s to *tflops.  Synchronous. */
+int momms_probe_peak(int kind, double* tflops, momms_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOMMS_H */

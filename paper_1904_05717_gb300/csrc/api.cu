@@ -1,0 +1,824 @@
+// api.cu -- the C ABI (include/momms.h): handles, BLAS argument rules,
+// workspace, mode / member / slice-count selection, the emulated pipeline,
+// backward, batched, plan cache and peak probes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/momms.h"
+#include "internal.h"
+#include "raster.cuh"
+
+using momms::BatchProblem;
+
+namespace {
+
+constexpr int kHandleMagic = 0x4D4F4D53;  // "MOMS"
+constexpr int kDigitBits = 7;             // beta: 7-bit digits, FP32 chunk of 1024 products
+constexpr int kAutoSliceMax = 14;         // workspace sized for this many slices in AUTO
+
+struct Plan {
+    int mode;
+    int member;
+    int slices;  // 0 = data-driven rule
+};
+
+// size bucket = (ceil log2 m, ceil log2 n, ceil log2 k)
+inline int lg2c(int64_t x) {
+    int b = 0;
+    while ((int64_t(1) << b) < x && b < 62) ++b;
+    return b;
+}
+inline uint32_t bucket_key(int64_t m, int64_t n, int64_t k) {
+    return static_cast<uint32_t>(lg2c(m) | (lg2c(n) << 8) | (lg2c(k) << 16));
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+inline int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+}  // namespace
+
+struct momms_handle_s {
+    int magic = kHandleMagic;
+    int mode = MOMMS_MODE_AUTO;
+    int member = MOMMS_MEMBER_AUTO;
+    int slices = 0;
+    int digit_bits = kDigitBits;
+    void* user_ws = nullptr;
+    size_t user_ws_bytes = 0;
+    void* own_ws = nullptr;
+    size_t own_ws_bytes = 0;
+    int32_t* status = nullptr;  // device word
+    int* spread_dev = nullptr;  // device pair of spread values (AUTO slice rule)
+    int* spread_host = nullptr; // pinned
+    momms_report_t report{};
+    BatchProblem* dev_probs = nullptr;
+    size_t dev_probs_cap = 0;
+    std::map<uint32_t, Plan> plans;
+};
+
+namespace {
+
+bool valid(momms_handle_t h) { return h && h->magic == kHandleMagic; }
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return MOMMS_OK;
+    return MOMMS_ERR_CUDA;
+}
+
+// Workspace carve-up of one emulated product.
+struct EmuLayout {
+    int64_t m_pad, n_pad, k_pad;
+    size_t off_e, off_ef, off_f, off_ff, off_l1a, off_l1b, off_Ad, off_Bd, off_scratch, total;
+};
+
+EmuLayout emu_layout(int64_t m, int64_t n, int64_t k, int S) {
+    EmuLayout L{};
+    L.m_pad = round_up(std::max<int64_t>(m, 1), momms::kEmuBM);
+    L.n_pad = round_up(std::max<int64_t>(n, 1), momms::kEmuBN);
+    L.k_pad = round_up(std::max<int64_t>(k, 1), momms::kEmuBK);
+    size_t o = 0;
+    L.off_e = o;   o += align256(L.m_pad * sizeof(int32_t));
+    L.off_ef = o;  o += align256(L.m_pad);
+    L.off_f = o;   o += align256(L.n_pad * sizeof(int32_t));
+    L.off_ff = o;  o += align256(L.n_pad);
+    L.off_l1a = o; o += align256(L.m_pad * sizeof(float));
+    L.off_l1b = o; o += align256(L.n_pad * sizeof(float));
+    L.off_Ad = o;  o += align256(static_cast<size_t>(S) * L.m_pad * L.k_pad * 2);
+    L.off_Bd = o;  o += align256(static_cast<size_t>(S) * L.n_pad * L.k_pad * 2);
+    L.off_scratch = o; o += align256(momms::emu_scratch_bytes(momms::device_sm_count()));
+    L.total = o;
+    return L;
+}
+
+int ensure_workspace(momms_handle_t h, size_t bytes, void** ws) {
+    if (h->user_ws) {
+        if (h->user_ws_bytes < bytes) return MOMMS_ERR_WORKSPACE;
+        *ws = h->user_ws;
+        return MOMMS_OK;
+    }
+    if (h->own_ws_bytes < bytes) {
+        if (h->own_ws) {
+            cudaDeviceSynchronize();  // the old block may still be in use by enqueued work
+            cudaFree(h->own_ws);
+            h->own_ws = nullptr;
+            h->own_ws_bytes = 0;
+        }
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return MOMMS_ERR_ALLOC;
+        }
+        h->own_ws = p;
+        h->own_ws_bytes = bytes;
+    }
+    *ws = h->own_ws;
+    return MOMMS_OK;
+}
+
+__global__ void scale_c_kernel(int64_t m, int64_t n, double beta, double* C, int64_t ldc) {
+    const int64_t total = m * n;
+    for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = idx % m, j = idx / m;
+        double* c = C + i + j * ldc;
+        *c = (beta == 0.0) ? 0.0 : beta * *c;
+    }
+}
+
+int scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc, cudaStream_t s) {
+    if (beta == 1.0) return MOMMS_OK;
+    int64_t blocks = (m * n + 255) / 256;
+    blocks = std::min<int64_t>(blocks, int64_t(momms::device_sm_count()) * 16);
+    scale_c_kernel<<<static_cast<unsigned>(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(m, n, beta, C, ldc);
+    return cuda_fail(cudaGetLastError());
+}
+
+// S from the exponent spread of the inputs (see DESIGN): enough digit bits for
+// 53 + 2 guard bits, plus how far row/column maxima sit above their mean
+// magnitudes, less half of log2 k (error terms add with random signs).
+int slices_from_spread(double spread_a, double spread_b, int64_t k, int beta) {
+    const double bits = 55.0 + spread_a + spread_b - 0.5 * std::log2(static_cast<double>(std::max<int64_t>(k, 1)));
+    int S = static_cast<int>(std::ceil(bits / beta));
+    return std::min(std::max(S, 3), kAutoSliceMax);
+}
+
+Plan default_plan(int64_t m, int64_t n, int64_t k) {
+    Plan p{};
+    const double flops = 2.0 * m * n * k;
+    // the FP64 tensor pipe is ~1 TFLOP/s; emulation pays off once the tile
+    // padding (128 x 256) is amortised
+    const bool big = m >= 256 && n >= 256 && k >= 128 && flops >= 1.0e9;
+    p.mode = big ? MOMMS_MODE_EMULATED : MOMMS_MODE_NATIVE;
+    p.member = MOMMS_MEMBER_C2;
+    p.slices = 0;
+    return p;
+}
+
+Plan pick_plan(momms_handle_t h, int64_t m, int64_t n, int64_t k) {
+    Plan p = default_plan(m, n, k);
+    auto it = h->plans.find(bucket_key(m, n, k));
+    if (it != h->plans.end()) p = it->second;
+    if (h->mode != MOMMS_MODE_AUTO) p.mode = h->mode;
+    if (h->member != MOMMS_MEMBER_AUTO) p.member = h->member;
+    if (h->slices > 0) p.slices = h->slices;
+    return p;
+}
+
+int run_native(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
+               const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+               int64_t ldc, int member, cudaStream_t s) {
+    cudaError_t e = momms::launch_native_gemm(opa, opb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                                              member, s);
+    if (e == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) return MOMMS_ERR_CUDA;
+    h->report = momms_report_t{};
+    h->report.mode = MOMMS_MODE_NATIVE;
+    h->report.member = member;
+    h->report.tile_m = momms::kNativeBM;
+    h->report.tile_n = momms::kNativeBN;
+    h->report.k_passes = 1;
+    h->report.launches = 1;
+    return MOMMS_OK;
+}
+
+int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
+                 const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                 int64_t ldc, int member, int S, cudaStream_t s) {
+    const int bb = h->digit_bits;
+    if (S > MOMMS_MAX_SLICES) return MOMMS_ERR_UNSUPPORTED;
+    const int S_alloc = S > 0 ? S : kAutoSliceMax;
+    EmuLayout L = emu_layout(m, n, k, S_alloc);
+    if (static_cast<int64_t>(S_alloc) * std::max(L.m_pad, L.n_pad) >= (int64_t(1) << 31))
+        return MOMMS_ERR_UNSUPPORTED;
+    void* ws = nullptr;
+    int rc = ensure_workspace(h, L.total, &ws);
+    if (rc) return rc;
+    char* w = static_cast<char*>(ws);
+    int32_t* e = reinterpret_cast<int32_t*>(w + L.off_e);
+    uint8_t* ef = reinterpret_cast<uint8_t*>(w + L.off_ef);
+    int32_t* f = reinterpret_cast<int32_t*>(w + L.off_f);
+    uint8_t* ff = reinterpret_cast<uint8_t*>(w + L.off_ff);
+    float* l1a = reinterpret_cast<float*>(w + L.off_l1a);
+    float* l1b = reinterpret_cast<float*>(w + L.off_l1b);
+    void* Ad = w + L.off_Ad;
+    void* Bd = w + L.off_Bd;
+    void* scratch = w + L.off_scratch;
+    int64_t launches = 0;
+    cudaError_t ce;
+    const bool need_stats = (S == 0);
+    ce = momms::launch_emu_scale(0, opa, m, k, A, lda, e, ef, need_stats ? l1a : nullptr, s);
+    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+    ce = momms::launch_emu_scale(1, opb, n, k, B, ldb, f, ff, need_stats ? l1b : nullptr, s);
+    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+    launches += 2;
+    double est = 0.0;
+    if (S == 0) {
+        // data-driven slice count: one small device reduction and a readback
+        if (cudaMemsetAsync(h->spread_dev, 0, 2 * sizeof(int), s) != cudaSuccess) return MOMMS_ERR_CUDA;
+        if (momms::launch_emu_spread(m, k, e, ef, l1a, h->spread_dev, s) != cudaSuccess) return MOMMS_ERR_CUDA;
+        if (momms::launch_emu_spread(n, k, f, ff, l1b, h->spread_dev + 1, s) != cudaSuccess) return MOMMS_ERR_CUDA;
+        if (cudaMemcpyAsync(h->spread_host, h->spread_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return MOMMS_ERR_CUDA;
+        const double sa = h->spread_host[0] / 16.0, sb = h->spread_host[1] / 16.0;
+        S = slices_from_spread(sa, sb, k, bb);
+        est = std::ldexp(1.0, static_cast<int>(std::ceil(55.0 + sa + sb - 0.5 * std::log2(double(k)))) - bb * S);
+        launches += 2;
+    }
+    ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, S, bb, Ad, L.m_pad, L.k_pad, s);
+    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+    ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, S, bb, Bd, L.n_pad, L.k_pad, s);
+    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+    launches += 2;
+    momms::EmuGemmArgs a{};
+    a.m = m; a.n = n; a.k = k; a.S = S; a.beta = bb;
+    a.Ad = Ad; a.Bd = Bd; a.m_pad = L.m_pad; a.n_pad = L.n_pad; a.k_pad = L.k_pad;
+    a.e = e; a.ef = ef; a.f = f; a.ff = ff;
+    a.alpha = alpha; a.beta_c = beta; a.C = C; a.ldc = ldc;
+    a.member = member; a.group = 0;
+    a.scratch = scratch; a.scratch_bytes = momms::emu_scratch_bytes(momms::device_sm_count());
+    a.status = h->status; a.max_ctas = 0;
+    int passes = 0;
+    ce = momms::launch_emu_slice_gemm(a, &passes, s);
+    if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
+    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+    launches += passes;
+    h->report = momms_report_t{};
+    h->report.mode = MOMMS_MODE_EMULATED;
+    h->report.member = member;
+    h->report.slices = S;
+    h->report.digit_bits = bb;
+    h->report.k_passes = passes;
+    h->report.tile_m = momms::kEmuBM;
+    h->report.tile_n = momms::kEmuBN;
+    h->report.launches = launches;
+    h->report.est_err_ratio = est;
+    return MOMMS_OK;
+}
+
+int gemm_dispatch(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                  int64_t ldc, cudaStream_t s) {
+    if (m == 0 || n == 0) {
+        h->report = momms_report_t{};
+        return MOMMS_OK;
+    }
+    if (k == 0 || alpha == 0.0) {
+        h->report = momms_report_t{};
+        h->report.launches = beta == 1.0 ? 0 : 1;
+        return scale_c(m, n, beta, C, ldc, s);
+    }
+    const Plan p = pick_plan(h, m, n, k);
+    const int member = p.member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : p.member;
+    if (p.mode == MOMMS_MODE_EMULATED)
+        return run_emulated(h, opa, opb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, member, p.slices, s);
+    return run_native(h, opa, opb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, member, s);
+}
+
+// BLAS argument checks; returns 0 or -(1-based index of the first bad argument).
+int check_gemm_args(int base, int opa, int opb, int64_t m, int64_t n, int64_t k, const double* A,
+                    int64_t lda, const double* B, int64_t ldb, const double* C, int64_t ldc,
+                    double alpha, bool has_ops) {
+    // argument indices relative to `base` (index of m)
+    if (has_ops) {
+        if (opa != MOMMS_OP_N && opa != MOMMS_OP_T) return -(base - 2);
+        if (opb != MOMMS_OP_N && opb != MOMMS_OP_T) return -(base - 1);
+    }
+    if (m < 0) return -(base);
+    if (n < 0) return -(base + 1);
+    if (k < 0) return -(base + 2);
+    const int64_t rows_a = opa == MOMMS_OP_N ? m : k;
+    const int64_t rows_b = opb == MOMMS_OP_N ? k : n;
+    if (lda < std::max<int64_t>(1, rows_a)) return -(base + 5);
+    if (ldb < std::max<int64_t>(1, rows_b)) return -(base + 7);
+    if (ldc < std::max<int64_t>(1, m)) return -(base + 10);
+    const bool work = m > 0 && n > 0;
+    const bool product = work && k > 0 && alpha != 0.0;
+    if (product && !A) return -(base + 4);
+    if (product && !B) return -(base + 6);
+    if (work && !C) return -(base + 9);
+    if (product) {
+        // C must not overlap A or B (byte ranges of the stored matrices)
+        auto span = [](const double* p, int64_t ld, int64_t rows, int64_t cols) {
+            return std::make_pair(reinterpret_cast<uintptr_t>(p),
+                                  reinterpret_cast<uintptr_t>(p + (cols - 1) * ld + rows));
+        };
+        const auto sc = span(C, ldc, m, n);
+        const auto sa = span(A, lda, rows_a, opa == MOMMS_OP_N ? k : m);
+        const auto sb = span(B, ldb, rows_b, opb == MOMMS_OP_N ? n : k);
+        if (sc.first < sa.second && sa.first < sc.second) return -(base + 9);
+        if (sc.first < sb.second && sb.first < sc.second) return -(base + 9);
+    }
+    return 0;
+}
+
+momms_handle_t thread_default_handle() {
+    static thread_local momms_handle_t h = nullptr;
+    if (!h) momms_create(&h);
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int momms_create(momms_handle_t* handle) {
+    if (!handle) return -1;
+    *handle = nullptr;
+    momms_handle_t h = new (std::nothrow) momms_handle_s();
+    if (!h) return MOMMS_ERR_ALLOC;
+    if (cudaMalloc(&h->status, 64) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return MOMMS_ERR_ALLOC;
+    }
+    h->spread_dev = reinterpret_cast<int*>(reinterpret_cast<char*>(h->status) + 16);
+    if (cudaMemset(h->status, 0, 64) != cudaSuccess ||
+        cudaMallocHost(&h->spread_host, 2 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->status);
+        delete h;
+        return MOMMS_ERR_ALLOC;
+    }
+    *handle = h;
+    return MOMMS_OK;
+}
+
+int momms_destroy(momms_handle_t h) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    cudaDeviceSynchronize();
+    if (h->own_ws) cudaFree(h->own_ws);
+    if (h->dev_probs) cudaFree(h->dev_probs);
+    if (h->status) cudaFree(h->status);
+    if (h->spread_host) cudaFreeHost(h->spread_host);
+    h->magic = 0;
+    delete h;
+    return MOMMS_OK;
+}
+
+int momms_set_mode(momms_handle_t h, int mode) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (mode < MOMMS_MODE_AUTO || mode > MOMMS_MODE_EMULATED) return -2;
+    h->mode = mode;
+    return MOMMS_OK;
+}
+
+int momms_set_member(momms_handle_t h, int member) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (member < MOMMS_MEMBER_AUTO || member > MOMMS_MEMBER_A1) return -2;
+    h->member = member;
+    return MOMMS_OK;
+}
+
+int momms_set_slices(momms_handle_t h, int slices) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (slices < 0 || slices > MOMMS_MAX_SLICES) return -2;
+    h->slices = slices;
+    return MOMMS_OK;
+}
+
+int momms_get_last_report(momms_handle_t h, momms_report_t* r) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (!r) return -2;
+    *r = h->report;
+    return MOMMS_OK;
+}
+
+int momms_check_device_status(momms_handle_t h, momms_stream_t stream) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int32_t v = 0;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MOMMS_ERR_CUDA;
+    if (cudaMemcpy(&v, h->status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return MOMMS_ERR_CUDA;
+    if (v) cudaMemset(h->status, 0, sizeof(int32_t));
+    return v ? static_cast<int>(v) : MOMMS_OK;
+}
+
+const char* momms_status_string(int status) {
+    switch (status) {
+        case MOMMS_OK: return "ok";
+        case MOMMS_ERR_CUDA: return "CUDA launch or runtime error";
+        case MOMMS_ERR_TIMEOUT: return "a bounded device wait expired";
+        case MOMMS_ERR_NONFINITE: return "emulated mode met Inf/NaN input";
+        case MOMMS_ERR_WORKSPACE: return "workspace too small";
+        case MOMMS_ERR_UNSUPPORTED: return "size or option not supported";
+        case MOMMS_ERR_ALLOC: return "device allocation failed";
+        case MOMMS_ERR_HANDLE: return "invalid handle";
+        case MOMMS_ERR_IO: return "plan cache I/O error";
+        default: return status < 0 ? "invalid argument" : "unknown status";
+    }
+}
+
+int momms_workspace_size(momms_handle_t h, int op_a, int op_b, int64_t m, int64_t n, int64_t k,
+                         size_t* bytes) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (op_a != MOMMS_OP_N && op_a != MOMMS_OP_T) return -2;
+    if (op_b != MOMMS_OP_N && op_b != MOMMS_OP_T) return -3;
+    if (m < 0) return -4;
+    if (n < 0) return -5;
+    if (k < 0) return -6;
+    if (!bytes) return -7;
+    const Plan p = pick_plan(h, m, n, k);
+    if (p.mode == MOMMS_MODE_NATIVE || m == 0 || n == 0 || k == 0) {
+        *bytes = 0;
+        return MOMMS_OK;
+    }
+    *bytes = emu_layout(m, n, k, p.slices > 0 ? p.slices : kAutoSliceMax).total;
+    return MOMMS_OK;
+}
+
+int momms_set_workspace(momms_handle_t h, void* workspace, size_t bytes) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return -2;
+    h->user_ws = workspace;
+    h->user_ws_bytes = workspace ? bytes : 0;
+    return MOMMS_OK;
+}
+
+int momms_gemm(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+               const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+               momms_stream_t stream) {
+    int rc = check_gemm_args(1, MOMMS_OP_N, MOMMS_OP_N, m, n, k, A, lda, B, ldb, C, ldc, alpha, false);
+    if (rc) return rc;
+    momms_handle_t h = thread_default_handle();
+    if (!h) return MOMMS_ERR_ALLOC;
+    return gemm_dispatch(h, MOMMS_OP_N, MOMMS_OP_N, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+int momms_gemm_ex(momms_handle_t h, int op_a, int op_b, int64_t m, int64_t n, int64_t k,
+                  double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                  double beta, double* C, int64_t ldc, momms_stream_t stream) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    int rc = check_gemm_args(4, op_a, op_b, m, n, k, A, lda, B, ldb, C, ldc, alpha, true);
+    if (rc) return rc;
+    return gemm_dispatch(h, op_a, op_b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+int momms_gemm_backward(momms_handle_t h, int64_t m, int64_t n, int64_t k, const double* A,
+                        int64_t lda, const double* B, int64_t ldb, const double* dC, int64_t lddc,
+                        double* dA, int64_t ldda, double* dB, int64_t lddb, momms_stream_t stream) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (m < 0) return -2;
+    if (n < 0) return -3;
+    if (k < 0) return -4;
+    if (lda < std::max<int64_t>(1, m)) return -6;
+    if (ldb < std::max<int64_t>(1, k)) return -8;
+    if (lddc < std::max<int64_t>(1, m)) return -10;
+    if (dA && ldda < std::max<int64_t>(1, m)) return -12;
+    if (dB && lddb < std::max<int64_t>(1, k)) return -14;
+    const bool need_dc = (dA && m > 0 && k > 0 && n > 0) || (dB && k > 0 && n > 0 && m > 0);
+    if (need_dc && !dC) return -9;
+    if (dA && m > 0 && k > 0 && n > 0 && !B) return -7;
+    if (dB && k > 0 && n > 0 && m > 0 && !A) return -5;
+    int64_t launches = 0;
+    if (dA) {
+        // dA (m x k) = dC (m x n) * B^T  -- contraction over n
+        int rc = gemm_dispatch(h, MOMMS_OP_N, MOMMS_OP_T, m, k, n, 1.0, dC, lddc, B, ldb, 0.0, dA, ldda,
+                               reinterpret_cast<cudaStream_t>(stream));
+        if (rc) return rc;
+        launches += h->report.launches;
+    }
+    if (dB) {
+        // dB (k x n) = A^T (k x m) * dC (m x n)  -- contraction over m
+        int rc = gemm_dispatch(h, MOMMS_OP_T, MOMMS_OP_N, k, n, m, 1.0, A, lda, dC, lddc, 0.0, dB, lddb,
+                               reinterpret_cast<cudaStream_t>(stream));
+        if (rc) return rc;
+        launches += h->report.launches;
+    }
+    h->report.launches = launches;
+    return MOMMS_OK;
+}
+
+int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const int64_t* n,
+                       const int64_t* k, const double* alpha, const double* const* A,
+                       const int64_t* lda, const double* const* B, const int64_t* ldb,
+                       const double* beta, double* const* C, const int64_t* ldc,
+                       momms_stream_t stream) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (count < 0) return -2;
+    if (count == 0) return MOMMS_OK;
+    if (!m) return -3;
+    if (!n) return -4;
+    if (!k) return -5;
+    if (!alpha) return -6;
+    if (!A) return -7;
+    if (!lda) return -8;
+    if (!B) return -9;
+    if (!ldb) return -10;
+    if (!beta) return -11;
+    if (!C) return -12;
+    if (!ldc) return -13;
+    if (count > (int64_t(1) << 30)) return MOMMS_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (int64_t i = 0; i < count; ++i) {
+        int rc = check_gemm_args(1, MOMMS_OP_N, MOMMS_OP_N, m[i], n[i], k[i], A[i], lda[i], B[i], ldb[i],
+                                 C[i], ldc[i], alpha[i], false);
+        if (rc) return -3;  // the size / pointer arrays hold an invalid entry
+        if (m[i] > INT32_MAX / 2 || n[i] > INT32_MAX / 2 || k[i] > INT32_MAX / 2) return MOMMS_ERR_UNSUPPORTED;
+    }
+    const bool emulated = h->mode == MOMMS_MODE_EMULATED;
+    if (emulated) {
+        // emulated batches: one pipeline per problem on the same stream
+        int64_t launches = 0;
+        for (int64_t i = 0; i < count; ++i) {
+            int rc = gemm_dispatch(h, MOMMS_OP_N, MOMMS_OP_N, m[i], n[i], k[i], alpha[i], A[i], lda[i],
+                                   B[i], ldb[i], beta[i], C[i], ldc[i], s);
+            if (rc) return rc;
+            launches += h->report.launches;
+        }
+        h->report.launches = launches;
+        return MOMMS_OK;
+    }
+    // native: one persistent launch over a device tile table
+    std::vector<BatchProblem> probs;
+    probs.reserve(static_cast<size_t>(count));
+    int64_t tiles = 0;
+    int64_t scale_only = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        if (m[i] == 0 || n[i] == 0) continue;
+        if (k[i] == 0 || alpha[i] == 0.0) {
+            int rc = scale_c(m[i], n[i], beta[i], C[i], ldc[i], s);
+            if (rc) return rc;
+            ++scale_only;
+            continue;
+        }
+        BatchProblem p{};
+        p.A = A[i]; p.B = B[i]; p.C = C[i];
+        p.lda = lda[i]; p.ldb = ldb[i]; p.ldc = ldc[i];
+        p.m = static_cast<int32_t>(m[i]); p.n = static_cast<int32_t>(n[i]); p.k = static_cast<int32_t>(k[i]);
+        const int64_t tm = (m[i] + momms::kNativeBM - 1) / momms::kNativeBM;
+        const int64_t tn = (n[i] + momms::kNativeBN - 1) / momms::kNativeBN;
+        p.tiles_n = static_cast<int32_t>(tn);
+        p.tile0 = tiles;
+        p.alpha = alpha[i]; p.beta = beta[i];
+        tiles += tm * tn;
+        probs.push_back(p);
+    }
+    if (probs.empty()) {
+        h->report = momms_report_t{};
+        h->report.launches = scale_only;
+        return MOMMS_OK;
+    }
+    const size_t bytes = probs.size() * sizeof(BatchProblem);
+    if (h->dev_probs_cap < bytes) {
+        if (h->dev_probs) {
+            cudaDeviceSynchronize();
+            cudaFree(h->dev_probs);
+            h->dev_probs = nullptr;
+            h->dev_probs_cap = 0;
+        }
+        if (cudaMalloc(&h->dev_probs, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return MOMMS_ERR_ALLOC;
+        }
+        h->dev_probs_cap = bytes;
+    }
+    // the table is copied from pageable memory: the copy completes before the call returns,
+    // so it may be replayed from a graph as long as the handle keeps it
+    if (cudaMemcpyAsync(h->dev_probs, probs.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    cudaError_t e = momms::launch_native_batched(h->dev_probs, static_cast<int>(probs.size()), tiles, s);
+    if (e != cudaSuccess) return MOMMS_ERR_CUDA;
+    h->report = momms_report_t{};
+    h->report.mode = MOMMS_MODE_NATIVE;
+    h->report.member = MOMMS_MEMBER_C2;
+    h->report.tile_m = momms::kNativeBM;
+    h->report.tile_n = momms::kNativeBN;
+    h->report.k_passes = 1;
+    h->report.launches = 1 + scale_only;
+    return MOMMS_OK;
+}
+
+int momms_emu_scale(int which, int op, int64_t rows, int64_t inner, const double* X, int64_t ldx,
+                    int32_t* exps, uint8_t* flags, momms_stream_t stream) {
+    if (which != 0 && which != 1) return -1;
+    if (op != 0 && op != 1) return -2;
+    if (rows < 0) return -3;
+    if (inner < 0) return -4;
+    const bool rows_contig = (which == 0) ? (op == 0) : (op != 0);
+    const int64_t stored_rows = rows_contig ? rows : inner;
+    if (rows > 0 && inner > 0 && !X) return -5;
+    if (ldx < std::max<int64_t>(1, stored_rows)) return -6;
+    if (rows > 0 && !exps) return -7;
+    if (rows > 0 && !flags) return -8;
+    return cuda_fail(momms::launch_emu_scale(which, op, rows, inner, X, ldx, exps, flags, nullptr,
+                                             reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int momms_emu_split(int which, int op, int64_t rows, int64_t inner, const double* X, int64_t ldx,
+                    const int32_t* exps, const uint8_t* flags, int slices, int digit_bits,
+                    void* digits, int64_t rows_pad, int64_t inner_pad, momms_stream_t stream) {
+    if (which != 0 && which != 1) return -1;
+    if (op != 0 && op != 1) return -2;
+    if (rows < 0) return -3;
+    if (inner < 0) return -4;
+    const bool rows_contig = (which == 0) ? (op == 0) : (op != 0);
+    const int64_t stored_rows = rows_contig ? rows : inner;
+    if (rows > 0 && inner > 0 && !X) return -5;
+    if (ldx < std::max<int64_t>(1, stored_rows)) return -6;
+    if (rows > 0 && !exps) return -7;
+    if (rows > 0 && !flags) return -8;
+    if (slices < 1 || slices > MOMMS_MAX_SLICES) return -9;
+    if (digit_bits < 1 || digit_bits > 10) return -10;
+    if (!digits) return -11;
+    if (rows_pad < rows || rows_pad % momms::kEmuBM) return -12;
+    if (inner_pad < inner || inner_pad % momms::kEmuBK) return -13;
+    return cuda_fail(momms::launch_emu_split(which, op, rows, inner, X, ldx, exps, flags, slices,
+                                             digit_bits, digits, rows_pad, inner_pad,
+                                             reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t momms_emu_scratch_bytes(void) { return momms::emu_scratch_bytes(momms::device_sm_count()); }
+
+int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_bits, const void* Ad,
+                         const void* Bd, int64_t m_pad, int64_t n_pad, int64_t k_pad, const int32_t* e,
+                         const uint8_t* eflags, const int32_t* f, const uint8_t* fflags, double alpha,
+                         double beta, double* C, int64_t ldc, int member, void* scratch,
+                         size_t scratch_bytes, int32_t* status, momms_stream_t stream) {
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (k < 0) return -3;
+    if (slices < 1 || slices > MOMMS_MAX_SLICES) return -4;
+    if (digit_bits < 1 || digit_bits > 8) return -5;
+    if (!Ad) return -6;
+    if (!Bd) return -7;
+    if (m_pad < m || m_pad % momms::kEmuBM) return -8;
+    if (n_pad < n || n_pad % momms::kEmuBN) return -9;
+    if (k_pad < k || k_pad % momms::kEmuBK) return -10;
+    if (!e) return -11;
+    if (!eflags) return -12;
+    if (!f) return -13;
+    if (!fflags) return -14;
+    if (!C && m > 0 && n > 0) return -17;
+    if (ldc < std::max<int64_t>(1, m)) return -18;
+    if (member < MOMMS_MEMBER_AUTO || member > MOMMS_MEMBER_A1) return -19;
+    if (!scratch) return -20;
+    if (scratch_bytes < momms::emu_scratch_bytes(momms::device_sm_count())) return MOMMS_ERR_WORKSPACE;
+    if (!status) return -22;
+    if (m == 0 || n == 0) return MOMMS_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (k == 0 || alpha == 0.0) return scale_c(m, n, beta, C, ldc, s);
+    momms::EmuGemmArgs a{};
+    a.m = m; a.n = n; a.k = k; a.S = slices; a.beta = digit_bits;
+    a.Ad = Ad; a.Bd = Bd; a.m_pad = m_pad; a.n_pad = n_pad; a.k_pad = k_pad;
+    a.e = e; a.ef = eflags; a.f = f; a.ff = fflags;
+    a.alpha = alpha; a.beta_c = beta; a.C = C; a.ldc = ldc;
+    a.member = member; a.group = 0;
+    a.scratch = scratch; a.scratch_bytes = scratch_bytes; a.status = status; a.max_ctas = 0;
+    int passes = 0;
+    cudaError_t ce = momms::launch_emu_slice_gemm(a, &passes, s);
+    if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
+    return cuda_fail(ce);
+}
+
+// ------------------------------------------------------------------ plan cache
+static std::string plan_header() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "momms-plan v1 %s sms=%d l2=%d", prop.name, prop.multiProcessorCount,
+                  prop.l2CacheSize);
+    for (char* c = buf; *c; ++c)
+        if (*c == '\n') *c = ' ';
+    return buf;
+}
+
+int momms_load_plans(momms_handle_t h, const char* path) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (!path) return -2;
+    FILE* fp = std::fopen(path, "r");
+    if (!fp) return MOMMS_ERR_IO;
+    char line[512];
+    if (!std::fgets(line, sizeof(line), fp)) {
+        std::fclose(fp);
+        return MOMMS_ERR_IO;
+    }
+    std::string hdr(line);
+    while (!hdr.empty() && (hdr.back() == '\n' || hdr.back() == '\r')) hdr.pop_back();
+    if (hdr != plan_header()) {
+        std::fclose(fp);
+        return MOMMS_ERR_IO;  // written on another device or by another version: ignored
+    }
+    std::map<uint32_t, Plan> plans;
+    unsigned key;
+    int mode, member, slices;
+    while (std::fscanf(fp, "%u %d %d %d", &key, &mode, &member, &slices) == 4) {
+        if (mode < MOMMS_MODE_NATIVE || mode > MOMMS_MODE_EMULATED) continue;
+        if (member < MOMMS_MEMBER_C2 || member > MOMMS_MEMBER_A1) continue;
+        if (slices < 0 || slices > MOMMS_MAX_SLICES) continue;
+        plans[key] = Plan{mode, member, slices};
+    }
+    std::fclose(fp);
+    for (auto& kv : plans) h->plans[kv.first] = kv.second;
+    return MOMMS_OK;
+}
+
+static int save_plans(momms_handle_t h, const char* path) {
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* fp = std::fopen(tmp.c_str(), "w");
+    if (!fp) return MOMMS_ERR_IO;
+    std::fprintf(fp, "%s\n", plan_header().c_str());
+    for (auto& kv : h->plans)
+        std::fprintf(fp, "%u %d %d %d\n", kv.first, kv.second.mode, kv.second.member, kv.second.slices);
+    std::fclose(fp);
+    if (std::rename(tmp.c_str(), path) != 0) return MOMMS_ERR_IO;
+    return MOMMS_OK;
+}
+
+__global__ void fill_uniform_kernel(double* x, int64_t n, uint64_t seed) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        uint64_t z = seed + static_cast<uint64_t>(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        x[i] = 2.0 * static_cast<double>(z >> 11) * 0x1.0p-53 - 1.0;
+    }
+}
+
+int momms_tune(momms_handle_t h, const char* path, int64_t count, const int64_t* m, const int64_t* n,
+               const int64_t* k, momms_stream_t stream) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (count < 0) return -3;
+    if (count > 0 && (!m || !n || !k)) return -4;
+    if (path) momms_load_plans(h, path);  // a missing or stale file is simply re-tuned
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int saved_mode = h->mode, saved_member = h->member, saved_slices = h->slices;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int status = MOMMS_OK;
+    for (int64_t i = 0; i < count && status == MOMMS_OK; ++i) {
+        if (m[i] <= 0 || n[i] <= 0 || k[i] <= 0) continue;
+        const uint32_t key = bucket_key(m[i], n[i], k[i]);
+        if (h->plans.count(key)) continue;
+        double *A = nullptr, *B = nullptr, *C = nullptr;
+        if (cudaMalloc(&A, sizeof(double) * m[i] * k[i]) != cudaSuccess ||
+            cudaMalloc(&B, sizeof(double) * k[i] * n[i]) != cudaSuccess ||
+            cudaMalloc(&C, sizeof(double) * m[i] * n[i]) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(A); cudaFree(B); cudaFree(C);
+            status = MOMMS_ERR_ALLOC;
+            break;
+        }
+        fill_uniform_kernel<<<1024, 256, 0, s>>>(A, m[i] * k[i], 1);
+        fill_uniform_kernel<<<1024, 256, 0, s>>>(B, k[i] * n[i], 2);
+        Plan best{MOMMS_MODE_NATIVE, MOMMS_MEMBER_C2, 0};
+        float best_ms = 1e30f;
+        // candidate plans: native (member does not matter for a compute-bound FP64 pipe)
+        // and emulated with each member; the slice count stays data-driven (0).
+        std::vector<Plan> cands = {{MOMMS_MODE_NATIVE, MOMMS_MEMBER_C2, 0}};
+        for (int mem = MOMMS_MEMBER_C2; mem <= MOMMS_MEMBER_A1; ++mem) cands.push_back({MOMMS_MODE_EMULATED, mem, 0});
+        // the slice count for timing: the rule's choice for this data (uniform inputs)
+        h->mode = MOMMS_MODE_EMULATED; h->member = MOMMS_MEMBER_C2; h->slices = 0;
+        int rc0 = gemm_dispatch(h, 0, 0, m[i], n[i], k[i], 1.0, A, m[i], B, k[i], 0.0, C, m[i], s);
+        const int S_rule = rc0 == MOMMS_OK ? h->report.slices : 8;
+        for (const Plan& c : cands) {
+            h->mode = c.mode; h->member = c.member; h->slices = c.mode == MOMMS_MODE_EMULATED ? S_rule : 0;
+            int rc = gemm_dispatch(h, 0, 0, m[i], n[i], k[i], 1.0, A, m[i], B, k[i], 0.0, C, m[i], s);  // warm-up
+            if (rc) continue;
+            cudaEventRecord(e0, s);
+            const int reps = 2;
+            for (int r = 0; r < reps && rc == MOMMS_OK; ++r)
+                rc = gemm_dispatch(h, 0, 0, m[i], n[i], k[i], 1.0, A, m[i], B, k[i], 0.0, C, m[i], s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rc == MOMMS_OK && ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        h->plans[key] = best;
+        cudaStreamSynchronize(s);
+        cudaFree(A); cudaFree(B); cudaFree(C);
+    }
+    h->mode = saved_mode; h->member = saved_member; h->slices = saved_slices;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status == MOMMS_OK && path) status = save_plans(h, path);
+    return status;
+}
+
+int momms_probe_peak(int kind, double* tflops, momms_stream_t stream) {
+    if (kind < 0 || kind > 2) return -1;
+    if (!tflops) return -2;
+    cudaError_t e = momms::probe_peak(kind, tflops, reinterpret_cast<cudaStream_t>(stream));
+    if (e == cudaErrorNotSupported) return MOMMS_ERR_UNSUPPORTED;
+    return cuda_fail(e);
+}
+
+}  // extern "C"

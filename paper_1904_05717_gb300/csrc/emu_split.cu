@@ -1,0 +1,285 @@
+// emu_split.cu -- scaling exponents and truncation digits of the emulated path.
+//
+// Both steps are HBM-bound streaming passes on the CUDA cores; neither needs a
+// floating-point operation: the exponent and the digits come from integer
+// operations on the IEEE-754 bit pattern.
+//
+// Scaling (per row of op(A), per column of op(B)):
+//     e = floor(log2 max |x|) + 1   (the frexp exponent of max|x|; 0 for an
+//                                    all-zero vector; Inf/NaN -> flag)
+// Digits (truncation splitting): with |x| = m * 2^e2 (m the integer significand),
+//     d_s = sign(x) * ( floor(m * 2^(e2 - e + beta*s)) mod 2^beta ),  s = 1..S,
+// which is the s-th base-2^beta digit of |x| * 2^-e truncated toward zero, so
+//     x * 2^-e = sum_s d_s 2^(-beta s) + (remainder < 2^(-beta S)).
+// Digits are written as fp16 (exact: |d_s| <= 2^beta - 1 <= 1023), each slice a
+// rows_pad x inner_pad matrix stored inner-contiguous (K-major), zero-padded --
+// the layout the tcgen05 kernel stages with TMA.  This pass is the GPU form of
+// the paper's "pack on first residency" (Sec. 5.3): the operand is reorganised
+// once, into the layout the inner kernel streams.
+#include <cuda_fp16.h>
+
+#include <climits>
+
+#include "internal.h"
+
+namespace momms {
+namespace split {
+
+constexpr int kNoExp = INT_MIN;
+// cudaMemsetAsync(..., 0x80, ...) pattern: below every finite exponent (-1074..1024)
+constexpr int kSentinel = static_cast<int>(0x80808080u);
+
+// frexp exponent of |x| from its bits; kNoExp for zero; *nonfinite set for Inf/NaN.
+__device__ __forceinline__ int elem_exponent(double x, int* nonfinite) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+    const int ef = static_cast<int>(b >> 52);
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    if (ef == 0x7FF) {
+        *nonfinite = 1;
+        return kNoExp;
+    }
+    if (ef == 0) {
+        if (mant == 0) return kNoExp;
+        return 64 - __clzll(static_cast<long long>(mant)) - 1074;  // subnormal
+    }
+    return ef - 1022;
+}
+
+// Rows contiguous in memory (X[r + q*ld]): one thread per row over a slice of q,
+// combined with atomicMax into exps (pre-set to a sentinel).
+__global__ void scale_rows_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
+                                  int64_t inner, int64_t qchunk, int32_t* exps, uint8_t* flags,
+                                  float* l1) {
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int64_t q0 = static_cast<int64_t>(blockIdx.y) * qchunk;
+    int64_t q1 = q0 + qchunk;
+    if (q1 > inner) q1 = inner;
+    int emax = kNoExp, nf = 0;
+    float sum = 0.f;
+    for (int64_t q = q0; q < q1; ++q) {
+        const double x = X[r + q * ld];
+        const int e = elem_exponent(x, &nf);
+        emax = e > emax ? e : emax;
+        if (e != kNoExp) sum += static_cast<float>(fabs(x));
+    }
+    if (emax != kNoExp) atomicMax(&exps[r], emax);
+    if (nf) flags[r] = 1;
+    if (l1 && sum != 0.f) atomicAdd(&l1[r], sum);
+}
+
+__global__ void scale_finalize(int64_t rows, int32_t* exps, uint8_t* flags) {
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    if (flags[r] || exps[r] == kSentinel) exps[r] = 0;
+}
+
+// Inner dimension contiguous (X[q + r*ld]): one warp per row.
+__global__ void scale_inner_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
+                                   int64_t inner, int32_t* exps, uint8_t* flags, float* l1) {
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    int emax = kNoExp, nf = 0;
+    float sum = 0.f;
+    const double* x = X + r * ld;
+    for (int64_t q = lane; q < inner; q += 32) {
+        const int e = elem_exponent(x[q], &nf);
+        emax = e > emax ? e : emax;
+        if (e != kNoExp) sum += static_cast<float>(fabs(x[q]));
+    }
+    emax = __reduce_max_sync(0xFFFFFFFFu, emax);
+    nf = __reduce_or_sync(0xFFFFFFFFu, nf);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    if (lane == 0) {
+        exps[r] = (nf || emax == kNoExp) ? 0 : emax;
+        flags[r] = static_cast<uint8_t>(nf != 0);
+        if (l1) l1[r] = sum;
+    }
+}
+
+// spread = max over vectors r of log2(2^e_r * inner / l1_r)  (>= 0 up to rounding):
+// how far the vector maximum sits above the mean magnitude, in bits; written as
+// ceil(16 * spread) with atomicMax into *out (pre-set to 0).
+__global__ void spread_kernel(int64_t rows, int64_t inner, const int32_t* __restrict__ exps,
+                              const uint8_t* __restrict__ flags, const float* __restrict__ l1,
+                              int* out) {
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    int v = 0;
+    if (r < rows && !flags[r] && l1[r] > 0.f) {
+        const float mean_log2 = log2f(l1[r]) - log2f(static_cast<float>(inner));
+        const float sp = static_cast<float>(exps[r]) - mean_log2;
+        v = sp > 0.f ? static_cast<int>(ceilf(16.f * sp)) : 0;
+    }
+    v = __reduce_max_sync(0xFFFFFFFFu, v);
+    if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(out, v);
+}
+
+// Digit s (1-based) of x relative to exponent e.
+__device__ __forceinline__ __half digit_of(unsigned long long mag, bool neg, int e2, int e, int beta,
+                                           int s) {
+    const unsigned long long mask = (1ull << beta) - 1ull;
+    const int sh = e2 - e + beta * s;
+    unsigned int v;
+    if (sh >= 0) {
+        v = sh >= beta ? 0u : static_cast<unsigned int>((mag << sh) & mask);
+    } else {
+        v = (-sh >= 64) ? 0u : static_cast<unsigned int>((mag >> (-sh)) & mask);
+    }
+    const int iv = neg ? -static_cast<int>(v) : static_cast<int>(v);
+    return __int2half_rn(iv);
+}
+
+// Decompose x into (integer significand, binary exponent e2, sign); zero / non-finite -> mag 0.
+__device__ __forceinline__ void decompose(double x, unsigned long long* mag, int* e2, bool* neg) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    *neg = (b >> 63) != 0;
+    const int ef = static_cast<int>((b >> 52) & 0x7FF);
+    unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (ef == 0x7FF) {
+        m = 0;
+        *e2 = 0;
+    } else if (ef == 0) {
+        *e2 = -1074;
+    } else {
+        m |= 1ull << 52;
+        *e2 = ef - 1075;
+    }
+    *mag = m;
+}
+
+// Inner dimension contiguous in memory: thread per (r, q), q fastest.
+__global__ void split_inner_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
+                                   int64_t inner, const int32_t* __restrict__ exps,
+                                   const uint8_t* __restrict__ flags, int S, int beta,
+                                   __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad) {
+    const int64_t total = rows_pad * inner_pad;
+    const int64_t plane = rows_pad * inner_pad;
+    for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = idx / inner_pad;
+        const int64_t q = idx - r * inner_pad;
+        unsigned long long mag = 0;
+        int e2 = 0, e = 0;
+        bool neg = false;
+        if (r < rows && q < inner && !flags[r]) {
+            decompose(X[q + r * ld], &mag, &e2, &neg);
+            e = exps[r];
+        }
+        for (int s = 1; s <= S; ++s)
+            digits[(s - 1) * plane + idx] = mag ? digit_of(mag, neg, e2, e, beta, s) : __int2half_rn(0);
+    }
+}
+
+// Rows contiguous in memory: 64 x 64 tile transposed through shared memory so that
+// reads are coalesced along r and digit writes along q.
+constexpr int TT = 64;
+__global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
+                                  int64_t inner, const int32_t* __restrict__ exps,
+                                  const uint8_t* __restrict__ flags, int S, int beta,
+                                  __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad) {
+    __shared__ double tile[TT][TT + 1];  // [q][r]
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TT;
+    const int64_t q0 = static_cast<int64_t>(blockIdx.y) * TT;
+    const int tid = threadIdx.x;  // 256 threads
+    for (int i = tid; i < TT * TT; i += 256) {
+        const int rr = i % TT, qq = i / TT;
+        const int64_t r = r0 + rr, q = q0 + qq;
+        tile[qq][rr] = (r < rows && q < inner) ? X[r + q * ld] : 0.0;
+    }
+    __syncthreads();
+    const int64_t plane = rows_pad * inner_pad;
+    for (int i = tid; i < TT * TT; i += 256) {
+        const int qq = i % TT, rr = i / TT;
+        const int64_t r = r0 + rr, q = q0 + qq;
+        if (r >= rows_pad || q >= inner_pad) continue;
+        unsigned long long mag = 0;
+        int e2 = 0, e = 0;
+        bool neg = false;
+        if (r < rows && q < inner && !flags[r]) {
+            decompose(tile[qq][rr], &mag, &e2, &neg);
+            e = exps[r];
+        }
+        const int64_t off = r * inner_pad + q;
+        for (int s = 1; s <= S; ++s)
+            digits[(s - 1) * plane + off] = mag ? digit_of(mag, neg, e2, e, beta, s) : __int2half_rn(0);
+    }
+}
+
+// Logical matrix Y (rows x inner): Y(r, q) = X[r*sr + q*sq]; returns true when rows
+// are the contiguous dimension (sr == 1).
+inline bool rows_contiguous(int which, int op) {
+    // which 0: rows of op(A) -- op N: A[r + q*ld] (rows contiguous); op T: A[q + r*ld]
+    // which 1: columns of op(B) -- op N: B[q + r*ld] (inner contiguous); op T: B[r + q*ld]
+    return (which == 0) ? (op == 0) : (op != 0);
+}
+
+}  // namespace split
+
+cudaError_t launch_emu_scale(int which, int op, int64_t rows, int64_t inner, const double* X,
+                             int64_t ldx, int32_t* exps, uint8_t* flags, float* l1,
+                             cudaStream_t stream) {
+    using namespace split;
+    if (rows <= 0) return cudaSuccess;
+    if (split::rows_contiguous(which, op)) {
+        cudaError_t e = cudaMemsetAsync(exps, 0x80, static_cast<size_t>(rows) * sizeof(int32_t), stream);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(flags, 0, static_cast<size_t>(rows), stream);
+        if (e != cudaSuccess) return e;
+        if (l1) {
+            e = cudaMemsetAsync(l1, 0, static_cast<size_t>(rows) * sizeof(float), stream);
+            if (e != cudaSuccess) return e;
+        }
+        if (inner > 0) {
+            const int64_t bx = (rows + 255) / 256;
+            int64_t by = (2 * device_sm_count() * 4 + bx - 1) / bx;  // enough blocks to fill the GPU
+            if (by < 1) by = 1;
+            if (by > inner) by = inner;
+            if (by > 65535) by = 65535;
+            const int64_t qchunk = (inner + by - 1) / by;
+            by = (inner + qchunk - 1) / qchunk;
+            dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(by));
+            scale_rows_contig<<<grid, 256, 0, stream>>>(X, ldx, rows, inner, qchunk, exps, flags, l1);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        scale_finalize<<<static_cast<unsigned>((rows + 255) / 256), 256, 0, stream>>>(rows, exps, flags);
+        return cudaGetLastError();
+    }
+    const int64_t blocks = (rows + 7) / 8;
+    scale_inner_contig<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(X, ldx, rows, inner, exps, flags, l1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emu_spread(int64_t rows, int64_t inner, const int32_t* exps, const uint8_t* flags,
+                              const float* l1, int* out, cudaStream_t stream) {
+    if (rows <= 0) return cudaSuccess;
+    split::spread_kernel<<<static_cast<unsigned>((rows + 255) / 256), 256, 0, stream>>>(rows, inner, exps, flags, l1, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, const double* X,
+                             int64_t ldx, const int32_t* exps, const uint8_t* flags, int S, int beta,
+                             void* digits, int64_t rows_pad, int64_t inner_pad, cudaStream_t stream) {
+    using namespace split;
+    if (rows_pad <= 0 || inner_pad <= 0) return cudaSuccess;
+    if (S < 1 || beta < 1 || beta > 10) return cudaErrorInvalidValue;
+    __half* dg = static_cast<__half*>(digits);
+    if (split::rows_contiguous(which, op)) {
+        dim3 grid(static_cast<unsigned>((rows_pad + TT - 1) / TT), static_cast<unsigned>((inner_pad + TT - 1) / TT));
+        if (grid.y > 65535) return cudaErrorInvalidValue;
+        split_rows_contig<<<grid, 256, 0, stream>>>(X, ldx, rows, inner, exps, flags, S, beta, dg,
+                                                    rows_pad, inner_pad);
+        return cudaGetLastError();
+    }
+    const int64_t total = rows_pad * inner_pad;
+    int64_t blocks = (total + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(device_sm_count()) * 16;
+    if (blocks > cap) blocks = cap;
+    split_inner_contig<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(X, ldx, rows, inner, exps, flags,
+                                                                          S, beta, dg, rows_pad, inner_pad);
+    return cudaGetLastError();
+}
+
+}  // namespace momms
