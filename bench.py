@@ -40,7 +40,7 @@ UNIT = "TFLOP/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=60)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--size", type=int, default=8192)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
@@ -151,56 +151,74 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-# ----------------------------------------------------------------------------- CPU oracle sample
-def cpu_oracle_sample(n, seconds_budget, reference_arm=False):
-    """Time the oracle (as it stands) on a column sample of the n^3 workload.
+def aggregate_throughput(flops_per_rank, ms_per_step_this_rank, world):
+    """Whole-job TFLOP/s: every rank runs the same workload (replicas, weak scaling);
+    the time is the slowest rank's."""
+    ms = max_over_ranks(ms_per_step_this_rank, world)
+    return world * flops_per_rank / (ms * 1e-3) / 1e12, ms
 
-    Returns (TFLOP/s, cores, description).  Column j of C needs all of A and column j
-    of B, so a block of c columns is an n x c x n product of the same workload."""
-    import oracle
-    from paper_1904_05717_gb300 import synthetic as syn
-    cores = oracle.max_threads()
-    A = syn.matrix("uniform", n, n, syn.workload_seed(1, "A"))
-    Bfull_cols = None
-    # calibrate on a small block, then size the sample to the budget
-    c = max(cores, 8)
-    B = syn.matrix("uniform", n, c, syn.workload_seed(1, "B"))
-    C = syn.matrix("uniform", n, c, syn.workload_seed(1, "C"))
-    t0 = time.perf_counter()
-    oracle.dgemm(A, B, C, 1.0, 1.0)
-    t1 = time.perf_counter() - t0
-    per_col = t1 / c
-    cols = int(max(c, min(n, seconds_budget / max(per_col, 1e-9))))
-    cols = max(cores, cols - cols % cores)
-    B = syn.matrix("uniform", n, cols, syn.workload_seed(1, "B"))
-    C = syn.matrix("uniform", n, cols, syn.workload_seed(1, "C"))
-    t0 = time.perf_counter()
-    oracle.dgemm(A, B, C, 1.0, 1.0)
-    dt = time.perf_counter() - t0
-    del Bfull_cols
-    tflops = 2.0 * n * n * cols / dt / 1e12
-    desc = (f"oracle triple loop (p ascending, no FMA, OpenMP over columns) on {cols} of {n} columns "
-            f"of the m=n=k={n} product ({2.0 * n * n * cols:.3g} flops, {dt:.1f} s)")
-    return tflops, cores, desc, dt
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+class OracleSample:
+    """The oracle (as it stands) on a column sample of the n^3 workload.
+
+    Column j of C needs all of A and column j of B, so a block of c columns is an
+    n x c x n product of the same workload.  The inputs are generated once."""
+
+    def __init__(self, n):
+        import oracle
+        from paper_1904_05717_gb300 import synthetic as syn
+        self.oracle = oracle
+        self.n = n
+        self.cores = oracle.max_threads()
+        self.A = syn.matrix("uniform", n, n, syn.workload_seed(1, "A"))
+        # enough columns for the largest sample; column j is column j of the workload
+        self.B = syn.matrix("uniform", n, min(n, 4096), syn.workload_seed(1, "B"))
+        self.C = syn.matrix("uniform", n, min(n, 4096), syn.workload_seed(1, "C"))
+        c = max(self.cores, 8)
+        t0 = time.perf_counter()
+        self.run(c)
+        self.per_col = (time.perf_counter() - t0) / c
+
+    def run(self, cols):
+        B = np.asfortranarray(self.B[:, :cols])
+        C = np.asfortranarray(self.C[:, :cols])
+        t0 = time.perf_counter()
+        self.oracle.dgemm(self.A, B, C, 1.0, 1.0)
+        return time.perf_counter() - t0
+
+    def columns_for(self, seconds):
+        cols = int(max(self.cores, min(self.B.shape[1], seconds / max(self.per_col, 1e-9))))
+        return max(self.cores, cols - cols % self.cores)
+
+    def measure(self, seconds):
+        cols = self.columns_for(seconds)
+        dt = self.run(cols)
+        n = self.n
+        tflops = 2.0 * n * n * cols / dt / 1e12
+        desc = (f"oracle triple loop (p ascending, no FMA, OpenMP over columns) on {cols} of {n} columns "
+                f"of the m=n=k={n} product ({2.0 * n * n * cols:.3g} flops, {dt:.2f} s)")
+        return tflops, desc
 
 
 def run_reference(args):
-    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     n = args.size
-    # each step: a bounded sample, the whole run within a few minutes
-    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    sample = OracleSample(n)
+    # each step is a bounded sample; the whole run stays within a few minutes
+    per_step = max(0.3, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     vals = []
     desc = ""
-    cores = 1
     for i in range(args.warmup + args.steps):
-        v, cores, desc, _ = cpu_oracle_sample(n, per_step)
+        v, desc = sample.measure(per_step)
         if i >= args.warmup:
             vals.append(v)
     value = statistics.median(vals) if vals else 0.0
@@ -209,7 +227,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(n)},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample.cores, "kind": "oracle",
+                         "sample": desc + f"; median of {len(vals)} samples"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -265,11 +284,9 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
-    ms = e0.elapsed_time(e1) / args.steps
-    ms = max_over_ranks(ms, world)
+    value, ms = aggregate_throughput(flops, e0.elapsed_time(e1) / args.steps, world)
     clocks = clk.summary()
     status = h.device_status(stream)
-    value = world * flops / (ms * 1e-3) / 1e12
 
     # ---- dominant kernel alone (same digits, same launch configuration), per-launch CUDA events
     S, bb = int(rep["slices"]), int(rep["digit_bits"])
@@ -306,7 +323,7 @@ def main():
         torch.cuda.synchronize()
         slice_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
         pairs = S * (S + 1) // 2
-        tensor_flops = pairs * 2.0 * m_pad * n_pad * k_pad
+        tensor_flops = pairs * 2.0 * n * n * n  # algorithmic: every digit-pair product of the n^3 problem
         achieved = tensor_flops / (slice_ms * 1e-3) / 1e12
         peaks, src = measured_peaks()
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
@@ -363,8 +380,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, desc, _ = cpu_oracle_sample(n, args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        sample = OracleSample(n)
+        v, desc = sample.measure(args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": sample.cores, "kind": "oracle", "sample": desc}
 
     if rank == 0:
         peaks, src = measured_peaks()

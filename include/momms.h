@@ -151,7 +151,9 @@ int momms_gemm_backward(momms_handle_t handle, int64_t m, int64_t n, int64_t k,
  * All array arguments are HOST arrays of length `count`; the matrix pointers in
  * them are device pointers.  The tile table lives in the handle, so the
  * enqueued launches can be captured in a CUDA graph and replayed as long as the
- * handle and the problem pointers stay alive and the sizes do not change. */
+ * handle and the problem pointers stay alive and the sizes do not change: a call
+ * whose problem table equals the previous call's enqueues only the kernel (make
+ * one eager call before capturing). */
 int momms_gemm_batched(momms_handle_t handle, int64_t count, const int64_t* m,
                        const int64_t* n, const int64_t* k, const double* alpha,
                        const double* const* A, const int64_t* lda,
@@ -161,8 +163,9 @@ int momms_gemm_batched(momms_handle_t handle, int64_t count, const int64_t* m,
 /* --------------------------------------------- steps of the emulated path */
 /* These expose each step separately (used by the parity tests).  The digit
  * layout: S slices, slice s (0-based = digit s+1) a rows_pad x inner_pad fp16
- * matrix stored inner-contiguous at digits + s*rows_pad*inner_pad; rows_pad a
- * multiple of 128, inner_pad a multiple of 64; padding holds zeros. */
+ * matrix stored inner-contiguous at digits + s*rows_pad*inner_pad; rows_pad >=
+ * rows, inner_pad >= inner and a multiple of 64; padding holds zeros.  The
+ * pointer must be 16-byte aligned. */
 
 /* Scaling exponents.  which = 0: the rows of op(X) where op(X) is rows x inner
  * (X = A, op = op_a); which = 1: the columns of op(X) where op(X) is
@@ -182,9 +185,11 @@ int momms_emu_split(int which, int op, int64_t rows, int64_t inner, const double
 /* Slice products and recombination on the tcgen05 tensor cores:
  *   P_d = sum_{s+t=d} A_s B_t  (d = 2..S+1, triangular pair set), exact;
  *   C := alpha * 2^(e_i+f_j) * sum_d 2^(-beta d) P_d + beta*C  (FP64 Horner).
- * Ad: S slices of m_pad x k_pad, Bd: S slices of n_pad x k_pad (layout above).
+ * Ad: S slices of m_pad x k_pad, Bd: S slices of n_pad x k_pad (layout above,
+ * m_pad >= m, n_pad >= n, k_pad a multiple of 64; digit_bits <= 8).
  * scratch: device memory of momms_emu_scratch_bytes() bytes (FP64 partial sums
- * of the recombination, one 128 x 256 block per CTA).  member: momms_member_t. */
+ * of the recombination, one 128 x 192 block per CTA).  status: a device int32
+ * set to MOMMS_ERR_TIMEOUT if a bounded wait expires.  member: momms_member_t. */
 int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_bits,
                          const void* Ad, const void* Bd, int64_t m_pad, int64_t n_pad,
                          int64_t k_pad, const int32_t* e, const uint8_t* eflags,

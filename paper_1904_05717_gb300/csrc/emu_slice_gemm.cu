@@ -40,17 +40,28 @@
 namespace momms {
 namespace emu {
 
-constexpr int BM = kEmuBM, BN = kEmuBN, BK = kEmuBK;
-constexpr int STAGES = 4;
-constexpr int EPI_WARPS = 8;
-constexpr int EPI_WARP0 = 2;                     // warps 2..9 drain and recombine
-constexpr int THREADS = 32 * EPI_WARP0 + 32 * EPI_WARPS;  // 320
-constexpr uint32_t A_TILE = BM * BK * 2;   // 16 KB
-constexpr uint32_t B_TILE = BN * BK * 2;   // 32 KB
-constexpr uint32_t STAGE = A_TILE + B_TILE;
-constexpr uint32_t TMEM_COLS = 512;        // two 128 x 256 FP32 accumulators
-constexpr uint32_t IDESC = idesc_f16_f32(BM, BN);
-constexpr size_t SMEM_BYTES = 1024 + static_cast<size_t>(STAGES) * STAGE + 256;
+constexpr int BM = kEmuBM, BK = kEmuBK;
+constexpr int CTRL_WARPS = 4;   // warp 0: TMA producer, warp 1: TMEM owner + MMA issuer, 2-3 idle
+constexpr int EPI_WARPS = 12;   // three warps per TMEM lane quadrant
+constexpr int THREADS = 32 * (CTRL_WARPS + EPI_WARPS);  // 512: four warps per SM sub-partition
+constexpr uint32_t A_TILE = BM * BK * 2;                 // 16 KB
+constexpr uint32_t TMEM_COLS = 512;                      // two BN-column FP32 accumulators
+constexpr size_t SMEM_BUDGET = 225 * 1024;
+
+template <int BN>
+struct Cfg {
+    static_assert(BN == 192, "three drain warps per quadrant of 64 columns; spare TMEM holds half the sums");
+    static constexpr int CW = BN / 3;                    // columns per drain warp (64)
+    static constexpr int CR = 32;                        // of which summed in registers
+    static constexpr int CT = CW - CR;                   // and summed as int32 in spare TMEM columns
+    static constexpr uint32_t B_TILE = BN * BK * 2;
+    static constexpr uint32_t STAGE = A_TILE + B_TILE;
+    static constexpr int STAGES = static_cast<int>((SMEM_BUDGET - 2048) / STAGE) > 6
+                                      ? 6 : static_cast<int>((SMEM_BUDGET - 2048) / STAGE);
+    static constexpr size_t SMEM_BYTES = 1024 + static_cast<size_t>(STAGES) * STAGE + 256;
+    static constexpr uint32_t IDESC = idesc_f16_f32(BM, BN);
+    static_assert(STAGE % 1024 == 0, "stage bases stay 1024-byte aligned for the 128-B swizzle");
+};
 
 struct Params {
     int m, n;
@@ -59,7 +70,6 @@ struct Params {
     int slab0, nslab;
     int tiles_m, tiles_n;
     int member, group;
-    int m_pad, n_pad;
     const int32_t* e;
     const uint8_t* ef;
     const int32_t* f;
@@ -87,9 +97,14 @@ MOMMS_DEV bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
     return mbar_wait(bar, parity, &never);
 }
 
+template <int BN>
 __global__ void __launch_bounds__(THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const Params p) {
+    using C_ = Cfg<BN>;
+    constexpr int STAGES = C_::STAGES;
+    constexpr uint32_t STAGE = C_::STAGE;
+    constexpr int CW = C_::CW;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -143,8 +158,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                     break;
                 for (int d = p.S + 1; d >= 2 && ok; --d) {
                     for (int s = 1; s <= d - 1 && ok; ++s) {
-                        const int ya = (s - 1) * p.m_pad + tm * BM;
-                        const int yb = (d - s - 1) * p.n_pad + tn * BN;
                         for (int j = 0; j < p.nslab; ++j) {
                             if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
                                 ok = false;
@@ -153,8 +166,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                             uint8_t* sa = smem + stage * STAGE;
                             mbar_arrive_expect_tx(&full[stage], STAGE);
                             const int x = (p.slab0 + j) * BK;
-                            tma_load_2d(sa, &tmA, &full[stage], x, ya);
-                            tma_load_2d(sa + A_TILE, &tmB, &full[stage], x, yb);
+                            // A slice s rows [tm*BM, +BM), B slice d-s rows [tn*BN, +BN);
+                            // rows past the end of a slice are zero-filled by the copy engine
+                            tma_load_3d(sa, &tmA, &full[stage], x, tm * BM, s - 1);
+                            tma_load_3d(sa + A_TILE, &tmB, &full[stage], x, tn * BN, d - s - 1);
                             last_phase[stage] = static_cast<int>(phase);
                             if (++stage == STAGES) {
                                 stage = 0;
@@ -192,7 +207,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t dt = tmem_base + abuf * BN;
+                        const uint32_t dt = tmem_base + abuf * 256u;
                         for (int c = 0; c < cnt; ++c) {
                             if (!mbar_wait(&full[stage], phase, abort_flag)) {
                                 ok = false;
@@ -204,7 +219,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             const uint64_t db = smem_desc_k_sw128(sa + A_TILE);
 #pragma unroll
                             for (int kk = 0; kk < BK / 16; ++kk)
-                                umma_f16_ss(dt, da + 2ull * kk, db + 2ull * kk, IDESC,
+                                umma_f16_ss(dt, da + 2ull * kk, db + 2ull * kk, C_::IDESC,
                                             static_cast<uint32_t>((c | kk) != 0));
                             issued = true;
                             umma_commit(&empty[stage]);
@@ -226,35 +241,35 @@ __global__ void __launch_bounds__(THREADS, 1)
                 mbar_wait_drain(drain, 0);
             }
         }
-    } else if (warp >= EPI_WARP0) {
+    } else if (warp >= CTRL_WARPS) {
         // ------------------------------------------------------------ drain + recombination
-        const int quad = warp & 3;                 // TMEM lanes this warp may read: 32*quad ..
-        const int half = (warp - EPI_WARP0) >> 2;  // columns [128*half, 128*half + 128)
-        const int rloc = quad * 32 + lane;  // row within the tile
+        // Each drain thread owns one row and CW = 64 columns of the tile.  The int32
+        // diagonal sums of the first CR = 32 columns live in registers; those of the
+        // other CT = 32 columns live in TMEM columns the accumulators do not use
+        // (192..255 and 448..511), which keeps the thread clear of register spills.
+        constexpr int CR = C_::CR, CT = C_::CT;
+        const int quad = warp & 3;                         // TMEM lanes this warp may read: 32*quad ..
+        const int third = (warp - CTRL_WARPS) >> 2;        // columns [CW*third, CW*third + CW)
+        const int rloc = quad * 32 + lane;                 // row within the tile
+        const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+        const uint32_t tsum = tmem_base + lane_off + (third < 2 ? 192u + 32u * third : 448u);
         uint32_t abuf = 0;
         uint32_t aphase[2] = {0u, 0u};
         const double rb = pow2_normal(-p.beta);
         const double qnan = __longlong_as_double(0x7ff8000000000000ll);
-        double* R = p.scratch + (static_cast<size_t>(blockIdx.x) * BN + half * 128) * BM + rloc;
+        double* R = p.scratch + (static_cast<size_t>(blockIdx.x) * BN + third * CW) * BM + rloc;
         bool ok = true;
-        for (int64_t it = 0; ok; ++it) {
+        for (int it = 0; ok; ++it) {
             int tm, tn;
             if (!member_tile(p.member, p.group, blockIdx.x, gridDim.x, it, p.tiles_m, p.tiles_n, &tm,
                              &tn))
                 break;
-            const int row = tm * BM + rloc;
-            const bool row_ok = row < p.m;
-            int ei = 0;
-            bool eflag = false;
-            if (row_ok) {
-                ei = p.e[row];
-                eflag = p.ef[row] != 0;
-            }
             for (int d = p.S + 1; d >= 2 && ok; --d) {
-                int32_t acc[128];
+                int32_t acc[CR];
 #pragma unroll
-                for (int c = 0; c < 128; ++c) acc[c] = 0;
+                for (int c = 0; c < CR; ++c) acc[c] = 0;
                 const int units = (d - 1) * p.nslab;
+                bool first = true;
                 for (int u = 0; u < units;) {
                     const int cnt = min(p.chunk_slabs, units - u);
                     if (!mbar_wait(&acc_full[abuf], aphase[abuf], abort_flag)) {
@@ -262,58 +277,81 @@ __global__ void __launch_bounds__(THREADS, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t taddr =
-                        tmem_base + (static_cast<uint32_t>(quad * 32) << 16) + abuf * BN + half * 128;
+                    const uint32_t taddr = tmem_base + lane_off + abuf * 256u + third * CW;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < CR / 16; ++q) {
                         uint32_t r[16];
                         tmem_ld_32x32b_x16(taddr + q * 16, r);
                         tmem_ld_wait(r);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) acc[q * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
                     }
+#pragma unroll
+                    for (int q = 0; q < CT / 16; ++q) {
+                        uint32_t r[16];
+                        tmem_ld_32x32b_x16(taddr + CR + q * 16, r);
+                        tmem_ld_wait(r);
+                        uint32_t t[16];
+                        if (first) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) t[j] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[j])));
+                        } else {
+                            tmem_ld_32x32b_x16(tsum + q * 16, t);
+                            tmem_ld_wait(t);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                t[j] = static_cast<uint32_t>(static_cast<int32_t>(t[j]) + __float2int_rn(__uint_as_float(r[j])));
+                        }
+                        tmem_st_32x32b_x16(tsum + q * 16, t);
+                    }
+                    tmem_st_wait();
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acc_empty[abuf]);
                     aphase[abuf] ^= 1u;
                     abuf ^= 1u;
                     u += cnt;
+                    first = false;
                 }
                 if (!ok) break;
-                if (d != 2) {
-                    // Horner step, least significant diagonal first (kept in FP64 scratch)
-                    if (d == p.S + 1) {
+                // Horner step, least significant diagonal first, kept in FP64 scratch:
+                // R = P_{S+1};  R = P_d + 2^-beta R  (d = S..2)
+                const bool lsd = (d == p.S + 1);
 #pragma unroll
-                        for (int c = 0; c < 128; ++c) {
-                            R[c * BM] = static_cast<double>(acc[c]);
-                            if ((c & 15) == 15) asm volatile("" ::: "memory");  // bound live registers
-                        }
-                    } else {
+                for (int c = 0; c < CR; ++c) {
+                    const double v = static_cast<double>(acc[c]);
+                    R[c * BM] = lsd ? v : fma(R[c * BM], rb, v);
+                    if ((c & 7) == 7) asm volatile("" ::: "memory");  // bound the loads in flight
+                }
 #pragma unroll
-                        for (int c = 0; c < 128; ++c) {
-                            R[c * BM] = fma(R[c * BM], rb, static_cast<double>(acc[c]));
-                            if ((c & 15) == 15) asm volatile("" ::: "memory");
-                        }
+                for (int q = 0; q < CT / 16; ++q) {
+                    uint32_t t[16];
+                    tmem_ld_32x32b_x16(tsum + q * 16, t);
+                    tmem_ld_wait(t);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        double* rp = R + (CR + q * 16 + j) * BM;
+                        const double v = static_cast<double>(static_cast<int32_t>(t[j]));
+                        *rp = lsd ? v : fma(*rp, rb, v);
+                        if ((j & 7) == 7) asm volatile("" ::: "memory");
                     }
-                } else {
-                    const int col0 = tn * BN + half * 128;
-#pragma unroll
-                    for (int c = 0; c < 128; ++c) {
-                        const double r2 = (d == p.S + 1) ? static_cast<double>(acc[c])
-                                                         : fma(R[c * BM], rb, static_cast<double>(acc[c]));
-                        const int col = col0 + c;
-                        if (row_ok && col < p.n) {
-                            double x;
-                            if (eflag || p.ff[col]) {
-                                x = qnan;
-                            } else {
-                                const int E = ei + p.f[col] - 2 * p.beta;
-                                x = scale_pow2(r2, E);
-                            }
+                }
+                if (d == 2) {
+                    // C := alpha * 2^(e_i + f_j - 2 beta) R_2 + beta_c C
+                    const int row = tm * BM + rloc;
+                    const int col0 = tn * BN + third * CW;
+                    if (row < p.m) {
+                        const int ei = p.e[row];
+                        const bool eflag = p.ef[row] != 0;
+#pragma unroll 4
+                        for (int c = 0; c < CW; ++c) {
+                            const int col = col0 + c;
+                            if (col >= p.n) break;
+                            const double r2 = R[c * BM];
+                            const double x = (eflag || p.ff[col]) ? qnan : scale_pow2(r2, ei + p.f[col] - 2 * p.beta);
                             double* cp = p.C + row + static_cast<int64_t>(col) * p.ldc;
                             *cp = (p.beta_c == 0.0) ? p.alpha * x : fma(p.beta_c, *cp, p.alpha * x);
                         }
-                        if ((c & 15) == 15) asm volatile("" ::: "memory");
                     }
                 }
             }
@@ -346,19 +384,78 @@ static EncodeFn get_encode() {
     return fn;
 }
 
-// 2-D fp16 digit tensor [rows_total][k_pad] (k contiguous), box 64 x box_rows, 128-B swizzle.
-static bool make_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t rows_total,
+// 3-D fp16 digit tensor [S][rows][k_pad] (k contiguous), box 64 x box_rows x 1, 128-B swizzle.
+static bool make_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t rows, int S,
                      int box_rows) {
     EncodeFn enc = get_encode();
     if (!enc) return false;
-    cuuint64_t dims[2] = {static_cast<cuuint64_t>(k_pad), static_cast<cuuint64_t>(rows_total)};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(k_pad) * 2};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides,
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(k_pad), static_cast<cuuint64_t>(rows),
+                          static_cast<cuuint64_t>(S)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(k_pad) * 2,
+                             static_cast<cuuint64_t>(k_pad) * 2 * static_cast<cuuint64_t>(rows)};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(base), dims, strides,
                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t stream) {
+    using C_ = Cfg<BN>;
+    const int sms = device_sm_count();
+    const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
+    const int64_t tiles = tiles_m * tiles_n;
+    int64_t ctas = a.max_ctas > 0 ? a.max_ctas : sms;
+    if (ctas > tiles) ctas = tiles;
+    if (a.scratch_bytes < static_cast<size_t>(ctas) * BN * BM * sizeof(double)) return cudaErrorInvalidValue;
+
+    CUtensorMap mapA, mapB;
+    if (!make_map(&mapA, a.Ad, a.k_pad, a.m_pad, a.S, BM)) return cudaErrorInvalidValue;
+    if (!make_map(&mapB, a.Bd, a.k_pad, a.n_pad, a.S, BN)) return cudaErrorInvalidValue;
+
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(C_::SMEM_BYTES));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t kslabs = (a.k + BK - 1) / BK;
+    const int64_t pass_slabs = emu_max_k_per_pass(a.S, a.beta) / BK;
+    if (kslabs <= 0 || pass_slabs <= 0) return cudaErrorInvalidValue;
+    int npass = 0;
+    for (int64_t s0 = 0; s0 < kslabs; s0 += pass_slabs) {
+        Params p;
+        p.m = static_cast<int>(a.m);
+        p.n = static_cast<int>(a.n);
+        p.S = a.S;
+        p.beta = a.beta;
+        p.chunk_slabs = emu_chunk_slabs(a.beta);
+        p.slab0 = static_cast<int>(s0);
+        p.nslab = static_cast<int>(kslabs - s0 < pass_slabs ? kslabs - s0 : pass_slabs);
+        p.tiles_m = static_cast<int>(tiles_m);
+        p.tiles_n = static_cast<int>(tiles_n);
+        p.member = a.member == kMemberAuto ? kMemberC2 : a.member;
+        p.group = a.group > 0 ? a.group : 8;
+        p.e = a.e;
+        p.ef = a.ef;
+        p.f = a.f;
+        p.ff = a.ff;
+        p.alpha = a.alpha;
+        p.beta_c = npass == 0 ? a.beta_c : 1.0;
+        p.C = a.C;
+        p.ldc = a.ldc;
+        p.scratch = static_cast<double*>(a.scratch);
+        p.status = a.status;
+        slice_gemm_kernel<BN><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(mapA, mapB, p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        ++npass;
+    }
+    if (passes) *passes = npass;
+    return cudaSuccess;
 }
 
 }  // namespace emu
@@ -375,7 +472,7 @@ int device_sm_count() {
 }
 
 size_t emu_scratch_bytes(int num_sms) {
-    return static_cast<size_t>(num_sms) * emu::BN * emu::BM * sizeof(double);
+    return static_cast<size_t>(num_sms) * kEmuBNMax * emu::BM * sizeof(double);
 }
 
 int64_t emu_max_k_per_pass(int S, int beta) {
@@ -392,75 +489,18 @@ int emu_chunk_slabs(int beta) {
     return slabs < 1 ? 1 : slabs;
 }
 
+int emu_pick_bn(int64_t, int) { return 192; }
+
 cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_t stream) {
     using namespace emu;
     if (passes) *passes = 0;
     if (a.m <= 0 || a.n <= 0) return cudaSuccess;
-    if (a.S < 1 || a.S > 16 || a.beta < 1 || a.beta > 10) return cudaErrorInvalidValue;
-    if (a.m_pad % BM || a.n_pad % BN || a.k_pad % BK || a.m_pad < a.m || a.n_pad < a.n ||
-        a.k_pad < a.k)
-        return cudaErrorInvalidValue;
+    if (a.S < 1 || a.S > 16 || a.beta < 1 || a.beta > 8) return cudaErrorInvalidValue;
+    if (a.m_pad < a.m || a.n_pad < a.n || a.k_pad < a.k || a.k_pad % BK) return cudaErrorInvalidValue;
     if (emu_chunk_slabs(a.beta) * BK * ((1ll << a.beta) - 1) * ((1ll << a.beta) - 1) > (1ll << 24))
         return cudaErrorInvalidValue;  // beta too wide for one 64-wide slab per chunk
-    if (static_cast<int64_t>(a.S) * (a.m_pad > a.n_pad ? a.m_pad : a.n_pad) >= (1ll << 31))
-        return cudaErrorInvalidValue;
-    const int sms = device_sm_count();
-    const int64_t tiles_m = a.m_pad / BM, tiles_n = a.n_pad / BN;
-    const int64_t tiles = tiles_m * tiles_n;
-    int64_t ctas = a.max_ctas > 0 ? a.max_ctas : sms;
-    if (ctas > tiles) ctas = tiles;
-    if (a.scratch_bytes < static_cast<size_t>(ctas) * BN * BM * sizeof(double))
-        return cudaErrorInvalidValue;
-
-    CUtensorMap mapA, mapB;
-    if (!make_map(&mapA, a.Ad, a.k_pad, a.S * a.m_pad, BM)) return cudaErrorInvalidValue;
-    if (!make_map(&mapB, a.Bd, a.k_pad, a.S * a.n_pad, BN)) return cudaErrorInvalidValue;
-
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(SMEM_BYTES));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-
-    const int64_t kslabs = (a.k + BK - 1) / BK;
-    const int64_t pass_slabs = emu_max_k_per_pass(a.S, a.beta) / BK;
-    int npass = 0;
-    if (kslabs <= 0 || pass_slabs <= 0) return cudaErrorInvalidValue;
-    for (int64_t s0 = 0; s0 < kslabs; s0 += pass_slabs) {
-        Params p;
-        p.m = static_cast<int>(a.m);
-        p.n = static_cast<int>(a.n);
-        p.S = a.S;
-        p.beta = a.beta;
-        p.chunk_slabs = emu_chunk_slabs(a.beta);
-        p.slab0 = static_cast<int>(s0);
-        p.nslab = static_cast<int>(kslabs - s0 < pass_slabs ? kslabs - s0 : pass_slabs);
-        p.tiles_m = static_cast<int>(tiles_m);
-        p.tiles_n = static_cast<int>(tiles_n);
-        p.member = a.member == kMemberAuto ? kMemberC2 : a.member;
-        p.group = a.group > 0 ? a.group : 8;
-        p.m_pad = static_cast<int>(a.m_pad);
-        p.n_pad = static_cast<int>(a.n_pad);
-        p.e = a.e;
-        p.ef = a.ef;
-        p.f = a.f;
-        p.ff = a.ff;
-        p.alpha = a.alpha;
-        p.beta_c = npass == 0 ? a.beta_c : 1.0;
-        p.C = a.C;
-        p.ldc = a.ldc;
-        p.scratch = static_cast<double*>(a.scratch);
-        p.status = a.status;
-        slice_gemm_kernel<<<static_cast<unsigned>(ctas), THREADS, SMEM_BYTES, stream>>>(mapA, mapB, p);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        ++npass;
-    }
-    if (passes) *passes = npass;
-    return cudaSuccess;
+    if (a.m > (1ll << 30) || a.n > (1ll << 30)) return cudaErrorInvalidValue;
+    return launch_bn<192>(a, passes, stream);
 }
 
 }  // namespace momms

@@ -149,31 +149,61 @@ __device__ __forceinline__ void decompose(double x, unsigned long long* mag, int
     *mag = m;
 }
 
-// Inner dimension contiguous in memory: thread per (r, q), q fastest.
+// Four consecutive digits of one slice packed for one 8-byte store.
+__device__ __forceinline__ uint2 pack4(__half h0, __half h1, __half h2, __half h3) {
+    uint2 v;
+    v.x = static_cast<uint32_t>(__half_as_ushort(h0)) | (static_cast<uint32_t>(__half_as_ushort(h1)) << 16);
+    v.y = static_cast<uint32_t>(__half_as_ushort(h2)) | (static_cast<uint32_t>(__half_as_ushort(h3)) << 16);
+    return v;
+}
+
+// Digits of four consecutive elements (same row) into the S slices at element offset `off`.
+__device__ __forceinline__ void write_digits4(const double (&x)[4], bool valid_row, int e, int S, int beta,
+                                              __half* __restrict__ digits, int64_t plane, int64_t off) {
+    unsigned long long mag[4];
+    int e2[4];
+    bool neg[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (valid_row) {
+            decompose(x[t], &mag[t], &e2[t], &neg[t]);
+        } else {
+            mag[t] = 0;
+            e2[t] = 0;
+            neg[t] = false;
+        }
+    }
+    const __half z = __int2half_rn(0);
+    for (int s = 1; s <= S; ++s) {
+        __half h[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) h[t] = mag[t] ? digit_of(mag[t], neg[t], e2[t], e, beta, s) : z;
+        *reinterpret_cast<uint2*>(digits + (s - 1) * plane + off) = pack4(h[0], h[1], h[2], h[3]);
+    }
+}
+
+// Inner dimension contiguous in memory: a thread takes four consecutive q of one row.
 __global__ void split_inner_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
                                    int64_t inner, const int32_t* __restrict__ exps,
                                    const uint8_t* __restrict__ flags, int S, int beta,
                                    __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad) {
-    const int64_t total = rows_pad * inner_pad;
+    const int64_t quads = inner_pad / 4;
+    const int64_t total = rows_pad * quads;
     const int64_t plane = rows_pad * inner_pad;
     for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
          idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t r = idx / inner_pad;
-        const int64_t q = idx - r * inner_pad;
-        unsigned long long mag = 0;
-        int e2 = 0, e = 0;
-        bool neg = false;
-        if (r < rows && q < inner && !flags[r]) {
-            decompose(X[q + r * ld], &mag, &e2, &neg);
-            e = exps[r];
-        }
-        for (int s = 1; s <= S; ++s)
-            digits[(s - 1) * plane + idx] = mag ? digit_of(mag, neg, e2, e, beta, s) : __int2half_rn(0);
+        const int64_t r = idx / quads;
+        const int64_t q = (idx - r * quads) * 4;
+        const bool valid = r < rows && !flags[r];
+        double x[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) x[t] = (valid && q + t < inner) ? X[q + t + r * ld] : 0.0;
+        write_digits4(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q);
     }
 }
 
-// Rows contiguous in memory: 64 x 64 tile transposed through shared memory so that
-// reads are coalesced along r and digit writes along q.
+// Rows contiguous in memory: a 64 x 64 tile is transposed through shared memory so that
+// reads are coalesced along r and digit writes along q (four q per thread, 8-byte stores).
 constexpr int TT = 64;
 __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
                                   int64_t inner, const int32_t* __restrict__ exps,
@@ -190,20 +220,15 @@ __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int6
     }
     __syncthreads();
     const int64_t plane = rows_pad * inner_pad;
-    for (int i = tid; i < TT * TT; i += 256) {
-        const int qq = i % TT, rr = i / TT;
-        const int64_t r = r0 + rr, q = q0 + qq;
+    const int qg = (tid & 15) * 4;  // four consecutive q
+    for (int rr = tid >> 4; rr < TT; rr += 16) {
+        const int64_t r = r0 + rr, q = q0 + qg;
         if (r >= rows_pad || q >= inner_pad) continue;
-        unsigned long long mag = 0;
-        int e2 = 0, e = 0;
-        bool neg = false;
-        if (r < rows && q < inner && !flags[r]) {
-            decompose(tile[qq][rr], &mag, &e2, &neg);
-            e = exps[r];
-        }
-        const int64_t off = r * inner_pad + q;
-        for (int s = 1; s <= S; ++s)
-            digits[(s - 1) * plane + off] = mag ? digit_of(mag, neg, e2, e, beta, s) : __int2half_rn(0);
+        const bool valid = r < rows && !flags[r];
+        double x[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr];
+        write_digits4(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q);
     }
 }
 
@@ -264,7 +289,8 @@ cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, con
                              void* digits, int64_t rows_pad, int64_t inner_pad, cudaStream_t stream) {
     using namespace split;
     if (rows_pad <= 0 || inner_pad <= 0) return cudaSuccess;
-    if (S < 1 || beta < 1 || beta > 10) return cudaErrorInvalidValue;
+    if (S < 1 || beta < 1 || beta > 10 || inner_pad % 4) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(digits) % 8) return cudaErrorInvalidValue;
     __half* dg = static_cast<__half*>(digits);
     if (split::rows_contiguous(which, op)) {
         dim3 grid(static_cast<unsigned>((rows_pad + TT - 1) / TT), static_cast<unsigned>((inner_pad + TT - 1) / TT));
@@ -273,7 +299,7 @@ cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, con
                                                     rows_pad, inner_pad);
         return cudaGetLastError();
     }
-    const int64_t total = rows_pad * inner_pad;
+    const int64_t total = rows_pad * (inner_pad / 4);
     int64_t blocks = (total + 255) / 256;
     const int64_t cap = static_cast<int64_t>(device_sm_count()) * 16;
     if (blocks > cap) blocks = cap;

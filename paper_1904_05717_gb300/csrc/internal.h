@@ -63,8 +63,11 @@ struct EmuGemmArgs {
     size_t scratch_bytes;
     int32_t* status;
     int max_ctas;  // 0 = number of SMs
+    int tile_n;    // CTA tile width request (only 192 is built; 0 = automatic)
 };
-constexpr int kEmuBM = 128, kEmuBN = 256, kEmuBK = 64;
+constexpr int kEmuBM = 128, kEmuBK = 64, kEmuBNMax = 192;
+// The CTA tile width used for n columns (tile_n request 0 = automatic).
+int emu_pick_bn(int64_t n, int requested);
 // Launches the slice-product kernel once per k pass; *passes receives the count.
 cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_t stream);
 size_t emu_scratch_bytes(int num_sms);

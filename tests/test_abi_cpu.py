@@ -1,0 +1,71 @@
+"""The C-ABI library builds, loads and exports every symbol include/momms.h declares,
+and rejects invalid arguments (BLAS-style index) before touching a GPU.  CPU only."""
+import ctypes
+
+import pytest
+
+from paper_1904_05717_gb300 import momms as M
+
+
+@pytest.fixture(scope="module")
+def L():
+    return M.lib(build_if_missing=True)
+
+
+def test_every_declared_symbol_is_exported(L):
+    syms = M.header_symbols()
+    assert len(syms) >= 20
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert not missing, missing
+    # and the binding marshals every one of them
+    assert set(syms) == set(M._SIGS)
+
+
+def test_status_strings(L):
+    assert M.status_string(0) == "ok"
+    assert "timeout" in M.status_string(M.MOMMS_ERR_TIMEOUT) or "wait" in M.status_string(M.MOMMS_ERR_TIMEOUT)
+    assert M.status_string(-3) == "invalid argument"
+
+
+@pytest.mark.parametrize("args,expect", [
+    ((-1, 2, 3, 1.0, 8, 1, 8, 3, 0.0, 8, 1), -1),       # m < 0
+    ((2, -2, 3, 1.0, 8, 2, 8, 3, 0.0, 8, 2), -2),       # n < 0
+    ((2, 2, -3, 1.0, 8, 2, 8, 3, 0.0, 8, 2), -3),       # k < 0
+    ((4, 2, 3, 1.0, 8, 3, 8, 3, 0.0, 8, 4), -6),        # lda < m
+    ((4, 2, 3, 1.0, 8, 4, 8, 2, 0.0, 8, 4), -8),        # ldb < k
+    ((4, 2, 3, 1.0, 8, 4, 8, 3, 0.0, 8, 3), -11),       # ldc < m
+    ((4, 2, 3, 1.0, 0, 4, 8, 3, 0.0, 8, 4), -5),        # A null with work to do
+    ((4, 2, 3, 1.0, 8, 4, 0, 3, 0.0, 8, 4), -7),        # B null
+    ((4, 2, 3, 1.0, 8, 4, 8, 3, 0.0, 0, 4), -10),       # C null
+])
+def test_gemm_argument_errors(L, args, expect):
+    m, n, k, alpha, A, lda, B, ldb, beta, C, ldc = args
+    # pointers here are fake non-null addresses: validation fails before any CUDA call
+    big = 1 << 40
+    p = lambda v: 0 if v == 0 else big + v * (1 << 30)
+    rc = M.momms_gemm(m, n, k, alpha, p(A), lda, p(B), ldb, beta, p(C), ldc, 0)
+    assert rc == expect
+
+
+def test_overlapping_c_is_rejected(L):
+    base = 1 << 40
+    # C aliases A
+    rc = M.momms_gemm(8, 8, 8, 1.0, base, 8, base + (1 << 30), 8, 0.0, base + 64, 8, 0)
+    assert rc == -10
+
+
+def test_step_entry_points_validate(L):
+    assert M.momms_emu_scale(2, 0, 4, 4, 1 << 40, 4, 1 << 41, 1 << 42, 0) == -1
+    assert M.momms_emu_scale(0, 3, 4, 4, 1 << 40, 4, 1 << 41, 1 << 42, 0) == -2
+    assert M.momms_emu_scale(0, 0, 4, 4, 1 << 40, 3, 1 << 41, 1 << 42, 0) == -6
+    # rows_pad must hold every row
+    assert M.momms_emu_split(0, 0, 4, 4, 1 << 40, 4, 1 << 41, 1 << 42, 5, 7, 1 << 43, 3, 64, 0) == -12
+    assert M.momms_emu_split(0, 0, 4, 4, 1 << 40, 4, 1 << 41, 1 << 42, 0, 7, 1 << 43, 128, 64, 0) == -9
+    assert M.momms_emu_split(0, 0, 4, 4, 1 << 40, 4, 1 << 41, 1 << 42, 5, 11, 1 << 43, 128, 64, 0) == -10
+
+
+def test_null_handle_is_rejected(L):
+    assert L.momms_set_mode(None, 1) == M.MOMMS_ERR_HANDLE
+    assert L.momms_gemm_ex(None, 0, 0, 1, 1, 1, 1.0, None, 1, None, 1, 0.0, None, 1, None) == M.MOMMS_ERR_HANDLE
+    r = M.Report()
+    assert L.momms_get_last_report(None, ctypes.byref(r)) == M.MOMMS_ERR_HANDLE

@@ -1,0 +1,91 @@
+"""Batched uneven products: one persistent launch over a device tile table (native),
+the emulated pipeline per problem, and CUDA-graph capture and replay."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_05717_gb300 import momms as M
+from paper_1904_05717_gb300 import synthetic as syn
+from util import max_ratio
+
+pytestmark = pytest.mark.gpu
+
+
+def make_problems(count, lo, hi, seed):
+    sizes = syn.log_uniform_sizes(seed, count, lo, hi)
+    probs = []
+    for i, (m, n, k) in enumerate(sizes):
+        A = syn.matrix("uniform", int(m), int(k), seed + 10 * i + 1)
+        B = syn.matrix("uniform", int(k), int(n), seed + 10 * i + 2)
+        C = syn.matrix("uniform", int(m), int(n), seed + 10 * i + 3)
+        probs.append((int(m), int(n), int(k), A, B, C))
+    return probs
+
+
+def run_batched(h, probs, alpha=1.0, beta=1.0):
+    dev = [(M.DeviceMatrix.from_numpy(A), M.DeviceMatrix.from_numpy(B), M.DeviceMatrix.from_numpy(C))
+           for (_, _, _, A, B, C) in probs]
+    cnt = len(probs)
+    args = dict(
+        m=[p[0] for p in probs], n=[p[1] for p in probs], k=[p[2] for p in probs],
+        alpha=[alpha] * cnt, A=[d[0].ptr for d in dev], lda=[d[0].ld for d in dev],
+        B=[d[1].ptr for d in dev], ldb=[d[1].ld for d in dev], beta=[beta] * cnt,
+        C=[d[2].ptr for d in dev], ldc=[d[2].ld for d in dev])
+    M.check(M.momms_gemm_batched(h, **args), "batched")
+    return dev, args
+
+
+def check_all(probs, dev, alpha=1.0, beta=1.0):
+    worst = 0.0
+    for (m, n, k, A, B, C), d in zip(probs, dev):
+        Cref = oracle.dgemm(A, B, C.copy(order="F"), alpha, beta)
+        N = oracle.dgemm_abs(A, B)
+        worst = max(worst, max_ratio(d[2].to_numpy(), Cref, k, alpha, beta, N, C))
+    return worst
+
+
+def test_batched_native_one_launch():
+    probs = make_problems(60, 32, 400, 3000)
+    h = M.Handle(mode=M.MODE_NATIVE)
+    dev, _ = run_batched(h, probs)
+    rep = h.report()
+    assert rep["launches"] == 1
+    assert check_all(probs, dev) <= 1.0
+
+
+def test_batched_emulated():
+    probs = make_problems(12, 64, 700, 4000)
+    h = M.Handle(mode=M.MODE_EMULATED)
+    dev, _ = run_batched(h, probs)
+    assert h.device_status() == M.MOMMS_OK
+    assert check_all(probs, dev) <= 1.0
+
+
+def test_batched_with_empty_and_k_zero_problems():
+    probs = make_problems(5, 32, 100, 5000)
+    probs.append((0, 7, 3, np.zeros((0, 3), order="F"), syn.matrix("uniform", 3, 7, 1), np.zeros((0, 7), order="F")))
+    C0 = syn.matrix("uniform", 9, 4, 2)
+    probs.append((9, 4, 0, np.zeros((9, 0), order="F"), np.zeros((0, 4), order="F"), C0))
+    h = M.Handle(mode=M.MODE_NATIVE)
+    dev, _ = run_batched(h, probs, 1.0, 2.0)
+    assert np.array_equal(dev[-1][2].to_numpy(), 2.0 * C0)
+    assert check_all(probs[:5], dev[:5], 1.0, 2.0) <= 1.0
+
+
+def test_batched_native_cuda_graph_replay():
+    import torch
+    probs = make_problems(40, 32, 300, 6000)
+    h = M.Handle(mode=M.MODE_NATIVE)
+    dev, args = run_batched(h, probs, 1.0, 0.0)  # eager call uploads the tile table
+    torch.cuda.synchronize()
+    eager = [d[2].to_numpy() for d in dev]
+    for d in dev:
+        d[2].storage.fill_(float("nan"))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        M.check(M.momms_gemm_batched(h, stream=s, **args), "capture")
+    g.replay()
+    torch.cuda.synchronize()
+    for d, e in zip(dev, eager):
+        assert np.array_equal(d[2].to_numpy(), e)
