@@ -198,6 +198,35 @@ int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_
                          size_t scratch_bytes, int32_t* status, momms_stream_t stream);
 size_t momms_emu_scratch_bytes(void);
 
+/* ------------------------------------------------ allocation-free variant */
+/* The emulated product (scale, split and slice-product kernels of EMULATED mode)
+ * for callers that cannot allocate device memory: code that runs while a CUDA graph
+ * is being captured, runtimes without a device allocator, or libraries whose
+ * owners forbid any allocation outside their own memory pool.  The paper has no
+ * counterpart; it exists only for such callers.
+ *
+ * It makes no cudaMalloc / cudaFree and calls no allocating routine.  All of its
+ * scratch (exponents, flags, digit slices, FP64 recombination blocks, the status
+ * word) lives in one file-scope device array of momms_noalloc_scratch_bytes()
+ * bytes (64 MiB) that every GPU which loads the library holds until the process
+ * exits.  The caller passes the inputs and the output as for momms_gemm_ex.
+ *   - The first call on a device looks up the array's device address (with that
+ *     device current); make the first call on each device before any stream
+ *     capture.
+ *   - Every call shares the array, which keeps the previous call's contents:
+ *     calls that overlap on the GPU (other streams, other host threads on the same
+ *     device) race on it.  Issue them in order on one stream.
+ *   - slices must be given (1..16).  A problem whose scratch does not fit returns
+ *     MOMMS_ERR_WORKSPACE before anything is enqueued; m = 0 or n = 0 is a no-op;
+ *     k = 0 or alpha = 0 returns MOMMS_ERR_UNSUPPORTED (use momms_gemm_ex).
+ *   - Arguments: op_a 1, op_b 2, m 3, n 4, k 5, slices 6, alpha 7, A 8, lda 9,
+ *     B 10, ldb 11, beta 12, C 13, ldc 14, stream 15 (negative return = index). */
+int momms_gemm_emulated_noalloc(int op_a, int op_b, int64_t m, int64_t n, int64_t k, int slices,
+                                double alpha, const double* A, int64_t lda, const double* B,
+                                int64_t ldb, double beta, double* C, int64_t ldc,
+                                momms_stream_t stream);
+size_t momms_noalloc_scratch_bytes(void);
+
 /* ---------------------------------------------------------------- tuning */
 /* Time the candidate plans (mode x member x slices) for the size buckets of the
  * given shapes (count triples m[i], n[i], k[i]) on `stream`, keep the fastest

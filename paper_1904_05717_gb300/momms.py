@@ -76,6 +76,9 @@ _SIGS = {
     "momms_tune": ([_VP, ctypes.c_char_p, _I64, _VP, _VP, _VP, _VP], _I32),
     "momms_load_plans": ([_VP, ctypes.c_char_p], _I32),
     "momms_probe_peak": ([_I32, ctypes.POINTER(_DBL), _VP], _I32),
+    "momms_gemm_emulated_noalloc": ([_I32, _I32, _I64, _I64, _I64, _I32, _DBL, _VP, _I64, _VP, _I64, _DBL, _VP,
+                                     _I64, _VP], _I32),
+    "momms_noalloc_scratch_bytes": ([], _SZ),
 }
 
 
@@ -174,6 +177,16 @@ def momms_emu_slice_gemm(m, n, k, slices, digit_bits, Ad, Bd, m_pad, n_pad, k_pa
 
 def momms_emu_scratch_bytes():
     return int(lib().momms_emu_scratch_bytes())
+
+
+def momms_gemm_emulated_noalloc(op_a, op_b, m, n, k, slices, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
+    """The allocation-free emulated product (scratch in the library's static device array)."""
+    return lib().momms_gemm_emulated_noalloc(op_a, op_b, m, n, k, slices, alpha, _VP(A), lda, _VP(B), ldb, beta,
+                                             _VP(C), ldc, _stream(stream))
+
+
+def momms_noalloc_scratch_bytes():
+    return int(lib().momms_noalloc_scratch_bytes())
 
 
 def momms_probe_peak(kind, stream=None):
