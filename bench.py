@@ -34,6 +34,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "FP64-accurate GEMM TFLOP/s (2mnk/t) & % roofline, native vs emulated"
+
+# DRAM bytes (read + write) of one slice-product launch from the ncu capture summarised in
+# profiles/slice_gemm_4096.md (m=n=k=4096, S=6), with that launch's algorithmic tensor flops.
+# The 8192^3 launch is too large to capture with --set full, so its traffic is this figure scaled
+# by the tensor flops (the per-pair panel re-reads grow in proportion).  Set to None whenever the
+# slice-product kernel changes until it is captured again.
+NCU_SLICE_CAPTURE = {"dram_bytes": 4.683078e9 + 0.768095e9, "tensor_flops": 21 * 2.0 * 4096 ** 3}
 UNIT = "TFLOP/s"
 
 
@@ -327,8 +334,12 @@ def main():
         achieved = tensor_flops / (slice_ms * 1e-3) / 1e12
         peaks, src = measured_peaks()
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        traffic = None
+        if NCU_SLICE_CAPTURE is not None:
+            traffic = NCU_SLICE_CAPTURE["dram_bytes"] * tensor_flops / NCU_SLICE_CAPTURE["tensor_flops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": "ncu 4096^3 capture scaled by tensor flops (profiles/slice_gemm_4096.md)",
                 "kernel": "momms::emu::slice_gemm_kernel (tcgen05 kind::f16)",
                 "peak_source": f"{src} bf16_tflops_sustained (fp16 rate = bf16 rate)",
                 "algorithmic_flops_per_launch": tensor_flops, "launch_ms": slice_ms}

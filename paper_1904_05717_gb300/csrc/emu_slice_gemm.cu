@@ -58,7 +58,7 @@ struct Cfg {
     static constexpr uint32_t STAGE = A_TILE + B_TILE;
     static constexpr int STAGES = static_cast<int>((SMEM_BUDGET - 2048) / STAGE) > 6
                                       ? 6 : static_cast<int>((SMEM_BUDGET - 2048) / STAGE);
-    static constexpr size_t SMEM_BYTES = 1024 + static_cast<size_t>(STAGES) * STAGE + 256;
+    static constexpr size_t SMEM_BYTES = 1024 + static_cast<size_t>(STAGES) * STAGE + 256 + 5 * BN;
     static constexpr uint32_t IDESC = idesc_f16_f32(BM, BN);
     static_assert(STAGE % 1024 == 0, "stage bases stay 1024-byte aligned for the 128-B swizzle");
 };
@@ -77,7 +77,9 @@ struct Params {
     double alpha, beta_c;
     double* C;
     int64_t ldc;
-    double* scratch;
+    double* scratch;      // FP64 partial recombination R, one BN x BM block per CTA
+    long long* qscratch;  // int64 exact group sums Q, one BN x BM block per CTA
+    uint32_t group_end;   // bit d set: diagonal d closes an exact int64 group
     int32_t* status;
 };
 
@@ -89,6 +91,88 @@ MOMMS_DEV double scale_pow2(double r, int E) {
     int E2 = E - E1;
     E2 = E2 > 1023 ? 1023 : (E2 < -1022 ? -1022 : E2);
     return (r * pow2_normal(E1)) * pow2_normal(E2);
+}
+
+// ---------------------------------------------------------------- recombination
+// One drain thread's columns after the last chunk of diagonal d.  Q / R point at the
+// thread's row in the per-CTA int64 / FP64 scratch blocks (column stride BM).
+struct RecombineCtx {
+    long long* Q;
+    double* R;
+    uint32_t tsum;     // TMEM address of the int32 sums of the last CT columns
+    int sh;            // beta * (position of d in its group)
+    double gscale;     // 2^-(beta * position)
+    double rb;         // 2^-beta
+    bool gfirst;       // d is the least significant diagonal of its group
+    bool rfirst;       // no earlier group has produced R yet
+};
+struct FinalCtx {
+    bool row_ok, eflag;
+    int ei;
+    const int* colexp;       // f_j - 2 beta of the thread's columns (shared memory)
+    const uint8_t* colflag;  // non-finite flags of the thread's columns (shared memory)
+    int ncols;               // columns of the thread inside the matrix
+    double* cp;              // &C[row, first column of the thread]
+    int64_t ldc;
+    double alpha, beta_c, qnan;
+};
+enum { kMid = 0, kGroupEnd = 1, kLast = 2 };
+constexpr int BM_ = kEmuBM;
+
+// 8 columns [c0, c0 + 8): exact int64 group sum, FP64 fold at the group end, C at the end.
+template <int MODE>
+MOMMS_DEV void recombine8(const RecombineCtx& rc, const int32_t (&pv)[8], int c0, const FinalCtx* fc) {
+    long long qv[8];
+    double rv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        qv[j] = rc.gfirst ? 0ll : rc.Q[(c0 + j) * BM_];
+        if (MODE != kMid) rv[j] = rc.rfirst ? 0.0 : rc.R[(c0 + j) * BM_];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const long long p64 = static_cast<long long>(pv[j]);
+        const long long v = rc.gfirst ? p64 : qv[j] + (p64 << rc.sh);
+        if (MODE == kMid) {
+            rc.Q[(c0 + j) * BM_] = v;
+        } else {
+            const double x = static_cast<double>(v);
+            const double r = (rc.rfirst ? x : fma(rv[j], rc.rb, x)) * rc.gscale;
+            if (MODE == kGroupEnd) {
+                rc.R[(c0 + j) * BM_] = r;
+            } else if (fc->row_ok && c0 + j < fc->ncols) {
+                const double y = (fc->eflag || fc->colflag[c0 + j]) ? fc->qnan
+                                                                    : scale_pow2(r, fc->ei + fc->colexp[c0 + j]);
+                double* cp = fc->cp + static_cast<int64_t>(c0 + j) * fc->ldc;
+                *cp = (fc->beta_c == 0.0) ? fc->alpha * y : fma(fc->beta_c, *cp, fc->alpha * y);
+            }
+        }
+    }
+    asm volatile("" ::: "memory");  // one batch of loads in flight at a time
+}
+
+template <int MODE, int CR, int CT>
+MOMMS_DEV void recombine(const RecombineCtx& rc, const int32_t (&acc)[CR], const FinalCtx* fc) {
+#pragma unroll
+    for (int b = 0; b < CR / 8; ++b) {
+        int32_t pv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pv[j] = acc[b * 8 + j];
+        recombine8<MODE>(rc, pv, b * 8, fc);
+    }
+#pragma unroll
+    for (int q = 0; q < CT / 16; ++q) {
+        uint32_t t[16];
+        tmem_ld_32x32b_x16(rc.tsum + q * 16, t);
+        tmem_ld_wait(t);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int32_t pv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) pv[j] = static_cast<int32_t>(t[h * 8 + j]);
+            recombine8<MODE>(rc, pv, CR + q * 16 + h * 8, fc);
+        }
+    }
 }
 
 // Wait used while shutting down after an abort: ignores the abort flag, keeps the time limit.
@@ -116,6 +200,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t* drain = bars + 2 * STAGES + 4;      // 1
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* colexp = reinterpret_cast<int*>(smem + STAGES * STAGE + 256);   // BN column exponents
+    uint8_t* colflag = reinterpret_cast<uint8_t*>(colexp + BN);          // BN column flags
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -257,6 +343,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t aphase[2] = {0u, 0u};
         const double rb = pow2_normal(-p.beta);
         const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+        long long* Q = p.qscratch + (static_cast<size_t>(blockIdx.x) * BN + third * CW) * BM + rloc;
         double* R = p.scratch + (static_cast<size_t>(blockIdx.x) * BN + third * CW) * BM + rloc;
         bool ok = true;
         for (int it = 0; ok; ++it) {
@@ -264,6 +351,16 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!member_tile(p.member, p.group, blockIdx.x, gridDim.x, it, p.tiles_m, p.tiles_n, &tm,
                              &tn))
                 break;
+            int gj = 0;           // position of the current diagonal inside its int64 group
+            bool rfirst = true;   // no FP64 partial R yet for this tile
+            // stage the column exponents (minus 2 beta) and flags of this tile in shared memory
+            named_bar_sync(1, 32 * EPI_WARPS);  // the previous tile's columns are no longer read
+            for (int c = threadIdx.x - 32 * CTRL_WARPS; c < BN; c += 32 * EPI_WARPS) {
+                const int col = tn * BN + c;
+                colexp[c] = col < p.n ? p.f[col] - 2 * p.beta : 0;
+                colflag[c] = col < p.n ? p.ff[col] : 0;
+            }
+            named_bar_sync(1, 32 * EPI_WARPS);
             for (int d = p.S + 1; d >= 2 && ok; --d) {
                 int32_t acc[CR];
 #pragma unroll
@@ -314,45 +411,40 @@ __global__ void __launch_bounds__(THREADS, 1)
                     first = false;
                 }
                 if (!ok) break;
-                // Horner step, least significant diagonal first, kept in FP64 scratch:
-                // R = P_{S+1};  R = P_d + 2^-beta R  (d = S..2)
-                const bool lsd = (d == p.S + 1);
-#pragma unroll
-                for (int c = 0; c < CR; ++c) {
-                    const double v = static_cast<double>(acc[c]);
-                    R[c * BM] = lsd ? v : fma(R[c * BM], rb, v);
-                    if ((c & 7) == 7) asm volatile("" ::: "memory");  // bound the loads in flight
-                }
-#pragma unroll
-                for (int q = 0; q < CT / 16; ++q) {
-                    uint32_t t[16];
-                    tmem_ld_32x32b_x16(tsum + q * 16, t);
-                    tmem_ld_wait(t);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        double* rp = R + (CR + q * 16 + j) * BM;
-                        const double v = static_cast<double>(static_cast<int32_t>(t[j]));
-                        *rp = lsd ? v : fma(*rp, rb, v);
-                        if ((j & 7) == 7) asm volatile("" ::: "memory");
-                    }
-                }
-                if (d == 2) {
-                    // C := alpha * 2^(e_i + f_j - 2 beta) R_2 + beta_c C
+                // Recombination, least significant diagonal first.  Inside a group the
+                // diagonal sums are combined exactly in int64, Q = sum_j P_{hi-j} 2^(beta j)
+                // (the host chose the groups so that |Q| < 2^63); at the group's most
+                // significant diagonal lo, R = 2^(-beta (hi-lo)) (Q + 2^-beta R_prev) in FP64.
+                // The last group ends at d = 2 and goes straight to C:
+                //     C := alpha 2^(e_i + f_j - 2 beta) R + beta_c C.
+                const bool gfirst = (gj == 0);
+                const bool gend = (p.group_end >> d) & 1u;
+                const RecombineCtx rc{Q, R, tsum, p.beta * gj, pow2_normal(-p.beta * gj), rb, gfirst, rfirst};
+                if (!gend) {
+                    recombine<kMid, CR, CT>(rc, acc, nullptr);
+                } else if (d != 2) {
+                    recombine<kGroupEnd, CR, CT>(rc, acc, nullptr);
+                } else {
                     const int row = tm * BM + rloc;
-                    const int col0 = tn * BN + third * CW;
-                    if (row < p.m) {
-                        const int ei = p.e[row];
-                        const bool eflag = p.ef[row] != 0;
-#pragma unroll 4
-                        for (int c = 0; c < CW; ++c) {
-                            const int col = col0 + c;
-                            if (col >= p.n) break;
-                            const double r2 = R[c * BM];
-                            const double x = (eflag || p.ff[col]) ? qnan : scale_pow2(r2, ei + p.f[col] - 2 * p.beta);
-                            double* cp = p.C + row + static_cast<int64_t>(col) * p.ldc;
-                            *cp = (p.beta_c == 0.0) ? p.alpha * x : fma(p.beta_c, *cp, p.alpha * x);
-                        }
-                    }
+                    FinalCtx fc;
+                    fc.row_ok = row < p.m;
+                    fc.ei = fc.row_ok ? p.e[row] : 0;
+                    fc.eflag = fc.row_ok ? (p.ef[row] != 0) : false;
+                    fc.colexp = colexp + third * CW;
+                    fc.colflag = colflag + third * CW;
+                    fc.ncols = min(CW, p.n - (tn * BN + third * CW));
+                    fc.cp = p.C + row + static_cast<int64_t>(tn * BN + third * CW) * p.ldc;
+                    fc.ldc = p.ldc;
+                    fc.alpha = p.alpha;
+                    fc.beta_c = p.beta_c;
+                    fc.qnan = qnan;
+                    recombine<kLast, CR, CT>(rc, acc, &fc);
+                }
+                if (gend) {
+                    gj = 0;
+                    rfirst = false;
+                } else {
+                    ++gj;
                 }
             }
         }
@@ -409,7 +501,9 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     const int64_t tiles = tiles_m * tiles_n;
     int64_t ctas = a.max_ctas > 0 ? a.max_ctas : sms;
     if (ctas > tiles) ctas = tiles;
-    if (a.scratch_bytes < static_cast<size_t>(ctas) * BN * BM * sizeof(double)) return cudaErrorInvalidValue;
+    const size_t half = static_cast<size_t>(ctas) * BN * BM * sizeof(double);
+    if (a.scratch_bytes < 2 * half) return cudaErrorInvalidValue;
+    // int64 group sums Q in the first half, FP64 partial sums R (several groups only) in the second
 
     CUtensorMap mapA, mapB;
     if (!make_map(&mapA, a.Ad, a.k_pad, a.m_pad, a.S, BM)) return cudaErrorInvalidValue;
@@ -447,7 +541,9 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         p.beta_c = npass == 0 ? a.beta_c : 1.0;
         p.C = a.C;
         p.ldc = a.ldc;
-        p.scratch = static_cast<double*>(a.scratch);
+        p.qscratch = static_cast<long long*>(a.scratch);
+        p.scratch = reinterpret_cast<double*>(static_cast<char*>(a.scratch) + half);
+        p.group_end = emu_group_ends(a.S, a.beta, p.nslab * static_cast<int64_t>(BK));
         p.status = a.status;
         slice_gemm_kernel<BN><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(mapA, mapB, p);
         cudaError_t e = cudaGetLastError();
@@ -471,8 +567,38 @@ int device_sm_count() {
     return sms;
 }
 
-size_t emu_scratch_bytes(int num_sms) {
-    return static_cast<size_t>(num_sms) * kEmuBNMax * emu::BM * sizeof(double);
+size_t emu_scratch_bytes(int num_sms) { return emu_scratch_bytes_for_ctas(num_sms); }
+
+size_t emu_scratch_bytes_for_ctas(int ctas) {
+    // FP64 partial sums R and int64 group sums Q, one 128 x 192 block each per CTA
+    return 2 * static_cast<size_t>(ctas) * kEmuBNMax * emu::BM * sizeof(double);
+}
+
+uint32_t emu_group_ends(int S, int beta, int64_t k_pass) {
+    // Diagonal d sums (d - 1) pair products over k_pass, each |digit product| <= (2^beta - 1)^2:
+    // |P_d| <= (d - 1) (2^beta - 1)^2 k_pass.  Walking from the least significant diagonal,
+    // a group [lo, hi] holds Q = sum_{d=lo}^{hi} P_d 2^(beta (hi - d)); a group is closed
+    // before the bound on |Q| would reach 2^63.
+    const unsigned __int128 limit = static_cast<unsigned __int128>(1) << 63;
+    const unsigned __int128 dmax = static_cast<unsigned __int128>((1ll << beta) - 1);
+    uint32_t mask = 0;
+    unsigned __int128 acc = 0;
+    int j = 0;
+    for (int d = S + 1; d >= 2; --d) {
+        const unsigned __int128 pb =
+            static_cast<unsigned __int128>(d - 1) * dmax * dmax * static_cast<unsigned __int128>(k_pass);
+        bool fits = (j == 0);
+        if (j > 0 && beta * j < 64) fits = acc + (pb << (beta * j)) < limit;
+        if (!fits) {
+            mask |= 1u << (d + 1);  // diagonal d + 1 closed the previous group
+            acc = 0;
+            j = 0;
+        }
+        acc += pb << (beta * j);
+        ++j;
+    }
+    mask |= 1u << 2;  // the most significant diagonal always closes the last group
+    return mask;
 }
 
 int64_t emu_max_k_per_pass(int S, int beta) {

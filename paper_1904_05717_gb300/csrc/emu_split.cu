@@ -57,7 +57,19 @@ __global__ void scale_rows_contig(const double* __restrict__ X, int64_t ld, int6
     if (q1 > inner) q1 = inner;
     int emax = kNoExp, nf = 0;
     float sum = 0.f;
-    for (int64_t q = q0; q < q1; ++q) {
+    int64_t q = q0;
+    for (; q + 4 <= q1; q += 4) {  // four independent loads in flight per thread
+        double x[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) x[t] = X[r + (q + t) * ld];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int e = elem_exponent(x[t], &nf);
+            emax = e > emax ? e : emax;
+            if (e != kNoExp) sum += static_cast<float>(fabs(x[t]));
+        }
+    }
+    for (; q < q1; ++q) {
         const double x = X[r + q * ld];
         const int e = elem_exponent(x, &nf);
         emax = e > emax ? e : emax;
@@ -83,7 +95,19 @@ __global__ void scale_inner_contig(const double* __restrict__ X, int64_t ld, int
     int emax = kNoExp, nf = 0;
     float sum = 0.f;
     const double* x = X + r * ld;
-    for (int64_t q = lane; q < inner; q += 32) {
+    int64_t q = lane;
+    for (; q + 96 < inner; q += 128) {  // four independent loads in flight per lane
+        double v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v[t] = x[q + 32 * t];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int e = elem_exponent(v[t], &nf);
+            emax = e > emax ? e : emax;
+            if (e != kNoExp) sum += static_cast<float>(fabs(v[t]));
+        }
+    }
+    for (; q < inner; q += 32) {
         const int e = elem_exponent(x[q], &nf);
         emax = e > emax ? e : emax;
         if (e != kNoExp) sum += static_cast<float>(fabs(x[q]));
@@ -301,7 +325,7 @@ cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, con
     }
     const int64_t total = rows_pad * (inner_pad / 4);
     int64_t blocks = (total + 255) / 256;
-    const int64_t cap = static_cast<int64_t>(device_sm_count()) * 16;
+    const int64_t cap = static_cast<int64_t>(device_sm_count()) * 32;
     if (blocks > cap) blocks = cap;
     split_inner_contig<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(X, ldx, rows, inner, exps, flags,
                                                                           S, beta, dg, rows_pad, inner_pad);

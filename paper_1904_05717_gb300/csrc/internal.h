@@ -71,6 +71,9 @@ int emu_pick_bn(int64_t n, int requested);
 // Launches the slice-product kernel once per k pass; *passes receives the count.
 cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_t stream);
 size_t emu_scratch_bytes(int num_sms);
+size_t emu_scratch_bytes_for_ctas(int ctas);
+// Bit d set: diagonal d is the most significant of an exact int64 group (S, beta, k per pass).
+uint32_t emu_group_ends(int S, int beta, int64_t k_pass);
 // Largest k one pass may cover so that every diagonal sum stays below 2^31.
 int64_t emu_max_k_per_pass(int S, int beta);
 // Products per FP32 accumulation chunk (every partial sum below 2^24), in 64-wide slabs.

@@ -100,7 +100,7 @@ extern "C" int momms_gemm_emulated_noalloc(int op_a, int op_b, int64_t m, int64_
     const size_t off_Ad = o;      o += up256(size_t(2) * slices * m * k_pad);
     const size_t off_Bd = o;      o += up256(size_t(2) * slices * n * k_pad);
     const size_t off_R = o;
-    const size_t r_bytes = size_t(ctas) * momms::kEmuBNMax * momms::kEmuBM * sizeof(double);
+    const size_t r_bytes = momms::emu_scratch_bytes_for_ctas(ctas);
     o += up256(r_bytes);
     if (o > kNoAllocBytes) return MOMMS_ERR_WORKSPACE;
 

@@ -89,3 +89,35 @@ def test_batched_native_cuda_graph_replay():
     torch.cuda.synchronize()
     for d, e in zip(dev, eager):
         assert np.array_equal(d[2].to_numpy(), e)
+
+
+def test_batched_2000_uneven_problems_native_one_launch():
+    # the batched workload: 2000 problems, m, n, k log-uniform in [32, 2048], uniform[-1, 1];
+    # one persistent launch; every 10th problem checked against the oracle in full
+    import torch
+    count = 2000
+    sizes = syn.log_uniform_sizes(syn.workload_seed(4, "A"), count, 32, 2048)
+    h = M.Handle(mode=M.MODE_NATIVE)
+    dev, hosts = [], []
+    for i, (m, n, k) in enumerate(sizes):
+        m, n, k = int(m), int(n), int(k)
+        A = syn.matrix("uniform", m, k, 100000 + 3 * i)
+        B = syn.matrix("uniform", k, n, 100001 + 3 * i)
+        C = syn.matrix("uniform", m, n, 100002 + 3 * i)
+        dev.append((M.DeviceMatrix.from_numpy(A), M.DeviceMatrix.from_numpy(B), M.DeviceMatrix.from_numpy(C)))
+        hosts.append((m, n, k, A, B, C) if i % 10 == 0 else None)
+    args = dict(m=[int(s[0]) for s in sizes], n=[int(s[1]) for s in sizes], k=[int(s[2]) for s in sizes],
+                alpha=[1.0] * count, A=[d[0].ptr for d in dev], lda=[d[0].ld for d in dev],
+                B=[d[1].ptr for d in dev], ldb=[d[1].ld for d in dev], beta=[1.0] * count,
+                C=[d[2].ptr for d in dev], ldc=[d[2].ld for d in dev])
+    M.check(M.momms_gemm_batched(h, **args), "batched 2000")
+    torch.cuda.synchronize()
+    assert h.report()["launches"] == 1
+    worst = 0.0
+    for hst, d in zip(hosts, dev):
+        if hst is None:
+            continue
+        m, n, k, A, B, C = hst
+        Cref = oracle.dgemm(A, B, C.copy(order="F"), 1.0, 1.0)
+        worst = max(worst, max_ratio(d[2].to_numpy(), Cref, k, 1.0, 1.0, oracle.dgemm_abs(A, B), C))
+    assert worst <= 1.0

@@ -129,13 +129,25 @@ def test_emulated_within_bound(kind, phi, S, m, n, k):
 
 def test_emulated_matches_oracle_emulation():
     # same digits, same pair set: only the FP64 rounding of the recombination differs
-    m, n, k, S = 100, 90, 300, 6
+    m, n, k, S = 100, 90, 300, 11  # several int64 groups: FP64 folds between them
     A = syn.matrix("phi", m, k, 51, phi=1.0)
     B = syn.matrix("phi", k, n, 52, phi=1.0)
     Co, _ = oracle.emulated_dgemm(A, B, S, BETA)
     C, _, _ = emulated(A, B, F(np.zeros((m, n))), 1.0, 0.0, S)
     N = oracle.dgemm_abs(A, B)
     assert np.all(np.abs(C - Co) <= 4 * (S + 2) * U * N + 2.0 ** -1021)
+
+
+@pytest.mark.parametrize("S", [4, 6])
+def test_emulated_single_group_bitwise_vs_oracle_emulation(S):
+    # With S <= 6 and k <= 8192 every diagonal sum fits one exact int64 group, so the
+    # kernel's recombination is the exact digit expansion rounded once -- the oracle's.
+    m, n, k = 200, 300, 1000
+    A = syn.matrix("phi", m, k, 55, phi=1.0)
+    B = syn.matrix("phi", k, n, 56, phi=1.0)
+    Co, _ = oracle.emulated_dgemm(A, B, S, BETA)
+    C, _, _ = emulated(A, B, F(np.zeros((m, n))), 1.0, 0.0, S)
+    assert np.array_equal(C, Co)
 
 
 @pytest.mark.parametrize("opa,opb", [(1, 0), (0, 1), (1, 1)])
