@@ -64,6 +64,14 @@ struct momms_handle_s {
     BatchProblem* dev_probs = nullptr;
     size_t dev_probs_cap = 0;
     std::vector<BatchProblem> host_probs;  // the table last uploaded to dev_probs
+    // batched emulated products: per-problem statistics, device tables, spread readback
+    void* batch_meta = nullptr;
+    size_t batch_meta_cap = 0;
+    void* batch_tables = nullptr;
+    size_t batch_tables_cap = 0;
+    std::vector<char> host_tables;         // the bytes last uploaded to batch_tables
+    int* spread_host_big = nullptr;        // pinned, 2 per problem
+    size_t spread_host_cap = 0;
     std::map<uint32_t, Plan> plans;
 };
 
@@ -124,6 +132,24 @@ int ensure_workspace(momms_handle_t h, size_t bytes, void** ws) {
         h->own_ws_bytes = bytes;
     }
     *ws = h->own_ws;
+    return MOMMS_OK;
+}
+
+// Grows a handle-owned device buffer (contents are not kept).
+int grow_device(void** buf, size_t* cap, size_t bytes) {
+    if (*cap >= bytes && *buf) return MOMMS_OK;
+    if (*buf) {
+        cudaDeviceSynchronize();  // enqueued work may still use the old block
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    if (cudaMalloc(buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return MOMMS_ERR_ALLOC;
+    }
+    *cap = bytes;
     return MOMMS_OK;
 }
 
@@ -230,7 +256,7 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
     ce = momms::launch_emu_scale(1, opb, n, k, B, ldb, f, ff, need_stats ? l1b : nullptr, s);
     if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-    launches += 2;
+    launches += momms::emu_scale_kernel_count(0, opa) + momms::emu_scale_kernel_count(1, opb);
     double est = 0.0;
     if (S == 0) {
         // data-driven slice count: one small device reduction and a readback
@@ -274,6 +300,184 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     h->report.tile_n = momms::emu_pick_bn(n, h->tile_n);
     h->report.launches = launches;
     h->report.est_err_ratio = est;
+    return MOMMS_OK;
+}
+
+// Batched emulated products (op = N, N): 2 scale + 2 split launches over work lists and ONE
+// persistent slice-product launch over the concatenated tiles of all problems.  With a fixed
+// slice count nothing is read back, and a repeated call with the same problems only re-enqueues
+// the five kernels (tables are uploaded only when they change), so it can be graph-captured.
+// With the data-driven slice count the per-problem spreads are read back once per call.
+int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, const int64_t* m, const int64_t* n,
+                         const int64_t* k, const double* alpha, const double* const* A, const int64_t* lda,
+                         const double* const* B, const int64_t* ldb, const double* beta, double* const* C,
+                         const int64_t* ldc, cudaStream_t s) {
+    const int count = static_cast<int>(idx.size());
+    const int bb = h->digit_bits;
+    // ---- per-problem statistics region (exponents, flags, spreads)
+    std::vector<size_t> off_e(count), off_ef(count), off_f(count), off_ff(count);
+    size_t meta = align256(sizeof(int32_t) * 2 * static_cast<size_t>(count));  // spreads first
+    for (int i = 0; i < count; ++i) {
+        const int64_t p = idx[i];
+        off_e[i] = meta;  meta += align256(sizeof(int32_t) * m[p]);
+        off_ef[i] = meta; meta += align256(static_cast<size_t>(m[p]));
+        off_f[i] = meta;  meta += align256(sizeof(int32_t) * n[p]);
+        off_ff[i] = meta; meta += align256(static_cast<size_t>(n[p]));
+    }
+    int rc = grow_device(&h->batch_meta, &h->batch_meta_cap, meta);
+    if (rc) return rc;
+    char* mb = static_cast<char*>(h->batch_meta);
+    int32_t* spreads = reinterpret_cast<int32_t*>(mb);
+
+    std::vector<momms::EmuBatchPrep> prep(count);
+    std::vector<int2> sa_items, sb_items, pa_items, pb_items;
+    for (int i = 0; i < count; ++i) {
+        const int64_t p = idx[i];
+        momms::EmuBatchPrep& q = prep[i];
+        q.A = A[p]; q.B = B[p]; q.lda = lda[p]; q.ldb = ldb[p];
+        q.m = static_cast<int32_t>(m[p]); q.n = static_cast<int32_t>(n[p]); q.k = static_cast<int32_t>(k[p]);
+        q.k_pad = static_cast<int32_t>(round_up(k[p], momms::kEmuBK));
+        q.S = h->slices; q.beta = bb;
+        q.e = reinterpret_cast<int32_t*>(mb + off_e[i]);
+        q.ef = reinterpret_cast<uint8_t*>(mb + off_ef[i]);
+        q.f = reinterpret_cast<int32_t*>(mb + off_f[i]);
+        q.ff = reinterpret_cast<uint8_t*>(mb + off_ff[i]);
+        q.spread = spreads + 2 * i;
+        for (int64_t b = 0; b < momms::emu_batch_scale_a_blocks(m[p]); ++b) sa_items.push_back(make_int2(i, (int)b));
+        for (int64_t b = 0; b < momms::emu_batch_scale_b_blocks(n[p]); ++b) sb_items.push_back(make_int2(i, (int)b));
+        for (int64_t b = 0; b < momms::emu_batch_split_a_blocks(m[p], q.k_pad); ++b) pa_items.push_back(make_int2(i, (int)b));
+        for (int64_t b = 0; b < momms::emu_batch_split_b_blocks(n[p], q.k_pad); ++b) pb_items.push_back(make_int2(i, (int)b));
+    }
+    if (sa_items.size() > INT32_MAX || pa_items.size() > INT32_MAX || pb_items.size() > INT32_MAX)
+        return MOMMS_ERR_UNSUPPORTED;
+
+    // ---- slice counts
+    std::vector<int> S(count, h->slices);
+    const bool auto_s = h->slices <= 0;
+    // ---- device tables: [prep][items sa][sb][pa][pb][gemm table]; rebuilt below once S is known
+    auto upload = [&](const std::vector<momms::EmuBatchProblem>& gemm, size_t* off_gemm, size_t* off_items) -> int {
+        std::vector<char> buf;
+        auto put = [&](const void* src, size_t bytes) {
+            size_t o = align256(buf.size());
+            buf.resize(o + bytes);
+            if (bytes) std::memcpy(buf.data() + o, src, bytes);
+            return o;
+        };
+        put(prep.data(), sizeof(momms::EmuBatchPrep) * prep.size());
+        off_items[0] = put(sa_items.data(), sizeof(int2) * sa_items.size());
+        off_items[1] = put(sb_items.data(), sizeof(int2) * sb_items.size());
+        off_items[2] = put(pa_items.data(), sizeof(int2) * pa_items.size());
+        off_items[3] = put(pb_items.data(), sizeof(int2) * pb_items.size());
+        *off_gemm = put(gemm.data(), sizeof(momms::EmuBatchProblem) * gemm.size());
+        const bool same = buf.size() == h->host_tables.size() && h->batch_tables &&
+                          std::memcmp(buf.data(), h->host_tables.data(), buf.size()) == 0;
+        if (same) return MOMMS_OK;
+        int r = grow_device(&h->batch_tables, &h->batch_tables_cap, buf.size());
+        if (r) return r;
+        if (cudaMemcpyAsync(h->batch_tables, buf.data(), buf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        h->host_tables.swap(buf);
+        return MOMMS_OK;
+    };
+    size_t off_gemm = 0, off_items[4] = {0, 0, 0, 0};
+    char* tb = nullptr;
+    auto items = [&](int w) { return reinterpret_cast<const int2*>(tb + off_items[w]); };
+    int64_t launches = 0;
+    if (auto_s) {
+        // statistics first, then one readback of every problem's spreads
+        for (auto& q : prep) q.S = 1;
+        rc = upload({}, &off_gemm, off_items);
+        if (rc) return rc;
+        tb = static_cast<char*>(h->batch_tables);
+        if (cudaMemsetAsync(spreads, 0, sizeof(int32_t) * 2 * count, s) != cudaSuccess) return MOMMS_ERR_CUDA;
+        if (momms::launch_emu_batch_scale(reinterpret_cast<const momms::EmuBatchPrep*>(tb), items(0),
+                                          (int)sa_items.size(), items(1), (int)sb_items.size(), s) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        launches += 2;
+        if (h->spread_host_cap < static_cast<size_t>(2 * count)) {
+            if (h->spread_host_big) cudaFreeHost(h->spread_host_big);
+            h->spread_host_big = nullptr;
+            h->spread_host_cap = 0;
+            if (cudaMallocHost(&h->spread_host_big, sizeof(int) * 2 * count) != cudaSuccess) return MOMMS_ERR_ALLOC;
+            h->spread_host_cap = 2 * count;
+        }
+        if (cudaMemcpyAsync(h->spread_host_big, spreads, sizeof(int) * 2 * count, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        for (int i = 0; i < count; ++i)
+            S[i] = slices_from_spread(h->spread_host_big[2 * i] / 16.0, h->spread_host_big[2 * i + 1] / 16.0,
+                                      k[idx[i]], bb, nullptr);
+    }
+    for (int i = 0; i < count; ++i) {
+        if (S[i] > MOMMS_MAX_SLICES || k[idx[i]] > momms::emu_max_k_per_pass(S[i], bb)) return MOMMS_ERR_UNSUPPORTED;
+    }
+    // ---- digits and recombination scratch in the workspace
+    std::vector<size_t> off_ad(count), off_bd(count);
+    size_t ws_bytes = 0;
+    for (int i = 0; i < count; ++i) {
+        off_ad[i] = ws_bytes; ws_bytes += align256(size_t(2) * S[i] * prep[i].m * prep[i].k_pad);
+        off_bd[i] = ws_bytes; ws_bytes += align256(size_t(2) * S[i] * prep[i].n * prep[i].k_pad);
+    }
+    const size_t off_scratch = ws_bytes;
+    const size_t scratch_bytes = momms::emu_scratch_bytes(momms::device_sm_count());
+    ws_bytes += align256(scratch_bytes);
+    void* ws = nullptr;
+    rc = ensure_workspace(h, ws_bytes, &ws);
+    if (rc) return rc;
+    char* w = static_cast<char*>(ws);
+    std::vector<momms::EmuBatchProblem> gemm(count);
+    int64_t tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t p = idx[i];
+        momms::EmuBatchPrep& q = prep[i];
+        q.S = S[i];
+        q.Ad = w + off_ad[i];
+        q.Bd = w + off_bd[i];
+        momms::EmuBatchProblem& g = gemm[i];
+        std::memset(&g, 0, sizeof(g));
+        if (!momms::emu_make_digit_map(&g.mapA, q.Ad, q.k_pad, q.m, S[i], momms::kEmuBM) ||
+            !momms::emu_make_digit_map(&g.mapB, q.Bd, q.k_pad, q.n, S[i], momms::kEmuBNMax))
+            return MOMMS_ERR_UNSUPPORTED;
+        g.e = q.e; g.ef = q.ef; g.f = q.f; g.ff = q.ff;
+        g.C = C[p]; g.ldc = ldc[p]; g.alpha = alpha[p]; g.beta_c = beta[p];
+        g.m = q.m; g.n = q.n; g.S = S[i]; g.beta = bb;
+        g.nslab = q.k_pad / momms::kEmuBK;
+        g.chunk_slabs = momms::emu_chunk_slabs(bb);
+        g.group_end = momms::emu_group_ends(S[i], bb, q.k_pad);
+        g.tiles_n = static_cast<int32_t>((q.n + momms::kEmuBNMax - 1) / momms::kEmuBNMax);
+        g.tile0 = tiles;
+        tiles += ((q.m + momms::kEmuBM - 1) / momms::kEmuBM) * g.tiles_n;
+    }
+    rc = upload(gemm, &off_gemm, off_items);
+    if (rc) return rc;
+    tb = static_cast<char*>(h->batch_tables);
+    const auto* dprep = reinterpret_cast<const momms::EmuBatchPrep*>(tb);
+    if (!auto_s) {
+        if (momms::launch_emu_batch_scale(dprep, items(0), (int)sa_items.size(), items(1), (int)sb_items.size(), s) !=
+            cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        launches += 2;
+    }
+    if (momms::launch_emu_batch_split(dprep, items(2), (int)pa_items.size(), items(3), (int)pb_items.size(), s) !=
+        cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    launches += 2;
+    cudaError_t ce = momms::launch_emu_slice_gemm_batched(reinterpret_cast<const momms::EmuBatchProblem*>(tb + off_gemm),
+                                                          count, tiles, w + off_scratch, scratch_bytes, h->status, s);
+    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+    launches += 1;
+    int smin = MOMMS_MAX_SLICES, smax = 0;
+    for (int v : S) { smin = std::min(smin, v); smax = std::max(smax, v); }
+    h->report = momms_report_t{};
+    h->report.mode = MOMMS_MODE_EMULATED;
+    h->report.member = MOMMS_MEMBER_AUTO;
+    h->report.slices = smax;
+    h->report.digit_bits = bb;
+    h->report.k_passes = 1;
+    h->report.tile_m = momms::kEmuBM;
+    h->report.tile_n = momms::kEmuBNMax;
+    h->report.launches = launches;
     return MOMMS_OK;
 }
 
@@ -371,6 +575,9 @@ int momms_destroy(momms_handle_t h) {
     cudaDeviceSynchronize();
     if (h->own_ws) cudaFree(h->own_ws);
     if (h->dev_probs) cudaFree(h->dev_probs);
+    if (h->batch_meta) cudaFree(h->batch_meta);
+    if (h->batch_tables) cudaFree(h->batch_tables);
+    if (h->spread_host_big) cudaFreeHost(h->spread_host_big);
     if (h->status) cudaFree(h->status);
     if (h->spread_host) cudaFreeHost(h->spread_host);
     h->magic = 0;
@@ -542,15 +749,28 @@ int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const 
     }
     const bool emulated = h->mode == MOMMS_MODE_EMULATED;
     if (emulated) {
-        // emulated batches: one pipeline per problem on the same stream
+        // problems with work go to one batched pipeline; the rest only scale C
+        std::vector<int64_t> idx;
         int64_t launches = 0;
         for (int64_t i = 0; i < count; ++i) {
-            int rc = gemm_dispatch(h, MOMMS_OP_N, MOMMS_OP_N, m[i], n[i], k[i], alpha[i], A[i], lda[i],
-                                   B[i], ldb[i], beta[i], C[i], ldc[i], s);
-            if (rc) return rc;
-            launches += h->report.launches;
+            if (m[i] == 0 || n[i] == 0) continue;
+            if (k[i] == 0 || alpha[i] == 0.0) {
+                int rc = scale_c(m[i], n[i], beta[i], C[i], ldc[i], s);
+                if (rc) return rc;
+                ++launches;
+                continue;
+            }
+            idx.push_back(i);
         }
-        h->report.launches = launches;
+        if (idx.empty()) {
+            h->report = momms_report_t{};
+            h->report.launches = launches;
+            return MOMMS_OK;
+        }
+        if (idx.size() > (size_t(1) << 24)) return MOMMS_ERR_UNSUPPORTED;
+        int rc = run_emulated_batched(h, idx, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+        if (rc) return rc;
+        h->report.launches += launches;
         return MOMMS_OK;
     }
     // native: one persistent launch over a device tile table

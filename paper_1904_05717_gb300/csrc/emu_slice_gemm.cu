@@ -63,13 +63,13 @@ struct Cfg {
     static_assert(STAGE % 1024 == 0, "stage bases stay 1024-byte aligned for the 128-B swizzle");
 };
 
-struct Params {
+// The per-problem quantities every role needs for one tile.
+struct Prob {
     int m, n;
     int S, beta;
     int chunk_slabs;
     int slab0, nslab;
-    int tiles_m, tiles_n;
-    int member, group;
+    uint32_t group_end;       // bit d set: diagonal d closes an exact int64 group
     const int32_t* e;
     const uint8_t* ef;
     const int32_t* f;
@@ -77,11 +77,61 @@ struct Params {
     double alpha, beta_c;
     double* C;
     int64_t ldc;
-    double* scratch;      // FP64 partial recombination R, one BN x BM block per CTA
-    long long* qscratch;  // int64 exact group sums Q, one BN x BM block per CTA
-    uint32_t group_end;   // bit d set: diagonal d closes an exact int64 group
+};
+
+struct Params {
+    Prob one;                 // single problem (unused when table != nullptr)
+    int tiles_m, tiles_n;
+    int member, group;
+    const EmuBatchProblem* table;  // batched: one entry per problem, ordered by tile0
+    int count;
+    int64_t total_tiles;
+    double* scratch;          // FP64 partial recombination R, one BN x BM block per CTA
+    long long* qscratch;      // int64 exact group sums Q, one BN x BM block per CTA
     int32_t* status;
 };
+
+// The it-th tile of this CTA: its problem (-1 = the single problem of p.one) and tile
+// coordinates.  A single problem uses the member's tile order; a batch walks the
+// concatenated tile list of all problems cyclically.
+MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn) {
+    if (p.table == nullptr) {
+        *prob = -1;
+        return member_tile(p.member, p.group, blockIdx.x, gridDim.x, it, p.tiles_m, p.tiles_n, tm, tn);
+    }
+    const int64_t t = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
+    if (t >= p.total_tiles) return false;
+    int lo = 0, hi = p.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.table[mid].tile0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t local = t - p.table[lo].tile0;
+    const int tiles_n = p.table[lo].tiles_n;
+    *prob = lo;
+    *tm = static_cast<int>(local / tiles_n);
+    *tn = static_cast<int>(local % tiles_n);
+    return true;
+}
+
+// Small per-tile integers every role keeps in registers.
+struct TileInts {
+    int S, beta, chunk_slabs, slab0, nslab;
+    uint32_t group_end;
+};
+MOMMS_DEV TileInts tile_ints(const Params& p, int prob) {
+    TileInts t;
+    if (prob < 0) {
+        t.S = p.one.S; t.beta = p.one.beta; t.chunk_slabs = p.one.chunk_slabs;
+        t.slab0 = p.one.slab0; t.nslab = p.one.nslab; t.group_end = p.one.group_end;
+    } else {
+        const EmuBatchProblem& b = p.table[prob];
+        t.S = b.S; t.beta = b.beta; t.chunk_slabs = b.chunk_slabs;
+        t.slab0 = 0; t.nslab = b.nslab; t.group_end = b.group_end;
+    }
+    return t;
+}
 
 // r * 2^E with one rounding for every E (two exact power-of-two factors outside
 // the normal exponent range; results beyond the double range saturate to 0 / inf).
@@ -231,31 +281,34 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            prefetch_tensormap(&tmA);
-            prefetch_tensormap(&tmB);
+            if (p.table == nullptr) {
+                prefetch_tensormap(&tmA);
+                prefetch_tensormap(&tmB);
+            }
             uint32_t stage = 0, phase = 0;
             int last_phase[STAGES];
             for (int i = 0; i < STAGES; ++i) last_phase[i] = -1;
             bool ok = true;
-            for (int64_t it = 0; ok; ++it) {
-                int tm, tn;
-                if (!member_tile(p.member, p.group, blockIdx.x, gridDim.x, it, p.tiles_m, p.tiles_n,
-                                 &tm, &tn))
-                    break;
-                for (int d = p.S + 1; d >= 2 && ok; --d) {
+            for (int it = 0; ok; ++it) {
+                int tm, tn, prob;
+                if (!tile_of(p, it, &prob, &tm, &tn)) break;
+                const TileInts pr = tile_ints(p, prob);
+                const CUtensorMap* mapA = prob < 0 ? &tmA : &p.table[prob].mapA;
+                const CUtensorMap* mapB = prob < 0 ? &tmB : &p.table[prob].mapB;
+                for (int d = pr.S + 1; d >= 2 && ok; --d) {
                     for (int s = 1; s <= d - 1 && ok; ++s) {
-                        for (int j = 0; j < p.nslab; ++j) {
+                        for (int j = 0; j < pr.nslab; ++j) {
                             if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
                                 ok = false;
                                 break;
                             }
                             uint8_t* sa = smem + stage * STAGE;
                             mbar_arrive_expect_tx(&full[stage], STAGE);
-                            const int x = (p.slab0 + j) * BK;
+                            const int x = (pr.slab0 + j) * BK;
                             // A slice s rows [tm*BM, +BM), B slice d-s rows [tn*BN, +BN);
                             // rows past the end of a slice are zero-filled by the copy engine
-                            tma_load_3d(sa, &tmA, &full[stage], x, tm * BM, s - 1);
-                            tma_load_3d(sa + A_TILE, &tmB, &full[stage], x, tn * BN, d - s - 1);
+                            tma_load_3d(sa, mapA, &full[stage], x, tm * BM, s - 1);
+                            tma_load_3d(sa + A_TILE, mapB, &full[stage], x, tn * BN, d - s - 1);
                             last_phase[stage] = static_cast<int>(phase);
                             if (++stage == STAGES) {
                                 stage = 0;
@@ -279,15 +332,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t aphase[2] = {0u, 0u};
             bool ok = true;
             bool issued = false;
-            for (int64_t it = 0; ok; ++it) {
-                int tm, tn;
-                if (!member_tile(p.member, p.group, blockIdx.x, gridDim.x, it, p.tiles_m, p.tiles_n,
-                                 &tm, &tn))
-                    break;
-                for (int d = p.S + 1; d >= 2 && ok; --d) {
-                    const int units = (d - 1) * p.nslab;
+            for (int it = 0; ok; ++it) {
+                int tm, tn, prob;
+                if (!tile_of(p, it, &prob, &tm, &tn)) break;
+                const TileInts pr = tile_ints(p, prob);
+                for (int d = pr.S + 1; d >= 2 && ok; --d) {
+                    const int units = (d - 1) * pr.nslab;
                     for (int u = 0; u < units && ok;) {
-                        const int cnt = min(p.chunk_slabs, units - u);
+                        const int cnt = min(pr.chunk_slabs, units - u);
                         if (!mbar_wait(&acc_empty[abuf], aphase[abuf] ^ 1u, abort_flag)) {
                             ok = false;
                             break;
@@ -341,34 +393,36 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t tsum = tmem_base + lane_off + (third < 2 ? 192u + 32u * third : 448u);
         uint32_t abuf = 0;
         uint32_t aphase[2] = {0u, 0u};
-        const double rb = pow2_normal(-p.beta);
         const double qnan = __longlong_as_double(0x7ff8000000000000ll);
         long long* Q = p.qscratch + (static_cast<size_t>(blockIdx.x) * BN + third * CW) * BM + rloc;
         double* R = p.scratch + (static_cast<size_t>(blockIdx.x) * BN + third * CW) * BM + rloc;
         bool ok = true;
         for (int it = 0; ok; ++it) {
-            int tm, tn;
-            if (!member_tile(p.member, p.group, blockIdx.x, gridDim.x, it, p.tiles_m, p.tiles_n, &tm,
-                             &tn))
-                break;
+            int tm, tn, prob;
+            if (!tile_of(p, it, &prob, &tm, &tn)) break;
+            const TileInts pr = tile_ints(p, prob);
+            const double rb = pow2_normal(-pr.beta);
             int gj = 0;           // position of the current diagonal inside its int64 group
             bool rfirst = true;   // no FP64 partial R yet for this tile
             // stage the column exponents (minus 2 beta) and flags of this tile in shared memory
             named_bar_sync(1, 32 * EPI_WARPS);  // the previous tile's columns are no longer read
             for (int c = threadIdx.x - 32 * CTRL_WARPS; c < BN; c += 32 * EPI_WARPS) {
                 const int col = tn * BN + c;
-                colexp[c] = col < p.n ? p.f[col] - 2 * p.beta : 0;
-                colflag[c] = col < p.n ? p.ff[col] : 0;
+                const int n_ = prob < 0 ? p.one.n : p.table[prob].n;
+                const int32_t* f_ = prob < 0 ? p.one.f : p.table[prob].f;
+                const uint8_t* ff_ = prob < 0 ? p.one.ff : p.table[prob].ff;
+                colexp[c] = col < n_ ? f_[col] - 2 * pr.beta : 0;
+                colflag[c] = col < n_ ? ff_[col] : 0;
             }
             named_bar_sync(1, 32 * EPI_WARPS);
-            for (int d = p.S + 1; d >= 2 && ok; --d) {
+            for (int d = pr.S + 1; d >= 2 && ok; --d) {
                 int32_t acc[CR];
 #pragma unroll
                 for (int c = 0; c < CR; ++c) acc[c] = 0;
-                const int units = (d - 1) * p.nslab;
+                const int units = (d - 1) * pr.nslab;
                 bool first = true;
                 for (int u = 0; u < units;) {
-                    const int cnt = min(p.chunk_slabs, units - u);
+                    const int cnt = min(pr.chunk_slabs, units - u);
                     if (!mbar_wait(&acc_full[abuf], aphase[abuf], abort_flag)) {
                         ok = false;
                         break;
@@ -418,8 +472,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 // The last group ends at d = 2 and goes straight to C:
                 //     C := alpha 2^(e_i + f_j - 2 beta) R + beta_c C.
                 const bool gfirst = (gj == 0);
-                const bool gend = (p.group_end >> d) & 1u;
-                const RecombineCtx rc{Q, R, tsum, p.beta * gj, pow2_normal(-p.beta * gj), rb, gfirst, rfirst};
+                const bool gend = (pr.group_end >> d) & 1u;
+                const RecombineCtx rc{Q, R, tsum, pr.beta * gj, pow2_normal(-pr.beta * gj), rb, gfirst, rfirst};
                 if (!gend) {
                     recombine<kMid, CR, CT>(rc, acc, nullptr);
                 } else if (d != 2) {
@@ -427,16 +481,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                 } else {
                     const int row = tm * BM + rloc;
                     FinalCtx fc;
-                    fc.row_ok = row < p.m;
-                    fc.ei = fc.row_ok ? p.e[row] : 0;
-                    fc.eflag = fc.row_ok ? (p.ef[row] != 0) : false;
+                    const Prob& one = p.one;
+                    const EmuBatchProblem* bp = prob < 0 ? nullptr : &p.table[prob];
+                    const int m_ = bp ? bp->m : one.m;
+                    const int n_ = bp ? bp->n : one.n;
+                    fc.row_ok = row < m_;
+                    fc.ei = fc.row_ok ? (bp ? bp->e : one.e)[row] : 0;
+                    fc.eflag = fc.row_ok ? ((bp ? bp->ef : one.ef)[row] != 0) : false;
                     fc.colexp = colexp + third * CW;
                     fc.colflag = colflag + third * CW;
-                    fc.ncols = min(CW, p.n - (tn * BN + third * CW));
-                    fc.cp = p.C + row + static_cast<int64_t>(tn * BN + third * CW) * p.ldc;
-                    fc.ldc = p.ldc;
-                    fc.alpha = p.alpha;
-                    fc.beta_c = p.beta_c;
+                    fc.ncols = min(CW, n_ - (tn * BN + third * CW));
+                    fc.ldc = bp ? bp->ldc : one.ldc;
+                    fc.cp = (bp ? bp->C : one.C) + row + static_cast<int64_t>(tn * BN + third * CW) * fc.ldc;
+                    fc.alpha = bp ? bp->alpha : one.alpha;
+                    fc.beta_c = bp ? bp->beta_c : one.beta_c;
                     fc.qnan = qnan;
                     recombine<kLast, CR, CT>(rc, acc, &fc);
                 }
@@ -476,9 +534,11 @@ static EncodeFn get_encode() {
     return fn;
 }
 
+}  // namespace emu
+
 // 3-D fp16 digit tensor [S][rows][k_pad] (k contiguous), box 64 x box_rows x 1, 128-B swizzle.
-static bool make_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t rows, int S,
-                     int box_rows) {
+bool emu_make_digit_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t rows, int S, int box_rows) {
+    using namespace emu;
     EncodeFn enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(k_pad), static_cast<cuuint64_t>(rows),
@@ -493,6 +553,8 @@ static bool make_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t 
     return r == CUDA_SUCCESS;
 }
 
+namespace emu {
+
 template <int BN>
 static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t stream) {
     using C_ = Cfg<BN>;
@@ -506,8 +568,8 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     // int64 group sums Q in the first half, FP64 partial sums R (several groups only) in the second
 
     CUtensorMap mapA, mapB;
-    if (!make_map(&mapA, a.Ad, a.k_pad, a.m_pad, a.S, BM)) return cudaErrorInvalidValue;
-    if (!make_map(&mapB, a.Bd, a.k_pad, a.n_pad, a.S, BN)) return cudaErrorInvalidValue;
+    if (!emu_make_digit_map(&mapA, a.Ad, a.k_pad, a.m_pad, a.S, BM)) return cudaErrorInvalidValue;
+    if (!emu_make_digit_map(&mapB, a.Bd, a.k_pad, a.n_pad, a.S, BN)) return cudaErrorInvalidValue;
 
     static bool attr_set = false;
     if (!attr_set) {
@@ -521,29 +583,30 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     if (kslabs <= 0 || pass_slabs <= 0) return cudaErrorInvalidValue;
     int npass = 0;
     for (int64_t s0 = 0; s0 < kslabs; s0 += pass_slabs) {
-        Params p;
-        p.m = static_cast<int>(a.m);
-        p.n = static_cast<int>(a.n);
-        p.S = a.S;
-        p.beta = a.beta;
-        p.chunk_slabs = emu_chunk_slabs(a.beta);
-        p.slab0 = static_cast<int>(s0);
-        p.nslab = static_cast<int>(kslabs - s0 < pass_slabs ? kslabs - s0 : pass_slabs);
+        Params p{};
+        p.one.m = static_cast<int>(a.m);
+        p.one.n = static_cast<int>(a.n);
+        p.one.S = a.S;
+        p.one.beta = a.beta;
+        p.one.chunk_slabs = emu_chunk_slabs(a.beta);
+        p.one.slab0 = static_cast<int>(s0);
+        p.one.nslab = static_cast<int>(kslabs - s0 < pass_slabs ? kslabs - s0 : pass_slabs);
+        p.one.group_end = emu_group_ends(a.S, a.beta, p.one.nslab * static_cast<int64_t>(BK));
+        p.one.e = a.e;
+        p.one.ef = a.ef;
+        p.one.f = a.f;
+        p.one.ff = a.ff;
+        p.one.alpha = a.alpha;
+        p.one.beta_c = npass == 0 ? a.beta_c : 1.0;
+        p.one.C = a.C;
+        p.one.ldc = a.ldc;
         p.tiles_m = static_cast<int>(tiles_m);
         p.tiles_n = static_cast<int>(tiles_n);
         p.member = a.member == kMemberAuto ? kMemberC2 : a.member;
         p.group = a.group > 0 ? a.group : 8;
-        p.e = a.e;
-        p.ef = a.ef;
-        p.f = a.f;
-        p.ff = a.ff;
-        p.alpha = a.alpha;
-        p.beta_c = npass == 0 ? a.beta_c : 1.0;
-        p.C = a.C;
-        p.ldc = a.ldc;
+        p.table = nullptr;
         p.qscratch = static_cast<long long*>(a.scratch);
         p.scratch = reinterpret_cast<double*>(static_cast<char*>(a.scratch) + half);
-        p.group_end = emu_group_ends(a.S, a.beta, p.nslab * static_cast<int64_t>(BK));
         p.status = a.status;
         slice_gemm_kernel<BN><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(mapA, mapB, p);
         cudaError_t e = cudaGetLastError();
@@ -554,7 +617,41 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     return cudaSuccess;
 }
 
+template <int BN>
+static cudaError_t launch_bn_batched(const EmuBatchProblem* table, int count, int64_t total_tiles, void* scratch,
+                                     size_t scratch_bytes, int32_t* status, cudaStream_t stream) {
+    using C_ = Cfg<BN>;
+    int64_t ctas = device_sm_count();
+    if (ctas > total_tiles) ctas = total_tiles;
+    const size_t half = static_cast<size_t>(ctas) * BN * BM * sizeof(double);
+    if (scratch_bytes < 2 * half) return cudaErrorInvalidValue;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(C_::SMEM_BYTES));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    Params p{};
+    p.table = table;
+    p.count = count;
+    p.total_tiles = total_tiles;
+    p.qscratch = static_cast<long long*>(scratch);
+    p.scratch = reinterpret_cast<double*>(static_cast<char*>(scratch) + half);
+    p.status = status;
+    CUtensorMap unused{};  // the batch reads each problem's maps from the table
+    slice_gemm_kernel<BN><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(unused, unused, p);
+    return cudaGetLastError();
+}
+
 }  // namespace emu
+
+cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_tiles,
+                                          void* scratch, size_t scratch_bytes, int32_t* status,
+                                          cudaStream_t stream) {
+    if (count <= 0 || total_tiles <= 0) return cudaSuccess;
+    return emu::launch_bn_batched<192>(dev_table, count, total_tiles, scratch, scratch_bytes, status, stream);
+}
 
 int device_sm_count() {
     static int sms = 0;

@@ -264,7 +264,149 @@ inline bool rows_contiguous(int which, int op) {
     return (which == 0) ? (op == 0) : (op != 0);
 }
 
+// ---------------------------------------------------------------- batched passes
+// Per-row statistics (exponent, flag, L1 norm) and the row's spread, folded into *spread.
+__device__ __forceinline__ void finish_vector(int emax, int nf, float l1, int64_t inner, int32_t* e, uint8_t* ef,
+                                              int32_t* spread, bool valid) {
+    int v = 0;
+    if (valid) {
+        *e = (nf || emax == kNoExp) ? 0 : emax;
+        *ef = static_cast<uint8_t>(nf != 0);
+        if (!nf && emax != kNoExp && l1 > 0.f) {
+            const float sp = static_cast<float>(emax) - (log2f(l1) - log2f(static_cast<float>(inner)));
+            v = sp > 0.f ? static_cast<int>(ceilf(16.f * sp)) : 0;
+        }
+    }
+    v = __reduce_max_sync(0xFFFFFFFFu, v);
+    if (spread && (threadIdx.x & 31) == 0 && v > 0) atomicMax(spread, v);
+}
+
+// A (rows contiguous): a thread per row over all of k.
+__global__ void batch_scale_a(const EmuBatchPrep* __restrict__ probs, const int2* __restrict__ items) {
+    const int2 it = items[blockIdx.x];
+    const EmuBatchPrep& pr = probs[it.x];
+    const int64_t r = static_cast<int64_t>(it.y) * 256 + threadIdx.x;
+    const bool valid = r < pr.m;
+    int emax = kNoExp, nf = 0;
+    float sum = 0.f;
+    if (valid) {
+        const double* x = pr.A + r;
+        int64_t q = 0;
+        for (; q + 4 <= pr.k; q += 4) {
+            double v[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) v[t] = x[(q + t) * pr.lda];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int e = elem_exponent(v[t], &nf);
+                emax = e > emax ? e : emax;
+                if (e != kNoExp) sum += static_cast<float>(fabs(v[t]));
+            }
+        }
+        for (; q < pr.k; ++q) {
+            const double v = x[q * pr.lda];
+            const int e = elem_exponent(v, &nf);
+            emax = e > emax ? e : emax;
+            if (e != kNoExp) sum += static_cast<float>(fabs(v));
+        }
+    }
+    finish_vector(emax, nf, sum, pr.k, valid ? pr.e + r : nullptr, valid ? pr.ef + r : nullptr,
+                  pr.spread ? pr.spread : nullptr, valid);
+}
+
+// B (columns contiguous): a warp per column.
+__global__ void batch_scale_b(const EmuBatchPrep* __restrict__ probs, const int2* __restrict__ items) {
+    const int2 it = items[blockIdx.x];
+    const EmuBatchPrep& pr = probs[it.x];
+    const int64_t j = static_cast<int64_t>(it.y) * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const bool valid = j < pr.n;
+    int emax = kNoExp, nf = 0;
+    float sum = 0.f;
+    if (valid) {
+        const double* x = pr.B + j * pr.ldb;
+        for (int64_t q = lane; q < pr.k; q += 32) {
+            const int e = elem_exponent(x[q], &nf);
+            emax = e > emax ? e : emax;
+            if (e != kNoExp) sum += static_cast<float>(fabs(x[q]));
+        }
+    }
+    emax = __reduce_max_sync(0xFFFFFFFFu, emax);
+    nf = __reduce_or_sync(0xFFFFFFFFu, nf);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    // one lane per column writes; the spread is reduced over the warp (one column) by finish_vector
+    const bool writer = valid && lane == 0;
+    finish_vector(emax, nf, sum, pr.k, writer ? pr.f + j : nullptr, writer ? pr.ff + j : nullptr,
+                  pr.spread ? pr.spread + 1 : nullptr, writer);
+}
+
+// A: 64 (rows) x 64 (k) tile through shared memory, as split_rows_contig.
+__global__ void batch_split_a(const EmuBatchPrep* __restrict__ probs, const int2* __restrict__ items) {
+    __shared__ double tile[TT][TT + 1];  // [q][r]
+    const int2 it = items[blockIdx.x];
+    const EmuBatchPrep& pr = probs[it.x];
+    const int64_t qtiles = pr.k_pad / TT;
+    const int64_t r0 = (it.y / qtiles) * TT;
+    const int64_t q0 = (it.y % qtiles) * TT;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < TT * TT; i += 256) {
+        const int rr = i % TT, qq = i / TT;
+        const int64_t r = r0 + rr, q = q0 + qq;
+        tile[qq][rr] = (r < pr.m && q < pr.k) ? pr.A[r + q * pr.lda] : 0.0;
+    }
+    __syncthreads();
+    const int64_t plane = static_cast<int64_t>(pr.m) * pr.k_pad;
+    const int qg = (tid & 15) * 4;
+    __half* dg = static_cast<__half*>(pr.Ad);
+    for (int rr = tid >> 4; rr < TT; rr += 16) {
+        const int64_t r = r0 + rr, q = q0 + qg;
+        if (r >= pr.m) continue;
+        const bool valid = !pr.ef[r];
+        double x[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr];
+        write_digits4(x, valid, valid ? pr.e[r] : 0, pr.S, pr.beta, dg, plane, r * pr.k_pad + q);
+    }
+}
+
+// B: a thread per four consecutive k of one column, as split_inner_contig.
+__global__ void batch_split_b(const EmuBatchPrep* __restrict__ probs, const int2* __restrict__ items) {
+    const int2 it = items[blockIdx.x];
+    const EmuBatchPrep& pr = probs[it.x];
+    const int64_t quads = pr.k_pad / 4;
+    const int64_t idx = static_cast<int64_t>(it.y) * 256 + threadIdx.x;
+    if (idx >= static_cast<int64_t>(pr.n) * quads) return;
+    const int64_t j = idx / quads;
+    const int64_t q = (idx - j * quads) * 4;
+    const bool valid = !pr.ff[j];
+    double x[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) x[t] = (valid && q + t < pr.k) ? pr.B[q + t + j * pr.ldb] : 0.0;
+    const int64_t plane = static_cast<int64_t>(pr.n) * pr.k_pad;
+    write_digits4(x, valid, valid ? pr.f[j] : 0, pr.S, pr.beta, static_cast<__half*>(pr.Bd), plane,
+                  j * pr.k_pad + q);
+}
+
 }  // namespace split
+
+cudaError_t launch_emu_batch_scale(const EmuBatchPrep* probs, const int2* items_a, int n_a, const int2* items_b,
+                                   int n_b, cudaStream_t stream) {
+    if (n_a > 0) split::batch_scale_a<<<static_cast<unsigned>(n_a), 256, 0, stream>>>(probs, items_a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (n_b > 0) split::batch_scale_b<<<static_cast<unsigned>(n_b), 256, 0, stream>>>(probs, items_b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emu_batch_split(const EmuBatchPrep* probs, const int2* items_a, int n_a, const int2* items_b,
+                                   int n_b, cudaStream_t stream) {
+    if (n_a > 0) split::batch_split_a<<<static_cast<unsigned>(n_a), 256, 0, stream>>>(probs, items_a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (n_b > 0) split::batch_split_b<<<static_cast<unsigned>(n_b), 256, 0, stream>>>(probs, items_b);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_emu_scale(int which, int op, int64_t rows, int64_t inner, const double* X,
                              int64_t ldx, int32_t* exps, uint8_t* flags, float* l1,

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace momms {
@@ -36,6 +37,8 @@ cudaError_t launch_native_batched(const BatchProblem* dev_problems, int count, i
 cudaError_t launch_emu_scale(int which, int op, int64_t rows, int64_t inner, const double* X,
                              int64_t ldx, int32_t* exps, uint8_t* flags, float* l1,
                              cudaStream_t stream);
+// Kernels one launch_emu_scale call enqueues (the row-contiguous case adds a finalize kernel).
+inline int emu_scale_kernel_count(int which, int op) { return ((which == 0) == (op == 0)) ? 2 : 1; }
 // atomicMax into *out of ceil(16 * max_r log2(2^e_r * inner / l1_r)).
 cudaError_t launch_emu_spread(int64_t rows, int64_t inner, const int32_t* exps, const uint8_t* flags,
                               const float* l1, int* out, cudaStream_t stream);
@@ -66,6 +69,55 @@ struct EmuGemmArgs {
     int tile_n;    // CTA tile width request (only 192 is built; 0 = automatic)
 };
 constexpr int kEmuBM = 128, kEmuBK = 64, kEmuBNMax = 192;
+
+// One problem of a batched emulated call (device table entry; the tensor maps describe
+// the problem's digit slices and keep the alignment CUtensorMap demands).
+struct EmuBatchProblem {
+    CUtensorMap mapA;
+    CUtensorMap mapB;
+    const int32_t* e;
+    const uint8_t* ef;
+    const int32_t* f;
+    const uint8_t* ff;
+    double* C;
+    int64_t ldc;
+    double alpha, beta_c;
+    int64_t tile0;     // first tile of this problem in the concatenated tile list
+    int32_t m, n, S, beta, nslab, chunk_slabs, tiles_n;
+    uint32_t group_end;
+};
+// Per-problem inputs and outputs of the batched scale and split passes (op = N, N).
+struct EmuBatchPrep {
+    const double* A;
+    const double* B;
+    int64_t lda, ldb;
+    int32_t m, n, k, k_pad, S, beta;
+    int32_t* e;
+    uint8_t* ef;
+    int32_t* f;
+    uint8_t* ff;
+    void* Ad;          // S slices [S][m][k_pad] fp16 (unused by the scale passes)
+    void* Bd;          // S slices [S][n][k_pad] fp16
+    int32_t* spread;   // 2 values (A, B): ceil(16 x spread) by atomicMax, or null
+};
+// Work items are (problem, block) pairs; the block's meaning depends on the pass:
+//   scale A: 256 rows   scale B: 8 columns   split A: a 64 x 64 (row, k) tile   split B: 1024 digits.
+cudaError_t launch_emu_batch_scale(const EmuBatchPrep* probs, const int2* items_a, int n_a, const int2* items_b,
+                                   int n_b, cudaStream_t stream);
+cudaError_t launch_emu_batch_split(const EmuBatchPrep* probs, const int2* items_a, int n_a, const int2* items_b,
+                                   int n_b, cudaStream_t stream);
+// Work-list sizes of one problem.
+inline int64_t emu_batch_scale_a_blocks(int64_t m) { return (m + 255) / 256; }
+inline int64_t emu_batch_scale_b_blocks(int64_t n) { return (n + 7) / 8; }
+inline int64_t emu_batch_split_a_blocks(int64_t m, int64_t k_pad) { return ((m + 63) / 64) * (k_pad / 64); }
+inline int64_t emu_batch_split_b_blocks(int64_t n, int64_t k_pad) { return (n * (k_pad / 4) + 255) / 256; }
+
+// Tensor map of S digit slices [S][rows][k_pad] (fp16, k contiguous); box 64 x box_rows.
+bool emu_make_digit_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t rows, int S, int box_rows);
+// One persistent launch of the slice-product kernel over the tiles of all problems.
+cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_tiles,
+                                          void* scratch, size_t scratch_bytes, int32_t* status,
+                                          cudaStream_t stream);
 // The CTA tile width used for n columns (tile_n request 0 = automatic).
 int emu_pick_bn(int64_t n, int requested);
 // Launches the slice-product kernel once per k pass; *passes receives the count.

@@ -121,3 +121,58 @@ def test_batched_2000_uneven_problems_native_one_launch():
         Cref = oracle.dgemm(A, B, C.copy(order="F"), 1.0, 1.0)
         worst = max(worst, max_ratio(d[2].to_numpy(), Cref, k, 1.0, 1.0, oracle.dgemm_abs(A, B), C))
     assert worst <= 1.0
+
+
+def test_batched_emulated_one_slice_launch_and_graph_replay():
+    # fixed slice count: 2 scale + 2 split + ONE slice-product launch, and a captured graph replays it
+    import torch
+    probs = make_problems(30, 48, 600, 7000)
+    h = M.Handle(mode=M.MODE_EMULATED, slices=9)
+    dev, args = run_batched(h, probs, 1.0, 0.0)
+    torch.cuda.synchronize()
+    assert h.report()["launches"] == 5
+    assert h.device_status() == M.MOMMS_OK
+    assert check_all(probs, dev, 1.0, 0.0) <= 1.0
+    eager = [d[2].to_numpy() for d in dev]
+    for d in dev:
+        d[2].storage.fill_(float("nan"))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        M.check(M.momms_gemm_batched(h, stream=s, **args), "capture")
+    g.replay()
+    torch.cuda.synchronize()
+    for d, e in zip(dev, eager):
+        assert np.array_equal(d[2].to_numpy(), e)
+
+
+def test_batched_2000_uneven_problems_emulated():
+    # the batched workload in emulated mode (data-driven slice count per problem)
+    import torch
+    count = 2000
+    sizes = syn.log_uniform_sizes(syn.workload_seed(4, "A"), count, 32, 2048)
+    h = M.Handle(mode=M.MODE_EMULATED)
+    dev, hosts = [], []
+    for i, (m, n, k) in enumerate(sizes):
+        m, n, k = int(m), int(n), int(k)
+        A = syn.matrix("uniform", m, k, 100000 + 3 * i)
+        B = syn.matrix("uniform", k, n, 100001 + 3 * i)
+        C = syn.matrix("uniform", m, n, 100002 + 3 * i)
+        dev.append((M.DeviceMatrix.from_numpy(A), M.DeviceMatrix.from_numpy(B), M.DeviceMatrix.from_numpy(C)))
+        hosts.append((m, n, k, A, B, C) if i % 20 == 0 else None)
+    args = dict(m=[int(s[0]) for s in sizes], n=[int(s[1]) for s in sizes], k=[int(s[2]) for s in sizes],
+                alpha=[1.0] * count, A=[d[0].ptr for d in dev], lda=[d[0].ld for d in dev],
+                B=[d[1].ptr for d in dev], ldb=[d[1].ld for d in dev], beta=[1.0] * count,
+                C=[d[2].ptr for d in dev], ldc=[d[2].ld for d in dev])
+    M.check(M.momms_gemm_batched(h, **args), "batched 2000 emulated")
+    torch.cuda.synchronize()
+    assert h.device_status() == M.MOMMS_OK
+    assert h.report()["launches"] == 5
+    worst = 0.0
+    for hst, d in zip(hosts, dev):
+        if hst is None:
+            continue
+        m, n, k, A, B, C = hst
+        Cref = oracle.dgemm(A, B, C.copy(order="F"), 1.0, 1.0)
+        worst = max(worst, max_ratio(d[2].to_numpy(), Cref, k, 1.0, 1.0, oracle.dgemm_abs(A, B), C))
+    assert worst <= 1.0
