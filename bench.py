@@ -40,7 +40,7 @@ METRIC = "FP64-accurate GEMM TFLOP/s (2mnk/t) & % roofline, native vs emulated"
 # The 8192^3 launch is too large to capture with --set full, so its traffic is this figure scaled
 # by the tensor flops (the per-pair panel re-reads grow in proportion).  Set to None whenever the
 # slice-product kernel changes until it is captured again.
-NCU_SLICE_CAPTURE = {"dram_bytes": 4.683078e9 + 0.768095e9, "tensor_flops": 21 * 2.0 * 4096 ** 3}
+NCU_SLICE_CAPTURE = {"dram_bytes": 4.705411e9 + 0.775041e9, "tensor_flops": 21 * 2.0 * 4096 ** 3}
 UNIT = "TFLOP/s"
 
 
@@ -50,6 +50,11 @@ def parse():
     p.add_argument("--steps", type=int, default=60)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--size", type=int, default=8192)
+    p.add_argument("--shape", default="square", choices=["square", "rankk", "panel"],
+                   help="square: m=n=k=size; rankk: m=n=2*size, k=256; panel: m=k=2*size, n=256")
+    p.add_argument("--mode", default="auto", choices=["auto", "native", "emulated"])
+    p.add_argument("--member", default="auto", choices=["auto", "C2", "A2", "B2", "A1"])
+    p.add_argument("--slices", type=int, default=0, help="emulated slice count (0 = from the data)")
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--native-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -57,8 +62,19 @@ def parse():
     return p.parse_args()
 
 
-def workload_name(n):
-    return (f"square FP64 GEMM C := A*B + C, m=n=k={n}, column-major (ld = rows), "
+def shape_of(args):
+    n = args.size
+    if args.shape == "rankk":
+        return 2 * n, 2 * n, 256
+    if args.shape == "panel":
+        return 2 * n, 256, 2 * n
+    return n, n, n
+
+
+def workload_name(args):
+    m, n, k = shape_of(args)
+    kind = {"square": "square", "rankk": "rank-k", "panel": "panel-panel"}[args.shape]
+    return (f"{kind} FP64 GEMM C := A*B + C, m={m} n={n} k={k}, column-major (ld = rows), "
             f"A, B, C uniform[-1,1] (seeded SplitMix64)")
 
 
@@ -233,7 +249,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(n)},
+        "config": {"workload": workload_name(args)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample.cores, "kind": "oracle",
                          "sample": desc + f"; median of {len(vals)} samples"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -255,23 +271,26 @@ def main():
     from paper_1904_05717_gb300 import synthetic as syn
 
     M.lib(build_if_missing=True)
-    n = args.size
-    flops = 2.0 * n ** 3
+    m, n, k = shape_of(args)
+    flops = 2.0 * m * n * k
     stream = torch.cuda.current_stream()
+    mode = {"auto": M.MODE_AUTO, "native": M.MODE_NATIVE, "emulated": M.MODE_EMULATED}[args.mode]
+    member = {"auto": M.MEMBER_AUTO, "C2": M.MEMBER_C2, "A2": M.MEMBER_A2, "B2": M.MEMBER_B2,
+              "A1": M.MEMBER_A1}[args.member]
 
     # inputs generated on the host (seeded), copied once: device-resident for `value`
-    A_h = syn.matrix("uniform", n, n, syn.workload_seed(1, "A"))
-    B_h = syn.matrix("uniform", n, n, syn.workload_seed(1, "B"))
-    C_h = syn.matrix("uniform", n, n, syn.workload_seed(1, "C"))
+    A_h = syn.matrix("uniform", m, k, syn.workload_seed(1, "A"))
+    B_h = syn.matrix("uniform", k, n, syn.workload_seed(1, "B"))
+    C_h = syn.matrix("uniform", m, n, syn.workload_seed(1, "C"))
     dA = M.DeviceMatrix.from_numpy(A_h)
     dB = M.DeviceMatrix.from_numpy(B_h)
     dC = M.DeviceMatrix.from_numpy(C_h)
     dC0 = dC.storage.clone()
 
-    h = M.Handle(mode=M.MODE_AUTO)
+    h = M.Handle(mode=mode, member=member, slices=args.slices)
 
     def step():
-        M.check(M.momms_gemm_ex(h, 0, 0, n, n, n, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream),
+        M.check(M.momms_gemm_ex(h, 0, 0, m, n, k, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream),
                 "momms_gemm_ex")
 
     for _ in range(args.warmup):
@@ -298,68 +317,70 @@ def main():
     # ---- dominant kernel alone (same digits, same launch configuration), per-launch CUDA events
     S, bb = int(rep["slices"]), int(rep["digit_bits"])
     roof = None
-    slice_ms = None
     if rep["mode"] == M.MODE_EMULATED:
-        m_pad = -(-n // 128) * 128
-        n_pad = -(-n // 256) * 256
-        k_pad = -(-n // 64) * 64
-        e = torch.empty(n, dtype=torch.int32, device="cuda"); ef = torch.empty(n, dtype=torch.uint8, device="cuda")
+        k_pad = -(-k // 64) * 64
+        e = torch.empty(m, dtype=torch.int32, device="cuda"); ef = torch.empty(m, dtype=torch.uint8, device="cuda")
         f = torch.empty(n, dtype=torch.int32, device="cuda"); ff = torch.empty(n, dtype=torch.uint8, device="cuda")
-        M.check(M.momms_emu_scale(0, 0, n, n, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), stream), "scale")
-        M.check(M.momms_emu_scale(1, 0, n, n, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), stream), "scale")
-        Ad = torch.empty((S, m_pad, k_pad), dtype=torch.float16, device="cuda")
-        Bd = torch.empty((S, n_pad, k_pad), dtype=torch.float16, device="cuda")
-        M.check(M.momms_emu_split(0, 0, n, n, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), S, bb, Ad.data_ptr(), m_pad, k_pad, stream), "split")
-        M.check(M.momms_emu_split(1, 0, n, n, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), S, bb, Bd.data_ptr(), n_pad, k_pad, stream), "split")
+        M.check(M.momms_emu_scale(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), stream), "scale")
+        M.check(M.momms_emu_scale(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), stream), "scale")
+        Ad = torch.empty((S, m, k_pad), dtype=torch.float16, device="cuda")
+        Bd = torch.empty((S, n, k_pad), dtype=torch.float16, device="cuda")
+        M.check(M.momms_emu_split(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), S, bb, Ad.data_ptr(), m, k_pad, stream), "split")
+        M.check(M.momms_emu_split(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), S, bb, Bd.data_ptr(), n, k_pad, stream), "split")
         nbytes = M.momms_emu_scratch_bytes()
         scratch = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
-        Cs = M.DeviceMatrix(n, n)
+        Cs = M.DeviceMatrix(m, n)
         evs = []
         reps = max(3, min(args.steps, 10))
         for i in range(reps + 1):
             a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-            M.check(M.momms_emu_slice_gemm(n, n, n, S, bb, Ad.data_ptr(), Bd.data_ptr(), m_pad, n_pad, k_pad,
+            M.check(M.momms_emu_slice_gemm(m, n, k, S, bb, Ad.data_ptr(), Bd.data_ptr(), m, n, k_pad,
                                            e.data_ptr(), ef.data_ptr(), f.data_ptr(), ff.data_ptr(), 1.0, 0.0,
-                                           Cs.ptr, Cs.ld, M.MEMBER_AUTO, scratch.data_ptr(), nbytes, st.data_ptr(),
-                                           stream), "slice gemm")
+                                           Cs.ptr, Cs.ld, int(rep["member"]), scratch.data_ptr(), nbytes,
+                                           st.data_ptr(), stream), "slice gemm")
             a1.record(stream)
             if i > 0:  # first launch is a warm-up
                 evs.append((a0, a1))
         torch.cuda.synchronize()
         slice_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
         pairs = S * (S + 1) // 2
-        tensor_flops = pairs * 2.0 * n * n * n  # algorithmic: every digit-pair product of the n^3 problem
+        tensor_flops = pairs * 2.0 * m * n * k  # algorithmic: every digit-pair product of the problem
         achieved = tensor_flops / (slice_ms * 1e-3) / 1e12
         peaks, src = measured_peaks()
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         traffic = None
-        if NCU_SLICE_CAPTURE is not None:
+        if NCU_SLICE_CAPTURE is not None and args.shape == "square" and args.member in ("auto", "C2"):
             traffic = NCU_SLICE_CAPTURE["dram_bytes"] * tensor_flops / NCU_SLICE_CAPTURE["tensor_flops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_source": "ncu 4096^3 capture scaled by tensor flops (profiles/slice_gemm_4096.md)",
-                "kernel": "momms::emu::slice_gemm_kernel (tcgen05 kind::f16)",
+                "kernel": "momms::emu::slice_gemm_kernel<192> (tcgen05 kind::f16)",
                 "peak_source": f"{src} bf16_tflops_sustained (fp16 rate = bf16 rate)",
                 "algorithmic_flops_per_launch": tensor_flops, "launch_ms": slice_ms}
         del Ad, Bd, scratch
 
     # ---- native FP64 DMMA path on the same inputs (the other half of the metric)
-    hn = M.Handle(mode=M.MODE_NATIVE)
-    dC.storage.copy_(dC0)
-    M.check(M.momms_gemm_ex(hn, 0, 0, n, n, n, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream), "native")
-    torch.cuda.synchronize()
-    n0 = torch.cuda.Event(enable_timing=True); n1 = torch.cuda.Event(enable_timing=True)
-    n0.record(stream)
-    for _ in range(args.native_steps):
-        M.check(M.momms_gemm_ex(hn, 0, 0, n, n, n, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream), "native")
-    n1.record(stream)
-    torch.cuda.synchronize()
-    native_ms = n0.elapsed_time(n1) / args.native_steps
-    native_tflops = flops / (native_ms * 1e-3) / 1e12
-    dmma_peak = M.momms_probe_peak(0, stream)
-    hn.close()
+    native = None
+    if args.native_steps > 0:
+        hn = M.Handle(mode=M.MODE_NATIVE, member=member)
+        dC.storage.copy_(dC0)
+        M.check(M.momms_gemm_ex(hn, 0, 0, m, n, k, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream), "native")
+        torch.cuda.synchronize()
+        n0 = torch.cuda.Event(enable_timing=True); n1 = torch.cuda.Event(enable_timing=True)
+        n0.record(stream)
+        for _ in range(args.native_steps):
+            M.check(M.momms_gemm_ex(hn, 0, 0, m, n, k, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream),
+                    "native")
+        n1.record(stream)
+        torch.cuda.synchronize()
+        native_ms = n0.elapsed_time(n1) / args.native_steps
+        native_tflops = flops / (native_ms * 1e-3) / 1e12
+        dmma_peak = M.momms_probe_peak(0, stream)
+        hn.close()
+        native = {"value": native_tflops, "unit": UNIT, "ms_per_gemm": native_ms, "dmma_peak_probe_tflops": dmma_peak,
+                  "frac_of_probe": native_tflops / dmma_peak if dmma_peak else None}
 
     # ---- end to end through the public API with host buffers (pinned), copies inside the timed region.
     # Every step copies its inputs A, B, C host->device and its result C device->host.  Two device
@@ -368,9 +389,9 @@ def main():
     B_p = torch.from_numpy(np.ascontiguousarray(B_h.T)).pin_memory()
     C_p = torch.from_numpy(np.ascontiguousarray(C_h.T)).pin_memory()
     C_out = torch.empty_like(C_p).pin_memory()
-    h2d = 3 * n * n * 8
-    d2h = n * n * 8
-    sets = [(dA, dB, dC), (M.DeviceMatrix(n, n), M.DeviceMatrix(n, n), M.DeviceMatrix(n, n))]
+    h2d = (m * k + k * n + m * n) * 8
+    d2h = m * n * 8
+    sets = [(dA, dB, dC), (M.DeviceMatrix(m, k), M.DeviceMatrix(k, n), M.DeviceMatrix(m, n))]
     copy_s = torch.cuda.Stream()
     comp_s = stream
     ev_in = [torch.cuda.Event(), torch.cuda.Event()]
@@ -393,7 +414,7 @@ def main():
                 h2d_into(i + 1)
             A_, B_, C_ = sets[i % 2]
             comp_s.wait_event(ev_in[i % 2])
-            M.check(M.momms_gemm_ex(h, 0, 0, n, n, n, 1.0, A_.ptr, A_.ld, B_.ptr, B_.ld, 1.0, C_.ptr, C_.ld,
+            M.check(M.momms_gemm_ex(h, 0, 0, m, n, k, 1.0, A_.ptr, A_.ld, B_.ptr, B_.ld, 1.0, C_.ptr, C_.ld,
                                     comp_s), "momms_gemm_ex")
             ev_done[i % 2].record(comp_s)
             with torch.cuda.stream(copy_s):
@@ -411,30 +432,28 @@ def main():
     e2e_value, e2e_ms = aggregate_throughput(flops, e2e_s * 1e3 / esteps, world)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.shape == "square":
         sample = OracleSample(n)
         v, desc = sample.measure(args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": sample.cores, "kind": "oracle", "sample": desc}
 
     if rank == 0:
-        peaks, src = measured_peaks()
+        emulated = rep["mode"] == M.MODE_EMULATED
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64",
             "dtype_detail": (f"FP64-accurate; emulated path: {S} slices of {bb}-bit integer digits in fp16 on "
-                             f"tcgen05 kind::f16, exact FP32 accumulation drained to int32, FP64 recombination"
-                             if rep["mode"] == M.MODE_EMULATED else "native FP64 DMMA"),
+                             f"tcgen05 kind::f16, exact FP32 accumulation drained to int32, int64/FP64 recombination"
+                             if emulated else "native FP64 DMMA"),
             "data": "synthetic",
-            "config": {"workload": workload_name(n), "path": "emulated" if rep["mode"] == M.MODE_EMULATED else "native",
-                       "slices": S, "digit_bits": bb, "member": M.MEMBER_NAMES.get(int(rep["member"]), "?"),
-                       "l2": "each operand (512 MB) exceeds L2 (126 MB): no flush between steps",
+            "config": {"workload": workload_name(args), "path": "emulated" if emulated else "native",
+                       "slices": S, "digit_bits": bb, "member": M.MEMBER_NAMES.get(int(rep["member"]), "auto"),
+                       "l2": "operands exceed L2 (126 MB) at the default size: no flush between steps",
                        "replicas": world},
             "roofline": roof,
-            "native": {"value": native_tflops, "unit": UNIT, "ms_per_gemm": native_ms,
-                       "dmma_peak_probe_tflops": dmma_peak,
-                       "frac_of_probe": native_tflops / dmma_peak if dmma_peak else None},
-            "emulated_vs_native": value / world / native_tflops if native_tflops else None,
+            "native": native,
+            "emulated_vs_native": (value / world / native["value"]) if (native and emulated) else None,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms, "steps": esteps,
                     "how": "host wall clock over all steps; pinned host buffers; copies of step i+1 overlap "

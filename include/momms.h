@@ -238,6 +238,14 @@ int momms_tune(momms_handle_t handle, const char* path, int64_t count, const int
  * ignored and reported as MOMMS_ERR_IO). */
 int momms_load_plans(momms_handle_t handle, const char* path);
 
+/* ------------------------------------------------------- schedule query */
+/* The member's tile order (host side, no GPU needed): the i-th tile taken by CTA `cta`
+ * of `ctas` persistent CTAs over a tiles_m x tiles_n tile grid (group = tile rows per
+ * group of the C2 raster; <= 0 means 8).  Returns 1 and writes (tm, tn), 0 when that CTA
+ * has no i-th tile, or a negative argument index.  The kernels use the same function. */
+int momms_member_tile(int member, int group, int64_t cta, int64_t ctas, int64_t i, int tiles_m,
+                      int tiles_n, int* tm, int* tn);
+
 /* ------------------------------------------------------- microbenchmarks */
 /* Peak probes used as roofline denominators: kind 0 = FP64 DMMA, 1 = FP64 DFMA,
  * 2 = fp16 tcgen05 (kind::f16, FP32 accumulate).  Writes the achieved rate in

@@ -60,6 +60,8 @@ struct momms_handle_s {
     int32_t* status = nullptr;  // device word
     int* spread_dev = nullptr;  // device pair of spread values (AUTO slice rule)
     int* spread_host = nullptr; // pinned
+    cudaEvent_t spread_ready = nullptr;
+    int last_auto_slices = 6;   // speculative slice count for the next AUTO call
     momms_report_t report{};
     BatchProblem* dev_probs = nullptr;
     size_t dev_probs_cap = 0;
@@ -258,25 +260,39 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
     launches += momms::emu_scale_kernel_count(0, opa) + momms::emu_scale_kernel_count(1, opb);
     double est = 0.0;
+    int split_done = 0;  // slices already written
     if (S == 0) {
-        // data-driven slice count: one small device reduction and a readback
+        // Data-driven slice count: the spreads are reduced on the device and read back.  While the
+        // readback is in flight the digits are already split for a guessed S (the last call's):
+        // a slice's digits do not depend on S, so only missing slices are added afterwards.
         if (cudaMemsetAsync(h->spread_dev, 0, 2 * sizeof(int), s) != cudaSuccess) return MOMMS_ERR_CUDA;
         if (momms::launch_emu_spread(m, k, e, ef, l1a, h->spread_dev, s) != cudaSuccess) return MOMMS_ERR_CUDA;
         if (momms::launch_emu_spread(n, k, f, ff, l1b, h->spread_dev + 1, s) != cudaSuccess) return MOMMS_ERR_CUDA;
         if (cudaMemcpyAsync(h->spread_host, h->spread_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return MOMMS_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return MOMMS_ERR_CUDA;
+        if (!h->spread_ready || cudaEventRecord(h->spread_ready, s) != cudaSuccess) return MOMMS_ERR_CUDA;
+        launches += 2;
+        const int guess = std::min(std::max(h->last_auto_slices, 1), S_alloc);
+        ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, guess, bb, Ad, L.m_pad, L.k_pad, s);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, guess, bb, Bd, L.n_pad, L.k_pad, s);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        launches += 2;
+        split_done = guess;
+        if (cudaEventSynchronize(h->spread_ready) != cudaSuccess) return MOMMS_ERR_CUDA;
         const double sa = h->spread_host[0] / 16.0, sb = h->spread_host[1] / 16.0;
         double bits = 0.0;
         S = slices_from_spread(sa, sb, k, bb, &bits);
         est = 0.1 * std::exp2(bits - static_cast<double>(bb) * S);  // the rule keeps a 10x margin
+        h->last_auto_slices = S;
+    }
+    if (S > split_done) {
+        ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, S, bb, Ad, L.m_pad, L.k_pad, s, split_done);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, S, bb, Bd, L.n_pad, L.k_pad, s, split_done);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
         launches += 2;
     }
-    ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, S, bb, Ad, L.m_pad, L.k_pad, s);
-    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-    ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, S, bb, Bd, L.n_pad, L.k_pad, s);
-    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-    launches += 2;
     momms::EmuGemmArgs a{};
     a.m = m; a.n = n; a.k = k; a.S = S; a.beta = bb;
     a.Ad = Ad; a.Bd = Bd; a.m_pad = L.m_pad; a.n_pad = L.n_pad; a.k_pad = L.k_pad;
@@ -558,6 +574,10 @@ int momms_create(momms_handle_t* handle) {
         return MOMMS_ERR_ALLOC;
     }
     h->spread_dev = reinterpret_cast<int*>(reinterpret_cast<char*>(h->status) + 16);
+    if (cudaEventCreateWithFlags(&h->spread_ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        h->spread_ready = nullptr;
+    }
     if (const char* v = std::getenv("MOMMS_TILE_N")) h->tile_n = std::atoi(v);
     if (cudaMemset(h->status, 0, 64) != cudaSuccess ||
         cudaMallocHost(&h->spread_host, 2 * sizeof(int)) != cudaSuccess) {
@@ -580,6 +600,7 @@ int momms_destroy(momms_handle_t h) {
     if (h->spread_host_big) cudaFreeHost(h->spread_host_big);
     if (h->status) cudaFree(h->status);
     if (h->spread_host) cudaFreeHost(h->spread_host);
+    if (h->spread_ready) cudaEventDestroy(h->spread_ready);
     h->magic = 0;
     delete h;
     return MOMMS_OK;
@@ -1051,6 +1072,19 @@ int momms_tune(momms_handle_t h, const char* path, int64_t count, const int64_t*
     cudaEventDestroy(e1);
     if (status == MOMMS_OK && path) status = save_plans(h, path);
     return status;
+}
+
+int momms_member_tile(int member, int group, int64_t cta, int64_t ctas, int64_t i, int tiles_m, int tiles_n,
+                      int* tm, int* tn) {
+    if (member < MOMMS_MEMBER_AUTO || member > MOMMS_MEMBER_A1) return -1;
+    if (ctas < 1 || cta < 0 || cta >= ctas) return -4;
+    if (i < 0) return -5;
+    if (tiles_m < 0) return -6;
+    if (tiles_n < 0) return -7;
+    if (!tm) return -8;
+    if (!tn) return -9;
+    const int mem = member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : member;
+    return momms::member_tile(mem, group > 0 ? group : 8, cta, ctas, i, tiles_m, tiles_n, tm, tn) ? 1 : 0;
 }
 
 int momms_probe_peak(int kind, double* tflops, momms_stream_t stream) {

@@ -140,21 +140,6 @@ __global__ void spread_kernel(int64_t rows, int64_t inner, const int32_t* __rest
     if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(out, v);
 }
 
-// Digit s (1-based) of x relative to exponent e.
-__device__ __forceinline__ __half digit_of(unsigned long long mag, bool neg, int e2, int e, int beta,
-                                           int s) {
-    const unsigned long long mask = (1ull << beta) - 1ull;
-    const int sh = e2 - e + beta * s;
-    unsigned int v;
-    if (sh >= 0) {
-        v = sh >= beta ? 0u : static_cast<unsigned int>((mag << sh) & mask);
-    } else {
-        v = (-sh >= 64) ? 0u : static_cast<unsigned int>((mag >> (-sh)) & mask);
-    }
-    const int iv = neg ? -static_cast<int>(v) : static_cast<int>(v);
-    return __int2half_rn(iv);
-}
-
 // Decompose x into (integer significand, binary exponent e2, sign); zero / non-finite -> mag 0.
 __device__ __forceinline__ void decompose(double x, unsigned long long* mag, int* e2, bool* neg) {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
@@ -173,6 +158,22 @@ __device__ __forceinline__ void decompose(double x, unsigned long long* mag, int
     *mag = m;
 }
 
+// Magnitude of digit s: bits [rs, rs + beta) of the significand m = hi:lo, rs = (e - e2) - beta*s
+// (negative rs: the digit's low bits lie below the significand and are zero).
+__device__ __forceinline__ uint32_t digit_bits(uint32_t lo, uint32_t hi, int rs, uint32_t mask) {
+    if (rs >= 32) return rs >= 64 ? 0u : (hi >> (rs - 32)) & mask;
+    if (rs >= 0) return __funnelshift_r(lo, hi, rs) & mask;
+    return rs > -32 ? (lo << (-rs)) & mask : 0u;
+}
+
+// Two digit magnitudes u0, u1 < 1024 with signs as an fp16 pair: 1024 + u is exact in fp16
+// (bits 0x6400 | u), subtracting 1024 leaves u exactly, the sign bit is set afterwards.
+__device__ __forceinline__ uint32_t digits_to_half2(uint32_t u0, uint32_t u1, uint32_t s0, uint32_t s1) {
+    const uint32_t biased = (0x6400u | u0) | ((0x6400u | u1) << 16);
+    const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&biased), __half2half2(__ushort_as_half(0x6400)));
+    return *reinterpret_cast<const uint32_t*>(&v) ^ (s0 | (s1 << 16));
+}
+
 // Four consecutive digits of one slice packed for one 8-byte store.
 __device__ __forceinline__ uint2 pack4(__half h0, __half h1, __half h2, __half h3) {
     uint2 v;
@@ -182,47 +183,79 @@ __device__ __forceinline__ uint2 pack4(__half h0, __half h1, __half h2, __half h
 }
 
 // Digits of four consecutive elements (same row) into the S slices at element offset `off`.
+// Per element: significand words, the exponent distance t = e - e2, and the fp16 sign bit.
+__device__ __forceinline__ void digit_source(double x, bool valid, int e, uint32_t* lo, uint32_t* hi, int* t,
+                                             uint32_t* sgn) {
+    unsigned long long mag = 0;
+    int e2 = 0;
+    bool neg = false;
+    if (valid) decompose(x, &mag, &e2, &neg);
+    *lo = static_cast<uint32_t>(mag);
+    *hi = static_cast<uint32_t>(mag >> 32);
+    *t = mag ? e - e2 : 1 << 20;  // zero: every digit shift runs past the significand
+    *sgn = neg ? 0x8000u : 0u;
+}
+
+// Writes the digits of slices s_first+1 .. S (1-based); the digit of slice s does not depend on S.
 __device__ __forceinline__ void write_digits4(const double (&x)[4], bool valid_row, int e, int S, int beta,
-                                              __half* __restrict__ digits, int64_t plane, int64_t off) {
-    unsigned long long mag[4];
-    int e2[4];
-    bool neg[4];
+                                              __half* __restrict__ digits, int64_t plane, int64_t off,
+                                              int s_first = 0) {
+    uint32_t lo[4], hi[4], sg[4];
+    int t[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        if (valid_row) {
-            decompose(x[t], &mag[t], &e2[t], &neg[t]);
-        } else {
-            mag[t] = 0;
-            e2[t] = 0;
-            neg[t] = false;
-        }
-    }
-    const __half z = __int2half_rn(0);
-    for (int s = 1; s <= S; ++s) {
-        __half h[4];
+    for (int i = 0; i < 4; ++i) digit_source(x[i], valid_row, e, &lo[i], &hi[i], &t[i], &sg[i]);
+    const uint32_t mask = (1u << beta) - 1u;
+    for (int s = s_first + 1; s <= S; ++s) {
+        uint32_t u[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) h[t] = mag[t] ? digit_of(mag[t], neg[t], e2[t], e, beta, s) : z;
-        *reinterpret_cast<uint2*>(digits + (s - 1) * plane + off) = pack4(h[0], h[1], h[2], h[3]);
+        for (int i = 0; i < 4; ++i) u[i] = digit_bits(lo[i], hi[i], t[i] - beta * s, mask);
+        uint2 v;
+        v.x = digits_to_half2(u[0], u[1], sg[0], sg[1]);
+        v.y = digits_to_half2(u[2], u[3], sg[2], sg[3]);
+        *reinterpret_cast<uint2*>(digits + (s - 1) * plane + off) = v;
     }
 }
 
-// Inner dimension contiguous in memory: a thread takes four consecutive q of one row.
+// Eight consecutive digits of each slice s_first+1 .. S with one 16-byte store per slice.
+__device__ __forceinline__ void write_digits8(const double (&x)[8], bool valid_row, int e, int S, int beta,
+                                              __half* __restrict__ digits, int64_t plane, int64_t off,
+                                              int s_first) {
+    uint32_t lo[8], hi[8], sg[8];
+    int t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) digit_source(x[i], valid_row, e, &lo[i], &hi[i], &t[i], &sg[i]);
+    const uint32_t mask = (1u << beta) - 1u;
+    for (int s = s_first + 1; s <= S; ++s) {
+        uint32_t u[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) u[i] = digit_bits(lo[i], hi[i], t[i] - beta * s, mask);
+        uint4 v;
+        v.x = digits_to_half2(u[0], u[1], sg[0], sg[1]);
+        v.y = digits_to_half2(u[2], u[3], sg[2], sg[3]);
+        v.z = digits_to_half2(u[4], u[5], sg[4], sg[5]);
+        v.w = digits_to_half2(u[6], u[7], sg[6], sg[7]);
+        *reinterpret_cast<uint4*>(digits + (s - 1) * plane + off) = v;
+    }
+}
+
+// Inner dimension contiguous in memory: a thread takes eight consecutive q of one row.
 __global__ void split_inner_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
                                    int64_t inner, const int32_t* __restrict__ exps,
                                    const uint8_t* __restrict__ flags, int S, int beta,
-                                   __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad) {
-    const int64_t quads = inner_pad / 4;
-    const int64_t total = rows_pad * quads;
+                                   __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad,
+                                   int s_first) {
+    const int64_t octs = inner_pad / 8;
+    const int64_t total = rows_pad * octs;
     const int64_t plane = rows_pad * inner_pad;
     for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
          idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t r = idx / quads;
-        const int64_t q = (idx - r * quads) * 4;
+        const int64_t r = idx / octs;
+        const int64_t q = (idx - r * octs) * 8;
         const bool valid = r < rows && !flags[r];
-        double x[4];
+        double x[8];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) x[t] = (valid && q + t < inner) ? X[q + t + r * ld] : 0.0;
-        write_digits4(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q);
+        for (int t = 0; t < 8; ++t) x[t] = (valid && q + t < inner) ? X[q + t + r * ld] : 0.0;
+        write_digits8(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
     }
 }
 
@@ -232,7 +265,8 @@ constexpr int TT = 64;
 __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
                                   int64_t inner, const int32_t* __restrict__ exps,
                                   const uint8_t* __restrict__ flags, int S, int beta,
-                                  __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad) {
+                                  __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad,
+                                  int s_first) {
     __shared__ double tile[TT][TT + 1];  // [q][r]
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TT;
     const int64_t q0 = static_cast<int64_t>(blockIdx.y) * TT;
@@ -252,12 +286,12 @@ __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int6
         double x[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr];
-        write_digits4(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q);
+        write_digits4(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
     }
 }
 
-// Logical matrix Y (rows x inner): Y(r, q) = X[r*sr + q*sq]; returns true when rows
-// are the contiguous dimension (sr == 1).
+// Logical matrix Y (rows x inner): Y(r, q) = X[r*sr + q*sq]; true when rows are the
+// contiguous dimension (sr == 1).
 inline bool rows_contiguous(int which, int op) {
     // which 0: rows of op(A) -- op N: A[r + q*ld] (rows contiguous); op T: A[q + r*ld]
     // which 1: columns of op(B) -- op N: B[q + r*ld] (inner contiguous); op T: B[r + q*ld]
@@ -452,25 +486,27 @@ cudaError_t launch_emu_spread(int64_t rows, int64_t inner, const int32_t* exps, 
 
 cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, const double* X,
                              int64_t ldx, const int32_t* exps, const uint8_t* flags, int S, int beta,
-                             void* digits, int64_t rows_pad, int64_t inner_pad, cudaStream_t stream) {
+                             void* digits, int64_t rows_pad, int64_t inner_pad, cudaStream_t stream,
+                             int s_first) {
     using namespace split;
     if (rows_pad <= 0 || inner_pad <= 0) return cudaSuccess;
-    if (S < 1 || beta < 1 || beta > 10 || inner_pad % 4) return cudaErrorInvalidValue;
-    if (reinterpret_cast<uintptr_t>(digits) % 8) return cudaErrorInvalidValue;
+    if (S < 1 || beta < 1 || beta > 10 || inner_pad % 8 || s_first < 0) return cudaErrorInvalidValue;
+    if (s_first >= S) return cudaSuccess;
+    if (reinterpret_cast<uintptr_t>(digits) % 16) return cudaErrorInvalidValue;
     __half* dg = static_cast<__half*>(digits);
     if (split::rows_contiguous(which, op)) {
         dim3 grid(static_cast<unsigned>((rows_pad + TT - 1) / TT), static_cast<unsigned>((inner_pad + TT - 1) / TT));
         if (grid.y > 65535) return cudaErrorInvalidValue;
         split_rows_contig<<<grid, 256, 0, stream>>>(X, ldx, rows, inner, exps, flags, S, beta, dg,
-                                                    rows_pad, inner_pad);
+                                                    rows_pad, inner_pad, s_first);
         return cudaGetLastError();
     }
-    const int64_t total = rows_pad * (inner_pad / 4);
+    const int64_t total = rows_pad * (inner_pad / 8);
     int64_t blocks = (total + 255) / 256;
     const int64_t cap = static_cast<int64_t>(device_sm_count()) * 32;
     if (blocks > cap) blocks = cap;
     split_inner_contig<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(X, ldx, rows, inner, exps, flags,
-                                                                          S, beta, dg, rows_pad, inner_pad);
+                                                                          S, beta, dg, rows_pad, inner_pad, s_first);
     return cudaGetLastError();
 }
 

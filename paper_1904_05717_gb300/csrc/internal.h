@@ -42,11 +42,12 @@ inline int emu_scale_kernel_count(int which, int op) { return ((which == 0) == (
 // atomicMax into *out of ceil(16 * max_r log2(2^e_r * inner / l1_r)).
 cudaError_t launch_emu_spread(int64_t rows, int64_t inner, const int32_t* exps, const uint8_t* flags,
                               const float* l1, int* out, cudaStream_t stream);
-// Truncation digits (fp16, integer valued), layout [S][rows_pad][inner_pad].
+// Truncation digits (fp16, integer valued), layout [S][rows_pad][inner_pad].  Only the
+// slices s_first .. S-1 (0-based) are written; a slice's digits do not depend on S.
 cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, const double* X,
                              int64_t ldx, const int32_t* exps, const uint8_t* flags, int S,
                              int beta, void* digits, int64_t rows_pad, int64_t inner_pad,
-                             cudaStream_t stream);
+                             cudaStream_t stream, int s_first = 0);
 
 struct EmuGemmArgs {
     int64_t m, n, k;

@@ -79,6 +79,8 @@ _SIGS = {
     "momms_gemm_emulated_noalloc": ([_I32, _I32, _I64, _I64, _I64, _I32, _DBL, _VP, _I64, _VP, _I64, _DBL, _VP,
                                      _I64, _VP], _I32),
     "momms_noalloc_scratch_bytes": ([], _SZ),
+    "momms_member_tile": ([_I32, _I32, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
+                          _I32),
 }
 
 
