@@ -36,11 +36,11 @@ sys.path.insert(0, ROOT)
 METRIC = "FP64-accurate GEMM TFLOP/s (2mnk/t) & % roofline, native vs emulated"
 
 # DRAM bytes (read + write) of one slice-product launch from the ncu capture summarised in
-# profiles/slice_gemm_4096.md (m=n=k=4096, S=6), with that launch's algorithmic tensor flops.
-# The 8192^3 launch is too large to capture with --set full, so its traffic is this figure scaled
-# by the tensor flops (the per-pair panel re-reads grow in proportion).  Set to None whenever the
-# slice-product kernel changes until it is captured again.
-NCU_SLICE_CAPTURE = {"dram_bytes": 4.705411e9 + 0.775041e9, "tensor_flops": 21 * 2.0 * 4096 ** 3}
+# profiles/slice_gemm_members_4096.md (m=n=k=4096, S=6, default C2 group), with that launch's
+# algorithmic tensor flops.  The 8192^3 traffic is this figure scaled by the tensor flops (the
+# per-pair panel re-reads grow about in proportion).  Set to None whenever the slice-product
+# kernel changes until it is captured again.
+NCU_SLICE_CAPTURE = {"dram_bytes": 3.6479e9 + 0.4276e9, "tensor_flops": 21 * 2.0 * 4096 ** 3}
 UNIT = "TFLOP/s"
 
 
@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--mode", default="auto", choices=["auto", "native", "emulated"])
     p.add_argument("--member", default="auto", choices=["auto", "C2", "A2", "B2", "A1"])
     p.add_argument("--slices", type=int, default=0, help="emulated slice count (0 = from the data)")
+    p.add_argument("--group", type=int, default=0, help="C2 raster group in tile rows (0 = library default)")
+    p.add_argument("--ctas", type=int, default=0, help="grid cap of the product launch (0 = library default)")
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--native-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -288,6 +290,8 @@ def main():
     dC0 = dC.storage.clone()
 
     h = M.Handle(mode=mode, member=member, slices=args.slices)
+    h.set_raster_group(args.group)
+    h.set_max_ctas(args.ctas)
 
     def step():
         M.check(M.momms_gemm_ex(h, 0, 0, m, n, k, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream),
@@ -355,7 +359,7 @@ def main():
             traffic = NCU_SLICE_CAPTURE["dram_bytes"] * tensor_flops / NCU_SLICE_CAPTURE["tensor_flops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": "ncu 4096^3 capture scaled by tensor flops (profiles/slice_gemm_4096.md)",
+                "traffic_source": "ncu 4096^3 capture scaled by tensor flops (profiles/slice_gemm_members_4096.md)",
                 "kernel": "momms::emu::slice_gemm_kernel<192> (tcgen05 kind::f16)",
                 "peak_source": f"{src} bf16_tflops_sustained (fp16 rate = bf16 rate)",
                 "algorithmic_flops_per_launch": tensor_flops, "launch_ms": slice_ms}
@@ -392,16 +396,18 @@ def main():
     h2d = (m * k + k * n + m * n) * 8
     d2h = m * n * 8
     sets = [(dA, dB, dC), (M.DeviceMatrix(m, k), M.DeviceMatrix(k, n), M.DeviceMatrix(m, n))]
-    copy_s = torch.cuda.Stream()
+    copy_s = torch.cuda.Stream()  # host -> device
+    back_s = torch.cuda.Stream()  # device -> host (the other copy direction, its own engine)
     comp_s = stream
     ev_in = [torch.cuda.Event(), torch.cuda.Event()]
     ev_done = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_read = [torch.cuda.Event(), torch.cuda.Event()]
 
     def h2d_into(i):
         A_, B_, C_ = sets[i % 2]
         with torch.cuda.stream(copy_s):
             if i >= 2:
-                copy_s.wait_event(ev_done[i % 2])  # the set's previous step has finished
+                copy_s.wait_event(ev_read[i % 2])  # the set's previous result has been read back
             A_.storage.copy_(A_p, non_blocking=True)
             B_.storage.copy_(B_p, non_blocking=True)
             C_.storage.copy_(C_p, non_blocking=True)
@@ -417,9 +423,10 @@ def main():
             M.check(M.momms_gemm_ex(h, 0, 0, m, n, k, 1.0, A_.ptr, A_.ld, B_.ptr, B_.ld, 1.0, C_.ptr, C_.ld,
                                     comp_s), "momms_gemm_ex")
             ev_done[i % 2].record(comp_s)
-            with torch.cuda.stream(copy_s):
-                copy_s.wait_event(ev_done[i % 2])
+            with torch.cuda.stream(back_s):
+                back_s.wait_event(ev_done[i % 2])
                 C_out.copy_(C_.storage, non_blocking=True)
+                ev_read[i % 2].record(back_s)
         torch.cuda.synchronize()
 
     e2e_run(2)
@@ -449,6 +456,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload_name(args), "path": "emulated" if emulated else "native",
                        "slices": S, "digit_bits": bb, "member": M.MEMBER_NAMES.get(int(rep["member"]), "auto"),
+                       "raster_group": int(rep["group"]), "ctas": int(rep["ctas"]),
                        "l2": "operands exceed L2 (126 MB) at the default size: no flush between steps",
                        "replicas": world},
             "roofline": roof,
@@ -456,8 +464,9 @@ def main():
             "emulated_vs_native": (value / world / native["value"]) if (native and emulated) else None,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms, "steps": esteps,
-                    "how": "host wall clock over all steps; pinned host buffers; copies of step i+1 overlap "
-                           "step i on a second stream (two device buffer sets)"},
+                    "how": "host wall clock over all steps; pinned host buffers; the inputs of step i+1 are "
+                           "copied in on one stream and the result of step i-1 copied out on another "
+                           "while step i computes (two device buffer sets)"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "device_status": status,

@@ -92,6 +92,8 @@ typedef struct {
     int digit_bits;      /* beta (bits per digit), 0 for native                      */
     int k_passes;        /* launches along k (emulated: keeps int32 sums exact)      */
     int tile_m, tile_n;  /* CTA tile                                                 */
+    int ctas;            /* CTAs of the (last) product launch                        */
+    int group;           /* C2 raster group: tile rows of the C block a wave covers  */
     int64_t launches;    /* kernels enqueued by the call                             */
     double est_err_ratio;/* emulated: estimated truncation error / bound (heuristic) */
 } momms_report_t;
@@ -105,6 +107,21 @@ int momms_set_member(momms_handle_t handle, int member);  /* momms_member_t     
  * spread of the inputs), else 1..MOMMS_MAX_SLICES. */
 int momms_set_slices(momms_handle_t handle, int slices);
 #define MOMMS_MAX_SLICES 16
+/* Caps the grid of the single-product launches of this handle at `ctas` CTAs that each
+ * loop over their share of the member's tiles (0 = default: one CTA per SM for the
+ * emulated slice products, one CTA per tile for the native kernel).  Fewer CTAs lower
+ * the engine's compute rate while the memory system stays the same, which moves the
+ * compute-to-bandwidth ratio the paper varies between its experiments (Sec. 5.2,
+ * Fig. 6) -- the knob of the bandwidth-ratio sweep.  Values above the SM count are
+ * clamped to it in emulated mode.  Batched calls ignore it.  Returns -2 for ctas < 0. */
+int momms_set_max_ctas(momms_handle_t handle, int ctas);
+/* Tile rows of the block of C that one wave of CTAs covers under member C2 (the
+ * resident block's m_c in tiles, Sec. 2.2.1; its n_c is the wave size over this).
+ * 0 = default: for the emulated kernel the group, near sqrt(wave * 192 / 128), that
+ * minimises the operand rows all waves read per unit of k (counted over the actual tile
+ * order, so waves straddling two groups are included); 16 for the native kernel.
+ * Single-product calls only.  Returns -2 for group < 0. */
+int momms_set_raster_group(momms_handle_t handle, int group);
 int momms_get_last_report(momms_handle_t handle, momms_report_t* report);
 /* Device status word of the handle (0 = fine, MOMMS_ERR_TIMEOUT after a capped
  * wait expired).  Synchronises `stream` first.  Clears the word. */
@@ -241,7 +258,8 @@ int momms_load_plans(momms_handle_t handle, const char* path);
 /* ------------------------------------------------------- schedule query */
 /* The member's tile order (host side, no GPU needed): the i-th tile taken by CTA `cta`
  * of `ctas` persistent CTAs over a tiles_m x tiles_n tile grid (group = tile rows per
- * group of the C2 raster; <= 0 means 8).  Returns 1 and writes (tm, tn), 0 when that CTA
+ * group of the C2 raster; <= 0 means the emulated kernel's default for `ctas` CTAs, see
+ * momms_set_raster_group).  Returns 1 and writes (tm, tn), 0 when that CTA
  * has no i-th tile, or a negative argument index.  The kernels use the same function. */
 int momms_member_tile(int member, int group, int64_t cta, int64_t ctas, int64_t i, int tiles_m,
                       int tiles_n, int* tm, int* tn);
@@ -251,6 +269,17 @@ int momms_member_tile(int member, int group, int64_t cta, int64_t ctas, int64_t 
  * 2 = fp16 tcgen05 (kind::f16, FP32 accumulate).  Writes the achieved rate in
  * TFLOP/s to *tflops.  Synchronous. */
 int momms_probe_peak(int kind, double* tflops, momms_stream_t stream);
+/* Copies `bytes` of device memory from src to dst, `repeats` times over, on `ctas` SMs
+ * (one CTA of 1024 threads per SM; 0 = every SM), asynchronously on `stream`, with
+ * streaming cache hints.  Both pointers 16-byte aligned, bytes a multiple of 16, the
+ * ranges disjoint; the caller owns both buffers.  An HBM bandwidth probe, and the
+ * background traffic of the bandwidth-ratio experiment: launched on a second stream it
+ * takes HBM bandwidth away from a product running beside it on the other SMs, the GPU
+ * counterpart of the paper's lowered main-memory bandwidth (Sec. 5.2, Fig. 6).  The
+ * paper has no such routine.  Returns -1 (dst), -2 (src), -3 (bytes), -4 (ctas) or
+ * -5 (repeats) for a bad argument, MOMMS_ERR_CUDA if the launch fails. */
+int momms_stream_copy(void* dst, const void* src, size_t bytes, int ctas, int repeats,
+                      momms_stream_t stream);
 
 #ifdef __cplusplus
 }

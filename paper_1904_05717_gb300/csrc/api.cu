@@ -52,7 +52,8 @@ struct momms_handle_s {
     int member = MOMMS_MEMBER_AUTO;
     int slices = 0;
     int digit_bits = kDigitBits;
-    int tile_n = 0;                 // emulated CTA tile width (192 / 240; 0 = automatic)
+    int max_ctas = 0;               // grid cap of the single-product launches (0 = default)
+    int group = 0;                  // C2 raster group in tile rows (0 = default)
     void* user_ws = nullptr;
     size_t user_ws_bytes = 0;
     void* own_ws = nullptr;
@@ -216,11 +217,14 @@ Plan pick_plan(momms_handle_t h, int64_t m, int64_t n, int64_t k) {
 int run_native(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
                const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                int64_t ldc, int member, cudaStream_t s) {
+    int ctas = 0, group = 0;
     cudaError_t e = momms::launch_native_gemm(opa, opb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
-                                              member, s);
+                                              member, h->max_ctas, h->group, s, &ctas, &group);
     if (e == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return MOMMS_ERR_CUDA;
     h->report = momms_report_t{};
+    h->report.ctas = ctas;
+    h->report.group = group;
     h->report.mode = MOMMS_MODE_NATIVE;
     h->report.member = member;
     h->report.tile_m = momms::kNativeBM;
@@ -298,22 +302,25 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     a.Ad = Ad; a.Bd = Bd; a.m_pad = L.m_pad; a.n_pad = L.n_pad; a.k_pad = L.k_pad;
     a.e = e; a.ef = ef; a.f = f; a.ff = ff;
     a.alpha = alpha; a.beta_c = beta; a.C = C; a.ldc = ldc;
-    a.member = member; a.group = 0;
+    a.member = member; a.group = h->group;
     a.scratch = scratch; a.scratch_bytes = momms::emu_scratch_bytes(momms::device_sm_count());
-    a.status = h->status; a.max_ctas = 0; a.tile_n = h->tile_n;
-    int passes = 0;
+    a.status = h->status; a.max_ctas = h->max_ctas; a.tile_n = 0;
+    int passes = 0, used_ctas = 0, used_group = 0;
+    a.used_ctas = &used_ctas; a.used_group = &used_group;
     ce = momms::launch_emu_slice_gemm(a, &passes, s);
     if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
     if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
     launches += passes;
     h->report = momms_report_t{};
+    h->report.ctas = used_ctas;
+    h->report.group = used_group;
     h->report.mode = MOMMS_MODE_EMULATED;
     h->report.member = member;
     h->report.slices = S;
     h->report.digit_bits = bb;
     h->report.k_passes = passes;
     h->report.tile_m = momms::kEmuBM;
-    h->report.tile_n = momms::emu_pick_bn(n, h->tile_n);
+    h->report.tile_n = momms::emu_pick_bn(n, 0);
     h->report.launches = launches;
     h->report.est_err_ratio = est;
     return MOMMS_OK;
@@ -578,7 +585,6 @@ int momms_create(momms_handle_t* handle) {
         cudaGetLastError();
         h->spread_ready = nullptr;
     }
-    if (const char* v = std::getenv("MOMMS_TILE_N")) h->tile_n = std::atoi(v);
     if (cudaMemset(h->status, 0, 64) != cudaSuccess ||
         cudaMallocHost(&h->spread_host, 2 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -624,6 +630,20 @@ int momms_set_slices(momms_handle_t h, int slices) {
     if (!valid(h)) return MOMMS_ERR_HANDLE;
     if (slices < 0 || slices > MOMMS_MAX_SLICES) return -2;
     h->slices = slices;
+    return MOMMS_OK;
+}
+
+int momms_set_max_ctas(momms_handle_t h, int ctas) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (ctas < 0) return -2;
+    h->max_ctas = ctas;
+    return MOMMS_OK;
+}
+
+int momms_set_raster_group(momms_handle_t h, int group) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (group < 0) return -2;
+    h->group = group;
     return MOMMS_OK;
 }
 
@@ -1084,7 +1104,8 @@ int momms_member_tile(int member, int group, int64_t cta, int64_t ctas, int64_t 
     if (!tm) return -8;
     if (!tn) return -9;
     const int mem = member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : member;
-    return momms::member_tile(mem, group > 0 ? group : 8, cta, ctas, i, tiles_m, tiles_n, tm, tn) ? 1 : 0;
+    const int g = group > 0 ? group : momms::emu_default_group(ctas, tiles_m, tiles_n);
+    return momms::member_tile(mem, g, cta, ctas, i, tiles_m, tiles_n, tm, tn) ? 1 : 0;
 }
 
 int momms_probe_peak(int kind, double* tflops, momms_stream_t stream) {
@@ -1093,6 +1114,19 @@ int momms_probe_peak(int kind, double* tflops, momms_stream_t stream) {
     cudaError_t e = momms::probe_peak(kind, tflops, reinterpret_cast<cudaStream_t>(stream));
     if (e == cudaErrorNotSupported) return MOMMS_ERR_UNSUPPORTED;
     return cuda_fail(e);
+}
+
+int momms_stream_copy(void* dst, const void* src, size_t bytes, int ctas, int repeats, momms_stream_t stream) {
+    if (!dst || (reinterpret_cast<uintptr_t>(dst) & 15)) return -1;
+    if (!src || (reinterpret_cast<uintptr_t>(src) & 15)) return -2;
+    if (bytes % 16) return -3;
+    if (ctas < 0) return -4;
+    if (repeats < 0) return -5;
+    const char* d = static_cast<const char*>(dst);
+    const char* s = static_cast<const char*>(src);
+    if (bytes && d < s + bytes && s < d + bytes) return -1;  // overlapping ranges
+    cudaError_t e = momms::stream_copy(dst, src, bytes, ctas, repeats, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MOMMS_OK : MOMMS_ERR_CUDA;
 }
 
 }  // extern "C"

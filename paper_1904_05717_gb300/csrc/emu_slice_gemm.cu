@@ -31,7 +31,13 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -149,6 +155,7 @@ MOMMS_DEV double scale_pow2(double r, int E) {
 struct RecombineCtx {
     long long* Q;
     double* R;
+    uint64_t keep;     // L2 policy of the scratch accesses (evict last)
     uint32_t tsum;     // TMEM address of the int32 sums of the last CT columns
     int sh;            // beta * (position of d in its group)
     double gscale;     // 2^-(beta * position)
@@ -176,20 +183,20 @@ MOMMS_DEV void recombine8(const RecombineCtx& rc, const int32_t (&pv)[8], int c0
     double rv[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        qv[j] = rc.gfirst ? 0ll : rc.Q[(c0 + j) * BM_];
-        if (MODE != kMid) rv[j] = rc.rfirst ? 0.0 : rc.R[(c0 + j) * BM_];
+        qv[j] = rc.gfirst ? 0ll : ld_l2_hint(rc.Q + (c0 + j) * BM_, rc.keep);
+        if (MODE != kMid) rv[j] = rc.rfirst ? 0.0 : ld_l2_hint(rc.R + (c0 + j) * BM_, rc.keep);
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const long long p64 = static_cast<long long>(pv[j]);
         const long long v = rc.gfirst ? p64 : qv[j] + (p64 << rc.sh);
         if (MODE == kMid) {
-            rc.Q[(c0 + j) * BM_] = v;
+            st_l2_hint(rc.Q + (c0 + j) * BM_, v, rc.keep);
         } else {
             const double x = static_cast<double>(v);
             const double r = (rc.rfirst ? x : fma(rv[j], rc.rb, x)) * rc.gscale;
             if (MODE == kGroupEnd) {
-                rc.R[(c0 + j) * BM_] = r;
+                st_l2_hint(rc.R + (c0 + j) * BM_, r, rc.keep);
             } else if (fc->row_ok && c0 + j < fc->ncols) {
                 const double y = (fc->eflag || fc->colflag[c0 + j]) ? fc->qnan
                                                                     : scale_pow2(r, fc->ei + fc->colexp[c0 + j]);
@@ -396,6 +403,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const double qnan = __longlong_as_double(0x7ff8000000000000ll);
         long long* Q = p.qscratch + (static_cast<size_t>(blockIdx.x) * BN + third * CW) * BM + rloc;
         double* R = p.scratch + (static_cast<size_t>(blockIdx.x) * BN + third * CW) * BM + rloc;
+        const uint64_t keep = l2_policy_evict_last();
         bool ok = true;
         for (int it = 0; ok; ++it) {
             int tm, tn, prob;
@@ -473,7 +481,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 //     C := alpha 2^(e_i + f_j - 2 beta) R + beta_c C.
                 const bool gfirst = (gj == 0);
                 const bool gend = (pr.group_end >> d) & 1u;
-                const RecombineCtx rc{Q, R, tsum, pr.beta * gj, pow2_normal(-pr.beta * gj), rb, gfirst, rfirst};
+                const RecombineCtx rc{Q, R, keep, tsum, pr.beta * gj, pow2_normal(-pr.beta * gj), rb, gfirst, rfirst};
                 if (!gend) {
                     recombine<kMid, CR, CT>(rc, acc, nullptr);
                 } else if (d != 2) {
@@ -561,7 +569,7 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     const int sms = device_sm_count();
     const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
     const int64_t tiles = tiles_m * tiles_n;
-    int64_t ctas = a.max_ctas > 0 ? a.max_ctas : sms;
+    int64_t ctas = a.max_ctas > 0 && a.max_ctas < sms ? a.max_ctas : sms;  // one CTA per SM at most
     if (ctas > tiles) ctas = tiles;
     const size_t half = static_cast<size_t>(ctas) * BN * BM * sizeof(double);
     if (a.scratch_bytes < 2 * half) return cudaErrorInvalidValue;
@@ -603,7 +611,9 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         p.tiles_m = static_cast<int>(tiles_m);
         p.tiles_n = static_cast<int>(tiles_n);
         p.member = a.member == kMemberAuto ? kMemberC2 : a.member;
-        p.group = a.group > 0 ? a.group : 8;
+        p.group = a.group > 0 ? a.group : emu_default_group(ctas, static_cast<int>(tiles_m), static_cast<int>(tiles_n));
+        if (a.used_ctas) *a.used_ctas = static_cast<int>(ctas);
+        if (a.used_group) *a.used_group = p.group;
         p.table = nullptr;
         p.qscratch = static_cast<long long*>(a.scratch);
         p.scratch = reinterpret_cast<double*>(static_cast<char*>(a.scratch) + half);
@@ -713,6 +723,45 @@ int emu_chunk_slabs(int beta) {
 }
 
 int emu_pick_bn(int64_t, int) { return 192; }
+
+// The C2 group (tile rows of the block of C one wave covers) with the fewest operand rows
+// read over all waves: a wave of `ctas` consecutive tiles of the raster reads the A rows of
+// its distinct tile rows and the B rows of its distinct tile columns once per unit of k
+// (Resident C at the L2 level, Sec. 2.2.1).  The continuous optimum r = sqrt(ctas*BN/BM)
+// ignores waves that straddle two groups, so the candidates around it are counted exactly.
+int emu_default_group(int64_t ctas, int tiles_m, int tiles_n) {
+    if (tiles_m <= 1 || tiles_n <= 0 || ctas <= 1) return 1;
+    static std::mutex mu;
+    static std::map<std::tuple<int64_t, int, int>, int> cache;
+    const auto key = std::make_tuple(ctas, tiles_m, tiles_n);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    const int64_t total = static_cast<int64_t>(tiles_m) * tiles_n;
+    const int r0 = static_cast<int>(std::sqrt(static_cast<double>(ctas) * kEmuBNMax / kEmuBM));
+    const int lo = std::max(1, r0 / 2), hi = std::min(tiles_m, std::max(1, 2 * r0 + 1));
+    std::vector<int64_t> row_seen(tiles_m), col_seen(tiles_n);
+    int best = std::min(std::max(1, r0), tiles_m);
+    int64_t best_cost = -1;
+    for (int r = lo; r <= hi; ++r) {
+        std::fill(row_seen.begin(), row_seen.end(), -1);
+        std::fill(col_seen.begin(), col_seen.end(), -1);
+        int64_t cost = 0;
+        for (int64_t t = 0; t < total; ++t) {
+            const int64_t wave = t / ctas;
+            int tm, tn;
+            member_tile(kMemberC2, r, t % ctas, ctas, wave, tiles_m, tiles_n, &tm, &tn);
+            if (row_seen[tm] != wave) { row_seen[tm] = wave; cost += kEmuBM; }
+            if (col_seen[tn] != wave) { col_seen[tn] = wave; cost += kEmuBNMax; }
+        }
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = r; }
+    }
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = best;
+    return best;
+}
 
 cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_t stream) {
     using namespace emu;

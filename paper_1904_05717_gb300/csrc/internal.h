@@ -11,8 +11,9 @@ namespace momms {
 // C := alpha*op(A)*op(B) + beta*C on the FP64 DMMA tensor instructions.
 cudaError_t launch_native_gemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, double alpha,
                                const double* A, int64_t lda, const double* B, int64_t ldb,
-                               double beta, double* C, int64_t ldc, int member,
-                               cudaStream_t stream);
+                               double beta, double* C, int64_t ldc, int member, int max_ctas,
+                               int group, cudaStream_t stream, int* used_ctas = nullptr,
+                               int* used_group = nullptr);
 constexpr int kNativeBM = 64, kNativeBN = 64;
 
 // One problem of a batched call (device-resident table entry).
@@ -68,6 +69,8 @@ struct EmuGemmArgs {
     int32_t* status;
     int max_ctas;  // 0 = number of SMs
     int tile_n;    // CTA tile width request (only 192 is built; 0 = automatic)
+    int* used_ctas;   // optional out: persistent CTAs launched
+    int* used_group;  // optional out: C2 raster group used
 };
 constexpr int kEmuBM = 128, kEmuBK = 64, kEmuBNMax = 192;
 
@@ -121,6 +124,9 @@ cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int 
                                           cudaStream_t stream);
 // The CTA tile width used for n columns (tile_n request 0 = automatic).
 int emu_pick_bn(int64_t n, int requested);
+// Default C2 group of the slice-product kernel for `ctas` persistent CTAs (tile rows of the
+// block of C one wave covers; fewest operand rows read per unit of k over all waves).
+int emu_default_group(int64_t ctas, int tiles_m, int tiles_n);
 // Launches the slice-product kernel once per k pass; *passes receives the count.
 cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_t stream);
 size_t emu_scratch_bytes(int num_sms);
@@ -136,5 +142,7 @@ int device_sm_count();
 
 // ------------------------------------------------------------------ probes
 cudaError_t probe_peak(int kind, double* tflops, cudaStream_t stream);
+// Copies `bytes` (multiple of 16, 16-byte aligned) `repeats` times on `ctas` SMs (0 = all).
+cudaError_t stream_copy(void* dst, const void* src, size_t bytes, int ctas, int repeats, cudaStream_t stream);
 
 }  // namespace momms

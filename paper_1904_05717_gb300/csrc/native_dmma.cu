@@ -174,8 +174,11 @@ __global__ void __launch_bounds__(THREADS)
                 int64_t ldc, int member, int group, int tiles_m, int tiles_n) {
     __shared__ Smem sm;
     int tm, tn;
-    if (!member_tile(member, group, blockIdx.x, gridDim.x, 0, tiles_m, tiles_n, &tm, &tn)) return;
-    gemm_tile<TA, TB>(sm, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tm, tn);
+    // one tile per CTA by default; a capped grid loops over the CTA's share in member order
+    for (int64_t i = 0; member_tile(member, group, blockIdx.x, gridDim.x, i, tiles_m, tiles_n, &tm, &tn); ++i) {
+        if (i > 0) __syncthreads();  // the shared panels are reused by the next tile
+        gemm_tile<TA, TB>(sm, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tm, tn);
+    }
 }
 
 // Persistent launch over the tiles of many problems (op = N, N).
@@ -204,7 +207,8 @@ __global__ void __launch_bounds__(THREADS)
 
 cudaError_t launch_native_gemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, double alpha,
                                const double* A, int64_t lda, const double* B, int64_t ldb,
-                               double beta, double* C, int64_t ldc, int member, cudaStream_t stream) {
+                               double beta, double* C, int64_t ldc, int member, int max_ctas,
+                               int group_req, cudaStream_t stream, int* used_ctas, int* used_group) {
     using namespace native;
     if (m <= 0 || n <= 0) return cudaSuccess;
     if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k > INT32_MAX / 2) return cudaErrorInvalidValue;
@@ -213,8 +217,10 @@ cudaError_t launch_native_gemm(int op_a, int op_b, int64_t m, int64_t n, int64_t
     const int64_t tiles = static_cast<int64_t>(tiles_m) * tiles_n;
     if (tiles > INT32_MAX) return cudaErrorInvalidValue;
     const int mem = member == kMemberAuto ? kMemberC2 : member;
-    const int group = 16;
-    const dim3 grid(static_cast<unsigned>(tiles));
+    const int group = group_req > 0 ? group_req : 16;
+    const dim3 grid(static_cast<unsigned>(max_ctas > 0 && max_ctas < tiles ? max_ctas : tiles));
+    if (used_ctas) *used_ctas = static_cast<int>(grid.x);
+    if (used_group) *used_group = group;
     const int mi = static_cast<int>(m), ni = static_cast<int>(n), ki = static_cast<int>(k);
     if (!op_a && !op_b)
         gemm_kernel<false, false><<<grid, THREADS, 0, stream>>>(mi, ni, ki, alpha, A, lda, B, ldb, beta, C, ldc, mem, group, tiles_m, tiles_n);

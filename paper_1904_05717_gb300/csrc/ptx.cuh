@@ -237,6 +237,31 @@ MOMMS_DEV void named_bar_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// L2 eviction priority "evict last" for every line the policy is attached to, and 8-byte
+// global accesses that carry it (PTX createpolicy / ld|st .L2::cache_hint): scratch that
+// is written and read back soon stays in L2 instead of being written back to HBM.
+MOMMS_DEV uint64_t l2_policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+MOMMS_DEV long long ld_l2_hint(const long long* p, uint64_t pol) {
+    long long v;
+    asm volatile("ld.global.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
+    return v;
+}
+MOMMS_DEV double ld_l2_hint(const double* p, uint64_t pol) {
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol) : "memory");
+    return v;
+}
+MOMMS_DEV void st_l2_hint(long long* p, long long v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.s64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+MOMMS_DEV void st_l2_hint(double* p, double v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+
 // 2^x as a double for -1022 <= x <= 1023 (exact construction of the bit pattern).
 MOMMS_DEV double pow2_normal(int x) {
     return __longlong_as_double(static_cast<long long>(x + 1023) << 52);

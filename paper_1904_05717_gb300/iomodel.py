@@ -73,7 +73,7 @@ def member_tile(member: int, group: int, cta: int, ctas: int, i: int, tiles_m: i
     return (tm.value, tn.value) if ok == 1 else None
 
 
-def waves(member: int, tiles_m: int, tiles_n: int, ctas: int, group: int = 8):
+def waves(member: int, tiles_m: int, tiles_n: int, ctas: int, group: int = 0):
     """For every round i of the persistent loop, the distinct tile rows and columns in flight."""
     out = []
     i = 0
@@ -92,7 +92,7 @@ def waves(member: int, tiles_m: int, tiles_n: int, ctas: int, group: int = 8):
 
 # ----------------------------------------------------------------------------- GPU predictions
 def emulated_dram_bytes(member: int, m: int, n: int, k: int, S: int, ctas: int = 152, bm: int = 128,
-                        bn: int = 192, group: int = 8, beta_nonzero: bool = True):
+                        bn: int = 192, group: int = 0, beta_nonzero: bool = True):
     """HBM bytes of one slice-product launch: per round of persistent CTAs and per digit pair, the
     tile rows of A's slice and tile columns of B's slice in flight are read once (Resident C at the
     L2 level, the round's tiles being the resident block); plus C read (beta != 0) and written."""

@@ -43,7 +43,8 @@ class MommsError(RuntimeError):
 class Report(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("member", ctypes.c_int), ("slices", ctypes.c_int),
                 ("digit_bits", ctypes.c_int), ("k_passes", ctypes.c_int), ("tile_m", ctypes.c_int),
-                ("tile_n", ctypes.c_int), ("launches", ctypes.c_int64), ("est_err_ratio", ctypes.c_double)]
+                ("tile_n", ctypes.c_int), ("ctas", ctypes.c_int), ("group", ctypes.c_int),
+                ("launches", ctypes.c_int64), ("est_err_ratio", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -59,6 +60,8 @@ _SIGS = {
     "momms_set_mode": ([_VP, _I32], _I32),
     "momms_set_member": ([_VP, _I32], _I32),
     "momms_set_slices": ([_VP, _I32], _I32),
+    "momms_set_max_ctas": ([_VP, _I32], _I32),
+    "momms_set_raster_group": ([_VP, _I32], _I32),
     "momms_get_last_report": ([_VP, ctypes.POINTER(Report)], _I32),
     "momms_check_device_status": ([_VP, _VP], _I32),
     "momms_status_string": ([_I32], ctypes.c_char_p),
@@ -76,6 +79,7 @@ _SIGS = {
     "momms_tune": ([_VP, ctypes.c_char_p, _I64, _VP, _VP, _VP, _VP], _I32),
     "momms_load_plans": ([_VP, ctypes.c_char_p], _I32),
     "momms_probe_peak": ([_I32, ctypes.POINTER(_DBL), _VP], _I32),
+    "momms_stream_copy": ([_VP, _VP, _SZ, _I32, _I32, _VP], _I32),
     "momms_gemm_emulated_noalloc": ([_I32, _I32, _I64, _I64, _I64, _I32, _DBL, _VP, _I64, _VP, _I64, _DBL, _VP,
                                      _I64, _VP], _I32),
     "momms_noalloc_scratch_bytes": ([], _SZ),
@@ -197,6 +201,10 @@ def momms_probe_peak(kind, stream=None):
     return out.value
 
 
+def momms_stream_copy(dst, src, nbytes, ctas=0, repeats=1, stream=None):
+    return lib().momms_stream_copy(_VP(dst), _VP(src), nbytes, ctas, repeats, _stream(stream))
+
+
 def _h(handle):
     return handle.ptr if isinstance(handle, Handle) else _VP(handle)
 
@@ -230,6 +238,12 @@ class Handle:
 
     def set_slices(self, slices):
         check(lib().momms_set_slices(self.ptr, slices), "momms_set_slices")
+
+    def set_max_ctas(self, ctas):
+        check(lib().momms_set_max_ctas(self.ptr, ctas), "momms_set_max_ctas")
+
+    def set_raster_group(self, group):
+        check(lib().momms_set_raster_group(self.ptr, group), "momms_set_raster_group")
 
     def report(self):
         r = Report()

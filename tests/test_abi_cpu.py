@@ -69,3 +69,30 @@ def test_null_handle_is_rejected(L):
     assert L.momms_gemm_ex(None, 0, 0, 1, 1, 1, 1.0, None, 1, None, 1, 0.0, None, 1, None) == M.MOMMS_ERR_HANDLE
     r = M.Report()
     assert L.momms_get_last_report(None, ctypes.byref(r)) == M.MOMMS_ERR_HANDLE
+    assert L.momms_set_max_ctas(None, 4) == M.MOMMS_ERR_HANDLE
+    assert L.momms_set_raster_group(None, 4) == M.MOMMS_ERR_HANDLE
+
+
+def test_stream_copy_validates_before_launch(L):
+    base = 1 << 40
+
+    def copy(dst, src, nbytes, ctas=0, repeats=1):
+        return M.momms_stream_copy(dst, src, nbytes, ctas, repeats, stream=0)
+    assert copy(base + 8, base + (1 << 30), 64) == -1       # dst not 16-byte aligned
+    assert copy(base, base + (1 << 30) + 4, 64) == -2       # src not 16-byte aligned
+    assert copy(base, base + (1 << 30), 63) == -3           # not a multiple of 16
+    assert copy(base, base + (1 << 30), 64, ctas=-1) == -4
+    assert copy(base, base + (1 << 30), 64, repeats=-1) == -5
+    assert copy(base, base + 32, 64) == -1                  # overlapping ranges
+    assert copy(base, base + (1 << 30), 0) == 0             # nothing to copy
+
+
+def test_default_group_minimises_wave_rows():
+    # the library's default C2 group (momms_member_tile with group 0) is the candidate with the
+    # fewest operand rows over all waves; brute force over every group here
+    from paper_1904_05717_gb300 import iomodel as I
+    for tiles_m, tiles_n, ctas in [(64, 43, 152), (32, 22, 152), (128, 86, 152), (10, 7, 38), (64, 43, 76)]:
+        def cost(g):
+            return sum(r * 128 + c * 192 for r, c in I.waves(M.MEMBER_C2, tiles_m, tiles_n, ctas, g))
+        default = cost(0)
+        assert default == min(cost(g) for g in range(1, tiles_m + 1))

@@ -75,8 +75,9 @@ def test_split_bitwise(which, op, S, beta):
     assert not np.any(got[:, rows:, :]) and not np.any(got[:, :, inner:])  # zero padding
 
 
-def emulated(A, B, C0, alpha, beta, S, opa=0, opb=0, member=M.MEMBER_AUTO, ldc=None):
+def emulated(A, B, C0, alpha, beta, S, opa=0, opb=0, member=M.MEMBER_AUTO, ldc=None, ctas=0):
     h = M.Handle(mode=M.MODE_EMULATED, member=member, slices=S)
+    h.set_max_ctas(ctas)
     dA = M.DeviceMatrix.from_numpy(A)
     dB = M.DeviceMatrix.from_numpy(B)
     dC = M.DeviceMatrix.from_numpy(C0, ld=ldc)
@@ -170,6 +171,19 @@ def test_emulated_members_bitwise_identical():
             for mem in (M.MEMBER_C2, M.MEMBER_A2, M.MEMBER_B2, M.MEMBER_A1)]
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("ctas", [1, 5, 1000])
+def test_emulated_capped_grid_bitwise_identical(ctas):
+    # fewer persistent CTAs (or a cap above the SM count, clamped) change only which CTA
+    # computes a tile: 3 x 4 tiles of 128 x 192 with ragged edges
+    m, n, k = 300, 650, 200
+    A = syn.matrix("uniform", m, k, 81)
+    B = syn.matrix("uniform", k, n, 82)
+    C0 = syn.matrix("uniform", m, n, 83)
+    base = emulated(A, B, C0, 1.0, 1.0, 6)[0]
+    for mem in (M.MEMBER_C2, M.MEMBER_A2, M.MEMBER_B2, M.MEMBER_A1):
+        assert np.array_equal(emulated(A, B, C0, 1.0, 1.0, 6, member=mem, ctas=ctas)[0], base)
 
 
 def test_emulated_beta_zero_nan_and_padded_ldc():

@@ -9,8 +9,9 @@ from util import F, max_ratio, reference
 pytestmark = pytest.mark.gpu
 
 
-def run(A, B, C0, alpha, beta, opa=M.OP_N, opb=M.OP_N, member=M.MEMBER_AUTO, lds=(None, None, None)):
+def run(A, B, C0, alpha, beta, opa=M.OP_N, opb=M.OP_N, member=M.MEMBER_AUTO, lds=(None, None, None), ctas=0):
     h = M.Handle(mode=M.MODE_NATIVE, member=member)
+    h.set_max_ctas(ctas)
     dA = M.DeviceMatrix.from_numpy(A, ld=lds[0])
     dB = M.DeviceMatrix.from_numpy(B, ld=lds[1])
     dC = M.DeviceMatrix.from_numpy(C0, ld=lds[2])
@@ -91,6 +92,21 @@ def test_native_members_bitwise_identical_and_deterministic():
     outs.append(run(A, B, C0, 1.0, 1.0, member=M.MEMBER_C2)[0])
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("ctas", [1, 7, 152])
+def test_native_capped_grid_loops_over_member_tiles(ctas):
+    # a capped grid makes each CTA loop over its share of tiles in member order; every
+    # member must still cover every tile once (ragged 300 x 333: 5 x 6 tiles of 64)
+    m, n, k = 300, 333, 97
+    A = syn.matrix("uniform", m, k, 61)
+    B = syn.matrix("uniform", k, n, 62)
+    C0 = syn.matrix("uniform", m, n, 63)
+    base = run(A, B, C0, 1.0, 1.0)[0]
+    Cref, N = reference(A, B, C0, 1.0, 1.0)
+    assert max_ratio(base, Cref, k, 1.0, 1.0, N, C0) <= 1.0
+    for mem in (M.MEMBER_C2, M.MEMBER_A2, M.MEMBER_B2, M.MEMBER_A1):
+        assert np.array_equal(run(A, B, C0, 1.0, 1.0, member=mem, ctas=ctas)[0], base)
 
 
 def test_native_config1_512_cube():
