@@ -35,12 +35,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FP64-accurate GEMM TFLOP/s (2mnk/t) & % roofline, native vs emulated"
 
-# DRAM bytes (read + write) of one slice-product launch from the ncu capture summarised in
-# profiles/slice_gemm_members_4096.md (m=n=k=4096, S=6, default C2 group), with that launch's
-# algorithmic tensor flops.  The 8192^3 traffic is this figure scaled by the tensor flops (the
-# per-pair panel re-reads grow about in proportion).  Set to None whenever the slice-product
-# kernel changes until it is captured again.
-NCU_SLICE_CAPTURE = {"dram_bytes": 3.6479e9 + 0.4276e9, "tensor_flops": 21 * 2.0 * 4096 ** 3}
+# DRAM bytes (read + write) of one slice-product call (main + tail launch) from the ncu capture
+# summarised in profiles/slice_gemm_members_8192.md (m=n=k=8192, S=6, member C2, default group),
+# with that call's algorithmic tensor flops; other sizes scale it by the tensor flops.  Set to
+# None whenever the slice-product kernels change until they are captured again.
+NCU_SLICE_CAPTURE = {"dram_bytes": 32.51e9 + 2.04e9, "tensor_flops": 21 * 2.0 * 8192 ** 3}
 UNIT = "TFLOP/s"
 
 
@@ -331,7 +330,7 @@ def main():
         Bd = torch.empty((S, n, k_pad), dtype=torch.float16, device="cuda")
         M.check(M.momms_emu_split(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), S, bb, Ad.data_ptr(), m, k_pad, stream), "split")
         M.check(M.momms_emu_split(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), S, bb, Bd.data_ptr(), n, k_pad, stream), "split")
-        nbytes = M.momms_emu_scratch_bytes()
+        nbytes = M.momms_emu_scratch_bytes_for(m, n, k, S)
         scratch = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
         Cs = M.DeviceMatrix(m, n)
@@ -359,8 +358,9 @@ def main():
             traffic = NCU_SLICE_CAPTURE["dram_bytes"] * tensor_flops / NCU_SLICE_CAPTURE["tensor_flops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": "ncu 4096^3 capture scaled by tensor flops (profiles/slice_gemm_members_4096.md)",
-                "kernel": "momms::emu::slice_gemm_kernel<192> (tcgen05 kind::f16)",
+                "traffic_source": "ncu capture of the 8192^3 call, scaled by tensor flops for other sizes "
+                                  "(profiles/slice_gemm_members_8192.md)",
+                "kernel": "momms::emu::slice_gemm_kernel<192, 0|1> (tcgen05 kind::f16; main + tail launch)",
                 "peak_source": f"{src} bf16_tflops_sustained (fp16 rate = bf16 rate)",
                 "algorithmic_flops_per_launch": tensor_flops, "launch_ms": slice_ms}
         del Ad, Bd, scratch

@@ -204,9 +204,14 @@ int momms_emu_split(int which, int op, int64_t rows, int64_t inner, const double
  *   C := alpha * 2^(e_i+f_j) * sum_d 2^(-beta d) P_d + beta*C  (FP64 Horner).
  * Ad: S slices of m_pad x k_pad, Bd: S slices of n_pad x k_pad (layout above,
  * m_pad >= m, n_pad >= n, k_pad a multiple of 64; digit_bits <= 8).
- * scratch: device memory of momms_emu_scratch_bytes() bytes (FP64 partial sums
- * of the recombination, one 128 x 192 block per CTA).  status: a device int32
- * set to MOMMS_ERR_TIMEOUT if a bounded wait expires.  member: momms_member_t. */
+ * scratch: device memory of at least momms_emu_scratch_bytes() bytes (int64 / FP64
+ * partial sums of the recombination, one 128 x 192 block per CTA).  Given
+ * momms_emu_scratch_bytes_for(m, n, k, slices) bytes, the launch also splits the
+ * tiles of its last, partial round of CTAs along k (each part stores its exact int32
+ * diagonal sums there; the last part of a tile adds them up and recombines), so that
+ * round keeps most SMs busy; the result is bit-identical either way.  status: a
+ * device int32 set to MOMMS_ERR_TIMEOUT if a bounded wait expires.
+ * member: momms_member_t. */
 int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_bits,
                          const void* Ad, const void* Bd, int64_t m_pad, int64_t n_pad,
                          int64_t k_pad, const int32_t* e, const uint8_t* eflags,
@@ -214,6 +219,7 @@ int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_
                          double beta, double* C, int64_t ldc, int member, void* scratch,
                          size_t scratch_bytes, int32_t* status, momms_stream_t stream);
 size_t momms_emu_scratch_bytes(void);
+size_t momms_emu_scratch_bytes_for(int64_t m, int64_t n, int64_t k, int slices);
 
 /* ------------------------------------------------ allocation-free variant */
 /* The emulated product (scale, split and slice-product kernels of EMULATED mode)

@@ -90,10 +90,10 @@ int cuda_fail(cudaError_t e) {
 // Workspace carve-up of one emulated product.
 struct EmuLayout {
     int64_t m_pad, n_pad, k_pad;
-    size_t off_e, off_ef, off_f, off_ff, off_l1a, off_l1b, off_Ad, off_Bd, off_scratch, total;
+    size_t off_e, off_ef, off_f, off_ff, off_l1a, off_l1b, off_Ad, off_Bd, off_scratch, scratch_bytes, total;
 };
 
-EmuLayout emu_layout(int64_t m, int64_t n, int64_t k, int S) {
+EmuLayout emu_layout(int64_t m, int64_t n, int64_t k, int S, int max_ctas) {
     EmuLayout L{};
     // digit slices hold exactly m (n) rows: ragged tiles are zero-filled by the copy engine
     L.m_pad = std::max<int64_t>(m, 1);
@@ -108,7 +108,8 @@ EmuLayout emu_layout(int64_t m, int64_t n, int64_t k, int S) {
     L.off_l1b = o; o += align256(L.n_pad * sizeof(float));
     L.off_Ad = o;  o += align256(static_cast<size_t>(S) * L.m_pad * L.k_pad * 2);
     L.off_Bd = o;  o += align256(static_cast<size_t>(S) * L.n_pad * L.k_pad * 2);
-    L.off_scratch = o; o += align256(momms::emu_scratch_bytes(momms::device_sm_count()));
+    L.scratch_bytes = momms::emu_scratch_bytes_tail(m, n, k, S, max_ctas, kDigitBits);
+    L.off_scratch = o; o += align256(L.scratch_bytes);
     L.total = o;
     return L;
 }
@@ -240,7 +241,7 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     const int bb = h->digit_bits;
     if (S > MOMMS_MAX_SLICES) return MOMMS_ERR_UNSUPPORTED;
     const int S_alloc = S > 0 ? S : kAutoSliceMax;
-    EmuLayout L = emu_layout(m, n, k, S_alloc);
+    EmuLayout L = emu_layout(m, n, k, S_alloc, h->max_ctas);
     if (std::max(L.m_pad, L.n_pad) > (int64_t(1) << 30)) return MOMMS_ERR_UNSUPPORTED;
     void* ws = nullptr;
     int rc = ensure_workspace(h, L.total, &ws);
@@ -303,14 +304,14 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     a.e = e; a.ef = ef; a.f = f; a.ff = ff;
     a.alpha = alpha; a.beta_c = beta; a.C = C; a.ldc = ldc;
     a.member = member; a.group = h->group;
-    a.scratch = scratch; a.scratch_bytes = momms::emu_scratch_bytes(momms::device_sm_count());
+    a.scratch = scratch; a.scratch_bytes = L.scratch_bytes;
     a.status = h->status; a.max_ctas = h->max_ctas; a.tile_n = 0;
-    int passes = 0, used_ctas = 0, used_group = 0;
-    a.used_ctas = &used_ctas; a.used_group = &used_group;
+    int passes = 0, used_ctas = 0, used_group = 0, used_launches = 0;
+    a.used_ctas = &used_ctas; a.used_group = &used_group; a.used_launches = &used_launches;
     ce = momms::launch_emu_slice_gemm(a, &passes, s);
     if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
     if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-    launches += passes;
+    launches += used_launches;
     h->report = momms_report_t{};
     h->report.ctas = used_ctas;
     h->report.group = used_group;
@@ -693,7 +694,7 @@ int momms_workspace_size(momms_handle_t h, int op_a, int op_b, int64_t m, int64_
         *bytes = 0;
         return MOMMS_OK;
     }
-    *bytes = emu_layout(m, n, k, p.slices > 0 ? p.slices : kAutoSliceMax).total;
+    *bytes = emu_layout(m, n, k, p.slices > 0 ? p.slices : kAutoSliceMax, h->max_ctas).total;
     return MOMMS_OK;
 }
 
@@ -920,6 +921,11 @@ int momms_emu_split(int which, int op, int64_t rows, int64_t inner, const double
 }
 
 size_t momms_emu_scratch_bytes(void) { return momms::emu_scratch_bytes(momms::device_sm_count()); }
+
+size_t momms_emu_scratch_bytes_for(int64_t m, int64_t n, int64_t k, int slices) {
+    if (m <= 0 || n <= 0 || k <= 0 || slices < 1 || slices > MOMMS_MAX_SLICES) return momms_emu_scratch_bytes();
+    return momms::emu_scratch_bytes_tail(m, n, k, slices, 0, kDigitBits);
+}
 
 int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_bits, const void* Ad,
                          const void* Bd, int64_t m_pad, int64_t n_pad, int64_t k_pad, const int32_t* e,

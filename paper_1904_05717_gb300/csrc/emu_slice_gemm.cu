@@ -95,14 +95,37 @@ struct Params {
     double* scratch;          // FP64 partial recombination R, one BN x BM block per CTA
     long long* qscratch;      // int64 exact group sums Q, one BN x BM block per CTA
     int32_t* status;
+    // Tail split (single problem, round-robin members): the main launch stops after its whole
+    // rounds; the tiles of the last, partial round go to a second launch that cuts each along k
+    // into tail_parts units, one per CTA; each unit stores its int32 diagonal sums and the last
+    // unit of a tile to finish adds them up and recombines.
+    int full_rounds;          // whole-tile rounds of the main launch
+    int main_ctas;            // CTAs of the main launch (its round-robin order places the tail tiles)
+    int tail_tiles;           // tiles in the tail round
+    int tail_parts;           // k parts per tail tile (< 2: no split)
+    int32_t* tail_sums;       // [tail tile][part][diagonal d-2][column][row] int32 partial sums
+    int* tail_count;          // [tail tile][drain warp] parts stored (zero at launch)
 };
 
 // The it-th tile of this CTA: its problem (-1 = the single problem of p.one) and tile
 // coordinates.  A single problem uses the member's tile order; a batch walks the
 // concatenated tile list of all problems cyclically.
-MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn) {
+template <bool TAIL>
+MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int* part) {
+    *part = -1;
+    if constexpr (TAIL) {
+        // the tail launch: CTA b takes k part b % parts of tail tile b / parts, the tail tiles
+        // being the last, partial round of the main launch's round-robin order
+        if (it > 0) return false;
+        *prob = -1;
+        *part = static_cast<int>(blockIdx.x) % p.tail_parts;
+        const int64_t t = static_cast<int64_t>(p.full_rounds) * p.main_ctas + static_cast<int>(blockIdx.x) / p.tail_parts;
+        return member_tile(p.member, p.group, t % p.main_ctas, p.main_ctas, t / p.main_ctas, p.tiles_m, p.tiles_n,
+                           tm, tn);
+    }
     if (p.table == nullptr) {
         *prob = -1;
+        if (p.tail_parts >= 2 && it >= p.full_rounds) return false;  // the rest is the tail launch's
         return member_tile(p.member, p.group, blockIdx.x, gridDim.x, it, p.tiles_m, p.tiles_n, tm, tn);
     }
     const int64_t t = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
@@ -126,11 +149,16 @@ struct TileInts {
     int S, beta, chunk_slabs, slab0, nslab;
     uint32_t group_end;
 };
-MOMMS_DEV TileInts tile_ints(const Params& p, int prob) {
+MOMMS_DEV TileInts tile_ints(const Params& p, int prob, int part) {
     TileInts t;
     if (prob < 0) {
         t.S = p.one.S; t.beta = p.one.beta; t.chunk_slabs = p.one.chunk_slabs;
         t.slab0 = p.one.slab0; t.nslab = p.one.nslab; t.group_end = p.one.group_end;
+        if (part >= 0) {  // this unit's share of the pass's k slabs (every part gets at least one)
+            const int lo = part * t.nslab / p.tail_parts, hi = (part + 1) * t.nslab / p.tail_parts;
+            t.slab0 += lo;
+            t.nslab = hi - lo;
+        }
     } else {
         const EmuBatchProblem& b = p.table[prob];
         t.S = b.S; t.beta = b.beta; t.chunk_slabs = b.chunk_slabs;
@@ -238,10 +266,219 @@ MOMMS_DEV bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
     return mbar_wait(bar, parity, &never);
 }
 
+// Recombination of diagonal d of tile (tm, tn) once its int32 sums are complete: the first CR
+// columns of the thread in `acc`, the other CT in TMEM at `tsum`.  Diagonals arrive from the
+// least significant (d = S + 1) to the most significant (d = 2).  Inside a group the diagonal
+// sums are combined exactly in int64, Q = sum_j P_{hi-j} 2^(beta j) (the host chose the groups
+// so that |Q| < 2^63); at the group's most significant diagonal lo, R = 2^(-beta (hi-lo))
+// (Q + 2^-beta R_prev) in FP64.  The last group ends at d = 2 and goes straight to C:
+//     C := alpha 2^(e_i + f_j - 2 beta) R + beta_c C.
+template <int BN, int CR, int CT>
+MOMMS_DEV void recombine_diagonal(const Params& p, int prob, int tm, int tn, int d, const TileInts& pr,
+                                  long long* Q, double* R, uint64_t keep, uint32_t tsum, double rb, int third,
+                                  int rloc, const int* colexp, const uint8_t* colflag, double qnan,
+                                  const int32_t (&acc)[CR], int& gj, bool& rfirst) {
+    constexpr int CW = BN / 3;
+    const bool gfirst = (gj == 0);
+    const bool gend = (pr.group_end >> d) & 1u;
+    const RecombineCtx rc{Q, R, keep, tsum, pr.beta * gj, pow2_normal(-pr.beta * gj), rb, gfirst, rfirst};
+    if (!gend) {
+        recombine<kMid, CR, CT>(rc, acc, nullptr);
+    } else if (d != 2) {
+        recombine<kGroupEnd, CR, CT>(rc, acc, nullptr);
+    } else {
+        const int row = tm * BM + rloc;
+        FinalCtx fc;
+        const Prob& one = p.one;
+        const EmuBatchProblem* bp = prob < 0 ? nullptr : &p.table[prob];
+        const int m_ = bp ? bp->m : one.m;
+        const int n_ = bp ? bp->n : one.n;
+        fc.row_ok = row < m_;
+        fc.ei = fc.row_ok ? (bp ? bp->e : one.e)[row] : 0;
+        fc.eflag = fc.row_ok ? ((bp ? bp->ef : one.ef)[row] != 0) : false;
+        fc.colexp = colexp + third * CW;
+        fc.colflag = colflag + third * CW;
+        fc.ncols = min(CW, n_ - (tn * BN + third * CW));
+        fc.ldc = bp ? bp->ldc : one.ldc;
+        fc.cp = (bp ? bp->C : one.C) + row + static_cast<int64_t>(tn * BN + third * CW) * fc.ldc;
+        fc.alpha = bp ? bp->alpha : one.alpha;
+        fc.beta_c = bp ? bp->beta_c : one.beta_c;
+        fc.qnan = qnan;
+        recombine<kLast, CR, CT>(rc, acc, &fc);
+    }
+    if (gend) {
+        gj = 0;
+        rfirst = false;
+    } else {
+        ++gj;
+    }
+}
+
+// This thread's column c0 of the int32 partial sums of diagonal d of k part `part` of the
+// CTA's tail tile (column stride BM; consecutive lanes hold consecutive rows).
+MOMMS_DEV int32_t* tail_slot(const Params& p, int part, int S, int d, int c0, int rloc) {
+    const int tail = static_cast<int>(blockIdx.x) / p.tail_parts;
+    const size_t blk = (static_cast<size_t>(tail) * p.tail_parts + part) * S + (d - 2);
+    return p.tail_sums + (blk * kEmuBNMax + c0) * BM + rloc;
+}
+
+template <int CR, int CT>
+MOMMS_DEV void store_partial(int32_t* dst, const int32_t (&acc)[CR], uint32_t tsum) {
+#pragma unroll
+    for (int c = 0; c < CR; ++c) __stcg(dst + c * BM, acc[c]);
+#pragma unroll
+    for (int q = 0; q < CT / 16; ++q) {
+        uint32_t t[16];
+        tmem_ld_32x32b_x16(tsum + q * 16, t);
+        tmem_ld_wait(t);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) __stcg(dst + (CR + q * 16 + j) * BM, static_cast<int32_t>(t[j]));
+    }
+}
+
+// The complete int32 sums of diagonal d: the sum over the tile's k parts (integer addition,
+// so the result equals the unsplit sums bit for bit).  First CR columns to `acc`, the other
+// CT to TMEM at `tsum`.
+template <int CR, int CT>
+MOMMS_DEV void sum_partials(const Params& p, int S, int d, int c0, int rloc, int32_t (&acc)[CR], uint32_t tsum) {
+#pragma unroll
+    for (int c = 0; c < CR; ++c) acc[c] = 0;
+    for (int part = 0; part < p.tail_parts; ++part) {
+        const int32_t* src = tail_slot(p, part, S, d, c0, rloc);
+#pragma unroll
+        for (int c = 0; c < CR; ++c) acc[c] += __ldcg(src + c * BM);
+    }
+#pragma unroll
+    for (int q = 0; q < CT / 16; ++q) {
+        uint32_t t[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) t[j] = 0u;
+        for (int part = 0; part < p.tail_parts; ++part) {
+            const int32_t* src = tail_slot(p, part, S, d, c0, rloc) + (CR + q * 16) * BM;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) t[j] += static_cast<uint32_t>(__ldcg(src + j * BM));
+        }
+        tmem_st_32x32b_x16(tsum + q * 16, t);
+    }
+    tmem_st_wait();
+}
+
+// Stages the column exponents (minus 2 beta) and non-finite flags of tile column tn in shared
+// memory, between two barriers of the drain warps (the previous tile's columns are no longer read).
 template <int BN>
+MOMMS_DEV void stage_columns(const Params& p, int prob, int tn, int beta, int* colexp, uint8_t* colflag) {
+    named_bar_sync(1, 32 * EPI_WARPS);
+    for (int c = threadIdx.x - 32 * CTRL_WARPS; c < BN; c += 32 * EPI_WARPS) {
+        const int col = tn * BN + c;
+        const int n_ = prob < 0 ? p.one.n : p.table[prob].n;
+        const int32_t* f_ = prob < 0 ? p.one.f : p.table[prob].f;
+        const uint8_t* ff_ = prob < 0 ? p.one.ff : p.table[prob].ff;
+        colexp[c] = col < n_ ? f_[col] - 2 * beta : 0;
+        colflag[c] = col < n_ ? ff_[col] : 0;
+    }
+    named_bar_sync(1, 32 * EPI_WARPS);
+}
+
+// Drains the accumulator chunks of one diagonal (`units` k slabs, `chunk_slabs` per chunk) into
+// int32 sums: the first CR of the thread's columns in `acc`, the other CT in TMEM at `tsum`.
+// `tacc` is the thread's first accumulator column in buffer 0 (buffer 1 is 256 columns on).
+// Returns false if a bounded wait gave up.
+template <int CR, int CT>
+MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, uint64_t* acc_empty, uint32_t& abuf,
+                              uint32_t (&aphase)[2], volatile int* abort_flag, uint32_t tacc, uint32_t tsum,
+                              int lane, int32_t (&acc)[CR]) {
+#pragma unroll
+    for (int c = 0; c < CR; ++c) acc[c] = 0;
+    bool first = true;
+    for (int u = 0; u < units;) {
+        const int cnt = min(chunk_slabs, units - u);
+        if (!mbar_wait(&acc_full[abuf], aphase[abuf], abort_flag)) return false;
+        tc_fence_after();
+        const uint32_t taddr = tacc + abuf * 256u;
+#pragma unroll
+        for (int q = 0; q < CR / 16; ++q) {
+            uint32_t r[16];
+            tmem_ld_32x32b_x16(taddr + q * 16, r);
+            tmem_ld_wait(r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[q * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
+        }
+#pragma unroll
+        for (int q = 0; q < CT / 16; ++q) {
+            uint32_t r[16];
+            tmem_ld_32x32b_x16(taddr + CR + q * 16, r);
+            tmem_ld_wait(r);
+            uint32_t t[16];
+            if (first) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) t[j] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[j])));
+            } else {
+                tmem_ld_32x32b_x16(tsum + q * 16, t);
+                tmem_ld_wait(t);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    t[j] = static_cast<uint32_t>(static_cast<int32_t>(t[j]) + __float2int_rn(__uint_as_float(r[j])));
+            }
+            tmem_st_32x32b_x16(tsum + q * 16, t);
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[abuf]);
+        aphase[abuf] ^= 1u;
+        abuf ^= 1u;
+        u += cnt;
+        first = false;
+    }
+    return true;
+}
+
+// A drain warp's share of a k part of a split tail tile (always the CTA's last unit): drain
+// every diagonal and store its int32 sums; then, per drain warp (its 32 rows x 64 columns),
+// the warp of the last part to finish adds up all parts -- exact integer sums, so the result
+// equals the unsplit tile's bit for bit -- and recombines.  The warps count on their own (no
+// CTA-wide barrier).
+template <int BN>
+MOMMS_DEV void drain_tail_unit(const Params& p, int tm, int tn, int part, uint64_t* acc_full,
+                                             uint64_t* acc_empty, uint32_t abuf, uint32_t ph0, uint32_t ph1,
+                                             volatile int* abort_flag, uint32_t tacc, uint32_t tsum, int warp,
+                                             int lane, int third, int rloc, long long* Q, double* R,
+                                             uint64_t keep, int* colexp, uint8_t* colflag) {
+    using C_ = Cfg<BN>;
+    constexpr int CR = C_::CR, CT = C_::CT, CW = C_::CW;
+    const TileInts pr = tile_ints(p, -1, part);
+    uint32_t aphase[2] = {ph0, ph1};
+    stage_columns<BN>(p, -1, tn, pr.beta, colexp, colflag);
+    for (int d = pr.S + 1; d >= 2; --d) {
+        int32_t acc[CR];
+        if (!drain_diagonal<CR, CT>((d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty, abuf, aphase,
+                                    abort_flag, tacc, tsum, lane, acc))
+            return;
+        store_partial<CR, CT>(tail_slot(p, part, pr.S, d, third * CW, rloc), acc, tsum);
+    }
+    __threadfence();
+    __syncwarp();
+    const int slot = static_cast<int>(blockIdx.x) / p.tail_parts * EPI_WARPS + (warp - CTRL_WARPS);
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&p.tail_count[slot], 1) == p.tail_parts - 1;
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
+    __threadfence();
+    const double rb = pow2_normal(-pr.beta);
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    int gj = 0;
+    bool rfirst = true;
+    for (int d = pr.S + 1; d >= 2; --d) {
+        int32_t acc[CR];
+        sum_partials<CR, CT>(p, pr.S, d, third * CW, rloc, acc, tsum);
+        recombine_diagonal<BN, CR, CT>(p, -1, tm, tn, d, pr, Q, R, keep, tsum, rb, third, rloc, colexp, colflag,
+                                       qnan, acc, gj, rfirst);
+    }
+}
+
+template <int BN, bool TAIL>
 __global__ void __launch_bounds__(THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                      const __grid_constant__ CUtensorMap tmB, const Params p) {
+                      const __grid_constant__ CUtensorMap tmB, const __grid_constant__ Params p) {
     using C_ = Cfg<BN>;
     constexpr int STAGES = C_::STAGES;
     constexpr uint32_t STAGE = C_::STAGE;
@@ -297,9 +534,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int i = 0; i < STAGES; ++i) last_phase[i] = -1;
             bool ok = true;
             for (int it = 0; ok; ++it) {
-                int tm, tn, prob;
-                if (!tile_of(p, it, &prob, &tm, &tn)) break;
-                const TileInts pr = tile_ints(p, prob);
+                int tm, tn, prob, part;
+                if (!tile_of<TAIL>(p, it, &prob, &tm, &tn, &part)) break;
+                const TileInts pr = tile_ints(p, prob, part);
                 const CUtensorMap* mapA = prob < 0 ? &tmA : &p.table[prob].mapA;
                 const CUtensorMap* mapB = prob < 0 ? &tmB : &p.table[prob].mapB;
                 for (int d = pr.S + 1; d >= 2 && ok; --d) {
@@ -340,9 +577,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool ok = true;
             bool issued = false;
             for (int it = 0; ok; ++it) {
-                int tm, tn, prob;
-                if (!tile_of(p, it, &prob, &tm, &tn)) break;
-                const TileInts pr = tile_ints(p, prob);
+                int tm, tn, prob, part;
+                if (!tile_of<TAIL>(p, it, &prob, &tm, &tn, &part)) break;
+                const TileInts pr = tile_ints(p, prob, part);
                 for (int d = pr.S + 1; d >= 2 && ok; --d) {
                     const int units = (d - 1) * pr.nslab;
                     for (int u = 0; u < units && ok;) {
@@ -404,113 +641,32 @@ __global__ void __launch_bounds__(THREADS, 1)
         long long* Q = p.qscratch + (static_cast<size_t>(blockIdx.x) * BN + third * CW) * BM + rloc;
         double* R = p.scratch + (static_cast<size_t>(blockIdx.x) * BN + third * CW) * BM + rloc;
         const uint64_t keep = l2_policy_evict_last();
-        bool ok = true;
-        for (int it = 0; ok; ++it) {
-            int tm, tn, prob;
-            if (!tile_of(p, it, &prob, &tm, &tn)) break;
-            const TileInts pr = tile_ints(p, prob);
-            const double rb = pow2_normal(-pr.beta);
-            int gj = 0;           // position of the current diagonal inside its int64 group
-            bool rfirst = true;   // no FP64 partial R yet for this tile
-            // stage the column exponents (minus 2 beta) and flags of this tile in shared memory
-            named_bar_sync(1, 32 * EPI_WARPS);  // the previous tile's columns are no longer read
-            for (int c = threadIdx.x - 32 * CTRL_WARPS; c < BN; c += 32 * EPI_WARPS) {
-                const int col = tn * BN + c;
-                const int n_ = prob < 0 ? p.one.n : p.table[prob].n;
-                const int32_t* f_ = prob < 0 ? p.one.f : p.table[prob].f;
-                const uint8_t* ff_ = prob < 0 ? p.one.ff : p.table[prob].ff;
-                colexp[c] = col < n_ ? f_[col] - 2 * pr.beta : 0;
-                colflag[c] = col < n_ ? ff_[col] : 0;
-            }
-            named_bar_sync(1, 32 * EPI_WARPS);
-            for (int d = pr.S + 1; d >= 2 && ok; --d) {
-                int32_t acc[CR];
-#pragma unroll
-                for (int c = 0; c < CR; ++c) acc[c] = 0;
-                const int units = (d - 1) * pr.nslab;
-                bool first = true;
-                for (int u = 0; u < units;) {
-                    const int cnt = min(pr.chunk_slabs, units - u);
-                    if (!mbar_wait(&acc_full[abuf], aphase[abuf], abort_flag)) {
+        if constexpr (TAIL) {
+            int tm, tn, prob, part;
+            if (tile_of<true>(p, 0, &prob, &tm, &tn, &part))
+                drain_tail_unit<BN>(p, tm, tn, part, acc_full, acc_empty, abuf, aphase[0], aphase[1], abort_flag,
+                                    tmem_base + lane_off + third * CW, tsum, warp, lane, third, rloc, Q, R, keep,
+                                    colexp, colflag);
+        } else {
+            bool ok = true;
+            for (int it = 0; ok; ++it) {
+                int tm, tn, prob, part;
+                if (!tile_of<false>(p, it, &prob, &tm, &tn, &part)) break;
+                const TileInts pr = tile_ints(p, prob, -1);
+                const double rb = pow2_normal(-pr.beta);
+                int gj = 0;           // position of the current diagonal inside its int64 group
+                bool rfirst = true;   // no FP64 partial R yet for this tile
+                stage_columns<BN>(p, prob, tn, pr.beta, colexp, colflag);
+                for (int d = pr.S + 1; d >= 2; --d) {
+                    int32_t acc[CR];
+                    if (!drain_diagonal<CR, CT>((d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty, abuf,
+                                                aphase, abort_flag, tmem_base + lane_off + third * CW, tsum, lane,
+                                                acc)) {
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
-                    const uint32_t taddr = tmem_base + lane_off + abuf * 256u + third * CW;
-#pragma unroll
-                    for (int q = 0; q < CR / 16; ++q) {
-                        uint32_t r[16];
-                        tmem_ld_32x32b_x16(taddr + q * 16, r);
-                        tmem_ld_wait(r);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) acc[q * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
-                    }
-#pragma unroll
-                    for (int q = 0; q < CT / 16; ++q) {
-                        uint32_t r[16];
-                        tmem_ld_32x32b_x16(taddr + CR + q * 16, r);
-                        tmem_ld_wait(r);
-                        uint32_t t[16];
-                        if (first) {
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) t[j] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[j])));
-                        } else {
-                            tmem_ld_32x32b_x16(tsum + q * 16, t);
-                            tmem_ld_wait(t);
-#pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                t[j] = static_cast<uint32_t>(static_cast<int32_t>(t[j]) + __float2int_rn(__uint_as_float(r[j])));
-                        }
-                        tmem_st_32x32b_x16(tsum + q * 16, t);
-                    }
-                    tmem_st_wait();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&acc_empty[abuf]);
-                    aphase[abuf] ^= 1u;
-                    abuf ^= 1u;
-                    u += cnt;
-                    first = false;
-                }
-                if (!ok) break;
-                // Recombination, least significant diagonal first.  Inside a group the
-                // diagonal sums are combined exactly in int64, Q = sum_j P_{hi-j} 2^(beta j)
-                // (the host chose the groups so that |Q| < 2^63); at the group's most
-                // significant diagonal lo, R = 2^(-beta (hi-lo)) (Q + 2^-beta R_prev) in FP64.
-                // The last group ends at d = 2 and goes straight to C:
-                //     C := alpha 2^(e_i + f_j - 2 beta) R + beta_c C.
-                const bool gfirst = (gj == 0);
-                const bool gend = (pr.group_end >> d) & 1u;
-                const RecombineCtx rc{Q, R, keep, tsum, pr.beta * gj, pow2_normal(-pr.beta * gj), rb, gfirst, rfirst};
-                if (!gend) {
-                    recombine<kMid, CR, CT>(rc, acc, nullptr);
-                } else if (d != 2) {
-                    recombine<kGroupEnd, CR, CT>(rc, acc, nullptr);
-                } else {
-                    const int row = tm * BM + rloc;
-                    FinalCtx fc;
-                    const Prob& one = p.one;
-                    const EmuBatchProblem* bp = prob < 0 ? nullptr : &p.table[prob];
-                    const int m_ = bp ? bp->m : one.m;
-                    const int n_ = bp ? bp->n : one.n;
-                    fc.row_ok = row < m_;
-                    fc.ei = fc.row_ok ? (bp ? bp->e : one.e)[row] : 0;
-                    fc.eflag = fc.row_ok ? ((bp ? bp->ef : one.ef)[row] != 0) : false;
-                    fc.colexp = colexp + third * CW;
-                    fc.colflag = colflag + third * CW;
-                    fc.ncols = min(CW, n_ - (tn * BN + third * CW));
-                    fc.ldc = bp ? bp->ldc : one.ldc;
-                    fc.cp = (bp ? bp->C : one.C) + row + static_cast<int64_t>(tn * BN + third * CW) * fc.ldc;
-                    fc.alpha = bp ? bp->alpha : one.alpha;
-                    fc.beta_c = bp ? bp->beta_c : one.beta_c;
-                    fc.qnan = qnan;
-                    recombine<kLast, CR, CT>(rc, acc, &fc);
-                }
-                if (gend) {
-                    gj = 0;
-                    rfirst = false;
-                } else {
-                    ++gj;
+                    recombine_diagonal<BN, CR, CT>(p, prob, tm, tn, d, pr, Q, R, keep, tsum, rb, third, rloc,
+                                                   colexp, colflag, qnan, acc, gj, rfirst);
                 }
             }
         }
@@ -563,6 +719,32 @@ bool emu_make_digit_map(CUtensorMap* map, const void* base, int64_t k_pad, int64
 
 namespace emu {
 
+// Tail split of a single-problem launch.  With a round-robin member the last round holds only
+// tiles % ctas tiles; cutting each into `parts` k ranges (parts = ctas / that count, at most the
+// slabs of the shortest pass) lets parts x as many CTAs share that round.
+struct TailPlan {
+    int full_rounds = 0, tiles = 0, parts = 0;
+    size_t sums_bytes = 0, count_bytes = 0;
+};
+static size_t align256_(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+static TailPlan tail_plan(int64_t tiles, int64_t ctas, int64_t kslabs, int64_t pass_slabs, int S, int member) {
+    TailPlan t;
+    if (member == kMemberA1 || ctas <= 1 || kslabs <= 0 || pass_slabs <= 0) return t;
+    const int64_t r = tiles % ctas;
+    if (r == 0) return t;
+    const int64_t last_pass = kslabs - (kslabs - 1) / pass_slabs * pass_slabs;  // slabs of the shortest pass
+    int64_t parts = ctas / r;
+    if (parts > last_pass) parts = last_pass;
+    if (parts < 2) return t;
+    t.full_rounds = static_cast<int>(tiles / ctas);
+    t.tiles = static_cast<int>(r);
+    t.parts = static_cast<int>(parts);
+    t.sums_bytes = align256_(static_cast<size_t>(r) * parts * S * kEmuBNMax * BM * sizeof(int32_t));
+    t.count_bytes = align256_(static_cast<size_t>(r) * EPI_WARPS * sizeof(int));
+    return t;
+}
+
 template <int BN>
 static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t stream) {
     using C_ = Cfg<BN>;
@@ -581,15 +763,23 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
 
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(C_::SMEM_BYTES));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(slice_gemm_kernel<BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(C_::SMEM_BYTES));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int64_t kslabs = (a.k + BK - 1) / BK;
     const int64_t pass_slabs = emu_max_k_per_pass(a.S, a.beta) / BK;
     if (kslabs <= 0 || pass_slabs <= 0) return cudaErrorInvalidValue;
-    int npass = 0;
+    const int member = a.member == kMemberAuto ? kMemberC2 : a.member;
+    TailPlan tp = tail_plan(tiles, ctas, kslabs, pass_slabs, a.S, member);
+    if (tp.parts && a.scratch_bytes < 2 * half + tp.sums_bytes + tp.count_bytes) tp = TailPlan{};  // whole tiles
+    char* tail_base = static_cast<char*>(a.scratch) + 2 * half;
+    int npass = 0, nlaunch = 0;
     for (int64_t s0 = 0; s0 < kslabs; s0 += pass_slabs) {
         Params p{};
         p.one.m = static_cast<int>(a.m);
@@ -610,20 +800,41 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         p.one.ldc = a.ldc;
         p.tiles_m = static_cast<int>(tiles_m);
         p.tiles_n = static_cast<int>(tiles_n);
-        p.member = a.member == kMemberAuto ? kMemberC2 : a.member;
+        p.member = member;
         p.group = a.group > 0 ? a.group : emu_default_group(ctas, static_cast<int>(tiles_m), static_cast<int>(tiles_n));
+        if (tp.parts) {
+            p.full_rounds = tp.full_rounds;
+            p.main_ctas = static_cast<int>(ctas);
+            p.tail_tiles = tp.tiles;
+            p.tail_parts = tp.parts;
+            p.tail_sums = reinterpret_cast<int32_t*>(tail_base);
+            p.tail_count = reinterpret_cast<int*>(tail_base + tp.sums_bytes);
+        }
         if (a.used_ctas) *a.used_ctas = static_cast<int>(ctas);
         if (a.used_group) *a.used_group = p.group;
         p.table = nullptr;
         p.qscratch = static_cast<long long*>(a.scratch);
         p.scratch = reinterpret_cast<double*>(static_cast<char*>(a.scratch) + half);
         p.status = a.status;
-        slice_gemm_kernel<BN><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(mapA, mapB, p);
+        // main launch: the whole rounds (all tiles without a tail split)
+        slice_gemm_kernel<BN, false><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(mapA, mapB, p);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        ++nlaunch;
+        if (tp.parts) {
+            // tail launch: one CTA per k part of every tile of the last, partial round
+            e = cudaMemsetAsync(p.tail_count, 0, tp.count_bytes, stream);
+            if (e != cudaSuccess) return e;
+            slice_gemm_kernel<BN, true><<<static_cast<unsigned>(tp.tiles * tp.parts), THREADS, C_::SMEM_BYTES,
+                                          stream>>>(mapA, mapB, p);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            ++nlaunch;
+        }
         ++npass;
     }
     if (passes) *passes = npass;
+    if (a.used_launches) *a.used_launches = nlaunch;
     return cudaSuccess;
 }
 
@@ -637,7 +848,8 @@ static cudaError_t launch_bn_batched(const EmuBatchProblem* table, int count, in
     if (scratch_bytes < 2 * half) return cudaErrorInvalidValue;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(C_::SMEM_BYTES));
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -650,7 +862,7 @@ static cudaError_t launch_bn_batched(const EmuBatchProblem* table, int count, in
     p.scratch = reinterpret_cast<double*>(static_cast<char*>(scratch) + half);
     p.status = status;
     CUtensorMap unused{};  // the batch reads each problem's maps from the table
-    slice_gemm_kernel<BN><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(unused, unused, p);
+    slice_gemm_kernel<BN, false><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(unused, unused, p);
     return cudaGetLastError();
 }
 
@@ -675,6 +887,19 @@ int device_sm_count() {
 }
 
 size_t emu_scratch_bytes(int num_sms) { return emu_scratch_bytes_for_ctas(num_sms); }
+
+size_t emu_scratch_bytes_tail(int64_t m, int64_t n, int64_t k, int S, int max_ctas, int beta) {
+    const int sms = device_sm_count();
+    const int64_t tiles = ((m + emu::BM - 1) / emu::BM) * ((n + kEmuBNMax - 1) / kEmuBNMax);
+    int64_t ctas = max_ctas > 0 && max_ctas < sms ? max_ctas : sms;
+    if (ctas > tiles) ctas = tiles;
+    if (ctas < 1) ctas = 1;
+    const size_t base = emu_scratch_bytes_for_ctas(static_cast<int>(ctas));
+    const int64_t kslabs = (k + emu::BK - 1) / emu::BK;
+    const int64_t pass_slabs = emu_max_k_per_pass(S, beta) / emu::BK;
+    const emu::TailPlan tp = emu::tail_plan(tiles, ctas, kslabs, pass_slabs, S, kMemberC2);
+    return base + tp.sums_bytes + tp.count_bytes;
+}
 
 size_t emu_scratch_bytes_for_ctas(int ctas) {
     // FP64 partial sums R and int64 group sums Q, one 128 x 192 block each per CTA

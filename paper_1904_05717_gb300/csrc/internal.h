@@ -71,6 +71,7 @@ struct EmuGemmArgs {
     int tile_n;    // CTA tile width request (only 192 is built; 0 = automatic)
     int* used_ctas;   // optional out: persistent CTAs launched
     int* used_group;  // optional out: C2 raster group used
+    int* used_launches;  // optional out: kernels launched (a tail launch per pass when split)
 };
 constexpr int kEmuBM = 128, kEmuBK = 64, kEmuBNMax = 192;
 
@@ -130,6 +131,9 @@ int emu_default_group(int64_t ctas, int tiles_m, int tiles_n);
 // Launches the slice-product kernel once per k pass; *passes receives the count.
 cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_t stream);
 size_t emu_scratch_bytes(int num_sms);
+// Scratch for one single-problem launch including the tail split's partial sums (the launch
+// falls back to whole tiles when it is given only emu_scratch_bytes).
+size_t emu_scratch_bytes_tail(int64_t m, int64_t n, int64_t k, int S, int max_ctas, int beta);
 size_t emu_scratch_bytes_for_ctas(int ctas);
 // Bit d set: diagonal d is the most significant of an exact int64 group (S, beta, k per pass).
 uint32_t emu_group_ends(int S, int beta, int64_t k_pass);

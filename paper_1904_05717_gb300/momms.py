@@ -76,6 +76,7 @@ _SIGS = {
     "momms_emu_slice_gemm": ([_I64, _I64, _I64, _I32, _I32, _VP, _VP, _I64, _I64, _I64, _VP, _VP, _VP, _VP,
                               _DBL, _DBL, _VP, _I64, _I32, _VP, _SZ, _VP, _VP], _I32),
     "momms_emu_scratch_bytes": ([], _SZ),
+    "momms_emu_scratch_bytes_for": ([_I64, _I64, _I64, _I32], _SZ),
     "momms_tune": ([_VP, ctypes.c_char_p, _I64, _VP, _VP, _VP, _VP], _I32),
     "momms_load_plans": ([_VP, ctypes.c_char_p], _I32),
     "momms_probe_peak": ([_I32, ctypes.POINTER(_DBL), _VP], _I32),
@@ -183,6 +184,10 @@ def momms_emu_slice_gemm(m, n, k, slices, digit_bits, Ad, Bd, m_pad, n_pad, k_pa
 
 def momms_emu_scratch_bytes():
     return int(lib().momms_emu_scratch_bytes())
+
+
+def momms_emu_scratch_bytes_for(m, n, k, slices):
+    return int(lib().momms_emu_scratch_bytes_for(m, n, k, slices))
 
 
 def momms_gemm_emulated_noalloc(op_a, op_b, m, n, k, slices, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):

@@ -256,3 +256,64 @@ def test_slice_gemm_entry_point_and_k_passes():
     torch.cuda.synchronize()
     assert int(status.item()) == 0
     assert np.array_equal(dC.to_numpy(), C)
+
+
+def _slice_products(torch, A, B, S, nbytes):
+    """Scale, split and one slice-product call through the step entry points, with `nbytes`
+    of recombination scratch; returns C (beta = 0) and the device status word."""
+    m, k = A.shape
+    n = B.shape[1]
+    k_pad = -(-k // 64) * 64
+    dA = M.DeviceMatrix.from_numpy(A)
+    dB = M.DeviceMatrix.from_numpy(B)
+    e = torch.empty(m, dtype=torch.int32, device="cuda"); ef = torch.empty(m, dtype=torch.uint8, device="cuda")
+    f = torch.empty(n, dtype=torch.int32, device="cuda"); ff = torch.empty(n, dtype=torch.uint8, device="cuda")
+    M.check(M.momms_emu_scale(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr()), "scale A")
+    M.check(M.momms_emu_scale(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr()), "scale B")
+    Ad = torch.empty((S, m, k_pad), dtype=torch.float16, device="cuda")
+    Bd = torch.empty((S, n, k_pad), dtype=torch.float16, device="cuda")
+    M.check(M.momms_emu_split(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), S, BETA, Ad.data_ptr(), m, k_pad),
+            "split A")
+    M.check(M.momms_emu_split(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), S, BETA, Bd.data_ptr(), n, k_pad),
+            "split B")
+    scratch = torch.full((nbytes // 8,), 7.0, dtype=torch.float64, device="cuda")  # not zero on purpose
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dC = M.DeviceMatrix(m, n)
+    M.check(M.momms_emu_slice_gemm(m, n, k, S, BETA, Ad.data_ptr(), Bd.data_ptr(), m, n, k_pad, e.data_ptr(),
+                                   ef.data_ptr(), f.data_ptr(), ff.data_ptr(), 1.0, 0.0, dC.ptr, dC.ld, M.MEMBER_C2,
+                                   scratch.data_ptr(), nbytes, status.data_ptr()), "slice gemm")
+    torch.cuda.synchronize()
+    return dC.to_numpy(), int(status.item())
+
+
+@pytest.mark.parametrize("m,n,k,S", [
+    (1280, 3072, 1500, 6),    # 10 x 16 = 160 tiles: 8 left over for 152 CTAs, 19 k parts each
+    (1300, 3000, 700, 9),     # 11 x 16 = 176 tiles: 24 left over, 6 parts each, ragged edges
+    (1280, 3072, 8448, 16),   # two k passes (the second of 2 slabs: 2 parts), S = 16
+])
+def test_tail_split_bitwise_identical_to_whole_tiles(m, n, k, S):
+    # Given the larger scratch, the slice-product call cuts the tiles of its last, partial round
+    # of CTAs along k; the parts' int32 sums add up exactly, so C must not change by one bit.
+    torch = torch_mod()
+    A = syn.matrix("uniform", m, k, 5000 + m)
+    B = syn.matrix("uniform", k, n, 6000 + n)
+    base, big = M.momms_emu_scratch_bytes(), M.momms_emu_scratch_bytes_for(m, n, k, S)
+    assert big > base  # the tail split is on for these shapes on a 152-SM GB300
+    whole, st0 = _slice_products(torch, A, B, S, base)
+    split, st1 = _slice_products(torch, A, B, S, big)
+    assert st0 == 0 and st1 == 0
+    assert np.array_equal(split, whole)
+    rows = np.array([0, 1, m // 2, m - 1])
+    Cref, N = reference(F(A[rows, :]), B)
+    assert max_ratio(split[rows, :], Cref, k, 1.0, 0.0, N) <= 1.0
+    # every tile of the split round in full: the last tiles % ctas tiles of the C2 order
+    from paper_1904_05717_gb300 import iomodel as I
+    ctas = torch.cuda.get_device_properties(0).multi_processor_count
+    tiles_m, tiles_n = -(-m // 128), -(-n // 192)
+    total = tiles_m * tiles_n
+    for t in range(total // ctas * ctas, total):
+        tm, tn = I.member_tile(M.MEMBER_C2, 0, t % ctas, ctas, t // ctas, tiles_m, tiles_n)
+        r = np.arange(tm * 128, min(m, tm * 128 + 128))
+        c = np.arange(tn * 192, min(n, tn * 192 + 192))
+        Cref, N = reference(F(A[r, :]), F(B[:, c]))
+        assert max_ratio(split[np.ix_(r, c)], Cref, k, 1.0, 0.0, N) <= 1.0
