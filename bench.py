@@ -49,8 +49,10 @@ def parse():
     p.add_argument("--steps", type=int, default=60)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--size", type=int, default=8192)
-    p.add_argument("--shape", default="square", choices=["square", "rankk", "panel"],
-                   help="square: m=n=k=size; rankk: m=n=2*size, k=256; panel: m=k=2*size, n=256")
+    p.add_argument("--shape", default="square", choices=["square", "rankk", "panel", "backward", "batched"],
+                   help="square: m=n=k=size; rankk: m=n=2*size, k=256; panel: m=k=2*size, n=256; "
+                        "backward: dA = dC B^T and dB = A^T dC for A 4096x2048, B 2048x4096; "
+                        "batched: 2000 problems, m, n, k log-uniform in [32, 2048]")
     p.add_argument("--mode", default="auto", choices=["auto", "native", "emulated"])
     p.add_argument("--member", default="auto", choices=["auto", "C2", "A2", "B2", "A1"])
     p.add_argument("--slices", type=int, default=0, help="emulated slice count (0 = from the data)")
@@ -74,7 +76,7 @@ def shape_of(args):
 
 def workload_name(args):
     m, n, k = shape_of(args)
-    kind = {"square": "square", "rankk": "rank-k", "panel": "panel-panel"}[args.shape]
+    kind = {"square": "square", "rankk": "rank-k", "panel": "panel-panel"}.get(args.shape, args.shape)
     return (f"{kind} FP64 GEMM C := A*B + C, m={m} n={n} k={k}, column-major (ld = rows), "
             f"A, B, C uniform[-1,1] (seeded SplitMix64)")
 
@@ -260,10 +262,85 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def run_side_workload(args):
+    """The backward and batched workloads: one step = one momms_gemm_backward (both
+    products) or one momms_gemm_batched call on device-resident inputs, CUDA-event timed."""
+    import torch
+
+    from paper_1904_05717_gb300 import momms as M
+    from paper_1904_05717_gb300 import synthetic as syn
+
+    M.lib(build_if_missing=True)
+    stream = torch.cuda.current_stream()
+    mode = {"auto": M.MODE_AUTO, "native": M.MODE_NATIVE, "emulated": M.MODE_EMULATED}[args.mode]
+    h = M.Handle(mode=mode, slices=args.slices)
+    keep = []
+    if args.shape == "backward":
+        m, k, n = 4096, 2048, 4096
+        A = M.DeviceMatrix.from_numpy(syn.matrix("normal", m, k, syn.workload_seed(2, "A")))
+        B = M.DeviceMatrix.from_numpy(syn.matrix("normal", k, n, syn.workload_seed(2, "B")))
+        G = M.DeviceMatrix.from_numpy(syn.matrix("normal", m, n, syn.workload_seed(2, "dC")))
+        gA, gB = M.DeviceMatrix(m, k), M.DeviceMatrix(k, n)
+        flops = 2 * 2.0 * m * n * k
+        workload = ("backward of C = A B: dA = dC B^T (4096x2048) and dB = A^T dC (2048x4096), A 4096x2048, "
+                    "B 2048x4096, dC 4096x4096, N(0,1) (seeded SplitMix64)")
+
+        def step():
+            M.check(M.momms_gemm_backward(h, m, n, k, A.ptr, A.ld, B.ptr, B.ld, G.ptr, G.ld, gA.ptr, gA.ld, gB.ptr,
+                                          gB.ld, stream), "momms_gemm_backward")
+    else:
+        count = 2000
+        sizes = syn.log_uniform_sizes(syn.workload_seed(4, "A"), count, 32, 2048)
+        mats = []
+        for i, (m_, n_, k_) in enumerate(sizes):
+            m_, n_, k_ = int(m_), int(n_), int(k_)
+            mats.append((M.DeviceMatrix.from_numpy(syn.matrix("uniform", m_, k_, 100000 + 3 * i)),
+                         M.DeviceMatrix.from_numpy(syn.matrix("uniform", k_, n_, 100001 + 3 * i)),
+                         M.DeviceMatrix.from_numpy(syn.matrix("uniform", m_, n_, 100002 + 3 * i))))
+        keep.append(mats)
+        ms_, ns_, ks_ = ([int(s_[j]) for s_ in sizes] for j in range(3))
+        flops = sum(2.0 * a * b * c for a, b, c in zip(ms_, ns_, ks_))
+        args_ = dict(m=ms_, n=ns_, k=ks_, alpha=[1.0] * count, A=[t[0].ptr for t in mats], lda=[t[0].ld for t in mats],
+                     B=[t[1].ptr for t in mats], ldb=[t[1].ld for t in mats], beta=[1.0] * count,
+                     C=[t[2].ptr for t in mats], ldc=[t[2].ld for t in mats])
+        workload = ("batched C := A B + C, 2000 problems, m, n, k i.i.d. log-uniform in [32, 2048], "
+                    "uniform[-1,1] (seeded SplitMix64)")
+
+        def step():
+            M.check(M.momms_gemm_batched(h, stream=stream, **args_), "momms_gemm_batched")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    rep = h.report()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload, "mode": args.mode,
+                       "path": "emulated" if rep["mode"] == M.MODE_EMULATED else "native",
+                       "slices_last_call": int(rep["slices"])},
+            "roofline": None, "e2e": None, "gpu_launches": int(rep["launches"]) * args.steps,
+            "clocks": clk.summary(), "device_status": h.device_status(stream), "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.shape in ("backward", "batched"):
+        return run_side_workload(args)
     import torch
 
     world, rank, local = dist_setup(args)

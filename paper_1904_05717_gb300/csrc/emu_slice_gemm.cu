@@ -314,50 +314,70 @@ MOMMS_DEV void recombine_diagonal(const Params& p, int prob, int tm, int tn, int
     }
 }
 
-// This thread's column c0 of the int32 partial sums of diagonal d of k part `part` of the
-// CTA's tail tile (column stride BM; consecutive lanes hold consecutive rows).
-MOMMS_DEV int32_t* tail_slot(const Params& p, int part, int S, int d, int c0, int rloc) {
-    const int tail = static_cast<int>(blockIdx.x) / p.tail_parts;
+// The int32 partial sums of diagonal d of k part `part` of a tail tile: a 192 x 128 block
+// stored as [column / 4][row][4], so that a thread's four consecutive columns are one 16-byte
+// word and a warp's 32 rows one contiguous 512-byte segment.  Returns this thread's first
+// word (columns c0 .. c0 + 3, row rloc); the next four columns are 128 words on.
+MOMMS_DEV int4* tail_slot(const Params& p, int tail, int part, int S, int d, int c0, int rloc) {
     const size_t blk = (static_cast<size_t>(tail) * p.tail_parts + part) * S + (d - 2);
-    return p.tail_sums + (blk * kEmuBNMax + c0) * BM + rloc;
+    return reinterpret_cast<int4*>(p.tail_sums) + (blk * kEmuBNMax + c0) / 4 * BM + rloc;
 }
 
 template <int CR, int CT>
-MOMMS_DEV void store_partial(int32_t* dst, const int32_t (&acc)[CR], uint32_t tsum) {
+MOMMS_DEV void store_partial(int4* dst, const int32_t (&acc)[CR], uint32_t tsum) {
 #pragma unroll
-    for (int c = 0; c < CR; ++c) __stcg(dst + c * BM, acc[c]);
+    for (int c = 0; c < CR; c += 4) __stcg(dst + c / 4 * BM, make_int4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]));
 #pragma unroll
     for (int q = 0; q < CT / 16; ++q) {
         uint32_t t[16];
         tmem_ld_32x32b_x16(tsum + q * 16, t);
         tmem_ld_wait(t);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) __stcg(dst + (CR + q * 16 + j) * BM, static_cast<int32_t>(t[j]));
+        for (int j = 0; j < 16; j += 4)
+            __stcg(dst + (CR + q * 16 + j) / 4 * BM, make_int4(static_cast<int>(t[j]), static_cast<int>(t[j + 1]),
+                                                               static_cast<int>(t[j + 2]), static_cast<int>(t[j + 3])));
     }
 }
 
-// The complete int32 sums of diagonal d: the sum over the tile's k parts (integer addition,
-// so the result equals the unsplit sums bit for bit).  First CR columns to `acc`, the other
-// CT to TMEM at `tsum`.
+// Sixteen columns [c, c + 16) of the complete int32 sums: the sum over the tile's k parts, four
+// parts' words in flight at a time.
+MOMMS_DEV void sum_partials16(const Params& p, int tail, int S, int d, int c0, int c, int rloc, int32_t (&v)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = 0;
+    const int parts = p.tail_parts;
+#pragma unroll 4
+    for (int part = 0; part < parts; ++part) {
+        const int4* src = tail_slot(p, tail, part, S, d, c0, rloc) + c / 4 * BM;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int4 x = __ldcg(src + w * BM);
+            v[4 * w] += x.x;
+            v[4 * w + 1] += x.y;
+            v[4 * w + 2] += x.z;
+            v[4 * w + 3] += x.w;
+        }
+    }
+}
+
+// The complete int32 sums of diagonal d (integer addition over the parts, so they equal the
+// unsplit sums bit for bit): the first CR columns to `acc`, the other CT to TMEM at `tsum`.
 template <int CR, int CT>
-MOMMS_DEV void sum_partials(const Params& p, int S, int d, int c0, int rloc, int32_t (&acc)[CR], uint32_t tsum) {
+MOMMS_DEV void sum_partials(const Params& p, int tail, int S, int d, int c0, int rloc, int32_t (&acc)[CR],
+                            uint32_t tsum) {
 #pragma unroll
-    for (int c = 0; c < CR; ++c) acc[c] = 0;
-    for (int part = 0; part < p.tail_parts; ++part) {
-        const int32_t* src = tail_slot(p, part, S, d, c0, rloc);
+    for (int c = 0; c < CR; c += 16) {
+        int32_t v[16];
+        sum_partials16(p, tail, S, d, c0, c, rloc, v);
 #pragma unroll
-        for (int c = 0; c < CR; ++c) acc[c] += __ldcg(src + c * BM);
+        for (int j = 0; j < 16; ++j) acc[c + j] = v[j];
     }
 #pragma unroll
     for (int q = 0; q < CT / 16; ++q) {
+        int32_t v[16];
+        sum_partials16(p, tail, S, d, c0, CR + q * 16, rloc, v);
         uint32_t t[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) t[j] = 0u;
-        for (int part = 0; part < p.tail_parts; ++part) {
-            const int32_t* src = tail_slot(p, part, S, d, c0, rloc) + (CR + q * 16) * BM;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) t[j] += static_cast<uint32_t>(__ldcg(src + j * BM));
-        }
+        for (int j = 0; j < 16; ++j) t[j] = static_cast<uint32_t>(v[j]);
         tmem_st_32x32b_x16(tsum + q * 16, t);
     }
     tmem_st_wait();
@@ -447,6 +467,7 @@ MOMMS_DEV void drain_tail_unit(const Params& p, int tm, int tn, int part, uint64
     using C_ = Cfg<BN>;
     constexpr int CR = C_::CR, CT = C_::CT, CW = C_::CW;
     const TileInts pr = tile_ints(p, -1, part);
+    const int tail = static_cast<int>(blockIdx.x) / p.tail_parts;
     uint32_t aphase[2] = {ph0, ph1};
     stage_columns<BN>(p, -1, tn, pr.beta, colexp, colflag);
     for (int d = pr.S + 1; d >= 2; --d) {
@@ -454,11 +475,11 @@ MOMMS_DEV void drain_tail_unit(const Params& p, int tm, int tn, int part, uint64
         if (!drain_diagonal<CR, CT>((d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty, abuf, aphase,
                                     abort_flag, tacc, tsum, lane, acc))
             return;
-        store_partial<CR, CT>(tail_slot(p, part, pr.S, d, third * CW, rloc), acc, tsum);
+        store_partial<CR, CT>(tail_slot(p, tail, part, pr.S, d, third * CW, rloc), acc, tsum);
     }
     __threadfence();
     __syncwarp();
-    const int slot = static_cast<int>(blockIdx.x) / p.tail_parts * EPI_WARPS + (warp - CTRL_WARPS);
+    const int slot = tail * EPI_WARPS + (warp - CTRL_WARPS);
     int last = 0;
     if (lane == 0) last = atomicAdd(&p.tail_count[slot], 1) == p.tail_parts - 1;
     if (!__shfl_sync(0xffffffffu, last, 0)) return;
@@ -469,7 +490,7 @@ MOMMS_DEV void drain_tail_unit(const Params& p, int tm, int tn, int part, uint64
     bool rfirst = true;
     for (int d = pr.S + 1; d >= 2; --d) {
         int32_t acc[CR];
-        sum_partials<CR, CT>(p, pr.S, d, third * CW, rloc, acc, tsum);
+        sum_partials<CR, CT>(p, tail, pr.S, d, third * CW, rloc, acc, tsum);
         recombine_diagonal<BN, CR, CT>(p, -1, tm, tn, d, pr, Q, R, keep, tsum, rb, third, rloc, colexp, colflag,
                                        qnan, acc, gj, rfirst);
     }
@@ -643,10 +664,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint64_t keep = l2_policy_evict_last();
         if constexpr (TAIL) {
             int tm, tn, prob, part;
-            if (tile_of<true>(p, 0, &prob, &tm, &tn, &part))
+            if (tile_of<true>(p, 0, &prob, &tm, &tn, &part)) {
+                // the finishing warps of a tail tile use that tile's scratch block (the tail grid
+                // can exceed the SM count, the number of blocks; there are fewer tail tiles)
+                const size_t blk = static_cast<size_t>(blockIdx.x) / p.tail_parts;
+                long long* Qt = p.qscratch + (blk * BN + third * CW) * BM + rloc;
+                double* Rt = p.scratch + (blk * BN + third * CW) * BM + rloc;
                 drain_tail_unit<BN>(p, tm, tn, part, acc_full, acc_empty, abuf, aphase[0], aphase[1], abort_flag,
-                                    tmem_base + lane_off + third * CW, tsum, warp, lane, third, rloc, Q, R, keep,
+                                    tmem_base + lane_off + third * CW, tsum, warp, lane, third, rloc, Qt, Rt, keep,
                                     colexp, colflag);
+            }
         } else {
             bool ok = true;
             for (int it = 0; ok; ++it) {
@@ -732,15 +759,20 @@ static TailPlan tail_plan(int64_t tiles, int64_t ctas, int64_t kslabs, int64_t p
     TailPlan t;
     if (member == kMemberA1 || ctas <= 1 || kslabs <= 0 || pass_slabs <= 0) return t;
     const int64_t r = tiles % ctas;
-    if (r == 0) return t;
+    if (r == 0 || tiles < ctas) return t;
     const int64_t last_pass = kslabs - (kslabs - 1) / pass_slabs * pass_slabs;  // slabs of the shortest pass
-    int64_t parts = ctas / r;
-    if (parts > last_pass) parts = last_pass;
-    if (parts < 2) return t;
+    // One wave of parts only (r * parts <= ctas), and only when the saving clearly beats the
+    // tail launch's fixed cost (launch, pipeline fill, and the finishing warps' latency-bound
+    // reading and recombination: ~0.2 ms measured at 8192^3) -- a tile takes ~0.31 us per
+    // pair and k slab on the whole chip.
+    int64_t best_p = ctas / r;
+    if (best_p > last_pass) best_p = last_pass;
+    const double tile_us = 0.31 * (S * (S + 1) / 2) * static_cast<double>(last_pass);
+    if (best_p < 3 || tile_us * (1.0 - 1.0 / static_cast<double>(best_p)) < 250.0) return t;
     t.full_rounds = static_cast<int>(tiles / ctas);
     t.tiles = static_cast<int>(r);
-    t.parts = static_cast<int>(parts);
-    t.sums_bytes = align256_(static_cast<size_t>(r) * parts * S * kEmuBNMax * BM * sizeof(int32_t));
+    t.parts = static_cast<int>(best_p);
+    t.sums_bytes = align256_(static_cast<size_t>(r) * best_p * S * kEmuBNMax * BM * sizeof(int32_t));
     t.count_bytes = align256_(static_cast<size_t>(r) * EPI_WARPS * sizeof(int));
     return t;
 }
@@ -894,7 +926,8 @@ size_t emu_scratch_bytes_tail(int64_t m, int64_t n, int64_t k, int S, int max_ct
     int64_t ctas = max_ctas > 0 && max_ctas < sms ? max_ctas : sms;
     if (ctas > tiles) ctas = tiles;
     if (ctas < 1) ctas = 1;
-    const size_t base = emu_scratch_bytes_for_ctas(static_cast<int>(ctas));
+    // the recombination blocks for every SM (what momms_emu_slice_gemm requires), whatever the grid
+    const size_t base = emu_scratch_bytes_for_ctas(sms);
     const int64_t kslabs = (k + emu::BK - 1) / emu::BK;
     const int64_t pass_slabs = emu_max_k_per_pass(S, beta) / emu::BK;
     const emu::TailPlan tp = emu::tail_plan(tiles, ctas, kslabs, pass_slabs, S, kMemberC2);

@@ -287,9 +287,9 @@ def _slice_products(torch, A, B, S, nbytes):
 
 
 @pytest.mark.parametrize("m,n,k,S", [
-    (1280, 3072, 1500, 6),    # 10 x 16 = 160 tiles: 8 left over for 152 CTAs, 19 k parts each
-    (1300, 3000, 700, 9),     # 11 x 16 = 176 tiles: 24 left over, 6 parts each, ragged edges
-    (1280, 3072, 8448, 16),   # two k passes (the second of 2 slabs: 2 parts), S = 16
+    (1280, 3072, 3000, 6),    # 10 x 16 = 160 tiles: 8 left over for 152 CTAs, 19 k parts each
+    (1300, 3000, 2000, 9),    # 11 x 16 = 176 tiles: 24 left over, 6 parts each, ragged edges
+    (1280, 3072, 8832, 16),   # two k passes (the second of 8 slabs: 8 parts), S = 16
 ])
 def test_tail_split_bitwise_identical_to_whole_tiles(m, n, k, S):
     # Given the larger scratch, the slice-product call cuts the tiles of its last, partial round
@@ -317,3 +317,11 @@ def test_tail_split_bitwise_identical_to_whole_tiles(m, n, k, S):
         c = np.arange(tn * 192, min(n, tn * 192 + 192))
         Cref, N = reference(F(A[r, :]), F(B[:, c]))
         assert max_ratio(split[np.ix_(r, c)], Cref, k, 1.0, 0.0, N) <= 1.0
+
+
+def test_scratch_for_any_shape_covers_the_step_entry_minimum():
+    # momms_emu_slice_gemm requires at least momms_emu_scratch_bytes(); the size for a given
+    # problem only adds the tail split's partial sums, even when the grid has fewer CTAs than SMs
+    base = M.momms_emu_scratch_bytes()
+    for m, n, k, S in [(100, 100, 100, 4), (1024, 1024, 1024, 6), (8192, 8192, 8192, 6), (1, 1, 1, 1)]:
+        assert M.momms_emu_scratch_bytes_for(m, n, k, S) >= base
