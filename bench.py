@@ -49,10 +49,14 @@ def parse():
     p.add_argument("--steps", type=int, default=60)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--size", type=int, default=8192)
-    p.add_argument("--shape", default="square", choices=["square", "rankk", "panel", "backward", "batched"],
+    p.add_argument("--shape", default="square",
+                   choices=["square", "rankk", "panel", "backward", "batched", "host"],
                    help="square: m=n=k=size; rankk: m=n=2*size, k=256; panel: m=k=2*size, n=256; "
                         "backward: dA = dC B^T and dB = A^T dC for A 4096x2048, B 2048x4096; "
-                        "batched: 2000 problems, m, n, k log-uniform in [32, 2048]")
+                        "batched: 2000 problems, m, n, k log-uniform in [32, 2048]; "
+                        "host: m=n=k=size with A, B, C in pinned host memory (momms_gemm_host)")
+    p.add_argument("--block", type=int, default=0, help="momms_gemm_host block size (0 = from the budget)")
+    p.add_argument("--device-gb", type=float, default=0.0, help="momms_gemm_host device budget (0 = half free)")
     p.add_argument("--mode", default="auto", choices=["auto", "native", "emulated"])
     p.add_argument("--member", default="auto", choices=["auto", "C2", "A2", "B2", "A1"])
     p.add_argument("--slices", type=int, default=0, help="emulated slice count (0 = from the data)")
@@ -275,7 +279,22 @@ def run_side_workload(args):
     mode = {"auto": M.MODE_AUTO, "native": M.MODE_NATIVE, "emulated": M.MODE_EMULATED}[args.mode]
     h = M.Handle(mode=mode, slices=args.slices)
     keep = []
-    if args.shape == "backward":
+    io = {}
+    if args.shape == "host":
+        m = n = k = args.size
+        hosts = [torch.from_numpy(np.ascontiguousarray(syn.matrix("uniform", r, c, syn.workload_seed(1, nm)).T)).pin_memory()
+                 for r, c, nm in ((m, k, "A"), (k, n, "B"), (m, n, "C"))]
+        keep.append(hosts)
+        hA, hB, hC = (t.data_ptr() for t in hosts)
+        flops = 2.0 * m * n * k
+        workload = (f"square FP64 GEMM C := A*B + C, m=n=k={m}, A, B, C in pinned host memory, uniform[-1,1] "
+                    f"(seeded SplitMix64); out-of-core product, Resident C at the HBM level")
+
+        def step():
+            M.check(M.momms_gemm_host(h, m, n, k, 1.0, hA, m, hB, k, 1.0, hC, m, int(args.device_gb * 2 ** 30),
+                                      args.block, stream), "momms_gemm_host")
+            io.update(h.report())
+    elif args.shape == "backward":
         m, k, n = 4096, 2048, 4096
         A = M.DeviceMatrix.from_numpy(syn.matrix("normal", m, k, syn.workload_seed(2, "A")))
         B = M.DeviceMatrix.from_numpy(syn.matrix("normal", k, n, syn.workload_seed(2, "B")))
@@ -322,6 +341,9 @@ def run_side_workload(args):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    if io:
+        workload += (f"; block {io['ooc_block']}, {io['h2d_bytes']} B host->device and {io['d2h_bytes']} B "
+                     f"device->host per step")
     line = {"metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -339,7 +361,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.shape in ("backward", "batched"):
+    if args.shape in ("backward", "batched", "host"):
         return run_side_workload(args)
     import torch
 

@@ -96,6 +96,9 @@ typedef struct {
     int group;           /* C2 raster group: tile rows of the C block a wave covers  */
     int64_t launches;    /* kernels enqueued by the call                             */
     double est_err_ratio;/* emulated: estimated truncation error / bound (heuristic) */
+    int64_t ooc_block;   /* momms_gemm_host: block size b (0 for the other calls)    */
+    int64_t h2d_bytes;   /* momms_gemm_host: bytes copied host -> device             */
+    int64_t d2h_bytes;   /* momms_gemm_host: bytes copied device -> host             */
 } momms_report_t;
 
 /* ---------------------------------------------------------------- handles */
@@ -220,6 +223,29 @@ int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_
                          size_t scratch_bytes, int32_t* status, momms_stream_t stream);
 size_t momms_emu_scratch_bytes(void);
 size_t momms_emu_scratch_bytes_for(int64_t m, int64_t n, int64_t k, int slices);
+
+/* ------------------------------------------------------- out-of-core product */
+/* C := alpha*A*B + beta*C with A, B and C in HOST memory (column-major, leading
+ * dimensions as for momms_gemm; no transposes), for problems larger than the device
+ * memory one wants to give them.  The paper proposes MOMMS for out-of-core use with
+ * the slow level reached by explicit transfers overlapped with computation (Sec. 7);
+ * here host memory is the slow level and HBM the fast one, with Resident C at the HBM
+ * level (Sec. 2.2.1): a b x b block of C stays on the device while b x b blocks of A
+ * and B are copied in along k, so A is read ceil(n/b) times, B ceil(m/b) times and C
+ * read once (beta != 0) and written once (counts in the report: h2d_bytes, d2h_bytes).
+ * Copies run on two streams of the handle, double-buffered against the block products,
+ * which run on `stream` in the handle's mode (native / emulated / auto).
+ * block: b, a multiple of 256, or 0 to take the largest b whose six b x b FP64 buffers
+ * plus one b x b x b product's workspace fit in `device_bytes` (0 = half the free
+ * device memory).  Asynchronous on `stream`: C is complete in host memory when the
+ * stream is; A, B and C must stay valid until then.  Pinned host memory lets the copies
+ * overlap the products; pageable memory works but the copies then block the host.
+ * Block buffers are kept by the handle.  Errors: BLAS-style negative index (-14: block
+ * not a multiple of 256), MOMMS_ERR_ALLOC, MOMMS_ERR_CUDA. */
+int momms_gemm_host(momms_handle_t handle, int64_t m, int64_t n, int64_t k, double alpha,
+                    const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                    double* C, int64_t ldc, size_t device_bytes, int64_t block,
+                    momms_stream_t stream);
 
 /* ------------------------------------------------ allocation-free variant */
 /* The emulated product (scale, split and slice-product kernels of EMULATED mode)

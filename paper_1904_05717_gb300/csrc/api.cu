@@ -76,6 +76,11 @@ struct momms_handle_s {
     int* spread_host_big = nullptr;        // pinned, 2 per problem
     size_t spread_host_cap = 0;
     std::map<uint32_t, Plan> plans;
+    // out-of-core products (momms_gemm_host): block buffers, copy streams, slot events
+    void* ooc_buf = nullptr;
+    size_t ooc_bytes = 0;
+    cudaStream_t ooc_in = nullptr, ooc_out = nullptr;
+    cudaEvent_t ooc_ev[11] = {};
 };
 
 namespace {
@@ -608,6 +613,11 @@ int momms_destroy(momms_handle_t h) {
     if (h->status) cudaFree(h->status);
     if (h->spread_host) cudaFreeHost(h->spread_host);
     if (h->spread_ready) cudaEventDestroy(h->spread_ready);
+    if (h->ooc_buf) cudaFree(h->ooc_buf);
+    if (h->ooc_in) cudaStreamDestroy(h->ooc_in);
+    if (h->ooc_out) cudaStreamDestroy(h->ooc_out);
+    for (cudaEvent_t e : h->ooc_ev)
+        if (e) cudaEventDestroy(e);
     h->magic = 0;
     delete h;
     return MOMMS_OK;
@@ -1098,6 +1108,171 @@ int momms_tune(momms_handle_t h, const char* path, int64_t count, const int64_t*
     cudaEventDestroy(e1);
     if (status == MOMMS_OK && path) status = save_plans(h, path);
     return status;
+}
+
+// ------------------------------------------------------------------ out-of-core products
+// Host memory (Grace LPDDR over NVLink-C2C on GB300) is the slow level and HBM the fast one:
+// Resident C at the HBM level (Sec. 2.2.1).  A b x b block of C stays in HBM while b x b
+// blocks of A and B stream in along k; A is read ceil(n/b) times, B ceil(m/b) times, C read
+// once (beta != 0) and written once.  Two buffers per operand let the copies of the next
+// blocks run on their own streams while the current block product computes.
+namespace {
+
+constexpr int64_t kOocAlign = 256;
+
+// Device bytes of the out-of-core pipeline for block size b (six b x b FP64 buffers) plus the
+// workspace of one b x b x b product in the handle's mode.
+size_t ooc_device_bytes(momms_handle_t h, int64_t b) {
+    size_t ws = 0;
+    const Plan p = pick_plan(h, b, b, b);
+    if (p.mode == MOMMS_MODE_EMULATED) ws = emu_layout(b, b, b, p.slices > 0 ? p.slices : kAutoSliceMax, h->max_ctas).total;
+    return 6 * static_cast<size_t>(b) * b * sizeof(double) + ws;
+}
+
+int64_t ooc_block(momms_handle_t h, int64_t m, int64_t n, int64_t k, size_t budget) {
+    const int64_t top = round_up(std::max(std::max(m, n), std::max<int64_t>(k, 1)), kOocAlign);
+    int64_t best = kOocAlign;
+    for (int64_t b = kOocAlign; b <= top; b += kOocAlign)
+        if (ooc_device_bytes(h, b) <= budget) best = b;
+    return best;
+}
+
+int ooc_setup(momms_handle_t h, size_t bytes) {
+    if (!h->ooc_in && cudaStreamCreateWithFlags(&h->ooc_in, cudaStreamNonBlocking) != cudaSuccess) return MOMMS_ERR_CUDA;
+    if (!h->ooc_out && cudaStreamCreateWithFlags(&h->ooc_out, cudaStreamNonBlocking) != cudaSuccess) return MOMMS_ERR_CUDA;
+    for (cudaEvent_t& e : h->ooc_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return MOMMS_ERR_CUDA;
+    if (h->ooc_bytes < bytes) {
+        if (h->ooc_buf) {
+            cudaDeviceSynchronize();
+            cudaFree(h->ooc_buf);
+            h->ooc_buf = nullptr;
+            h->ooc_bytes = 0;
+        }
+        if (cudaMalloc(&h->ooc_buf, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return MOMMS_ERR_ALLOC;
+        }
+        h->ooc_bytes = bytes;
+    }
+    return MOMMS_OK;
+}
+
+// A rows x cols block of a column-major matrix, copied between host and a device buffer with
+// leading dimension `dld`.
+cudaError_t copy_block(double* dst, int64_t dld, const double* src, int64_t sld, int64_t rows, int64_t cols,
+                       cudaMemcpyKind kind, cudaStream_t st) {
+    return cudaMemcpy2DAsync(dst, static_cast<size_t>(dld) * sizeof(double), src, static_cast<size_t>(sld) * sizeof(double),
+                             static_cast<size_t>(rows) * sizeof(double), static_cast<size_t>(cols), kind, st);
+}
+
+}  // namespace
+
+int momms_gemm_host(momms_handle_t h, int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+                    const double* B, int64_t ldb, double beta, double* C, int64_t ldc, size_t device_bytes,
+                    int64_t block, momms_stream_t stream) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    int rc = check_gemm_args(2, MOMMS_OP_N, MOMMS_OP_N, m, n, k, A, lda, B, ldb, C, ldc, alpha, false);
+    if (rc) return rc;
+    if (block < 0 || block % kOocAlign) return -14;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    momms_report_t total{};
+    if (m == 0 || n == 0) {
+        h->report = total;
+        return MOMMS_OK;
+    }
+    if (block == 0) {
+        size_t budget = device_bytes;
+        if (budget == 0) {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return MOMMS_ERR_CUDA;
+            budget = free_b / 2;
+        }
+        block = ooc_block(h, m, n, k, budget);
+    }
+    const int64_t b = block;
+    const size_t blk = static_cast<size_t>(b) * b;
+    rc = ooc_setup(h, 6 * blk * sizeof(double));
+    if (rc) return rc;
+    double* buf = static_cast<double*>(h->ooc_buf);
+    double* Cb[2] = {buf, buf + blk};
+    double* Ab[2] = {buf + 2 * blk, buf + 3 * blk};
+    double* Bb[2] = {buf + 4 * blk, buf + 5 * blk};
+    cudaEvent_t* ev = h->ooc_ev;
+    cudaEvent_t ab_ready[2] = {ev[0], ev[1]}, ab_free[2] = {ev[2], ev[3]};
+    cudaEvent_t c_ready[2] = {ev[4], ev[5]}, c_done[2] = {ev[6], ev[7]}, c_free[2] = {ev[8], ev[9]};
+    cudaEvent_t start = ev[10];
+    // the copy streams start after the work already on the caller's stream
+    if (cudaEventRecord(start, s) != cudaSuccess || cudaStreamWaitEvent(h->ooc_in, start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(h->ooc_out, start, 0) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    const bool kzero = (k == 0 || alpha == 0.0);
+    int64_t step = 0, cblk = 0, h2d = 0, d2h = 0, launches = 0;
+    for (int64_t jc = 0; jc < n; jc += b) {
+        const int64_t nb = std::min(b, n - jc);
+        for (int64_t ic = 0; ic < m; ic += b, ++cblk) {
+            const int64_t mb = std::min(b, m - ic);
+            const int cs = static_cast<int>(cblk & 1);
+            double* hC = C + ic + jc * ldc;
+            const bool read_c = beta != 0.0;
+            if (cudaStreamWaitEvent(h->ooc_in, c_free[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+            if (read_c) {
+                if (copy_block(Cb[cs], b, hC, ldc, mb, nb, cudaMemcpyHostToDevice, h->ooc_in) != cudaSuccess)
+                    return MOMMS_ERR_CUDA;
+                h2d += mb * nb * 8;
+            }
+            if (cudaEventRecord(c_ready[cs], h->ooc_in) != cudaSuccess) return MOMMS_ERR_CUDA;
+            if (cudaStreamWaitEvent(s, c_ready[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+            if (kzero) {
+                rc = scale_c(mb, nb, beta, Cb[cs], b, s);
+                if (rc) return rc;
+                launches += beta == 1.0 ? 0 : 1;
+            }
+            for (int64_t pc = 0; !kzero && pc < k; pc += b, ++step) {
+                const int64_t kb = std::min(b, k - pc);
+                const int as = static_cast<int>(step & 1);
+                if (cudaStreamWaitEvent(h->ooc_in, ab_free[as], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+                if (copy_block(Ab[as], b, A + ic + pc * lda, lda, mb, kb, cudaMemcpyHostToDevice, h->ooc_in) !=
+                        cudaSuccess ||
+                    copy_block(Bb[as], b, B + pc + jc * ldb, ldb, kb, nb, cudaMemcpyHostToDevice, h->ooc_in) !=
+                        cudaSuccess)
+                    return MOMMS_ERR_CUDA;
+                h2d += (mb * kb + kb * nb) * 8;
+                if (cudaEventRecord(ab_ready[as], h->ooc_in) != cudaSuccess) return MOMMS_ERR_CUDA;
+                if (cudaStreamWaitEvent(s, ab_ready[as], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+                rc = gemm_dispatch(h, MOMMS_OP_N, MOMMS_OP_N, mb, nb, kb, alpha, Ab[as], b, Bb[as], b,
+                                   pc == 0 ? beta : 1.0, Cb[cs], b, s);
+                if (rc) return rc;
+                launches += h->report.launches;
+                total.mode = h->report.mode;
+                total.member = h->report.member;
+                total.slices = std::max(total.slices, h->report.slices);
+                total.digit_bits = h->report.digit_bits;
+                total.k_passes = std::max(total.k_passes, h->report.k_passes);
+                total.tile_m = h->report.tile_m;
+                total.tile_n = h->report.tile_n;
+                total.ctas = h->report.ctas;
+                total.group = h->report.group;
+                total.est_err_ratio = std::max(total.est_err_ratio, h->report.est_err_ratio);
+                if (cudaEventRecord(ab_free[as], s) != cudaSuccess) return MOMMS_ERR_CUDA;
+            }
+            if (cudaEventRecord(c_done[cs], s) != cudaSuccess) return MOMMS_ERR_CUDA;
+            if (cudaStreamWaitEvent(h->ooc_out, c_done[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+            if (copy_block(hC, ldc, Cb[cs], b, mb, nb, cudaMemcpyDeviceToHost, h->ooc_out) != cudaSuccess)
+                return MOMMS_ERR_CUDA;
+            d2h += mb * nb * 8;
+            if (cudaEventRecord(c_free[cs], h->ooc_out) != cudaSuccess) return MOMMS_ERR_CUDA;
+        }
+    }
+    // the caller's stream completes only after the last block is back in host memory
+    for (int cs = 0; cs < 2; ++cs)
+        if (cudaStreamWaitEvent(s, c_free[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+    total.launches = launches;
+    total.ooc_block = b;
+    total.h2d_bytes = h2d;
+    total.d2h_bytes = d2h;
+    h->report = total;
+    return MOMMS_OK;
 }
 
 int momms_member_tile(int member, int group, int64_t cta, int64_t ctas, int64_t i, int tiles_m, int tiles_n,

@@ -44,7 +44,8 @@ class Report(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("member", ctypes.c_int), ("slices", ctypes.c_int),
                 ("digit_bits", ctypes.c_int), ("k_passes", ctypes.c_int), ("tile_m", ctypes.c_int),
                 ("tile_n", ctypes.c_int), ("ctas", ctypes.c_int), ("group", ctypes.c_int),
-                ("launches", ctypes.c_int64), ("est_err_ratio", ctypes.c_double)]
+                ("launches", ctypes.c_int64), ("est_err_ratio", ctypes.c_double),
+                ("ooc_block", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -69,6 +70,7 @@ _SIGS = {
     "momms_set_workspace": ([_VP, _VP, _SZ], _I32),
     "momms_gemm": ([_I64, _I64, _I64, _DBL, _VP, _I64, _VP, _I64, _DBL, _VP, _I64, _VP], _I32),
     "momms_gemm_ex": ([_VP, _I32, _I32, _I64, _I64, _I64, _DBL, _VP, _I64, _VP, _I64, _DBL, _VP, _I64, _VP], _I32),
+    "momms_gemm_host": ([_VP, _I64, _I64, _I64, _DBL, _VP, _I64, _VP, _I64, _DBL, _VP, _I64, _SZ, _I64, _VP], _I32),
     "momms_gemm_backward": ([_VP, _I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _VP], _I32),
     "momms_gemm_batched": ([_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I32),
     "momms_emu_scale": ([_I32, _I32, _I64, _I64, _VP, _I64, _VP, _VP, _VP], _I32),
@@ -146,6 +148,12 @@ def momms_gemm(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
 def momms_gemm_ex(handle, op_a, op_b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
     return lib().momms_gemm_ex(_h(handle), op_a, op_b, m, n, k, alpha, _VP(A), lda, _VP(B), ldb, beta,
                                _VP(C), ldc, _stream(stream))
+
+
+def momms_gemm_host(handle, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, device_bytes=0, block=0, stream=None):
+    """A, B, C: host addresses (ints), e.g. of pinned torch tensors or numpy arrays."""
+    return lib().momms_gemm_host(_h(handle), m, n, k, alpha, _VP(A), lda, _VP(B), ldb, beta, _VP(C), ldc,
+                                 device_bytes, block, _stream(stream))
 
 
 def momms_gemm_backward(handle, m, n, k, A, lda, B, ldb, dC, lddc, dA, ldda, dB, lddb, stream=None):
