@@ -57,6 +57,7 @@ enum {
 };
 
 typedef enum { MOMMS_OP_N = 0, MOMMS_OP_T = 1 } momms_op_t;
+typedef enum { MOMMS_LOWER = 0, MOMMS_UPPER = 1 } momms_uplo_t;
 
 /* How the product is computed.
  *   NATIVE    FP64 DMMA tensor instructions, C micro-tile resident in registers
@@ -223,6 +224,21 @@ int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_
                          size_t scratch_bytes, int32_t* status, momms_stream_t stream);
 size_t momms_emu_scratch_bytes(void);
 size_t momms_emu_scratch_bytes_for(int64_t m, int64_t n, int64_t k, int slices);
+
+/* --------------------------------------------------- symmetric rank-k update */
+/* C := alpha*op(A)*op(A)^T + beta*C on the uplo triangle of the n x n matrix C
+ * (BLAS dsyrk: trans = N uses A n x k, trans = T uses A k x n; the other triangle is
+ * neither read nor written).  The paper names the other level-3 BLAS as the next use
+ * of the family (Sec. 7); this one needs half the products of a GEMM.  Native mode:
+ * the DMMA kernel over the triangle's tiles, elements masked on the diagonal tiles.
+ * Emulated mode: op(A) is scaled and split into digits ONCE and serves as both
+ * operands; the slice products run over the 128-row blocks of the triangle in one
+ * batched launch per k pass.  The error bound is the GEMM one with B = op(A)^T.
+ * Device pointers, asynchronous on `stream`.  Errors: BLAS-style negative index
+ * (uplo -2, trans -3, n -4, k -5, A -7, lda -8, C -10, ldc -11), MOMMS_ERR_*. */
+int momms_syrk(momms_handle_t handle, int uplo, int trans, int64_t n, int64_t k, double alpha,
+               const double* A, int64_t lda, double beta, double* C, int64_t ldc,
+               momms_stream_t stream);
 
 /* ------------------------------------------------------- out-of-core product */
 /* C := alpha*A*B + beta*C with A, B and C in HOST memory (column-major, leading

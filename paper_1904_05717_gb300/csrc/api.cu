@@ -162,21 +162,23 @@ int grow_device(void** buf, size_t* cap, size_t bytes) {
     return MOMMS_OK;
 }
 
-__global__ void scale_c_kernel(int64_t m, int64_t n, double beta, double* C, int64_t ldc) {
+// C := beta*C on all of C (tri 0), its lower (1) or its upper (2) triangle.
+__global__ void scale_c_kernel(int64_t m, int64_t n, double beta, double* C, int64_t ldc, int tri) {
     const int64_t total = m * n;
     for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
          idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t i = idx % m, j = idx / m;
+        if ((tri == 1 && j > i) || (tri == 2 && j < i)) continue;
         double* c = C + i + j * ldc;
         *c = (beta == 0.0) ? 0.0 : beta * *c;
     }
 }
 
-int scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc, cudaStream_t s) {
+int scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc, cudaStream_t s, int tri = 0) {
     if (beta == 1.0) return MOMMS_OK;
     int64_t blocks = (m * n + 255) / 256;
     blocks = std::min<int64_t>(blocks, int64_t(momms::device_sm_count()) * 16);
-    scale_c_kernel<<<static_cast<unsigned>(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(m, n, beta, C, ldc);
+    scale_c_kernel<<<static_cast<unsigned>(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(m, n, beta, C, ldc, tri);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -1108,6 +1110,164 @@ int momms_tune(momms_handle_t h, const char* path, int64_t count, const int64_t*
     cudaEventDestroy(e1);
     if (status == MOMMS_OK && path) status = save_plans(h, path);
     return status;
+}
+
+// ------------------------------------------------------------------ symmetric rank-k update
+namespace {
+
+// Emulated SYRK: op(A) is split into digits once and serves as both operands; the slice
+// products run over the tile rows of the referenced triangle only (one problem of the
+// batched slice-product launch per 128-row block, the diagonal tiles masked), in k passes
+// that keep the int32 diagonal sums exact.
+int run_syrk_emulated(momms_handle_t h, int uplo, int trans, int64_t n, int64_t k, double alpha, const double* A,
+                      int64_t lda, double beta, double* C, int64_t ldc, int S, cudaStream_t s) {
+    const int bb = h->digit_bits;
+    const int64_t k_pad = round_up(std::max<int64_t>(k, 1), momms::kEmuBK);
+    const int S_alloc = S > 0 ? S : kAutoSliceMax;
+    const int64_t tiles_m = (n + momms::kEmuBM - 1) / momms::kEmuBM;
+    // workspace: exponents, flags, norms, digits, recombination scratch
+    size_t o = 0;
+    const size_t off_e = o;  o += align256(sizeof(int32_t) * n);
+    const size_t off_ef = o; o += align256(static_cast<size_t>(n));
+    const size_t off_l1 = o; o += align256(sizeof(float) * n);
+    const size_t off_d = o;  o += align256(size_t(2) * S_alloc * n * k_pad);
+    const size_t scratch_bytes = momms::emu_scratch_bytes(momms::device_sm_count());
+    const size_t off_scr = o; o += align256(scratch_bytes);
+    void* ws = nullptr;
+    int rc = ensure_workspace(h, o, &ws);
+    if (rc) return rc;
+    char* w = static_cast<char*>(ws);
+    int32_t* e = reinterpret_cast<int32_t*>(w + off_e);
+    uint8_t* ef = reinterpret_cast<uint8_t*>(w + off_ef);
+    float* l1 = reinterpret_cast<float*>(w + off_l1);
+    char* Ad = w + off_d;
+    int64_t launches = 0;
+    if (momms::launch_emu_scale(0, trans, n, k, A, lda, e, ef, S > 0 ? nullptr : l1, s) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    launches += momms::emu_scale_kernel_count(0, trans);
+    if (S <= 0) {
+        // one spread: the second operand is the first one transposed
+        if (cudaMemsetAsync(h->spread_dev, 0, sizeof(int), s) != cudaSuccess ||
+            momms::launch_emu_spread(n, k, e, ef, l1, h->spread_dev, s) != cudaSuccess ||
+            cudaMemcpyAsync(h->spread_host, h->spread_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        launches += 1;
+        S = slices_from_spread(h->spread_host[0] / 16.0, h->spread_host[0] / 16.0, k, bb, nullptr);
+    }
+    if (S > S_alloc) return MOMMS_ERR_UNSUPPORTED;
+    if (momms::launch_emu_split(0, trans, n, k, A, lda, e, ef, S, bb, Ad, n, k_pad, s) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    launches += 1;
+    // one batched slice-product launch per k pass over the triangle's tile rows
+    const int64_t pass = momms::emu_max_k_per_pass(S, bb);
+    std::vector<momms::EmuBatchProblem> table;
+    std::vector<char> all;
+    for (int64_t k0 = 0; k0 < k_pad; k0 += pass) {
+        const int64_t kp = std::min(pass, k_pad - k0);
+        table.assign(static_cast<size_t>(tiles_m), momms::EmuBatchProblem{});
+        int64_t tiles = 0;
+        for (int64_t tm = 0; tm < tiles_m; ++tm) {
+            momms::EmuBatchProblem& g = table[static_cast<size_t>(tm)];
+            std::memset(&g, 0, sizeof(g));
+            const int64_t r0 = tm * momms::kEmuBM, mb = std::min<int64_t>(momms::kEmuBM, n - r0);
+            const int64_t c0 = uplo == MOMMS_LOWER ? 0 : r0;
+            const int64_t nb = uplo == MOMMS_LOWER ? std::min<int64_t>(n, r0 + momms::kEmuBM) : n - r0;
+            const char* baseA = Ad + (static_cast<size_t>(r0) * k_pad + k0) * 2;
+            const char* baseB = Ad + (static_cast<size_t>(c0) * k_pad + k0) * 2;
+            if (!momms::emu_make_digit_map(&g.mapA, baseA, kp, mb, S, momms::kEmuBM, n, k_pad) ||
+                !momms::emu_make_digit_map(&g.mapB, baseB, kp, nb, S, momms::kEmuBNMax, n, k_pad))
+                return MOMMS_ERR_UNSUPPORTED;
+            g.e = e + r0; g.ef = ef + r0; g.f = e + c0; g.ff = ef + c0;
+            g.C = C + r0 + c0 * ldc; g.ldc = ldc;
+            g.alpha = alpha; g.beta_c = k0 == 0 ? beta : 1.0;
+            g.m = static_cast<int32_t>(mb); g.n = static_cast<int32_t>(nb); g.S = S; g.beta = bb;
+            g.nslab = static_cast<int32_t>(kp / momms::kEmuBK);
+            g.chunk_slabs = momms::emu_chunk_slabs(bb);
+            g.group_end = momms::emu_group_ends(S, bb, kp);
+            g.tiles_n = static_cast<int32_t>((nb + momms::kEmuBNMax - 1) / momms::kEmuBNMax);
+            g.tile0 = tiles;
+            g.tri = uplo == MOMMS_LOWER ? 1 : 2;
+            g.diag = uplo == MOMMS_LOWER ? static_cast<int32_t>(r0) : 0;
+            tiles += g.tiles_n;
+        }
+        const size_t off = align256(all.size());
+        all.resize(off + sizeof(momms::EmuBatchProblem) * table.size());
+        std::memcpy(all.data() + off, table.data(), sizeof(momms::EmuBatchProblem) * table.size());
+    }
+    // upload every pass's table at once (kept by the handle until the next upload)
+    rc = grow_device(&h->batch_tables, &h->batch_tables_cap, all.size());
+    if (rc) return rc;
+    if (cudaMemcpyAsync(h->batch_tables, all.data(), all.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    h->host_tables.swap(all);
+    size_t off = 0;
+    int npass = 0;
+    for (int64_t k0 = 0; k0 < k_pad; k0 += pass, ++npass) {
+        off = align256(off);
+        const auto* dt = reinterpret_cast<const momms::EmuBatchProblem*>(static_cast<char*>(h->batch_tables) + off);
+        int64_t tiles = 0;
+        const auto* ht = reinterpret_cast<const momms::EmuBatchProblem*>(h->host_tables.data() + off);
+        for (int64_t tm = 0; tm < tiles_m; ++tm) tiles += ht[tm].tiles_n;
+        if (momms::launch_emu_slice_gemm_batched(dt, static_cast<int>(tiles_m), tiles, w + off_scr, scratch_bytes,
+                                                 h->status, s) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        launches += 1;
+        off += sizeof(momms::EmuBatchProblem) * static_cast<size_t>(tiles_m);
+    }
+    h->report = momms_report_t{};
+    h->report.mode = MOMMS_MODE_EMULATED;
+    h->report.member = MOMMS_MEMBER_AUTO;
+    h->report.slices = S;
+    h->report.digit_bits = bb;
+    h->report.k_passes = npass;
+    h->report.tile_m = momms::kEmuBM;
+    h->report.tile_n = momms::kEmuBNMax;
+    h->report.launches = launches;
+    return MOMMS_OK;
+}
+
+}  // namespace
+
+int momms_syrk(momms_handle_t h, int uplo, int trans, int64_t n, int64_t k, double alpha, const double* A,
+               int64_t lda, double beta, double* C, int64_t ldc, momms_stream_t stream) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (uplo != MOMMS_LOWER && uplo != MOMMS_UPPER) return -2;
+    if (trans != MOMMS_OP_N && trans != MOMMS_OP_T) return -3;
+    if (n < 0) return -4;
+    if (k < 0) return -5;
+    if (lda < std::max<int64_t>(1, trans == MOMMS_OP_N ? n : k)) return -8;
+    if (ldc < std::max<int64_t>(1, n)) return -11;
+    const bool product = n > 0 && k > 0 && alpha != 0.0;
+    if (product && !A) return -7;
+    if (n > 0 && !C) return -10;
+    if (n > (int64_t(1) << 30) || k > (int64_t(1) << 30)) return MOMMS_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int tri = uplo == MOMMS_LOWER ? 1 : 2;
+    h->report = momms_report_t{};
+    if (n == 0) return MOMMS_OK;
+    if (!product) {
+        h->report.launches = beta == 1.0 ? 0 : 1;
+        return scale_c(n, n, beta, C, ldc, s, tri);
+    }
+    const Plan p = pick_plan(h, n, n, k);
+    if (p.mode == MOMMS_MODE_EMULATED)
+        return run_syrk_emulated(h, uplo, trans, n, k, alpha, A, lda, beta, C, ldc, p.slices, s);
+    const int member = p.member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : p.member;
+    int ctas = 0, group = 0;
+    cudaError_t e = momms::launch_native_gemm(trans, 1 - trans, n, n, k, alpha, A, lda, A, lda, beta, C, ldc, member,
+                                              h->max_ctas, h->group, s, &ctas, &group, tri);
+    if (e == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) return MOMMS_ERR_CUDA;
+    h->report.mode = MOMMS_MODE_NATIVE;
+    h->report.member = member;
+    h->report.tile_m = momms::kNativeBM;
+    h->report.tile_n = momms::kNativeBN;
+    h->report.k_passes = 1;
+    h->report.ctas = ctas;
+    h->report.group = group;
+    h->report.launches = 1;
+    return MOMMS_OK;
 }
 
 // ------------------------------------------------------------------ out-of-core products

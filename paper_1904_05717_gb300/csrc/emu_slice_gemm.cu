@@ -197,6 +197,7 @@ struct FinalCtx {
     const int* colexp;       // f_j - 2 beta of the thread's columns (shared memory)
     const uint8_t* colflag;  // non-finite flags of the thread's columns (shared memory)
     int ncols;               // columns of the thread inside the matrix
+    int tri, lim;            // triangle mask: 1 keeps columns c <= lim, 2 keeps c >= lim (c local)
     double* cp;              // &C[row, first column of the thread]
     int64_t ldc;
     double alpha, beta_c, qnan;
@@ -225,7 +226,8 @@ MOMMS_DEV void recombine8(const RecombineCtx& rc, const int32_t (&pv)[8], int c0
             const double r = (rc.rfirst ? x : fma(rv[j], rc.rb, x)) * rc.gscale;
             if (MODE == kGroupEnd) {
                 st_l2_hint(rc.R + (c0 + j) * BM_, r, rc.keep);
-            } else if (fc->row_ok && c0 + j < fc->ncols) {
+            } else if (fc->row_ok && c0 + j < fc->ncols &&
+                       (fc->tri == 0 || (fc->tri == 1 ? c0 + j <= fc->lim : c0 + j >= fc->lim))) {
                 const double y = (fc->eflag || fc->colflag[c0 + j]) ? fc->qnan
                                                                     : scale_pow2(r, fc->ei + fc->colexp[c0 + j]);
                 double* cp = fc->cp + static_cast<int64_t>(c0 + j) * fc->ldc;
@@ -299,6 +301,8 @@ MOMMS_DEV void recombine_diagonal(const Params& p, int prob, int tm, int tn, int
         fc.colexp = colexp + third * CW;
         fc.colflag = colflag + third * CW;
         fc.ncols = min(CW, n_ - (tn * BN + third * CW));
+        fc.tri = bp ? bp->tri : 0;
+        fc.lim = bp ? row + bp->diag - (tn * BN + third * CW) : 0;
         fc.ldc = bp ? bp->ldc : one.ldc;
         fc.cp = (bp ? bp->C : one.C) + row + static_cast<int64_t>(tn * BN + third * CW) * fc.ldc;
         fc.alpha = bp ? bp->alpha : one.alpha;
@@ -560,6 +564,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const TileInts pr = tile_ints(p, prob, part);
                 const CUtensorMap* mapA = prob < 0 ? &tmA : &p.table[prob].mapA;
                 const CUtensorMap* mapB = prob < 0 ? &tmB : &p.table[prob].mapB;
+
                 for (int d = pr.S + 1; d >= 2 && ok; --d) {
                     for (int s = 1; s <= d - 1 && ok; ++s) {
                         for (int j = 0; j < pr.nslab; ++j) {
@@ -728,14 +733,19 @@ static EncodeFn get_encode() {
 }  // namespace emu
 
 // 3-D fp16 digit tensor [S][rows][k_pad] (k contiguous), box 64 x box_rows x 1, 128-B swizzle.
-bool emu_make_digit_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t rows, int S, int box_rows) {
+bool emu_make_digit_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t rows, int S, int box_rows,
+                        int64_t plane_rows, int64_t row_pitch) {
     using namespace emu;
     EncodeFn enc = get_encode();
     if (!enc) return false;
+    // The map covers k_pad digits of `rows` rows from `base`; in memory a row is row_pitch digits
+    // and a slice plane_rows rows (a block of rows or a range of k may start inside the tensor).
+    if (plane_rows <= 0) plane_rows = rows;
+    if (row_pitch <= 0) row_pitch = k_pad;
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(k_pad), static_cast<cuuint64_t>(rows),
                           static_cast<cuuint64_t>(S)};
-    cuuint64_t strides[2] = {static_cast<cuuint64_t>(k_pad) * 2,
-                             static_cast<cuuint64_t>(k_pad) * 2 * static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(row_pitch) * 2,
+                             static_cast<cuuint64_t>(row_pitch) * 2 * static_cast<cuuint64_t>(plane_rows)};
     cuuint32_t box[3] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(base), dims, strides,

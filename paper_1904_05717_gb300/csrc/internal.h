@@ -9,11 +9,13 @@ namespace momms {
 
 // ---------------------------------------------------------------- native FP64
 // C := alpha*op(A)*op(B) + beta*C on the FP64 DMMA tensor instructions.
+// tri: 0 = all of C, 1 = lower triangle only (j <= i), 2 = upper only (j >= i); tiles wholly
+// outside the triangle do no work.
 cudaError_t launch_native_gemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, double alpha,
                                const double* A, int64_t lda, const double* B, int64_t ldb,
                                double beta, double* C, int64_t ldc, int member, int max_ctas,
                                int group, cudaStream_t stream, int* used_ctas = nullptr,
-                               int* used_group = nullptr);
+                               int* used_group = nullptr, int tri = 0);
 constexpr int kNativeBM = 64, kNativeBN = 64;
 
 // One problem of a batched call (device-resident table entry).
@@ -90,6 +92,9 @@ struct EmuBatchProblem {
     int64_t tile0;     // first tile of this problem in the concatenated tile list
     int32_t m, n, S, beta, nslab, chunk_slabs, tiles_n;
     uint32_t group_end;
+    // triangle of C written (symmetric rank-k updates): 0 = all, 1 = lower (column <= row +
+    // diag), 2 = upper (column >= row + diag), rows and columns local to the problem
+    int32_t tri, diag;
 };
 // Per-problem inputs and outputs of the batched scale and split passes (op = N, N).
 struct EmuBatchPrep {
@@ -118,7 +123,10 @@ inline int64_t emu_batch_split_a_blocks(int64_t m, int64_t k_pad) { return ((m +
 inline int64_t emu_batch_split_b_blocks(int64_t n, int64_t k_pad) { return (n * (k_pad / 4) + 255) / 256; }
 
 // Tensor map of S digit slices [S][rows][k_pad] (fp16, k contiguous); box 64 x box_rows.
-bool emu_make_digit_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t rows, int S, int box_rows);
+// TMA map of digit slices [S][plane_rows][row_pitch] (fp16, K-major): k_pad digits of `rows`
+// rows from `base`, boxes of 64 digits x box_rows rows (plane_rows, row_pitch 0 = rows, k_pad).
+bool emu_make_digit_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t rows, int S, int box_rows,
+                        int64_t plane_rows = 0, int64_t row_pitch = 0);
 // One persistent launch of the slice-product kernel over the tiles of all problems.
 cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_tiles,
                                           void* scratch, size_t scratch_bytes, int32_t* status,

@@ -104,7 +104,7 @@ __device__ __forceinline__ void store_panels(Smem& sm, int buf, const double (&r
 template <bool TA, bool TB>
 __device__ void gemm_tile(Smem& sm, int m, int n, int k, double alpha, const double* __restrict__ A,
                           int64_t lda, const double* __restrict__ B, int64_t ldb, double beta,
-                          double* __restrict__ C, int64_t ldc, int tm, int tn) {
+                          double* __restrict__ C, int64_t ldc, int tm, int tn, int tri = 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
     const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
@@ -157,7 +157,7 @@ __device__ void gemm_tile(Smem& sm, int m, int n, int k, double alpha, const dou
             for (int c = 0; c < 4; ++c) {
                 const int i = i0 + wm + mi * 16 + g + ((c & 2) ? 8 : 0);
                 const int j = j0 + wn + ni * 8 + 2 * t + (c & 1);
-                if (i < m && j < n) {
+                if (i < m && j < n && (tri == 0 || (tri == 1 ? j <= i : j >= i))) {
                     double* cp = C + i + static_cast<int64_t>(j) * ldc;
                     const double v = alpha * acc[mi][ni][c];
                     *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
@@ -171,13 +171,18 @@ template <bool TA, bool TB>
 __global__ void __launch_bounds__(THREADS)
     gemm_kernel(int m, int n, int k, double alpha, const double* __restrict__ A, int64_t lda,
                 const double* __restrict__ B, int64_t ldb, double beta, double* __restrict__ C,
-                int64_t ldc, int member, int group, int tiles_m, int tiles_n) {
+                int64_t ldc, int member, int group, int tiles_m, int tiles_n, int tri) {
     __shared__ Smem sm;
     int tm, tn;
     // one tile per CTA by default; a capped grid loops over the CTA's share in member order
+    bool synced = true;
     for (int64_t i = 0; member_tile(member, group, blockIdx.x, gridDim.x, i, tiles_m, tiles_n, &tm, &tn); ++i) {
-        if (i > 0) __syncthreads();  // the shared panels are reused by the next tile
-        gemm_tile<TA, TB>(sm, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tm, tn);
+        // a triangle-only product skips the tiles that lie wholly outside its triangle
+        if (tri == 1 && tn * BN > tm * BM + BM - 1) continue;
+        if (tri == 2 && tn * BN + BN - 1 < tm * BM) continue;
+        if (!synced) __syncthreads();  // the shared panels are reused by the next tile
+        gemm_tile<TA, TB>(sm, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tm, tn, tri);
+        synced = false;
     }
 }
 
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(THREADS)
 cudaError_t launch_native_gemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, double alpha,
                                const double* A, int64_t lda, const double* B, int64_t ldb,
                                double beta, double* C, int64_t ldc, int member, int max_ctas,
-                               int group_req, cudaStream_t stream, int* used_ctas, int* used_group) {
+                               int group_req, cudaStream_t stream, int* used_ctas, int* used_group, int tri) {
     using namespace native;
     if (m <= 0 || n <= 0) return cudaSuccess;
     if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k > INT32_MAX / 2) return cudaErrorInvalidValue;
@@ -223,13 +228,13 @@ cudaError_t launch_native_gemm(int op_a, int op_b, int64_t m, int64_t n, int64_t
     if (used_group) *used_group = group;
     const int mi = static_cast<int>(m), ni = static_cast<int>(n), ki = static_cast<int>(k);
     if (!op_a && !op_b)
-        gemm_kernel<false, false><<<grid, THREADS, 0, stream>>>(mi, ni, ki, alpha, A, lda, B, ldb, beta, C, ldc, mem, group, tiles_m, tiles_n);
+        gemm_kernel<false, false><<<grid, THREADS, 0, stream>>>(mi, ni, ki, alpha, A, lda, B, ldb, beta, C, ldc, mem, group, tiles_m, tiles_n, tri);
     else if (op_a && !op_b)
-        gemm_kernel<true, false><<<grid, THREADS, 0, stream>>>(mi, ni, ki, alpha, A, lda, B, ldb, beta, C, ldc, mem, group, tiles_m, tiles_n);
+        gemm_kernel<true, false><<<grid, THREADS, 0, stream>>>(mi, ni, ki, alpha, A, lda, B, ldb, beta, C, ldc, mem, group, tiles_m, tiles_n, tri);
     else if (!op_a && op_b)
-        gemm_kernel<false, true><<<grid, THREADS, 0, stream>>>(mi, ni, ki, alpha, A, lda, B, ldb, beta, C, ldc, mem, group, tiles_m, tiles_n);
+        gemm_kernel<false, true><<<grid, THREADS, 0, stream>>>(mi, ni, ki, alpha, A, lda, B, ldb, beta, C, ldc, mem, group, tiles_m, tiles_n, tri);
     else
-        gemm_kernel<true, true><<<grid, THREADS, 0, stream>>>(mi, ni, ki, alpha, A, lda, B, ldb, beta, C, ldc, mem, group, tiles_m, tiles_n);
+        gemm_kernel<true, true><<<grid, THREADS, 0, stream>>>(mi, ni, ki, alpha, A, lda, B, ldb, beta, C, ldc, mem, group, tiles_m, tiles_n, tri);
     return cudaGetLastError();
 }
 

@@ -176,3 +176,15 @@ def test_batched_2000_uneven_problems_emulated():
         Cref = oracle.dgemm(A, B, C.copy(order="F"), 1.0, 1.0)
         worst = max(worst, max_ratio(d[2].to_numpy(), Cref, k, 1.0, 1.0, oracle.dgemm_abs(A, B), C))
     assert worst <= 1.0
+
+
+def test_batched_emulated_same_handle_new_problems_reuses_table_memory():
+    # two calls on one handle with the same problem count: the second call's tensor maps are
+    # uploaded to the same device table as the first call's and must be the ones used
+    h = M.Handle(mode=M.MODE_EMULATED, slices=9)
+    for seed in (8100, 8200):
+        probs = make_problems(6, 64, 500, seed)
+        dev, _ = run_batched(h, probs)
+        assert h.device_status() == M.MOMMS_OK
+        assert check_all(probs, dev) <= 1.0
+    h.close()
