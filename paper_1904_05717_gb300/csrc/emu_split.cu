@@ -196,10 +196,74 @@ __device__ __forceinline__ void digit_source(double x, bool valid, int e, uint32
     *sgn = neg ? 0x8000u : 0u;
 }
 
+// 7-bit digits (the width the library uses) with shifts known at compile time.  |x| 2^-e is
+// formed once per element as a 128-bit fixed-point fraction F = fh:fl (bit 127 worth 2^-1):
+// F = m 2^(128 + e2 - e), truncated below 2^-128, i.e. past the 18th digit.  |x| < 2^e keeps F
+// below 2^128.  Digit s (1-based) is then bits [128 - 7s, 135 - 7s) of F: with s unrolled every
+// shift is a constant, two or three instructions a digit.
+constexpr int kFastBeta = 7, kFastMaxS = 16;
+
+__device__ __forceinline__ void fraction128(double x, bool valid, int e, unsigned long long* fh,
+                                            unsigned long long* fl, uint32_t* sgn) {
+    unsigned long long m = 0;
+    int e2 = 0;
+    bool neg = false;
+    if (valid) decompose(x, &m, &e2, &neg);
+    const int sh = 128 + e2 - e;
+    *sgn = neg ? 0x8000u : 0u;
+    if (m == 0 || sh <= -64) {
+        *fh = 0;
+        *fl = 0;
+    } else if (sh >= 64) {
+        *fh = m << (sh - 64);
+        *fl = 0;
+    } else if (sh > 0) {
+        *fh = m >> (64 - sh);
+        *fl = m << sh;
+    } else {
+        *fh = 0;
+        *fl = m >> (-sh);
+    }
+}
+
+__device__ __forceinline__ uint32_t digit7(unsigned long long fh, unsigned long long fl, int s) {
+    const int lo = 128 - kFastBeta * s;  // lowest bit of digit s
+    if (lo >= 64) return static_cast<uint32_t>(fh >> (lo - 64)) & 0x7Fu;
+    if (lo + kFastBeta <= 64) return static_cast<uint32_t>(fl >> lo) & 0x7Fu;
+    return static_cast<uint32_t>((fl >> lo) | (fh << (64 - lo))) & 0x7Fu;
+}
+
+template <int N>
+__device__ __forceinline__ void write_digits_fast(const double (&x)[N], bool valid_row, int e, int S,
+                                                  __half* __restrict__ digits, int64_t plane, int64_t off,
+                                                  int s_first) {
+    unsigned long long fh[N], fl[N];
+    uint32_t sg[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) fraction128(x[i], valid_row, e, &fh[i], &fl[i], &sg[i]);
+#pragma unroll
+    for (int s = 1; s <= kFastMaxS; ++s) {
+        if (s > S) break;
+        if (s <= s_first) continue;
+        uint32_t w[N / 2];
+#pragma unroll
+        for (int i = 0; i < N; i += 2)
+            w[i / 2] = digits_to_half2(digit7(fh[i], fl[i], s), digit7(fh[i + 1], fl[i + 1], s), sg[i], sg[i + 1]);
+        if constexpr (N == 8)
+            *reinterpret_cast<uint4*>(digits + (s - 1) * plane + off) = make_uint4(w[0], w[1], w[2], w[3]);
+        else
+            *reinterpret_cast<uint2*>(digits + (s - 1) * plane + off) = make_uint2(w[0], w[1]);
+    }
+}
+
 // Writes the digits of slices s_first+1 .. S (1-based); the digit of slice s does not depend on S.
 __device__ __forceinline__ void write_digits4(const double (&x)[4], bool valid_row, int e, int S, int beta,
                                               __half* __restrict__ digits, int64_t plane, int64_t off,
                                               int s_first = 0) {
+    if (beta == kFastBeta && S <= kFastMaxS) {
+        write_digits_fast<4>(x, valid_row, e, S, digits, plane, off, s_first);
+        return;
+    }
     uint32_t lo[4], hi[4], sg[4];
     int t[4];
 #pragma unroll
@@ -220,6 +284,10 @@ __device__ __forceinline__ void write_digits4(const double (&x)[4], bool valid_r
 __device__ __forceinline__ void write_digits8(const double (&x)[8], bool valid_row, int e, int S, int beta,
                                               __half* __restrict__ digits, int64_t plane, int64_t off,
                                               int s_first) {
+    if (beta == kFastBeta && S <= kFastMaxS) {
+        write_digits_fast<8>(x, valid_row, e, S, digits, plane, off, s_first);
+        return;
+    }
     uint32_t lo[8], hi[8], sg[8];
     int t[8];
 #pragma unroll
@@ -261,20 +329,24 @@ __global__ void split_inner_contig(const double* __restrict__ X, int64_t ld, int
 
 // Rows contiguous in memory: a 64 x 64 tile is transposed through shared memory so that
 // reads are coalesced along r and digit writes along q (four q per thread, 8-byte stores).
+// The tile is stored [q][r ^ swz(q)], swz(q) = (q / 4) mod 16: a warp that fills one q row
+// (32 consecutive r) and a warp that reads four consecutive q of one r per thread (16
+// threads along q) both touch every bank pair evenly, with no padding.
+__device__ __forceinline__ int swz(int q) { return (q >> 2) & 15; }
 constexpr int TT = 64;
 __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
                                   int64_t inner, const int32_t* __restrict__ exps,
                                   const uint8_t* __restrict__ flags, int S, int beta,
                                   __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad,
                                   int s_first) {
-    __shared__ double tile[TT][TT + 1];  // [q][r]
+    __shared__ double tile[TT][TT];  // [q][r ^ swz(q)]
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TT;
     const int64_t q0 = static_cast<int64_t>(blockIdx.y) * TT;
     const int tid = threadIdx.x;  // 256 threads
     for (int i = tid; i < TT * TT; i += 256) {
         const int rr = i % TT, qq = i / TT;
         const int64_t r = r0 + rr, q = q0 + qq;
-        tile[qq][rr] = (r < rows && q < inner) ? X[r + q * ld] : 0.0;
+        tile[qq][rr ^ swz(qq)] = (r < rows && q < inner) ? X[r + q * ld] : 0.0;
     }
     __syncthreads();
     const int64_t plane = rows_pad * inner_pad;
@@ -285,7 +357,7 @@ __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int6
         const bool valid = r < rows && !flags[r];
         double x[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr];
+        for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr ^ swz(qg + t)];
         write_digits4(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
     }
 }
@@ -377,7 +449,7 @@ __global__ void batch_scale_b(const EmuBatchPrep* __restrict__ probs, const int2
 
 // A: 64 (rows) x 64 (k) tile through shared memory, as split_rows_contig.
 __global__ void batch_split_a(const EmuBatchPrep* __restrict__ probs, const int2* __restrict__ items) {
-    __shared__ double tile[TT][TT + 1];  // [q][r]
+    __shared__ double tile[TT][TT];  // [q][r ^ swz(q)]
     const int2 it = items[blockIdx.x];
     const EmuBatchPrep& pr = probs[it.x];
     const int64_t qtiles = pr.k_pad / TT;
@@ -387,7 +459,7 @@ __global__ void batch_split_a(const EmuBatchPrep* __restrict__ probs, const int2
     for (int i = tid; i < TT * TT; i += 256) {
         const int rr = i % TT, qq = i / TT;
         const int64_t r = r0 + rr, q = q0 + qq;
-        tile[qq][rr] = (r < pr.m && q < pr.k) ? pr.A[r + q * pr.lda] : 0.0;
+        tile[qq][rr ^ swz(qq)] = (r < pr.m && q < pr.k) ? pr.A[r + q * pr.lda] : 0.0;
     }
     __syncthreads();
     const int64_t plane = static_cast<int64_t>(pr.m) * pr.k_pad;
@@ -399,7 +471,7 @@ __global__ void batch_split_a(const EmuBatchPrep* __restrict__ probs, const int2
         const bool valid = !pr.ef[r];
         double x[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr];
+        for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr ^ swz(qg + t)];
         write_digits4(x, valid, valid ? pr.e[r] : 0, pr.S, pr.beta, dg, plane, r * pr.k_pad + q);
     }
 }
