@@ -218,10 +218,23 @@ class OracleSample:
 
     def run(self, cols):
         B = np.asfortranarray(self.B[:, :cols])
-        C = np.asfortranarray(self.C[:, :cols])
+        C = np.array(self.C[:, :cols], order="F")  # the oracle updates C in place; keep the workload's C
         t0 = time.perf_counter()
         self.oracle.dgemm(self.A, B, C, 1.0, 1.0)
         return time.perf_counter() - t0
+
+    def error_ratio(self, C_gpu_cols):
+        """max over the given leading columns of |C_gpu - C_oracle| / bound, the bound being
+        4 k u (|A||B| + |C0|)(1 + 4ku) + 2^-1021 (alpha = beta = 1)."""
+        cols = C_gpu_cols.shape[1]
+        B = np.asfortranarray(self.B[:, :cols])
+        C0 = np.asfortranarray(self.C[:, :cols])
+        Cref = self.oracle.dgemm(self.A, B, C0.copy(order="F"), 1.0, 1.0)
+        N = self.oracle.dgemm_abs(self.A, B)
+        u = 2.0 ** -53
+        k = self.n
+        bound = 4.0 * k * u * (N + np.abs(C0)) * (1.0 + 4.0 * k * u) + 2.0 ** -1021
+        return float(np.max(np.abs(C_gpu_cols - Cref) / bound))
 
     def columns_for(self, seconds):
         cols = int(max(self.cores, min(self.B.shape[1], seconds / max(self.per_col, 1e-9))))
@@ -538,10 +551,20 @@ def main():
     e2e_value, e2e_ms = aggregate_throughput(flops, e2e_s * 1e3 / esteps, world)
 
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.shape == "square":
         sample = OracleSample(n)
         v, desc = sample.measure(args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": sample.cores, "kind": "oracle", "sample": desc}
+        # the error of one step of the timed path against the oracle, on leading columns of C
+        acc_cols = 16
+        dC.storage.copy_(dC0)
+        step()
+        torch.cuda.synchronize()
+        ratio = sample.error_ratio(dC.to_numpy()[:, :acc_cols])
+        accuracy = {"max_error_over_bound": ratio, "columns_checked": acc_cols,
+                    "bound": "4 k 2^-53 (|A||B| + |C0|)(1 + 4 k 2^-53) + 2^-1021, componentwise",
+                    "slices": int(h.report()["slices"]) if h.report()["mode"] == M.MODE_EMULATED else 0}
 
     if rank == 0:
         emulated = rep["mode"] == M.MODE_EMULATED
@@ -570,6 +593,7 @@ def main():
             "clocks": clocks,
             "device_status": status,
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
