@@ -97,14 +97,13 @@ struct Params {
     int32_t* status;
     // Tail split (single problem, round-robin members): the main launch stops after its whole
     // rounds; the tiles of the last, partial round go to a second launch that cuts each along k
-    // into tail_parts units, one per CTA; each unit stores its int32 diagonal sums and the last
-    // unit of a tile to finish adds them up and recombines.
+    // into tail_parts units, one per CTA, each storing its int32 diagonal sums; a third launch
+    // adds the parts and recombines.
     int full_rounds;          // whole-tile rounds of the main launch
     int main_ctas;            // CTAs of the main launch (its round-robin order places the tail tiles)
     int tail_tiles;           // tiles in the tail round
     int tail_parts;           // k parts per tail tile (< 2: no split)
-    int32_t* tail_sums;       // [tail tile][part][diagonal d-2][column][row] int32 partial sums
-    int* tail_count;          // [tail tile][drain warp] parts stored (zero at launch)
+    int32_t* tail_sums;       // [tail tile][part][diagonal d-2][column / 4][row][4] int32 partial sums
 };
 
 // The it-th tile of this CTA: its problem (-1 = the single problem of p.one) and tile
@@ -343,50 +342,6 @@ MOMMS_DEV void store_partial(int4* dst, const int32_t (&acc)[CR], uint32_t tsum)
     }
 }
 
-// Sixteen columns [c, c + 16) of the complete int32 sums: the sum over the tile's k parts, four
-// parts' words in flight at a time.
-MOMMS_DEV void sum_partials16(const Params& p, int tail, int S, int d, int c0, int c, int rloc, int32_t (&v)[16]) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = 0;
-    const int parts = p.tail_parts;
-#pragma unroll 4
-    for (int part = 0; part < parts; ++part) {
-        const int4* src = tail_slot(p, tail, part, S, d, c0, rloc) + c / 4 * BM;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const int4 x = __ldcg(src + w * BM);
-            v[4 * w] += x.x;
-            v[4 * w + 1] += x.y;
-            v[4 * w + 2] += x.z;
-            v[4 * w + 3] += x.w;
-        }
-    }
-}
-
-// The complete int32 sums of diagonal d (integer addition over the parts, so they equal the
-// unsplit sums bit for bit): the first CR columns to `acc`, the other CT to TMEM at `tsum`.
-template <int CR, int CT>
-MOMMS_DEV void sum_partials(const Params& p, int tail, int S, int d, int c0, int rloc, int32_t (&acc)[CR],
-                            uint32_t tsum) {
-#pragma unroll
-    for (int c = 0; c < CR; c += 16) {
-        int32_t v[16];
-        sum_partials16(p, tail, S, d, c0, c, rloc, v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[c + j] = v[j];
-    }
-#pragma unroll
-    for (int q = 0; q < CT / 16; ++q) {
-        int32_t v[16];
-        sum_partials16(p, tail, S, d, c0, CR + q * 16, rloc, v);
-        uint32_t t[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) t[j] = static_cast<uint32_t>(v[j]);
-        tmem_st_32x32b_x16(tsum + q * 16, t);
-    }
-    tmem_st_wait();
-}
-
 // Stages the column exponents (minus 2 beta) and non-finite flags of tile column tn in shared
 // memory, between two barriers of the drain warps (the previous tile's columns are no longer read).
 template <int BN>
@@ -458,22 +413,18 @@ MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, ui
 }
 
 // A drain warp's share of a k part of a split tail tile (always the CTA's last unit): drain
-// every diagonal and store its int32 sums; then, per drain warp (its 32 rows x 64 columns),
-// the warp of the last part to finish adds up all parts -- exact integer sums, so the result
-// equals the unsplit tile's bit for bit -- and recombines.  The warps count on their own (no
-// CTA-wide barrier).
+// every diagonal and store its int32 sums for the fix-up launch (tail_fixup_kernel), which
+// adds the parts and recombines once all of them are done.
 template <int BN>
-MOMMS_DEV void drain_tail_unit(const Params& p, int tm, int tn, int part, uint64_t* acc_full,
-                                             uint64_t* acc_empty, uint32_t abuf, uint32_t ph0, uint32_t ph1,
-                                             volatile int* abort_flag, uint32_t tacc, uint32_t tsum, int warp,
-                                             int lane, int third, int rloc, long long* Q, double* R,
-                                             uint64_t keep, int* colexp, uint8_t* colflag) {
+MOMMS_DEV void drain_tail_unit(const Params& p, int tn, int part, uint64_t* acc_full, uint64_t* acc_empty,
+                               uint32_t abuf, uint32_t ph0, uint32_t ph1, volatile int* abort_flag, uint32_t tacc,
+                               uint32_t tsum, int lane, int third, int rloc) {
     using C_ = Cfg<BN>;
     constexpr int CR = C_::CR, CT = C_::CT, CW = C_::CW;
     const TileInts pr = tile_ints(p, -1, part);
     const int tail = static_cast<int>(blockIdx.x) / p.tail_parts;
     uint32_t aphase[2] = {ph0, ph1};
-    stage_columns<BN>(p, -1, tn, pr.beta, colexp, colflag);
+    (void)tn;
     for (int d = pr.S + 1; d >= 2; --d) {
         int32_t acc[CR];
         if (!drain_diagonal<CR, CT>((d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty, abuf, aphase,
@@ -481,22 +432,74 @@ MOMMS_DEV void drain_tail_unit(const Params& p, int tm, int tn, int part, uint64
             return;
         store_partial<CR, CT>(tail_slot(p, tail, part, pr.S, d, third * CW, rloc), acc, tsum);
     }
-    __threadfence();
-    __syncwarp();
-    const int slot = tail * EPI_WARPS + (warp - CTRL_WARPS);
-    int last = 0;
-    if (lane == 0) last = atomicAdd(&p.tail_count[slot], 1) == p.tail_parts - 1;
-    if (!__shfl_sync(0xffffffffu, last, 0)) return;
-    __threadfence();
-    const double rb = pow2_normal(-pr.beta);
-    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// The fix-up of the split tail tiles, one thread per row and 8 columns of a tile: the int32
+// diagonal sums of all k parts are added (integer addition: they equal the unsplit sums) and
+// recombined in registers with the arithmetic of recombine8 -- exact int64 group sums, FP64
+// only at group ends, the final scaling and alpha / beta_c -- so C is bit-identical to the
+// unsplit kernel's.
+__global__ void __launch_bounds__(256) tail_fixup_kernel(const __grid_constant__ Params p) {
+    constexpr int GROUPS = kEmuBNMax / 8;  // column groups of a tile
+    const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t per_tile = static_cast<int64_t>(BM) * GROUPS;
+    const int tail = static_cast<int>(gid / per_tile);
+    if (tail >= p.tail_tiles) return;
+    const int w = static_cast<int>(gid - tail * per_tile);
+    const int rloc = w % BM, cg = w / BM;  // consecutive threads: consecutive rows
+    const int64_t t = static_cast<int64_t>(p.full_rounds) * p.main_ctas + tail;
+    int tm, tn;
+    if (!member_tile(p.member, p.group, t % p.main_ctas, p.main_ctas, t / p.main_ctas, p.tiles_m, p.tiles_n, &tm, &tn))
+        return;
+    const Prob& one = p.one;
+    const int S = one.S, beta = one.beta;
+    const double rb = pow2_normal(-beta);
+    long long q[8];
+    double r[8];
     int gj = 0;
     bool rfirst = true;
-    for (int d = pr.S + 1; d >= 2; --d) {
-        int32_t acc[CR];
-        sum_partials<CR, CT>(p, tail, pr.S, d, third * CW, rloc, acc, tsum);
-        recombine_diagonal<BN, CR, CT>(p, -1, tm, tn, d, pr, Q, R, keep, tsum, rb, third, rloc, colexp, colflag,
-                                       qnan, acc, gj, rfirst);
+    for (int d = S + 1; d >= 2; --d) {
+        int32_t pv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int part = 0; part < p.tail_parts; ++part) {
+            const int4* src = tail_slot(p, tail, part, S, d, cg * 8, rloc);
+            const int4 a = __ldcg(src), b = __ldcg(src + BM);
+            pv[0] += a.x; pv[1] += a.y; pv[2] += a.z; pv[3] += a.w;
+            pv[4] += b.x; pv[5] += b.y; pv[6] += b.z; pv[7] += b.w;
+        }
+        const bool gfirst = (gj == 0);
+        const bool gend = (one.group_end >> d) & 1u;
+        const int sh = beta * gj;
+        const double gscale = pow2_normal(-beta * gj);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const long long p64 = static_cast<long long>(pv[j]);
+            const long long v = gfirst ? p64 : q[j] + (p64 << sh);
+            if (!gend) {
+                q[j] = v;
+            } else {
+                const double x = static_cast<double>(v);
+                r[j] = (rfirst ? x : fma(r[j], rb, x)) * gscale;
+            }
+        }
+        if (gend) {
+            gj = 0;
+            rfirst = false;
+        } else {
+            ++gj;
+        }
+    }
+    const int row = tm * BM + rloc;
+    if (row >= one.m) return;
+    const int ei = one.e[row];
+    const bool eflag = one.ef[row] != 0;
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int col = tn * kEmuBNMax + cg * 8 + j;
+        if (col >= one.n) break;
+        const double y = (eflag || one.ff[col]) ? qnan : scale_pow2(r[j], ei + (one.f[col] - 2 * beta));
+        double* cp = one.C + row + static_cast<int64_t>(col) * one.ldc;
+        *cp = (one.beta_c == 0.0) ? one.alpha * y : fma(one.beta_c, *cp, one.alpha * y);
     }
 }
 
@@ -669,16 +672,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint64_t keep = l2_policy_evict_last();
         if constexpr (TAIL) {
             int tm, tn, prob, part;
-            if (tile_of<true>(p, 0, &prob, &tm, &tn, &part)) {
-                // the finishing warps of a tail tile use that tile's scratch block (the tail grid
-                // can exceed the SM count, the number of blocks; there are fewer tail tiles)
-                const size_t blk = static_cast<size_t>(blockIdx.x) / p.tail_parts;
-                long long* Qt = p.qscratch + (blk * BN + third * CW) * BM + rloc;
-                double* Rt = p.scratch + (blk * BN + third * CW) * BM + rloc;
-                drain_tail_unit<BN>(p, tm, tn, part, acc_full, acc_empty, abuf, aphase[0], aphase[1], abort_flag,
-                                    tmem_base + lane_off + third * CW, tsum, warp, lane, third, rloc, Qt, Rt, keep,
-                                    colexp, colflag);
-            }
+            if (tile_of<true>(p, 0, &prob, &tm, &tn, &part))
+                drain_tail_unit<BN>(p, tn, part, acc_full, acc_empty, abuf, aphase[0], aphase[1], abort_flag,
+                                    tmem_base + lane_off + third * CW, tsum, lane, third, rloc);
         } else {
             bool ok = true;
             for (int it = 0; ok; ++it) {
@@ -761,7 +757,7 @@ namespace emu {
 // slabs of the shortest pass) lets parts x as many CTAs share that round.
 struct TailPlan {
     int full_rounds = 0, tiles = 0, parts = 0;
-    size_t sums_bytes = 0, count_bytes = 0;
+    size_t sums_bytes = 0;
 };
 static size_t align256_(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
@@ -772,18 +768,16 @@ static TailPlan tail_plan(int64_t tiles, int64_t ctas, int64_t kslabs, int64_t p
     if (r == 0 || tiles < ctas) return t;
     const int64_t last_pass = kslabs - (kslabs - 1) / pass_slabs * pass_slabs;  // slabs of the shortest pass
     // One wave of parts only (r * parts <= ctas), and only when the saving clearly beats the
-    // tail launch's fixed cost (launch, pipeline fill, and the finishing warps' latency-bound
-    // reading and recombination: ~0.2 ms measured at 8192^3) -- a tile takes ~0.31 us per
-    // pair and k slab on the whole chip.
+    // fixed cost of the two extra launches (launch gaps, pipeline fill, the fix-up pass: a few
+    // tens of microseconds) -- a tile takes ~0.31 us per pair and k slab on the whole chip.
     int64_t best_p = ctas / r;
     if (best_p > last_pass) best_p = last_pass;
     const double tile_us = 0.31 * (S * (S + 1) / 2) * static_cast<double>(last_pass);
-    if (best_p < 3 || tile_us * (1.0 - 1.0 / static_cast<double>(best_p)) < 250.0) return t;
+    if (best_p < 2 || tile_us * (1.0 - 1.0 / static_cast<double>(best_p)) < 60.0) return t;
     t.full_rounds = static_cast<int>(tiles / ctas);
     t.tiles = static_cast<int>(r);
     t.parts = static_cast<int>(best_p);
     t.sums_bytes = align256_(static_cast<size_t>(r) * best_p * S * kEmuBNMax * BM * sizeof(int32_t));
-    t.count_bytes = align256_(static_cast<size_t>(r) * EPI_WARPS * sizeof(int));
     return t;
 }
 
@@ -819,7 +813,7 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     if (kslabs <= 0 || pass_slabs <= 0) return cudaErrorInvalidValue;
     const int member = a.member == kMemberAuto ? kMemberC2 : a.member;
     TailPlan tp = tail_plan(tiles, ctas, kslabs, pass_slabs, a.S, member);
-    if (tp.parts && a.scratch_bytes < 2 * half + tp.sums_bytes + tp.count_bytes) tp = TailPlan{};  // whole tiles
+    if (tp.parts && a.scratch_bytes < 2 * half + tp.sums_bytes) tp = TailPlan{};  // whole tiles
     char* tail_base = static_cast<char*>(a.scratch) + 2 * half;
     int npass = 0, nlaunch = 0;
     for (int64_t s0 = 0; s0 < kslabs; s0 += pass_slabs) {
@@ -850,7 +844,6 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
             p.tail_tiles = tp.tiles;
             p.tail_parts = tp.parts;
             p.tail_sums = reinterpret_cast<int32_t*>(tail_base);
-            p.tail_count = reinterpret_cast<int*>(tail_base + tp.sums_bytes);
         }
         if (a.used_ctas) *a.used_ctas = static_cast<int>(ctas);
         if (a.used_group) *a.used_group = p.group;
@@ -864,14 +857,17 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         if (e != cudaSuccess) return e;
         ++nlaunch;
         if (tp.parts) {
-            // tail launch: one CTA per k part of every tile of the last, partial round
-            e = cudaMemsetAsync(p.tail_count, 0, tp.count_bytes, stream);
-            if (e != cudaSuccess) return e;
+            // tail launch: one CTA per k part of every tile of the last, partial round ...
             slice_gemm_kernel<BN, true><<<static_cast<unsigned>(tp.tiles * tp.parts), THREADS, C_::SMEM_BYTES,
                                           stream>>>(mapA, mapB, p);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
-            ++nlaunch;
+            // ... and the fix-up: sum of the parts and recombination, one thread per row x 8 columns
+            const int64_t threads = static_cast<int64_t>(tp.tiles) * BM * (kEmuBNMax / 8);
+            tail_fixup_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, stream>>>(p);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            nlaunch += 2;
         }
         ++npass;
     }
@@ -941,7 +937,7 @@ size_t emu_scratch_bytes_tail(int64_t m, int64_t n, int64_t k, int S, int max_ct
     const int64_t kslabs = (k + emu::BK - 1) / emu::BK;
     const int64_t pass_slabs = emu_max_k_per_pass(S, beta) / emu::BK;
     const emu::TailPlan tp = emu::tail_plan(tiles, ctas, kslabs, pass_slabs, S, kMemberC2);
-    return base + tp.sums_bytes + tp.count_bytes;
+    return base + tp.sums_bytes;
 }
 
 size_t emu_scratch_bytes_for_ctas(int ctas) {
