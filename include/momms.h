@@ -58,6 +58,8 @@ enum {
 
 typedef enum { MOMMS_OP_N = 0, MOMMS_OP_T = 1 } momms_op_t;
 typedef enum { MOMMS_LOWER = 0, MOMMS_UPPER = 1 } momms_uplo_t;
+typedef enum { MOMMS_LEFT = 0, MOMMS_RIGHT = 1 } momms_side_t;
+typedef enum { MOMMS_NON_UNIT = 0, MOMMS_UNIT = 1 } momms_diag_t;
 
 /* How the product is computed.
  *   NATIVE    FP64 DMMA tensor instructions, C micro-tile resident in registers
@@ -238,6 +240,20 @@ size_t momms_emu_scratch_bytes_for(int64_t m, int64_t n, int64_t k, int slices);
  * (uplo -2, trans -3, n -4, k -5, A -7, lda -8, C -10, ldc -11), MOMMS_ERR_*. */
 int momms_syrk(momms_handle_t handle, int uplo, int trans, int64_t n, int64_t k, double alpha,
                const double* A, int64_t lda, double beta, double* C, int64_t ldc,
+               momms_stream_t stream);
+
+/* ------------------------------------------------------ triangular product */
+/* B := alpha*op(A)*B (side LEFT, A m x m) or B := alpha*B*op(A) (side RIGHT, A n x n),
+ * A triangular (uplo; diag UNIT: ones on the diagonal, which is not read), B m x n
+ * overwritten (BLAS dtrmm).  The triangle is first copied into a dense zero-filled
+ * operand kept by the handle; the product then runs as a GEMM in the handle's mode --
+ * emulated: in place (both operands are split into digits before the slice products
+ * write B); native: from a copy of B.  Device pointers, asynchronous on `stream`.  The
+ * bound is the GEMM one with the zero triangle counted as exact zeros.  Errors:
+ * BLAS-style negative index (side -2, uplo -3, trans -4, diag -5, m -6, n -7, A -9,
+ * lda -10, B -11, ldb -12), MOMMS_ERR_*. */
+int momms_trmm(momms_handle_t handle, int side, int uplo, int trans, int diag, int64_t m, int64_t n,
+               double alpha, const double* A, int64_t lda, double* B, int64_t ldb,
                momms_stream_t stream);
 
 /* ------------------------------------------------------- out-of-core product */

@@ -1270,6 +1270,87 @@ int momms_syrk(momms_handle_t h, int uplo, int trans, int64_t n, int64_t k, doub
     return MOMMS_OK;
 }
 
+// ------------------------------------------------------------------ triangular product
+namespace {
+
+// T (t x t, leading dimension t) := the uplo triangle of A with the other triangle zero and,
+// for a unit diagonal, ones on the diagonal (A's diagonal is then not read).
+__global__ void tri_extract_kernel(int64_t t, const double* __restrict__ A, int64_t lda, int uplo, int unit,
+                                   double* __restrict__ T) {
+    const int64_t total = t * t;
+    for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = idx % t, j = idx / t;
+        const bool inside = uplo == MOMMS_LOWER ? (i >= j) : (i <= j);
+        double v = 0.0;
+        if (i == j && unit) v = 1.0;
+        else if (inside) v = A[i + j * lda];
+        T[idx] = v;
+    }
+}
+
+}  // namespace
+
+int momms_trmm(momms_handle_t h, int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha,
+               const double* A, int64_t lda, double* B, int64_t ldb, momms_stream_t stream) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (side != MOMMS_LEFT && side != MOMMS_RIGHT) return -2;
+    if (uplo != MOMMS_LOWER && uplo != MOMMS_UPPER) return -3;
+    if (trans != MOMMS_OP_N && trans != MOMMS_OP_T) return -4;
+    if (diag != MOMMS_NON_UNIT && diag != MOMMS_UNIT) return -5;
+    if (m < 0) return -6;
+    if (n < 0) return -7;
+    const int64_t t = side == MOMMS_LEFT ? m : n;  // order of the triangular matrix
+    if (lda < std::max<int64_t>(1, t)) return -10;
+    if (ldb < std::max<int64_t>(1, m)) return -12;
+    if (m > 0 && n > 0 && alpha != 0.0 && !A) return -9;
+    if (m > 0 && n > 0 && !B) return -11;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->report = momms_report_t{};
+    if (m == 0 || n == 0) return MOMMS_OK;
+    if (alpha == 0.0) {
+        h->report.launches = 1;
+        return scale_c(m, n, 0.0, B, ldb, s);
+    }
+    // the triangle (zero elsewhere) as a dense t x t operand; B is overwritten with the product
+    const Plan p = pick_plan(h, m, n, t);
+    const bool emulated = p.mode == MOMMS_MODE_EMULATED;
+    const size_t tbytes = align256(static_cast<size_t>(t) * t * sizeof(double));
+    const size_t bbytes = emulated ? 0 : align256(static_cast<size_t>(m) * n * sizeof(double));
+    int rc = grow_device(&h->ooc_buf, &h->ooc_bytes, tbytes + bbytes);
+    if (rc) return rc;
+    double* T = static_cast<double*>(h->ooc_buf);
+    int64_t blocks = (t * t + 255) / 256;
+    blocks = std::min<int64_t>(blocks, int64_t(momms::device_sm_count()) * 16);
+    tri_extract_kernel<<<static_cast<unsigned>(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(t, A, lda, uplo, diag,
+                                                                                          T);
+    if (cudaGetLastError() != cudaSuccess) return MOMMS_ERR_CUDA;
+    int64_t launches = 1;
+    if (emulated) {
+        // in place: the emulated path splits both operands into digits before the slice products
+        // write C, and B is not read again (beta = 0)
+        rc = side == MOMMS_LEFT
+                 ? run_emulated(h, trans, MOMMS_OP_N, m, n, m, alpha, T, t, B, ldb, 0.0, B, ldb,
+                                p.member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : p.member, p.slices, s)
+                 : run_emulated(h, MOMMS_OP_N, trans, m, n, n, alpha, B, ldb, T, t, 0.0, B, ldb,
+                                p.member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : p.member, p.slices, s);
+    } else {
+        // the native kernel reads B while it writes C: product from a copy of B
+        double* Bc = reinterpret_cast<double*>(reinterpret_cast<char*>(h->ooc_buf) + tbytes);
+        if (cudaMemcpy2DAsync(Bc, static_cast<size_t>(m) * sizeof(double), B, static_cast<size_t>(ldb) * sizeof(double),
+                              static_cast<size_t>(m) * sizeof(double), static_cast<size_t>(n),
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        const int member = p.member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : p.member;
+        rc = side == MOMMS_LEFT
+                 ? run_native(h, trans, MOMMS_OP_N, m, n, m, alpha, T, t, Bc, m, 0.0, B, ldb, member, s)
+                 : run_native(h, MOMMS_OP_N, trans, m, n, n, alpha, Bc, m, T, t, 0.0, B, ldb, member, s);
+    }
+    if (rc) return rc;
+    h->report.launches += launches;
+    return MOMMS_OK;
+}
+
 // ------------------------------------------------------------------ out-of-core products
 // Host memory (Grace LPDDR over NVLink-C2C on GB300) is the slow level and HBM the fast one:
 // Resident C at the HBM level (Sec. 2.2.1).  A b x b block of C stays in HBM while b x b

@@ -29,6 +29,8 @@ MOMMS_ERR_IO = 1008
 
 OP_N, OP_T = 0, 1
 LOWER, UPPER = 0, 1
+LEFT, RIGHT = 0, 1
+NON_UNIT, UNIT = 0, 1
 MODE_AUTO, MODE_NATIVE, MODE_EMULATED = 0, 1, 2
 MEMBER_AUTO, MEMBER_C2, MEMBER_A2, MEMBER_B2, MEMBER_A1 = 0, 1, 2, 3, 4
 MEMBER_NAMES = {MEMBER_C2: "C2", MEMBER_A2: "A2", MEMBER_B2: "B2", MEMBER_A1: "A1"}
@@ -73,6 +75,7 @@ _SIGS = {
     "momms_gemm_ex": ([_VP, _I32, _I32, _I64, _I64, _I64, _DBL, _VP, _I64, _VP, _I64, _DBL, _VP, _I64, _VP], _I32),
     "momms_gemm_host": ([_VP, _I64, _I64, _I64, _DBL, _VP, _I64, _VP, _I64, _DBL, _VP, _I64, _SZ, _I64, _VP], _I32),
     "momms_syrk": ([_VP, _I32, _I32, _I64, _I64, _DBL, _VP, _I64, _DBL, _VP, _I64, _VP], _I32),
+    "momms_trmm": ([_VP, _I32, _I32, _I32, _I32, _I64, _I64, _DBL, _VP, _I64, _VP, _I64, _VP], _I32),
     "momms_gemm_backward": ([_VP, _I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _VP], _I32),
     "momms_gemm_batched": ([_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I32),
     "momms_emu_scale": ([_I32, _I32, _I64, _I64, _VP, _I64, _VP, _VP, _VP], _I32),
@@ -160,6 +163,11 @@ def momms_gemm_host(handle, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, device
 
 def momms_syrk(handle, uplo, trans, n, k, alpha, A, lda, beta, C, ldc, stream=None):
     return lib().momms_syrk(_h(handle), uplo, trans, n, k, alpha, _VP(A), lda, beta, _VP(C), ldc, _stream(stream))
+
+
+def momms_trmm(handle, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, stream=None):
+    return lib().momms_trmm(_h(handle), side, uplo, trans, diag, m, n, alpha, _VP(A), lda, _VP(B), ldb,
+                            _stream(stream))
 
 
 def momms_gemm_backward(handle, m, n, k, A, lda, B, ldb, dC, lddc, dA, ldda, dB, lddb, stream=None):

@@ -74,6 +74,7 @@ def test_null_handle_is_rejected(L):
     assert M.momms_gemm_host(None, 4, 4, 4, 1.0, 1 << 40, 4, 1 << 41, 4, 0.0, 1 << 42, 4, stream=0) == \
         M.MOMMS_ERR_HANDLE
     assert M.momms_syrk(None, 0, 0, 4, 4, 1.0, 1 << 40, 4, 0.0, 1 << 41, 4, stream=0) == M.MOMMS_ERR_HANDLE
+    assert M.momms_trmm(None, 0, 0, 0, 0, 4, 4, 1.0, 1 << 40, 4, 1 << 41, 4, stream=0) == M.MOMMS_ERR_HANDLE
 
 
 def test_stream_copy_validates_before_launch(L):
