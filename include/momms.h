@@ -128,6 +128,13 @@ int momms_set_max_ctas(momms_handle_t handle, int ctas);
  * order, so waves straddling two groups are included); 16 for the native kernel.
  * Single-product calls only.  Returns -2 for group < 0. */
 int momms_set_raster_group(momms_handle_t handle, int group);
+/* Emulated tile width: 192 (wide: half the int32 sums in spare TMEM, the int64 group sums of
+ * the recombination in a global scratch block) or 96 (narrow: every sum in registers and the
+ * group sums in TMEM, so a diagonal's recombination stays on chip; twice the operand-tile
+ * reloads per flop).  0 = automatic: 96 when the 192-wide tiles would be fewer than the SMs
+ * (small products: more SMs at work), else 192.  Results are bit-identical either way.
+ * Single-product calls only.  Returns -2 for other values. */
+int momms_set_tile_n(momms_handle_t handle, int tile_n);
 int momms_get_last_report(momms_handle_t handle, momms_report_t* report);
 /* Device status word of the handle (0 = fine, MOMMS_ERR_TIMEOUT after a capped
  * wait expired).  Synchronises `stream` first.  Clears the word. */

@@ -54,12 +54,17 @@ constexpr uint32_t A_TILE = BM * BK * 2;                 // 16 KB
 constexpr uint32_t TMEM_COLS = 512;                      // two BN-column FP32 accumulators
 constexpr size_t SMEM_BUDGET = 225 * 1024;
 
+// Two tile widths.  BN = 192: a drain thread owns 64 columns, the int32 sums of 32 in registers
+// and of 32 in spare TMEM, the int64 group sums Q in a global scratch block.  BN = 96 (small k
+// or narrow n): 32 columns, all sums in registers, and Q in TMEM next to the accumulators --
+// the recombination of a diagonal then makes no round trip to L2.
 template <int BN>
 struct Cfg {
-    static_assert(BN == 192, "three drain warps per quadrant of 64 columns; spare TMEM holds half the sums");
-    static constexpr int CW = BN / 3;                    // columns per drain warp (64)
+    static_assert(BN == 192 || BN == 96, "three drain warps per TMEM lane quadrant");
+    static constexpr int CW = BN / 3;                    // columns per drain warp (64 or 32)
     static constexpr int CR = 32;                        // of which summed in registers
     static constexpr int CT = CW - CR;                   // and summed as int32 in spare TMEM columns
+    static constexpr bool QT = (BN == 96);               // int64 group sums in TMEM
     static constexpr uint32_t B_TILE = BN * BK * 2;
     static constexpr uint32_t STAGE = A_TILE + B_TILE;
     static constexpr int STAGES = static_cast<int>((SMEM_BUDGET - 2048) / STAGE) > 6
@@ -182,6 +187,8 @@ MOMMS_DEV double scale_pow2(double r, int E) {
 struct RecombineCtx {
     long long* Q;
     double* R;
+    uint32_t qt;       // TMEM address of the thread's int64 group sums (tile width 96): low words at
+                       // qt + c, high words at qt + 32 + c for column c
     uint64_t keep;     // L2 policy of the scratch accesses (evict last)
     uint32_t tsum;     // TMEM address of the int32 sums of the last CT columns
     int sh;            // beta * (position of d in its group)
@@ -205,21 +212,42 @@ enum { kMid = 0, kGroupEnd = 1, kLast = 2 };
 constexpr int BM_ = kEmuBM;
 
 // 8 columns [c0, c0 + 8): exact int64 group sum, FP64 fold at the group end, C at the end.
-template <int MODE>
+template <int MODE, bool QT = false>
 MOMMS_DEV void recombine8(const RecombineCtx& rc, const int32_t (&pv)[8], int c0, const FinalCtx* fc) {
     long long qv[8];
     double rv[8];
+    if constexpr (QT) {
+        if (!rc.gfirst) {
+            uint32_t lo[8], hi[8];
+            tmem_ld_32x32b_x8(rc.qt + c0, lo);
+            tmem_ld_32x32b_x8(rc.qt + 32 + c0, hi);
+            tmem_ld_wait(lo);
+            tmem_ld_wait(hi);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                qv[j] = static_cast<long long>((static_cast<unsigned long long>(hi[j]) << 32) | lo[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) qv[j] = 0ll;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        qv[j] = rc.gfirst ? 0ll : ld_l2_hint(rc.Q + (c0 + j) * BM_, rc.keep);
+        if constexpr (!QT) qv[j] = rc.gfirst ? 0ll : ld_l2_hint(rc.Q + (c0 + j) * BM_, rc.keep);
         if (MODE != kMid) rv[j] = rc.rfirst ? 0.0 : ld_l2_hint(rc.R + (c0 + j) * BM_, rc.keep);
     }
+    uint32_t qlo[8], qhi[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const long long p64 = static_cast<long long>(pv[j]);
         const long long v = rc.gfirst ? p64 : qv[j] + (p64 << rc.sh);
         if (MODE == kMid) {
-            st_l2_hint(rc.Q + (c0 + j) * BM_, v, rc.keep);
+            if constexpr (QT) {
+                qlo[j] = static_cast<uint32_t>(static_cast<unsigned long long>(v));
+                qhi[j] = static_cast<uint32_t>(static_cast<unsigned long long>(v) >> 32);
+            } else {
+                st_l2_hint(rc.Q + (c0 + j) * BM_, v, rc.keep);
+            }
         } else {
             const double x = static_cast<double>(v);
             const double r = (rc.rfirst ? x : fma(rv[j], rc.rb, x)) * rc.gscale;
@@ -234,17 +262,25 @@ MOMMS_DEV void recombine8(const RecombineCtx& rc, const int32_t (&pv)[8], int c0
             }
         }
     }
+    if constexpr (QT) {
+        if (MODE == kMid) {
+            tmem_st_32x32b_x8(rc.qt + c0, qlo);
+            tmem_st_32x32b_x8(rc.qt + 32 + c0, qhi);
+            tmem_st_wait();
+        }
+    }
     asm volatile("" ::: "memory");  // one batch of loads in flight at a time
 }
 
 template <int MODE, int CR, int CT>
 MOMMS_DEV void recombine(const RecombineCtx& rc, const int32_t (&acc)[CR], const FinalCtx* fc) {
+    constexpr bool QT = (CT == 0);  // the narrow tile keeps every sum in registers and Q in TMEM
 #pragma unroll
     for (int b = 0; b < CR / 8; ++b) {
         int32_t pv[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) pv[j] = acc[b * 8 + j];
-        recombine8<MODE>(rc, pv, b * 8, fc);
+        recombine8<MODE, QT>(rc, pv, b * 8, fc);
     }
 #pragma unroll
     for (int q = 0; q < CT / 16; ++q) {
@@ -282,7 +318,7 @@ MOMMS_DEV void recombine_diagonal(const Params& p, int prob, int tm, int tn, int
     constexpr int CW = BN / 3;
     const bool gfirst = (gj == 0);
     const bool gend = (pr.group_end >> d) & 1u;
-    const RecombineCtx rc{Q, R, keep, tsum, pr.beta * gj, pow2_normal(-pr.beta * gj), rb, gfirst, rfirst};
+    const RecombineCtx rc{Q, R, tsum, keep, tsum, pr.beta * gj, pow2_normal(-pr.beta * gj), rb, gfirst, rfirst};
     if (!gend) {
         recombine<kMid, CR, CT>(rc, acc, nullptr);
     } else if (d != 2) {
@@ -663,7 +699,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int third = (warp - CTRL_WARPS) >> 2;        // columns [CW*third, CW*third + CW)
         const int rloc = quad * 32 + lane;                 // row within the tile
         const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
-        const uint32_t tsum = tmem_base + lane_off + (third < 2 ? 192u + 32u * third : 448u);
+        // wide tile: half the int32 sums in TMEM columns 192..255 / 448..511; narrow tile: the int64
+        // group sums Q in TMEM columns 96..223 / 352..415 (64 per third: low and high words)
+        const uint32_t tsum = C_::QT ? tmem_base + lane_off + (third < 2 ? 96u + 64u * third : 352u)
+                                     : tmem_base + lane_off + (third < 2 ? 192u + 32u * third : 448u);
         uint32_t abuf = 0;
         uint32_t aphase[2] = {0u, 0u};
         const double qnan = __longlong_as_double(0x7ff8000000000000ll);
@@ -812,7 +851,7 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     const int64_t pass_slabs = emu_max_k_per_pass(a.S, a.beta) / BK;
     if (kslabs <= 0 || pass_slabs <= 0) return cudaErrorInvalidValue;
     const int member = a.member == kMemberAuto ? kMemberC2 : a.member;
-    TailPlan tp = tail_plan(tiles, ctas, kslabs, pass_slabs, a.S, member);
+    TailPlan tp = BN == kEmuBNMax ? tail_plan(tiles, ctas, kslabs, pass_slabs, a.S, member) : TailPlan{};
     if (tp.parts && a.scratch_bytes < 2 * half + tp.sums_bytes) tp = TailPlan{};  // whole tiles
     char* tail_base = static_cast<char*>(a.scratch) + 2 * half;
     int npass = 0, nlaunch = 0;
@@ -986,7 +1025,15 @@ int emu_chunk_slabs(int beta) {
     return slabs < 1 ? 1 : slabs;
 }
 
-int emu_pick_bn(int64_t, int) { return 192; }
+// Tile width: an explicit request of 96 or 192, else the narrow tile only when the wide tiles
+// are fewer than the SMs (the narrow ones then put more of the chip to work; measured: 1024^3
+// +28 %).  With enough wide tiles the narrow one loses -- twice the tiles' fixed costs and 40 %
+// more operand traffic per flop (rank-k 16384 x 16384 x 256: -10 %, panel: -16 %).
+int emu_pick_bn(int64_t m, int64_t n, int64_t, int requested) {
+    if (requested == 96 || requested == 192) return requested;
+    const int64_t wide_tiles = ((m + emu::BM - 1) / emu::BM) * ((n + kEmuBNMax - 1) / kEmuBNMax);
+    return wide_tiles < device_sm_count() ? 96 : 192;
+}
 
 // The C2 group (tile rows of the block of C one wave covers) with the fewest operand rows
 // read over all waves: a wave of `ctas` consecutive tiles of the raster reads the A rows of
@@ -1036,6 +1083,7 @@ cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_
     if (emu_chunk_slabs(a.beta) * BK * ((1ll << a.beta) - 1) * ((1ll << a.beta) - 1) > (1ll << 24))
         return cudaErrorInvalidValue;  // beta too wide for one 64-wide slab per chunk
     if (a.m > (1ll << 30) || a.n > (1ll << 30)) return cudaErrorInvalidValue;
+    if (emu_pick_bn(a.m, a.n, a.k, a.tile_n) == 96) return launch_bn<96>(a, passes, stream);
     return launch_bn<192>(a, passes, stream);
 }
 

@@ -70,7 +70,7 @@ struct EmuGemmArgs {
     size_t scratch_bytes;
     int32_t* status;
     int max_ctas;  // 0 = number of SMs
-    int tile_n;    // CTA tile width request (only 192 is built; 0 = automatic)
+    int tile_n;    // CTA tile width request (96 or 192; 0 = automatic)
     int* used_ctas;   // optional out: persistent CTAs launched
     int* used_group;  // optional out: C2 raster group used
     int* used_launches;  // optional out: kernels launched (a tail launch per pass when split)
@@ -132,7 +132,7 @@ cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int 
                                           void* scratch, size_t scratch_bytes, int32_t* status,
                                           cudaStream_t stream);
 // The CTA tile width used for n columns (tile_n request 0 = automatic).
-int emu_pick_bn(int64_t n, int requested);
+int emu_pick_bn(int64_t m, int64_t n, int64_t k, int requested);
 // Default C2 group of the slice-product kernel for `ctas` persistent CTAs (tile rows of the
 // block of C one wave covers; fewest operand rows read per unit of k over all waves).
 int emu_default_group(int64_t ctas, int tiles_m, int tiles_n);

@@ -66,6 +66,7 @@ _SIGS = {
     "momms_set_slices": ([_VP, _I32], _I32),
     "momms_set_max_ctas": ([_VP, _I32], _I32),
     "momms_set_raster_group": ([_VP, _I32], _I32),
+    "momms_set_tile_n": ([_VP, _I32], _I32),
     "momms_get_last_report": ([_VP, ctypes.POINTER(Report)], _I32),
     "momms_check_device_status": ([_VP, _VP], _I32),
     "momms_status_string": ([_I32], ctypes.c_char_p),
@@ -271,6 +272,9 @@ class Handle:
 
     def set_raster_group(self, group):
         check(lib().momms_set_raster_group(self.ptr, group), "momms_set_raster_group")
+
+    def set_tile_n(self, tile_n):
+        check(lib().momms_set_tile_n(self.ptr, tile_n), "momms_set_tile_n")
 
     def report(self):
         r = Report()

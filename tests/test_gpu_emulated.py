@@ -325,3 +325,30 @@ def test_scratch_for_any_shape_covers_the_step_entry_minimum():
     base = M.momms_emu_scratch_bytes()
     for m, n, k, S in [(100, 100, 100, 4), (1024, 1024, 1024, 6), (8192, 8192, 8192, 6), (1, 1, 1, 1)]:
         assert M.momms_emu_scratch_bytes_for(m, n, k, S) >= base
+
+
+@pytest.mark.parametrize("m,n,k,S,opa,opb", [
+    (300, 650, 200, 8, 0, 0),     # ragged in m and n, one group
+    (257, 200, 1500, 9, 1, 0),    # two int64 groups (FP64 fold between them), op(A) = A^T
+    (130, 97, 64, 12, 0, 1),      # one k slab, op(B) = B^T, many groups
+    (700, 400, 3000, 7, 1, 1),    # both transposed
+])
+def test_emulated_tile_widths_bitwise_identical(m, n, k, S, opa, opb):
+    # the narrow tile (96 columns, group sums in tensor memory) and the wide one (192, group sums
+    # in a global scratch block) do the same exact integer sums and the same FP64 operations
+    A = syn.matrix("uniform", k if opa else m, m if opa else k, 1401)
+    B = syn.matrix("uniform", n if opb else k, k if opb else n, 1402)
+    C0 = syn.matrix("uniform", m, n, 1403)
+    outs = []
+    for tn in (96, 192):
+        h = M.Handle(mode=M.MODE_EMULATED, slices=S)
+        h.set_tile_n(tn)
+        dA, dB, dC = (M.DeviceMatrix.from_numpy(X) for X in (A, B, C0))
+        M.gemm(dA, dB, dC, 0.5, -1.0, opa, opb, handle=h)
+        assert h.device_status() == M.MOMMS_OK
+        assert h.report()["tile_n"] == tn
+        outs.append(dC.to_numpy())
+        h.close()
+    assert np.array_equal(outs[0], outs[1])
+    Cref, N = reference(A, B, C0, 0.5, -1.0, bool(opa), bool(opb))
+    assert max_ratio(outs[0], Cref, k, 0.5, -1.0, N, C0) <= 1.0
