@@ -82,6 +82,9 @@ struct momms_handle_s {
     size_t ooc_bytes = 0;
     cudaStream_t ooc_in = nullptr, ooc_out = nullptr;
     cudaEvent_t ooc_ev[11] = {};
+    // the B operand's scale and split run on a second stream beside A's (fork / join events)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -244,6 +247,22 @@ int run_native(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t
     return MOMMS_OK;
 }
 
+int ensure_aux(momms_handle_t h) {
+    if (!h->aux && cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess) return MOMMS_ERR_CUDA;
+    if (!h->ev_fork && cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    if (!h->ev_join && cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    return MOMMS_OK;
+}
+
+// The work on the second stream joins the caller's stream.
+int join_aux(momms_handle_t h, cudaStream_t s) {
+    if (cudaEventRecord(h->ev_join, h->aux) != cudaSuccess || cudaStreamWaitEvent(s, h->ev_join, 0) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    return MOMMS_OK;
+}
+
 int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                  int64_t ldc, int member, int S, cudaStream_t s) {
@@ -268,9 +287,17 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     int64_t launches = 0;
     cudaError_t ce;
     const bool need_stats = (S == 0);
+    // A's scale and split run on the caller's stream, B's on a second stream forked from it, so
+    // that the two HBM-bound passes overlap; the slice products wait for both.
+    rc = ensure_aux(h);
+    if (rc) return rc;
+    cudaStream_t sb = h->aux;
+    if (need_stats && cudaMemsetAsync(h->spread_dev, 0, 2 * sizeof(int), s) != cudaSuccess) return MOMMS_ERR_CUDA;
+    if (cudaEventRecord(h->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(sb, h->ev_fork, 0) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
     ce = momms::launch_emu_scale(0, opa, m, k, A, lda, e, ef, need_stats ? l1a : nullptr, s);
     if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-    ce = momms::launch_emu_scale(1, opb, n, k, B, ldb, f, ff, need_stats ? l1b : nullptr, s);
+    ce = momms::launch_emu_scale(1, opb, n, k, B, ldb, f, ff, need_stats ? l1b : nullptr, sb);
     if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
     launches += momms::emu_scale_kernel_count(0, opa) + momms::emu_scale_kernel_count(1, opb);
     double est = 0.0;
@@ -279,9 +306,10 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
         // Data-driven slice count: the spreads are reduced on the device and read back.  While the
         // readback is in flight the digits are already split for a guessed S (the last call's):
         // a slice's digits do not depend on S, so only missing slices are added afterwards.
-        if (cudaMemsetAsync(h->spread_dev, 0, 2 * sizeof(int), s) != cudaSuccess) return MOMMS_ERR_CUDA;
         if (momms::launch_emu_spread(m, k, e, ef, l1a, h->spread_dev, s) != cudaSuccess) return MOMMS_ERR_CUDA;
-        if (momms::launch_emu_spread(n, k, f, ff, l1b, h->spread_dev + 1, s) != cudaSuccess) return MOMMS_ERR_CUDA;
+        if (momms::launch_emu_spread(n, k, f, ff, l1b, h->spread_dev + 1, sb) != cudaSuccess) return MOMMS_ERR_CUDA;
+        rc = join_aux(h, s);  // the readback needs both spreads
+        if (rc) return rc;
         if (cudaMemcpyAsync(h->spread_host, h->spread_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return MOMMS_ERR_CUDA;
         if (!h->spread_ready || cudaEventRecord(h->spread_ready, s) != cudaSuccess) return MOMMS_ERR_CUDA;
@@ -289,24 +317,26 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
         const int guess = std::min(std::max(h->last_auto_slices, 1), S_alloc);
         ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, guess, bb, Ad, L.m_pad, L.k_pad, s);
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-        ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, guess, bb, Bd, L.n_pad, L.k_pad, s);
+        ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, guess, bb, Bd, L.n_pad, L.k_pad, sb);
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
         launches += 2;
         split_done = guess;
         if (cudaEventSynchronize(h->spread_ready) != cudaSuccess) return MOMMS_ERR_CUDA;
-        const double sa = h->spread_host[0] / 16.0, sb = h->spread_host[1] / 16.0;
+        const double sa = h->spread_host[0] / 16.0, sbs = h->spread_host[1] / 16.0;
         double bits = 0.0;
-        S = slices_from_spread(sa, sb, k, bb, &bits);
+        S = slices_from_spread(sa, sbs, k, bb, &bits);
         est = 0.1 * std::exp2(bits - static_cast<double>(bb) * S);  // the rule keeps a 10x margin
         h->last_auto_slices = S;
     }
     if (S > split_done) {
         ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, S, bb, Ad, L.m_pad, L.k_pad, s, split_done);
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-        ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, S, bb, Bd, L.n_pad, L.k_pad, s, split_done);
+        ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, S, bb, Bd, L.n_pad, L.k_pad, sb, split_done);
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
         launches += 2;
     }
+    rc = join_aux(h, s);  // the slice products need B's exponents and digits
+    if (rc) return rc;
     momms::EmuGemmArgs a{};
     a.m = m; a.n = n; a.k = k; a.S = S; a.beta = bb;
     a.Ad = Ad; a.Bd = Bd; a.m_pad = L.m_pad; a.n_pad = L.n_pad; a.k_pad = L.k_pad;
@@ -622,6 +652,9 @@ int momms_destroy(momms_handle_t h) {
     if (h->ooc_out) cudaStreamDestroy(h->ooc_out);
     for (cudaEvent_t e : h->ooc_ev)
         if (e) cudaEventDestroy(e);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     h->magic = 0;
     delete h;
     return MOMMS_OK;
