@@ -214,7 +214,9 @@ int momms_emu_split(int which, int op, int64_t rows, int64_t inner, const double
 
 /* Slice products and recombination on the tcgen05 tensor cores:
  *   P_d = sum_{s+t=d} A_s B_t  (d = 2..S+1, triangular pair set), exact;
- *   C := alpha * 2^(e_i+f_j) * sum_d 2^(-beta d) P_d + beta*C  (FP64 Horner).
+ *   C := alpha * 2^(e_i+f_j) * sum_d 2^(-beta d) P_d + beta*C, the diagonals combined
+ *   exactly in int64 groups and in FP64 only between groups (one rounding when a single
+ *   group covers all diagonals).
  * Ad: S slices of m_pad x k_pad, Bd: S slices of n_pad x k_pad (layout above,
  * m_pad >= m, n_pad >= n, k_pad a multiple of 64; digit_bits <= 8).
  * scratch: device memory of at least momms_emu_scratch_bytes() bytes (int64 / FP64

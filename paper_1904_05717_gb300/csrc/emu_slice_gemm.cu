@@ -1,33 +1,36 @@
 // emu_slice_gemm.cu -- the slice products of the emulated FP64 product on the
 // fifth-generation tensor cores, with the recombination fused into the epilogue.
 //
-// For a C tile (BM x BN = 128 x 256) the kernel computes, for every diagonal
+// For a C tile (BM x BN = 128 x 192, or 128 x 96) the kernel computes, for every diagonal
 // d = S+1 down to 2 of the triangular pair set,
 //     P_d = sum_{s+t=d} A_s B_t          (A_s, B_t: integer digit slices in fp16)
-// exactly, and folds it into the FP64 Horner sum
-//     R_{S+1} = P_{S+1},   R_d = P_d + 2^-beta R_{d+1},
-// so that C := alpha * 2^(e_i + f_j - 2 beta) R_2 + beta_c C.
+// exactly, and combines the diagonals from the least significant one: consecutive
+// diagonals exactly in int64, Q = sum_j P_{hi-j} 2^(beta j), for as many as the host proves
+// stay below 2^63 (emu_group_ends); FP64 only where a group ends,
+// R = 2^(-beta (hi-lo)) (Q + 2^-beta R_prev); and at d = 2
+//     C := alpha * 2^(e_i + f_j - 2 beta) R + beta_c C.
 //
-// Exactness.  A tcgen05 kind::f16 MMA multiplies fp16 integers exactly and
-// accumulates in FP32 in tensor memory (TMEM).  Every partial sum of at most
-// `chunk` products of digits |d| <= 2^beta - 1 stays an integer below 2^24, so
-// the FP32 accumulator is exact; after each chunk the accumulator is drained
-// (tcgen05.ld -> exact float->int conversion -> int32 add in registers).  The
-// int32 diagonal sums stay below 2^31 because one launch covers at most
+// Exactness.  A tcgen05 kind::f16 MMA multiplies fp16 integers exactly and accumulates in
+// FP32 in tensor memory (TMEM).  Every partial sum of at most `chunk` products of digits
+// |d| <= 2^beta - 1 stays an integer below 2^24, so the FP32 accumulator is exact; after each
+// chunk the accumulator is drained (tcgen05.ld -> exact float->int conversion -> int32 add).
+// The int32 diagonal sums stay below 2^31 because one launch covers at most
 // emu_max_k_per_pass(S, beta) of k.
 //
-// Memory levels (the paper's Sec. 3.3 vocabulary): the C tile is the resident
-// block of registers/TMEM (Resident C at L0, Sec. 3.4); A and B digit tiles are
-// streamed through a 4-stage shared-memory ring by TMA; which panels stay in L2
-// is set by the member's tile order (raster.cuh).
+// Memory levels (the paper's Sec. 3.3 vocabulary): the C tile is the resident block of
+// TMEM/registers (Resident C at L0, Sec. 3.4); A and B digit tiles stream through a
+// multi-stage shared-memory ring filled by TMA; which panels stay in L2 is set by the
+// member's tile order (raster.cuh).
 //
-// Roles (320 threads): warp 0 = TMA producer (one thread), warp 1 = TMEM owner
-// and MMA issuer (one thread), warps 2..9 = drain / recombination; each drain
-// thread holds the 128 int32 diagonal sums of its row in registers.  TMEM holds
-// two 256-column FP32 accumulators so that draining one overlaps MMAs into the
-// other.  Every mbarrier wait is bounded; on expiry the kernel raises a CTA-wide
-// abort flag, lets in-flight copies and MMAs finish, frees TMEM, and reports
-// status 1002 (timeout) through p.status.
+// Roles (512 threads, one CTA per SM): warp 0 = TMA producer (one thread), warp 1 = TMEM
+// owner and MMA issuer (one thread), warps 4..15 = drain / recombination, three per TMEM
+// lane quadrant, each thread one row and BN/3 columns.  TMEM holds two FP32 accumulators
+// (columns 0 and 256) so that draining one overlaps MMAs into the other; the rest holds
+// half of the int32 sums (wide tile) or the int64 group sums (narrow tile).  Every mbarrier
+// wait is bounded; on expiry the kernel raises a CTA-wide abort flag, lets in-flight copies
+// and MMAs finish, frees TMEM, and reports status 1002 (timeout) through p.status.
+// A single-problem launch may be followed by a tail launch (the last, partial round of
+// tiles cut along k) and a fix-up launch that adds the parts and recombines.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
