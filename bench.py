@@ -40,8 +40,14 @@ METRIC = "FP64-accurate GEMM TFLOP/s (2mnk/t) & % roofline, native vs emulated"
 # with that call's algorithmic tensor flops; other sizes scale it by the tensor flops.  Set to
 # None whenever the slice-product kernels change until they are captured again.
 NCU_SLICE_CAPTURE = {"dram_bytes": (27.75e9 + 0.706e9 + 0.087e9) + (1.93e9 + 0.0545e9),
-                     "tensor_flops": 21 * 2.0 * 8192 ** 3}
+                     "tensor_flops": 21 * 2.0 * 8192 ** 3,
+                     "source": "ncu capture of the 8192^3 call, scaled by tensor flops for other sizes "
+                               "(profiles/slice_gemm_members_8192.md)"}
+# The same for the residue-product launch of the modular encoding (None: not captured since
+# the kernel last changed).
+NCU_RESIDUE_CAPTURE = None
 UNIT = "TFLOP/s"
+SCHEMES = {"auto": 0, "slices": 1, "moduli": 2}  # momms_scheme_t
 
 
 def parse():
@@ -57,6 +63,8 @@ def parse():
                         "batched: 2000 problems, m, n, k log-uniform in [32, 2048]; "
                         "host: m=n=k=size with A, B, C in pinned host memory (momms_gemm_host)")
     p.add_argument("--block", type=int, default=0, help="momms_gemm_host block size (0 = from the budget)")
+    p.add_argument("--scheme", default="auto", choices=["auto", "slices", "moduli"],
+                   help="integer encoding of the emulated product (momms_set_scheme)")
     p.add_argument("--device-gb", type=float, default=0.0, help="momms_gemm_host device budget (0 = half free)")
     p.add_argument("--mode", default="auto", choices=["auto", "native", "emulated"])
     p.add_argument("--member", default="auto", choices=["auto", "C2", "A2", "B2", "A1"])
@@ -291,7 +299,7 @@ def run_side_workload(args):
     M.lib(build_if_missing=True)
     stream = torch.cuda.current_stream()
     mode = {"auto": M.MODE_AUTO, "native": M.MODE_NATIVE, "emulated": M.MODE_EMULATED}[args.mode]
-    h = M.Handle(mode=mode, slices=args.slices)
+    h = M.Handle(mode=mode, slices=args.slices, scheme=SCHEMES[args.scheme])
     keep = []
     io = {}
     if args.shape == "host":
@@ -401,7 +409,7 @@ def main():
     dC = M.DeviceMatrix.from_numpy(C_h)
     dC0 = dC.storage.clone()
 
-    h = M.Handle(mode=mode, member=member, slices=args.slices)
+    h = M.Handle(mode=mode, member=member, slices=args.slices, scheme=SCHEMES[args.scheme])
     h.set_raster_group(args.group)
     h.set_max_ctas(args.ctas)
 
@@ -430,8 +438,9 @@ def main():
     clocks = clk.summary()
     status = h.device_status(stream)
 
-    # ---- dominant kernel alone (same digits, same launch configuration), per-launch CUDA events
+    # ---- dominant kernel alone (same digits or residues, same launch configuration), per-launch CUDA events
     S, bb = int(rep["slices"]), int(rep["digit_bits"])
+    n_mod, op_bits = int(rep["moduli"]), int(rep["operand_bits"])
     roof = None
     if rep["mode"] == M.MODE_EMULATED:
         k_pad = -(-k // 64) * 64
@@ -439,41 +448,67 @@ def main():
         f = torch.empty(n, dtype=torch.int32, device="cuda"); ff = torch.empty(n, dtype=torch.uint8, device="cuda")
         M.check(M.momms_emu_scale(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), stream), "scale")
         M.check(M.momms_emu_scale(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), stream), "scale")
-        Ad = torch.empty((S, m, k_pad), dtype=torch.float16, device="cuda")
-        Bd = torch.empty((S, n, k_pad), dtype=torch.float16, device="cuda")
-        M.check(M.momms_emu_split(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), S, bb, Ad.data_ptr(), m, k_pad, stream), "split")
-        M.check(M.momms_emu_split(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), S, bb, Bd.data_ptr(), n, k_pad, stream), "split")
-        nbytes = M.momms_emu_scratch_bytes_for(m, n, k, S)
-        scratch = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
+        planes = n_mod if n_mod else S
+        Ad = torch.empty((planes, m, k_pad), dtype=torch.float16, device="cuda")
+        Bd = torch.empty((planes, n, k_pad), dtype=torch.float16, device="cuda")
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
-        Cs = M.DeviceMatrix(m, n)
+        if n_mod:
+            # modular encoding: the residue planes, then one residue product per modulus
+            M.check(M.momms_emu_residues(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), op_bits, k,
+                                         Ad.data_ptr(), m, k_pad, stream), "residues")
+            M.check(M.momms_emu_residues(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), op_bits, k,
+                                         Bd.data_ptr(), n, k_pad, stream), "residues")
+            nbytes = M.momms_emu_scratch_bytes()
+            scratch = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
+            res = torch.empty(n_mod * m * n, dtype=torch.uint8, device="cuda")
+
+            def product():
+                M.check(M.momms_emu_residue_gemm(m, n, k, op_bits, Ad.data_ptr(), Bd.data_ptr(), m, n, k_pad,
+                                                 int(rep["member"]), res.data_ptr(), scratch.data_ptr(), nbytes,
+                                                 st.data_ptr(), stream), "residue gemm")
+            products = n_mod
+            kernel = (f"momms::emu::slice_gemm_kernel<{int(rep['tile_n'])}, 0, 1> (tcgen05 kind::f16; modular "
+                      f"encoding: one residue product per modulus)")
+            capture = NCU_RESIDUE_CAPTURE
+        else:
+            M.check(M.momms_emu_split(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), S, bb, Ad.data_ptr(),
+                                      m, k_pad, stream), "split")
+            M.check(M.momms_emu_split(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), S, bb, Bd.data_ptr(),
+                                      n, k_pad, stream), "split")
+            nbytes = M.momms_emu_scratch_bytes_for(m, n, k, S)
+            scratch = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
+            Cs = M.DeviceMatrix(m, n)
+
+            def product():
+                M.check(M.momms_emu_slice_gemm(m, n, k, S, bb, Ad.data_ptr(), Bd.data_ptr(), m, n, k_pad,
+                                               e.data_ptr(), ef.data_ptr(), f.data_ptr(), ff.data_ptr(), 1.0, 0.0,
+                                               Cs.ptr, Cs.ld, int(rep["member"]), scratch.data_ptr(), nbytes,
+                                               st.data_ptr(), stream), "slice gemm")
+            products = S * (S + 1) // 2
+            kernel = f"momms::emu::slice_gemm_kernel<{int(rep['tile_n'])}, 0|1> (tcgen05 kind::f16; main + tail launch)"
+            capture = NCU_SLICE_CAPTURE
         evs = []
         reps = max(3, min(args.steps, 10))
         for i in range(reps + 1):
             a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-            M.check(M.momms_emu_slice_gemm(m, n, k, S, bb, Ad.data_ptr(), Bd.data_ptr(), m, n, k_pad,
-                                           e.data_ptr(), ef.data_ptr(), f.data_ptr(), ff.data_ptr(), 1.0, 0.0,
-                                           Cs.ptr, Cs.ld, int(rep["member"]), scratch.data_ptr(), nbytes,
-                                           st.data_ptr(), stream), "slice gemm")
+            product()
             a1.record(stream)
             if i > 0:  # first launch is a warm-up
                 evs.append((a0, a1))
         torch.cuda.synchronize()
         slice_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
-        pairs = S * (S + 1) // 2
-        tensor_flops = pairs * 2.0 * m * n * k  # algorithmic: every digit-pair product of the problem
+        tensor_flops = products * 2.0 * m * n * k  # algorithmic: every digit-pair / residue product
         achieved = tensor_flops / (slice_ms * 1e-3) / 1e12
         peaks, src = measured_peaks()
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         traffic = None
-        if NCU_SLICE_CAPTURE is not None and args.shape == "square" and args.member in ("auto", "C2"):
-            traffic = NCU_SLICE_CAPTURE["dram_bytes"] * tensor_flops / NCU_SLICE_CAPTURE["tensor_flops"]
+        if capture is not None and args.shape == "square" and args.member in ("auto", "C2"):
+            traffic = capture["dram_bytes"] * tensor_flops / capture["tensor_flops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": "ncu capture of the 8192^3 call, scaled by tensor flops for other sizes "
-                                  "(profiles/slice_gemm_members_8192.md)",
-                "kernel": "momms::emu::slice_gemm_kernel<192, 0|1> (tcgen05 kind::f16; main + tail launch)",
+                "traffic_source": (capture or {}).get("source"),
+                "kernel": kernel,
                 "peak_source": f"{src} bf16_tflops_sustained (fp16 rate = bf16 rate)",
                 "algorithmic_flops_per_launch": tensor_flops, "launch_ms": slice_ms}
         del Ad, Bd, scratch
@@ -573,12 +608,19 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64",
-            "dtype_detail": (f"FP64-accurate; emulated path: {S} slices of {bb}-bit integer digits in fp16 on "
-                             f"tcgen05 kind::f16, exact FP32 accumulation drained to int32, int64/FP64 recombination"
+            "dtype_detail": (("FP64-accurate; emulated path, modular encoding: operands truncated to "
+                              f"{op_bits}-bit integers, residues modulo {n_mod} coprime moduli <= 255 as fp16 on "
+                              "tcgen05 kind::f16, exact FP32 accumulation drained to int32, Chinese remainder "
+                              "reconstruction in 128-bit integers, one FP64 rounding")
+                             if (emulated and n_mod) else
+                             (f"FP64-accurate; emulated path: {S} slices of {bb}-bit integer digits in fp16 on "
+                              f"tcgen05 kind::f16, exact FP32 accumulation drained to int32, int64/FP64 recombination")
                              if emulated else "native FP64 DMMA"),
             "data": "synthetic",
             "config": {"workload": workload_name(args), "path": "emulated" if emulated else "native",
-                       "slices": S, "digit_bits": bb, "member": M.MEMBER_NAMES.get(int(rep["member"]), "auto"),
+                       "slices": S, "digit_bits": bb, "moduli": n_mod, "operand_bits": op_bits,
+                       "encoding": ("moduli" if n_mod else "slices") if emulated else None,
+                       "member": M.MEMBER_NAMES.get(int(rep["member"]), "auto"),
                        "raster_group": int(rep["group"]), "ctas": int(rep["ctas"]),
                        "l2": "operands exceed L2 (126 MB) at the default size: no flush between steps",
                        "replicas": world},

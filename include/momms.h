@@ -102,6 +102,8 @@ typedef struct {
     int64_t ooc_block;   /* momms_gemm_host: block size b (0 for the other calls)    */
     int64_t h2d_bytes;   /* momms_gemm_host: bytes copied host -> device             */
     int64_t d2h_bytes;   /* momms_gemm_host: bytes copied device -> host             */
+    int moduli;          /* emulated, modular encoding: N moduli (0: digit slices)   */
+    int operand_bits;    /* emulated: integer width of the operands (7 S for slices) */
 } momms_report_t;
 
 /* ---------------------------------------------------------------- handles */
@@ -113,6 +115,27 @@ int momms_set_member(momms_handle_t handle, int member);  /* momms_member_t     
  * spread of the inputs), else 1..MOMMS_MAX_SLICES. */
 int momms_set_slices(momms_handle_t handle, int slices);
 #define MOMMS_MAX_SLICES 16
+/* Integer encoding of an EMULATED single product.  Either way the operands become integers of
+ * b bits (b = 7S unless noted below): each row of op(A) and column of op(B) is scaled by its
+ * power-of-two maximum, A^ = trunc(A 2^(b - e_i)), B^ likewise.
+ *   SLICES  each operand as S signed 7-bit digit slices; the S(S+1)/2 most significant digit
+ *           pairs are multiplied (fp16 tensor products) and recombined in exact int64 groups
+ *           and FP64 (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 2012: the error-free split).
+ *   MODULI  the exact integer product A^B^ computed modulo N pairwise coprime moduli <= 255 --
+ *           residues |r| <= 127 as fp16, one tensor product per modulus -- and rebuilt by the
+ *           Chinese remainder theorem, P = prod p > 2 k (2^b - 1)^2 (Ozaki, Uchino & Imamura,
+ *           "Ozaki Scheme II", 2025).  N products instead of S(S+1)/2 (S = 6, k <= 65536: 13
+ *           instead of 21), and no dropped digit pairs: the only error is the truncation of the
+ *           operands.  Needs N <= 14 (S <= 6, or S = 7 with k <= 2048) and k <= 133,120;
+ *           otherwise the product falls back to SLICES (report.moduli = 0).
+ *   AUTO    MODULI when it takes at least two tensor products fewer than SLICES, else SLICES.
+ * With the automatic slice count (momms_set_slices(0)) the modular encoding takes the width
+ * the slice-count rule asks for, rounded up to whole bits rather than whole 7-bit digits
+ * (report.operand_bits), which can save a modulus.
+ * Single products (momms_gemm, its host-memory and triangular forms); batched calls and SYRK
+ * use SLICES.  Returns -2 for other values. */
+typedef enum { MOMMS_SCHEME_AUTO = 0, MOMMS_SCHEME_SLICES = 1, MOMMS_SCHEME_MODULI = 2 } momms_scheme_t;
+int momms_set_scheme(momms_handle_t handle, int scheme);
 /* Caps the grid of the single-product launches of this handle at `ctas` CTAs that each
  * loop over their share of the member's tiles (0 = default: one CTA per SM for the
  * emulated slice products, one CTA per tile for the native kernel).  Fewer CTAs lower
@@ -212,6 +235,25 @@ int momms_emu_split(int which, int op, int64_t rows, int64_t inner, const double
                     int digit_bits, void* digits, int64_t rows_pad, int64_t inner_pad,
                     momms_stream_t stream);
 
+/* Moduli of the modular encoding (MOMMS_SCHEME_MODULI) for operands of `bits` bits and
+ * contraction length k: the fewest of the library's pairwise coprime moduli <= 255 (largest
+ * first) whose product P exceeds 2 k (2^bits - 1)^2, so that the centred residue of the exact
+ * integer product modulo P is the product itself.  moduli: host array of 14 entries; *count
+ * receives N.  Host only (no device work).  Returns -1 for bits outside 1..56, -2 for k < 1,
+ * MOMMS_ERR_UNSUPPORTED when more than 14 moduli or k > 133,120 would be needed. */
+int momms_crt_moduli(int bits, int64_t k, int* count, uint32_t* moduli);
+
+/* Residues of the integer operand X^ = sign(x) trunc(|x| 2^(bits - e)) (e from
+ * momms_emu_scale; X^ is the first bits/7 digits of momms_emu_split when 7 divides bits)
+ * modulo each of the N moduli momms_crt_moduli(bits, k) returns, centred in
+ * [-floor(p/2), floor((p-1)/2)] and stored as fp16 in plane l of `planes` (layout of the
+ * digit slices: [N][rows_pad][inner_pad]; flagged vectors and padding give zeros).
+ * Returns the argument errors of momms_emu_split (bits in place of slices: -9 outside 1..56)
+ * and MOMMS_ERR_UNSUPPORTED when momms_crt_moduli would. */
+int momms_emu_residues(int which, int op, int64_t rows, int64_t inner, const double* X, int64_t ldx,
+                       const int32_t* exps, const uint8_t* flags, int bits, int64_t k, void* planes,
+                       int64_t rows_pad, int64_t inner_pad, momms_stream_t stream);
+
 /* Slice products and recombination on the tcgen05 tensor cores:
  *   P_d = sum_{s+t=d} A_s B_t  (d = 2..S+1, triangular pair set), exact;
  *   C := alpha * 2^(e_i+f_j) * sum_d 2^(-beta d) P_d + beta*C, the diagonals combined
@@ -235,6 +277,31 @@ int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_
                          size_t scratch_bytes, int32_t* status, momms_stream_t stream);
 size_t momms_emu_scratch_bytes(void);
 size_t momms_emu_scratch_bytes_for(int64_t m, int64_t n, int64_t k, int slices);
+
+/* Residue products of the modular encoding on the tcgen05 tensor cores: for each of the N
+ * moduli p_l of momms_crt_moduli(bits, k),
+ *     res[l][j][i] = (sum_p Ar[l][i][p] Br[l][j][p]) mod p_l   in [0, p_l),
+ * the sum exact (FP32 chunks of 1024 products in tensor memory drained to int32).  Ar / Br:
+ * residue planes from momms_emu_residues (N planes of m_pad x k_pad / n_pad x k_pad fp16,
+ * k_pad a multiple of 64); res: device bytes, N m n of them ([l][column][row], column-major m
+ * x n per modulus).  scratch / status as for momms_emu_slice_gemm (its recombination blocks are
+ * not used, but the launch keeps the same per-CTA layout).  Errors: -i for argument i, and
+ * MOMMS_ERR_UNSUPPORTED when the moduli do not exist for (bits, k). */
+int momms_emu_residue_gemm(int64_t m, int64_t n, int64_t k, int bits, const void* Ar, const void* Br,
+                           int64_t m_pad, int64_t n_pad, int64_t k_pad, int member, uint8_t* res, void* scratch,
+                           size_t scratch_bytes, int32_t* status, momms_stream_t stream);
+
+/* Chinese remainder reconstruction of the modular encoding: from the residues of
+ * momms_emu_residue_gemm, the exact product Z = A^B^ (the centred representative modulo
+ * P = prod p_l), then
+ *     C := alpha * round(Z_ij) 2^(e_i + f_j - 2 bits) + beta * C
+ * with round() to nearest FP64 (ties to even) and the power-of-two scaling exact for normal
+ * results; beta != 0 uses one fma(beta, C, alpha y); beta == 0 makes C write-only.  Rows i
+ * with eflags[i] or columns j with fflags[j] give NaN.  e, eflags, f, fflags from
+ * momms_emu_scale.  Errors: -i for argument i, MOMMS_ERR_UNSUPPORTED as above. */
+int momms_crt_reconstruct(int64_t m, int64_t n, int64_t k, int bits, const uint8_t* res, const int32_t* e,
+                          const uint8_t* eflags, const int32_t* f, const uint8_t* fflags, double alpha,
+                          double beta, double* C, int64_t ldc, momms_stream_t stream);
 
 /* --------------------------------------------------- symmetric rank-k update */
 /* C := alpha*op(A)*op(A)^T + beta*C on the uplo triangle of the n x n matrix C

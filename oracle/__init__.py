@@ -21,6 +21,16 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   recombine          pinned: exact rational value of the digit expansion
   count_member       pinned: the paper's closed-form I/O counts (Sec. 2.2) and
                      printed intensities (Sec. 5.2: 23.26 and 64 flops/byte)
+  truncated_integers pinned: the digit expansion of `split`, truncation identity
+  greedy_moduli,     pinned: pairwise coprimality, hand-listed factorisations,
+  moduli_suffice     the range argument written out
+  centred_residues,  pinned: reconstruction by sympy's CRT, round trip
+  crt_reconstruct
+  modular_dgemm      pinned: integer inputs exact, the one-slice emulation bit for
+                     bit, the FP64 componentwise bound at 56 bits, fma semantics
+The modular encoding is not in the paper: it is the alternative integer encoding of
+the emulated product (Ozaki, Uchino & Imamura, "Ozaki Scheme II", 2025); its oracle is
+the definition of what it computes (the exact product of the truncated operands).
 """
 from __future__ import annotations
 
@@ -254,3 +264,127 @@ def count_member(member, A, B, C, b1, b2, b3=0, c_read=True):
     if rc != 0:
         raise RuntimeError("oracle_count_member failed")
     return out.as_dict()
+
+
+# ---------------------------------------------------------------------------------------------
+# Modular (Chinese remainder) encoding of the emulated product.  Its result has a plain
+# definition -- the exact integer product of the operands truncated to `bits`-bit integers,
+# rounded once to FP64 and scaled -- so the oracle is that definition (Python integers), plus
+# the two pieces the CUDA path exposes on their own: the centred residues of the truncated
+# operands and the choice of moduli.
+#   truncated_integers  pinned: digit expansion of `split`, truncation identity
+#   centred_residues    pinned: reconstruction by the library CRT (sympy)
+#   crt_reconstruct     pinned: round trip on random integers, sympy
+#   greedy_moduli       pinned: pairwise coprimality, hand-listed factorisations
+#   modular_dgemm       pinned: integer inputs exact, S = 1 slice emulation (every digit pair
+#                       kept) bit for bit, FP64 error bound at 53 bits
+# ---------------------------------------------------------------------------------------------
+
+def _op_vectors(X, which, trans):
+    """The vectors the scaling runs along: rows of op(A) ('rows') or columns of op(B) ('cols'),
+    as a 2-D float64 array [vector, inner]."""
+    X = np.asarray(X, dtype=np.float64)
+    op = X.T if trans else X
+    return op if which == "rows" else op.T
+
+
+def truncated_integers(X, which, exps, flags, bits, trans=False):
+    """X^ = sign(x) trunc(|x| 2^(bits - e)) for each element x of op(X) (exponent e of its row
+    of op(A) or column of op(B), from `exponents`), as Python ints in an object array
+    [vector, inner]; flagged vectors give zeros.  |x| < 2^e makes |X^| < 2^bits."""
+    import math
+    V = _op_vectors(X, which, trans)
+    out = np.zeros(V.shape, dtype=object)
+    for r in range(V.shape[0]):
+        if flags[r]:
+            continue
+        for q in range(V.shape[1]):
+            out[r, q] = int(math.trunc(math.ldexp(float(V[r, q]), int(bits) - int(exps[r]))))
+    return out
+
+
+def greedy_moduli(count):
+    """The first `count` numbers taken walking down from 255 that are coprime to every number
+    taken before: pairwise coprime moduli whose centred residues fit in 8-bit digits."""
+    import math
+    taken = []
+    p = 255
+    while len(taken) < count and p >= 2:
+        if all(math.gcd(p, q) == 1 for q in taken):
+            taken.append(p)
+        p -= 1
+    return taken
+
+
+def moduli_suffice(moduli, bits, k):
+    """True when the product P of the moduli exceeds 2 k (2^bits - 1)^2, the width of the range
+    of a k-term dot product of `bits`-bit integers: its centred residue mod P is then itself."""
+    P = 1
+    for p in moduli:
+        P *= int(p)
+    return P > 2 * int(k) * (2 ** int(bits) - 1) ** 2
+
+
+def centred_residues(Xhat, moduli):
+    """r_l = X^ mod p_l moved into [-floor(p/2), floor((p-1)/2)]; int16 array [N, ...]."""
+    out = np.zeros((len(moduli),) + Xhat.shape, dtype=np.int16)
+    for l, p in enumerate(moduli):
+        p = int(p)
+        for idx, v in np.ndenumerate(Xhat):
+            r = int(v) % p          # Python: in [0, p) for either sign
+            if r > (p - 1) // 2:
+                r -= p
+            out[(l,) + idx] = r
+    return out
+
+
+def crt_reconstruct(residues, moduli):
+    """The integer x with |x| < P/2 and x = r_l (mod p_l) for every l (Chinese remainder
+    theorem, x = sum_l r_l M_l (M_l^-1 mod p_l) mod P, M_l = P / p_l, then centred)."""
+    P = 1
+    for p in moduli:
+        P *= int(p)
+    x = 0
+    for r, p in zip(residues, moduli):
+        p = int(p)
+        Ml = P // p
+        x += int(r) * Ml * pow(Ml % p, -1, p)
+    x %= P
+    return x - P if x > P // 2 else x
+
+
+def _fma(a, b, c):
+    """a * b + c rounded once (exact rationals), as the device fma does."""
+    from fractions import Fraction
+    import math
+    if not (math.isfinite(a) and math.isfinite(b) and math.isfinite(c)):
+        return a * b + c
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def modular_dgemm(A, B, bits, C=None, alpha=1.0, beta=0.0, transa=False, transb=False):
+    """C := alpha 2^(e_i + f_j - 2 bits) (A^ B^)_ij + beta C with A^, B^ the `bits`-bit truncated
+    integer operands and (A^ B^)_ij their exact dot product (Python integers), rounded once to
+    FP64 (ties to even) before the exact power-of-two scaling; alpha times it is rounded, then
+    fma(beta, C, that).  NaN in the rows of op(A) / columns of op(B) that hold Inf or NaN.
+    Small inputs only (pure Python).  Returns (C, details dict)."""
+    import math
+    e, ef = exponents(A, "rows", transa)
+    f, ff = exponents(B, "cols", transb)
+    Ah = truncated_integers(A, "rows", e, ef, bits, transa)
+    Bh = truncated_integers(B, "cols", f, ff, bits, transb)
+    m, n = Ah.shape[0], Bh.shape[0]
+    Z = np.zeros((m, n), dtype=object)
+    for i in range(m):
+        for j in range(n):
+            Z[i, j] = sum(int(a) * int(b) for a, b in zip(Ah[i], Bh[j]))
+    out = np.zeros((m, n), dtype=np.float64, order="F")
+    for i in range(m):
+        for j in range(n):
+            if ef[i] or ff[j]:
+                y = float("nan")
+            else:
+                y = math.ldexp(float(Z[i, j]), int(e[i]) + int(f[j]) - 2 * int(bits))
+            ay = float(alpha) * y
+            out[i, j] = ay if (C is None or beta == 0.0) else _fma(float(beta), float(C[i, j]), ay)
+    return out, {"e": e, "eflag": ef, "f": f, "fflag": ff, "Ahat": Ah, "Bhat": Bh, "Z": Z}

@@ -55,6 +55,7 @@ struct momms_handle_s {
     int max_ctas = 0;               // grid cap of the single-product launches (0 = default)
     int tile_n = 0;                 // emulated tile width request (96 / 192; 0 = automatic)
     int group = 0;                  // C2 raster group in tile rows (0 = default)
+    int scheme = MOMMS_SCHEME_AUTO; // integer encoding of the emulated product
     void* user_ws = nullptr;
     size_t user_ws_bytes = 0;
     void* own_ws = nullptr;
@@ -64,6 +65,8 @@ struct momms_handle_s {
     int* spread_host = nullptr; // pinned
     cudaEvent_t spread_ready = nullptr;
     int last_auto_slices = 6;   // speculative slice count for the next AUTO call
+    bool last_auto_mod = false; // ... whether it went to the modular encoding
+    int last_auto_bits = 0;     // ... and with which operand width
     momms_report_t report{};
     BatchProblem* dev_probs = nullptr;
     size_t dev_probs_cap = 0;
@@ -99,10 +102,30 @@ int cuda_fail(cudaError_t e) {
 // Workspace carve-up of one emulated product.
 struct EmuLayout {
     int64_t m_pad, n_pad, k_pad;
-    size_t off_e, off_ef, off_f, off_ff, off_l1a, off_l1b, off_Ad, off_Bd, off_scratch, scratch_bytes, total;
+    size_t off_e, off_ef, off_f, off_ff, off_l1a, off_l1b, off_Ad, off_Bd, off_scratch, scratch_bytes, off_res,
+        total;
 };
 
-EmuLayout emu_layout(int64_t m, int64_t n, int64_t k, int S, int max_ctas) {
+// The modular encoding in place of the S(S+1)/2 digit pairs: the moduli for `bits`-bit
+// operands, used when allowed and (AUTO) when they save at least two tensor products.
+bool use_moduli(int scheme, int bits, int S, int beta, int64_t k, momms::CrtConsts* c, momms::CrtRecon* r) {
+    if (scheme == MOMMS_SCHEME_SLICES || beta != kDigitBits || S < 1) return false;
+    if (!momms::crt_plan(bits, k, c, r)) return false;
+    return scheme == MOMMS_SCHEME_MODULI || c->N + 2 <= S * (S + 1) / 2;
+}
+
+// Moduli the workspace holds room for: those of a fixed S, the most any S may take in AUTO.
+int moduli_reserved(int scheme, int S, int64_t k) {
+    if (scheme == MOMMS_SCHEME_SLICES) return 0;
+    if (S <= 0) return momms::kCrtMaxModuli;
+    momms::CrtConsts c;
+    momms::CrtRecon r;
+    return use_moduli(scheme, kDigitBits * S, S, kDigitBits, k, &c, &r) ? c.N : 0;
+}
+
+// S digit planes per operand (or N residue planes when more), the recombination scratch and,
+// for N moduli, the N residue bytes of every element of C.
+EmuLayout emu_layout(int64_t m, int64_t n, int64_t k, int S, int max_ctas, int N = 0) {
     EmuLayout L{};
     // digit slices hold exactly m (n) rows: ragged tiles are zero-filled by the copy engine
     L.m_pad = std::max<int64_t>(m, 1);
@@ -115,10 +138,12 @@ EmuLayout emu_layout(int64_t m, int64_t n, int64_t k, int S, int max_ctas) {
     L.off_ff = o;  o += align256(L.n_pad);
     L.off_l1a = o; o += align256(L.m_pad * sizeof(float));
     L.off_l1b = o; o += align256(L.n_pad * sizeof(float));
-    L.off_Ad = o;  o += align256(static_cast<size_t>(S) * L.m_pad * L.k_pad * 2);
-    L.off_Bd = o;  o += align256(static_cast<size_t>(S) * L.n_pad * L.k_pad * 2);
+    const int planes = std::max(S, N);
+    L.off_Ad = o;  o += align256(static_cast<size_t>(planes) * L.m_pad * L.k_pad * 2);
+    L.off_Bd = o;  o += align256(static_cast<size_t>(planes) * L.n_pad * L.k_pad * 2);
     L.scratch_bytes = momms::emu_scratch_bytes_tail(m, n, k, S, max_ctas, kDigitBits);
     L.off_scratch = o; o += align256(L.scratch_bytes);
+    L.off_res = o; o += align256(static_cast<size_t>(N) * L.m_pad * L.n_pad);
     L.total = o;
     return L;
 }
@@ -269,7 +294,8 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     const int bb = h->digit_bits;
     if (S > MOMMS_MAX_SLICES) return MOMMS_ERR_UNSUPPORTED;
     const int S_alloc = S > 0 ? S : kAutoSliceMax;
-    EmuLayout L = emu_layout(m, n, k, S_alloc, h->max_ctas);
+    const int N_alloc = moduli_reserved(h->scheme, S, k);
+    EmuLayout L = emu_layout(m, n, k, S_alloc, h->max_ctas, N_alloc);
     if (std::max(L.m_pad, L.n_pad) > (int64_t(1) << 30)) return MOMMS_ERR_UNSUPPORTED;
     void* ws = nullptr;
     int rc = ensure_workspace(h, L.total, &ws);
@@ -284,9 +310,15 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     void* Ad = w + L.off_Ad;
     void* Bd = w + L.off_Bd;
     void* scratch = w + L.off_scratch;
+    uint8_t* res = reinterpret_cast<uint8_t*>(w + L.off_res);
     int64_t launches = 0;
     cudaError_t ce;
     const bool need_stats = (S == 0);
+    momms::CrtConsts cc{};
+    momms::CrtRecon cr{};
+    bool mod = false;        // the modular encoding serves this product
+    bool res_ready = false;  // the planes hold residues of the final width
+    int mbits = bb * S;      // operand width of the modular encoding
     // A's scale and split run on the caller's stream, B's on a second stream forked from it, so
     // that the two HBM-bound passes overlap; the slice products wait for both.
     rc = ensure_aux(h);
@@ -315,20 +347,47 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
         if (!h->spread_ready || cudaEventRecord(h->spread_ready, s) != cudaSuccess) return MOMMS_ERR_CUDA;
         launches += 2;
         const int guess = std::min(std::max(h->last_auto_slices, 1), S_alloc);
-        ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, guess, bb, Ad, L.m_pad, L.k_pad, s);
-        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-        ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, guess, bb, Bd, L.n_pad, L.k_pad, sb);
+        momms::CrtConsts gc;
+        momms::CrtRecon gr;
+        const int guess_bits = h->last_auto_bits;
+        const bool guess_mod = h->last_auto_mod && use_moduli(h->scheme, guess_bits, guess, bb, k, &gc, &gr) &&
+                               gc.N <= N_alloc;
+        if (guess_mod) {
+            // residues depend on the operand width: they serve only if the readback confirms S
+            ce = momms::launch_emu_residues(0, opa, m, k, A, lda, e, ef, gc, Ad, L.m_pad, L.k_pad, s);
+            if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+            ce = momms::launch_emu_residues(1, opb, n, k, B, ldb, f, ff, gc, Bd, L.n_pad, L.k_pad, sb);
+        } else {
+            ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, guess, bb, Ad, L.m_pad, L.k_pad, s);
+            if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+            ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, guess, bb, Bd, L.n_pad, L.k_pad, sb);
+        }
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
         launches += 2;
-        split_done = guess;
+        split_done = guess_mod ? 0 : guess;
         if (cudaEventSynchronize(h->spread_ready) != cudaSuccess) return MOMMS_ERR_CUDA;
         const double sa = h->spread_host[0] / 16.0, sbs = h->spread_host[1] / 16.0;
         double bits = 0.0;
         S = slices_from_spread(sa, sbs, k, bb, &bits);
         est = 0.1 * std::exp2(bits - static_cast<double>(bb) * S);  // the rule keeps a 10x margin
         h->last_auto_slices = S;
+        // the modular encoding takes the rule's width itself (not rounded up to whole digits)
+        mbits = std::min(bb * S, std::max(static_cast<int>(std::ceil(bits)), bb * S - bb + 1));
+        mod = use_moduli(h->scheme, mbits, S, bb, k, &cc, &cr) && cc.N <= N_alloc;
+        if (mod) est = 0.1 * std::exp2(bits - static_cast<double>(mbits));
+        h->last_auto_mod = mod;
+        h->last_auto_bits = mbits;
+        res_ready = mod && guess_mod && mbits == guess_bits;
+    } else {
+        mod = use_moduli(h->scheme, mbits, S, bb, k, &cc, &cr) && cc.N <= N_alloc;
     }
-    if (S > split_done) {
+    if (mod && !res_ready) {
+        ce = momms::launch_emu_residues(0, opa, m, k, A, lda, e, ef, cc, Ad, L.m_pad, L.k_pad, s);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        ce = momms::launch_emu_residues(1, opb, n, k, B, ldb, f, ff, cc, Bd, L.n_pad, L.k_pad, sb);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        launches += 2;
+    } else if (!mod && S > split_done) {
         ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, S, bb, Ad, L.m_pad, L.k_pad, s, split_done);
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
         ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, S, bb, Bd, L.n_pad, L.k_pad, sb, split_done);
@@ -338,7 +397,7 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     rc = join_aux(h, s);  // the slice products need B's exponents and digits
     if (rc) return rc;
     momms::EmuGemmArgs a{};
-    a.m = m; a.n = n; a.k = k; a.S = S; a.beta = bb;
+    a.m = m; a.n = n; a.k = k; a.S = mod ? cc.N : S; a.beta = bb;
     a.Ad = Ad; a.Bd = Bd; a.m_pad = L.m_pad; a.n_pad = L.n_pad; a.k_pad = L.k_pad;
     a.e = e; a.ef = ef; a.f = f; a.ff = ff;
     a.alpha = alpha; a.beta_c = beta; a.C = C; a.ldc = ldc;
@@ -347,10 +406,20 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     a.status = h->status; a.max_ctas = h->max_ctas; a.tile_n = h->tile_n;
     int passes = 0, used_ctas = 0, used_group = 0, used_launches = 0;
     a.used_ctas = &used_ctas; a.used_group = &used_group; a.used_launches = &used_launches;
+    if (mod) {
+        a.crt = &cc;
+        a.res = res;
+    }
     ce = momms::launch_emu_slice_gemm(a, &passes, s);
     if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
     if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
     launches += used_launches;
+    if (mod) {
+        // C from the residues of the product (Chinese remainder theorem), scaled, alpha / beta
+        ce = momms::launch_crt_reconstruct(m, n, res, cr, e, ef, f, ff, alpha, beta, C, ldc, s);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        launches += 1;
+    }
     h->report = momms_report_t{};
     h->report.ctas = used_ctas;
     h->report.group = used_group;
@@ -363,6 +432,8 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     h->report.tile_n = momms::emu_pick_bn(m, n, k, h->tile_n);
     h->report.launches = launches;
     h->report.est_err_ratio = est;
+    h->report.moduli = mod ? cc.N : 0;
+    h->report.operand_bits = mod ? mbits : bb * S;
     return MOMMS_OK;
 }
 
@@ -681,6 +752,13 @@ int momms_set_slices(momms_handle_t h, int slices) {
     return MOMMS_OK;
 }
 
+int momms_set_scheme(momms_handle_t h, int scheme) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (scheme < MOMMS_SCHEME_AUTO || scheme > MOMMS_SCHEME_MODULI) return -2;
+    h->scheme = scheme;
+    return MOMMS_OK;
+}
+
 int momms_set_max_ctas(momms_handle_t h, int ctas) {
     if (!valid(h)) return MOMMS_ERR_HANDLE;
     if (ctas < 0) return -2;
@@ -748,7 +826,8 @@ int momms_workspace_size(momms_handle_t h, int op_a, int op_b, int64_t m, int64_
         *bytes = 0;
         return MOMMS_OK;
     }
-    *bytes = emu_layout(m, n, k, p.slices > 0 ? p.slices : kAutoSliceMax, h->max_ctas).total;
+    *bytes = emu_layout(m, n, k, p.slices > 0 ? p.slices : kAutoSliceMax, h->max_ctas,
+                        moduli_reserved(h->scheme, p.slices, k)).total;
     return MOMMS_OK;
 }
 
@@ -974,6 +1053,44 @@ int momms_emu_split(int which, int op, int64_t rows, int64_t inner, const double
                                              reinterpret_cast<cudaStream_t>(stream)));
 }
 
+int momms_crt_moduli(int bits, int64_t k, int* count, uint32_t* moduli) {
+    if (bits < 1 || bits > 56) return -1;
+    if (k < 1) return -2;
+    if (!count) return -3;
+    if (!moduli) return -4;
+    momms::CrtConsts c;
+    momms::CrtRecon r;
+    if (!momms::crt_plan(bits, k, &c, &r)) return MOMMS_ERR_UNSUPPORTED;
+    *count = c.N;
+    for (int l = 0; l < c.N; ++l) moduli[l] = c.p[l];
+    return MOMMS_OK;
+}
+
+int momms_emu_residues(int which, int op, int64_t rows, int64_t inner, const double* X, int64_t ldx,
+                       const int32_t* exps, const uint8_t* flags, int bits, int64_t k, void* planes,
+                       int64_t rows_pad, int64_t inner_pad, momms_stream_t stream) {
+    if (which != 0 && which != 1) return -1;
+    if (op != 0 && op != 1) return -2;
+    if (rows < 0) return -3;
+    if (inner < 0) return -4;
+    const bool rows_contig = (which == 0) ? (op == 0) : (op != 0);
+    const int64_t stored_rows = rows_contig ? rows : inner;
+    if (rows > 0 && inner > 0 && !X) return -5;
+    if (ldx < std::max<int64_t>(1, stored_rows)) return -6;
+    if (rows > 0 && !exps) return -7;
+    if (rows > 0 && !flags) return -8;
+    if (bits < 1 || bits > 56) return -9;
+    if (k < 1) return -10;
+    if (!planes) return -11;
+    if (rows_pad < std::max<int64_t>(rows, 1)) return -12;
+    if (inner_pad < inner || inner_pad % momms::kEmuBK) return -13;
+    momms::CrtConsts c;
+    momms::CrtRecon r;
+    if (!momms::crt_plan(bits, k, &c, &r)) return MOMMS_ERR_UNSUPPORTED;
+    return cuda_fail(momms::launch_emu_residues(which, op, rows, inner, X, ldx, exps, flags, c, planes, rows_pad,
+                                                inner_pad, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 size_t momms_emu_scratch_bytes(void) { return momms::emu_scratch_bytes(momms::device_sm_count()); }
 
 size_t momms_emu_scratch_bytes_for(int64_t m, int64_t n, int64_t k, int slices) {
@@ -1020,6 +1137,62 @@ int momms_emu_slice_gemm(int64_t m, int64_t n, int64_t k, int slices, int digit_
     cudaError_t ce = momms::launch_emu_slice_gemm(a, &passes, s);
     if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
     return cuda_fail(ce);
+}
+
+int momms_emu_residue_gemm(int64_t m, int64_t n, int64_t k, int bits, const void* Ar, const void* Br,
+                           int64_t m_pad, int64_t n_pad, int64_t k_pad, int member, uint8_t* res, void* scratch,
+                           size_t scratch_bytes, int32_t* status, momms_stream_t stream) {
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (k < 1) return -3;
+    if (bits < 1 || bits > 56) return -4;
+    if (!Ar) return -5;
+    if (!Br) return -6;
+    if (m_pad < std::max<int64_t>(m, 1)) return -7;
+    if (n_pad < std::max<int64_t>(n, 1)) return -8;
+    if (k_pad < k || k_pad % momms::kEmuBK) return -9;
+    if (member < MOMMS_MEMBER_AUTO || member > MOMMS_MEMBER_A1) return -10;
+    if (!res && m > 0 && n > 0) return -11;
+    if (!scratch) return -12;
+    if (scratch_bytes < momms::emu_scratch_bytes(momms::device_sm_count())) return MOMMS_ERR_WORKSPACE;
+    if (!status) return -14;
+    momms::CrtConsts c;
+    momms::CrtRecon r;
+    if (!momms::crt_plan(bits, k, &c, &r)) return MOMMS_ERR_UNSUPPORTED;
+    if (m == 0 || n == 0) return MOMMS_OK;
+    momms::EmuGemmArgs a{};
+    a.m = m; a.n = n; a.k = k; a.S = c.N; a.beta = kDigitBits;
+    a.Ad = Ar; a.Bd = Br; a.m_pad = m_pad; a.n_pad = n_pad; a.k_pad = k_pad;
+    a.alpha = 1.0; a.beta_c = 0.0;
+    a.member = member; a.group = 0;
+    a.scratch = scratch; a.scratch_bytes = scratch_bytes; a.status = status; a.max_ctas = 0; a.tile_n = 0;
+    a.crt = &c;
+    a.res = res;
+    int passes = 0;
+    cudaError_t ce = momms::launch_emu_slice_gemm(a, &passes, reinterpret_cast<cudaStream_t>(stream));
+    if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
+    return cuda_fail(ce);
+}
+
+int momms_crt_reconstruct(int64_t m, int64_t n, int64_t k, int bits, const uint8_t* res, const int32_t* e,
+                          const uint8_t* eflags, const int32_t* f, const uint8_t* fflags, double alpha,
+                          double beta, double* C, int64_t ldc, momms_stream_t stream) {
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (k < 1) return -3;
+    if (bits < 1 || bits > 56) return -4;
+    if (!res && m > 0 && n > 0) return -5;
+    if (!e && m > 0) return -6;
+    if (!eflags && m > 0) return -7;
+    if (!f && n > 0) return -8;
+    if (!fflags && n > 0) return -9;
+    if (!C && m > 0 && n > 0) return -12;
+    if (ldc < std::max<int64_t>(1, m)) return -13;
+    momms::CrtConsts c;
+    momms::CrtRecon r;
+    if (!momms::crt_plan(bits, k, &c, &r)) return MOMMS_ERR_UNSUPPORTED;
+    return cuda_fail(momms::launch_crt_reconstruct(m, n, res, r, e, eflags, f, fflags, alpha, beta, C, ldc,
+                                                   reinterpret_cast<cudaStream_t>(stream)));
 }
 
 // ------------------------------------------------------------------ plan cache
@@ -1408,7 +1581,9 @@ constexpr int64_t kOocAlign = 256;
 size_t ooc_device_bytes(momms_handle_t h, int64_t b) {
     size_t ws = 0;
     const Plan p = pick_plan(h, b, b, b);
-    if (p.mode == MOMMS_MODE_EMULATED) ws = emu_layout(b, b, b, p.slices > 0 ? p.slices : kAutoSliceMax, h->max_ctas).total;
+    if (p.mode == MOMMS_MODE_EMULATED)
+        ws = emu_layout(b, b, b, p.slices > 0 ? p.slices : kAutoSliceMax, h->max_ctas,
+                        moduli_reserved(h->scheme, p.slices, b)).total;
     return 6 * static_cast<size_t>(b) * b * sizeof(double) + ws;
 }
 

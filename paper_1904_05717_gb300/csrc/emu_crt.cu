@@ -1,0 +1,220 @@
+// emu_crt.cu -- the modular (Chinese remainder) encoding of the emulated FP64 product:
+// the choice of moduli and the reconstruction of C from the residues of the product.
+//
+// The operands are truncated to `bits`-bit integers A^ = trunc(A 2^(bits - e)) (row exponent
+// e), B^ likewise; their exact product is known modulo each of N pairwise coprime moduli
+// p_l <= 255 (one tensor product of residues per modulus, emu_slice_gemm.cu), and as
+// |A^ B^| <= k (2^bits - 1)^2 < P / 2 with P = prod p_l, the Chinese remainder theorem gives
+// it exactly:  A^B^ = sum_l c_l w_l mod P, centred, with w_l = (P / p_l) ((P / p_l)^-1 mod p_l).
+// Then C := alpha 2^(e_i + f_j - 2 bits) A^B^ + beta C, rounded once to FP64 (plus the
+// scaling).  The error is the truncation of A and B to `bits` bits -- that of the slice
+// encoding with bits / 7 slices without its dropped digit pairs.
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace momms {
+
+namespace {
+
+using u128 = unsigned __int128;
+
+// The moduli: walking down from 255, every number coprime to all those already taken
+// (255 = 3 5 17, 254 = 2 127, 253 = 11 23, 247 = 13 19, 217 = 7 31, the rest prime); their
+// centred residues, |r| <= 127, are exact fp16 digits.
+constexpr uint32_t kModuli[kCrtMaxModuli] = {255, 254, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199};
+
+uint32_t inverse_mod(uint32_t a, uint32_t p) {  // a^-1 mod p (gcd(a, p) = 1)
+    long long t = 0, nt = 1, r = p, nr = a % p;
+    while (nr != 0) {
+        const long long q = r / nr;
+        long long tmp = t - q * nt;
+        t = nt;
+        nt = tmp;
+        tmp = r - q * nr;
+        r = nr;
+        nr = tmp;
+    }
+    if (t < 0) t += p;
+    return static_cast<uint32_t>(t);
+}
+
+// v rounded to nearest (ties to even) as a double: the leading 64 bits with the rest folded
+// into a sticky bit (bit 0 lies below the rounding position of a 53-bit significand), one
+// correctly rounded 64-bit conversion, then an exact power-of-two scaling.
+MOMMS_DEV double u128_to_double(u128 v) {
+    const unsigned long long hi = static_cast<unsigned long long>(v >> 64);
+    if (hi == 0) return static_cast<double>(static_cast<unsigned long long>(v));
+    const int lz = __clzll(static_cast<long long>(hi));
+    const u128 t = v << lz;
+    const unsigned long long top = static_cast<unsigned long long>(t >> 64) |
+                                   static_cast<unsigned long long>(static_cast<unsigned long long>(t) != 0);
+    return static_cast<double>(top) * pow2_normal(64 - lz);
+}
+
+// One element of C from its limb sums s_q = sum_l c_l w_l[q] (the CRT sum in 32-bit limbs):
+// the sum mod P, centred, rounded once to FP64 with its power-of-two scale folded into the
+// exponent field, then alpha / beta.  Integer arithmetic throughout except the last step (FP64
+// ALU work is scarce on this part); an exponent outside the normal range takes the FP64 route.
+MOMMS_DEV double crt_element(const unsigned long long (&s)[4], const CrtRecon& r, const u128 P, const u128 half,
+                             int E, bool flag, double alpha, double beta, const double* cp) {
+    // carries between the limbs: acc = s_0 + s_1 2^32 + s_2 2^64 + s_3 2^96 < N 256 P < 2^128
+    const unsigned long long t1 = s[1] + (s[0] >> 32);
+    const unsigned long long t2 = s[2] + (t1 >> 32);
+    const unsigned long long t3 = s[3] + (t2 >> 32);
+    const unsigned long long lo = (s[0] & 0xFFFFFFFFull) | (t1 << 32);
+    const unsigned long long hi = (t2 & 0xFFFFFFFFull) | (t3 << 32);
+    u128 acc = (static_cast<u128>(hi) << 64) | lo;
+    // acc mod P: an fp32 quotient estimate (relative error ~2^-21 on a quotient below 2^12, so
+    // off by at most one) and one exact correction either way
+    const float accf = __ull2float_rn(hi) * 18446744073709551616.0f + __ull2float_rn(lo);
+    const uint32_t q = static_cast<uint32_t>(accf * r.Pinv);
+    const u128 qP = static_cast<u128>(q) * P;
+    acc = qP > acc ? acc + P - qP : acc - qP;
+    if (acc >= P) acc -= P;
+    const bool neg = acc > half;
+    const u128 mag = neg ? P - acc : acc;
+    double y;
+    if (flag) {
+        y = __longlong_as_double(0x7ff8000000000000ll);
+    } else if (mag == 0) {
+        y = 0.0;
+    } else {
+        const unsigned long long mh = static_cast<unsigned long long>(mag >> 64);
+        const unsigned long long ml = static_cast<unsigned long long>(mag);
+        const int lz = mh ? __clzll(static_cast<long long>(mh)) : 64 + __clzll(static_cast<long long>(ml));
+        const u128 t = mag << lz;  // leading one at bit 127
+        const unsigned long long top = static_cast<unsigned long long>(t >> 64) |
+                                       static_cast<unsigned long long>(static_cast<unsigned long long>(t) != 0);
+        // round the 64-bit significand to 53 bits, to nearest, ties to even
+        unsigned long long mant = top >> 11;
+        const unsigned long long rem = top & 0x7FFull;
+        mant += (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+        int ex = 127 - lz + E;  // unbiased exponent of |y| = mant 2^(ex - 52)
+        if (mant == (1ull << 53)) {
+            mant >>= 1;
+            ++ex;
+        }
+        if (ex >= -1022 && ex <= 1023) {
+            y = __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(neg) << 63) |
+                                                            (static_cast<unsigned long long>(ex + 1023) << 52) |
+                                                            (mant & ((1ull << 52) - 1))));
+        } else {
+            y = scale_pow2(u128_to_double(mag), E);
+            if (neg) y = -y;
+        }
+    }
+    const double ay = alpha == 1.0 ? y : alpha * y;
+    return beta == 0.0 ? ay : fma(beta, *cp, ay);
+}
+
+// C from the residue bytes res[l][j][i] (m n per modulus).  Blocks stride over the columns,
+// threads over the rows of a column; with VEC (m a multiple of 4) a thread takes four
+// consecutive rows and loads one 32-bit word per modulus.
+template <bool VEC>
+__global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
+                                                  const __grid_constant__ CrtRecon r,
+                                                  const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
+                                                  const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
+                                                  double alpha, double beta, double* __restrict__ C, int64_t ldc) {
+    constexpr int V = VEC ? 4 : 1;
+    const int64_t mn = m * n;
+    const int64_t groups = m / V;
+    const u128 P = (static_cast<u128>(r.P_hi) << 64) | r.P_lo;
+    const u128 half = P >> 1;
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        const int Ej = f[j] - 2 * r.bits;
+        const bool fj = ff[j] != 0;
+        for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < groups;
+             g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+            const int64_t i0 = g * V;
+            unsigned long long s[V][4];
+#pragma unroll
+            for (int t = 0; t < V; ++t)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s[t][q] = 0;
+            const uint8_t* src = res + j * m + i0;
+            for (int l = 0; l < r.N; ++l) {
+                uint32_t word;
+                if constexpr (VEC) word = __ldcs(reinterpret_cast<const unsigned int*>(src + l * mn));
+                else word = src[l * mn];
+                const uint32_t w0 = r.w[l][0], w1 = r.w[l][1], w2 = r.w[l][2], w3 = r.w[l][3];
+#pragma unroll
+                for (int t = 0; t < V; ++t) {
+                    const uint32_t c = (word >> (8 * t)) & 0xFFu;
+                    s[t][0] += static_cast<unsigned long long>(c) * w0;
+                    s[t][1] += static_cast<unsigned long long>(c) * w1;
+                    s[t][2] += static_cast<unsigned long long>(c) * w2;
+                    s[t][3] += static_cast<unsigned long long>(c) * w3;
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                const int64_t i = i0 + t;
+                double* cp = C + i + j * ldc;
+                *cp = crt_element(s[t], r, P, half, e[i] + Ej, fj || ef[i] != 0, alpha, beta, cp);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int64_t crt_max_k() {
+    int64_t k = ((1ll << 31) - 1) / (127ll * 127ll);
+    return k - k % 64;
+}
+
+bool crt_plan(int bits, int64_t k, CrtConsts* c, CrtRecon* r) {
+    if (bits < 1 || bits > 56 || k < 1 || k > crt_max_k()) return false;
+    int lk = 0;
+    while ((int64_t(1) << lk) < k) ++lk;
+    if (2 * bits + lk + 1 > 118) return false;
+    const u128 v = (static_cast<u128>(1) << bits) - 1;
+    const u128 need = static_cast<u128>(2) * static_cast<u128>(k) * v * v;  // P must exceed 2 k (2^bits - 1)^2
+    u128 P = 1;
+    int N = 0;
+    while (N < kCrtMaxModuli && P <= need) P *= kModuli[N++];
+    if (P <= need) return false;
+    // the reconstruction sums N terms below 255 P each in 128 bits
+    if (P > (~static_cast<u128>(0)) / (static_cast<u128>(N) * 256)) return false;
+    *c = CrtConsts{};
+    *r = CrtRecon{};
+    c->N = r->N = N;
+    c->bits = r->bits = bits;
+    for (int l = 0; l < N; ++l) {
+        const uint32_t p = kModuli[l];
+        c->p[l] = p;
+        c->magic[l] = static_cast<uint32_t>((1ull << 32) / p + 1);
+        c->c16[l] = static_cast<uint32_t>((1ull << 16) % p);
+        c->c32[l] = static_cast<uint32_t>((1ull << 32) % p);
+        const u128 Ml = P / p;
+        const uint32_t inv = inverse_mod(static_cast<uint32_t>(Ml % p), p);
+        const u128 w = Ml * inv;  // < P
+        for (int q = 0; q < 4; ++q) r->w[l][q] = static_cast<uint32_t>(w >> (32 * q));
+    }
+    r->P_lo = static_cast<unsigned long long>(P);
+    r->P_hi = static_cast<unsigned long long>(P >> 64);
+    r->Pinv = static_cast<float>(1.0 / (static_cast<double>(r->P_hi) * 18446744073709551616.0 +
+                                        static_cast<double>(r->P_lo)));
+    return true;
+}
+
+cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, const CrtRecon& r, const int32_t* e,
+                                   const uint8_t* ef, const int32_t* f, const uint8_t* ff, double alpha,
+                                   double beta, double* C, int64_t ldc, cudaStream_t stream) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    const bool vec = m % 4 == 0 && reinterpret_cast<uintptr_t>(res) % 4 == 0;
+    const int64_t groups = vec ? m / 4 : m;
+    int64_t bx = (groups + 255) / 256;
+    if (bx > 64) bx = 64;
+    const int64_t want = static_cast<int64_t>(device_sm_count()) * 16;  // resident blocks to fill the chip
+    int64_t by = (want + bx - 1) / bx;
+    if (by > n) by = n;
+    if (by > 65535) by = 65535;
+    const dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(by));
+    if (vec) crt_kernel<true><<<grid, 256, 0, stream>>>(m, n, res, r, e, ef, f, ff, alpha, beta, C, ldc);
+    else crt_kernel<false><<<grid, 256, 0, stream>>>(m, n, res, r, e, ef, f, ff, alpha, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace momms

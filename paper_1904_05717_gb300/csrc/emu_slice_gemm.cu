@@ -112,6 +112,10 @@ struct Params {
     int tail_tiles;           // tiles in the tail round
     int tail_parts;           // k parts per tail tile (< 2: no split)
     int32_t* tail_sums;       // [tail tile][part][diagonal d-2][column / 4][row][4] int32 partial sums
+    // Modular encoding (single problem): `one.S` moduli, the unit of modulus l multiplies residue
+    // plane l of A by plane l of B and its epilogue stores (sum mod modp[l]) as a byte.
+    uint8_t* res;             // [l][col][row] residues of the product, m n bytes per modulus
+    uint32_t modp[kCrtMaxModuli];
 };
 
 // The it-th tile of this CTA: its problem (-1 = the single problem of p.one) and tile
@@ -174,15 +178,6 @@ MOMMS_DEV TileInts tile_ints(const Params& p, int prob, int part) {
     return t;
 }
 
-// r * 2^E with one rounding for every E (two exact power-of-two factors outside
-// the normal exponent range; results beyond the double range saturate to 0 / inf).
-MOMMS_DEV double scale_pow2(double r, int E) {
-    if (E >= -1022 && E <= 1023) return r * pow2_normal(E);
-    const int E1 = E > 0 ? 960 : -960;
-    int E2 = E - E1;
-    E2 = E2 > 1023 ? 1023 : (E2 < -1022 ? -1022 : E2);
-    return (r * pow2_normal(E1)) * pow2_normal(E2);
-}
 
 // ---------------------------------------------------------------- recombination
 // One drain thread's columns after the last chunk of diagonal d.  Q / R point at the
@@ -381,6 +376,39 @@ MOMMS_DEV void store_partial(int4* dst, const int32_t (&acc)[CR], uint32_t tsum)
     }
 }
 
+// The modular epilogue of modulus l: the thread's int32 sums (CR in `acc`, CT in TMEM at
+// `tsum`) reduced into [0, p) and stored as bytes at res[l][col][row].  The TMEM reads are
+// warp-wide, so every lane takes them before the bounds checks.
+template <int BN, int CR, int CT>
+MOMMS_DEV void store_residues(const Params& p, int tm, int tn, int l, int third, int rloc, const int32_t (&acc)[CR],
+                              uint32_t tsum) {
+    const int row = tm * BM + rloc;
+    const int col0 = tn * BN + third * (BN / 3);
+    const int pl = static_cast<int>(p.modp[l]);
+    const bool row_ok = row < p.one.m;
+    uint8_t* dst = p.res + static_cast<size_t>(l) * p.one.m * p.one.n + static_cast<size_t>(col0) * p.one.m + row;
+    const int ncols = min(BN / 3, p.one.n - col0);
+#pragma unroll
+    for (int c = 0; c < CR; ++c) {
+        int r = acc[c] % pl;
+        if (r < 0) r += pl;
+        if (row_ok && c < ncols) dst[static_cast<size_t>(c) * p.one.m] = static_cast<uint8_t>(r);
+    }
+#pragma unroll
+    for (int q = 0; q < CT / 16; ++q) {
+        uint32_t t[16];
+        tmem_ld_32x32b_x16(tsum + q * 16, t);
+        tmem_ld_wait(t);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int c = CR + q * 16 + j;
+            int r = static_cast<int32_t>(t[j]) % pl;
+            if (r < 0) r += pl;
+            if (row_ok && c < ncols) dst[static_cast<size_t>(c) * p.one.m] = static_cast<uint8_t>(r);
+        }
+    }
+}
+
 // Stages the column exponents (minus 2 beta) and non-finite flags of tile column tn in shared
 // memory, between two barriers of the drain warps (the previous tile's columns are no longer read).
 template <int BN>
@@ -542,7 +570,9 @@ __global__ void __launch_bounds__(256) tail_fixup_kernel(const __grid_constant__
     }
 }
 
-template <int BN, bool TAIL>
+// MOD: the modular encoding -- unit d (from S + 1 down to 2) is modulus l = S + 1 - d, one pair
+// (residue plane l of A, plane l of B), and its epilogue stores residues instead of recombining.
+template <int BN, bool TAIL, bool MOD = false>
 __global__ void __launch_bounds__(THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const __grid_constant__ Params p) {
@@ -608,7 +638,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const CUtensorMap* mapB = prob < 0 ? &tmB : &p.table[prob].mapB;
 
                 for (int d = pr.S + 1; d >= 2 && ok; --d) {
-                    for (int s = 1; s <= d - 1 && ok; ++s) {
+                    const int npairs = MOD ? 1 : d - 1;
+                    for (int s = 1; s <= npairs && ok; ++s) {
+                        const int plane_a = MOD ? pr.S + 1 - d : s - 1;
+                        const int plane_b = MOD ? plane_a : d - s - 1;
                         for (int j = 0; j < pr.nslab; ++j) {
                             if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
                                 ok = false;
@@ -617,10 +650,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                             uint8_t* sa = smem + stage * STAGE;
                             mbar_arrive_expect_tx(&full[stage], STAGE);
                             const int x = (pr.slab0 + j) * BK;
-                            // A slice s rows [tm*BM, +BM), B slice d-s rows [tn*BN, +BN);
-                            // rows past the end of a slice are zero-filled by the copy engine
-                            tma_load_3d(sa, mapA, &full[stage], x, tm * BM, s - 1);
-                            tma_load_3d(sa + A_TILE, mapB, &full[stage], x, tn * BN, d - s - 1);
+                            // A slice s rows [tm*BM, +BM), B slice d-s rows [tn*BN, +BN) (MOD: the
+                            // residue planes of one modulus); rows past the end of a plane are
+                            // zero-filled by the copy engine
+                            tma_load_3d(sa, mapA, &full[stage], x, tm * BM, plane_a);
+                            tma_load_3d(sa + A_TILE, mapB, &full[stage], x, tn * BN, plane_b);
                             last_phase[stage] = static_cast<int>(phase);
                             if (++stage == STAGES) {
                                 stage = 0;
@@ -649,7 +683,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!tile_of<TAIL>(p, it, &prob, &tm, &tn, &part)) break;
                 const TileInts pr = tile_ints(p, prob, part);
                 for (int d = pr.S + 1; d >= 2 && ok; --d) {
-                    const int units = (d - 1) * pr.nslab;
+                    const int units = (MOD ? 1 : d - 1) * pr.nslab;
                     for (int u = 0; u < units && ok;) {
                         const int cnt = min(pr.chunk_slabs, units - u);
                         if (!mbar_wait(&acc_empty[abuf], aphase[abuf] ^ 1u, abort_flag)) {
@@ -726,17 +760,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const double rb = pow2_normal(-pr.beta);
                 int gj = 0;           // position of the current diagonal inside its int64 group
                 bool rfirst = true;   // no FP64 partial R yet for this tile
-                stage_columns<BN>(p, prob, tn, pr.beta, colexp, colflag);
+                if constexpr (!MOD) stage_columns<BN>(p, prob, tn, pr.beta, colexp, colflag);
                 for (int d = pr.S + 1; d >= 2; --d) {
                     int32_t acc[CR];
-                    if (!drain_diagonal<CR, CT>((d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty, abuf,
-                                                aphase, abort_flag, tmem_base + lane_off + third * CW, tsum, lane,
-                                                acc)) {
+                    if (!drain_diagonal<CR, CT>((MOD ? 1 : d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty,
+                                                abuf, aphase, abort_flag, tmem_base + lane_off + third * CW, tsum,
+                                                lane, acc)) {
                         ok = false;
                         break;
                     }
-                    recombine_diagonal<BN, CR, CT>(p, prob, tm, tn, d, pr, Q, R, keep, tsum, rb, third, rloc,
-                                                   colexp, colflag, qnan, acc, gj, rfirst);
+                    if constexpr (MOD)
+                        store_residues<BN, CR, CT>(p, tm, tn, pr.S + 1 - d, third, rloc, acc, tsum);
+                    else
+                        recombine_diagonal<BN, CR, CT>(p, prob, tm, tn, d, pr, Q, R, keep, tsum, rb, third, rloc,
+                                                       colexp, colflag, qnan, acc, gj, rfirst);
                 }
             }
         }
@@ -847,14 +884,20 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(slice_gemm_kernel<BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(C_::SMEM_BYTES));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C_::SMEM_BYTES));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    const bool mod = a.crt != nullptr;
     const int64_t kslabs = (a.k + BK - 1) / BK;
-    const int64_t pass_slabs = emu_max_k_per_pass(a.S, a.beta) / BK;
+    // modular encoding: one pass (every k the moduli were planned for keeps the int32 sums exact)
+    const int64_t pass_slabs = mod ? kslabs : emu_max_k_per_pass(a.S, a.beta) / BK;
     if (kslabs <= 0 || pass_slabs <= 0) return cudaErrorInvalidValue;
+    if (mod && (a.res == nullptr || a.crt->N != a.S || kslabs * BK > crt_max_k())) return cudaErrorInvalidValue;
     const int member = a.member == kMemberAuto ? kMemberC2 : a.member;
-    TailPlan tp = BN == kEmuBNMax ? tail_plan(tiles, ctas, kslabs, pass_slabs, a.S, member) : TailPlan{};
+    TailPlan tp = BN == kEmuBNMax && !mod ? tail_plan(tiles, ctas, kslabs, pass_slabs, a.S, member) : TailPlan{};
     if (tp.parts && a.scratch_bytes < 2 * half + tp.sums_bytes) tp = TailPlan{};  // whole tiles
     char* tail_base = static_cast<char*>(a.scratch) + 2 * half;
     int npass = 0, nlaunch = 0;
@@ -893,6 +936,17 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         p.qscratch = static_cast<long long*>(a.scratch);
         p.scratch = reinterpret_cast<double*>(static_cast<char*>(a.scratch) + half);
         p.status = a.status;
+        if (mod) {
+            p.res = a.res;
+            for (int l = 0; l < a.crt->N; ++l) p.modp[l] = a.crt->p[l];
+            slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(
+                mapA, mapB, p);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            ++nlaunch;
+            ++npass;
+            continue;
+        }
         // main launch: the whole rounds (all tiles without a tail split)
         slice_gemm_kernel<BN, false><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(mapA, mapB, p);
         cudaError_t e = cudaGetLastError();
@@ -1082,6 +1136,7 @@ cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_
     if (passes) *passes = 0;
     if (a.m <= 0 || a.n <= 0) return cudaSuccess;
     if (a.S < 1 || a.S > 16 || a.beta < 1 || a.beta > 8) return cudaErrorInvalidValue;
+    if (a.crt && (a.beta != 7 || a.crt->N < 1 || a.crt->N > kCrtMaxModuli)) return cudaErrorInvalidValue;
     if (a.m_pad < a.m || a.n_pad < a.n || a.k_pad < a.k || a.k_pad % BK) return cudaErrorInvalidValue;
     if (emu_chunk_slabs(a.beta) * BK * ((1ll << a.beta) - 1) * ((1ll << a.beta) - 1) > (1ll << 24))
         return cudaErrorInvalidValue;  // beta too wide for one 64-wide slab per chunk

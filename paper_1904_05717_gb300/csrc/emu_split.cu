@@ -306,12 +306,60 @@ __device__ __forceinline__ void write_digits8(const double (&x)[8], bool valid_r
     }
 }
 
+// Residues of the integer operand A^ = trunc(|x| 2^(bits - e)) sign(x) modulo each p_l, in the
+// symmetric range [-floor(p/2), floor((p-1)/2)] (|r| <= 127: exact in fp16, products < 2^14 as
+// for the digits).  A^ is the top `bits` bits of the 128-bit fraction (the first bits/7
+// digits); its residue comes from 16-bit pieces, a0 + 2^16 a1 + 2^32 a2, with 2^16 and 2^32
+// reduced mod p beforehand, and one multiply-high quotient.
+template <int NE>
+__device__ __forceinline__ void write_residues(const double (&x)[NE], bool valid_row, int e, const CrtConsts& c,
+                                               __half* __restrict__ planes, int64_t plane, int64_t off) {
+    uint32_t a0[NE], a1[NE], a2[NE];
+    bool neg[NE];
+#pragma unroll
+    for (int i = 0; i < NE; ++i) {
+        unsigned long long fh, fl;
+        uint32_t sg;
+        fraction128(x[i], valid_row, e, &fh, &fl, &sg);
+        const unsigned long long A = fh >> (64 - c.bits);
+        a0[i] = static_cast<uint32_t>(A & 0xFFFFu);
+        a1[i] = static_cast<uint32_t>((A >> 16) & 0xFFFFu);
+        a2[i] = static_cast<uint32_t>(A >> 32);
+        neg[i] = sg != 0;
+    }
+    for (int l = 0; l < c.N; ++l) {
+        const uint32_t pl = c.p[l], mg = c.magic[l], k16 = c.c16[l], k32 = c.c32[l];
+        const int hi = static_cast<int>((pl - 1) / 2), lo = -static_cast<int>(pl / 2);
+        uint32_t u[NE], sgn[NE];
+#pragma unroll
+        for (int i = 0; i < NE; ++i) {
+            const uint32_t t = a2[i] * k32 + a1[i] * k16 + a0[i];  // < 2^32 for bits <= 56
+            const uint32_t q = __umulhi(t, mg);                    // floor(t / p) or one more
+            int r = static_cast<int>(t - q * pl);                  // in [-p, p)
+            if (r < 0) r += static_cast<int>(pl);
+            int v = neg[i] ? -r : r;
+            if (v > hi) v -= static_cast<int>(pl);
+            else if (v < lo) v += static_cast<int>(pl);
+            u[i] = static_cast<uint32_t>(v < 0 ? -v : v);
+            sgn[i] = v < 0 ? 0x8000u : 0u;
+        }
+        uint32_t w[NE / 2];
+#pragma unroll
+        for (int i = 0; i < NE; i += 2) w[i / 2] = digits_to_half2(u[i], u[i + 1], sgn[i], sgn[i + 1]);
+        if constexpr (NE == 8)
+            *reinterpret_cast<uint4*>(planes + l * plane + off) = make_uint4(w[0], w[1], w[2], w[3]);
+        else
+            *reinterpret_cast<uint2*>(planes + l * plane + off) = make_uint2(w[0], w[1]);
+    }
+}
+
 // Inner dimension contiguous in memory: a thread takes eight consecutive q of one row.
+template <bool RES>
 __global__ void split_inner_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
                                    int64_t inner, const int32_t* __restrict__ exps,
                                    const uint8_t* __restrict__ flags, int S, int beta,
                                    __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad,
-                                   int s_first) {
+                                   int s_first, const __grid_constant__ CrtConsts crt) {
     const int64_t octs = inner_pad / 8;
     const int64_t total = rows_pad * octs;
     const int64_t plane = rows_pad * inner_pad;
@@ -323,7 +371,10 @@ __global__ void split_inner_contig(const double* __restrict__ X, int64_t ld, int
         double x[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) x[t] = (valid && q + t < inner) ? X[q + t + r * ld] : 0.0;
-        write_digits8(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
+        if constexpr (RES)
+            write_residues<8>(x, valid, valid ? exps[r] : 0, crt, digits, plane, r * inner_pad + q);
+        else
+            write_digits8(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
     }
 }
 
@@ -334,11 +385,12 @@ __global__ void split_inner_contig(const double* __restrict__ X, int64_t ld, int
 // threads along q) both touch every bank pair evenly, with no padding.
 __device__ __forceinline__ int swz(int q) { return (q >> 2) & 15; }
 constexpr int TT = 64;
+template <bool RES>
 __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int64_t rows,
                                   int64_t inner, const int32_t* __restrict__ exps,
                                   const uint8_t* __restrict__ flags, int S, int beta,
                                   __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad,
-                                  int s_first) {
+                                  int s_first, const __grid_constant__ CrtConsts crt) {
     __shared__ double tile[TT][TT];  // [q][r ^ swz(q)]
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TT;
     const int64_t q0 = static_cast<int64_t>(blockIdx.y) * TT;
@@ -358,7 +410,10 @@ __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int6
         double x[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr ^ swz(qg + t)];
-        write_digits4(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
+        if constexpr (RES)
+            write_residues<4>(x, valid, valid ? exps[r] : 0, crt, digits, plane, r * inner_pad + q);
+        else
+            write_digits4(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
     }
 }
 
@@ -569,16 +624,40 @@ cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, con
     if (split::rows_contiguous(which, op)) {
         dim3 grid(static_cast<unsigned>((rows_pad + TT - 1) / TT), static_cast<unsigned>((inner_pad + TT - 1) / TT));
         if (grid.y > 65535) return cudaErrorInvalidValue;
-        split_rows_contig<<<grid, 256, 0, stream>>>(X, ldx, rows, inner, exps, flags, S, beta, dg,
-                                                    rows_pad, inner_pad, s_first);
+        split_rows_contig<false><<<grid, 256, 0, stream>>>(X, ldx, rows, inner, exps, flags, S, beta, dg,
+                                                           rows_pad, inner_pad, s_first, CrtConsts{});
         return cudaGetLastError();
     }
     const int64_t total = rows_pad * (inner_pad / 8);
     int64_t blocks = (total + 255) / 256;
     const int64_t cap = static_cast<int64_t>(device_sm_count()) * 32;
     if (blocks > cap) blocks = cap;
-    split_inner_contig<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(X, ldx, rows, inner, exps, flags,
-                                                                          S, beta, dg, rows_pad, inner_pad, s_first);
+    split_inner_contig<false><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
+        X, ldx, rows, inner, exps, flags, S, beta, dg, rows_pad, inner_pad, s_first, CrtConsts{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emu_residues(int which, int op, int64_t rows, int64_t inner, const double* X, int64_t ldx,
+                                const int32_t* exps, const uint8_t* flags, const CrtConsts& c, void* planes,
+                                int64_t rows_pad, int64_t inner_pad, cudaStream_t stream) {
+    using namespace split;
+    if (rows_pad <= 0 || inner_pad <= 0) return cudaSuccess;
+    if (c.N < 1 || c.N > kCrtMaxModuli || c.bits < 1 || c.bits > 56 || inner_pad % 8) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(planes) % 16) return cudaErrorInvalidValue;
+    __half* dg = static_cast<__half*>(planes);
+    if (split::rows_contiguous(which, op)) {
+        dim3 grid(static_cast<unsigned>((rows_pad + TT - 1) / TT), static_cast<unsigned>((inner_pad + TT - 1) / TT));
+        if (grid.y > 65535) return cudaErrorInvalidValue;
+        split_rows_contig<true><<<grid, 256, 0, stream>>>(X, ldx, rows, inner, exps, flags, c.N, 7, dg, rows_pad,
+                                                          inner_pad, 0, c);
+        return cudaGetLastError();
+    }
+    const int64_t total = rows_pad * (inner_pad / 8);
+    int64_t blocks = (total + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(device_sm_count()) * 32;
+    if (blocks > cap) blocks = cap;
+    split_inner_contig<true><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
+        X, ldx, rows, inner, exps, flags, c.N, 7, dg, rows_pad, inner_pad, 0, c);
     return cudaGetLastError();
 }
 

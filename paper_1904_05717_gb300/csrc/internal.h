@@ -52,6 +52,41 @@ cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, con
                              int beta, void* digits, int64_t rows_pad, int64_t inner_pad,
                              cudaStream_t stream, int s_first = 0);
 
+// ----------------------------------------------- emulated FP64, modular (CRT) encoding
+// The operands are truncated to integers of `bits` bits (the first bits/7 digits of the slice
+// encoding, A^ = trunc(A 2^(bits - e))), the exact integer product A^ B^ is computed modulo N
+// pairwise coprime moduli p_l <= 255 -- one fp16 tensor product of residues |r| <= 127 per
+// modulus -- and rebuilt by the Chinese remainder theorem; C := alpha 2^(e + f - 2 bits) A^B^
+// + beta C.  N products instead of the S(S+1)/2 of the slice encoding.
+constexpr int kCrtMaxModuli = 14;
+struct CrtConsts {                 // residue split and slice-product epilogue
+    int N;                         // moduli in use
+    int bits;                      // integer width of the operands (7 x slices)
+    uint32_t p[kCrtMaxModuli];
+    uint32_t magic[kCrtMaxModuli]; // floor(2^32 / p) + 1: exact quotients of a < 2^26
+    uint32_t c16[kCrtMaxModuli];   // 2^16 mod p
+    uint32_t c32[kCrtMaxModuli];   // 2^32 mod p
+};
+struct CrtRecon {                  // reconstruction
+    int N, bits;
+    uint32_t w[kCrtMaxModuli][4];  // CRT weights w_l < P in 32-bit limbs, least significant first
+    unsigned long long P_lo, P_hi; // P = prod p_l
+    float Pinv;                    // 1 / P in fp32 (quotient estimates)
+};
+// The moduli for `bits`-bit operands and contraction length k (|A^ B^| < P/2); false when more
+// than kCrtMaxModuli would be needed.
+bool crt_plan(int bits, int64_t k, CrtConsts* c, CrtRecon* r);
+// Largest k one modular product keeps exact in int32 (k * 127^2 < 2^31), a multiple of 64.
+int64_t crt_max_k();
+// Residues of the integer operand, layout [N][rows_pad][inner_pad] fp16 (as the digit slices).
+cudaError_t launch_emu_residues(int which, int op, int64_t rows, int64_t inner, const double* X, int64_t ldx,
+                                const int32_t* exps, const uint8_t* flags, const CrtConsts& c, void* planes,
+                                int64_t rows_pad, int64_t inner_pad, cudaStream_t stream);
+// C from the residue planes of the product ([N][n][m] bytes, residue in [0, p_l)).
+cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, const CrtRecon& r, const int32_t* e,
+                                   const uint8_t* ef, const int32_t* f, const uint8_t* ff, double alpha,
+                                   double beta, double* C, int64_t ldc, cudaStream_t stream);
+
 struct EmuGemmArgs {
     int64_t m, n, k;
     int S, beta;
@@ -74,6 +109,8 @@ struct EmuGemmArgs {
     int* used_ctas;   // optional out: persistent CTAs launched
     int* used_group;  // optional out: C2 raster group used
     int* used_launches;  // optional out: kernels launched (a tail launch per pass when split)
+    const CrtConsts* crt;  // modular encoding: S = N moduli, the epilogue writes residues to `res`
+    uint8_t* res;          // [N][n][m] residues of the product (modular encoding only)
 };
 constexpr int kEmuBM = 128, kEmuBK = 64, kEmuBNMax = 192;
 

@@ -272,4 +272,14 @@ MOMMS_DEV double pow2_normal(int x) {
     return __longlong_as_double(static_cast<long long>(x + 1023) << 52);
 }
 
+// r * 2^E with one rounding for every E (two exact power-of-two factors outside
+// the normal exponent range; results beyond the double range saturate to 0 / inf).
+MOMMS_DEV double scale_pow2(double r, int E) {
+    if (E >= -1022 && E <= 1023) return r * pow2_normal(E);
+    const int E1 = E > 0 ? 960 : -960;
+    int E2 = E - E1;
+    E2 = E2 > 1023 ? 1023 : (E2 < -1022 ? -1022 : E2);
+    return (r * pow2_normal(E1)) * pow2_normal(E2);
+}
+
 }  // namespace momms

@@ -32,6 +32,7 @@ LOWER, UPPER = 0, 1
 LEFT, RIGHT = 0, 1
 NON_UNIT, UNIT = 0, 1
 MODE_AUTO, MODE_NATIVE, MODE_EMULATED = 0, 1, 2
+SCHEME_AUTO, SCHEME_SLICES, SCHEME_MODULI = 0, 1, 2
 MEMBER_AUTO, MEMBER_C2, MEMBER_A2, MEMBER_B2, MEMBER_A1 = 0, 1, 2, 3, 4
 MEMBER_NAMES = {MEMBER_C2: "C2", MEMBER_A2: "A2", MEMBER_B2: "B2", MEMBER_A1: "A1"}
 MAX_SLICES = 16
@@ -48,7 +49,8 @@ class Report(ctypes.Structure):
                 ("digit_bits", ctypes.c_int), ("k_passes", ctypes.c_int), ("tile_m", ctypes.c_int),
                 ("tile_n", ctypes.c_int), ("ctas", ctypes.c_int), ("group", ctypes.c_int),
                 ("launches", ctypes.c_int64), ("est_err_ratio", ctypes.c_double),
-                ("ooc_block", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+                ("ooc_block", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
+                ("moduli", ctypes.c_int), ("operand_bits", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -67,6 +69,12 @@ _SIGS = {
     "momms_set_max_ctas": ([_VP, _I32], _I32),
     "momms_set_raster_group": ([_VP, _I32], _I32),
     "momms_set_tile_n": ([_VP, _I32], _I32),
+    "momms_set_scheme": ([_VP, _I32], _I32),
+    "momms_crt_moduli": ([_I32, _I64, _VP, _VP], _I32),
+    "momms_emu_residue_gemm": ([_I64, _I64, _I64, _I32, _VP, _VP, _I64, _I64, _I64, _I32, _VP, _VP, _SZ, _VP, _VP],
+                               _I32),
+    "momms_crt_reconstruct": ([_I64, _I64, _I64, _I32, _VP, _VP, _VP, _VP, _VP, _DBL, _DBL, _VP, _I64, _VP], _I32),
+    "momms_emu_residues": ([_I32, _I32, _I64, _I64, _VP, _I64, _VP, _VP, _I32, _I64, _VP, _I64, _I64, _VP], _I32),
     "momms_get_last_report": ([_VP, ctypes.POINTER(Report)], _I32),
     "momms_check_device_status": ([_VP, _VP], _I32),
     "momms_status_string": ([_I32], ctypes.c_char_p),
@@ -198,6 +206,32 @@ def momms_emu_split(which, op, rows, inner, X, ldx, exps, flags, slices, digit_b
                                  digit_bits, _VP(digits), rows_pad, inner_pad, _stream(stream))
 
 
+def momms_crt_moduli(bits, k):
+    """The moduli the modular encoding uses for `bits`-bit operands and contraction length k
+    (a list), or raises MommsError when they do not exist."""
+    count = ctypes.c_int(0)
+    buf = (ctypes.c_uint32 * 14)()
+    check(lib().momms_crt_moduli(bits, k, ctypes.byref(count), buf), "momms_crt_moduli")
+    return [int(buf[i]) for i in range(count.value)]
+
+
+def momms_emu_residues(which, op, rows, inner, X, ldx, exps, flags, bits, k, planes, rows_pad, inner_pad,
+                       stream=None):
+    return lib().momms_emu_residues(which, op, rows, inner, _VP(X), ldx, _VP(exps), _VP(flags), bits, k,
+                                    _VP(planes), rows_pad, inner_pad, _stream(stream))
+
+
+def momms_emu_residue_gemm(m, n, k, bits, Ar, Br, m_pad, n_pad, k_pad, member, res, scratch, scratch_bytes, status,
+                           stream=None):
+    return lib().momms_emu_residue_gemm(m, n, k, bits, _VP(Ar), _VP(Br), m_pad, n_pad, k_pad, member, _VP(res),
+                                        _VP(scratch), scratch_bytes, _VP(status), _stream(stream))
+
+
+def momms_crt_reconstruct(m, n, k, bits, res, e, ef, f, ff, alpha, beta, C, ldc, stream=None):
+    return lib().momms_crt_reconstruct(m, n, k, bits, _VP(res), _VP(e), _VP(ef), _VP(f), _VP(ff), alpha, beta,
+                                       _VP(C), ldc, _stream(stream))
+
+
 def momms_emu_slice_gemm(m, n, k, slices, digit_bits, Ad, Bd, m_pad, n_pad, k_pad, e, ef, f, ff, alpha,
                          beta, C, ldc, member, scratch, scratch_bytes, status, stream=None):
     return lib().momms_emu_slice_gemm(m, n, k, slices, digit_bits, _VP(Ad), _VP(Bd), m_pad, n_pad, k_pad,
@@ -240,12 +274,14 @@ def _h(handle):
 class Handle:
     """Owns a momms_handle_t."""
 
-    def __init__(self, mode=MODE_AUTO, member=MEMBER_AUTO, slices=0):
+    def __init__(self, mode=MODE_AUTO, member=MEMBER_AUTO, slices=0, scheme=SCHEME_AUTO):
         self.ptr = _VP()
         check(lib().momms_create(ctypes.byref(self.ptr)), "momms_create")
         self.set_mode(mode)
         self.set_member(member)
         self.set_slices(slices)
+        if scheme != SCHEME_AUTO:
+            self.set_scheme(scheme)
 
     def close(self):
         if self.ptr:
@@ -275,6 +311,9 @@ class Handle:
 
     def set_tile_n(self, tile_n):
         check(lib().momms_set_tile_n(self.ptr, tile_n), "momms_set_tile_n")
+
+    def set_scheme(self, scheme):
+        check(lib().momms_set_scheme(self.ptr, scheme), "momms_set_scheme")
 
     def report(self):
         r = Report()

@@ -75,8 +75,10 @@ def test_split_bitwise(which, op, S, beta):
     assert not np.any(got[:, rows:, :]) and not np.any(got[:, :, inner:])  # zero padding
 
 
-def emulated(A, B, C0, alpha, beta, S, opa=0, opb=0, member=M.MEMBER_AUTO, ldc=None, ctas=0):
-    h = M.Handle(mode=M.MODE_EMULATED, member=member, slices=S)
+def emulated(A, B, C0, alpha, beta, S, opa=0, opb=0, member=M.MEMBER_AUTO, ldc=None, ctas=0,
+             scheme=M.SCHEME_SLICES):
+    # the digit-slice encoding unless a test asks otherwise (test_gpu_moduli covers the other)
+    h = M.Handle(mode=M.MODE_EMULATED, member=member, slices=S, scheme=scheme)
     h.set_max_ctas(ctas)
     dA = M.DeviceMatrix.from_numpy(A)
     dB = M.DeviceMatrix.from_numpy(B)
@@ -119,12 +121,13 @@ def test_fp32_tensor_memory_accumulation_is_exact():
 
 @pytest.mark.parametrize("kind,phi,S", [("uniform", 0.0, 7), ("phi", 1.0, 9), ("phi", 4.0, 12)])
 @pytest.mark.parametrize("m,n,k", [(130, 270, 333), (256, 512, 1024)])
-def test_emulated_within_bound(kind, phi, S, m, n, k):
+@pytest.mark.parametrize("scheme", [M.SCHEME_SLICES, M.SCHEME_AUTO])
+def test_emulated_within_bound(kind, phi, S, m, n, k, scheme):
     A = syn.matrix(kind, m, k, 41, phi=phi)
     B = syn.matrix(kind, k, n, 42, phi=phi)
     C0 = syn.matrix("uniform", m, n, 43)
     Cref, N = reference(A, B, C0, 1.0, 1.0)
-    C, _, _ = emulated(A, B, C0, 1.0, 1.0, S)
+    C, _, _ = emulated(A, B, C0, 1.0, 1.0, S, scheme=scheme)
     assert max_ratio(C, Cref, k, 1.0, 1.0, N, C0) <= 1.0
 
 
@@ -213,12 +216,13 @@ def test_emulated_nonfinite_rows_give_nan():
 
 
 @pytest.mark.parametrize("phi", [0.0, 1.0, 4.0])
-def test_emulated_auto_slices_meet_bound(phi):
+@pytest.mark.parametrize("scheme", [M.SCHEME_SLICES, M.SCHEME_AUTO])
+def test_emulated_auto_slices_meet_bound(phi, scheme):
     m, n, k = 200, 300, 1024
     A = syn.matrix("phi", m, k, 101, phi=phi)
     B = syn.matrix("phi", k, n, 102, phi=phi)
     Cref, N = reference(A, B)
-    C, rep, _ = emulated(A, B, F(np.zeros((m, n))), 1.0, 0.0, 0)
+    C, rep, _ = emulated(A, B, F(np.zeros((m, n))), 1.0, 0.0, 0, scheme=scheme)
     assert 3 <= rep["slices"] <= 14
     assert max_ratio(C, Cref, k, 1.0, 0.0, N) <= 1.0
 

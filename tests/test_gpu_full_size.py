@@ -45,8 +45,8 @@ def freivalds_ok(A, B, C0, C, alpha, beta, seed=7):
     return bool(np.all(np.abs(lhs - rhs) <= tol))
 
 
-def run(A, B, C0, mode, slices=0, alpha=1.0, beta=1.0):
-    h = M.Handle(mode=mode, slices=slices)
+def run(A, B, C0, mode, slices=0, alpha=1.0, beta=1.0, scheme=M.SCHEME_AUTO):
+    h = M.Handle(mode=mode, slices=slices, scheme=scheme)
     dA, dB, dC = M.DeviceMatrix.from_numpy(A), M.DeviceMatrix.from_numpy(B), M.DeviceMatrix.from_numpy(C0)
     M.gemm(dA, dB, dC, alpha, beta, handle=h)
     assert h.device_status() == M.MOMMS_OK
@@ -64,7 +64,25 @@ def test_square_8192_auto_as_benchmarked():
     B = syn.matrix("uniform", n, n, syn.workload_seed(1, "B"))
     C0 = syn.matrix("uniform", n, n, syn.workload_seed(1, "C"))
     C, rep = run(A, B, C0, M.MODE_AUTO)
-    assert rep["mode"] == M.MODE_EMULATED
+    assert rep["mode"] == M.MODE_EMULATED and rep["moduli"] > 0
+    assert sample_ratio(A, B, C0, C, 1.0, 1.0) <= 1.0
+    assert freivalds_ok(A, B, C0, C, 1.0, 1.0)
+    # sampled elements bit for bit against the definition of the modular result: the exact
+    # product of the truncated rows and columns (their exponents span the whole k), rounded once
+    rs = np.array([0, 4095, 8191])
+    cs = np.array([0, 5000, 8191])
+    Co, _ = oracle.modular_dgemm(np.asfortranarray(A[rs, :]), np.asfortranarray(B[:, cs]), rep["operand_bits"],
+                                 np.asfortranarray(C0[np.ix_(rs, cs)]), 1.0, 1.0)
+    assert np.array_equal(C[np.ix_(rs, cs)], Co)
+
+
+def test_square_8192_slices():
+    n = 8192
+    A = syn.matrix("uniform", n, n, syn.workload_seed(1, "A"))
+    B = syn.matrix("uniform", n, n, syn.workload_seed(1, "B"))
+    C0 = syn.matrix("uniform", n, n, syn.workload_seed(1, "C"))
+    C, rep = run(A, B, C0, M.MODE_EMULATED, scheme=M.SCHEME_SLICES)
+    assert rep["moduli"] == 0
     assert sample_ratio(A, B, C0, C, 1.0, 1.0) <= 1.0
     assert freivalds_ok(A, B, C0, C, 1.0, 1.0)
 

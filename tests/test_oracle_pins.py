@@ -286,6 +286,115 @@ def test_emulated_nonfinite_rows_flagged_nan():
     assert np.all(np.isfinite(C[mask]))
 
 
+# --------------------------------------------------------------------------- modular encoding
+def test_truncated_integers_are_the_digit_expansion():
+    # bits = 7 S: X^ is the first S truncation digits read as one integer (the C split's digits)
+    for which, trans in (("rows", False), ("cols", False), ("rows", True)):
+        X = syn.matrix("phi", 9, 23, 141, phi=2.0)
+        e, fl = oracle.exponents(X, which, trans)
+        for S in (1, 3, 6):
+            D = oracle.split(X, which, e, fl, S, 7, trans)
+            Xh = oracle.truncated_integers(X, which, e, fl, 7 * S, trans)
+            expansion = sum(D[s].astype(object) * (2 ** (7 * (S - 1 - s))) for s in range(S))
+            assert np.array_equal(Xh, expansion)
+
+
+def test_truncated_integers_truncation_identity():
+    # any width: 0 <= |x| 2^(bits - e) - |X^| < 1, same sign, |X^| < 2^bits
+    X = syn.matrix("phi", 7, 31, 142, phi=3.0)
+    e, fl = oracle.exponents(X, "rows")
+    for bits in (5, 20, 39, 56):
+        Xh = oracle.truncated_integers(X, "rows", e, fl, bits)
+        for i in range(7):
+            for q in range(31):
+                scaled = Fraction(float(X[i, q])) * Fraction(2) ** (bits - int(e[i]))
+                h = int(Xh[i, q])
+                assert abs(h) < 2 ** bits and 0 <= abs(scaled) - abs(h) < 1
+                assert h == 0 or (h > 0) == (X[i, q] > 0)
+    assert int(oracle.truncated_integers(F([[0.75]]), "rows", np.array([0]), np.array([0]), 3)[0, 0]) == 6
+
+
+def test_greedy_moduli_are_pairwise_coprime_and_hand_listed():
+    mods = oracle.greedy_moduli(14)
+    assert all(math.gcd(a, b) == 1 for i, a in enumerate(mods) for b in mods[i + 1:])
+    # 252 = 2^2 3^2 7 and 250 = 2 5^3 share factors with 255 = 3 5 17 / 254 = 2 127; 217 = 7 31
+    # is the first composite taken after 247 = 13 19; 221 = 13 17 and 209 = 11 19 are skipped
+    assert mods == [255, 254, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199]
+    assert all(abs(p // 2) <= 127 for p in mods)
+
+
+def test_centred_residues_reconstruct_through_library_crt():
+    sympy_crt = pytest.importorskip("sympy.ntheory.modular").crt
+    mods = oracle.greedy_moduli(13)
+    rng = np.random.default_rng(143)
+    vals = np.array([int(v) for v in rng.integers(-2 ** 62, 2 ** 62, 40)] + [0, 1, -1, 127, -128, 2 ** 80, -(2 ** 80) + 7],
+                    dtype=object).reshape(47, 1)
+    R = oracle.centred_residues(vals, mods)
+    for l, p in enumerate(mods):
+        assert R[l].min() >= -(p // 2) and R[l].max() <= (p - 1) // 2
+    P = math.prod(mods)
+    for t in range(vals.shape[0]):
+        x, _ = sympy_crt(mods, [int(R[l, t, 0]) % p for l, p in enumerate(mods)])
+        x = int(x)
+        assert (x - P if x > P // 2 else x) == int(vals[t, 0])
+        assert oracle.crt_reconstruct([int(R[l, t, 0]) for l in range(len(mods))], mods) == int(vals[t, 0])
+
+
+def test_moduli_suffice_matches_the_range_argument():
+    mods = oracle.greedy_moduli(13)
+    P = math.prod(mods)
+    # 42-bit operands, k = 8192: |sum| <= k (2^42 - 1)^2 < 2^97 < P / 2
+    assert oracle.moduli_suffice(mods, 42, 8192) and P > 2 * 8192 * (2 ** 42 - 1) ** 2
+    assert not oracle.moduli_suffice(mods[:12], 42, 8192)
+    assert not oracle.moduli_suffice(oracle.greedy_moduli(14), 49, 8192)
+
+
+def test_modular_dgemm_integer_inputs_exact():
+    m, n, k = 11, 9, 30
+    A = syn.matrix("int", m, k, 144)
+    B = syn.matrix("int", k, n, 145)
+    C0 = syn.matrix("int", m, n, 146)
+    C, _ = oracle.modular_dgemm(A, B, 21, C0.copy(order="F"), 1.0, 1.0)
+    assert np.array_equal(C, A @ B + C0)
+
+
+def test_modular_dgemm_equals_one_slice_emulation_bitwise():
+    # bits = 7: the one-slice emulation keeps its only digit pair, so both compute the same exact
+    # integer product, rounded once
+    A = syn.matrix("phi", 8, 40, 147, phi=1.0)
+    B = syn.matrix("phi", 40, 6, 148, phi=1.0)
+    C1, _ = oracle.emulated_dgemm(A, B, S=1, beta_bits=7)
+    C2, _ = oracle.modular_dgemm(A, B, 7)
+    assert np.array_equal(C1, C2)
+
+
+@pytest.mark.parametrize("transa,transb", [(False, False), (True, True)])
+def test_modular_dgemm_within_bound_at_full_width(transa, transb):
+    m, n, k = 7, 6, 50
+    A = syn.matrix("phi", k if transa else m, m if transa else k, 149, phi=1.0)
+    B = syn.matrix("phi", n if transb else k, k if transb else n, 150, phi=1.0)
+    C, _ = oracle.modular_dgemm(A, B, 56, transa=transa, transb=transb)
+    ex = exact_product(A, B, transa, transb)
+    N = oracle.dgemm_abs(A, B, transa, transb)
+    for i in range(m):
+        for j in range(n):
+            assert abs(Fraction(float(C[i, j])) - ex[i][j]) <= Fraction(4 * k * U) * Fraction(float(N[i, j]))
+
+
+def test_modular_dgemm_alpha_beta_fma_and_nan():
+    A = syn.matrix("uniform", 4, 10, 151)
+    A[1, 3] = np.nan
+    B = syn.matrix("uniform", 10, 3, 152)
+    C0 = syn.matrix("uniform", 4, 3, 153)
+    C, det = oracle.modular_dgemm(A, B, 30, C0.copy(order="F"), -0.5, 3.0)
+    assert np.all(np.isnan(C[1, :])) and det["eflag"][1] == 1
+    for i in (0, 2, 3):
+        for j in range(3):
+            y = math.ldexp(float(det["Z"][i, j]), int(det["e"][i]) + int(det["f"][j]) - 60)
+            exact = Fraction(3.0) * Fraction(float(C0[i, j])) + Fraction(-0.5 * y)
+            assert C[i, j] == float(exact)
+
+
 # --------------------------------------------------------------------------- I/O counts
 def closed_form(member, m, n, k, b1, b2, c_read):
     """The paper's resident-algorithm I/O counts in margin (ceiling) form, Sec. 2.2."""
