@@ -429,7 +429,7 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     h->report.digit_bits = bb;
     h->report.k_passes = passes;
     h->report.tile_m = momms::kEmuBM;
-    h->report.tile_n = momms::emu_pick_bn(m, n, k, h->tile_n);
+    h->report.tile_n = momms::emu_pick_bn(m, n, k, h->tile_n, mod ? cc.N : 1);
     h->report.launches = launches;
     h->report.est_err_ratio = est;
     h->report.moduli = mod ? cc.N : 0;

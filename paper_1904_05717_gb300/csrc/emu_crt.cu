@@ -51,76 +51,81 @@ MOMMS_DEV double u128_to_double(u128 v) {
     return static_cast<double>(top) * pow2_normal(64 - lz);
 }
 
-// One element of C from its limb sums s_q = sum_l c_l w_l[q] (the CRT sum in 32-bit limbs):
-// the sum mod P, centred, rounded once to FP64 with its power-of-two scale folded into the
-// exponent field, then alpha / beta.  Integer arithmetic throughout except the last step (FP64
-// ALU work is scarce on this part); an exponent outside the normal range takes the FP64 route.
-MOMMS_DEV double crt_element(const unsigned long long (&s)[4], const CrtRecon& r, const u128 P, const u128 half,
-                             int E, bool flag, double alpha, double beta, const double* cp) {
-    // carries between the limbs: acc = s_0 + s_1 2^32 + s_2 2^64 + s_3 2^96 < N 256 P < 2^128
+// |Z| for one element from its limb sums s_q = sum_l c_l w_l[q] (the CRT sum in L 32-bit
+// limbs), reduced mod P and centred; integer arithmetic only (FP64 ALU work is scarce on this
+// part).  Returns the magnitude, *neg its sign.
+template <int L>
+MOMMS_DEV u128 crt_magnitude(const unsigned long long (&s)[4], const u128 P, const u128 half, float Pinv,
+                             bool* neg) {
+    // carries between the limbs: acc = sum_q s_q 2^(32 q) < N 256 P < 2^128
     const unsigned long long t1 = s[1] + (s[0] >> 32);
     const unsigned long long t2 = s[2] + (t1 >> 32);
-    const unsigned long long t3 = s[3] + (t2 >> 32);
     const unsigned long long lo = (s[0] & 0xFFFFFFFFull) | (t1 << 32);
-    const unsigned long long hi = (t2 & 0xFFFFFFFFull) | (t3 << 32);
+    unsigned long long hi;
+    if constexpr (L == 4) hi = (t2 & 0xFFFFFFFFull) | ((s[3] + (t2 >> 32)) << 32);
+    else hi = t2;
     u128 acc = (static_cast<u128>(hi) << 64) | lo;
     // acc mod P: an fp32 quotient estimate (relative error ~2^-21 on a quotient below 2^12, so
-    // off by at most one) and one exact correction either way
-    const float accf = __ull2float_rn(hi) * 18446744073709551616.0f + __ull2float_rn(lo);
-    const uint32_t q = static_cast<uint32_t>(accf * r.Pinv);
+    // off by at most one) and one exact correction either way.  The estimate converts the
+    // leading 32 bits of acc (64-bit conversions would run on the scarce FP64 pipe) and puts
+    // their weight 2^(96 - lz) into the exponent field.
+    uint32_t q = 0;
+    if (hi | lo) {
+        const int lz = hi ? __clzll(static_cast<long long>(hi)) : 64 + __clzll(static_cast<long long>(lo));
+        const uint32_t top = static_cast<uint32_t>((acc << lz) >> 96);
+        const float scale = __int_as_float((127 + 96 - lz) << 23);
+        q = static_cast<uint32_t>(__uint2float_rz(top) * scale * Pinv);
+    }
     const u128 qP = static_cast<u128>(q) * P;
     acc = qP > acc ? acc + P - qP : acc - qP;
     if (acc >= P) acc -= P;
-    const bool neg = acc > half;
-    const u128 mag = neg ? P - acc : acc;
-    double y;
-    if (flag) {
-        y = __longlong_as_double(0x7ff8000000000000ll);
-    } else if (mag == 0) {
-        y = 0.0;
-    } else {
-        const unsigned long long mh = static_cast<unsigned long long>(mag >> 64);
-        const unsigned long long ml = static_cast<unsigned long long>(mag);
-        const int lz = mh ? __clzll(static_cast<long long>(mh)) : 64 + __clzll(static_cast<long long>(ml));
-        const u128 t = mag << lz;  // leading one at bit 127
-        const unsigned long long top = static_cast<unsigned long long>(t >> 64) |
-                                       static_cast<unsigned long long>(static_cast<unsigned long long>(t) != 0);
-        // round the 64-bit significand to 53 bits, to nearest, ties to even
-        unsigned long long mant = top >> 11;
-        const unsigned long long rem = top & 0x7FFull;
-        mant += (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
-        int ex = 127 - lz + E;  // unbiased exponent of |y| = mant 2^(ex - 52)
-        if (mant == (1ull << 53)) {
-            mant >>= 1;
-            ++ex;
-        }
-        if (ex >= -1022 && ex <= 1023) {
-            y = __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(neg) << 63) |
-                                                            (static_cast<unsigned long long>(ex + 1023) << 52) |
-                                                            (mant & ((1ull << 52) - 1))));
-        } else {
-            y = scale_pow2(u128_to_double(mag), E);
-            if (neg) y = -y;
-        }
+    *neg = acc > half;
+    return *neg ? P - acc : acc;
+}
+
+// mag 2^E with the sign, rounded once to FP64 (to nearest, ties to even): the 53-bit
+// significand is rounded in integers and the scale goes into the exponent field; an exponent
+// outside the normal range takes the FP64 route.
+MOMMS_DEV double scaled_double(u128 mag, bool neg, int E) {
+    if (mag == 0) return 0.0;
+    const unsigned long long mh = static_cast<unsigned long long>(mag >> 64);
+    const unsigned long long ml = static_cast<unsigned long long>(mag);
+    const int lz = mh ? __clzll(static_cast<long long>(mh)) : 64 + __clzll(static_cast<long long>(ml));
+    const u128 t = mag << lz;  // leading one at bit 127
+    const unsigned long long top = static_cast<unsigned long long>(t >> 64) |
+                                   static_cast<unsigned long long>(static_cast<unsigned long long>(t) != 0);
+    unsigned long long mant = top >> 11;
+    const unsigned long long rem = top & 0x7FFull;
+    mant += (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+    int ex = 127 - lz + E;  // unbiased exponent of |y| = mant 2^(ex - 52)
+    if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++ex;
     }
-    const double ay = alpha == 1.0 ? y : alpha * y;
-    return beta == 0.0 ? ay : fma(beta, *cp, ay);
+    if (ex >= -1022 && ex <= 1023)
+        return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(neg) << 63) |
+                                                           (static_cast<unsigned long long>(ex + 1023) << 52) |
+                                                           (mant & ((1ull << 52) - 1))));
+    const double y = scale_pow2(u128_to_double(mag), E);
+    return neg ? -y : y;
 }
 
 // C from the residue bytes res[l][j][i] (m n per modulus).  Blocks stride over the columns,
-// threads over the rows of a column; with VEC (m a multiple of 4) a thread takes four
-// consecutive rows and loads one 32-bit word per modulus.
-template <bool VEC>
+// threads over the rows of a column; with V = 4 (m a multiple of 4) a thread takes four
+// consecutive rows and loads one 32-bit word per modulus, and with CV (16-byte aligned pairs
+// of C) reads and writes C as two double2.  L: 32-bit limbs of the CRT weights (3 when P < 2^96).
+template <int V, bool CV, int L>
 __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
                                                   const __grid_constant__ CrtRecon r,
                                                   const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
                                                   const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
                                                   double alpha, double beta, double* __restrict__ C, int64_t ldc) {
-    constexpr int V = VEC ? 4 : 1;
     const int64_t mn = m * n;
     const int64_t groups = m / V;
     const u128 P = (static_cast<u128>(r.P_hi) << 64) | r.P_lo;
     const u128 half = P >> 1;
+    const bool unit_alpha = alpha == 1.0, beta_zero = beta == 0.0;
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
         const int Ej = f[j] - 2 * r.bits;
         const bool fj = ff[j] != 0;
@@ -135,23 +140,41 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
             const uint8_t* src = res + j * m + i0;
             for (int l = 0; l < r.N; ++l) {
                 uint32_t word;
-                if constexpr (VEC) word = __ldcs(reinterpret_cast<const unsigned int*>(src + l * mn));
+                if constexpr (V == 4) word = __ldcs(reinterpret_cast<const unsigned int*>(src + l * mn));
                 else word = src[l * mn];
-                const uint32_t w0 = r.w[l][0], w1 = r.w[l][1], w2 = r.w[l][2], w3 = r.w[l][3];
 #pragma unroll
                 for (int t = 0; t < V; ++t) {
                     const uint32_t c = (word >> (8 * t)) & 0xFFu;
-                    s[t][0] += static_cast<unsigned long long>(c) * w0;
-                    s[t][1] += static_cast<unsigned long long>(c) * w1;
-                    s[t][2] += static_cast<unsigned long long>(c) * w2;
-                    s[t][3] += static_cast<unsigned long long>(c) * w3;
+#pragma unroll
+                    for (int q = 0; q < L; ++q) s[t][q] += static_cast<unsigned long long>(c) * r.w[l][q];
                 }
             }
+            double y[V];
 #pragma unroll
             for (int t = 0; t < V; ++t) {
+                bool neg;
+                const u128 mag = crt_magnitude<L>(s[t], P, half, r.Pinv, &neg);
                 const int64_t i = i0 + t;
-                double* cp = C + i + j * ldc;
-                *cp = crt_element(s[t], r, P, half, e[i] + Ej, fj || ef[i] != 0, alpha, beta, cp);
+                y[t] = (fj || ef[i] != 0) ? qnan : scaled_double(mag, neg, e[i] + Ej);
+                if (!unit_alpha) y[t] *= alpha;
+            }
+            double* cp = C + i0 + j * ldc;
+            if constexpr (CV) {
+                double2* c2 = reinterpret_cast<double2*>(cp);
+                double2 a = beta_zero ? make_double2(0.0, 0.0) : __ldcs(c2);
+                double2 b = beta_zero ? make_double2(0.0, 0.0) : __ldcs(c2 + 1);
+                if (!beta_zero) {
+                    a.x = fma(beta, a.x, y[0]); a.y = fma(beta, a.y, y[1]);
+                    b.x = fma(beta, b.x, y[2]); b.y = fma(beta, b.y, y[3]);
+                } else {
+                    a = make_double2(y[0], y[1]);
+                    b = make_double2(y[2], y[3]);
+                }
+                __stcs(c2, a);
+                __stcs(c2 + 1, b);
+            } else {
+#pragma unroll
+                for (int t = 0; t < V; ++t) cp[t] = beta_zero ? y[t] : fma(beta, cp[t], y[t]);
             }
         }
     }
@@ -204,6 +227,8 @@ cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, con
                                    double beta, double* C, int64_t ldc, cudaStream_t stream) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     const bool vec = m % 4 == 0 && reinterpret_cast<uintptr_t>(res) % 4 == 0;
+    const bool cvec = vec && ldc % 2 == 0 && reinterpret_cast<uintptr_t>(C) % 16 == 0;
+    const bool three = r.P_hi < (1ull << 32);  // P < 2^96: the weights fit three limbs
     const int64_t groups = vec ? m / 4 : m;
     int64_t bx = (groups + 255) / 256;
     if (bx > 64) bx = 64;
@@ -212,8 +237,18 @@ cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, con
     if (by > n) by = n;
     if (by > 65535) by = 65535;
     const dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(by));
-    if (vec) crt_kernel<true><<<grid, 256, 0, stream>>>(m, n, res, r, e, ef, f, ff, alpha, beta, C, ldc);
-    else crt_kernel<false><<<grid, 256, 0, stream>>>(m, n, res, r, e, ef, f, ff, alpha, beta, C, ldc);
+#define MOMMS_CRT_LAUNCH(V, CV, L) \
+    crt_kernel<V, CV, L><<<grid, 256, 0, stream>>>(m, n, res, r, e, ef, f, ff, alpha, beta, C, ldc)
+    if (cvec) {
+        if (three) MOMMS_CRT_LAUNCH(4, true, 3);
+        else MOMMS_CRT_LAUNCH(4, true, 4);
+    } else if (vec) {
+        if (three) MOMMS_CRT_LAUNCH(4, false, 3);
+        else MOMMS_CRT_LAUNCH(4, false, 4);
+    } else {
+        MOMMS_CRT_LAUNCH(1, false, 4);
+    }
+#undef MOMMS_CRT_LAUNCH
     return cudaGetLastError();
 }
 

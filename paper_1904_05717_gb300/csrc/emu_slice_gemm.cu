@@ -121,9 +121,22 @@ struct Params {
 // The it-th tile of this CTA: its problem (-1 = the single problem of p.one) and tile
 // coordinates.  A single problem uses the member's tile order; a batch walks the
 // concatenated tile list of all problems cyclically.
-template <bool TAIL>
-MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int* part) {
+template <bool TAIL, bool MOD = false>
+MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int* part, int* lmod = nullptr) {
     *part = -1;
+    if constexpr (MOD) {
+        // modular encoding: the unit is one modulus of one tile, units handed out round-robin in
+        // modulus-major order -- a wave covers one modulus of a block of tiles (the member's
+        // order; A1 visits rows as A2 does) and the last round is the only partial one
+        const int64_t tiles = static_cast<int64_t>(p.tiles_m) * p.tiles_n;
+        const int64_t u = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
+        if (u >= tiles * p.one.S) return false;
+        *prob = -1;
+        *lmod = static_cast<int>(u / tiles);
+        const int64_t t = u - *lmod * tiles;
+        const int member = p.member == kMemberA1 ? kMemberA2 : p.member;
+        return member_tile(member, p.group, t % gridDim.x, gridDim.x, t / gridDim.x, p.tiles_m, p.tiles_n, tm, tn);
+    }
     if constexpr (TAIL) {
         // the tail launch: CTA b takes k part b % parts of tail tile b / parts, the tail tiles
         // being the last, partial round of the main launch's round-robin order
@@ -570,7 +583,7 @@ __global__ void __launch_bounds__(256) tail_fixup_kernel(const __grid_constant__
     }
 }
 
-// MOD: the modular encoding -- unit d (from S + 1 down to 2) is modulus l = S + 1 - d, one pair
+// MOD: the modular encoding -- a unit is one modulus l of one tile (p.one.S moduli), one pair
 // (residue plane l of A, plane l of B), and its epilogue stores residues instead of recombining.
 template <int BN, bool TAIL, bool MOD = false>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -631,16 +644,16 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int i = 0; i < STAGES; ++i) last_phase[i] = -1;
             bool ok = true;
             for (int it = 0; ok; ++it) {
-                int tm, tn, prob, part;
-                if (!tile_of<TAIL>(p, it, &prob, &tm, &tn, &part)) break;
+                int tm, tn, prob, part, lm = 0;
+                if (!tile_of<TAIL, MOD>(p, it, &prob, &tm, &tn, &part, &lm)) break;
                 const TileInts pr = tile_ints(p, prob, part);
                 const CUtensorMap* mapA = prob < 0 ? &tmA : &p.table[prob].mapA;
                 const CUtensorMap* mapB = prob < 0 ? &tmB : &p.table[prob].mapB;
 
-                for (int d = pr.S + 1; d >= 2 && ok; --d) {
+                for (int d = MOD ? 2 : pr.S + 1; d >= 2 && ok; --d) {
                     const int npairs = MOD ? 1 : d - 1;
                     for (int s = 1; s <= npairs && ok; ++s) {
-                        const int plane_a = MOD ? pr.S + 1 - d : s - 1;
+                        const int plane_a = MOD ? lm : s - 1;
                         const int plane_b = MOD ? plane_a : d - s - 1;
                         for (int j = 0; j < pr.nslab; ++j) {
                             if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
@@ -679,10 +692,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool ok = true;
             bool issued = false;
             for (int it = 0; ok; ++it) {
-                int tm, tn, prob, part;
-                if (!tile_of<TAIL>(p, it, &prob, &tm, &tn, &part)) break;
+                int tm, tn, prob, part, lm = 0;
+                if (!tile_of<TAIL, MOD>(p, it, &prob, &tm, &tn, &part, &lm)) break;
                 const TileInts pr = tile_ints(p, prob, part);
-                for (int d = pr.S + 1; d >= 2 && ok; --d) {
+                for (int d = MOD ? 2 : pr.S + 1; d >= 2 && ok; --d) {
                     const int units = (MOD ? 1 : d - 1) * pr.nslab;
                     for (int u = 0; u < units && ok;) {
                         const int cnt = min(pr.chunk_slabs, units - u);
@@ -754,14 +767,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         } else {
             bool ok = true;
             for (int it = 0; ok; ++it) {
-                int tm, tn, prob, part;
-                if (!tile_of<false>(p, it, &prob, &tm, &tn, &part)) break;
+                int tm, tn, prob, part, lm = 0;
+                if (!tile_of<false, MOD>(p, it, &prob, &tm, &tn, &part, &lm)) break;
                 const TileInts pr = tile_ints(p, prob, -1);
                 const double rb = pow2_normal(-pr.beta);
                 int gj = 0;           // position of the current diagonal inside its int64 group
                 bool rfirst = true;   // no FP64 partial R yet for this tile
                 if constexpr (!MOD) stage_columns<BN>(p, prob, tn, pr.beta, colexp, colflag);
-                for (int d = pr.S + 1; d >= 2; --d) {
+                for (int d = MOD ? 2 : pr.S + 1; d >= 2; --d) {
                     int32_t acc[CR];
                     if (!drain_diagonal<CR, CT>((MOD ? 1 : d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty,
                                                 abuf, aphase, abort_flag, tmem_base + lane_off + third * CW, tsum,
@@ -770,7 +783,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         break;
                     }
                     if constexpr (MOD)
-                        store_residues<BN, CR, CT>(p, tm, tn, pr.S + 1 - d, third, rloc, acc, tsum);
+                        store_residues<BN, CR, CT>(p, tm, tn, lm, third, rloc, acc, tsum);
                     else
                         recombine_diagonal<BN, CR, CT>(p, prob, tm, tn, d, pr, Q, R, keep, tsum, rb, third, rloc,
                                                        colexp, colflag, qnan, acc, gj, rfirst);
@@ -866,8 +879,9 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     const int sms = device_sm_count();
     const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
     const int64_t tiles = tiles_m * tiles_n;
+    const int64_t units = a.crt ? tiles * a.crt->N : tiles;  // modular encoding: one unit per modulus and tile
     int64_t ctas = a.max_ctas > 0 && a.max_ctas < sms ? a.max_ctas : sms;  // one CTA per SM at most
-    if (ctas > tiles) ctas = tiles;
+    if (ctas > units) ctas = units;
     const size_t half = static_cast<size_t>(ctas) * BN * BM * sizeof(double);
     if (a.scratch_bytes < 2 * half) return cudaErrorInvalidValue;
     // int64 group sums Q in the first half, FP64 partial sums R (several groups only) in the second
@@ -1083,13 +1097,13 @@ int emu_chunk_slabs(int beta) {
 }
 
 // Tile width: an explicit request of 96 or 192, else the narrow tile only when the wide tiles
-// are fewer than the SMs (the narrow ones then put more of the chip to work; measured: 1024^3
-// +28 %).  With enough wide tiles the narrow one loses -- twice the tiles' fixed costs and 40 %
+// (times the units per tile: the moduli of the modular encoding) are fewer than the SMs (the
+// narrow ones then put more of the chip to work; measured: 1024^3 +28 %).  With enough wide tiles the narrow one loses -- twice the tiles' fixed costs and 40 %
 // more operand traffic per flop (rank-k 16384 x 16384 x 256: -10 %, panel: -16 %).
-int emu_pick_bn(int64_t m, int64_t n, int64_t, int requested) {
+int emu_pick_bn(int64_t m, int64_t n, int64_t, int requested, int units_per_tile) {
     if (requested == 96 || requested == 192) return requested;
-    const int64_t wide_tiles = ((m + emu::BM - 1) / emu::BM) * ((n + kEmuBNMax - 1) / kEmuBNMax);
-    return wide_tiles < device_sm_count() ? 96 : 192;
+    const int64_t wide_units = ((m + emu::BM - 1) / emu::BM) * ((n + kEmuBNMax - 1) / kEmuBNMax) * units_per_tile;
+    return wide_units < device_sm_count() ? 96 : 192;
 }
 
 // The C2 group (tile rows of the block of C one wave covers) with the fewest operand rows
@@ -1141,7 +1155,7 @@ cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_
     if (emu_chunk_slabs(a.beta) * BK * ((1ll << a.beta) - 1) * ((1ll << a.beta) - 1) > (1ll << 24))
         return cudaErrorInvalidValue;  // beta too wide for one 64-wide slab per chunk
     if (a.m > (1ll << 30) || a.n > (1ll << 30)) return cudaErrorInvalidValue;
-    if (emu_pick_bn(a.m, a.n, a.k, a.tile_n) == 96) return launch_bn<96>(a, passes, stream);
+    if (emu_pick_bn(a.m, a.n, a.k, a.tile_n, a.crt ? a.crt->N : 1) == 96) return launch_bn<96>(a, passes, stream);
     return launch_bn<192>(a, passes, stream);
 }
 

@@ -169,7 +169,7 @@ cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int 
                                           void* scratch, size_t scratch_bytes, int32_t* status,
                                           cudaStream_t stream);
 // The CTA tile width used for n columns (tile_n request 0 = automatic).
-int emu_pick_bn(int64_t m, int64_t n, int64_t k, int requested);
+int emu_pick_bn(int64_t m, int64_t n, int64_t k, int requested, int units_per_tile = 1);
 // Default C2 group of the slice-product kernel for `ctas` persistent CTAs (tile rows of the
 // block of C one wave covers; fewest operand rows read per unit of k over all waves).
 int emu_default_group(int64_t ctas, int tiles_m, int tiles_n);

@@ -43,8 +43,9 @@ def test_handle_knobs_are_reported():
     M.gemm(A, B, C, 1.0, 0.0, handle=h)
     rep = h.report()
     import torch
-    tiles = -(-700 // 128) * -(-900 // rep["tile_n"])
-    assert rep["ctas"] == min(torch.cuda.get_device_properties(0).multi_processor_count, tiles)
+    # one unit per tile (digit slices) or per tile and modulus (modular encoding)
+    units = -(-700 // 128) * -(-900 // rep["tile_n"]) * max(1, rep["moduli"])
+    assert rep["ctas"] == min(torch.cuda.get_device_properties(0).multi_processor_count, units)
     assert rep["group"] >= 1
     h.close()
 
