@@ -123,10 +123,10 @@ int momms_set_slices(momms_handle_t handle, int slices);
  *           and FP64 (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 2012: the error-free split).
  *   MODULI  the exact integer product A^B^ computed modulo N pairwise coprime moduli <= 255 --
  *           residues |r| <= 127 as fp16, one tensor product per modulus -- and rebuilt by the
- *           Chinese remainder theorem, P = prod p > 2 k (2^b - 1)^2 (Ozaki, Uchino & Imamura,
- *           "Ozaki Scheme II", 2025).  N products instead of S(S+1)/2 (S = 6, k <= 65536: 13
+ *           Chinese remainder theorem, P = prod p > 4 k (2^b - 1)^2 (Ozaki, Uchino & Imamura,
+ *           "Ozaki Scheme II", 2025).  N products instead of S(S+1)/2 (S = 6, k = 8192: 13
  *           instead of 21), and no dropped digit pairs: the only error is the truncation of the
- *           operands.  Needs N <= 14 (S <= 6, or S = 7 with k <= 2048) and k <= 133,120;
+ *           operands.  Needs N <= 16 (any S <= 7; S = 8 for k <= 2048) and k <= 133,120;
  *           otherwise the product falls back to SLICES (report.moduli = 0).
  *   AUTO    MODULI when it takes at least two tensor products fewer than SLICES, else SLICES.
  * With the automatic slice count (momms_set_slices(0)) the modular encoding takes the width
@@ -236,11 +236,13 @@ int momms_emu_split(int which, int op, int64_t rows, int64_t inner, const double
                     momms_stream_t stream);
 
 /* Moduli of the modular encoding (MOMMS_SCHEME_MODULI) for operands of `bits` bits and
- * contraction length k: the fewest of the library's pairwise coprime moduli <= 255 (largest
- * first) whose product P exceeds 2 k (2^bits - 1)^2, so that the centred residue of the exact
- * integer product modulo P is the product itself.  moduli: host array of 14 entries; *count
- * receives N.  Host only (no device work).  Returns -1 for bits outside 1..56, -2 for k < 1,
- * MOMMS_ERR_UNSUPPORTED when more than 14 moduli or k > 133,120 would be needed. */
+ * contraction length k: the fewest of the library's pairwise coprime moduli <= 255 (walking
+ * down from 255, each coprime to all taken before) whose product P exceeds 4 k (2^bits - 1)^2:
+ * the centred residue of the exact integer product modulo P is then the product itself, with
+ * |product| <= P/4 (the margin the reconstruction's quotient estimate uses).  moduli: host
+ * array of 16 entries; *count receives N.  Host only (no device work).  Returns -1 for bits
+ * outside 1..56, -2 for k < 1, MOMMS_ERR_UNSUPPORTED when more than 16 moduli or k > 133,120
+ * would be needed. */
 int momms_crt_moduli(int bits, int64_t k, int* count, uint32_t* moduli);
 
 /* Residues of the integer operand X^ = sign(x) trunc(|x| 2^(bits - e)) (e from

@@ -316,13 +316,14 @@ def greedy_moduli(count):
     return taken
 
 
-def moduli_suffice(moduli, bits, k):
-    """True when the product P of the moduli exceeds 2 k (2^bits - 1)^2, the width of the range
-    of a k-term dot product of `bits`-bit integers: its centred residue mod P is then itself."""
+def moduli_suffice(moduli, bits, k, margin=1):
+    """True when the product P of the moduli exceeds margin * 2 k (2^bits - 1)^2; margin 1: the
+    width of the range of a k-term dot product of `bits`-bit integers, so that its centred
+    residue mod P is the product itself (margin 2 leaves |product| <= P / 4)."""
     P = 1
     for p in moduli:
         P *= int(p)
-    return P > 2 * int(k) * (2 ** int(bits) - 1) ** 2
+    return P > int(margin) * 2 * int(k) * (2 ** int(bits) - 1) ** 2
 
 
 def centred_residues(Xhat, moduli):

@@ -4,7 +4,7 @@
 // The operands are truncated to `bits`-bit integers A^ = trunc(A 2^(bits - e)) (row exponent
 // e), B^ likewise; their exact product is known modulo each of N pairwise coprime moduli
 // p_l <= 255 (one tensor product of residues per modulus, emu_slice_gemm.cu), and as
-// |A^ B^| <= k (2^bits - 1)^2 < P / 2 with P = prod p_l, the Chinese remainder theorem gives
+// |A^ B^| <= k (2^bits - 1)^2 < P / 4 with P = prod p_l, the Chinese remainder theorem gives
 // it exactly:  A^B^ = sum_l c_l w_l mod P, centred, with w_l = (P / p_l) ((P / p_l)^-1 mod p_l).
 // Then C := alpha 2^(e_i + f_j - 2 bits) A^B^ + beta C, rounded once to FP64 (plus the
 // scaling).  The error is the truncation of A and B to `bits` bits -- that of the slice
@@ -21,7 +21,8 @@ using u128 = unsigned __int128;
 // The moduli: walking down from 255, every number coprime to all those already taken
 // (255 = 3 5 17, 254 = 2 127, 253 = 11 23, 247 = 13 19, 217 = 7 31, the rest prime); their
 // centred residues, |r| <= 127, are exact fp16 digits.
-constexpr uint32_t kModuli[kCrtMaxModuli] = {255, 254, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199};
+constexpr uint32_t kModuli[kCrtMaxModuli] = {255, 254, 253, 251, 247, 241, 239, 233,
+                                             229, 227, 223, 217, 211, 199, 197, 193};
 
 uint32_t inverse_mod(uint32_t a, uint32_t p) {  // a^-1 mod p (gcd(a, p) = 1)
     long long t = 0, nt = 1, r = p, nr = a % p;
@@ -51,49 +52,27 @@ MOMMS_DEV double u128_to_double(u128 v) {
     return static_cast<double>(top) * pow2_normal(64 - lz);
 }
 
-// |Z| for one element from its limb sums s_q = sum_l c_l w_l[q] (the CRT sum in L 32-bit
-// limbs), reduced mod P and centred; integer arithmetic only (FP64 ALU work is scarce on this
-// part).  Returns the magnitude, *neg its sign.
-template <int L>
-MOMMS_DEV u128 crt_magnitude(const unsigned long long (&s)[4], const u128 P, const u128 half, float Pinv,
-                             bool* neg) {
-    // carries between the limbs: acc = sum_q s_q 2^(32 q) < N 256 P < 2^128
-    const unsigned long long t1 = s[1] + (s[0] >> 32);
-    const unsigned long long t2 = s[2] + (t1 >> 32);
-    const unsigned long long lo = (s[0] & 0xFFFFFFFFull) | (t1 << 32);
-    unsigned long long hi;
-    if constexpr (L == 4) hi = (t2 & 0xFFFFFFFFull) | ((s[3] + (t2 >> 32)) << 32);
-    else hi = t2;
-    u128 acc = (static_cast<u128>(hi) << 64) | lo;
-    // acc mod P: an fp32 quotient estimate (relative error ~2^-21 on a quotient below 2^12, so
-    // off by at most one) and one exact correction either way.  The estimate converts the
-    // leading 32 bits of acc (64-bit conversions would run on the scarce FP64 pipe) and puts
-    // their weight 2^(96 - lz) into the exponent field.
-    uint32_t q = 0;
-    if (hi | lo) {
-        const int lz = hi ? __clzll(static_cast<long long>(hi)) : 64 + __clzll(static_cast<long long>(lo));
-        const uint32_t top = static_cast<uint32_t>((acc << lz) >> 96);
-        const float scale = __int_as_float((127 + 96 - lz) << 23);
-        q = static_cast<uint32_t>(__uint2float_rz(top) * scale * Pinv);
+// mag 2^(E) with the sign, mag = hi 2^64 + lo, rounded once to FP64 (to nearest, ties to even):
+// the 53-bit significand is rounded in integers and the scale goes into the exponent field;
+// an exponent outside the normal range takes the FP64 route.
+MOMMS_DEV double scaled_double(unsigned long long hi, unsigned long long lo, bool neg, int E) {
+    if ((hi | lo) == 0) return 0.0;
+    // the leading 64 bits of mag in `top`, the bits below folded into its bit 0 (a sticky bit,
+    // under the rounding position of a 53-bit significand)
+    int lz;
+    unsigned long long top;
+    if (hi) {
+        lz = __clzll(static_cast<long long>(hi));
+        if (lz == 0) {
+            top = hi | static_cast<unsigned long long>(lo != 0);
+        } else {
+            top = (hi << lz) | (lo >> (64 - lz));
+            top |= static_cast<unsigned long long>((lo << lz) != 0);
+        }
+    } else {
+        lz = 64 + __clzll(static_cast<long long>(lo));
+        top = lo << (lz - 64);
     }
-    const u128 qP = static_cast<u128>(q) * P;
-    acc = qP > acc ? acc + P - qP : acc - qP;
-    if (acc >= P) acc -= P;
-    *neg = acc > half;
-    return *neg ? P - acc : acc;
-}
-
-// mag 2^E with the sign, rounded once to FP64 (to nearest, ties to even): the 53-bit
-// significand is rounded in integers and the scale goes into the exponent field; an exponent
-// outside the normal range takes the FP64 route.
-MOMMS_DEV double scaled_double(u128 mag, bool neg, int E) {
-    if (mag == 0) return 0.0;
-    const unsigned long long mh = static_cast<unsigned long long>(mag >> 64);
-    const unsigned long long ml = static_cast<unsigned long long>(mag);
-    const int lz = mh ? __clzll(static_cast<long long>(mh)) : 64 + __clzll(static_cast<long long>(ml));
-    const u128 t = mag << lz;  // leading one at bit 127
-    const unsigned long long top = static_cast<unsigned long long>(t >> 64) |
-                                   static_cast<unsigned long long>(static_cast<unsigned long long>(t) != 0);
     unsigned long long mant = top >> 11;
     const unsigned long long rem = top & 0x7FFull;
     mant += (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
@@ -106,14 +85,22 @@ MOMMS_DEV double scaled_double(u128 mag, bool neg, int E) {
         return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(neg) << 63) |
                                                            (static_cast<unsigned long long>(ex + 1023) << 52) |
                                                            (mant & ((1ull << 52) - 1))));
-    const double y = scale_pow2(u128_to_double(mag), E);
+    const double y = scale_pow2(u128_to_double((static_cast<u128>(hi) << 64) | lo), E);
     return neg ? -y : y;
 }
 
-// C from the residue bytes res[l][j][i] (m n per modulus).  Blocks stride over the columns,
-// threads over the rows of a column; with V = 4 (m a multiple of 4) a thread takes four
-// consecutive rows and loads one 32-bit word per modulus, and with CV (16-byte aligned pairs
-// of C) reads and writes C as two double2.  L: 32-bit limbs of the CRT weights (3 when P < 2^96).
+// C from the residue bytes res[l][j][i] (m n per modulus).  Per element, with S = sum_l c_l w_l
+// (so S = Z mod P, and S / P = q + Z / P with |Z / P| <= 1/4 by the choice of moduli):
+//   q  = round(sum_l c_l F_l / 2^19), F_l = round(2^19 w_l / P): one 32-bit multiply-add per
+//        modulus (sum < 16 * 255 * 2^19 < 2^32), error below 16 * 255 * 2^-20 = 2^-8, far inside
+//        the 1/4 margin,
+//   Z  = S - q P computed modulo 2^(32 L) (|Z| < P / 2 <= 2^(32 L - 1): the wrap-around is exact),
+// so no 128-bit division, comparison or reduction is needed: L limb sums of wide multiply-adds,
+// one borrow chain, then the rounding of |Z| into the double's fields.  Blocks stride over the
+// columns, threads over the rows of a column; with V = 4 (m a multiple of 4) a thread takes four
+// consecutive rows and loads one 32-bit word per modulus, and with CV (16-byte aligned pairs of
+// C) reads and writes C as two double2.  L = 3 when P < 2^96, else 4.  The modulus loop keeps
+// few registers live, so that many warps hide the load latency.
 template <int V, bool CV, int L>
 __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
                                                   const __grid_constant__ CrtRecon r,
@@ -122,8 +109,6 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
                                                   double alpha, double beta, double* __restrict__ C, int64_t ldc) {
     const int64_t mn = m * n;
     const int64_t groups = m / V;
-    const u128 P = (static_cast<u128>(r.P_hi) << 64) | r.P_lo;
-    const u128 half = P >> 1;
     const bool unit_alpha = alpha == 1.0, beta_zero = beta == 0.0;
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
@@ -132,43 +117,91 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
         for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < groups;
              g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
             const int64_t i0 = g * V;
-            unsigned long long s[V][4];
+            unsigned long long s[V][L];
+            uint32_t qs[V];
 #pragma unroll
-            for (int t = 0; t < V; ++t)
+            for (int t = 0; t < V; ++t) {
+                qs[t] = 0u;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) s[t][q] = 0;
+                for (int q = 0; q < L; ++q) s[t][q] = 0;
+            }
             const uint8_t* src = res + j * m + i0;
             for (int l = 0; l < r.N; ++l) {
                 uint32_t word;
                 if constexpr (V == 4) word = __ldcs(reinterpret_cast<const unsigned int*>(src + l * mn));
                 else word = src[l * mn];
+                const uint32_t fl = r.frac[l];
 #pragma unroll
                 for (int t = 0; t < V; ++t) {
                     const uint32_t c = (word >> (8 * t)) & 0xFFu;
 #pragma unroll
                     for (int q = 0; q < L; ++q) s[t][q] += static_cast<unsigned long long>(c) * r.w[l][q];
+                    qs[t] += c * fl;
                 }
             }
             double y[V];
 #pragma unroll
             for (int t = 0; t < V; ++t) {
-                bool neg;
-                const u128 mag = crt_magnitude<L>(s[t], P, half, r.Pinv, &neg);
+                // S mod 2^(32 L) in 32-bit words z[0..L-1]
+                uint32_t z[L];
+                unsigned long long carry = 0;
+#pragma unroll
+                for (int q = 0; q < L; ++q) {
+                    const unsigned long long v = s[t][q] + carry;
+                    z[q] = static_cast<uint32_t>(v);
+                    carry = v >> 32;
+                }
+                // Z = S - q P modulo 2^(32 L)
+                const uint32_t qv = (qs[t] + (1u << 18)) >> 19;
+                unsigned long long mc = 0;
+                uint32_t borrow = 0;
+#pragma unroll
+                for (int q = 0; q < L; ++q) {
+                    const unsigned long long pq = static_cast<unsigned long long>(qv) * r.Pw[q] + mc;
+                    mc = pq >> 32;
+                    const uint32_t sub = static_cast<uint32_t>(pq);
+                    const unsigned long long d = static_cast<unsigned long long>(z[q]) - sub - borrow;
+                    z[q] = static_cast<uint32_t>(d);
+                    borrow = static_cast<uint32_t>(d >> 63);
+                }
+                const bool neg = (z[L - 1] >> 31) != 0;
+                if (neg) {  // two's complement magnitude
+                    uint32_t c1 = 1;
+#pragma unroll
+                    for (int q = 0; q < L; ++q) {
+                        const unsigned long long v = static_cast<unsigned long long>(~z[q]) + c1;
+                        z[q] = static_cast<uint32_t>(v);
+                        c1 = static_cast<uint32_t>(v >> 32);
+                    }
+                }
+                // |Z| = hi 2^64 + lo, scaled by 2^(32 (4 - L)) when L = 3
+                unsigned long long hi, lo;
+                int Eadj;
+                if constexpr (L == 4) {
+                    hi = (static_cast<unsigned long long>(z[3]) << 32) | z[2];
+                    lo = (static_cast<unsigned long long>(z[1]) << 32) | z[0];
+                    Eadj = 0;
+                } else {
+                    hi = (static_cast<unsigned long long>(z[2]) << 32) | z[1];
+                    lo = static_cast<unsigned long long>(z[0]) << 32;
+                    Eadj = -32;
+                }
                 const int64_t i = i0 + t;
-                y[t] = (fj || ef[i] != 0) ? qnan : scaled_double(mag, neg, e[i] + Ej);
+                y[t] = (fj || ef[i] != 0) ? qnan : scaled_double(hi, lo, neg, e[i] + Ej + Eadj);
                 if (!unit_alpha) y[t] *= alpha;
             }
             double* cp = C + i0 + j * ldc;
             if constexpr (CV) {
                 double2* c2 = reinterpret_cast<double2*>(cp);
-                double2 a = beta_zero ? make_double2(0.0, 0.0) : __ldcs(c2);
-                double2 b = beta_zero ? make_double2(0.0, 0.0) : __ldcs(c2 + 1);
-                if (!beta_zero) {
-                    a.x = fma(beta, a.x, y[0]); a.y = fma(beta, a.y, y[1]);
-                    b.x = fma(beta, b.x, y[2]); b.y = fma(beta, b.y, y[3]);
-                } else {
+                double2 a, b;
+                if (beta_zero) {
                     a = make_double2(y[0], y[1]);
                     b = make_double2(y[2], y[3]);
+                } else {
+                    a = __ldcs(c2);
+                    b = __ldcs(c2 + 1);
+                    a.x = fma(beta, a.x, y[0]); a.y = fma(beta, a.y, y[1]);
+                    b.x = fma(beta, b.x, y[2]); b.y = fma(beta, b.y, y[3]);
                 }
                 __stcs(c2, a);
                 __stcs(c2 + 1, b);
@@ -191,19 +224,21 @@ bool crt_plan(int bits, int64_t k, CrtConsts* c, CrtRecon* r) {
     if (bits < 1 || bits > 56 || k < 1 || k > crt_max_k()) return false;
     int lk = 0;
     while ((int64_t(1) << lk) < k) ++lk;
-    if (2 * bits + lk + 1 > 118) return false;
+    if (2 * bits + lk + 2 > 126) return false;
+    // P > 4 k (2^bits - 1)^2: twice the range the centred residue needs, so that |Z / P| <= 1/4
+    // and the reconstruction's fixed-point quotient estimate has a margin of 1/4
     const u128 v = (static_cast<u128>(1) << bits) - 1;
-    const u128 need = static_cast<u128>(2) * static_cast<u128>(k) * v * v;  // P must exceed 2 k (2^bits - 1)^2
+    const u128 need = static_cast<u128>(4) * static_cast<u128>(k) * v * v;
     u128 P = 1;
     int N = 0;
     while (N < kCrtMaxModuli && P <= need) P *= kModuli[N++];
     if (P <= need) return false;
-    // the reconstruction sums N terms below 255 P each in 128 bits
-    if (P > (~static_cast<u128>(0)) / (static_cast<u128>(N) * 256)) return false;
     *c = CrtConsts{};
     *r = CrtRecon{};
     c->N = r->N = N;
     c->bits = r->bits = bits;
+    const long double Pl = static_cast<long double>(static_cast<unsigned long long>(P >> 64)) * 18446744073709551616.0L +
+                           static_cast<long double>(static_cast<unsigned long long>(P));
     for (int l = 0; l < N; ++l) {
         const uint32_t p = kModuli[l];
         c->p[l] = p;
@@ -214,11 +249,12 @@ bool crt_plan(int bits, int64_t k, CrtConsts* c, CrtRecon* r) {
         const uint32_t inv = inverse_mod(static_cast<uint32_t>(Ml % p), p);
         const u128 w = Ml * inv;  // < P
         for (int q = 0; q < 4; ++q) r->w[l][q] = static_cast<uint32_t>(w >> (32 * q));
+        const long double wl = static_cast<long double>(static_cast<unsigned long long>(w >> 64)) *
+                                   18446744073709551616.0L +
+                               static_cast<long double>(static_cast<unsigned long long>(w));
+        r->frac[l] = static_cast<uint32_t>(wl / Pl * 524288.0L + 0.5L);  // round(2^19 w_l / P)
     }
-    r->P_lo = static_cast<unsigned long long>(P);
-    r->P_hi = static_cast<unsigned long long>(P >> 64);
-    r->Pinv = static_cast<float>(1.0 / (static_cast<double>(r->P_hi) * 18446744073709551616.0 +
-                                        static_cast<double>(r->P_lo)));
+    for (int q = 0; q < 4; ++q) r->Pw[q] = static_cast<uint32_t>(P >> (32 * q));
     return true;
 }
 
@@ -228,7 +264,7 @@ cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, con
     if (m <= 0 || n <= 0) return cudaSuccess;
     const bool vec = m % 4 == 0 && reinterpret_cast<uintptr_t>(res) % 4 == 0;
     const bool cvec = vec && ldc % 2 == 0 && reinterpret_cast<uintptr_t>(C) % 16 == 0;
-    const bool three = r.P_hi < (1ull << 32);  // P < 2^96: the weights fit three limbs
+    const bool three = r.Pw[3] == 0;  // P < 2^96: |Z| < 2^95, arithmetic modulo 2^96
     const int64_t groups = vec ? m / 4 : m;
     int64_t bx = (groups + 255) / 256;
     if (bx > 64) bx = 64;

@@ -330,7 +330,7 @@ __device__ __forceinline__ void write_residues(const double (&x)[NE], bool valid
     for (int l = 0; l < c.N; ++l) {
         const uint32_t pl = c.p[l], mg = c.magic[l], k16 = c.c16[l], k32 = c.c32[l];
         const int hi = static_cast<int>((pl - 1) / 2), lo = -static_cast<int>(pl / 2);
-        uint32_t u[NE], sgn[NE];
+        uint32_t h[NE];
 #pragma unroll
         for (int i = 0; i < NE; ++i) {
             const uint32_t t = a2[i] * k32 + a1[i] * k16 + a0[i];  // < 2^32 for bits <= 56
@@ -340,12 +340,17 @@ __device__ __forceinline__ void write_residues(const double (&x)[NE], bool valid
             int v = neg[i] ? -r : r;
             if (v > hi) v -= static_cast<int>(pl);
             else if (v < lo) v += static_cast<int>(pl);
-            u[i] = static_cast<uint32_t>(v < 0 ? -v : v);
-            sgn[i] = v < 0 ? 0x8000u : 0u;
+            // fp16 bits of 1536 + v: in [1024, 2048) the fp16 integers are consecutive codes
+            h[i] = static_cast<uint32_t>(0x6600 + v);
         }
         uint32_t w[NE / 2];
+        const __half2 bias = __half2half2(__ushort_as_half(0x6600));  // 1536
 #pragma unroll
-        for (int i = 0; i < NE; i += 2) w[i / 2] = digits_to_half2(u[i], u[i + 1], sgn[i], sgn[i + 1]);
+        for (int i = 0; i < NE; i += 2) {
+            const uint32_t b = h[i] | (h[i + 1] << 16);
+            const __half2 v2 = __hsub2(*reinterpret_cast<const __half2*>(&b), bias);  // exact: v
+            w[i / 2] = *reinterpret_cast<const uint32_t*>(&v2);
+        }
         if constexpr (NE == 8)
             *reinterpret_cast<uint4*>(planes + l * plane + off) = make_uint4(w[0], w[1], w[2], w[3]);
         else

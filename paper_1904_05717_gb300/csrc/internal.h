@@ -58,7 +58,7 @@ cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, con
 // pairwise coprime moduli p_l <= 255 -- one fp16 tensor product of residues |r| <= 127 per
 // modulus -- and rebuilt by the Chinese remainder theorem; C := alpha 2^(e + f - 2 bits) A^B^
 // + beta C.  N products instead of the S(S+1)/2 of the slice encoding.
-constexpr int kCrtMaxModuli = 14;
+constexpr int kCrtMaxModuli = 16;
 struct CrtConsts {                 // residue split and slice-product epilogue
     int N;                         // moduli in use
     int bits;                      // integer width of the operands (7 x slices)
@@ -70,11 +70,11 @@ struct CrtConsts {                 // residue split and slice-product epilogue
 struct CrtRecon {                  // reconstruction
     int N, bits;
     uint32_t w[kCrtMaxModuli][4];  // CRT weights w_l < P in 32-bit limbs, least significant first
-    unsigned long long P_lo, P_hi; // P = prod p_l
-    float Pinv;                    // 1 / P in fp32 (quotient estimates)
+    uint32_t frac[kCrtMaxModuli];  // w_l / P as 19-bit fixed point (quotient estimates)
+    uint32_t Pw[4];                // P = prod p_l in 32-bit limbs
 };
-// The moduli for `bits`-bit operands and contraction length k (|A^ B^| < P/2); false when more
-// than kCrtMaxModuli would be needed.
+// The moduli for `bits`-bit operands and contraction length k (P > 4 k (2^bits - 1)^2, so
+// |A^ B^| <= P/4); false when more than kCrtMaxModuli would be needed.
 bool crt_plan(int bits, int64_t k, CrtConsts* c, CrtRecon* r);
 // Largest k one modular product keeps exact in int32 (k * 127^2 < 2^31), a multiple of 64.
 int64_t crt_max_k();

@@ -210,7 +210,7 @@ def momms_crt_moduli(bits, k):
     """The moduli the modular encoding uses for `bits`-bit operands and contraction length k
     (a list), or raises MommsError when they do not exist."""
     count = ctypes.c_int(0)
-    buf = (ctypes.c_uint32 * 14)()
+    buf = (ctypes.c_uint32 * 16)()
     check(lib().momms_crt_moduli(bits, k, ctypes.byref(count), buf), "momms_crt_moduli")
     return [int(buf[i]) for i in range(count.value)]
 

@@ -104,28 +104,29 @@ def test_default_group_minimises_wave_rows():
 
 def test_crt_moduli_are_the_fewest_greedy_moduli(L):
     # host-only planning call: the library's moduli are the oracle's greedy coprime moduli,
-    # as few as the range argument allows
+    # as few as the range argument with a factor-2 margin allows (|product| <= P / 4)
     import oracle
-    ref = oracle.greedy_moduli(14)
-    for bits, k in [(7, 1), (21, 64), (35, 1024), (39, 8192), (42, 8192), (42, 65536), (49, 2048), (56, 1 << 0)]:
-        need = [n for n in range(1, 15) if oracle.moduli_suffice(ref[:n], bits, k)]
+    ref = oracle.greedy_moduli(16)
+    for bits, k in [(7, 1), (21, 64), (35, 1024), (39, 8192), (42, 8192), (42, 65536), (49, 2048), (49, 133120),
+                    (56, 1), (56, 4096)]:
+        need = [n for n in range(1, 17) if oracle.moduli_suffice(ref[:n], bits, k, margin=2)]
         if not need:
             with pytest.raises(M.MommsError):
                 M.momms_crt_moduli(bits, k)
             continue
         assert M.momms_crt_moduli(bits, k) == ref[:need[0]], (bits, k)
     with pytest.raises(M.MommsError):
-        M.momms_crt_moduli(49, 8192)       # would take 15 moduli
+        M.momms_crt_moduli(56, 8192)       # would take 17 moduli
     with pytest.raises(M.MommsError):
         M.momms_crt_moduli(7, 200000)      # the int32 residue sums would overflow
-    buf = (ctypes.c_uint32 * 14)()
+    buf = (ctypes.c_uint32 * 16)()
     cnt = ctypes.c_int(0)
     assert L.momms_crt_moduli(0, 4, ctypes.byref(cnt), buf) == -1
     assert L.momms_crt_moduli(10, 0, ctypes.byref(cnt), buf) == -2
     # the residue split validates before any launch
     assert M.momms_emu_residues(0, 0, 4, 4, 1 << 40, 4, 1 << 41, 1 << 42, 0, 4, 1 << 43, 128, 64, 0) == -9
     assert M.momms_emu_residues(0, 0, 4, 4, 1 << 40, 4, 1 << 41, 1 << 42, 21, 4, 1 << 43, 3, 64, 0) == -12
-    assert M.momms_emu_residues(0, 0, 4, 4, 1 << 40, 4, 1 << 41, 1 << 42, 49, 8192, 1 << 43, 128, 64, 0) == \
+    assert M.momms_emu_residues(0, 0, 4, 4, 1 << 40, 4, 1 << 41, 1 << 42, 56, 8192, 1 << 43, 128, 64, 0) == \
         M.MOMMS_ERR_UNSUPPORTED
     assert L.momms_set_scheme(None, 1) == M.MOMMS_ERR_HANDLE
     # the residue product and the reconstruction validate before any launch
@@ -139,5 +140,5 @@ def test_crt_moduli_are_the_fewest_greedy_moduli(L):
                                    1 << 45, 4, stream=0) == -4
     assert M.momms_crt_reconstruct(4, 4, 4, 21, 1 << 40, 1 << 41, 1 << 42, 1 << 43, 1 << 44, 1.0, 0.0,
                                    1 << 45, 3, stream=0) == -13
-    assert M.momms_crt_reconstruct(4, 4, 8192, 49, 1 << 40, 1 << 41, 1 << 42, 1 << 43, 1 << 44, 1.0, 0.0,
+    assert M.momms_crt_reconstruct(4, 4, 8192, 56, 1 << 40, 1 << 41, 1 << 42, 1 << 43, 1 << 44, 1.0, 0.0,
                                    1 << 45, 4, stream=0) == M.MOMMS_ERR_UNSUPPORTED

@@ -23,7 +23,7 @@ def stored(which, op, rows, inner, seed, kind="phi", phi=1.0):
 
 
 @pytest.mark.parametrize("which,op", [(0, 0), (0, 1), (1, 0), (1, 1)])
-@pytest.mark.parametrize("bits,k", [(21, 64), (39, 8192), (42, 1000)])
+@pytest.mark.parametrize("bits,k", [(21, 64), (39, 8192), (42, 1000), (49, 1000)])
 def test_residue_split_bitwise(which, op, bits, k):
     import torch
     rows, inner = 150, 200
@@ -35,7 +35,7 @@ def test_residue_split_bitwise(which, op, bits, k):
         X[(7, 0) if op else (0, 7)] = np.inf
     rows_pad, inner_pad = 160, 256
     mods = M.momms_crt_moduli(bits, k)
-    assert mods == oracle.greedy_moduli(14)[:len(mods)] and oracle.moduli_suffice(mods, bits, k)
+    assert mods == oracle.greedy_moduli(16)[:len(mods)] and oracle.moduli_suffice(mods, bits, k, margin=2)
     dX = M.DeviceMatrix.from_numpy(X)
     e = torch.empty(rows, dtype=torch.int32, device="cuda")
     fl = torch.empty(rows, dtype=torch.uint8, device="cuda")
@@ -143,20 +143,21 @@ def test_scheme_choice_and_fallbacks():
     B = syn.matrix("uniform", k, n, 362)
     C0 = syn.matrix("uniform", m, n, 363)
     Cref, N = reference(A, B, C0, 1.0, 1.0)
-    # AUTO: 4 slices take 10 pairs, their moduli 9 -- not two fewer: slices
-    C, rep = modular(A, B, C0, 1.0, 1.0, 4, scheme=M.SCHEME_AUTO)
+    # AUTO: 3 slices take 6 pairs, 21-bit operands 7 moduli -- not two fewer: slices
+    assert len(M.momms_crt_moduli(21, k)) == 7
+    C, rep = modular(A, B, C0, 1.0, 1.0, 3, scheme=M.SCHEME_AUTO)
     assert rep["moduli"] == 0
-    # AUTO with 6 slices: 12 moduli (42-bit operands, k = 512) against 21 pairs
+    # AUTO with 6 slices: 13 moduli (42-bit operands, k = 512) against 21 pairs
     C, rep = modular(A, B, C0, 1.0, 1.0, 6, scheme=M.SCHEME_AUTO)
-    assert rep["moduli"] == len(M.momms_crt_moduli(42, k)) == 12
+    assert rep["moduli"] == len(M.momms_crt_moduli(42, k)) == 13
     assert max_ratio(C, Cref, k, 1.0, 1.0, N, C0) <= 1.0
-    # MODULI requested where 15 moduli would be needed (49-bit operands, k = 8192): slices
+    # MODULI requested where 17 moduli would be needed (56-bit operands, k = 8192): slices
     k2 = 8192
     A2 = syn.matrix("uniform", 128, k2, 364)
     B2 = syn.matrix("uniform", k2, 192, 365)
     C2 = syn.matrix("uniform", 128, 192, 366)
-    C, rep = modular(A2, B2, C2, 1.0, 1.0, 7)
-    assert rep["moduli"] == 0 and rep["slices"] == 7
+    C, rep = modular(A2, B2, C2, 1.0, 1.0, 8)
+    assert rep["moduli"] == 0 and rep["slices"] == 8
     Cref2, N2 = reference(A2, B2, C2, 1.0, 1.0)
     assert max_ratio(C, Cref2, k2, 1.0, 1.0, N2, C2) <= 1.0
     # SLICES requested: never moduli
@@ -231,3 +232,64 @@ def test_residue_products_and_reconstruction_pieces_bitwise():
     M.check(M.momms_crt_reconstruct(m, n, k, bits, res.data_ptr(), e.data_ptr(), ef.data_ptr(), f.data_ptr(),
                                     ff.data_ptr(), 0.5, -2.0, dC.ptr, dC.ld), "crt")
     assert np.array_equal(dC.to_numpy(), Co)
+
+
+def test_sixteen_moduli_product_bitwise():
+    # 50-bit operands, k = 65536: all 16 moduli (P ~ 2^125, arithmetic modulo 2^128)
+    m, n, k = 20, 12, 65536
+    assert len(M.momms_crt_moduli(50, k)) == 16
+    A = syn.matrix("phi", m, k, 391, phi=1.0)
+    B = syn.matrix("phi", k, n, 392, phi=1.0)
+    C0 = syn.matrix("uniform", m, n, 393)
+    dA, dB, dC = M.DeviceMatrix.from_numpy(A), M.DeviceMatrix.from_numpy(B), M.DeviceMatrix.from_numpy(C0)
+    # 50 bits is not a whole number of digits: drive the pieces through the ABI
+    import torch
+    e = torch.empty(m, dtype=torch.int32, device="cuda"); ef = torch.empty(m, dtype=torch.uint8, device="cuda")
+    f = torch.empty(n, dtype=torch.int32, device="cuda"); ff = torch.empty(n, dtype=torch.uint8, device="cuda")
+    M.check(M.momms_emu_scale(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr()), "scale")
+    M.check(M.momms_emu_scale(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr()), "scale")
+    Ar = torch.empty((16, m, k), dtype=torch.float16, device="cuda")
+    Br = torch.empty((16, n, k), dtype=torch.float16, device="cuda")
+    M.check(M.momms_emu_residues(0, 0, m, k, dA.ptr, dA.ld, e.data_ptr(), ef.data_ptr(), 50, k, Ar.data_ptr(), m, k),
+            "residues")
+    M.check(M.momms_emu_residues(1, 0, n, k, dB.ptr, dB.ld, f.data_ptr(), ff.data_ptr(), 50, k, Br.data_ptr(), n, k),
+            "residues")
+    res = torch.empty((16, n, m), dtype=torch.uint8, device="cuda")
+    nbytes = M.momms_emu_scratch_bytes()
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    M.check(M.momms_emu_residue_gemm(m, n, k, 50, Ar.data_ptr(), Br.data_ptr(), m, n, k, 0, res.data_ptr(),
+                                     scratch.data_ptr(), nbytes, st.data_ptr()), "residue gemm")
+    M.check(M.momms_crt_reconstruct(m, n, k, 50, res.data_ptr(), e.data_ptr(), ef.data_ptr(), f.data_ptr(),
+                                    ff.data_ptr(), 1.0, 1.0, dC.ptr, dC.ld), "crt")
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    Co, _ = oracle.modular_dgemm(A, B, 50, C0.copy(order="F"), 1.0, 1.0)
+    assert np.array_equal(dC.to_numpy(), Co)
+
+
+def test_residue_products_exact_at_the_chunk_edge():
+    # residue planes at the largest magnitude (127): every 1024-product FP32 chunk reaches
+    # 1024 * 127^2 = 16,516,096 < 2^24 and the int32 sums k * 127^2 (k = 65536: 1.06e9) stay exact
+    import torch
+    m, n, k, bits = 130, 200, 65536, 30
+    mods = M.momms_crt_moduli(bits, k)
+    N = len(mods)
+    sa = np.where((np.arange(m)[:, None] + np.arange(k)[None, :]) % 5 == 0, -1.0, 1.0)
+    sa[:64] = 1.0                                  # rows whose every product is +127^2
+    sb = np.where((np.arange(n)[:, None] * 3 + np.arange(k)[None, :]) % 7 == 0, -1.0, 1.0)
+    sb[:96] = 1.0
+    Ar = torch.from_numpy(np.ascontiguousarray(np.broadcast_to((127.0 * sa).astype(np.float16), (N, m, k)))).cuda()
+    Br = torch.from_numpy(np.ascontiguousarray(np.broadcast_to((127.0 * sb).astype(np.float16), (N, n, k)))).cuda()
+    res = torch.full((N, n, m), 255, dtype=torch.uint8, device="cuda")
+    nbytes = M.momms_emu_scratch_bytes()
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    M.check(M.momms_emu_residue_gemm(m, n, k, bits, Ar.data_ptr(), Br.data_ptr(), m, n, k, 0, res.data_ptr(),
+                                     scratch.data_ptr(), nbytes, st.data_ptr()), "residue gemm")
+    # integer sums below 2^53: the FP64 product of the sign patterns is exact
+    Z = np.rint((127.0 * sa) @ (127.0 * sb).T).astype(np.int64)
+    assert Z.max() == k * 127 * 127
+    want = np.stack([np.mod(Z.T, p) for p in mods])                      # [l][j][i]
+    assert int(st.item()) == 0
+    assert np.array_equal(res.cpu().numpy().astype(np.int64), want)
