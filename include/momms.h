@@ -334,6 +334,24 @@ int momms_trmm(momms_handle_t handle, int side, int uplo, int trans, int diag, i
                double alpha, const double* A, int64_t lda, double* B, int64_t ldb,
                momms_stream_t stream);
 
+/* ------------------------------------------------------- triangular solve */
+/* B := alpha*op(A)^-1*B (side LEFT: solves op(A) X = alpha B, A m x m) or
+ * B := alpha*B*op(A)^-1 (side RIGHT: X op(A) = alpha B, A n x n), A triangular (uplo;
+ * diag UNIT: ones on the diagonal, which is not read), B m x n overwritten by X (BLAS
+ * dtrsm).  Recursive blocked solve: op(A) is halved (at multiples of 128) until blocks of
+ * order <= 128 remain; the off-diagonal half becomes one GEMM update of the right-hand sides
+ * (this library's product, in the handle's mode -- the updates carry ~all m^2 n (n^2 m)
+ * flops), and each 128 x 128 diagonal block is applied as a GEMM with its explicit inverse,
+ * computed in FP64 by a substitution kernel (one CTA per block).  The error is that of the
+ * GEMMs plus the inverses' (well-conditioned diagonal blocks: a small multiple of
+ * 2^-53 (|op(A)| |X|) componentwise).  Device pointers, asynchronous on `stream` (the
+ * data-driven slice count of the emulated GEMMs reads back a spread per GEMM).  Errors:
+ * BLAS-style negative index (side -2, uplo -3, trans -4, diag -5, m -6, n -7, A -9,
+ * lda -10, B -11, ldb -12), MOMMS_ERR_*. */
+int momms_trsm(momms_handle_t handle, int side, int uplo, int trans, int diag, int64_t m, int64_t n,
+               double alpha, const double* A, int64_t lda, double* B, int64_t ldb,
+               momms_stream_t stream);
+
 /* ------------------------------------------------------- out-of-core product */
 /* C := alpha*A*B + beta*C with A, B and C in HOST memory (column-major, leading
  * dimensions as for momms_gemm; no transposes), for problems larger than the device

@@ -28,6 +28,8 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   crt_reconstruct
   modular_dgemm      pinned: integer inputs exact, the one-slice emulation bit for
                      bit, the FP64 componentwise bound at 56 bits, fma semantics
+  trsm               pinned: exact integer recovery, scipy.linalg.solve_triangular,
+                     the identity
 The modular encoding is not in the paper: it is the alternative integer encoding of
 the emulated product (Ozaki, Uchino & Imamura, "Ozaki Scheme II", 2025); its oracle is
 the definition of what it computes (the exact product of the truncated operands).
@@ -389,3 +391,37 @@ def modular_dgemm(A, B, bits, C=None, alpha=1.0, beta=0.0, transa=False, transb=
             ay = float(alpha) * y
             out[i, j] = ay if (C is None or beta == 0.0) else _fma(float(beta), float(C[i, j]), ay)
     return out, {"e": e, "eflag": ef, "f": f, "fflag": ff, "Ahat": Ah, "Bhat": Bh, "Z": Z}
+
+
+# ---------------------------------------------------------------------------------------------
+# Triangular solve (BLAS dtrsm semantics).  Plain substitution, row by row, in FP64.
+#   trsm   pinned: exact integer recovery (unit triangle, integer solution), agreement with
+#          scipy.linalg.solve_triangular, identity
+# ---------------------------------------------------------------------------------------------
+
+def trsm(A, B, alpha=1.0, side="L", lower=True, trans=False, unit=False):
+    """X with op(A) X = alpha B (side 'L') or X op(A) = alpha B (side 'R'), A triangular (only
+    the `lower` / upper triangle read; `unit`: ones on the diagonal, not read), by forward or
+    back substitution: x_i = (r_i - sum_{k before i} M_ik x_k) / M_ii along the rows of
+    M = op(A) (side 'R' solves M^T X^T = alpha B^T the same way)."""
+    A = np.asarray(A, dtype=np.float64)
+    T = np.tril(A) if lower else np.triu(A)
+    if unit:
+        T = T.copy()
+        np.fill_diagonal(T, 1.0)
+    M = T.T if trans else T
+    R = float(alpha) * np.asarray(B, dtype=np.float64)
+    if side == "R":
+        M = M.T
+        R = R.T
+    is_lower = np.array_equal(M, np.tril(M))
+    t = M.shape[0]
+    X = np.zeros_like(R)
+    order = range(t) if is_lower else range(t - 1, -1, -1)
+    for i in order:
+        if is_lower:
+            acc = R[i] - M[i, :i] @ X[:i]
+        else:
+            acc = R[i] - M[i, i + 1:] @ X[i + 1:]
+        X[i] = acc / M[i, i]
+    return np.asfortranarray(X.T if side == "R" else X)

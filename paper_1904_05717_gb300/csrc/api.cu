@@ -1566,6 +1566,140 @@ int momms_trmm(momms_handle_t h, int side, int uplo, int trans, int diag, int64_
     return MOMMS_OK;
 }
 
+// ------------------------------------------------------------------ triangular solve
+namespace {
+
+struct TrsmCtx {
+    momms_handle_t h;
+    int side, uplo, trans;
+    bool eff_lower;        // op(A) is lower triangular
+    int64_t m, n;
+    const double* A;
+    int64_t lda;
+    double* B;
+    int64_t ldb;
+    const double* W;       // inverses of the diagonal blocks (kTrsmNb^2 each)
+    double* T;             // leaf product before it is copied into B
+    cudaStream_t s;
+    int64_t launches;
+};
+
+int trsm_gemm(TrsmCtx& c, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+              int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
+    const int rc = gemm_dispatch(c.h, opa, opb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, c.s);
+    c.launches += c.h->report.launches;
+    return rc;
+}
+
+// Element (r, q) block of op(A): pointer into A and the op that yields it.
+const double* op_block(const TrsmCtx& c, int64_t r, int64_t q, int* op) {
+    *op = c.trans;
+    return c.trans == MOMMS_OP_N ? c.A + r + q * c.lda : c.A + q + r * c.lda;
+}
+
+// Rows [r0, r1) of op(A) X = alpha B (side LEFT) or columns [r0, r1) of X op(A) = alpha B
+// (side RIGHT), the blocks of op(A) before (LEFT, lower) or after them already solved.
+int trsm_rec(TrsmCtx& c, int64_t r0, int64_t r1, double alpha) {
+    const int64_t size = r1 - r0;
+    const bool left = c.side == MOMMS_LEFT;
+    if (size <= momms::kTrsmNb) {
+        // leaf: X = alpha op(inv(A_bb)) B_b through the scratch T, then copied into B
+        const double* Wb = c.W + (r0 / momms::kTrsmNb) * momms::kTrsmNb * momms::kTrsmNb;
+        int rc;
+        if (left) {
+            rc = trsm_gemm(c, c.trans, MOMMS_OP_N, size, c.n, size, alpha, Wb, momms::kTrsmNb, c.B + r0, c.ldb, 0.0,
+                           c.T, size);
+            if (rc) return rc;
+            if (cudaMemcpy2DAsync(c.B + r0, c.ldb * sizeof(double), c.T, size * sizeof(double), size * sizeof(double),
+                                  c.n, cudaMemcpyDeviceToDevice, c.s) != cudaSuccess)
+                return MOMMS_ERR_CUDA;
+        } else {
+            rc = trsm_gemm(c, MOMMS_OP_N, c.trans, c.m, size, size, alpha, c.B + r0 * c.ldb, c.ldb, Wb,
+                           momms::kTrsmNb, 0.0, c.T, c.m);
+            if (rc) return rc;
+            if (cudaMemcpy2DAsync(c.B + r0 * c.ldb, c.ldb * sizeof(double), c.T, c.m * sizeof(double),
+                                  c.m * sizeof(double), size, cudaMemcpyDeviceToDevice, c.s) != cudaSuccess)
+                return MOMMS_ERR_CUDA;
+        }
+        return MOMMS_OK;
+    }
+    // split at a multiple of the block order, near the middle
+    const int64_t half_blocks = ((size + momms::kTrsmNb - 1) / momms::kTrsmNb) / 2;
+    const int64_t mid = r0 + half_blocks * momms::kTrsmNb;
+    // LEFT: op(A) lower -> first half first; RIGHT: op(A) upper -> first half first
+    const bool first_half_first = left ? c.eff_lower : !c.eff_lower;
+    const int64_t a0 = first_half_first ? r0 : mid, a1 = first_half_first ? mid : r1;   // solved first
+    const int64_t b0 = first_half_first ? mid : r0, b1 = first_half_first ? r1 : mid;   // updated, then solved
+    int rc = trsm_rec(c, a0, a1, alpha);
+    if (rc) return rc;
+    int op;
+    if (left) {
+        // B_b := alpha B_b - op(A)[b, a] X_a
+        const double* Aba = op_block(c, b0, a0, &op);
+        rc = trsm_gemm(c, op, MOMMS_OP_N, b1 - b0, c.n, a1 - a0, -1.0, Aba, c.lda, c.B + a0, c.ldb, alpha, c.B + b0,
+                       c.ldb);
+    } else {
+        // B_b := alpha B_b - X_a op(A)[a, b]
+        const double* Aab = op_block(c, a0, b0, &op);
+        rc = trsm_gemm(c, MOMMS_OP_N, op, c.m, b1 - b0, a1 - a0, -1.0, c.B + a0 * c.ldb, c.ldb, Aab, c.lda, alpha,
+                       c.B + b0 * c.ldb, c.ldb);
+    }
+    if (rc) return rc;
+    return trsm_rec(c, b0, b1, 1.0);
+}
+
+}  // namespace
+
+int momms_trsm(momms_handle_t h, int side, int uplo, int trans, int diag, int64_t m, int64_t n, double alpha,
+               const double* A, int64_t lda, double* B, int64_t ldb, momms_stream_t stream) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (side != MOMMS_LEFT && side != MOMMS_RIGHT) return -2;
+    if (uplo != MOMMS_LOWER && uplo != MOMMS_UPPER) return -3;
+    if (trans != MOMMS_OP_N && trans != MOMMS_OP_T) return -4;
+    if (diag != MOMMS_NON_UNIT && diag != MOMMS_UNIT) return -5;
+    if (m < 0) return -6;
+    if (n < 0) return -7;
+    const int64_t t = side == MOMMS_LEFT ? m : n;  // order of the triangular matrix
+    if (lda < std::max<int64_t>(1, t)) return -10;
+    if (ldb < std::max<int64_t>(1, m)) return -12;
+    if (m > 0 && n > 0 && alpha != 0.0 && !A) return -9;
+    if (m > 0 && n > 0 && !B) return -11;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->report = momms_report_t{};
+    if (m == 0 || n == 0) return MOMMS_OK;
+    if (alpha == 0.0) {
+        h->report.launches = 1;
+        return scale_c(m, n, 0.0, B, ldb, s);
+    }
+    // scratch kept by the handle: the diagonal blocks' inverses and one leaf's product
+    const size_t wbytes = align256(momms::tri_inverse_bytes(t));
+    const size_t tbytes = align256(static_cast<size_t>(momms::kTrsmNb) * (side == MOMMS_LEFT ? n : m) * sizeof(double));
+    int rc = grow_device(&h->ooc_buf, &h->ooc_bytes, wbytes + tbytes);
+    if (rc) return rc;
+    double* W = static_cast<double*>(h->ooc_buf);
+    if (momms::launch_tri_inverse(t, A, lda, uplo, diag == MOMMS_UNIT, W, s) != cudaSuccess) return MOMMS_ERR_CUDA;
+    TrsmCtx c{};
+    c.h = h;
+    c.side = side;
+    c.uplo = uplo;
+    c.trans = trans;
+    c.eff_lower = (uplo == MOMMS_LOWER) != (trans == MOMMS_OP_T);
+    c.m = m;
+    c.n = n;
+    c.A = A;
+    c.lda = lda;
+    c.B = B;
+    c.ldb = ldb;
+    c.W = W;
+    c.T = reinterpret_cast<double*>(reinterpret_cast<char*>(h->ooc_buf) + wbytes);
+    c.s = s;
+    c.launches = 1;
+    rc = trsm_rec(c, 0, t, alpha);
+    if (rc) return rc;
+    h->report.launches = c.launches;
+    return MOMMS_OK;
+}
+
 // ------------------------------------------------------------------ out-of-core products
 // Host memory (Grace LPDDR over NVLink-C2C on GB300) is the slow level and HBM the fast one:
 // Resident C at the HBM level (Sec. 2.2.1).  A b x b block of C stays in HBM while b x b

@@ -70,6 +70,7 @@ _SIGS = {
     "momms_set_raster_group": ([_VP, _I32], _I32),
     "momms_set_tile_n": ([_VP, _I32], _I32),
     "momms_set_scheme": ([_VP, _I32], _I32),
+    "momms_trsm": ([_VP, _I32, _I32, _I32, _I32, _I64, _I64, _DBL, _VP, _I64, _VP, _I64, _VP], _I32),
     "momms_crt_moduli": ([_I32, _I64, _VP, _VP], _I32),
     "momms_emu_residue_gemm": ([_I64, _I64, _I64, _I32, _VP, _VP, _I64, _I64, _I64, _I32, _VP, _VP, _SZ, _VP, _VP],
                                _I32),
@@ -176,6 +177,11 @@ def momms_syrk(handle, uplo, trans, n, k, alpha, A, lda, beta, C, ldc, stream=No
 
 def momms_trmm(handle, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, stream=None):
     return lib().momms_trmm(_h(handle), side, uplo, trans, diag, m, n, alpha, _VP(A), lda, _VP(B), ldb,
+                            _stream(stream))
+
+
+def momms_trsm(handle, side, uplo, trans, diag, m, n, alpha, A, lda, B, ldb, stream=None):
+    return lib().momms_trsm(_h(handle), side, uplo, trans, diag, m, n, alpha, _VP(A), lda, _VP(B), ldb,
                             _stream(stream))
 
 

@@ -395,6 +395,42 @@ def test_modular_dgemm_alpha_beta_fma_and_nan():
             assert C[i, j] == float(exact)
 
 
+# --------------------------------------------------------------------------- triangular solve
+@pytest.mark.parametrize("side", ["L", "R"])
+@pytest.mark.parametrize("lower", [True, False])
+@pytest.mark.parametrize("trans", [False, True])
+def test_trsm_integer_recovery_exact(side, lower, trans):
+    # unit triangle of small integers, integer solution: every substitution step is exact
+    t, r = 12, 5
+    rng = np.random.default_rng(161)
+    A = rng.integers(-2, 3, (t, t)).astype(np.float64)
+    A[np.diag_indices(t)] = np.nan                     # unit diagonal: never read
+    T = np.tril(A, -1) if lower else np.triu(A, 1)
+    T = T + np.eye(t)
+    M = T.T if trans else T
+    X = rng.integers(-3, 4, (t, r) if side == "L" else (r, t)).astype(np.float64)
+    B = M @ X if side == "L" else X @ M
+    got = oracle.trsm(A, B, 1.0, side, lower, trans, unit=True)
+    assert np.array_equal(got, X)
+
+
+@pytest.mark.parametrize("side", ["L", "R"])
+@pytest.mark.parametrize("lower,trans", [(True, False), (False, True), (False, False)])
+def test_trsm_agrees_with_scipy(side, lower, trans):
+    sl = pytest.importorskip("scipy.linalg")
+    t, r = 40, 7
+    A = syn.matrix("uniform", t, t, 162) / t + np.diag(1.0 + syn.unit_uniform(163, t))
+    B = syn.matrix("uniform", t, r, 164) if side == "L" else syn.matrix("uniform", r, t, 165)
+    got = oracle.trsm(A, B, -2.0, side, lower, trans)
+    if side == "L":
+        want = sl.solve_triangular(A, -2.0 * B, lower=lower, trans=1 if trans else 0)
+    else:   # X op(A) = B  <=>  op(A)^T X^T = B^T
+        want = sl.solve_triangular(A, -2.0 * B.T, lower=lower, trans=0 if trans else 1).T
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-13)
+    I = np.eye(t)
+    assert np.array_equal(oracle.trsm(I, B, 3.0, side, lower, trans), 3.0 * B)
+
+
 # --------------------------------------------------------------------------- I/O counts
 def closed_form(member, m, n, k, b1, b2, c_read):
     """The paper's resident-algorithm I/O counts in margin (ceiling) form, Sec. 2.2."""
