@@ -43,9 +43,13 @@ NCU_SLICE_CAPTURE = {"dram_bytes": (27.75e9 + 0.706e9 + 0.087e9) + (1.93e9 + 0.0
                      "tensor_flops": 21 * 2.0 * 8192 ** 3,
                      "source": "ncu capture of the 8192^3 call, scaled by tensor flops for other sizes "
                                "(profiles/slice_gemm_members_8192.md)"}
-# The same for the residue-product launch of the modular encoding (None: not captured since
-# the kernel last changed).
-NCU_RESIDUE_CAPTURE = None
+# The same for the residue-product launch of the modular encoding (m=n=k=8192, 12 moduli; two
+# launches averaged), summarised in profiles/residue_product_8192.md.  None whenever the kernel
+# changes until it is captured again.
+NCU_RESIDUE_CAPTURE = {"dram_bytes": ((10.371e9 + 0.803e9) + (9.848e9 + 0.800e9)) / 2,
+                       "tensor_flops": 12 * 2.0 * 8192 ** 3,
+                       "source": "ncu capture of the 8192^3 residue-product launch (12 moduli), scaled by tensor "
+                                 "flops for other sizes (profiles/residue_product_8192.md)"}
 UNIT = "TFLOP/s"
 SCHEMES = {"auto": 0, "slices": 1, "moduli": 2}  # momms_scheme_t
 
@@ -57,11 +61,13 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--size", type=int, default=8192)
     p.add_argument("--shape", default="square",
-                   choices=["square", "rankk", "panel", "backward", "batched", "host"],
+                   choices=["square", "rankk", "panel", "backward", "batched", "host", "trsm", "trmm", "syrk"],
                    help="square: m=n=k=size; rankk: m=n=2*size, k=256; panel: m=k=2*size, n=256; "
                         "backward: dA = dC B^T and dB = A^T dC for A 4096x2048, B 2048x4096; "
                         "batched: 2000 problems, m, n, k log-uniform in [32, 2048]; "
-                        "host: m=n=k=size with A, B, C in pinned host memory (momms_gemm_host)")
+                        "host: m=n=k=size with A, B, C in pinned host memory (momms_gemm_host); "
+                        "trsm / trmm: lower triangular A size x size, B size x size (momms_trsm / momms_trmm, "
+                        "B restored from a copy each step); syrk: C lower += A A^T, A size x size")
     p.add_argument("--block", type=int, default=0, help="momms_gemm_host block size (0 = from the budget)")
     p.add_argument("--scheme", default="auto", choices=["auto", "slices", "moduli"],
                    help="integer encoding of the emulated product (momms_set_scheme)")
@@ -316,6 +322,34 @@ def run_side_workload(args):
             M.check(M.momms_gemm_host(h, m, n, k, 1.0, hA, m, hB, k, 1.0, hC, m, int(args.device_gb * 2 ** 30),
                                       args.block, stream), "momms_gemm_host")
             io.update(h.report())
+    elif args.shape in ("trsm", "trmm"):
+        m = n = args.size
+        A_h = syn.matrix("uniform", m, m, syn.workload_seed(5, "A")) / np.sqrt(m)
+        A_h[np.diag_indices(m)] = 1.0 + syn.unit_uniform(syn.workload_seed(5, "C"), m)
+        A = M.DeviceMatrix.from_numpy(np.tril(A_h))
+        B0 = M.DeviceMatrix.from_numpy(syn.matrix("uniform", m, n, syn.workload_seed(5, "B")))
+        B = M.DeviceMatrix(m, n)
+        flops = 1.0 * m * m * n
+        fn = M.momms_trsm if args.shape == "trsm" else M.momms_trmm
+        workload = (f"{'triangular solve B := A^-1 B' if args.shape == 'trsm' else 'triangular product B := A B'}, "
+                    f"A {m}x{m} lower (off-diagonal uniform[-1,1]/sqrt(m), diagonal in [1,2]), B {m}x{n} "
+                    f"uniform[-1,1] (seeded SplitMix64), restored from a device copy every step (counted); "
+                    f"flops m^2 n")
+
+        def step():
+            B.storage.copy_(B0.storage)
+            M.check(fn(h, M.LEFT, M.LOWER, M.OP_N, M.NON_UNIT, m, n, 1.0, A.ptr, A.ld, B.ptr, B.ld, stream),
+                    args.shape)
+    elif args.shape == "syrk":
+        n = k = args.size
+        A = M.DeviceMatrix.from_numpy(syn.matrix("uniform", n, k, syn.workload_seed(6, "A")))
+        C = M.DeviceMatrix.from_numpy(syn.matrix("uniform", n, n, syn.workload_seed(6, "C")))
+        flops = 1.0 * n * (n + 1) * k
+        workload = (f"symmetric rank-k update C := A A^T + C on the lower triangle, n=k={n}, uniform[-1,1] "
+                    f"(seeded SplitMix64); flops n (n + 1) k")
+
+        def step():
+            M.check(M.momms_syrk(h, M.LOWER, M.OP_N, n, k, 1.0, A.ptr, A.ld, 1.0, C.ptr, C.ld, stream), "syrk")
     elif args.shape == "backward":
         m, k, n = 4096, 2048, 4096
         A = M.DeviceMatrix.from_numpy(syn.matrix("normal", m, k, syn.workload_seed(2, "A")))
@@ -383,7 +417,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.shape in ("backward", "batched", "host"):
+    if args.shape in ("backward", "batched", "host", "trsm", "trmm", "syrk"):
         return run_side_workload(args)
     import torch
 
@@ -600,7 +634,8 @@ def main():
         ratio = sample.error_ratio(dC.to_numpy()[:, :acc_cols])
         accuracy = {"max_error_over_bound": ratio, "columns_checked": acc_cols,
                     "bound": "4 k 2^-53 (|A||B| + |C0|)(1 + 4 k 2^-53) + 2^-1021, componentwise",
-                    "slices": int(h.report()["slices"]) if h.report()["mode"] == M.MODE_EMULATED else 0}
+                    "slices": int(h.report()["slices"]) if h.report()["mode"] == M.MODE_EMULATED else 0,
+                    "moduli": int(h.report()["moduli"]), "operand_bits": int(h.report()["operand_bits"])}
 
     if rank == 0:
         emulated = rep["mode"] == M.MODE_EMULATED

@@ -234,8 +234,9 @@ Plan default_plan(int64_t m, int64_t n, int64_t k) {
     const double flops = 2.0 * m * n * k;
     // the FP64 tensor pipe is ~1 TFLOP/s; emulation pays off once its fixed costs (five to
     // seven launches, a slice-count readback, 128-row tiles) are amortised: measured 3.5x the
-    // native rate at 512^3 (2.7e8 flops)
-    const bool big = m >= 256 && n >= 256 && k >= 128 && flops >= 2.0e8;
+    // native rate at 512^3 (2.7e8 flops).  Thin products qualify too (a 128 x 8192 x 128 block
+    // of a triangular solve: the modular encoding's units are tiles x moduli, enough for all SMs)
+    const bool big = std::min(m, n) >= 64 && k >= 64 && flops >= 2.0e8;
     p.mode = big ? MOMMS_MODE_EMULATED : MOMMS_MODE_NATIVE;
     p.member = MOMMS_MEMBER_C2;
     p.slices = 0;
