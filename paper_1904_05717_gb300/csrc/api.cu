@@ -917,13 +917,17 @@ int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const 
     if (!ldc) return -13;
     if (count > (int64_t(1) << 30)) return MOMMS_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double total_flops = 0.0;
     for (int64_t i = 0; i < count; ++i) {
         int rc = check_gemm_args(1, MOMMS_OP_N, MOMMS_OP_N, m[i], n[i], k[i], A[i], lda[i], B[i], ldb[i],
                                  C[i], ldc[i], alpha[i], false);
         if (rc) return -3;  // the size / pointer arrays hold an invalid entry
         if (m[i] > INT32_MAX / 2 || n[i] > INT32_MAX / 2 || k[i] > INT32_MAX / 2) return MOMMS_ERR_UNSUPPORTED;
+        total_flops += 2.0 * static_cast<double>(m[i]) * static_cast<double>(n[i]) * static_cast<double>(k[i]);
     }
-    const bool emulated = h->mode == MOMMS_MODE_EMULATED;
+    // AUTO: the emulated pipeline (five launches for the whole batch) once the batch's work
+    // amortises them, as for a single product of that many flops
+    const bool emulated = h->mode == MOMMS_MODE_EMULATED || (h->mode == MOMMS_MODE_AUTO && total_flops >= 2.0e9);
     if (emulated) {
         // problems with work go to one batched pipeline; the rest only scale C
         std::vector<int64_t> idx;

@@ -188,3 +188,23 @@ def test_batched_emulated_same_handle_new_problems_reuses_table_memory():
         assert h.device_status() == M.MOMMS_OK
         assert check_all(probs, dev) <= 1.0
     h.close()
+
+
+def test_batched_auto_picks_emulation_by_total_work():
+    # AUTO: the emulated pipeline once the batch holds >= 2e9 flops (here ~2.2e9), native below
+    big = []
+    for i in range(8):
+        A = syn.matrix("uniform", 520, 512, 2000 + 3 * i)
+        B = syn.matrix("uniform", 512, 530, 2001 + 3 * i)
+        C = syn.matrix("uniform", 520, 530, 2002 + 3 * i)
+        big.append((520, 530, 512, A, B, C))
+    h = M.Handle()
+    dev, _ = run_batched(h, big)
+    assert h.report()["mode"] == M.MODE_EMULATED
+    assert h.device_status() == M.MOMMS_OK
+    assert check_all(big, dev) <= 1.0
+    small = make_problems(6, 32, 200, 2100)
+    dev, _ = run_batched(h, small)
+    assert h.report()["mode"] == M.MODE_NATIVE
+    assert check_all(small, dev) <= 1.0
+    h.close()
