@@ -116,6 +116,8 @@ struct Params {
     // plane l of A by plane l of B and its epilogue stores (sum mod modp[l]) as a byte.
     uint8_t* res;             // [l][col][row] residues of the product, m n bytes per modulus
     uint32_t modp[kCrtMaxModuli];
+    uint32_t modmagic[kCrtMaxModuli];  // floor(2^32 / p) + 1
+    uint32_t modoff[kCrtMaxModuli];    // p ceil(2^31 / p): makes any int32 sum a uint32 of equal residue
 };
 
 // The it-th tile of this CTA: its problem (-1 = the single problem of p.one) and tile
@@ -389,6 +391,18 @@ MOMMS_DEV void store_partial(int4* dst, const int32_t (&acc)[CR], uint32_t tsum)
     }
 }
 
+// x mod p in [0, p) for an int32 sum |x| <= k 127^2 < 2^31 - 255: u = x + p ceil(2^31 / p) lies
+// in [0, 2^32) with the same residue, and one multiply-high quotient (floor or one over) with a
+// correction finishes it -- no integer division (whose reciprocal estimate runs on the slow
+// conversion pipe).
+MOMMS_DEV uint32_t residue_of(int32_t x, uint32_t p, uint32_t magic, uint32_t off) {
+    const uint32_t u = static_cast<uint32_t>(x) + off;
+    const uint32_t q = __umulhi(u, magic);
+    int r = static_cast<int>(u - q * p);
+    if (r < 0) r += static_cast<int>(p);
+    return static_cast<uint32_t>(r);
+}
+
 // The modular epilogue of modulus l: the thread's int32 sums (CR in `acc`, CT in TMEM at
 // `tsum`) reduced into [0, p) and stored as bytes at res[l][col][row].  The TMEM reads are
 // warp-wide, so every lane takes them before the bounds checks.
@@ -397,14 +411,13 @@ MOMMS_DEV void store_residues(const Params& p, int tm, int tn, int l, int third,
                               uint32_t tsum) {
     const int row = tm * BM + rloc;
     const int col0 = tn * BN + third * (BN / 3);
-    const int pl = static_cast<int>(p.modp[l]);
+    const uint32_t pl = p.modp[l], mg = p.modmagic[l], off = p.modoff[l];
     const bool row_ok = row < p.one.m;
     uint8_t* dst = p.res + static_cast<size_t>(l) * p.one.m * p.one.n + static_cast<size_t>(col0) * p.one.m + row;
     const int ncols = min(BN / 3, p.one.n - col0);
 #pragma unroll
     for (int c = 0; c < CR; ++c) {
-        int r = acc[c] % pl;
-        if (r < 0) r += pl;
+        const uint32_t r = residue_of(acc[c], pl, mg, off);
         if (row_ok && c < ncols) dst[static_cast<size_t>(c) * p.one.m] = static_cast<uint8_t>(r);
     }
 #pragma unroll
@@ -415,8 +428,7 @@ MOMMS_DEV void store_residues(const Params& p, int tm, int tn, int l, int third,
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int c = CR + q * 16 + j;
-            int r = static_cast<int32_t>(t[j]) % pl;
-            if (r < 0) r += pl;
+            const uint32_t r = residue_of(static_cast<int32_t>(t[j]), pl, mg, off);
             if (row_ok && c < ncols) dst[static_cast<size_t>(c) * p.one.m] = static_cast<uint8_t>(r);
         }
     }
@@ -952,7 +964,12 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         p.status = a.status;
         if (mod) {
             p.res = a.res;
-            for (int l = 0; l < a.crt->N; ++l) p.modp[l] = a.crt->p[l];
+            for (int l = 0; l < a.crt->N; ++l) {
+                const uint32_t pl = a.crt->p[l];
+                p.modp[l] = pl;
+                p.modmagic[l] = a.crt->magic[l];
+                p.modoff[l] = static_cast<uint32_t>(pl * (((1ull << 31) + pl - 1) / pl));
+            }
             slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(
                 mapA, mapB, p);
             cudaError_t e = cudaGetLastError();
