@@ -338,11 +338,12 @@ int momms_trmm(momms_handle_t handle, int side, int uplo, int trans, int diag, i
 /* B := alpha*op(A)^-1*B (side LEFT: solves op(A) X = alpha B, A m x m) or
  * B := alpha*B*op(A)^-1 (side RIGHT: X op(A) = alpha B, A n x n), A triangular (uplo;
  * diag UNIT: ones on the diagonal, which is not read), B m x n overwritten by X (BLAS
- * dtrsm).  Recursive blocked solve: op(A) is halved (at multiples of 128) until blocks of
- * order <= 128 remain; the off-diagonal half becomes one GEMM update of the right-hand sides
+ * dtrsm).  Recursive blocked solve: op(A) is halved (at multiples of 512) until blocks of
+ * order <= 512 remain; the off-diagonal half becomes one GEMM update of the right-hand sides
  * (this library's product, in the handle's mode -- the updates carry ~all m^2 n (n^2 m)
- * flops), and each 128 x 128 diagonal block is applied as a GEMM with its explicit inverse,
- * computed in FP64 by a substitution kernel (one CTA per block).  The error is that of the
+ * flops), and each 512 x 512 diagonal block is applied as a GEMM with its explicit inverse:
+ * the inverses of its 64 x 64 blocks come from an FP64 substitution kernel (one CTA per
+ * block) and are joined pairwise by batched products.  The error is that of the
  * GEMMs plus the inverses' (well-conditioned diagonal blocks: a small multiple of
  * 2^-53 (|op(A)| |X|) componentwise).  Device pointers, asynchronous on `stream` (the
  * data-driven slice count of the emulated GEMMs reads back a spread per GEMM).  Errors:

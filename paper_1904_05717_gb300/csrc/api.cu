@@ -1583,7 +1583,7 @@ struct TrsmCtx {
     int64_t lda;
     double* B;
     int64_t ldb;
-    const double* W;       // inverses of the diagonal blocks (kTrsmNb^2 each)
+    const double* W;       // inverses of the leaf blocks (kTrsmLeaf^2 each, stride kTrsmLeaf)
     double* T;             // leaf product before it is copied into B
     cudaStream_t s;
     int64_t launches;
@@ -1607,12 +1607,13 @@ const double* op_block(const TrsmCtx& c, int64_t r, int64_t q, int* op) {
 int trsm_rec(TrsmCtx& c, int64_t r0, int64_t r1, double alpha) {
     const int64_t size = r1 - r0;
     const bool left = c.side == MOMMS_LEFT;
-    if (size <= momms::kTrsmNb) {
+    constexpr int64_t leaf = momms::kTrsmLeaf;
+    if (size <= leaf) {
         // leaf: X = alpha op(inv(A_bb)) B_b through the scratch T, then copied into B
-        const double* Wb = c.W + (r0 / momms::kTrsmNb) * momms::kTrsmNb * momms::kTrsmNb;
+        const double* Wb = c.W + (r0 / leaf) * leaf * leaf;
         int rc;
         if (left) {
-            rc = trsm_gemm(c, c.trans, MOMMS_OP_N, size, c.n, size, alpha, Wb, momms::kTrsmNb, c.B + r0, c.ldb, 0.0,
+            rc = trsm_gemm(c, c.trans, MOMMS_OP_N, size, c.n, size, alpha, Wb, leaf, c.B + r0, c.ldb, 0.0,
                            c.T, size);
             if (rc) return rc;
             if (cudaMemcpy2DAsync(c.B + r0, c.ldb * sizeof(double), c.T, size * sizeof(double), size * sizeof(double),
@@ -1620,7 +1621,7 @@ int trsm_rec(TrsmCtx& c, int64_t r0, int64_t r1, double alpha) {
                 return MOMMS_ERR_CUDA;
         } else {
             rc = trsm_gemm(c, MOMMS_OP_N, c.trans, c.m, size, size, alpha, c.B + r0 * c.ldb, c.ldb, Wb,
-                           momms::kTrsmNb, 0.0, c.T, c.m);
+                           leaf, 0.0, c.T, c.m);
             if (rc) return rc;
             if (cudaMemcpy2DAsync(c.B + r0 * c.ldb, c.ldb * sizeof(double), c.T, c.m * sizeof(double),
                                   c.m * sizeof(double), size, cudaMemcpyDeviceToDevice, c.s) != cudaSuccess)
@@ -1628,9 +1629,9 @@ int trsm_rec(TrsmCtx& c, int64_t r0, int64_t r1, double alpha) {
         }
         return MOMMS_OK;
     }
-    // split at a multiple of the block order, near the middle
-    const int64_t half_blocks = ((size + momms::kTrsmNb - 1) / momms::kTrsmNb) / 2;
-    const int64_t mid = r0 + half_blocks * momms::kTrsmNb;
+    // split at a multiple of the leaf order, near the middle
+    const int64_t half_blocks = ((size + leaf - 1) / leaf) / 2;
+    const int64_t mid = r0 + half_blocks * leaf;
     // LEFT: op(A) lower -> first half first; RIGHT: op(A) upper -> first half first
     const bool first_half_first = left ? c.eff_lower : !c.eff_lower;
     const int64_t a0 = first_half_first ? r0 : mid, a1 = first_half_first ? mid : r1;   // solved first
@@ -1651,6 +1652,77 @@ int trsm_rec(TrsmCtx& c, int64_t r0, int64_t r1, double alpha) {
     }
     if (rc) return rc;
     return trsm_rec(c, b0, b1, 1.0);
+}
+
+// The inverses of the leaf blocks from those of their kTrsmNb-blocks (already on W's diagonal):
+// at each level s = kTrsmNb, 2 kTrsmNb, .. < kTrsmLeaf, every pair of s-blocks of a leaf is joined,
+//   lower: [L11 0; L21 L22]^-1 = [I11 0; -I22 (L21 I11) I22],
+//   upper: [U11 U12; 0 U22]^-1 = [I11 -I11 (U12 I22); 0 I22],
+// as two batched products per level (all the inner products, then all the outer ones) -- emulated
+// unless the handle asks for native (the batches are small: ~1 GFLOP per 8192 rows, 1 ms on the
+// FP64 tensor pipe).  Tmp holds the inner products.
+int trsm_join_inverses(momms_handle_t h, int64_t t, const double* A, int64_t lda, int uplo, double* W, double* Tmp,
+                       cudaStream_t s, int64_t* launches) {
+    constexpr int64_t leaf = momms::kTrsmLeaf;
+    const bool lower = uplo == MOMMS_LOWER;
+    struct ModeGuard {  // the batched calls below run emulated in AUTO; the caller's mode comes back after
+        momms_handle_t h;
+        int saved;
+        ~ModeGuard() { h->mode = saved; }
+    } guard{h, h->mode};
+    if (h->mode == MOMMS_MODE_AUTO) h->mode = MOMMS_MODE_EMULATED;
+    for (int64_t sz = momms::kTrsmNb; sz < leaf; sz *= 2) {
+        std::vector<int64_t> m1, n1, k1, lda1, ldb1, ldc1, m2, n2, k2, lda2, ldb2, ldc2;
+        std::vector<const double*> a1, b1, a2, b2;
+        std::vector<double*> c1, c2;
+        double* tmp = Tmp;
+        for (int64_t b0 = 0; b0 < t; b0 += leaf) {
+            const int64_t lsz = std::min(leaf, t - b0);
+            double* Wl = W + (b0 / leaf) * leaf * leaf;
+            for (int64_t o = 0; o + sz < lsz; o += 2 * sz) {
+                const int64_t s1 = sz, s2 = std::min(sz, lsz - o - sz);  // sizes of the two diagonal blocks
+                const double* I11 = Wl + o + o * leaf;
+                const double* I22 = Wl + (o + sz) + (o + sz) * leaf;
+                if (lower) {
+                    // Tmp = L21 I11 (s2 x s1); W21 = -I22 Tmp
+                    m1.push_back(s2); n1.push_back(s1); k1.push_back(s1);
+                    a1.push_back(A + (b0 + o + sz) + (b0 + o) * lda); lda1.push_back(lda);
+                    b1.push_back(I11); ldb1.push_back(leaf);
+                    c1.push_back(tmp); ldc1.push_back(s2);
+                    m2.push_back(s2); n2.push_back(s1); k2.push_back(s2);
+                    a2.push_back(I22); lda2.push_back(leaf);
+                    b2.push_back(tmp); ldb2.push_back(s2);
+                    c2.push_back(Wl + (o + sz) + o * leaf); ldc2.push_back(leaf);
+                    tmp += s2 * s1;
+                } else {
+                    // Tmp = U12 I22 (s1 x s2); W12 = -I11 Tmp
+                    m1.push_back(s1); n1.push_back(s2); k1.push_back(s2);
+                    a1.push_back(A + (b0 + o) + (b0 + o + sz) * lda); lda1.push_back(lda);
+                    b1.push_back(I22); ldb1.push_back(leaf);
+                    c1.push_back(tmp); ldc1.push_back(s1);
+                    m2.push_back(s1); n2.push_back(s2); k2.push_back(s1);
+                    a2.push_back(I11); lda2.push_back(leaf);
+                    b2.push_back(tmp); ldb2.push_back(s1);
+                    c2.push_back(Wl + o + (o + sz) * leaf); ldc2.push_back(leaf);
+                    tmp += s1 * s2;
+                }
+            }
+        }
+        const int64_t cnt = static_cast<int64_t>(m1.size());
+        if (cnt == 0) continue;
+        const std::vector<double> one(cnt, 1.0), minus_one(cnt, -1.0), zero(cnt, 0.0);
+        int rc = momms_gemm_batched(h, cnt, m1.data(), n1.data(), k1.data(), one.data(), a1.data(), lda1.data(),
+                                    b1.data(), ldb1.data(), zero.data(), c1.data(), ldc1.data(),
+                                    reinterpret_cast<momms_stream_t>(s));
+        if (rc) return rc;
+        *launches += h->report.launches;
+        rc = momms_gemm_batched(h, cnt, m2.data(), n2.data(), k2.data(), minus_one.data(), a2.data(), lda2.data(),
+                                b2.data(), ldb2.data(), zero.data(), c2.data(), ldc2.data(),
+                                reinterpret_cast<momms_stream_t>(s));
+        if (rc) return rc;
+        *launches += h->report.launches;
+    }
+    return MOMMS_OK;
 }
 
 }  // namespace
@@ -1676,13 +1748,21 @@ int momms_trsm(momms_handle_t h, int side, int uplo, int trans, int diag, int64_
         h->report.launches = 1;
         return scale_c(m, n, 0.0, B, ldb, s);
     }
-    // scratch kept by the handle: the diagonal blocks' inverses and one leaf's product
+    // scratch kept by the handle: the leaf blocks' inverses, one leaf's product, and the inner
+    // products of the inverses' assembly (at most half a leaf block per leaf)
     const size_t wbytes = align256(momms::tri_inverse_bytes(t));
-    const size_t tbytes = align256(static_cast<size_t>(momms::kTrsmNb) * (side == MOMMS_LEFT ? n : m) * sizeof(double));
-    int rc = grow_device(&h->ooc_buf, &h->ooc_bytes, wbytes + tbytes);
+    const size_t tbytes =
+        align256(static_cast<size_t>(momms::kTrsmLeaf) * (side == MOMMS_LEFT ? n : m) * sizeof(double));
+    const size_t jbytes = align256(momms::tri_inverse_bytes(t) / 4);
+    int rc = grow_device(&h->ooc_buf, &h->ooc_bytes, wbytes + tbytes + jbytes);
     if (rc) return rc;
     double* W = static_cast<double*>(h->ooc_buf);
+    double* J = reinterpret_cast<double*>(reinterpret_cast<char*>(h->ooc_buf) + wbytes + tbytes);
+    if (cudaMemsetAsync(W, 0, wbytes, s) != cudaSuccess) return MOMMS_ERR_CUDA;
     if (momms::launch_tri_inverse(t, A, lda, uplo, diag == MOMMS_UNIT, W, s) != cudaSuccess) return MOMMS_ERR_CUDA;
+    int64_t join_launches = 0;
+    rc = trsm_join_inverses(h, t, A, lda, uplo, W, J, s, &join_launches);
+    if (rc) return rc;
     TrsmCtx c{};
     c.h = h;
     c.side = side;
@@ -1698,7 +1778,7 @@ int momms_trsm(momms_handle_t h, int side, int uplo, int trans, int diag, int64_
     c.W = W;
     c.T = reinterpret_cast<double*>(reinterpret_cast<char*>(h->ooc_buf) + wbytes);
     c.s = s;
-    c.launches = 1;
+    c.launches = 1 + join_launches;
     rc = trsm_rec(c, 0, t, alpha);
     if (rc) return rc;
     h->report.launches = c.launches;

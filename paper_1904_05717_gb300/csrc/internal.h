@@ -88,13 +88,14 @@ cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, con
                                    double beta, double* C, int64_t ldc, cudaStream_t stream);
 
 // ----------------------------------------------- triangular solve (leaf step)
-constexpr int kTrsmNb = 128;      // order of the diagonal blocks applied through their inverses
+constexpr int kTrsmNb = 64;       // order of the blocks inverted by substitution
+constexpr int kTrsmLeaf = 512;    // order of the diagonal blocks applied through their inverses
 constexpr int kTrsmLower = 0;     // MOMMS_LOWER
-// Bytes of the inverses of the ceil(t / kTrsmNb) diagonal blocks (dense kTrsmNb^2 each).
+// Bytes of the inverses of the ceil(t / kTrsmLeaf) leaf blocks (dense kTrsmLeaf^2 each).
 size_t tri_inverse_bytes(int64_t t);
-// W := the inverses of the diagonal blocks of the t x t triangle of A (uplo 0 lower / 1 upper;
-// unit: the diagonal is taken as ones and not read), each in the stored orientation, zero outside
-// the triangle.
+// The inverses of the kTrsmNb-blocks of the t x t triangle of A (uplo 0 lower / 1 upper; unit: the
+// diagonal is taken as ones and not read), each in the stored orientation, into the diagonal
+// sub-blocks of W's leaf blocks (the rest of W is left as it is).
 cudaError_t launch_tri_inverse(int64_t t, const double* A, int64_t lda, int uplo, int unit, double* W,
                                cudaStream_t stream);
 

@@ -3,8 +3,10 @@
 //
 // The solve op(A) X = alpha B (or X op(A) = alpha B) is done recursively: the off-diagonal
 // blocks become GEMM updates of the right-hand sides (the product of this library), and each
-// nb x nb diagonal block is applied as a GEMM with its explicit inverse.  The inverses are
-// computed here in FP64, one CTA per block, by forward substitution on the block's columns:
+// kTrsmLeaf x kTrsmLeaf diagonal block is applied as a GEMM with its explicit inverse.  The
+// inverses of the nb x nb blocks inside a leaf are computed here in FP64, one CTA per block, by
+// forward substitution on the block's columns (api.cu then joins them into the leaf's inverse
+// with batched GEMMs, [L11 0; L21 L22]^-1 = [I11 0; -I22 L21 I11 I22]):
 // for a lower triangle L, column t of L^-1 is x with x_t = 1 / L_tt and
 //     x_i = -(sum_{k=t}^{i-1} L_ik x_k) / L_ii,   i > t.
 // An upper triangle U is handled as L = U^T (inv(U) = inv(U^T)^T).
@@ -17,9 +19,10 @@ namespace {
 // Packed lower triangle by rows: element (i, k), k <= i, at i (i + 1) / 2 + k.
 __device__ __forceinline__ int tri_row(int i, int k) { return i * (i + 1) / 2 + k; }
 
-// One CTA (kTrsmNb threads) per diagonal block b of the t x t triangle.  W receives the block's
-// inverse as a dense nb x nb column-major block (stride nb, block b at W + b nb nb), zero outside
-// the triangle (and outside the block's size for the last, partial block).
+// One CTA (kTrsmNb threads) per diagonal block g of the t x t triangle.  The block's inverse goes
+// to the diagonal sub-block g % (kTrsmLeaf / nb) of leaf block g / (kTrsmLeaf / nb) of W (dense
+// kTrsmLeaf x kTrsmLeaf column-major blocks), zero outside the triangle and outside the block's
+// size for the last, partial block.
 __global__ void __launch_bounds__(kTrsmNb) tri_inverse_kernel(int64_t t, const double* __restrict__ A, int64_t lda,
                                                               int uplo, int unit, double* __restrict__ W) {
     extern __shared__ double sm[];
@@ -55,7 +58,10 @@ __global__ void __launch_bounds__(kTrsmNb) tri_inverse_kernel(int64_t t, const d
         }
     }
     __syncthreads();
-    double* Wb = W + static_cast<int64_t>(blockIdx.x) * nb * nb;
+    constexpr int per_leaf = kTrsmLeaf / nb;
+    constexpr int64_t ldw = kTrsmLeaf;
+    double* Wb = W + static_cast<int64_t>(blockIdx.x / per_leaf) * ldw * ldw +
+                 static_cast<int64_t>(blockIdx.x % per_leaf) * nb * (ldw + 1);
     for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
         const int r = idx % nb, c = idx / nb;  // element (r, c) of the stored-orientation inverse
         double v = 0.0;
@@ -63,15 +69,15 @@ __global__ void __launch_bounds__(kTrsmNb) tri_inverse_kernel(int64_t t, const d
             if (uplo == kTrsmLower) v = r >= c ? X[tri_row(r, c)] : 0.0;
             else v = r <= c ? X[tri_row(c, r)] : 0.0;  // inv(U) = inv(U^T)^T
         }
-        Wb[idx] = v;
+        Wb[r + c * ldw] = v;
     }
 }
 
 }  // namespace
 
 size_t tri_inverse_bytes(int64_t t) {
-    const int64_t blocks = (t + kTrsmNb - 1) / kTrsmNb;
-    return static_cast<size_t>(blocks) * kTrsmNb * kTrsmNb * sizeof(double);
+    const int64_t leaves = (t + kTrsmLeaf - 1) / kTrsmLeaf;
+    return static_cast<size_t>(leaves) * kTrsmLeaf * kTrsmLeaf * sizeof(double);
 }
 
 cudaError_t launch_tri_inverse(int64_t t, const double* A, int64_t lda, int uplo, int unit, double* W,
