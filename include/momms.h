@@ -104,6 +104,7 @@ typedef struct {
     int64_t d2h_bytes;   /* momms_gemm_host: bytes copied device -> host             */
     int moduli;          /* emulated, modular encoding: N moduli (0: digit slices)   */
     int operand_bits;    /* emulated: integer width of the operands (7 S for slices) */
+    int crt_fused;       /* moduli: 1 when the residue product rebuilt C itself       */
 } momms_report_t;
 
 /* ---------------------------------------------------------------- handles */
@@ -136,6 +137,15 @@ int momms_set_slices(momms_handle_t handle, int slices);
  * use SLICES.  Returns -2 for other values. */
 typedef enum { MOMMS_SCHEME_AUTO = 0, MOMMS_SCHEME_SLICES = 1, MOMMS_SCHEME_MODULI = 2 } momms_scheme_t;
 int momms_set_scheme(momms_handle_t handle, int scheme);
+/* Where the modular encoding rebuilds C: 1 = a separate reconstruction launch after the residue
+ * products; 2 = fused: the epilogue of a tile's last modulus (the units run modulus by modulus,
+ * so the other moduli of the tile finished long before) reads the other moduli's residues
+ * (published per tile through a device counter; a bounded wait) and writes C -- the same
+ * arithmetic, the same bits, without the separate pass over C; 0 = automatic = 1 (the fused form
+ * measured slower: the drain warps rebuild C at a fraction of the separate kernel's rate and the
+ * products wait behind them -- 11.9 against 10.4 ms per 8192^3 step).  Returns -2 for other
+ * values. */
+int momms_set_crt_fusion(momms_handle_t handle, int mode);
 /* Caps the grid of the single-product launches of this handle at `ctas` CTAs that each
  * loop over their share of the member's tiles (0 = default: one CTA per SM for the
  * emulated slice products, one CTA per tile for the native kernel).  Fewer CTAs lower

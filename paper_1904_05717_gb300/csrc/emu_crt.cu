@@ -9,14 +9,13 @@
 // Then C := alpha 2^(e_i + f_j - 2 bits) A^B^ + beta C, rounded once to FP64 (plus the
 // scaling).  The error is the truncation of A and B to `bits` bits -- that of the slice
 // encoding with bits / 7 slices without its dropped digit pairs.
+#include "crt.cuh"
 #include "internal.h"
 #include "ptx.cuh"
 
 namespace momms {
 
 namespace {
-
-using u128 = unsigned __int128;
 
 // The moduli: walking down from 255, every number coprime to all those already taken
 // (255 = 3 5 17, 254 = 2 127, 253 = 11 23, 247 = 13 19, 217 = 7 31, the rest prime); their
@@ -37,56 +36,6 @@ uint32_t inverse_mod(uint32_t a, uint32_t p) {  // a^-1 mod p (gcd(a, p) = 1)
     }
     if (t < 0) t += p;
     return static_cast<uint32_t>(t);
-}
-
-// v rounded to nearest (ties to even) as a double: the leading 64 bits with the rest folded
-// into a sticky bit (bit 0 lies below the rounding position of a 53-bit significand), one
-// correctly rounded 64-bit conversion, then an exact power-of-two scaling.
-MOMMS_DEV double u128_to_double(u128 v) {
-    const unsigned long long hi = static_cast<unsigned long long>(v >> 64);
-    if (hi == 0) return static_cast<double>(static_cast<unsigned long long>(v));
-    const int lz = __clzll(static_cast<long long>(hi));
-    const u128 t = v << lz;
-    const unsigned long long top = static_cast<unsigned long long>(t >> 64) |
-                                   static_cast<unsigned long long>(static_cast<unsigned long long>(t) != 0);
-    return static_cast<double>(top) * pow2_normal(64 - lz);
-}
-
-// mag 2^(E) with the sign, mag = hi 2^64 + lo, rounded once to FP64 (to nearest, ties to even):
-// the 53-bit significand is rounded in integers and the scale goes into the exponent field;
-// an exponent outside the normal range takes the FP64 route.
-MOMMS_DEV double scaled_double(unsigned long long hi, unsigned long long lo, bool neg, int E) {
-    if ((hi | lo) == 0) return 0.0;
-    // the leading 64 bits of mag in `top`, the bits below folded into its bit 0 (a sticky bit,
-    // under the rounding position of a 53-bit significand)
-    int lz;
-    unsigned long long top;
-    if (hi) {
-        lz = __clzll(static_cast<long long>(hi));
-        if (lz == 0) {
-            top = hi | static_cast<unsigned long long>(lo != 0);
-        } else {
-            top = (hi << lz) | (lo >> (64 - lz));
-            top |= static_cast<unsigned long long>((lo << lz) != 0);
-        }
-    } else {
-        lz = 64 + __clzll(static_cast<long long>(lo));
-        top = lo << (lz - 64);
-    }
-    unsigned long long mant = top >> 11;
-    const unsigned long long rem = top & 0x7FFull;
-    mant += (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
-    int ex = 127 - lz + E;  // unbiased exponent of |y| = mant 2^(ex - 52)
-    if (mant == (1ull << 53)) {
-        mant >>= 1;
-        ++ex;
-    }
-    if (ex >= -1022 && ex <= 1023)
-        return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(neg) << 63) |
-                                                           (static_cast<unsigned long long>(ex + 1023) << 52) |
-                                                           (mant & ((1ull << 52) - 1))));
-    const double y = scale_pow2(u128_to_double((static_cast<u128>(hi) << 64) | lo), E);
-    return neg ? -y : y;
 }
 
 // C from the residue bytes res[l][j][i] (m n per modulus).  Per element, with S = sum_l c_l w_l
@@ -132,62 +81,13 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
                 else word = src[l * mn];
                 const uint32_t fl = r.frac[l];
 #pragma unroll
-                for (int t = 0; t < V; ++t) {
-                    const uint32_t c = (word >> (8 * t)) & 0xFFu;
-#pragma unroll
-                    for (int q = 0; q < L; ++q) s[t][q] += static_cast<unsigned long long>(c) * r.w[l][q];
-                    qs[t] += c * fl;
-                }
+                for (int t = 0; t < V; ++t) crt_accumulate<L>(s[t], qs[t], (word >> (8 * t)) & 0xFFu, r.w[l], fl);
             }
             double y[V];
 #pragma unroll
             for (int t = 0; t < V; ++t) {
-                // S mod 2^(32 L) in 32-bit words z[0..L-1]
-                uint32_t z[L];
-                unsigned long long carry = 0;
-#pragma unroll
-                for (int q = 0; q < L; ++q) {
-                    const unsigned long long v = s[t][q] + carry;
-                    z[q] = static_cast<uint32_t>(v);
-                    carry = v >> 32;
-                }
-                // Z = S - q P modulo 2^(32 L)
-                const uint32_t qv = (qs[t] + (1u << 18)) >> 19;
-                unsigned long long mc = 0;
-                uint32_t borrow = 0;
-#pragma unroll
-                for (int q = 0; q < L; ++q) {
-                    const unsigned long long pq = static_cast<unsigned long long>(qv) * r.Pw[q] + mc;
-                    mc = pq >> 32;
-                    const uint32_t sub = static_cast<uint32_t>(pq);
-                    const unsigned long long d = static_cast<unsigned long long>(z[q]) - sub - borrow;
-                    z[q] = static_cast<uint32_t>(d);
-                    borrow = static_cast<uint32_t>(d >> 63);
-                }
-                const bool neg = (z[L - 1] >> 31) != 0;
-                if (neg) {  // two's complement magnitude
-                    uint32_t c1 = 1;
-#pragma unroll
-                    for (int q = 0; q < L; ++q) {
-                        const unsigned long long v = static_cast<unsigned long long>(~z[q]) + c1;
-                        z[q] = static_cast<uint32_t>(v);
-                        c1 = static_cast<uint32_t>(v >> 32);
-                    }
-                }
-                // |Z| = hi 2^64 + lo, scaled by 2^(32 (4 - L)) when L = 3
-                unsigned long long hi, lo;
-                int Eadj;
-                if constexpr (L == 4) {
-                    hi = (static_cast<unsigned long long>(z[3]) << 32) | z[2];
-                    lo = (static_cast<unsigned long long>(z[1]) << 32) | z[0];
-                    Eadj = 0;
-                } else {
-                    hi = (static_cast<unsigned long long>(z[2]) << 32) | z[1];
-                    lo = static_cast<unsigned long long>(z[0]) << 32;
-                    Eadj = -32;
-                }
                 const int64_t i = i0 + t;
-                y[t] = (fj || ef[i] != 0) ? qnan : scaled_double(hi, lo, neg, e[i] + Ej + Eadj);
+                y[t] = (fj || ef[i] != 0) ? qnan : crt_value<L>(s[t], qs[t], r.Pw, e[i] + Ej);
                 if (!unit_alpha) y[t] *= alpha;
             }
             double* cp = C + i0 + j * ldc;

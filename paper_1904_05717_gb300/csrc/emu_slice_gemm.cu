@@ -42,6 +42,7 @@
 #include <tuple>
 #include <vector>
 
+#include "crt.cuh"
 #include "internal.h"
 #include "ptx.cuh"
 #include "raster.cuh"
@@ -115,6 +116,16 @@ struct Params {
     // Modular encoding (single problem): `one.S` moduli, the unit of modulus l multiplies residue
     // plane l of A by plane l of B and its epilogue stores (sum mod modp[l]) as a byte.
     uint8_t* res;             // [l][col][row] residues of the product, m n bytes per modulus
+    int group_tiles;          // the unit order: groups of this many tiles, moduli in turn
+    // Fused reconstruction: the epilogue of a tile's last modulus rebuilds C itself once done[tile]
+    // shows the other moduli's residues stored (crt_fused; else a separate reconstruction launch).
+    int crt_fused;
+    int crt_L;                // limbs of the reconstruction arithmetic (3: P < 2^96, else 4)
+    int crt_bits;             // integer width of the operands
+    int* done;                // per tile: moduli whose residues are stored
+    uint32_t crt_w[kCrtMaxModuli][4];
+    uint32_t crt_F[kCrtMaxModuli];
+    uint32_t crt_Pw[4];
     uint32_t modp[kCrtMaxModuli];
     uint32_t modmagic[kCrtMaxModuli];  // floor(2^32 / p) + 1
     uint32_t modoff[kCrtMaxModuli];    // p ceil(2^31 / p): makes any int32 sum a uint32 of equal residue
@@ -124,18 +135,28 @@ struct Params {
 // coordinates.  A single problem uses the member's tile order; a batch walks the
 // concatenated tile list of all problems cyclically.
 template <bool TAIL, bool MOD = false>
-MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int* part, int* lmod = nullptr) {
+MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int* part, int* lmod = nullptr,
+                       int64_t* tile = nullptr) {
     *part = -1;
     if constexpr (MOD) {
-        // modular encoding: the unit is one modulus of one tile, units handed out round-robin in
-        // modulus-major order -- a wave covers one modulus of a block of tiles (the member's
-        // order; A1 visits rows as A2 does) and the last round is the only partial one
+        // modular encoding: the unit is one modulus of one tile, units handed out round-robin over
+        // groups of group_tiles tiles (the member's order; A1 visits rows as A2 does), each group
+        // modulus by modulus.  A wave covers one modulus of a block of tiles (the L2 footprint of a
+        // digit pair), only the last round is partial, and with group_tiles = the grid a full
+        // group keeps every modulus of a tile on one CTA.
         const int64_t tiles = static_cast<int64_t>(p.tiles_m) * p.tiles_n;
+        const int64_t N = p.one.S;
         const int64_t u = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
-        if (u >= tiles * p.one.S) return false;
+        if (u >= tiles * N) return false;
+        const int64_t GT = p.group_tiles;
+        const int64_t g = u / (GT * N);
+        const int64_t first = g * GT;
+        const int64_t gt = tiles - first < GT ? tiles - first : GT;  // tiles of this group
+        const int64_t r = u - g * GT * N;
         *prob = -1;
-        *lmod = static_cast<int>(u / tiles);
-        const int64_t t = u - *lmod * tiles;
+        *lmod = static_cast<int>(r / gt);
+        const int64_t t = first + r % gt;
+        if (tile) *tile = t;
         const int member = p.member == kMemberA1 ? kMemberA2 : p.member;
         return member_tile(member, p.group, t % gridDim.x, gridDim.x, t / gridDim.x, p.tiles_m, p.tiles_n, tm, tn);
     }
@@ -404,8 +425,10 @@ MOMMS_DEV uint32_t residue_of(int32_t x, uint32_t p, uint32_t magic, uint32_t of
 }
 
 // The modular epilogue of modulus l: the thread's int32 sums (CR in `acc`, CT in TMEM at
-// `tsum`) reduced into [0, p) and stored as bytes at res[l][col][row].  The TMEM reads are
-// warp-wide, so every lane takes them before the bounds checks.
+// `tsum`) reduced into [0, p) and stored as bytes at res[l][col][row] (a warp's 32 rows: one
+// 32-byte sector per column; 16-byte strided bytes per element instead made the residue
+// product 30 % slower).  The TMEM reads are warp-wide, so every lane takes them before the
+// bounds checks.
 template <int BN, int CR, int CT>
 MOMMS_DEV void store_residues(const Params& p, int tm, int tn, int l, int third, int rloc, const int32_t (&acc)[CR],
                               uint32_t tsum) {
@@ -414,11 +437,12 @@ MOMMS_DEV void store_residues(const Params& p, int tm, int tn, int l, int third,
     const uint32_t pl = p.modp[l], mg = p.modmagic[l], off = p.modoff[l];
     const bool row_ok = row < p.one.m;
     uint8_t* dst = p.res + static_cast<size_t>(l) * p.one.m * p.one.n + static_cast<size_t>(col0) * p.one.m + row;
+    const size_t cstep = static_cast<size_t>(p.one.m);
     const int ncols = min(BN / 3, p.one.n - col0);
 #pragma unroll
     for (int c = 0; c < CR; ++c) {
         const uint32_t r = residue_of(acc[c], pl, mg, off);
-        if (row_ok && c < ncols) dst[static_cast<size_t>(c) * p.one.m] = static_cast<uint8_t>(r);
+        if (row_ok && c < ncols) dst[c * cstep] = static_cast<uint8_t>(r);
     }
 #pragma unroll
     for (int q = 0; q < CT / 16; ++q) {
@@ -429,9 +453,134 @@ MOMMS_DEV void store_residues(const Params& p, int tm, int tn, int l, int third,
         for (int j = 0; j < 16; ++j) {
             const int c = CR + q * 16 + j;
             const uint32_t r = residue_of(static_cast<int32_t>(t[j]), pl, mg, off);
-            if (row_ok && c < ncols) dst[static_cast<size_t>(c) * p.one.m] = static_cast<uint8_t>(r);
+            if (row_ok && c < ncols) dst[c * cstep] = static_cast<uint8_t>(r);
         }
     }
+}
+
+// The tile's residues of this modulus are stored: once every drain thread has issued its
+// stores, one thread publishes them (fence, then the tile's counter).
+MOMMS_DEV void signal_tile(const Params& p, int64_t tile) {
+    named_bar_sync(1, 32 * EPI_WARPS);
+    if (threadIdx.x == 32 * CTRL_WARPS) {
+        __threadfence();
+        atomicAdd(p.done + tile, 1);
+    }
+}
+
+// Waits (bounded) until `need` moduli of the tile are published; false if the wait gave up.
+MOMMS_DEV bool wait_tile(const Params& p, int64_t tile, int need, volatile int* abort_flag, volatile int* wait_ok) {
+    if (threadIdx.x == 32 * CTRL_WARPS) {
+        int ok = 1;
+        const volatile int* cnt = p.done + tile;
+        if (*cnt < need) {
+            const uint64_t t0 = globaltimer_ns();
+            for (uint32_t it = 1; *cnt < need; ++it) {
+                if ((it & 63u) == 0) {
+                    if (*abort_flag || globaltimer_ns() - t0 > kWaitTimeoutNs) {
+                        *abort_flag = 1;
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+        }
+        __threadfence();
+        *wait_ok = ok;
+    }
+    named_bar_sync(1, 32 * EPI_WARPS);
+    return *wait_ok != 0;
+}
+
+// L2 prefetch of the residues a final unit will read (other moduli of the warp's 32 rows and the
+// thread's columns), issued before the unit's products so that they arrive under them: one
+// prefetch per 32-byte sector, spread over the lanes.
+template <int BN>
+MOMMS_DEV void prefetch_residues(const Params& p, int tm, int tn, int last, int third, int quad, int lane) {
+    constexpr int CW = BN / 3;
+    const int row0 = tm * BM + quad * 32;
+    const int col0 = tn * BN + third * CW;
+    if (row0 >= p.one.m) return;
+    const int ncols = min(CW, p.one.n - col0);
+    const size_t mn = static_cast<size_t>(p.one.m) * p.one.n;
+    for (int idx = lane; idx < last * ncols; idx += 32) {
+        const int l = idx / ncols, c = idx - l * ncols;
+        const uint8_t* a = p.res + l * mn + static_cast<size_t>(col0 + c) * p.one.m + row0;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+}
+
+// Two elements of the fused reconstruction (columns col and col + 1 of one row, the second only
+// when `two`): the other moduli's residues from res (all loads issued first), this modulus's
+// `own`, then C := alpha y + beta C as the separate reconstruction kernel computes it (crt.cuh).
+template <int L>
+MOMMS_DEV void crt_pair(const Params& p, int row, int col, bool two, uint32_t own0, uint32_t own1, int last, int Erow,
+                        bool flag_row, const int* colexp, const uint8_t* colflag) {
+    const size_t mn = static_cast<size_t>(p.one.m) * p.one.n;
+    const uint8_t* src = p.res + static_cast<size_t>(col) * p.one.m + row;
+    uint32_t r0[kCrtMaxModuli], r1[kCrtMaxModuli];
+#pragma unroll
+    for (int l = 0; l < kCrtMaxModuli; ++l) {
+        r0[l] = l < last ? __ldcg(src + l * mn) : 0u;
+        r1[l] = (two && l < last) ? __ldcg(src + l * mn + p.one.m) : 0u;
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        if (e == 1 && !two) break;
+        unsigned long long s[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) s[q] = 0;
+        uint32_t qs = 0;
+#pragma unroll
+        for (int l = 0; l < kCrtMaxModuli; ++l)
+            if (l < last) crt_accumulate<L>(s, qs, e == 0 ? r0[l] : r1[l], p.crt_w[l], p.crt_F[l]);
+        crt_accumulate<L>(s, qs, e == 0 ? own0 : own1, p.crt_w[last], p.crt_F[last]);
+        double y = (flag_row || colflag[e] != 0) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                 : crt_value<L>(s, qs, p.crt_Pw, Erow + colexp[e]);
+        if (p.one.alpha != 1.0) y *= p.one.alpha;
+        double* cp = p.one.C + row + static_cast<int64_t>(col + e) * p.one.ldc;
+        *cp = p.one.beta_c == 0.0 ? y : fma(p.one.beta_c, *cp, y);
+    }
+}
+
+// The last modulus of a tile with the reconstruction fused: this modulus's residues of the
+// thread's columns, then each element of C.
+template <int BN, int CR, int CT, int L>
+MOMMS_DEV void crt_final(const Params& p, int tm, int tn, int last, int third, int rloc, const int32_t (&acc)[CR],
+                         uint32_t tsum, const int* colexp, const uint8_t* colflag) {
+    constexpr int CW = BN / 3;
+    const int row = tm * BM + rloc;
+    const int col0 = tn * BN + third * CW;
+    const uint32_t pl = p.modp[last], mg = p.modmagic[last], off = p.modoff[last];
+    const bool row_ok = row < p.one.m;
+    const int ncols = min(CW, p.one.n - col0);
+    const int Erow = row_ok ? p.one.e[row] : 0;
+    const bool frow = row_ok ? p.one.ef[row] != 0 : false;
+    // this modulus's residues of the thread's columns, packed four to a word (static indexing
+    // keeps `acc` in registers for the drain of every unit)
+    uint32_t own[CW / 4];
+#pragma unroll
+    for (int c = 0; c < CR; c += 4)
+        own[c / 4] = residue_of(acc[c], pl, mg, off) | (residue_of(acc[c + 1], pl, mg, off) << 8) |
+                     (residue_of(acc[c + 2], pl, mg, off) << 16) | (residue_of(acc[c + 3], pl, mg, off) << 24);
+#pragma unroll
+    for (int q = 0; q < CT / 16; ++q) {
+        uint32_t t[16];
+        tmem_ld_32x32b_x16(tsum + q * 16, t);
+        tmem_ld_wait(t);
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+            own[(CR + q * 16 + j) / 4] = residue_of(static_cast<int32_t>(t[j]), pl, mg, off) |
+                                         (residue_of(static_cast<int32_t>(t[j + 1]), pl, mg, off) << 8) |
+                                         (residue_of(static_cast<int32_t>(t[j + 2]), pl, mg, off) << 16) |
+                                         (residue_of(static_cast<int32_t>(t[j + 3]), pl, mg, off) << 24);
+    }
+    if (!row_ok) return;
+    for (int c = 0; c < ncols; c += 2)
+        crt_pair<L>(p, row, col0 + c, c + 1 < ncols, (own[c >> 2] >> (8 * (c & 3))) & 0xFFu,
+                    (own[(c + 1) >> 2] >> (8 * ((c + 1) & 3))) & 0xFFu, last, Erow, frow, colexp + third * CW + c,
+                    colflag + third * CW + c);
 }
 
 // Stages the column exponents (minus 2 beta) and non-finite flags of tile column tn in shared
@@ -616,6 +765,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t* drain = bars + 2 * STAGES + 4;      // 1
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* wait_ok = reinterpret_cast<volatile int*>(tmem_slot + 2);  // fused reconstruction
     int* colexp = reinterpret_cast<int*>(smem + STAGES * STAGE + 256);   // BN column exponents
     uint8_t* colflag = reinterpret_cast<uint8_t*>(colexp + BN);          // BN column flags
 
@@ -780,12 +930,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool ok = true;
             for (int it = 0; ok; ++it) {
                 int tm, tn, prob, part, lm = 0;
-                if (!tile_of<false, MOD>(p, it, &prob, &tm, &tn, &part, &lm)) break;
+                int64_t tile = 0;
+                if (!tile_of<false, MOD>(p, it, &prob, &tm, &tn, &part, &lm, &tile)) break;
                 const TileInts pr = tile_ints(p, prob, -1);
                 const double rb = pow2_normal(-pr.beta);
                 int gj = 0;           // position of the current diagonal inside its int64 group
                 bool rfirst = true;   // no FP64 partial R yet for this tile
+                const bool final_unit = MOD && p.crt_fused && lm == pr.S - 1;
                 if constexpr (!MOD) stage_columns<BN>(p, prob, tn, pr.beta, colexp, colflag);
+                else if (final_unit) {
+                    stage_columns<BN>(p, prob, tn, p.crt_bits, colexp, colflag);
+                    prefetch_residues<BN>(p, tm, tn, lm, third, quad, lane);
+                }
                 for (int d = MOD ? 2 : pr.S + 1; d >= 2; --d) {
                     int32_t acc[CR];
                     if (!drain_diagonal<CR, CT>((MOD ? 1 : d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty,
@@ -794,9 +950,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                         ok = false;
                         break;
                     }
-                    if constexpr (MOD)
-                        store_residues<BN, CR, CT>(p, tm, tn, lm, third, rloc, acc, tsum);
-                    else
+                    if constexpr (MOD) {
+                        if (!final_unit) {
+                            store_residues<BN, CR, CT>(p, tm, tn, lm, third, rloc, acc, tsum);
+                            if (p.crt_fused) signal_tile(p, tile);
+                        } else if (wait_tile(p, tile, pr.S - 1, abort_flag, wait_ok)) {
+                            if (p.crt_L == 3)
+                                crt_final<BN, CR, CT, 3>(p, tm, tn, lm, third, rloc, acc, tsum, colexp, colflag);
+                            else
+                                crt_final<BN, CR, CT, 4>(p, tm, tn, lm, third, rloc, acc, tsum, colexp, colflag);
+                        } else {
+                            ok = false;
+                            break;
+                        }
+                    } else
                         recombine_diagonal<BN, CR, CT>(p, prob, tm, tn, d, pr, Q, R, keep, tsum, rb, third, rloc,
                                                        colexp, colflag, qnan, acc, gj, rfirst);
                 }
@@ -964,6 +1131,24 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         p.status = a.status;
         if (mod) {
             p.res = a.res;
+            // Separate reconstruction: one group, modulus-major over all tiles (consecutive waves of
+            // the same modulus reuse operand panels in L2).  Fused: groups of four waves' tiles keep a
+            // tile's moduli on one CTA and spread the last-modulus epilogues over the launch, while
+            // four consecutive waves still share a modulus (groups of one wave's tiles lost that reuse:
+            // 8.3 -> 10.9 ms at 8192^3)
+            p.group_tiles = a.crt_fuse ? static_cast<int>(std::min<int64_t>(tiles, 4 * ctas)) : static_cast<int>(tiles);
+            if (a.crt_fuse) {
+                if (a.done == nullptr || a.crt_fuse->N != a.crt->N) return cudaErrorInvalidValue;
+                p.crt_fused = 1;
+                p.done = a.done;
+                p.crt_bits = a.crt_fuse->bits;
+                p.crt_L = a.crt_fuse->Pw[3] == 0 ? 3 : 4;
+                for (int l = 0; l < a.crt->N; ++l) {
+                    for (int q = 0; q < 4; ++q) p.crt_w[l][q] = a.crt_fuse->w[l][q];
+                    p.crt_F[l] = a.crt_fuse->frac[l];
+                }
+                for (int q = 0; q < 4; ++q) p.crt_Pw[q] = a.crt_fuse->Pw[q];
+            }
             for (int l = 0; l < a.crt->N; ++l) {
                 const uint32_t pl = a.crt->p[l];
                 p.modp[l] = pl;

@@ -123,6 +123,8 @@ struct EmuGemmArgs {
     int* used_launches;  // optional out: kernels launched (a tail launch per pass when split)
     const CrtConsts* crt;  // modular encoding: S = N moduli, the epilogue writes residues to `res`
     uint8_t* res;          // [N][n][m] residues of the product (modular encoding only)
+    const CrtRecon* crt_fuse;  // non-null: the last modulus of each tile rebuilds C itself
+    int* done;             // fused: one zeroed counter per tile (device)
 };
 constexpr int kEmuBM = 128, kEmuBK = 64, kEmuBNMax = 192;
 

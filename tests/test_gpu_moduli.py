@@ -52,10 +52,11 @@ def test_residue_split_bitwise(which, op, bits, k):
     assert not np.any(got[:, rows:, :]) and not np.any(got[:, :, inner:])
 
 
-def modular(A, B, C0, alpha, beta, S=0, opa=0, opb=0, scheme=M.SCHEME_MODULI, tile_n=0, ctas=0):
+def modular(A, B, C0, alpha, beta, S=0, opa=0, opb=0, scheme=M.SCHEME_MODULI, tile_n=0, ctas=0, fusion=0):
     h = M.Handle(mode=M.MODE_EMULATED, slices=S, scheme=scheme)
     h.set_tile_n(tile_n)
     h.set_max_ctas(ctas)
+    h.set_crt_fusion(fusion)
     dA = M.DeviceMatrix.from_numpy(A)
     dB = M.DeviceMatrix.from_numpy(B)
     dC = M.DeviceMatrix.from_numpy(C0)
@@ -68,13 +69,16 @@ def modular(A, B, C0, alpha, beta, S=0, opa=0, opb=0, scheme=M.SCHEME_MODULI, ti
 
 
 @pytest.mark.parametrize("S,alpha,beta", [(6, 1.0, 1.0), (5, -0.75, 2.5), (3, 1.5, 0.0)])
-def test_modular_product_bitwise_vs_oracle(S, alpha, beta):
-    # ragged in every dimension: 2 x 2 tiles of 128 x 192 with partial edges, 3 k slabs
+@pytest.mark.parametrize("fusion", [1, 2])
+def test_modular_product_bitwise_vs_oracle(S, alpha, beta, fusion):
+    # ragged in every dimension: 2 x 2 tiles of 128 x 192 with partial edges, 3 k slabs; the
+    # reconstruction as its own launch and fused into the last modulus's epilogue
     m, n, k = 150, 200, 150
     A = syn.matrix("phi", m, k, 311, phi=1.0)
     B = syn.matrix("phi", k, n, 312, phi=1.0)
     C0 = syn.matrix("uniform", m, n, 313)
-    C, rep = modular(A, B, C0, alpha, beta, S)
+    C, rep = modular(A, B, C0, alpha, beta, S, fusion=fusion)
+    assert rep["crt_fused"] == (fusion == 2)
     assert rep["moduli"] == len(M.momms_crt_moduli(7 * S, k)) and rep["operand_bits"] == 7 * S
     Co, _ = oracle.modular_dgemm(A, B, 7 * S, C0.copy(order="F"), alpha, beta)
     assert np.array_equal(C, Co)
@@ -293,3 +297,21 @@ def test_residue_products_exact_at_the_chunk_edge():
     want = np.stack([np.mod(Z.T, p) for p in mods])                      # [l][j][i]
     assert int(st.item()) == 0
     assert np.array_equal(res.cpu().numpy().astype(np.int64), want)
+
+
+@pytest.mark.parametrize("m,n,k", [(2000, 2000, 2100), (300, 1000, 2048), (1030, 770, 4096)])
+def test_fused_reconstruction_bitwise_equal_to_separate(m, n, k):
+    # fused: groups of four waves' tiles keep a tile's moduli on one CTA, the last, partial group
+    # spreads them over several CTAs (published through the tile counters); tiles above and below
+    # the grid size
+    A = syn.matrix("uniform", m, k, 401)
+    B = syn.matrix("normal", k, n, 402)
+    C0 = syn.matrix("uniform", m, n, 403)
+    # data-driven width (S = 0): the bound holds; both runs take the same width from the same data
+    Cs, rs = modular(A, B, C0, -1.25, 0.5, 0, fusion=0)
+    Cf, rf = modular(A, B, C0, -1.25, 0.5, 0, fusion=2)
+    assert rs["moduli"] > 0 and rs["crt_fused"] == 0
+    assert rf["crt_fused"] == 1 and rf["launches"] == rs["launches"] - 1
+    assert np.array_equal(Cf, Cs)
+    Cref, N = reference(A, B, C0, -1.25, 0.5)
+    assert max_ratio(Cf, Cref, k, 1.25, 0.5, N, C0) <= 1.0
