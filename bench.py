@@ -646,7 +646,7 @@ def main():
             "dtype_detail": (("FP64-accurate; emulated path, modular encoding: operands truncated to "
                               f"{op_bits}-bit integers, residues modulo {n_mod} coprime moduli <= 255 as fp16 on "
                               "tcgen05 kind::f16, exact FP32 accumulation drained to int32, Chinese remainder "
-                              "reconstruction in 128-bit integers, one FP64 rounding")
+                              "reconstruction in integer arithmetic (approximate CRT), one FP64 rounding")
                              if (emulated and n_mod) else
                              (f"FP64-accurate; emulated path: {S} slices of {bb}-bit integer digits in fp16 on "
                               f"tcgen05 kind::f16, exact FP32 accumulation drained to int32, int64/FP64 recombination")

@@ -109,6 +109,22 @@ def emulated_dram_bytes(member: int, m: int, n: int, k: int, S: int, ctas: int =
             "mean_cols_per_round": b_cols / max(len(w), 1) / bn}
 
 
+def modular_dram_bytes(member: int, m: int, n: int, k: int, N: int, ctas: int = 152, bm: int = 128,
+                       bn: int = 192, group: int = 0):
+    """HBM bytes of one residue-product launch of the modular encoding: the units run modulus by
+    modulus through the member's tile order, so per modulus and round the tile rows of A's residue
+    plane and tile columns of B's plane in flight are read once (as a digit pair of the slice
+    kernel); the launch writes the N residue bytes of every element of C and does not touch C."""
+    tiles_m, tiles_n = cdiv(m, bm), cdiv(n, bn)
+    k_pad = cdiv(k, 64) * 64
+    w = waves(member, tiles_m, tiles_n, min(ctas, tiles_m * tiles_n), group)
+    a_rows = sum(min(r * bm, m) for r, _ in w)
+    b_cols = sum(min(c * bn, n) for _, c in w)
+    planes = N * (a_rows + b_cols) * k_pad * 2
+    residues = N * m * n
+    return {"planes": planes, "residues": residues, "total": planes + residues, "rounds": len(w)}
+
+
 def emulated_l2_to_sm_bytes(m: int, n: int, k: int, S: int, bm: int = 128, bn: int = 192):
     """L2 -> SM bytes: every tile streams its A (bm rows) and B (bn rows) digit panels per pair."""
     tiles_m, tiles_n = cdiv(m, bm), cdiv(n, bn)

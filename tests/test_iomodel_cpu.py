@@ -68,3 +68,13 @@ def test_wave_model_orders_members_as_the_paper_predicts():
     sizes = {name: I.emulated_dram_bytes(mem, 8192, 8192, 8192, 6)["total"] for name, mem in I.MEMBERS.items()}
     assert sizes["C2"] < sizes["A2"] < sizes["A1"]
     assert sizes["C2"] < sizes["B2"] < sizes["A1"]
+
+
+def test_modular_model_is_the_slice_model_with_moduli_for_pairs():
+    # the residue product streams one plane pair per modulus as the slice kernel streams one per
+    # digit pair: with N = S(S+1)/2 the operand bytes agree; it writes N bytes per element of C
+    m, n, k = 4096, 4096, 4096
+    for member in (1, 2, 3, 4):
+        s = I.emulated_dram_bytes(member, m, n, k, S=4)
+        r = I.modular_dram_bytes(member, m, n, k, N=10)
+        assert r["planes"] == s["digits"] and r["residues"] == 10 * m * n
