@@ -76,12 +76,20 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
             }
             const uint8_t* src = res + j * m + i0;
             for (int l = 0; l < r.N; ++l) {
-                uint32_t word;
-                if constexpr (V == 4) word = __ldcs(reinterpret_cast<const unsigned int*>(src + l * mn));
-                else word = src[l * mn];
+                uint32_t word[V > 4 ? 2 : 1];
+                if constexpr (V == 8) {
+                    const uint2 w2 = __ldcs(reinterpret_cast<const uint2*>(src + l * mn));
+                    word[0] = w2.x;
+                    word[1] = w2.y;
+                } else if constexpr (V == 4) {
+                    word[0] = __ldcs(reinterpret_cast<const unsigned int*>(src + l * mn));
+                } else {
+                    word[0] = src[l * mn];
+                }
                 const uint32_t fl = r.frac[l];
 #pragma unroll
-                for (int t = 0; t < V; ++t) crt_accumulate<L>(s[t], qs[t], (word >> (8 * t)) & 0xFFu, r.w[l], fl);
+                for (int t = 0; t < V; ++t)
+                    crt_accumulate<L>(s[t], qs[t], (word[t >> 2] >> (8 * (t & 3))) & 0xFFu, r.w[l], fl);
             }
             double y[V];
 #pragma unroll
@@ -93,18 +101,18 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
             double* cp = C + i0 + j * ldc;
             if constexpr (CV) {
                 double2* c2 = reinterpret_cast<double2*>(cp);
-                double2 a, b;
-                if (beta_zero) {
-                    a = make_double2(y[0], y[1]);
-                    b = make_double2(y[2], y[3]);
-                } else {
-                    a = __ldcs(c2);
-                    b = __ldcs(c2 + 1);
-                    a.x = fma(beta, a.x, y[0]); a.y = fma(beta, a.y, y[1]);
-                    b.x = fma(beta, b.x, y[2]); b.y = fma(beta, b.y, y[3]);
+#pragma unroll
+                for (int h2 = 0; h2 < V / 2; ++h2) {
+                    double2 a;
+                    if (beta_zero) {
+                        a = make_double2(y[2 * h2], y[2 * h2 + 1]);
+                    } else {
+                        a = __ldcs(c2 + h2);
+                        a.x = fma(beta, a.x, y[2 * h2]);
+                        a.y = fma(beta, a.y, y[2 * h2 + 1]);
+                    }
+                    __stcs(c2 + h2, a);
                 }
-                __stcs(c2, a);
-                __stcs(c2 + 1, b);
             } else {
 #pragma unroll
                 for (int t = 0; t < V; ++t) cp[t] = beta_zero ? y[t] : fma(beta, cp[t], y[t]);
@@ -162,6 +170,8 @@ cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, con
                                    const uint8_t* ef, const int32_t* f, const uint8_t* ff, double alpha,
                                    double beta, double* C, int64_t ldc, cudaStream_t stream) {
     if (m <= 0 || n <= 0) return cudaSuccess;
+    // four rows per thread: eight (96-104 registers, a quarter of the warps resident) measured
+    // 300 against 186 us at 4096^2
     const bool vec = m % 4 == 0 && reinterpret_cast<uintptr_t>(res) % 4 == 0;
     const bool cvec = vec && ldc % 2 == 0 && reinterpret_cast<uintptr_t>(C) % 16 == 0;
     const bool three = r.Pw[3] == 0;  // P < 2^96: |Z| < 2^95, arithmetic modulo 2^96

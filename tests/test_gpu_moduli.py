@@ -332,3 +332,32 @@ def test_tile_pairs_bitwise_identical(m, n, k, tile_n):
     assert np.array_equal(C1, C2)
     Cref, N = reference(A, B, C0, 1.0, 1.0)
     assert max_ratio(C2, Cref, k, 1.0, 1.0, N, C0) <= 1.0
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (3, 5, 70), (129, 1, 300), (1, 300, 64)])
+def test_modular_tiny_and_single_vector_shapes_bitwise(m, n, k):
+    # one element, ragged rows below the 4-row vector path of the reconstruction, one column
+    A = syn.matrix("phi", m, k, 421, phi=1.0)
+    B = syn.matrix("phi", k, n, 422, phi=1.0)
+    C0 = syn.matrix("uniform", m, n, 423)
+    C, rep = modular(A, B, C0, 2.0, -1.0, 5)
+    assert rep["moduli"] > 0
+    Co, _ = oracle.modular_dgemm(A, B, 35, C0.copy(order="F"), 2.0, -1.0)
+    assert np.array_equal(C, Co)
+
+
+def test_modular_odd_leading_dimension_bitwise():
+    # ldc odd: the reconstruction cannot pair C elements into 16-byte words
+    m, n, k = 64, 50, 200
+    A = syn.matrix("uniform", m, k, 431)
+    B = syn.matrix("uniform", k, n, 432)
+    C0 = syn.matrix("uniform", m, n, 433)
+    h = M.Handle(mode=M.MODE_EMULATED, slices=6, scheme=M.SCHEME_MODULI)
+    dA, dB = M.DeviceMatrix.from_numpy(A), M.DeviceMatrix.from_numpy(B)
+    dC = M.DeviceMatrix.from_numpy(C0, ld=m + 1)
+    M.gemm(dA, dB, dC, 1.0, 1.0, handle=h)
+    assert h.device_status() == M.MOMMS_OK and h.report()["moduli"] > 0
+    h.close()
+    Co, _ = oracle.modular_dgemm(A, B, 42, C0.copy(order="F"), 1.0, 1.0)
+    assert np.array_equal(dC.to_numpy(), Co)
+    assert np.all(np.isnan(dC.padding_numpy()))          # the row of padding is never written
