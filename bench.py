@@ -501,7 +501,7 @@ def main():
                                                  int(rep["member"]), res.data_ptr(), scratch.data_ptr(), nbytes,
                                                  st.data_ptr(), stream), "residue gemm")
             products = n_mod
-            kernel = (f"momms::emu::slice_gemm_kernel<{int(rep['tile_n'])}, 0, 1> (tcgen05 kind::f16; modular "
+            kernel = (f"momms::emu::slice_gemm_kernel<{int(rep['tile_n'])}, 0, 1, 0> (tcgen05 kind::f16; modular "
                       f"encoding: one residue product per modulus)")
             capture = NCU_RESIDUE_CAPTURE
         else:
@@ -519,7 +519,7 @@ def main():
                                                Cs.ptr, Cs.ld, int(rep["member"]), scratch.data_ptr(), nbytes,
                                                st.data_ptr(), stream), "slice gemm")
             products = S * (S + 1) // 2
-            kernel = f"momms::emu::slice_gemm_kernel<{int(rep['tile_n'])}, 0|1> (tcgen05 kind::f16; main + tail launch)"
+            kernel = f"momms::emu::slice_gemm_kernel<{int(rep['tile_n'])}, 0|1, 0, 0> (tcgen05 kind::f16; main + tail launch)"
             capture = NCU_SLICE_CAPTURE
         evs = []
         reps = max(3, min(args.steps, 10))
