@@ -82,8 +82,11 @@ def _operands(torch, m, n, k, seed):
 DEFAULT_POINTS = ((152, 0), (114, 38), (76, 0), (76, 38), (76, 76))
 
 
+SCHEMES = {"auto": M.SCHEME_AUTO, "slices": M.SCHEME_SLICES, "moduli": M.SCHEME_MODULI}
+
+
 def run(size=8192, members=("C2", "A2", "B2", "A1"), points=DEFAULT_POINTS, reps=3, native_size=4096, slices=6,
-        engines=("emulated", "native"), check_results=False):
+        engines=("emulated", "native"), check_results=False, scheme="auto"):
     """Times every (engine, point, member); a point is (product CTAs, background SMs).  The
     native kernel keeps its default grid (one CTA per tile) at every point.  Returns one dict
     per measurement.
@@ -112,7 +115,7 @@ def run(size=8192, members=("C2", "A2", "B2", "A1"), points=DEFAULT_POINTS, reps
             seen.add(key)
             for mem in members:
                 h = M.Handle(mode=M.MODE_EMULATED if emulated else M.MODE_NATIVE, member=MEMBER_IDS[mem],
-                             slices=slices if emulated else 0)
+                             slices=slices if emulated else 0, scheme=SCHEMES[scheme])
                 h.set_max_ctas(ctas if emulated else 0)
 
                 def call():
@@ -127,7 +130,8 @@ def run(size=8192, members=("C2", "A2", "B2", "A1"), points=DEFAULT_POINTS, reps
                 alone_ms = e0.elapsed_time(e1)
                 rep = h.report()
                 point = {"engine": engine, "size": n, "member": mem, "background_sms": H,
-                         "product_ctas": int(rep["ctas"]), "group": int(rep["group"]), "slices": int(rep["slices"])}
+                         "product_ctas": int(rep["ctas"]), "group": int(rep["group"]), "slices": int(rep["slices"]),
+                         "moduli": int(rep["moduli"])}
                 if H:
                     pass_ms, alone_gbs = bg.calibrate(H)
                     # enough passes to outlast the timed products even if they slow down 3x
@@ -146,10 +150,16 @@ def run(size=8192, members=("C2", "A2", "B2", "A1"), points=DEFAULT_POINTS, reps
                 if H:
                     # the background started before the first product and ended after the last
                     point["background_covered"] = b0.elapsed_time(e0) >= 0.0 and e1.elapsed_time(b1) >= 0.0
-                if emulated:
+                if emulated and rep["moduli"]:
+                    # modular encoding: the residue product's operand planes and residue bytes (its
+                    # units visit the rows of the A1 member in A2's order)
+                    mod = iomodel.modular_dram_bytes(MEMBER_IDS["A2" if mem == "A1" else mem], n, n, n,
+                                                     int(rep["moduli"]), ctas=int(rep["ctas"]), group=int(rep["group"]))
+                elif emulated:
                     mod = iomodel.emulated_dram_bytes(MEMBER_IDS[mem], n, n, n, int(rep["slices"]),
                                                       ctas=int(rep["ctas"]), group=int(rep["group"]),
                                                       beta_nonzero=False)
+                if emulated:
                     point["model_slice_dram_gb"] = mod["total"] / 1e9
                     point["model_gbs_at_measured_time"] = mod["total"] / (ms * 1e-3) / 1e9
                 if check_results:
@@ -164,7 +174,7 @@ def table(rows):
     c2 = {(r["engine"], r["product_ctas"] if r["engine"] == "emulated" else 0, r["background_sms"]): r["ms"]
           for r in rows if r["member"] == "C2"}
     out = ["| engine | n | product CTAs | background SMs | member | group | ms | TFLOP/s | ms / C2 | "
-           "model slice HBM GB | model GB/s at that time | background alone GB/s |",
+           "model product HBM GB | model GB/s at that time | background alone GB/s |",
            "|---|---|---|---|---|---|---|---|---|---|---|---|"]
     for r in rows:
         b = c2.get((r["engine"], r["product_ctas"] if r["engine"] == "emulated" else 0, r["background_sms"]))
@@ -186,11 +196,12 @@ def main(argv=None):
     p.add_argument("--members", default="C2,A2,B2,A1")
     p.add_argument("--engines", default="emulated,native")
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--scheme", default="auto", choices=sorted(SCHEMES))
     p.add_argument("--json", default=None)
     a = p.parse_args(argv)
     points = tuple(tuple(int(v) for v in pt.split(":")) for pt in a.points.split(","))
     rows = run(size=a.size, members=tuple(a.members.split(",")), points=points, reps=a.reps,
-               native_size=a.native_size, engines=tuple(a.engines.split(",")))
+               native_size=a.native_size, engines=tuple(a.engines.split(",")), scheme=a.scheme)
     print(table(rows))
     if a.json:
         with open(a.json, "w") as f:
