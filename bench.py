@@ -405,7 +405,7 @@ def run_side_workload(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload, "mode": args.mode,
                        "path": "emulated" if rep["mode"] == M.MODE_EMULATED else "native",
-                       "slices_last_call": int(rep["slices"])},
+                       "slices_last_call": int(rep["slices"]), "moduli_last_call": int(rep["moduli"])},
             "roofline": None, "e2e": None, "gpu_launches": int(rep["launches"]) * args.steps,
             "clocks": clk.summary(), "device_status": h.device_status(stream), "cpu_baseline": None}
     print(json.dumps(line), flush=True)

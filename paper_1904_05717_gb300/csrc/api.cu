@@ -291,10 +291,18 @@ int join_aux(momms_handle_t h, cudaStream_t s) {
     return MOMMS_OK;
 }
 
+// tri = 1 / 2: the symmetric rank-k update C := alpha op(A) op(A)^T + beta C on the lower / upper
+// triangle (m = n, B = A with opb the other transposition of A): one scale and residue split
+// serve both operands, the residue products visit the tiles that meet the triangle and the
+// reconstruction writes only the triangle.  When the slice encoding is chosen instead it returns
+// kSlicesChosen before the products (only the scale, the spread and a guessed split have run).
+constexpr int kSlicesChosen = 1;
+
 int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
-                 int64_t ldc, int member, int S, cudaStream_t s) {
+                 int64_t ldc, int member, int S, cudaStream_t s, int tri = 0) {
     const int bb = h->digit_bits;
+    if (tri && (m != n || A != B || opa == opb)) return MOMMS_ERR_UNSUPPORTED;
     if (S > MOMMS_MAX_SLICES) return MOMMS_ERR_UNSUPPORTED;
     const int S_alloc = S > 0 ? S : kAutoSliceMax;
     const int N_alloc = moduli_reserved(h->scheme, S, k);
@@ -306,12 +314,13 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     char* w = static_cast<char*>(ws);
     int32_t* e = reinterpret_cast<int32_t*>(w + L.off_e);
     uint8_t* ef = reinterpret_cast<uint8_t*>(w + L.off_ef);
-    int32_t* f = reinterpret_cast<int32_t*>(w + L.off_f);
-    uint8_t* ff = reinterpret_cast<uint8_t*>(w + L.off_ff);
     float* l1a = reinterpret_cast<float*>(w + L.off_l1a);
-    float* l1b = reinterpret_cast<float*>(w + L.off_l1b);
     void* Ad = w + L.off_Ad;
-    void* Bd = w + L.off_Bd;
+    // a triangle's second operand is the first one transposed: the same exponents, flags and planes
+    int32_t* f = tri ? e : reinterpret_cast<int32_t*>(w + L.off_f);
+    uint8_t* ff = tri ? ef : reinterpret_cast<uint8_t*>(w + L.off_ff);
+    float* l1b = tri ? l1a : reinterpret_cast<float*>(w + L.off_l1b);
+    void* Bd = tri ? Ad : w + L.off_Bd;
     void* scratch = w + L.off_scratch;
     uint8_t* res = reinterpret_cast<uint8_t*>(w + L.off_res);
     int64_t launches = 0;
@@ -332,9 +341,12 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
         return MOMMS_ERR_CUDA;
     ce = momms::launch_emu_scale(0, opa, m, k, A, lda, e, ef, need_stats ? l1a : nullptr, s);
     if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-    ce = momms::launch_emu_scale(1, opb, n, k, B, ldb, f, ff, need_stats ? l1b : nullptr, sb);
-    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-    launches += momms::emu_scale_kernel_count(0, opa) + momms::emu_scale_kernel_count(1, opb);
+    if (!tri) {
+        ce = momms::launch_emu_scale(1, opb, n, k, B, ldb, f, ff, need_stats ? l1b : nullptr, sb);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        launches += momms::emu_scale_kernel_count(1, opb);
+    }
+    launches += momms::emu_scale_kernel_count(0, opa);
     double est = 0.0;
     int split_done = 0;  // slices already written
     if (S == 0) {
@@ -342,13 +354,14 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
         // readback is in flight the digits are already split for a guessed S (the last call's):
         // a slice's digits do not depend on S, so only missing slices are added afterwards.
         if (momms::launch_emu_spread(m, k, e, ef, l1a, h->spread_dev, s) != cudaSuccess) return MOMMS_ERR_CUDA;
-        if (momms::launch_emu_spread(n, k, f, ff, l1b, h->spread_dev + 1, sb) != cudaSuccess) return MOMMS_ERR_CUDA;
+        if (!tri && momms::launch_emu_spread(n, k, f, ff, l1b, h->spread_dev + 1, sb) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
         rc = join_aux(h, s);  // the readback needs both spreads
         if (rc) return rc;
         if (cudaMemcpyAsync(h->spread_host, h->spread_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return MOMMS_ERR_CUDA;
         if (!h->spread_ready || cudaEventRecord(h->spread_ready, s) != cudaSuccess) return MOMMS_ERR_CUDA;
-        launches += 2;
+        launches += tri ? 1 : 2;
         const int guess = std::min(std::max(h->last_auto_slices, 1), S_alloc);
         momms::CrtConsts gc;
         momms::CrtRecon gr;
@@ -359,17 +372,17 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
             // residues depend on the operand width: they serve only if the readback confirms S
             ce = momms::launch_emu_residues(0, opa, m, k, A, lda, e, ef, gc, Ad, L.m_pad, L.k_pad, s);
             if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-            ce = momms::launch_emu_residues(1, opb, n, k, B, ldb, f, ff, gc, Bd, L.n_pad, L.k_pad, sb);
-        } else {
+            if (!tri) ce = momms::launch_emu_residues(1, opb, n, k, B, ldb, f, ff, gc, Bd, L.n_pad, L.k_pad, sb);
+        } else if (!tri) {
             ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, guess, bb, Ad, L.m_pad, L.k_pad, s);
             if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
             ce = momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, guess, bb, Bd, L.n_pad, L.k_pad, sb);
         }
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-        launches += 2;
-        split_done = guess_mod ? 0 : guess;
+        if (guess_mod || !tri) launches += tri ? 1 : 2;
+        split_done = guess_mod || tri ? 0 : guess;
         if (cudaEventSynchronize(h->spread_ready) != cudaSuccess) return MOMMS_ERR_CUDA;
-        const double sa = h->spread_host[0] / 16.0, sbs = h->spread_host[1] / 16.0;
+        const double sa = h->spread_host[0] / 16.0, sbs = tri ? sa : h->spread_host[1] / 16.0;
         double bits = 0.0;
         S = slices_from_spread(sa, sbs, k, bb, &bits);
         est = 0.1 * std::exp2(bits - static_cast<double>(bb) * S);  // the rule keeps a 10x margin
@@ -384,12 +397,19 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     } else {
         mod = use_moduli(h->scheme, mbits, S, bb, k, &cc, &cr) && cc.N <= N_alloc;
     }
+    if (tri && !mod) {
+        // the slice encoding's triangle is the batched slice-product path of the caller
+        rc = join_aux(h, s);
+        return rc ? rc : kSlicesChosen;
+    }
     if (mod && !res_ready) {
         ce = momms::launch_emu_residues(0, opa, m, k, A, lda, e, ef, cc, Ad, L.m_pad, L.k_pad, s);
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-        ce = momms::launch_emu_residues(1, opb, n, k, B, ldb, f, ff, cc, Bd, L.n_pad, L.k_pad, sb);
-        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-        launches += 2;
+        if (!tri) {
+            ce = momms::launch_emu_residues(1, opb, n, k, B, ldb, f, ff, cc, Bd, L.n_pad, L.k_pad, sb);
+            if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        }
+        launches += tri ? 1 : 2;
     } else if (!mod && S > split_done) {
         ce = momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, S, bb, Ad, L.m_pad, L.k_pad, s, split_done);
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
@@ -413,10 +433,11 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     // on request: measured slower than the separate launch (8192^3: 11.9 against 10.4 ms per step --
     // twelve drain warps per SM rebuild C at a fraction of the separate kernel's rate and stall the
     // products behind them)
-    const bool fuse = mod && h->crt_fusion == 2;
+    const bool fuse = mod && h->crt_fusion == 2 && !tri;
     if (mod) {
         a.crt = &cc;
         a.res = res;
+        a.tri = tri;
         a.tile_pairs = h->tile_pairs == 2;  // measured neutral (8192^3: 11.67-11.80 ms either way)
         if (fuse) {
             // one counter per tile (either tile width), in the recombination scratch the modular
@@ -435,7 +456,7 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     launches += used_launches;
     if (mod && !fuse) {
         // C from the residues of the product (Chinese remainder theorem), scaled, alpha / beta
-        ce = momms::launch_crt_reconstruct(m, n, res, cr, e, ef, f, ff, alpha, beta, C, ldc, s);
+        ce = momms::launch_crt_reconstruct(m, n, res, cr, e, ef, f, ff, alpha, beta, C, ldc, s, tri);
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
         launches += 1;
     }
@@ -1504,8 +1525,16 @@ int momms_syrk(momms_handle_t h, int uplo, int trans, int64_t n, int64_t k, doub
         return scale_c(n, n, beta, C, ldc, s, tri);
     }
     const Plan p = pick_plan(h, n, n, k);
-    if (p.mode == MOMMS_MODE_EMULATED)
+    if (p.mode == MOMMS_MODE_EMULATED) {
+        if (h->scheme != MOMMS_SCHEME_SLICES && h->digit_bits == kDigitBits) {
+            // the modular encoding over the triangle's tiles, when it is chosen (op(A) times its
+            // transpose: the product's second operand is A with the other transposition)
+            const int rc = run_emulated(h, trans, 1 - trans, n, n, k, alpha, A, lda, A, lda, beta, C, ldc,
+                                        MOMMS_MEMBER_AUTO, p.slices, s, tri);
+            if (rc != kSlicesChosen) return rc;
+        }
         return run_syrk_emulated(h, uplo, trans, n, k, alpha, A, lda, beta, C, ldc, p.slices, s);
+    }
     const int member = p.member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : p.member;
     int ctas = 0, group = 0;
     cudaError_t e = momms::launch_native_gemm(trans, 1 - trans, n, n, k, alpha, A, lda, A, lda, beta, C, ldc, member,

@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
                                                   const __grid_constant__ CrtRecon r,
                                                   const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
                                                   const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
-                                                  double alpha, double beta, double* __restrict__ C, int64_t ldc) {
+                                                  double alpha, double beta, double* __restrict__ C, int64_t ldc,
+                                                  int tri) {
     const int64_t mn = m * n;
     const int64_t groups = m / V;
     const bool unit_alpha = alpha == 1.0, beta_zero = beta == 0.0;
@@ -63,7 +64,10 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
     for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
         const int Ej = f[j] - 2 * r.bits;
         const bool fj = ff[j] != 0;
-        for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < groups;
+        // a triangle (m = n): rows i >= j (lower) or i <= j (upper) of column j; the groups of V
+        // rows that hold the diagonal element are written element by element
+        const int64_t g_lo = tri == 1 ? j / V : 0, g_hi = tri == 2 ? min(groups, j / V + 1) : groups;
+        for (int64_t g = g_lo + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < g_hi;
              g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
             const int64_t i0 = g * V;
             unsigned long long s[V][L];
@@ -99,7 +103,11 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
                 if (!unit_alpha) y[t] *= alpha;
             }
             double* cp = C + i0 + j * ldc;
-            if constexpr (CV) {
+            if (tri != 0 && j >= i0 && j < i0 + V) {
+#pragma unroll
+                for (int t = 0; t < V; ++t)
+                    if (tri == 1 ? i0 + t >= j : i0 + t <= j) cp[t] = beta_zero ? y[t] : fma(beta, cp[t], y[t]);
+            } else if constexpr (CV) {
                 double2* c2 = reinterpret_cast<double2*>(cp);
 #pragma unroll
                 for (int h2 = 0; h2 < V / 2; ++h2) {
@@ -168,8 +176,9 @@ bool crt_plan(int bits, int64_t k, CrtConsts* c, CrtRecon* r) {
 
 cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, const CrtRecon& r, const int32_t* e,
                                    const uint8_t* ef, const int32_t* f, const uint8_t* ff, double alpha,
-                                   double beta, double* C, int64_t ldc, cudaStream_t stream) {
+                                   double beta, double* C, int64_t ldc, cudaStream_t stream, int tri) {
     if (m <= 0 || n <= 0) return cudaSuccess;
+    if (tri != 0 && (m != n || tri < 0 || tri > 2)) return cudaErrorInvalidValue;
     // four rows per thread: eight (96-104 registers, a quarter of the warps resident) measured
     // 300 against 186 us at 4096^2
     const bool vec = m % 4 == 0 && reinterpret_cast<uintptr_t>(res) % 4 == 0;
@@ -184,7 +193,7 @@ cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, con
     if (by > 65535) by = 65535;
     const dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(by));
 #define MOMMS_CRT_LAUNCH(V, CV, L) \
-    crt_kernel<V, CV, L><<<grid, 256, 0, stream>>>(m, n, res, r, e, ef, f, ff, alpha, beta, C, ldc)
+    crt_kernel<V, CV, L><<<grid, 256, 0, stream>>>(m, n, res, r, e, ef, f, ff, alpha, beta, C, ldc, tri)
     if (cvec) {
         if (three) MOMMS_CRT_LAUNCH(4, true, 3);
         else MOMMS_CRT_LAUNCH(4, true, 4);

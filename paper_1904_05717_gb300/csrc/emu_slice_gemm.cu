@@ -125,6 +125,11 @@ struct Params {
     // Fused reconstruction: the epilogue of a tile's last modulus rebuilds C itself once done[tile]
     // shows the other moduli's residues stored (crt_fused; else a separate reconstruction launch).
     int crt_fused;
+    // Triangular product (modular encoding, m = n): only the tri_tiles tiles that meet the lower
+    // (tri = 1) or upper (tri = 2) triangle of C are units, taken row by row (tri_tile).
+    int tri;
+    int tri_bn;
+    int64_t tri_tiles;
     int crt_L;                // limbs of the reconstruction arithmetic (3: P < 2^96, else 4)
     int crt_bits;             // integer width of the operands
     int* done;                // per tile: moduli whose residues are stored
@@ -165,7 +170,7 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
         // modulus by modulus.  A wave covers one modulus of a block of tiles (the L2 footprint of a
         // digit pair), only the last round is partial, and with group_tiles = the grid a full
         // group keeps every modulus of a tile on one CTA.
-        const int64_t tiles = static_cast<int64_t>(p.tiles_m) * p.tiles_n;
+        const int64_t tiles = p.tri ? p.tri_tiles : static_cast<int64_t>(p.tiles_m) * p.tiles_n;
         const int64_t N = p.one.S;
         const int64_t u = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
         if (u >= tiles * N) return false;
@@ -178,6 +183,7 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
         *lmod = static_cast<int>(r / gt);
         const int64_t t = first + r % gt;
         if (tile) *tile = t;
+        if (p.tri) return tri_tile(p.tri == 1, t, p.tiles_m, p.tiles_n, p.tri_bn, tm, tn);
         const int member = p.member == kMemberA1 ? kMemberA2 : p.member;
         return member_tile(member, p.group, t % gridDim.x, gridDim.x, t / gridDim.x, p.tiles_m, p.tiles_n, tm, tn);
     }
@@ -1089,7 +1095,10 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     using C_ = Cfg<BN>;
     const int sms = device_sm_count();
     const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
-    const int64_t tiles = tiles_m * tiles_n;
+    // a triangular product visits the tiles that meet the triangle (modular encoding, m = n)
+    if (a.tri && (a.crt == nullptr || a.crt_fuse != nullptr || a.m != a.n || 384 % BN != 0))
+        return cudaErrorInvalidValue;
+    const int64_t tiles = a.tri ? tri_prefix(a.tri == 1, tiles_m, static_cast<int>(tiles_n), BN) : tiles_m * tiles_n;
     const int64_t units = a.crt ? tiles * a.crt->N : tiles;  // modular encoding: one unit per modulus and tile
     int64_t ctas = a.max_ctas > 0 && a.max_ctas < sms ? a.max_ctas : sms;  // one CTA per SM at most
     if (ctas > units) ctas = units;
@@ -1190,8 +1199,13 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
                 p.modmagic[l] = a.crt->magic[l];
                 p.modoff[l] = static_cast<uint32_t>(pl * (((1ull << 31) + pl - 1) / pl));
             }
+            if (a.tri) {
+                p.tri = a.tri;
+                p.tri_bn = BN;
+                p.tri_tiles = tiles;
+            }
             cudaError_t e;
-            const bool pair = a.tile_pairs && !a.crt_fuse && tiles_m >= 2 && ctas >= 4;
+            const bool pair = a.tile_pairs && !a.crt_fuse && !a.tri && tiles_m >= 2 && ctas >= 4;
             if (pair) {
                 // clusters of two CTAs over tile pairs; the raster group counted in pair rows
                 p.pairs = 1;

@@ -82,10 +82,11 @@ int64_t crt_max_k();
 cudaError_t launch_emu_residues(int which, int op, int64_t rows, int64_t inner, const double* X, int64_t ldx,
                                 const int32_t* exps, const uint8_t* flags, const CrtConsts& c, void* planes,
                                 int64_t rows_pad, int64_t inner_pad, cudaStream_t stream);
-// C from the residue planes of the product ([N][n][m] bytes, residue in [0, p_l)).
+// C from the residue planes of the product ([N][n][m] bytes, residue in [0, p_l)); tri = 1 / 2
+// (m = n): only the lower / upper triangle of C is read from the residues and written.
 cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, const CrtRecon& r, const int32_t* e,
                                    const uint8_t* ef, const int32_t* f, const uint8_t* ff, double alpha,
-                                   double beta, double* C, int64_t ldc, cudaStream_t stream);
+                                   double beta, double* C, int64_t ldc, cudaStream_t stream, int tri = 0);
 
 // ----------------------------------------------- triangular solve (leaf step)
 constexpr int kTrsmNb = 64;       // order of the blocks inverted by substitution
@@ -126,6 +127,8 @@ struct EmuGemmArgs {
     const CrtRecon* crt_fuse;  // non-null: the last modulus of each tile rebuilds C itself
     int tile_pairs;        // modular encoding: clusters of two CTAs share the B tile of a tile pair
     int* done;             // fused: one zeroed counter per tile (device)
+    int tri;               // modular, m = n, separate reconstruction: 1 / 2 = only the tiles meeting the
+                           // lower / upper triangle of C
 };
 constexpr int kEmuBM = 128, kEmuBK = 64, kEmuBNMax = 192;
 

@@ -56,4 +56,50 @@ __host__ __device__ inline bool member_tile(int member, int group, int64_t cta, 
     return true;
 }
 
+// Triangular products (the symmetric rank-k update): of an m x m C, only the tiles that meet
+// the stored triangle are visited, tile row by tile row.  Tile rows are 128 high and tile
+// columns bn wide, bn dividing 384, so that three tile rows span pc = 384 / bn tile columns.
+// Lower: tile row r holds the columns [0, min(tiles_n, floor((128 r + 127) / bn) + 1)) (its
+// last row reaches the column's first one); upper: [floor(128 r / bn), tiles_n) (its first row
+// reaches the column's last one).
+
+// sum_{r < R} floor((128 r + b) / bn): with r = 3q + j the term is q pc + floor((128 j + b) / bn).
+__host__ __device__ inline int64_t tri_floor_sum(int64_t R, int b, int bn) {
+    const int64_t pc = 384 / bn;
+    const int64_t Q = R / 3, J = R - 3 * Q;
+    const int64_t g0 = b / bn, g1 = (128 + b) / bn, g2 = (256 + b) / bn;
+    int64_t s = 3 * pc * (Q * (Q - 1) / 2) + Q * (g0 + g1 + g2) + J * Q * pc;
+    if (J > 0) s += g0;
+    if (J > 1) s += g1;
+    return s;
+}
+
+// Tiles of the triangle in tile rows [0, R).
+__host__ __device__ inline int64_t tri_prefix(bool lower, int64_t R, int tiles_n, int bn) {
+    if (!lower) return R * tiles_n - tri_floor_sum(R, 0, bn);
+    // rows from rs on are full: floor((128 r + 127) / bn) >= tiles_n - 1
+    const int64_t need = static_cast<int64_t>(tiles_n - 1) * bn - 127;
+    const int64_t rs = need <= 0 ? 0 : (need + 127) / 128;
+    if (R <= rs) return tri_floor_sum(R, 127, bn) + R;
+    return tri_floor_sum(rs, 127, bn) + rs + (R - rs) * tiles_n;
+}
+
+// The t-th tile of the triangle (row by row); false when t is past the last one.
+__host__ __device__ inline bool tri_tile(bool lower, int64_t t, int tiles_m, int tiles_n, int bn, int* tm,
+                                         int* tn) {
+    if (t < 0 || tiles_m <= 0 || t >= tri_prefix(lower, tiles_m, tiles_n, bn)) return false;
+    int64_t lo = 0, hi = tiles_m;  // tri_prefix(lo) <= t < tri_prefix(hi)
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) / 2;
+        if (tri_prefix(lower, mid, tiles_n, bn) <= t) lo = mid;
+        else hi = mid;
+    }
+    const int64_t first = lower ? 0 : 128 * lo / bn;
+    const int64_t c = first + (t - tri_prefix(lower, lo, tiles_n, bn));
+    if (c < 0 || c >= tiles_n) return false;
+    *tm = static_cast<int>(lo);
+    *tn = static_cast<int>(c);
+    return true;
+}
+
 }  // namespace momms

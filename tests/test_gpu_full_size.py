@@ -118,3 +118,29 @@ def test_rank_k_and_panel_panel(shape, mode):
     C0 = syn.matrix("uniform", m, n, syn.workload_seed(1, "C") + k)
     C, _ = run(A, B, C0, mode)
     assert sample_ratio(A, B, C0, C, 1.0, 1.0, 16, 16) <= 1.0
+
+
+def test_syrk_8192_as_benchmarked():
+    # the benchmark's SYRK workload (C lower += A A^T, n = k = 8192, AUTO plan): the modular
+    # encoding over the triangle's tiles; sampled lower-triangle elements bit for bit against the
+    # definition of the modular result, the upper triangle untouched
+    n = 8192
+    A = syn.matrix("uniform", n, n, syn.workload_seed(6, "A"))
+    C0 = syn.matrix("uniform", n, n, syn.workload_seed(6, "C"))
+    h = M.Handle()
+    dA, dC = M.DeviceMatrix.from_numpy(A), M.DeviceMatrix.from_numpy(C0)
+    M.check(M.momms_syrk(h, M.LOWER, M.OP_N, n, n, 1.0, dA.ptr, dA.ld, 1.0, dC.ptr, dC.ld), "syrk")
+    assert h.device_status() == M.MOMMS_OK
+    rep = h.report()
+    h.close()
+    C = dC.to_numpy()
+    del dA, dC
+    assert rep["mode"] == M.MODE_EMULATED and rep["moduli"] > 0
+    up = np.triu(np.ones((n, n), bool), 1)
+    assert np.array_equal(C[up], C0[up])
+    rs = np.array([0, 127, 128, 4095, 5000, 8191])
+    cs = np.array([0, 127, 191, 192, 4095, 8191])
+    Co, _ = oracle.modular_dgemm(np.asfortranarray(A[rs, :]), np.asfortranarray(A[cs, :].T), rep["operand_bits"],
+                                 np.asfortranarray(C0[np.ix_(rs, cs)]), 1.0, 1.0)
+    low = rs[:, None] >= cs[None, :]
+    assert np.array_equal(C[np.ix_(rs, cs)][low], Co[low])

@@ -1,9 +1,12 @@
 """Symmetric rank-k update C := alpha op(A) op(A)^T + beta C on one triangle: the
 referenced triangle against the oracle's product within the bound, the other triangle
-untouched bit for bit, native and emulated (one split serving both operands)."""
+untouched bit for bit, native and emulated (one split serving both operands; the slice
+encoding's batched triangle and the modular encoding's triangle of residue products, the
+latter bit for bit against the oracle's definition of the modular result)."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1904_05717_gb300 import momms as M
 from paper_1904_05717_gb300 import synthetic as syn
 from util import max_ratio, reference
@@ -11,10 +14,12 @@ from util import max_ratio, reference
 pytestmark = pytest.mark.gpu
 
 
-def syrk(mode, S, uplo, trans, A, C0, alpha, beta):
+def syrk(mode, S, uplo, trans, A, C0, alpha, beta, scheme=M.SCHEME_AUTO, tile_n=0):
     n = C0.shape[0]
     k = A.shape[1] if trans == M.OP_N else A.shape[0]
-    h = M.Handle(mode=mode, slices=S)
+    h = M.Handle(mode=mode, slices=S, scheme=scheme)
+    if tile_n:
+        h.set_tile_n(tile_n)
     dA = M.DeviceMatrix.from_numpy(A)
     dC = M.DeviceMatrix.from_numpy(C0)
     M.check(M.momms_syrk(h, uplo, trans, n, k, alpha, dA.ptr, dA.ld, beta, dC.ptr, dC.ld), "syrk")
@@ -38,16 +43,51 @@ def check(C, C0, A, trans, uplo, alpha, beta):
                      np.asfortranarray(Nm), np.asfortranarray(C0m)) <= 1.0
 
 
-@pytest.mark.parametrize("mode,S", [(M.MODE_NATIVE, 0), (M.MODE_EMULATED, 8), (M.MODE_EMULATED, 0)])
+@pytest.mark.parametrize("mode,S,scheme", [(M.MODE_NATIVE, 0, M.SCHEME_AUTO), (M.MODE_EMULATED, 8, M.SCHEME_AUTO),
+                                           (M.MODE_EMULATED, 0, M.SCHEME_AUTO), (M.MODE_EMULATED, 8, M.SCHEME_SLICES)])
 @pytest.mark.parametrize("uplo", [M.LOWER, M.UPPER])
 @pytest.mark.parametrize("trans", [M.OP_N, M.OP_T])
-def test_syrk_matches_oracle_on_its_triangle(mode, S, uplo, trans):
+def test_syrk_matches_oracle_on_its_triangle(mode, S, scheme, uplo, trans):
     n, k = 333, 275   # ragged: 3 row blocks of 128, 2 column tiles of 192
     A = syn.matrix("uniform", n, k, 1201) if trans == M.OP_N else syn.matrix("uniform", k, n, 1202)
     C0 = syn.matrix("uniform", n, n, 1203)
-    C, rep = syrk(mode, S, uplo, trans, A, C0, 0.75, -1.25)
+    C, rep = syrk(mode, S, uplo, trans, A, C0, 0.75, -1.25, scheme)
     assert rep["mode"] == mode
+    if S == 8 and scheme == M.SCHEME_AUTO:
+        assert rep["moduli"] == 16        # 56-bit operands: AUTO takes 16 moduli for 36 digit pairs
+    if scheme == M.SCHEME_SLICES:
+        assert rep["moduli"] == 0
     check(C, C0, A, trans, uplo, 0.75, -1.25)
+
+
+@pytest.mark.parametrize("trans", [M.OP_N, M.OP_T])
+def test_syrk_moduli_triangle_bitwise(trans):
+    # n = 300: 3 tile rows of 128 (the last one 44 rows), 2 tile columns of 192 or 4 of 96, the
+    # reconstruction four rows per thread; n = 299 (op T): one row per thread
+    n, k = (300, 40) if trans == M.OP_N else (299, 40)
+    A = syn.matrix("normal", n, k, 1231) if trans == M.OP_N else syn.matrix("normal", k, n, 1232)
+    C0 = syn.matrix("uniform", n, n, 1233)
+    op = np.asfortranarray(A if trans == M.OP_N else A.T)
+    Co, _ = oracle.modular_dgemm(op, np.asfortranarray(op.T), 42, C0.copy(order="F"), 0.75, -1.25)
+    for uplo in (M.LOWER, M.UPPER):
+        tri = np.tril(np.ones((n, n), bool)) if uplo == M.LOWER else np.triu(np.ones((n, n), bool))
+        for tile_n in (96, 192):
+            C, rep = syrk(M.MODE_EMULATED, 6, uplo, trans, A, C0, 0.75, -1.25, M.SCHEME_MODULI, tile_n)
+            assert rep["moduli"] == 12 and rep["operand_bits"] == 42 and rep["tile_n"] == tile_n
+            assert np.array_equal(C[tri], Co[tri]), (uplo, tile_n)
+            assert np.array_equal(C[~tri], C0[~tri]), (uplo, tile_n)
+
+
+def test_syrk_moduli_beta_zero_nan_outside_and_one_tile():
+    # beta = 0 writes the triangle only (NaN stays outside); n = 100 is a single diagonal tile
+    for n in (100, 1):
+        A = syn.matrix("uniform", n, 70, 1241)
+        C0 = np.full((n, n), np.nan, order="F")
+        Co, _ = oracle.modular_dgemm(A, np.asfortranarray(A.T), 42, None, 2.0, 0.0)
+        C, rep = syrk(M.MODE_EMULATED, 6, M.UPPER, M.OP_N, A, C0, 2.0, 0.0, M.SCHEME_MODULI)
+        up = np.triu(np.ones((n, n), bool))
+        assert rep["moduli"] == 12
+        assert np.array_equal(C[up], Co[up]) and np.isnan(C[~up]).all()
 
 
 def test_syrk_beta_zero_leaves_nan_in_the_other_triangle_and_k_passes():
