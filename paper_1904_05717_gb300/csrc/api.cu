@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -81,6 +82,7 @@ struct momms_handle_s {
     std::vector<char> host_tables;         // the bytes last uploaded to batch_tables
     int* spread_host_big = nullptr;        // pinned, 2 per problem
     size_t spread_host_cap = 0;
+    std::unique_ptr<momms::CrtReconSet> crt_set;  // reconstruction constants by moduli count
     std::map<uint32_t, Plan> plans;
     // out-of-core products (momms_gemm_host): block buffers, copy streams, slot events
     void* ooc_buf = nullptr;
@@ -528,8 +530,14 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
 
     // ---- slice counts
     std::vector<int> S(count, h->slices);
+    std::vector<double> rule_bits(count, 0.0);
     const bool auto_s = h->slices <= 0;
-    // ---- device tables: [prep][items sa][sb][pa][pb][gemm table]; rebuilt below once S is known
+    // ---- device tables: [prep][items sa][sb][pa][pb][gemm table][modular: items pa][pb][gemm
+    // table][reconstruction table][items]; rebuilt below once S is known
+    std::vector<int2> pa_mod, pb_mod, crt_items;
+    std::vector<momms::EmuBatchProblem> gemm_mod;
+    std::vector<momms::CrtBatchProblem> crt_probs;
+    size_t off_mod[5] = {0, 0, 0, 0, 0};
     auto upload = [&](const std::vector<momms::EmuBatchProblem>& gemm, size_t* off_gemm, size_t* off_items) -> int {
         std::vector<char> buf;
         auto put = [&](const void* src, size_t bytes) {
@@ -544,6 +552,11 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
         off_items[2] = put(pa_items.data(), sizeof(int2) * pa_items.size());
         off_items[3] = put(pb_items.data(), sizeof(int2) * pb_items.size());
         *off_gemm = put(gemm.data(), sizeof(momms::EmuBatchProblem) * gemm.size());
+        off_mod[0] = put(pa_mod.data(), sizeof(int2) * pa_mod.size());
+        off_mod[1] = put(pb_mod.data(), sizeof(int2) * pb_mod.size());
+        off_mod[2] = put(gemm_mod.data(), sizeof(momms::EmuBatchProblem) * gemm_mod.size());
+        off_mod[3] = put(crt_probs.data(), sizeof(momms::CrtBatchProblem) * crt_probs.size());
+        off_mod[4] = put(crt_items.data(), sizeof(int2) * crt_items.size());
         const bool same = buf.size() == h->host_tables.size() && h->batch_tables &&
                           std::memcmp(buf.data(), h->host_tables.data(), buf.size()) == 0;
         if (same) return MOMMS_OK;
@@ -582,17 +595,44 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
             return MOMMS_ERR_CUDA;
         for (int i = 0; i < count; ++i)
             S[i] = slices_from_spread(h->spread_host_big[2 * i] / 16.0, h->spread_host_big[2 * i + 1] / 16.0,
-                                      k[idx[i]], bb, nullptr);
+                                      k[idx[i]], bb, &rule_bits[i]);
     }
+    // ---- encoding per problem: the modular one where the single-problem rule takes it (the
+    // operand width of the slice rule, moduli when they save two or more products) and, in AUTO,
+    // where its per-element costs that do not shrink with k are covered: the reconstruction of one
+    // element costs about what 850 k-steps of one residue product cost (measured: 1.08 ps per
+    // element and modulus against 1.27 fs per multiply-add step on the tensor cores), so moduli
+    // are taken when N (k + 850) <= 0.9 S (S + 1) / 2 k; digit slices otherwise
+    std::vector<char> mod(count, 0);
+    std::vector<int> planes(count), mbits(count, 0);
     for (int i = 0; i < count; ++i) {
-        if (S[i] > MOMMS_MAX_SLICES || k[idx[i]] > momms::emu_max_k_per_pass(S[i], bb)) return MOMMS_ERR_UNSUPPORTED;
+        momms::CrtConsts cc;
+        momms::CrtRecon cr;
+        const int w = auto_s ? std::min(bb * S[i], std::max(static_cast<int>(std::ceil(rule_bits[i])), bb * S[i] - bb + 1))
+                             : bb * S[i];
+        mod[i] = S[i] <= MOMMS_MAX_SLICES && use_moduli(h->scheme, w, S[i], bb, k[idx[i]], &cc, &cr);
+        if (mod[i] && h->scheme == MOMMS_SCHEME_AUTO) {
+            const double kk = static_cast<double>(k[idx[i]]);
+            mod[i] = cc.N * (kk + 850.0) <= 0.9 * (S[i] * (S[i] + 1) / 2) * kk;
+        }
+        if (mod[i]) {
+            planes[i] = cc.N;
+            mbits[i] = w;
+        } else {
+            if (S[i] > MOMMS_MAX_SLICES || k[idx[i]] > momms::emu_max_k_per_pass(S[i], bb)) return MOMMS_ERR_UNSUPPORTED;
+            planes[i] = S[i];
+        }
     }
-    // ---- digits and recombination scratch in the workspace
-    std::vector<size_t> off_ad(count), off_bd(count);
+    // ---- digits (residues), product residues and recombination scratch in the workspace
+    std::vector<size_t> off_ad(count), off_bd(count), off_res(count, 0);
     size_t ws_bytes = 0;
     for (int i = 0; i < count; ++i) {
-        off_ad[i] = ws_bytes; ws_bytes += align256(size_t(2) * S[i] * prep[i].m * prep[i].k_pad);
-        off_bd[i] = ws_bytes; ws_bytes += align256(size_t(2) * S[i] * prep[i].n * prep[i].k_pad);
+        off_ad[i] = ws_bytes; ws_bytes += align256(size_t(2) * planes[i] * prep[i].m * prep[i].k_pad);
+        off_bd[i] = ws_bytes; ws_bytes += align256(size_t(2) * planes[i] * prep[i].n * prep[i].k_pad);
+        if (mod[i]) {
+            off_res[i] = ws_bytes;
+            ws_bytes += align256(static_cast<size_t>(planes[i]) * prep[i].m * prep[i].n);
+        }
     }
     const size_t off_scratch = ws_bytes;
     const size_t scratch_bytes = momms::emu_scratch_bytes(momms::device_sm_count());
@@ -601,29 +641,57 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
     rc = ensure_workspace(h, ws_bytes, &ws);
     if (rc) return rc;
     char* w = static_cast<char*>(ws);
-    std::vector<momms::EmuBatchProblem> gemm(count);
-    int64_t tiles = 0;
+    std::vector<momms::EmuBatchProblem> gemm;
+    gemm.reserve(count);
+    int64_t tiles = 0, units_mod = 0;
+    int nmax = 0;
     for (int i = 0; i < count; ++i) {
         const int64_t p = idx[i];
         momms::EmuBatchPrep& q = prep[i];
-        q.S = S[i];
+        q.S = planes[i];
+        q.bits = mbits[i];
         q.Ad = w + off_ad[i];
         q.Bd = w + off_bd[i];
-        momms::EmuBatchProblem& g = gemm[i];
+        momms::EmuBatchProblem g;
         std::memset(&g, 0, sizeof(g));
-        if (!momms::emu_make_digit_map(&g.mapA, q.Ad, q.k_pad, q.m, S[i], momms::kEmuBM) ||
-            !momms::emu_make_digit_map(&g.mapB, q.Bd, q.k_pad, q.n, S[i], momms::kEmuBNMax))
+        if (!momms::emu_make_digit_map(&g.mapA, q.Ad, q.k_pad, q.m, planes[i], momms::kEmuBM) ||
+            !momms::emu_make_digit_map(&g.mapB, q.Bd, q.k_pad, q.n, planes[i], momms::kEmuBNMax))
             return MOMMS_ERR_UNSUPPORTED;
         g.e = q.e; g.ef = q.ef; g.f = q.f; g.ff = q.ff;
         g.C = C[p]; g.ldc = ldc[p]; g.alpha = alpha[p]; g.beta_c = beta[p];
-        g.m = q.m; g.n = q.n; g.S = S[i]; g.beta = bb;
+        g.m = q.m; g.n = q.n; g.S = planes[i]; g.beta = bb;
         g.nslab = q.k_pad / momms::kEmuBK;
         g.chunk_slabs = momms::emu_chunk_slabs(bb);
-        g.group_end = momms::emu_group_ends(S[i], bb, q.k_pad);
         g.tiles_n = static_cast<int32_t>((q.n + momms::kEmuBNMax - 1) / momms::kEmuBNMax);
-        g.tile0 = tiles;
-        tiles += ((q.m + momms::kEmuBM - 1) / momms::kEmuBM) * g.tiles_n;
+        const int64_t pt = ((q.m + momms::kEmuBM - 1) / momms::kEmuBM) * g.tiles_n;
+        if (mod[i]) {
+            // units = tiles x moduli; the residues of the product go to the problem's planes, the
+            // reconstruction reads them column by column
+            g.res = reinterpret_cast<uint8_t*>(w + off_res[i]);
+            g.tile0 = units_mod;
+            units_mod += pt * planes[i];
+            nmax = std::max(nmax, planes[i]);
+            gemm_mod.push_back(g);
+            const int ci = static_cast<int>(crt_probs.size());
+            crt_probs.push_back(momms::CrtBatchProblem{g.res, q.e, q.ef, q.f, q.ff, g.C, g.ldc, g.alpha, g.beta_c,
+                                                       q.m, q.n, planes[i], mbits[i]});
+            for (int64_t b = 0; b < momms::crt_batch_blocks(q.n); ++b) crt_items.push_back(make_int2(ci, (int)b));
+        } else {
+            g.group_end = momms::emu_group_ends(S[i], bb, q.k_pad);
+            g.tile0 = tiles;
+            tiles += pt;
+            gemm.push_back(g);
+        }
     }
+    // the split work lists of each encoding (the items name the problem's prep entry)
+    {
+        std::vector<int2> pa_s, pb_s;
+        for (const int2& it : pa_items) (mod[it.x] ? pa_mod : pa_s).push_back(it);
+        for (const int2& it : pb_items) (mod[it.x] ? pb_mod : pb_s).push_back(it);
+        pa_items.swap(pa_s);
+        pb_items.swap(pb_s);
+    }
+    if (crt_items.size() > INT32_MAX) return MOMMS_ERR_UNSUPPORTED;
     rc = upload(gemm, &off_gemm, off_items);
     if (rc) return rc;
     tb = static_cast<char*>(h->batch_tables);
@@ -634,20 +702,57 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
             return MOMMS_ERR_CUDA;
         launches += 2;
     }
-    if (momms::launch_emu_batch_split(dprep, items(2), (int)pa_items.size(), items(3), (int)pb_items.size(), s) !=
-        cudaSuccess)
-        return MOMMS_ERR_CUDA;
-    launches += 2;
-    cudaError_t ce = momms::launch_emu_slice_gemm_batched(reinterpret_cast<const momms::EmuBatchProblem*>(tb + off_gemm),
-                                                          count, tiles, w + off_scratch, scratch_bytes, h->status, s);
-    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
-    launches += 1;
-    int smin = MOMMS_MAX_SLICES, smax = 0;
-    for (int v : S) { smin = std::min(smin, v); smax = std::max(smax, v); }
+    const int nslices = static_cast<int>(gemm.size()), nmod = static_cast<int>(gemm_mod.size());
+    if (nslices > 0) {
+        if (momms::launch_emu_batch_split(dprep, items(2), (int)pa_items.size(), items(3), (int)pb_items.size(), s) !=
+            cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        launches += 2;
+    }
+    momms::CrtConsts c16;
+    momms::CrtRecon r16;
+    momms::crt_consts(momms::kCrtMaxModuli, 0, &c16, &r16);  // the moduli; each problem takes a prefix
+    if (nmod > 0) {
+        if (momms::launch_emu_batch_residues(dprep, reinterpret_cast<const int2*>(tb + off_mod[0]), (int)pa_mod.size(),
+                                             reinterpret_cast<const int2*>(tb + off_mod[1]), (int)pb_mod.size(), c16,
+                                             s) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        launches += 2;
+    }
+    if (nslices > 0) {
+        cudaError_t ce = momms::launch_emu_slice_gemm_batched(
+            reinterpret_cast<const momms::EmuBatchProblem*>(tb + off_gemm), nslices, tiles, w + off_scratch,
+            scratch_bytes, h->status, s);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        launches += 1;
+    }
+    if (nmod > 0) {
+        cudaError_t ce = momms::launch_emu_residue_gemm_batched(
+            reinterpret_cast<const momms::EmuBatchProblem*>(tb + off_mod[2]), nmod, units_mod, c16, w + off_scratch,
+            scratch_bytes, h->status, s);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        // C of the modular problems by the Chinese remainder theorem (the constants by moduli count)
+        if (!h->crt_set) {
+            h->crt_set.reset(new momms::CrtReconSet{});
+            for (int nm = 1; nm <= momms::kCrtMaxModuli; ++nm) {
+                momms::CrtConsts cn;
+                momms::crt_consts(nm, 0, &cn, &h->crt_set->by_n[nm]);
+            }
+        }
+        ce = momms::launch_crt_reconstruct_batched(reinterpret_cast<const momms::CrtBatchProblem*>(tb + off_mod[3]),
+                                                   reinterpret_cast<const int2*>(tb + off_mod[4]),
+                                                   (int)crt_items.size(), *h->crt_set, s);
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        launches += 2;
+    }
+    int smax = 0;
+    for (int i = 0; i < count; ++i)
+        if (!mod[i]) smax = std::max(smax, S[i]);
     h->report = momms_report_t{};
     h->report.mode = MOMMS_MODE_EMULATED;
     h->report.member = MOMMS_MEMBER_AUTO;
     h->report.slices = smax;
+    h->report.moduli = nmax;
     h->report.digit_bits = bb;
     h->report.k_passes = 1;
     h->report.tile_m = momms::kEmuBM;

@@ -129,7 +129,49 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
     }
 }
 
+// One column of one problem of a batch: the warp's lanes take its rows 32 apart, one element
+// each (byte loads, 32 consecutive bytes per warp and modulus), the arithmetic of crt_kernel.
+template <int L>
+__device__ __forceinline__ void crt_batch_column(const CrtBatchProblem& pr, const CrtRecon& r, int64_t j, int lane) {
+    const int64_t m = pr.m, mn = m * pr.n;
+    const int Ej = pr.f[j] - 2 * pr.bits;
+    const bool fj = pr.ff[j] != 0;
+    const bool unit_alpha = pr.alpha == 1.0, beta_zero = pr.beta == 0.0;
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int64_t i = lane; i < m; i += 32) {
+        unsigned long long s[L];
+        uint32_t qs = 0u;
+#pragma unroll
+        for (int q = 0; q < L; ++q) s[q] = 0;
+        const uint8_t* src = pr.res + j * m + i;
+        for (int l = 0; l < r.N; ++l) crt_accumulate<L>(s, qs, src[l * mn], r.w[l], r.frac[l]);
+        double y = (fj || pr.ef[i] != 0) ? qnan : crt_value<L>(s, qs, r.Pw, pr.e[i] + Ej);
+        if (!unit_alpha) y *= pr.alpha;
+        double* cp = pr.C + i + j * pr.ldc;
+        *cp = beta_zero ? y : fma(pr.beta, *cp, y);
+    }
+}
+
+__global__ void __launch_bounds__(256) crt_batch_kernel(const CrtBatchProblem* __restrict__ probs,
+                                                        const int2* __restrict__ items,
+                                                        const __grid_constant__ CrtReconSet set) {
+    const int2 it = items[blockIdx.x];
+    const CrtBatchProblem& pr = probs[it.x];
+    const int64_t j = static_cast<int64_t>(it.y) * 8 + (threadIdx.x >> 5);
+    if (j >= pr.n || pr.N < 1 || pr.N > kCrtMaxModuli) return;
+    const CrtRecon& r = set.by_n[pr.N];
+    if (r.Pw[3] == 0) crt_batch_column<3>(pr, r, j, threadIdx.x & 31);
+    else crt_batch_column<4>(pr, r, j, threadIdx.x & 31);
+}
+
 }  // namespace
+
+cudaError_t launch_crt_reconstruct_batched(const CrtBatchProblem* probs, const int2* items, int n_items,
+                                           const CrtReconSet& set, cudaStream_t stream) {
+    if (n_items <= 0) return cudaSuccess;
+    crt_batch_kernel<<<static_cast<unsigned>(n_items), 256, 0, stream>>>(probs, items, set);
+    return cudaGetLastError();
+}
 
 int64_t crt_max_k() {
     int64_t k = ((1ll << 31) - 1) / (127ll * 127ll);
@@ -149,8 +191,16 @@ bool crt_plan(int bits, int64_t k, CrtConsts* c, CrtRecon* r) {
     int N = 0;
     while (N < kCrtMaxModuli && P <= need) P *= kModuli[N++];
     if (P <= need) return false;
+    crt_consts(N, bits, c, r);
+    return true;
+}
+
+void crt_consts(int N, int bits, CrtConsts* c, CrtRecon* r) {
     *c = CrtConsts{};
     *r = CrtRecon{};
+    if (N < 1 || N > kCrtMaxModuli) return;
+    u128 P = 1;
+    for (int l = 0; l < N; ++l) P *= kModuli[l];
     c->N = r->N = N;
     c->bits = r->bits = bits;
     const long double Pl = static_cast<long double>(static_cast<unsigned long long>(P >> 64)) * 18446744073709551616.0L +
@@ -171,7 +221,6 @@ bool crt_plan(int bits, int64_t k, CrtConsts* c, CrtRecon* r) {
         r->frac[l] = static_cast<uint32_t>(wl / Pl * 524288.0L + 0.5L);  // round(2^19 w_l / P)
     }
     for (int q = 0; q < 4; ++q) r->Pw[q] = static_cast<uint32_t>(P >> (32 * q));
-    return true;
 }
 
 cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, const CrtRecon& r, const int32_t* e,

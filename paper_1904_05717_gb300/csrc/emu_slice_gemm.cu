@@ -149,6 +149,29 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
                        int64_t* tile = nullptr) {
     *part = -1;
     if constexpr (MOD) {
+        if (p.table != nullptr) {
+            // a batch: the units of each problem (its tiles times its moduli) follow one another,
+            // modulus-major inside the problem; tile0 is the problem's first unit
+            const int64_t u = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
+            if (u >= p.total_tiles) return false;
+            int lo = 0, hi = p.count - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (p.table[mid].tile0 <= u) lo = mid;
+                else hi = mid - 1;
+            }
+            const EmuBatchProblem& b = p.table[lo];
+            const int64_t tiles = static_cast<int64_t>((b.m + BM - 1) / BM) * b.tiles_n;
+            const int64_t v = u - b.tile0;
+            if (tiles <= 0 || v >= tiles * b.S) return false;
+            const int64_t t = v % tiles;
+            *prob = lo;
+            *lmod = static_cast<int>(v / tiles);
+            *tm = static_cast<int>(t / b.tiles_n);
+            *tn = static_cast<int>(t % b.tiles_n);
+            if (tile) *tile = 0;
+            return true;
+        }
         if (p.pairs) {
             // one unit per modulus and tile pair, per cluster; the pair rows follow the member's order
             const int64_t ncl = gridDim.x >> 1, cl = blockIdx.x >> 1;
@@ -457,15 +480,18 @@ MOMMS_DEV uint32_t residue_of(int32_t x, uint32_t p, uint32_t magic, uint32_t of
 // product 30 % slower).  The TMEM reads are warp-wide, so every lane takes them before the
 // bounds checks.
 template <int BN, int CR, int CT>
-MOMMS_DEV void store_residues(const Params& p, int tm, int tn, int l, int third, int rloc, const int32_t (&acc)[CR],
-                              uint32_t tsum) {
+MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, int third, int rloc,
+                              const int32_t (&acc)[CR], uint32_t tsum) {
     const int row = tm * BM + rloc;
     const int col0 = tn * BN + third * (BN / 3);
     const uint32_t pl = p.modp[l], mg = p.modmagic[l], off = p.modoff[l];
-    const bool row_ok = row < p.one.m;
-    uint8_t* dst = p.res + static_cast<size_t>(l) * p.one.m * p.one.n + static_cast<size_t>(col0) * p.one.m + row;
-    const size_t cstep = static_cast<size_t>(p.one.m);
-    const int ncols = min(BN / 3, p.one.n - col0);
+    const int m = prob < 0 ? p.one.m : p.table[prob].m;
+    const int n = prob < 0 ? p.one.n : p.table[prob].n;
+    uint8_t* res = prob < 0 ? p.res : p.table[prob].res;
+    const bool row_ok = row < m;
+    uint8_t* dst = res + static_cast<size_t>(l) * m * n + static_cast<size_t>(col0) * m + row;
+    const size_t cstep = static_cast<size_t>(m);
+    const int ncols = min(BN / 3, n - col0);
 #pragma unroll
     for (int c = 0; c < CR; ++c) {
         const uint32_t r = residue_of(acc[c], pl, mg, off);
@@ -988,7 +1014,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     if constexpr (MOD) {
                         if (!final_unit) {
-                            store_residues<BN, CR, CT>(p, tm, tn, lm, third, rloc, acc, tsum);
+                            store_residues<BN, CR, CT>(p, prob, tm, tn, lm, third, rloc, acc, tsum);
                             if (p.crt_fused) signal_tile(p, tile);
                         } else if (wait_tile(p, tile, pr.S - 1, abort_flag, wait_ok)) {
                             if (p.crt_L == 3)
@@ -1292,7 +1318,53 @@ static cudaError_t launch_bn_batched(const EmuBatchProblem* table, int count, in
     return cudaGetLastError();
 }
 
+// The residue products of a batch: one persistent launch over every problem's (modulus, tile)
+// units; the epilogue stores each problem's residues in its own planes.
+template <int BN>
+static cudaError_t launch_bn_batched_mod(const EmuBatchProblem* table, int count, int64_t total_units,
+                                         const CrtConsts& c, void* scratch, size_t scratch_bytes, int32_t* status,
+                                         cudaStream_t stream) {
+    using C_ = Cfg<BN>;
+    int64_t ctas = device_sm_count();
+    if (ctas > total_units) ctas = total_units;
+    const size_t half = static_cast<size_t>(ctas) * BN * BM * sizeof(double);
+    if (scratch_bytes < 2 * half) return cudaErrorInvalidValue;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(C_::SMEM_BYTES));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    Params p{};
+    p.table = table;
+    p.count = count;
+    p.total_tiles = total_units;
+    p.qscratch = static_cast<long long*>(scratch);
+    p.scratch = reinterpret_cast<double*>(static_cast<char*>(scratch) + half);
+    p.status = status;
+    for (int l = 0; l < c.N; ++l) {
+        const uint32_t pl = c.p[l];
+        p.modp[l] = pl;
+        p.modmagic[l] = c.magic[l];
+        p.modoff[l] = static_cast<uint32_t>(pl * (((1ull << 31) + pl - 1) / pl));
+    }
+    CUtensorMap unused{};
+    slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(unused, unused,
+                                                                                                      p);
+    return cudaGetLastError();
+}
+
 }  // namespace emu
+
+cudaError_t launch_emu_residue_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_units,
+                                            const CrtConsts& c, void* scratch, size_t scratch_bytes,
+                                            int32_t* status, cudaStream_t stream) {
+    if (count <= 0 || total_units <= 0) return cudaSuccess;
+    if (c.N < 1 || c.N > kCrtMaxModuli) return cudaErrorInvalidValue;
+    return emu::launch_bn_batched_mod<192>(dev_table, count, total_units, c, scratch, scratch_bytes, status, stream);
+}
 
 cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_tiles,
                                           void* scratch, size_t scratch_bytes, int32_t* status,

@@ -313,7 +313,8 @@ __device__ __forceinline__ void write_digits8(const double (&x)[8], bool valid_r
 // reduced mod p beforehand, and one multiply-high quotient.
 template <int NE>
 __device__ __forceinline__ void write_residues(const double (&x)[NE], bool valid_row, int e, const CrtConsts& c,
-                                               __half* __restrict__ planes, int64_t plane, int64_t off) {
+                                               __half* __restrict__ planes, int64_t plane, int64_t off,
+                                               int N, int bits) {
     uint32_t a0[NE], a1[NE], a2[NE];
     bool neg[NE];
 #pragma unroll
@@ -321,13 +322,13 @@ __device__ __forceinline__ void write_residues(const double (&x)[NE], bool valid
         unsigned long long fh, fl;
         uint32_t sg;
         fraction128(x[i], valid_row, e, &fh, &fl, &sg);
-        const unsigned long long A = fh >> (64 - c.bits);
+        const unsigned long long A = fh >> (64 - bits);
         a0[i] = static_cast<uint32_t>(A & 0xFFFFu);
         a1[i] = static_cast<uint32_t>((A >> 16) & 0xFFFFu);
         a2[i] = static_cast<uint32_t>(A >> 32);
         neg[i] = sg != 0;
     }
-    for (int l = 0; l < c.N; ++l) {
+    for (int l = 0; l < N; ++l) {
         const uint32_t pl = c.p[l], mg = c.magic[l], k16 = c.c16[l], k32 = c.c32[l];
         const int hi = static_cast<int>((pl - 1) / 2), lo = -static_cast<int>(pl / 2);
         uint32_t h[NE];
@@ -377,7 +378,7 @@ __global__ void split_inner_contig(const double* __restrict__ X, int64_t ld, int
 #pragma unroll
         for (int t = 0; t < 8; ++t) x[t] = (valid && q + t < inner) ? X[q + t + r * ld] : 0.0;
         if constexpr (RES)
-            write_residues<8>(x, valid, valid ? exps[r] : 0, crt, digits, plane, r * inner_pad + q);
+            write_residues<8>(x, valid, valid ? exps[r] : 0, crt, digits, plane, r * inner_pad + q, crt.N, crt.bits);
         else
             write_digits8(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
     }
@@ -416,7 +417,7 @@ __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int6
 #pragma unroll
         for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr ^ swz(qg + t)];
         if constexpr (RES)
-            write_residues<4>(x, valid, valid ? exps[r] : 0, crt, digits, plane, r * inner_pad + q);
+            write_residues<4>(x, valid, valid ? exps[r] : 0, crt, digits, plane, r * inner_pad + q, crt.N, crt.bits);
         else
             write_digits4(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
     }
@@ -507,8 +508,11 @@ __global__ void batch_scale_b(const EmuBatchPrep* __restrict__ probs, const int2
                   pr.spread ? pr.spread + 1 : nullptr, writer);
 }
 
-// A: 64 (rows) x 64 (k) tile through shared memory, as split_rows_contig.
-__global__ void batch_split_a(const EmuBatchPrep* __restrict__ probs, const int2* __restrict__ items) {
+// A: 64 (rows) x 64 (k) tile through shared memory, as split_rows_contig.  RES: residues of the
+// problem's S moduli (of c) at its `bits` instead of digits.
+template <bool RES>
+__global__ void batch_split_a(const EmuBatchPrep* __restrict__ probs, const int2* __restrict__ items,
+                              const __grid_constant__ CrtConsts c) {
     __shared__ double tile[TT][TT];  // [q][r ^ swz(q)]
     const int2 it = items[blockIdx.x];
     const EmuBatchPrep& pr = probs[it.x];
@@ -532,12 +536,17 @@ __global__ void batch_split_a(const EmuBatchPrep* __restrict__ probs, const int2
         double x[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr ^ swz(qg + t)];
-        write_digits4(x, valid, valid ? pr.e[r] : 0, pr.S, pr.beta, dg, plane, r * pr.k_pad + q);
+        if constexpr (RES)
+            write_residues<4>(x, valid, valid ? pr.e[r] : 0, c, dg, plane, r * pr.k_pad + q, pr.S, pr.bits);
+        else
+            write_digits4(x, valid, valid ? pr.e[r] : 0, pr.S, pr.beta, dg, plane, r * pr.k_pad + q);
     }
 }
 
 // B: a thread per four consecutive k of one column, as split_inner_contig.
-__global__ void batch_split_b(const EmuBatchPrep* __restrict__ probs, const int2* __restrict__ items) {
+template <bool RES>
+__global__ void batch_split_b(const EmuBatchPrep* __restrict__ probs, const int2* __restrict__ items,
+                              const __grid_constant__ CrtConsts c) {
     const int2 it = items[blockIdx.x];
     const EmuBatchPrep& pr = probs[it.x];
     const int64_t quads = pr.k_pad / 4;
@@ -550,8 +559,12 @@ __global__ void batch_split_b(const EmuBatchPrep* __restrict__ probs, const int2
 #pragma unroll
     for (int t = 0; t < 4; ++t) x[t] = (valid && q + t < pr.k) ? pr.B[q + t + j * pr.ldb] : 0.0;
     const int64_t plane = static_cast<int64_t>(pr.n) * pr.k_pad;
-    write_digits4(x, valid, valid ? pr.f[j] : 0, pr.S, pr.beta, static_cast<__half*>(pr.Bd), plane,
-                  j * pr.k_pad + q);
+    if constexpr (RES)
+        write_residues<4>(x, valid, valid ? pr.f[j] : 0, c, static_cast<__half*>(pr.Bd), plane, j * pr.k_pad + q,
+                          pr.S, pr.bits);
+    else
+        write_digits4(x, valid, valid ? pr.f[j] : 0, pr.S, pr.beta, static_cast<__half*>(pr.Bd), plane,
+                      j * pr.k_pad + q);
 }
 
 }  // namespace split
@@ -567,10 +580,20 @@ cudaError_t launch_emu_batch_scale(const EmuBatchPrep* probs, const int2* items_
 
 cudaError_t launch_emu_batch_split(const EmuBatchPrep* probs, const int2* items_a, int n_a, const int2* items_b,
                                    int n_b, cudaStream_t stream) {
-    if (n_a > 0) split::batch_split_a<<<static_cast<unsigned>(n_a), 256, 0, stream>>>(probs, items_a);
+    const CrtConsts none{};
+    if (n_a > 0) split::batch_split_a<false><<<static_cast<unsigned>(n_a), 256, 0, stream>>>(probs, items_a, none);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (n_b > 0) split::batch_split_b<<<static_cast<unsigned>(n_b), 256, 0, stream>>>(probs, items_b);
+    if (n_b > 0) split::batch_split_b<false><<<static_cast<unsigned>(n_b), 256, 0, stream>>>(probs, items_b, none);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emu_batch_residues(const EmuBatchPrep* probs, const int2* items_a, int n_a, const int2* items_b,
+                                      int n_b, const CrtConsts& c, cudaStream_t stream) {
+    if (n_a > 0) split::batch_split_a<true><<<static_cast<unsigned>(n_a), 256, 0, stream>>>(probs, items_a, c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (n_b > 0) split::batch_split_b<true><<<static_cast<unsigned>(n_b), 256, 0, stream>>>(probs, items_b, c);
     return cudaGetLastError();
 }
 

@@ -76,6 +76,8 @@ struct CrtRecon {                  // reconstruction
 // The moduli for `bits`-bit operands and contraction length k (P > 4 k (2^bits - 1)^2, so
 // |A^ B^| <= P/4); false when more than kCrtMaxModuli would be needed.
 bool crt_plan(int bits, int64_t k, CrtConsts* c, CrtRecon* r);
+// The constants of the first N moduli for `bits`-bit operands (no check of the range).
+void crt_consts(int N, int bits, CrtConsts* c, CrtRecon* r);
 // Largest k one modular product keeps exact in int32 (k * 127^2 < 2^31), a multiple of 64.
 int64_t crt_max_k();
 // Residues of the integer operand, layout [N][rows_pad][inner_pad] fp16 (as the digit slices).
@@ -144,12 +146,14 @@ struct EmuBatchProblem {
     double* C;
     int64_t ldc;
     double alpha, beta_c;
-    int64_t tile0;     // first tile of this problem in the concatenated tile list
+    int64_t tile0;     // first tile of this problem in the concatenated tile list (modular batch: first
+                       // unit, a unit being one modulus of one tile)
     int32_t m, n, S, beta, nslab, chunk_slabs, tiles_n;
     uint32_t group_end;
     // triangle of C written (symmetric rank-k updates): 0 = all, 1 = lower (column <= row +
     // diag), 2 = upper (column >= row + diag), rows and columns local to the problem
     int32_t tri, diag;
+    uint8_t* res;      // modular batch (S = N moduli): the product's residues, [N][n][m] bytes
 };
 // Per-problem inputs and outputs of the batched scale and split passes (op = N, N).
 struct EmuBatchPrep {
@@ -164,6 +168,7 @@ struct EmuBatchPrep {
     void* Ad;          // S slices [S][m][k_pad] fp16 (unused by the scale passes)
     void* Bd;          // S slices [S][n][k_pad] fp16
     int32_t* spread;   // 2 values (A, B): ceil(16 x spread) by atomicMax, or null
+    int32_t bits;      // modular batch: operand width, the S planes being residues of S moduli
 };
 // Work items are (problem, block) pairs; the block's meaning depends on the pass:
 //   scale A: 256 rows   scale B: 8 columns   split A: a 64 x 64 (row, k) tile   split B: 1024 digits.
@@ -171,6 +176,10 @@ cudaError_t launch_emu_batch_scale(const EmuBatchPrep* probs, const int2* items_
                                    int n_b, cudaStream_t stream);
 cudaError_t launch_emu_batch_split(const EmuBatchPrep* probs, const int2* items_a, int n_a, const int2* items_b,
                                    int n_b, cudaStream_t stream);
+// The residue split of a batch: the same work items, the planes of each problem holding its
+// operands' residues modulo the first S (= N) moduli of c at that problem's `bits`.
+cudaError_t launch_emu_batch_residues(const EmuBatchPrep* probs, const int2* items_a, int n_a, const int2* items_b,
+                                      int n_b, const CrtConsts& c, cudaStream_t stream);
 // Work-list sizes of one problem.
 inline int64_t emu_batch_scale_a_blocks(int64_t m) { return (m + 255) / 256; }
 inline int64_t emu_batch_scale_b_blocks(int64_t n) { return (n + 7) / 8; }
@@ -183,6 +192,30 @@ inline int64_t emu_batch_split_b_blocks(int64_t n, int64_t k_pad) { return (n * 
 bool emu_make_digit_map(CUtensorMap* map, const void* base, int64_t k_pad, int64_t rows, int S, int box_rows,
                         int64_t plane_rows = 0, int64_t row_pitch = 0);
 // One persistent launch of the slice-product kernel over the tiles of all problems.
+// Residue products of a batch (modular encoding): units (problem, modulus, tile), problem by
+// problem and modulus-major inside a problem; each problem's moduli are the first S of c.
+cudaError_t launch_emu_residue_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_units,
+                                            const CrtConsts& c, void* scratch, size_t scratch_bytes,
+                                            int32_t* status, cudaStream_t stream);
+// Reconstruction of a batch of modular products: work items (problem, block of 8 columns), a warp
+// per column.  The reconstruction constants depend only on the number of moduli.
+struct CrtBatchProblem {
+    const uint8_t* res;  // [N][n][m] residue bytes
+    const int32_t* e;
+    const uint8_t* ef;
+    const int32_t* f;
+    const uint8_t* ff;
+    double* C;
+    int64_t ldc;
+    double alpha, beta;
+    int32_t m, n, N, bits;
+};
+struct CrtReconSet {
+    CrtRecon by_n[kCrtMaxModuli + 1];  // index: number of moduli
+};
+inline int64_t crt_batch_blocks(int64_t n) { return (n + 7) / 8; }
+cudaError_t launch_crt_reconstruct_batched(const CrtBatchProblem* probs, const int2* items, int n_items,
+                                           const CrtReconSet& set, cudaStream_t stream);
 cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_tiles,
                                           void* scratch, size_t scratch_bytes, int32_t* status,
                                           cudaStream_t stream);

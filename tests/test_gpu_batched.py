@@ -1,5 +1,6 @@
 """Batched uneven products: one persistent launch over a device tile table (native),
-the emulated pipeline per problem, and CUDA-graph capture and replay."""
+the emulated pipeline per problem (digit slices or the modular encoding, chosen per problem),
+and CUDA-graph capture and replay."""
 import numpy as np
 import pytest
 
@@ -167,7 +168,10 @@ def test_batched_2000_uneven_problems_emulated():
     M.check(M.momms_gemm_batched(h, **args), "batched 2000 emulated")
     torch.cuda.synchronize()
     assert h.device_status() == M.MOMMS_OK
-    assert h.report()["launches"] == 5
+    rep = h.report()
+    # short k needs more than 56 bits (digit slices), long k takes the moduli: 2 scale, 2 split,
+    # 2 residue split, the slice-product and residue-product launches and the reconstruction
+    assert rep["slices"] > 0 and rep["moduli"] > 0 and rep["launches"] == 9
     worst = 0.0
     for hst, d in zip(hosts, dev):
         if hst is None:
@@ -207,4 +211,62 @@ def test_batched_auto_picks_emulation_by_total_work():
     dev, _ = run_batched(h, small)
     assert h.report()["mode"] == M.MODE_NATIVE
     assert check_all(small, dev) <= 1.0
+    h.close()
+
+
+def test_batched_moduli_bitwise_and_graph_replay():
+    # fixed S = 6 with the modular encoding: every problem's C bit for bit against the oracle's
+    # modular result (42-bit operands; 11 moduli at k = 1, 12 at the others), ragged tiles, m not a
+    # multiple of four, single rows and columns; then a captured graph replays the call
+    import torch
+    shapes = [(130, 200, 70), (1, 5, 3), (37, 1, 129), (257, 64, 1), (64, 193, 64), (100, 100, 100)]
+    probs = []
+    for i, (m, n, k) in enumerate(shapes):
+        A = syn.matrix("normal", m, k, 9100 + 3 * i)
+        B = syn.matrix("uniform", k, n, 9101 + 3 * i)
+        C = syn.matrix("uniform", m, n, 9102 + 3 * i)
+        probs.append((m, n, k, A, B, C))
+    h = M.Handle(mode=M.MODE_EMULATED, slices=6, scheme=M.SCHEME_MODULI)
+    dev, args = run_batched(h, probs, 0.5, -2.0)
+    torch.cuda.synchronize()
+    assert h.device_status() == M.MOMMS_OK
+    rep = h.report()
+    assert rep["moduli"] == 12 and rep["slices"] == 0
+    assert rep["launches"] == 6   # 2 scale, 2 residue split, residue products, reconstruction
+    eager = []
+    for (m, n, k, A, B, C), d in zip(probs, dev):
+        Co, _ = oracle.modular_dgemm(A, B, 42, C.copy(order="F"), 0.5, -2.0)
+        got = d[2].to_numpy()
+        assert np.array_equal(got, Co), (m, n, k)
+        eager.append(got)
+    for d, (_, _, _, _, _, C) in zip(dev, probs):
+        d[2].storage[: C.shape[1], : C.shape[0]].copy_(torch.from_numpy(np.ascontiguousarray(C.T)))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        M.check(M.momms_gemm_batched(h, stream=s, **args), "capture")
+    for d, (_, _, _, _, _, C) in zip(dev, probs):
+        d[2].storage[: C.shape[1], : C.shape[0]].copy_(torch.from_numpy(np.ascontiguousarray(C.T)))
+    g.replay()
+    torch.cuda.synchronize()
+    for d, e in zip(dev, eager):
+        assert np.array_equal(d[2].to_numpy(), e)
+    h.close()
+
+
+def test_batched_mixed_encodings_within_the_bound():
+    # data-driven S: k = 40 needs more than 56 bits (digit slices), k = 2048 and 3000 take the moduli
+    # (their reconstruction is paid for); one call runs both product launches
+    probs = []
+    for i, (m, n, k) in enumerate([(300, 260, 40), (200, 330, 2048), (129, 97, 33), (256, 256, 3000)]):
+        A = syn.matrix("uniform", m, k, 9200 + 3 * i)
+        B = syn.matrix("uniform", k, n, 9201 + 3 * i)
+        C = syn.matrix("uniform", m, n, 9202 + 3 * i)
+        probs.append((m, n, k, A, B, C))
+    h = M.Handle(mode=M.MODE_EMULATED)
+    dev, _ = run_batched(h, probs, 1.0, 1.0)
+    assert h.device_status() == M.MOMMS_OK
+    rep = h.report()
+    assert rep["slices"] > 0 and rep["moduli"] > 0 and rep["launches"] == 9
+    assert check_all(probs, dev) <= 1.0
     h.close()
