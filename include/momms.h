@@ -218,6 +218,13 @@ int momms_gemm_backward(momms_handle_t handle, int64_t m, int64_t n, int64_t k,
 /* `count` independent products C_i := alpha_i*A_i*B_i + beta_i*C_i (op = N, N),
  * of uneven sizes, in ONE persistent kernel launch over a device tile table
  * (plus, in EMULATED mode, one scale and one split launch over all problems).
+ * EMULATED mode chooses the integer encoding per problem (the handle's scheme; in
+ * AUTO the modular one where it saves two or more tensor products AND its
+ * reconstruction is paid for, N (k + 850) <= 0.9 S (S + 1) / 2 k): the problems on
+ * moduli get one residue split, ONE persistent residue-product launch over their
+ * (modulus, tile) units and one reconstruction launch, the others the digit split
+ * and the slice-product launch (up to 9 launches in all); report.slices and
+ * report.moduli give the largest of each.
  * All array arguments are HOST arrays of length `count`; the matrix pointers in
  * them are device pointers.  The tile table lives in the handle, so the
  * enqueued launches can be captured in a CUDA graph and replayed as long as the
@@ -328,9 +335,12 @@ int momms_crt_reconstruct(int64_t m, int64_t n, int64_t k, int bits, const uint8
  * neither read nor written).  The paper names the other level-3 BLAS as the next use
  * of the family (Sec. 7); this one needs half the products of a GEMM.  Native mode:
  * the DMMA kernel over the triangle's tiles, elements masked on the diagonal tiles.
- * Emulated mode: op(A) is scaled and split into digits ONCE and serves as both
- * operands; the slice products run over the 128-row blocks of the triangle in one
- * batched launch per k pass.  The error bound is the GEMM one with B = op(A)^T.
+ * Emulated mode: op(A) is scaled and split ONCE and serves as both operands.  With
+ * the modular encoding (chosen as for momms_gemm_ex) the residue products visit only
+ * the tiles that meet the triangle (momms_tri_tile gives their order) and the
+ * reconstruction writes only the triangle; with digit slices the slice products run
+ * over the 128-row blocks of the triangle in one batched launch per k pass.  The
+ * error bound is the GEMM one with B = op(A)^T.
  * Device pointers, asynchronous on `stream`.  Errors: BLAS-style negative index
  * (uplo -2, trans -3, n -4, k -5, A -7, lda -8, C -10, ldc -11), MOMMS_ERR_*. */
 int momms_syrk(momms_handle_t handle, int uplo, int trans, int64_t n, int64_t k, double alpha,
@@ -441,6 +451,14 @@ int momms_load_plans(momms_handle_t handle, const char* path);
  * has no i-th tile, or a negative argument index.  The kernels use the same function. */
 int momms_member_tile(int member, int group, int64_t cta, int64_t ctas, int64_t i, int tiles_m,
                       int tiles_n, int* tm, int* tn);
+
+/* The tile order of a triangular product (the modular symmetric rank-k update; host
+ * side, no GPU needed): of an n x n C cut into 128-row by tile_n-column tiles
+ * (tile_n = 96 or 192), the t-th tile that meets the uplo triangle, tile row by tile
+ * row.  Returns 1 and writes (tm, tn), 0 when t is past the last such tile, or a
+ * negative argument index (uplo -1, tile_n -2, n -3, t -4, tm -5, tn -6).  *count, when
+ * not null, receives the number of such tiles.  The kernel uses the same function. */
+int momms_tri_tile(int uplo, int tile_n, int64_t n, int64_t t, int* tm, int* tn, int64_t* count);
 
 /* ------------------------------------------------------- microbenchmarks */
 /* Peak probes used as roofline denominators: kind 0 = FP64 DMMA, 1 = FP64 DFMA,

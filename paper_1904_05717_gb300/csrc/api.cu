@@ -2133,6 +2133,20 @@ int momms_member_tile(int member, int group, int64_t cta, int64_t ctas, int64_t 
     return momms::member_tile(mem, g, cta, ctas, i, tiles_m, tiles_n, tm, tn) ? 1 : 0;
 }
 
+int momms_tri_tile(int uplo, int tile_n, int64_t n, int64_t t, int* tm, int* tn, int64_t* count) {
+    if (uplo != MOMMS_LOWER && uplo != MOMMS_UPPER) return -1;
+    if (tile_n != 96 && tile_n != 192) return -2;
+    if (n < 0 || n > (int64_t(1) << 30)) return -3;
+    if (t < 0) return -4;
+    if (!tm) return -5;
+    if (!tn) return -6;
+    const int tiles_m = static_cast<int>((n + momms::kEmuBM - 1) / momms::kEmuBM);
+    const int tiles_n = static_cast<int>((n + tile_n - 1) / tile_n);
+    const bool lower = uplo == MOMMS_LOWER;
+    if (count) *count = tiles_m > 0 ? momms::tri_prefix(lower, tiles_m, tiles_n, tile_n) : 0;
+    return momms::tri_tile(lower, t, tiles_m, tiles_n, tile_n, tm, tn) ? 1 : 0;
+}
+
 int momms_probe_peak(int kind, double* tflops, momms_stream_t stream) {
     if (kind < 0 || kind > 2) return -1;
     if (!tflops) return -2;

@@ -73,6 +73,27 @@ def member_tile(member: int, group: int, cta: int, ctas: int, i: int, tiles_m: i
     return (tm.value, tn.value) if ok == 1 else None
 
 
+def tri_tiles(uplo: int, tile_n: int, n: int):
+    """The tiles a triangular product (the modular symmetric rank-k update of an n x n C)
+    visits, in the kernel's order (``momms_tri_tile``)."""
+    tm = ctypes.c_int(0)
+    tn = ctypes.c_int(0)
+    cnt = ctypes.c_int64(0)
+    out = []
+    t = 0
+    while True:
+        ok = M.lib().momms_tri_tile(uplo, tile_n, n, t, ctypes.byref(tm), ctypes.byref(tn), ctypes.byref(cnt))
+        if ok < 0:
+            raise ValueError(f"momms_tri_tile: bad argument {-ok}")
+        if ok == 0:
+            break
+        out.append((tm.value, tn.value))
+        t += 1
+    if len(out) != cnt.value:
+        raise RuntimeError("momms_tri_tile: count and enumeration disagree")
+    return out
+
+
 def waves(member: int, tiles_m: int, tiles_n: int, ctas: int, group: int = 0):
     """For every round i of the persistent loop, the distinct tile rows and columns in flight."""
     out = []

@@ -105,6 +105,8 @@ _SIGS = {
     "momms_noalloc_scratch_bytes": ([], _SZ),
     "momms_member_tile": ([_I32, _I32, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
                           _I32),
+    "momms_tri_tile": ([_I32, _I32, _I64, _I64, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64)],
+                       _I32),
 }
 
 

@@ -1,0 +1,47 @@
+"""The tile order of the triangular (symmetric rank-k) residue product, host side: for
+every n up to 1500 and both triangles and tile widths, the tiles momms_tri_tile
+enumerates are exactly the 128 x tile_n tiles of the n x n C that hold an element of the
+triangle, each once, tile row by tile row -- checked against brute force over the tile
+grid (the kernel maps its units with the same function)."""
+import ctypes
+
+import pytest
+
+from paper_1904_05717_gb300 import iomodel
+from paper_1904_05717_gb300 import momms as M
+
+
+def brute(uplo, tile_n, n):
+    out = []
+    for r in range((n + 127) // 128):
+        r0, r1 = 128 * r, min(n, 128 * r + 128) - 1
+        for c in range((n + tile_n - 1) // tile_n):
+            c0, c1 = tile_n * c, min(n, tile_n * c + tile_n) - 1
+            if (r1 >= c0) if uplo == M.LOWER else (r0 <= c1):
+                out.append((r, c))
+    return out
+
+
+@pytest.mark.parametrize("uplo", [M.LOWER, M.UPPER])
+@pytest.mark.parametrize("tile_n", [96, 192])
+def test_tri_tile_order_is_the_triangle_row_by_row(uplo, tile_n):
+    sizes = list(range(1, 400)) + list(range(400, 1500, 37)) + [8192]
+    for n in sizes:
+        got = iomodel.tri_tiles(uplo, tile_n, n)
+        assert got == brute(uplo, tile_n, n), n
+
+
+def test_tri_tile_counts_and_errors():
+    tm, tn, cnt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    lib = M.lib()
+    # n = 8192 lower, 192-wide tiles: 64 tile rows, row r holds floor((128 r + 127) / 192) + 1 tiles
+    assert lib.momms_tri_tile(M.LOWER, 192, 8192, 0, ctypes.byref(tm), ctypes.byref(tn), ctypes.byref(cnt)) == 1
+    assert cnt.value == sum(min(43, (128 * r + 127) // 192 + 1) for r in range(64))
+    assert lib.momms_tri_tile(M.UPPER, 96, 0, 0, ctypes.byref(tm), ctypes.byref(tn), ctypes.byref(cnt)) == 0
+    assert cnt.value == 0
+    assert lib.momms_tri_tile(5, 96, 10, 0, ctypes.byref(tm), ctypes.byref(tn), None) == -1
+    assert lib.momms_tri_tile(M.LOWER, 128, 10, 0, ctypes.byref(tm), ctypes.byref(tn), None) == -2
+    assert lib.momms_tri_tile(M.LOWER, 96, -1, 0, ctypes.byref(tm), ctypes.byref(tn), None) == -3
+    assert lib.momms_tri_tile(M.LOWER, 96, 10, -1, ctypes.byref(tm), ctypes.byref(tn), None) == -4
+    assert lib.momms_tri_tile(M.LOWER, 96, 10, 0, None, ctypes.byref(tn), None) == -5
+    assert lib.momms_tri_tile(M.LOWER, 96, 10, 0, ctypes.byref(tm), None, None) == -6
