@@ -128,8 +128,9 @@ int moduli_reserved(int scheme, int S, int64_t k) {
 }
 
 // S digit planes per operand (or N residue planes when more), the recombination scratch and,
-// for N moduli, the N residue bytes of every element of C.
-EmuLayout emu_layout(int64_t m, int64_t n, int64_t k, int S, int max_ctas, int N = 0) {
+// for N moduli, the N residue bytes of every element of C.  shared_b: the second operand is the
+// first one transposed (symmetric rank-k update), its planes are the first operand's.
+EmuLayout emu_layout(int64_t m, int64_t n, int64_t k, int S, int max_ctas, int N = 0, bool shared_b = false) {
     EmuLayout L{};
     // digit slices hold exactly m (n) rows: ragged tiles are zero-filled by the copy engine
     L.m_pad = std::max<int64_t>(m, 1);
@@ -144,7 +145,9 @@ EmuLayout emu_layout(int64_t m, int64_t n, int64_t k, int S, int max_ctas, int N
     L.off_l1b = o; o += align256(L.n_pad * sizeof(float));
     const int planes = std::max(S, N);
     L.off_Ad = o;  o += align256(static_cast<size_t>(planes) * L.m_pad * L.k_pad * 2);
-    L.off_Bd = o;  o += align256(static_cast<size_t>(planes) * L.n_pad * L.k_pad * 2);
+    L.off_Bd = o;
+    if (shared_b) L.off_Bd = L.off_Ad;
+    else o += align256(static_cast<size_t>(planes) * L.n_pad * L.k_pad * 2);
     L.scratch_bytes = momms::emu_scratch_bytes_tail(m, n, k, S, max_ctas, kDigitBits);
     L.off_scratch = o; o += align256(L.scratch_bytes);
     L.off_res = o; o += align256(static_cast<size_t>(N) * L.m_pad * L.n_pad);
@@ -308,7 +311,7 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     if (S > MOMMS_MAX_SLICES) return MOMMS_ERR_UNSUPPORTED;
     const int S_alloc = S > 0 ? S : kAutoSliceMax;
     const int N_alloc = moduli_reserved(h->scheme, S, k);
-    EmuLayout L = emu_layout(m, n, k, S_alloc, h->max_ctas, N_alloc);
+    EmuLayout L = emu_layout(m, n, k, S_alloc, h->max_ctas, N_alloc, tri != 0);
     if (std::max(L.m_pad, L.n_pad) > (int64_t(1) << 30)) return MOMMS_ERR_UNSUPPORTED;
     void* ws = nullptr;
     int rc = ensure_workspace(h, L.total, &ws);
@@ -322,7 +325,7 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     int32_t* f = tri ? e : reinterpret_cast<int32_t*>(w + L.off_f);
     uint8_t* ff = tri ? ef : reinterpret_cast<uint8_t*>(w + L.off_ff);
     float* l1b = tri ? l1a : reinterpret_cast<float*>(w + L.off_l1b);
-    void* Bd = tri ? Ad : w + L.off_Bd;
+    void* Bd = w + L.off_Bd;  // = Ad for a triangle
     void* scratch = w + L.off_scratch;
     uint8_t* res = reinterpret_cast<uint8_t*>(w + L.off_res);
     int64_t launches = 0;
