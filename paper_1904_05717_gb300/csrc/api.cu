@@ -301,11 +301,13 @@ int join_aux(momms_handle_t h, cudaStream_t s) {
 // serve both operands, the residue products visit the tiles that meet the triangle and the
 // reconstruction writes only the triangle.  When the slice encoding is chosen instead it returns
 // kSlicesChosen before the products (only the scale, the spread and a guessed split have run).
+// kcap (triangular product): op(A) or op(B) is triangular with zeros stored elsewhere; the
+// modular encoding's residue products skip each tile's zero k range (EmuGemmArgs::kcap).
 constexpr int kSlicesChosen = 1;
 
 int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
-                 int64_t ldc, int member, int S, cudaStream_t s, int tri = 0) {
+                 int64_t ldc, int member, int S, cudaStream_t s, int tri = 0, int kcap = 0) {
     const int bb = h->digit_bits;
     if (tri && (m != n || A != B || opa == opb)) return MOMMS_ERR_UNSUPPORTED;
     if (S > MOMMS_MAX_SLICES) return MOMMS_ERR_UNSUPPORTED;
@@ -443,6 +445,7 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
         a.crt = &cc;
         a.res = res;
         a.tri = tri;
+        a.kcap = kcap;
         a.tile_pairs = h->tile_pairs == 2;  // measured neutral (8192^3: 11.67-11.80 ms either way)
         if (fuse) {
             // one counter per tile (either tile width), in the recombination scratch the modular
@@ -1718,12 +1721,16 @@ int momms_trmm(momms_handle_t h, int side, int uplo, int trans, int diag, int64_
     int64_t launches = 1;
     if (emulated) {
         // in place: the emulated path splits both operands into digits before the slice products
-        // write C, and B is not read again (beta = 0)
+        // write C, and B is not read again (beta = 0).  With the modular encoding each tile's
+        // products skip the k range where op(T) is zero: op(T) is lower when the stored triangle is
+        // lower and not transposed, or upper and transposed
+        const bool op_lower = (uplo == MOMMS_LOWER) != (trans == MOMMS_OP_T);
+        const int member = p.member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : p.member;
         rc = side == MOMMS_LEFT
-                 ? run_emulated(h, trans, MOMMS_OP_N, m, n, m, alpha, T, t, B, ldb, 0.0, B, ldb,
-                                p.member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : p.member, p.slices, s)
-                 : run_emulated(h, MOMMS_OP_N, trans, m, n, n, alpha, B, ldb, T, t, 0.0, B, ldb,
-                                p.member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : p.member, p.slices, s);
+                 ? run_emulated(h, trans, MOMMS_OP_N, m, n, m, alpha, T, t, B, ldb, 0.0, B, ldb, member, p.slices,
+                                s, 0, op_lower ? 1 : 2)
+                 : run_emulated(h, MOMMS_OP_N, trans, m, n, n, alpha, B, ldb, T, t, 0.0, B, ldb, member, p.slices,
+                                s, 0, op_lower ? 3 : 4);
     } else {
         // the native kernel reads B while it writes C: product from a copy of B
         double* Bc = reinterpret_cast<double*>(reinterpret_cast<char*>(h->ooc_buf) + tbytes);

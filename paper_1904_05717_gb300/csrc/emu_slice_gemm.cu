@@ -130,6 +130,10 @@ struct Params {
     int tri;
     int tri_bn;
     int64_t tri_tiles;
+    // Triangular operand (modular encoding, single problem): the k slabs where op(A) or op(B) is
+    // zero are skipped per unit.  1: op(A) lower (k < (tm + 1) BM), 2: op(A) upper (k >= tm BM),
+    // 3: op(B) lower (k >= tn BN), 4: op(B) upper (k < (tn + 1) BN); 0: every slab.
+    int kcap;
     int crt_L;                // limbs of the reconstruction arithmetic (3: P < 2^96, else 4)
     int crt_bits;             // integer width of the operands
     int* done;                // per tile: moduli whose residues are stored
@@ -262,6 +266,21 @@ MOMMS_DEV TileInts tile_ints(const Params& p, int prob, int part) {
         t.slab0 = 0; t.nslab = b.nslab; t.group_end = b.group_end;
     }
     return t;
+}
+
+// The unit's k slabs narrowed to where its triangular operand is not zero (Params::kcap); the
+// skipped slabs would add exact zeros.  Every role applies it, so all agree on the slab count.
+template <int BN>
+MOMMS_DEV void apply_kcap(const Params& p, int tm, int tn, TileInts& t) {
+    if (p.kcap == 0) return;
+    int lo = t.slab0, hi = t.slab0 + t.nslab;
+    if (p.kcap == 1) hi = min(hi, (tm + 1) * (BM / BK));
+    else if (p.kcap == 2) lo = max(lo, tm * (BM / BK));
+    else if (p.kcap == 3) lo = max(lo, (tn * BN) / BK);
+    else hi = min(hi, (tn * BN + BN + BK - 1) / BK);
+    if (hi <= lo) return;  // (not for a square triangle) keep the whole range
+    t.slab0 = lo;
+    t.nslab = hi - lo;
 }
 
 
@@ -863,7 +882,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int it = 0; ok; ++it) {
                 int tm, tn, prob, part, lm = 0;
                 if (!tile_of<TAIL, MOD>(p, it, &prob, &tm, &tn, &part, &lm)) break;
-                const TileInts pr = tile_ints(p, prob, part);
+                TileInts pr = tile_ints(p, prob, part);
+                if constexpr (MOD) apply_kcap<BN>(p, tm, tn, pr);
                 const CUtensorMap* mapA = prob < 0 ? &tmA : &p.table[prob].mapA;
                 const CUtensorMap* mapB = prob < 0 ? &tmB : &p.table[prob].mapB;
 
@@ -917,7 +937,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int it = 0; ok; ++it) {
                 int tm, tn, prob, part, lm = 0;
                 if (!tile_of<TAIL, MOD>(p, it, &prob, &tm, &tn, &part, &lm)) break;
-                const TileInts pr = tile_ints(p, prob, part);
+                TileInts pr = tile_ints(p, prob, part);
+                if constexpr (MOD) apply_kcap<BN>(p, tm, tn, pr);
                 for (int d = MOD ? 2 : pr.S + 1; d >= 2 && ok; --d) {
                     const int units = (MOD ? 1 : d - 1) * pr.nslab;
                     for (int u = 0; u < units && ok;) {
@@ -994,7 +1015,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 int tm, tn, prob, part, lm = 0;
                 int64_t tile = 0;
                 if (!tile_of<false, MOD>(p, it, &prob, &tm, &tn, &part, &lm, &tile)) break;
-                const TileInts pr = tile_ints(p, prob, -1);
+                TileInts pr = tile_ints(p, prob, -1);
+                if constexpr (MOD) apply_kcap<BN>(p, tm, tn, pr);
                 const double rb = pow2_normal(-pr.beta);
                 int gj = 0;           // position of the current diagonal inside its int64 group
                 bool rfirst = true;   // no FP64 partial R yet for this tile
@@ -1230,8 +1252,11 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
                 p.tri_bn = BN;
                 p.tri_tiles = tiles;
             }
+            if (a.kcap < 0 || a.kcap > 4) return cudaErrorInvalidValue;
+            p.kcap = a.kcap;
             cudaError_t e;
-            const bool pair = a.tile_pairs && !a.crt_fuse && !a.tri && tiles_m >= 2 && ctas >= 4;
+            // paired CTAs share B tiles slab by slab, so both must walk the same k range
+            const bool pair = a.tile_pairs && !a.crt_fuse && !a.tri && !a.kcap && tiles_m >= 2 && ctas >= 4;
             if (pair) {
                 // clusters of two CTAs over tile pairs; the raster group counted in pair rows
                 p.pairs = 1;

@@ -131,6 +131,8 @@ struct EmuGemmArgs {
     int* done;             // fused: one zeroed counter per tile (device)
     int tri;               // modular, m = n, separate reconstruction: 1 / 2 = only the tiles meeting the
                            // lower / upper triangle of C
+    int kcap;              // modular: a triangular operand, its zero k range skipped per tile (1 op(A)
+                           // lower, 2 op(A) upper, 3 op(B) lower, 4 op(B) upper; 0 none)
 };
 constexpr int kEmuBM = 128, kEmuBK = 64, kEmuBNMax = 192;
 
