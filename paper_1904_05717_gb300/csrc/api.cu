@@ -1371,7 +1371,7 @@ static std::string plan_header() {
     cudaGetDevice(&dev);
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, dev);
-    char buf[256];
+    char buf[sizeof(prop.name) + 64];  // the device name (up to 255 characters) and the numbers fit
     std::snprintf(buf, sizeof(buf), "momms-plan v1 %s sms=%d l2=%d", prop.name, prop.multiProcessorCount,
                   prop.l2CacheSize);
     for (char* c = buf; *c; ++c)
