@@ -146,6 +146,29 @@ def modular_dram_bytes(member: int, m: int, n: int, k: int, N: int, ctas: int = 
     return {"planes": planes, "residues": residues, "total": planes + residues, "rounds": len(w)}
 
 
+def triangle_dram_bytes(uplo: int, n: int, k: int, N: int, ctas: int = 152, bn: int = 192, bm: int = 128):
+    """HBM bytes of the residue-product launch of a symmetric rank-k update (C n x n, one
+    triangle): per modulus the units run through the tiles that meet the triangle in the kernel's
+    order (``tri_tiles``), a round being ``ctas`` consecutive tiles.  Both operands are the same
+    residue plane (op(A) and its transpose), so a round reads the union of the plane rows its tile
+    rows (bm each) and tile columns (bn each) need, once per modulus.  The launch writes the N
+    residue bytes of every element of the visited tiles (the whole diagonal tiles)."""
+    order = tri_tiles(uplo, bn, n)
+    k_pad = cdiv(k, 64) * 64
+    rows_read = 0
+    for r0 in range(0, len(order), ctas):
+        need = set()
+        for tm, tn in order[r0:r0 + ctas]:
+            need.update(range(tm * bm, min(n, tm * bm + bm)))
+            need.update(range(tn * bn, min(n, tn * bn + bn)))
+        rows_read += len(need)
+    planes = N * rows_read * k_pad * 2
+    elems = sum((min(n, tm * bm + bm) - tm * bm) * (min(n, tn * bn + bn) - tn * bn) for tm, tn in order)
+    residues = N * elems
+    return {"planes": planes, "residues": residues, "total": planes + residues,
+            "rounds": cdiv(len(order), ctas), "tiles": len(order)}
+
+
 def emulated_l2_to_sm_bytes(m: int, n: int, k: int, S: int, bm: int = 128, bn: int = 192):
     """L2 -> SM bytes: every tile streams its A (bm rows) and B (bn rows) digit panels per pair."""
     tiles_m, tiles_n = cdiv(m, bm), cdiv(n, bn)

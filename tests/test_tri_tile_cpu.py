@@ -45,3 +45,25 @@ def test_tri_tile_counts_and_errors():
     assert lib.momms_tri_tile(M.LOWER, 96, 10, -1, ctypes.byref(tm), ctypes.byref(tn), None) == -4
     assert lib.momms_tri_tile(M.LOWER, 96, 10, 0, None, ctypes.byref(tn), None) == -5
     assert lib.momms_tri_tile(M.LOWER, 96, 10, 0, ctypes.byref(tm), None, None) == -6
+
+
+def test_triangle_io_model_pins():
+    # one tile (n <= 128): the round reads the n plane rows once per modulus and writes the
+    # n^2 residues of each modulus
+    for n, k, N in [(1, 1, 7), (100, 70, 12), (128, 8192, 13)]:
+        b = iomodel.triangle_dram_bytes(M.LOWER, n, k, N)
+        k_pad = -(-k // 64) * 64
+        assert b["tiles"] == 1 and b["rounds"] == 1
+        assert b["planes"] == N * n * k_pad * 2 and b["residues"] == N * n * n
+    # the full 8192 problem: about half the full product's tiles, and each round of 152 tiles reads
+    # no more plane rows than the whole plane
+    b = iomodel.triangle_dram_bytes(M.LOWER, 8192, 8192, 12)
+    full_tiles = 64 * 43
+    assert full_tiles / 2 < b["tiles"] < full_tiles / 2 + 64
+    assert b["planes"] <= 12 * b["rounds"] * 8192 * 8192 * 2
+    assert b["residues"] == 12 * sum((min(8192, 128 * r + 128) - 128 * r) * (min(8192, 192 * c + 192) - 192 * c)
+                                     for r, c in iomodel.tri_tiles(M.LOWER, 192, 8192))
+    # the upper triangle visits about as many tiles as the lower one (the tiles are 128 x 192,
+    # so the two sets differ along the diagonal by at most one tile per tile row)
+    u = iomodel.triangle_dram_bytes(M.UPPER, 8192, 8192, 12)
+    assert abs(u["tiles"] - b["tiles"]) <= 64
