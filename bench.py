@@ -44,12 +44,15 @@ NCU_SLICE_CAPTURE = {"dram_bytes": (27.75e9 + 0.706e9 + 0.087e9) + (1.93e9 + 0.0
                      "source": "ncu capture of the 8192^3 call, scaled by tensor flops for other sizes "
                                "(profiles/slice_gemm_members_8192.md)"}
 # The same for the residue-product launch of the modular encoding (m=n=k=8192, 12 moduli; two
-# launches averaged), summarised in profiles/residue_product_8192.md.  None whenever the kernel
-# changes until it is captured again.
+# launches averaged), summarised in profiles/residue_product_8192.md.  "current" is False once the
+# kernel has changed since the capture: `traffic` is then null and the old figure is reported
+# beside it as `traffic_last_capture`, until it is captured again.
 NCU_RESIDUE_CAPTURE = {"dram_bytes": ((10.371e9 + 0.803e9) + (9.848e9 + 0.800e9)) / 2,
                        "tensor_flops": 12 * 2.0 * 8192 ** 3,
+                       "current": False,
                        "source": "ncu capture of the 8192^3 residue-product launch (12 moduli), scaled by tensor "
-                                 "flops for other sizes (profiles/residue_product_8192.md)"}
+                                 "flops for other sizes (profiles/residue_product_8192.md); taken before the kernel "
+                                 "gained its triangular, batched and k-range unit paths (inactive at this workload)"}
 UNIT = "TFLOP/s"
 SCHEMES = {"auto": 0, "slices": 1, "moduli": 2}  # momms_scheme_t
 
@@ -539,12 +542,15 @@ def main():
         traffic = None
         if capture is not None and args.shape == "square" and args.member in ("auto", "C2"):
             traffic = capture["dram_bytes"] * tensor_flops / capture["tensor_flops"]
+        stale = capture is not None and not capture.get("current", True)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
+                "frac": achieved / peak, "traffic": None if stale else traffic,
                 "traffic_source": (capture or {}).get("source"),
                 "kernel": kernel,
                 "peak_source": f"{src} bf16_tflops_sustained (fp16 rate = bf16 rate)",
                 "algorithmic_flops_per_launch": tensor_flops, "launch_ms": slice_ms}
+        if stale:
+            roof["traffic_last_capture"] = traffic
         del Ad, Bd, scratch
 
     # ---- native FP64 DMMA path on the same inputs (the other half of the metric)
