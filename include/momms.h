@@ -352,8 +352,10 @@ int momms_syrk(momms_handle_t handle, int uplo, int trans, int64_t n, int64_t k,
  * A triangular (uplo; diag UNIT: ones on the diagonal, which is not read), B m x n
  * overwritten (BLAS dtrmm).  The triangle is first copied into a dense zero-filled
  * operand kept by the handle; the product then runs as a GEMM in the handle's mode --
- * emulated: in place (both operands are split into digits before the slice products
- * write B); native: from a copy of B.  Device pointers, asynchronous on `stream`.  The
+ * emulated: in place (both operands are split before the products write B), and with
+ * the modular encoding each tile's residue products skip the k range where op(A) is
+ * zero (half the tensor work; the skipped products are exact zeros, so the result is
+ * unchanged); native: from a copy of B.  Device pointers, asynchronous on `stream`.  The
  * bound is the GEMM one with the zero triangle counted as exact zeros.  Errors:
  * BLAS-style negative index (side -2, uplo -3, trans -4, diag -5, m -6, n -7, A -9,
  * lda -10, B -11, ldb -12), MOMMS_ERR_*. */
