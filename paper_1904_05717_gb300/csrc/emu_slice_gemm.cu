@@ -1158,7 +1158,7 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     if (!emu_make_digit_map(&mapA, a.Ad, a.k_pad, a.m_pad, a.S, BM)) return cudaErrorInvalidValue;
     if (!emu_make_digit_map(&mapB, a.Bd, a.k_pad, a.n_pad, a.S, BN)) return cudaErrorInvalidValue;
 
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};  // idempotent; atomic for concurrent first calls
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1323,7 +1323,7 @@ static cudaError_t launch_bn_batched(const EmuBatchProblem* table, int count, in
     if (ctas > total_tiles) ctas = total_tiles;
     const size_t half = static_cast<size_t>(ctas) * BN * BM * sizeof(double);
     if (scratch_bytes < 2 * half) return cudaErrorInvalidValue;
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};  // idempotent; atomic for concurrent first calls
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1354,7 +1354,7 @@ static cudaError_t launch_bn_batched_mod(const EmuBatchProblem* table, int count
     if (ctas > total_units) ctas = total_units;
     const size_t half = static_cast<size_t>(ctas) * BN * BM * sizeof(double);
     if (scratch_bytes < 2 * half) return cudaErrorInvalidValue;
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};  // idempotent; atomic for concurrent first calls
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1399,13 +1399,13 @@ cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int 
 }
 
 int device_sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    // initialised once, thread-safely, on the first call's current device
+    static const int sms = [] {
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 1;
+    }();
     return sms;
 }
 

@@ -1,5 +1,6 @@
 // internal.h -- launchers shared between the C-ABI layer and the kernel files.
 #pragma once
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda.h>

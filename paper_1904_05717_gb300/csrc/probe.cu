@@ -74,7 +74,7 @@ constexpr int kCopyThreads = 1024, kCopySmem = 120 * 1024;
 cudaError_t stream_copy(void* dst, const void* src, size_t bytes, int ctas, int repeats,
                         cudaStream_t stream) {
     if (bytes == 0 || repeats == 0) return cudaSuccess;
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};  // idempotent; atomic for concurrent first calls
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(probe::copy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kCopySmem);
