@@ -146,13 +146,6 @@ int momms_set_scheme(momms_handle_t handle, int scheme);
  * products wait behind them -- 11.9 against 10.4 ms per 8192^3 step).  Returns -2 for other
  * values. */
 int momms_set_crt_fusion(momms_handle_t handle, int mode);
-/* Tile pairs of the modular encoding's residue products: clusters of two CTAs take two tiles
- * of one tile column together, and one of them loads the shared B tile into both (TMA
- * multicast within the cluster), which cuts the L2->SM operand traffic per flop by 30 %.
- * 0 = automatic = 1 (measured neutral at 4096^3 and 8192^3: L2 is not what bounds the residue
- * product), 1 = off, 2 = on.  Results are bit-identical either way.  Returns -2 for other
- * values. */
-int momms_set_tile_pairs(momms_handle_t handle, int mode);
 /* Caps the grid of the single-product launches of this handle at `ctas` CTAs that each
  * loop over their share of the member's tiles (0 = default: one CTA per SM for the
  * emulated slice products, one CTA per tile for the native kernel).  Fewer CTAs lower

@@ -58,7 +58,6 @@ struct momms_handle_s {
     int group = 0;                  // C2 raster group in tile rows (0 = default)
     int scheme = MOMMS_SCHEME_AUTO; // integer encoding of the emulated product
     int crt_fusion = 0;             // 0 auto, 1 separate reconstruction launch, 2 fused
-    int tile_pairs = 0;             // 0 auto (off), 1 off, 2 on: CTA pairs sharing B tiles (moduli)
     void* user_ws = nullptr;
     size_t user_ws_bytes = 0;
     void* own_ws = nullptr;
@@ -446,7 +445,6 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
         a.res = res;
         a.tri = tri;
         a.kcap = kcap;
-        a.tile_pairs = h->tile_pairs == 2;  // measured neutral (8192^3: 11.67-11.80 ms either way)
         if (fuse) {
             // one counter per tile (either tile width), in the recombination scratch the modular
             // product does not use
@@ -901,13 +899,6 @@ int momms_set_slices(momms_handle_t h, int slices) {
     if (!valid(h)) return MOMMS_ERR_HANDLE;
     if (slices < 0 || slices > MOMMS_MAX_SLICES) return -2;
     h->slices = slices;
-    return MOMMS_OK;
-}
-
-int momms_set_tile_pairs(momms_handle_t h, int mode) {
-    if (!valid(h)) return MOMMS_ERR_HANDLE;
-    if (mode < 0 || mode > 2) return -2;
-    h->tile_pairs = mode;
     return MOMMS_OK;
 }
 

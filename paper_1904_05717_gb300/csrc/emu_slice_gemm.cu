@@ -117,11 +117,6 @@ struct Params {
     // plane l of A by plane l of B and its epilogue stores (sum mod modp[l]) as a byte.
     uint8_t* res;             // [l][col][row] residues of the product, m n bytes per modulus
     int group_tiles;          // the unit order: groups of this many tiles, moduli in turn
-    // Tile pairs: clusters of two CTAs take the tiles (2 pm, tn) and (2 pm + 1, tn) of a pair
-    // together and share their B tile -- one CTA loads it into both (TMA multicast), and a stage is
-    // refilled once both MMAs released it.  Modular encoding, separate reconstruction only.
-    int pairs;
-    int tiles_mp;             // pair rows: ceil(tiles_m / 2)
     // Fused reconstruction: the epilogue of a tile's last modulus rebuilds C itself once done[tile]
     // shows the other moduli's residues stored (crt_fused; else a separate reconstruction launch).
     int crt_fused;
@@ -174,22 +169,6 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
             *tm = static_cast<int>(t / b.tiles_n);
             *tn = static_cast<int>(t % b.tiles_n);
             if (tile) *tile = 0;
-            return true;
-        }
-        if (p.pairs) {
-            // one unit per modulus and tile pair, per cluster; the pair rows follow the member's order
-            const int64_t ncl = gridDim.x >> 1, cl = blockIdx.x >> 1;
-            const int64_t ptiles = static_cast<int64_t>(p.tiles_mp) * p.tiles_n;
-            const int64_t u = cl + static_cast<int64_t>(it) * ncl;
-            if (u >= ptiles * p.one.S) return false;
-            *prob = -1;
-            *lmod = static_cast<int>(u / ptiles);
-            const int64_t pt = u - *lmod * ptiles;
-            if (tile) *tile = 0;
-            const int member = p.member == kMemberA1 ? kMemberA2 : p.member;
-            int pm;
-            if (!member_tile(member, p.group, pt % ncl, ncl, pt / ncl, p.tiles_mp, p.tiles_n, &pm, tn)) return false;
-            *tm = 2 * pm + static_cast<int>(blockIdx.x & 1);  // may pass the last tile row: zero-filled, not stored
             return true;
         }
         // modular encoding: the unit is one modulus of one tile, units handed out round-robin over
@@ -818,8 +797,7 @@ __global__ void __launch_bounds__(256) tail_fixup_kernel(const __grid_constant__
 
 // MOD: the modular encoding -- a unit is one modulus l of one tile (p.one.S moduli), one pair
 // (residue plane l of A, plane l of B), and its epilogue stores residues instead of recombining.
-// PAIR (with MOD): a cluster of two CTAs on a tile pair sharing the B tile (Params::pairs).
-template <int BN, bool TAIL, bool MOD = false, bool PAIR = false>
+template <int BN, bool TAIL, bool MOD = false>
 __global__ void __launch_bounds__(THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const __grid_constant__ Params p) {
@@ -848,7 +826,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], PAIR ? 2 : 1);  // pair: both CTAs' MMAs release a stage
+            mbar_init(&empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
@@ -864,7 +842,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if constexpr (PAIR) cluster_sync();  // the peer's barriers exist before any multicast or remote arrive
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -902,15 +879,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                             const int x = (pr.slab0 + j) * BK;
                             // A slice s rows [tm*BM, +BM), B slice d-s rows [tn*BN, +BN) (MOD: the
                             // residue planes of one modulus); rows past the end of a plane are
-                            // zero-filled by the copy engine.  PAIR: the even CTA brings the shared
-                            // B tile into both CTAs (the odd one expects its bytes all the same)
+                            // zero-filled by the copy engine
                             tma_load_3d(sa, mapA, &full[stage], x, tm * BM, plane_a);
-                            if constexpr (PAIR) {
-                                if ((blockIdx.x & 1) == 0)
-                                    tma_load_3d_multicast(sa + A_TILE, mapB, &full[stage], x, tn * BN, plane_b, 0x3);
-                            } else {
-                                tma_load_3d(sa + A_TILE, mapB, &full[stage], x, tn * BN, plane_b);
-                            }
+                            tma_load_3d(sa + A_TILE, mapB, &full[stage], x, tn * BN, plane_b);
                             last_phase[stage] = static_cast<int>(phase);
                             if (++stage == STAGES) {
                                 stage = 0;
@@ -963,8 +934,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 umma_f16_ss(dt, da + 2ull * kk, db + 2ull * kk, C_::IDESC,
                                             static_cast<uint32_t>((c | kk) != 0));
                             issued = true;
-                            if constexpr (PAIR) umma_commit_multicast(&empty[stage], 0x3);
-                            else umma_commit(&empty[stage]);
+                            umma_commit(&empty[stage]);
                             if (++stage == STAGES) {
                                 stage = 0;
                                 phase ^= 1u;
@@ -1057,8 +1027,6 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     tc_fence_before();
     __syncthreads();
-    // pair: neither CTA leaves while the other may still multicast into it or arrive on its barriers
-    if constexpr (PAIR) cluster_sync();
     if (threadIdx.x == 0 && *abort_flag) atomicExch(p.status, kStatusTimeout);
     if (warp == 1) {
         tc_fence_after();
@@ -1169,9 +1137,6 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C_::SMEM_BYTES));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false, true, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C_::SMEM_BYTES));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -1254,37 +1219,9 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
             }
             if (a.kcap < 0 || a.kcap > 4) return cudaErrorInvalidValue;
             p.kcap = a.kcap;
-            cudaError_t e;
-            // paired CTAs share B tiles slab by slab, so both must walk the same k range
-            const bool pair = a.tile_pairs && !a.crt_fuse && !a.tri && !a.kcap && tiles_m >= 2 && ctas >= 4;
-            if (pair) {
-                // clusters of two CTAs over tile pairs; the raster group counted in pair rows
-                p.pairs = 1;
-                p.tiles_mp = static_cast<int>((tiles_m + 1) / 2);
-                const int64_t ptile_units = static_cast<int64_t>(p.tiles_mp) * tiles_n * a.crt->N;
-                int64_t ncl = std::min<int64_t>(ctas / 2, ptile_units);
-                p.group = a.group > 0 ? a.group
-                                      : emu_default_group(ncl, p.tiles_mp, static_cast<int>(tiles_n));
-                if (a.used_ctas) *a.used_ctas = static_cast<int>(2 * ncl);
-                if (a.used_group) *a.used_group = p.group;
-                cudaLaunchConfig_t cfg{};
-                cfg.gridDim = dim3(static_cast<unsigned>(2 * ncl));
-                cfg.blockDim = dim3(THREADS);
-                cfg.dynamicSmemBytes = C_::SMEM_BYTES;
-                cfg.stream = stream;
-                cudaLaunchAttribute attr[1];
-                attr[0].id = cudaLaunchAttributeClusterDimension;
-                attr[0].val.clusterDim.x = 2;
-                attr[0].val.clusterDim.y = 1;
-                attr[0].val.clusterDim.z = 1;
-                cfg.attrs = attr;
-                cfg.numAttrs = 1;
-                e = cudaLaunchKernelEx(&cfg, slice_gemm_kernel<BN, false, true, true>, mapA, mapB, p);
-            } else {
-                slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(
-                    mapA, mapB, p);
-                e = cudaGetLastError();
-            }
+            slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(
+                mapA, mapB, p);
+            cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
             ++nlaunch;
             ++npass;

@@ -128,7 +128,6 @@ struct EmuGemmArgs {
     const CrtConsts* crt;  // modular encoding: S = N moduli, the epilogue writes residues to `res`
     uint8_t* res;          // [N][n][m] residues of the product (modular encoding only)
     const CrtRecon* crt_fuse;  // non-null: the last modulus of each tile rebuilds C itself
-    int tile_pairs;        // modular encoding: clusters of two CTAs share the B tile of a tile pair
     int* done;             // fused: one zeroed counter per tile (device)
     int tri;               // modular, m = n, separate reconstruction: 1 / 2 = only the tiles meeting the
                            // lower / upper triangle of C

@@ -88,16 +88,6 @@ MOMMS_DEV void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int
         : "memory");
 }
 // 3-D tiled load at (c0 inner, c1, c2 outer); out-of-range elements are zero-filled.
-// The same box into the shared memory of every CTA of the cluster in `mask`, at the same offset,
-// completing `bytes` on the barrier at the same offset in each of them.
-MOMMS_DEV void tma_load_3d_multicast(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
-                                     uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
-        : "memory");
-}
 MOMMS_DEV void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
@@ -137,15 +127,6 @@ MOMMS_DEV void umma_f16_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, ui
         : "memory");
 }
 // Arrive once on `bar` when every tcgen05.mma issued so far by this thread completes.
-// Arrive on the barrier at the same offset in every CTA of the cluster in `mask` once the MMAs
-// issued so far have completed.
-MOMMS_DEV void umma_commit_multicast(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
-}
 MOMMS_DEV void umma_commit(uint64_t* bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(

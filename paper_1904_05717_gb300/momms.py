@@ -71,7 +71,6 @@ _SIGS = {
     "momms_set_tile_n": ([_VP, _I32], _I32),
     "momms_set_scheme": ([_VP, _I32], _I32),
     "momms_set_crt_fusion": ([_VP, _I32], _I32),
-    "momms_set_tile_pairs": ([_VP, _I32], _I32),
     "momms_trsm": ([_VP, _I32, _I32, _I32, _I32, _I64, _I64, _DBL, _VP, _I64, _VP, _I64, _VP], _I32),
     "momms_crt_moduli": ([_I32, _I64, _VP, _VP], _I32),
     "momms_emu_residue_gemm": ([_I64, _I64, _I64, _I32, _VP, _VP, _I64, _I64, _I64, _I32, _VP, _VP, _SZ, _VP, _VP],
@@ -328,8 +327,6 @@ class Handle:
     def set_crt_fusion(self, mode):
         check(lib().momms_set_crt_fusion(self.ptr, mode), "momms_set_crt_fusion")
 
-    def set_tile_pairs(self, mode):
-        check(lib().momms_set_tile_pairs(self.ptr, mode), "momms_set_tile_pairs")
 
     def report(self):
         r = Report()

@@ -52,12 +52,11 @@ def test_residue_split_bitwise(which, op, bits, k):
     assert not np.any(got[:, rows:, :]) and not np.any(got[:, :, inner:])
 
 
-def modular(A, B, C0, alpha, beta, S=0, opa=0, opb=0, scheme=M.SCHEME_MODULI, tile_n=0, ctas=0, fusion=0, pairs=0):
+def modular(A, B, C0, alpha, beta, S=0, opa=0, opb=0, scheme=M.SCHEME_MODULI, tile_n=0, ctas=0, fusion=0):
     h = M.Handle(mode=M.MODE_EMULATED, slices=S, scheme=scheme)
     h.set_tile_n(tile_n)
     h.set_max_ctas(ctas)
     h.set_crt_fusion(fusion)
-    h.set_tile_pairs(pairs)
     dA = M.DeviceMatrix.from_numpy(A)
     dB = M.DeviceMatrix.from_numpy(B)
     dC = M.DeviceMatrix.from_numpy(C0)
@@ -316,22 +315,6 @@ def test_fused_reconstruction_bitwise_equal_to_separate(m, n, k):
     assert np.array_equal(Cf, Cs)
     Cref, N = reference(A, B, C0, -1.25, 0.5)
     assert max_ratio(Cf, Cref, k, 1.25, 0.5, N, C0) <= 1.0
-
-
-@pytest.mark.parametrize("m,n,k,tile_n", [(300, 1000, 520, 192), (2000, 900, 1100, 192), (650, 400, 700, 96)])
-def test_tile_pairs_bitwise_identical(m, n, k, tile_n):
-    # clusters of two CTAs sharing the B tile (an odd number of tile rows leaves the last pair's
-    # second tile past the matrix: zero operands, nothing stored) against single CTAs
-    A = syn.matrix("uniform", m, k, 411)
-    B = syn.matrix("uniform", k, n, 412)
-    C0 = syn.matrix("uniform", m, n, 413)
-    C1, r1 = modular(A, B, C0, 1.0, 1.0, 6, tile_n=tile_n, pairs=1)
-    C2, r2 = modular(A, B, C0, 1.0, 1.0, 6, tile_n=tile_n, pairs=2)
-    assert r1["moduli"] > 0 and r2["moduli"] == r1["moduli"]
-    assert r2["ctas"] % 2 == 0
-    assert np.array_equal(C1, C2)
-    Cref, N = reference(A, B, C0, 1.0, 1.0)
-    assert max_ratio(C2, Cref, k, 1.0, 1.0, N, C0) <= 1.0
 
 
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (3, 5, 70), (129, 1, 300), (1, 300, 64)])
