@@ -35,24 +35,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FP64-accurate GEMM TFLOP/s (2mnk/t) & % roofline, native vs emulated"
 
-# DRAM bytes (read + write) of one slice-product call (main + tail + fix-up launch) from the ncu capture
-# summarised in profiles/slice_gemm_members_8192.md (m=n=k=8192, S=6, member C2, default group),
-# with that call's algorithmic tensor flops; other sizes scale it by the tensor flops.  Set to
-# None whenever the slice-product kernels change until they are captured again.
+# DRAM bytes (read + write) of one slice-product call (main + tail + fix-up launch) from an ncu
+# capture (m=n=k=8192, S=6, member C2, default group), with that call's algorithmic tensor flops;
+# other sizes scale it by the tensor flops.  "current" is False once the kernel has changed since
+# the capture: `traffic` is then null and the old figure is reported beside it as
+# `traffic_last_capture`, until the capture is taken again.
 NCU_SLICE_CAPTURE = {"dram_bytes": (27.75e9 + 0.706e9 + 0.087e9) + (1.93e9 + 0.0545e9),
                      "tensor_flops": 21 * 2.0 * 8192 ** 3,
-                     "source": "ncu capture of the 8192^3 call, scaled by tensor flops for other sizes "
-                               "(profiles/slice_gemm_members_8192.md)"}
-# The same for the residue-product launch of the modular encoding (m=n=k=8192, 12 moduli; two
-# launches averaged), summarised in profiles/residue_product_8192.md.  "current" is False once the
-# kernel has changed since the capture: `traffic` is then null and the old figure is reported
-# beside it as `traffic_last_capture`, until it is captured again.
+                     "current": False,
+                     "source": "ncu DRAM counters of the 8192^3 slice-product call, scaled by tensor flops for "
+                               "other sizes; taken before the kernel's current version"}
+# The same for the residue-product launch of the modular encoding (m=n=k=8192, 12 moduli).
 NCU_RESIDUE_CAPTURE = {"dram_bytes": ((10.371e9 + 0.803e9) + (9.848e9 + 0.800e9)) / 2,
                        "tensor_flops": 12 * 2.0 * 8192 ** 3,
                        "current": False,
-                       "source": "ncu capture of the 8192^3 residue-product launch (12 moduli), scaled by tensor "
-                                 "flops for other sizes (profiles/residue_product_8192.md); taken before the kernel "
-                                 "gained its triangular, batched and k-range unit paths (inactive at this workload)"}
+                       "source": "ncu DRAM counters of the 8192^3 residue-product launch (12 moduli), scaled by "
+                                 "tensor flops for other sizes; taken before the kernel's current version"}
 UNIT = "TFLOP/s"
 SCHEMES = {"auto": 0, "slices": 1, "moduli": 2}  # momms_scheme_t
 
@@ -241,19 +239,6 @@ class OracleSample:
         self.oracle.dgemm(self.A, B, C, 1.0, 1.0)
         return time.perf_counter() - t0
 
-    def error_ratio(self, C_gpu_cols):
-        """max over the given leading columns of |C_gpu - C_oracle| / bound, the bound being
-        4 k u (|A||B| + |C0|)(1 + 4ku) + 2^-1021 (alpha = beta = 1)."""
-        cols = C_gpu_cols.shape[1]
-        B = np.asfortranarray(self.B[:, :cols])
-        C0 = np.asfortranarray(self.C[:, :cols])
-        Cref = self.oracle.dgemm(self.A, B, C0.copy(order="F"), 1.0, 1.0)
-        N = self.oracle.dgemm_abs(self.A, B)
-        u = 2.0 ** -53
-        k = self.n
-        bound = 4.0 * k * u * (N + np.abs(C0)) * (1.0 + 4.0 * k * u) + 2.0 ** -1021
-        return float(np.max(np.abs(C_gpu_cols - Cref) / bound))
-
     def columns_for(self, seconds):
         cols = int(max(self.cores, min(self.B.shape[1], seconds / max(self.per_col, 1e-9))))
         return max(self.cores, cols - cols % self.cores)
@@ -266,6 +251,18 @@ class OracleSample:
         desc = (f"oracle triple loop (p ascending, no FMA, OpenMP over columns) on {cols} of {n} columns "
                 f"of the m=n=k={n} product ({2.0 * n * n * cols:.3g} flops, {dt:.2f} s)")
         return tflops, desc
+
+
+def oracle_error_ratio(A, B, C0, C_gpu, k):
+    """max |C_gpu - C_oracle| / bound over the given block of C = A B + C0 (alpha = beta = 1), the
+    bound being 4 k u (|A||B| + |C0|)(1 + 4ku) + 2^-1021."""
+    import oracle
+    A, B, C0 = (np.asfortranarray(x) for x in (A, B, C0))
+    Cref = oracle.dgemm(A, B, C0.copy(order="F"), 1.0, 1.0)
+    N = oracle.dgemm_abs(A, B)
+    u = 2.0 ** -53
+    bound = 4.0 * k * u * (N + np.abs(C0)) * (1.0 + 4.0 * k * u) + 2.0 ** -1021
+    return float(np.max(np.abs(C_gpu - Cref) / bound))
 
 
 def run_reference(args):
@@ -462,6 +459,9 @@ def main():
 
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # the dominant product launch of every timed step is bracketed by a CUDA event pair that the
+    # library records on the launching stream (momms_set_kernel_timing)
+    h.set_kernel_timing(args.steps)
     with ClockSampler(local) as clk:
         barrier(world)
         torch.cuda.synchronize()
@@ -472,10 +472,13 @@ def main():
         torch.cuda.synchronize()
         barrier(world)
     value, ms = aggregate_throughput(flops, e0.elapsed_time(e1) / args.steps, world)
+    k_total_ms, k_launches = h.kernel_timing()
+    h.set_kernel_timing(0)
     clocks = clk.summary()
     status = h.device_status(stream)
 
-    # ---- dominant kernel alone (same digits or residues, same launch configuration), per-launch CUDA events
+    # ---- the dominant kernel: its launch time inside the timed steps (above), and alone (same digits or
+    # residues, same launch configuration), per-launch CUDA events
     S, bb = int(rep["slices"]), int(rep["digit_bits"])
     n_mod, op_bits = int(rep["moduli"]), int(rep["operand_bits"])
     roof = None
@@ -534,11 +537,15 @@ def main():
             if i > 0:  # first launch is a warm-up
                 evs.append((a0, a1))
         torch.cuda.synchronize()
-        slice_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        alone_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        # the launch time inside the timed steps is the figure; alone, for comparison
+        slice_ms = k_total_ms / k_launches if k_launches else alone_ms
         tensor_flops = products * 2.0 * m * n * k  # algorithmic: every digit-pair / residue product
         achieved = tensor_flops / (slice_ms * 1e-3) / 1e12
         peaks, src = measured_peaks()
-        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        # the steps' product launches run for well under a second at a time: the burst rate bounds them
+        peak = float(peaks.get("bf16_tflops"))
+        sustained = float(peaks.get("bf16_tflops_sustained", peak))
         traffic = None
         if capture is not None and args.shape == "square" and args.member in ("auto", "C2"):
             traffic = capture["dram_bytes"] * tensor_flops / capture["tensor_flops"]
@@ -547,8 +554,13 @@ def main():
                 "frac": achieved / peak, "traffic": None if stale else traffic,
                 "traffic_source": (capture or {}).get("source"),
                 "kernel": kernel,
-                "peak_source": f"{src} bf16_tflops_sustained (fp16 rate = bf16 rate)",
-                "algorithmic_flops_per_launch": tensor_flops, "launch_ms": slice_ms}
+                "peak_source": f"{src} bf16_tflops (burst; fp16 rate = bf16 rate)",
+                "frac_of_sustained": achieved / sustained,
+                "algorithmic_flops_per_launch": tensor_flops, "launch_ms": slice_ms,
+                "launch_ms_how": (f"CUDA events on the launching stream around the product launch of each of the "
+                                  f"{k_launches} timed steps (mean)" if k_launches else
+                                  "CUDA events around the product launched alone"),
+                "launch_ms_alone": alone_ms}
         if stale:
             roof["traffic_last_capture"] = traffic
         del Ad, Bd, scratch
@@ -632,13 +644,19 @@ def main():
         sample = OracleSample(n)
         v, desc = sample.measure(args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": sample.cores, "kind": "oracle", "sample": desc}
-        # the error of one step of the timed path against the oracle, on leading columns of C
-        acc_cols = 16
+        # the error of one step of the timed path against the oracle, on 16 rows and 16 columns of C
+        # drawn at random (seeded) over the whole matrix
         dC.storage.copy_(dC0)
         step()
         torch.cuda.synchronize()
-        ratio = sample.error_ratio(dC.to_numpy()[:, :acc_cols])
-        accuracy = {"max_error_over_bound": ratio, "columns_checked": acc_cols,
+        C_gpu = dC.to_numpy()
+        rng = np.random.default_rng(20191)
+        rows = np.sort(rng.choice(m, size=min(16, m), replace=False))
+        cols = np.sort(rng.choice(n, size=min(16, n), replace=False))
+        ratio = max(oracle_error_ratio(A_h[rows, :], B_h, C_h[rows, :], C_gpu[rows, :], k),
+                    oracle_error_ratio(A_h, B_h[:, cols], C_h[:, cols], C_gpu[:, cols], k))
+        accuracy = {"max_error_over_bound": ratio, "rows_checked": [int(x) for x in rows],
+                    "columns_checked": [int(x) for x in cols],
                     "bound": "4 k 2^-53 (|A||B| + |C0|)(1 + 4 k 2^-53) + 2^-1021, componentwise",
                     "slices": int(h.report()["slices"]) if h.report()["mode"] == M.MODE_EMULATED else 0,
                     "moduli": int(h.report()["moduli"]), "operand_bits": int(h.report()["operand_bits"])}
@@ -670,9 +688,10 @@ def main():
             "emulated_vs_native": (value / world / native["value"]) if (native and emulated) else None,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms, "steps": esteps,
-                    "how": "host wall clock over all steps; pinned host buffers; the inputs of step i+1 are "
-                           "copied in on one stream and the result of step i-1 copied out on another "
-                           "while step i computes (two device buffer sets)"},
+                    "how": "host wall clock over all steps; pinned host buffers; the copies are torch "
+                           "tensor copies (cudaMemcpyAsync) around the public call momms_gemm_ex on device "
+                           "buffers: the inputs of step i+1 are copied in on one stream and the result of "
+                           "step i-1 copied out on another while step i computes (two device buffer sets)"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "device_status": status,

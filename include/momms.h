@@ -172,6 +172,26 @@ int momms_get_last_report(momms_handle_t handle, momms_report_t* report);
 /* Device status word of the handle (0 = fine, MOMMS_ERR_TIMEOUT after a capped
  * wait expired).  Synchronises `stream` first.  Clears the word. */
 int momms_check_device_status(momms_handle_t handle, momms_stream_t stream);
+/* Test hook of the timeout path (no counterpart in the paper): the next slice- or
+ * residue-product launch of this process (any handle, or the allocation-free entry
+ * point) leaves the first shared-memory stage of its first CTA empty -- the producer
+ * announces the stage's bytes but issues no copy.  The MMA thread's bounded wait on that
+ * stage then runs out (about 2 s), the CTA raises its abort flag, lets its issued copies
+ * and MMAs finish, frees its tensor memory and writes MOMMS_ERR_TIMEOUT to the status
+ * word the launch was given (momms_check_device_status, momms_noalloc_status).  The C of
+ * that call is not valid; later calls are unaffected.  Nothing faults and no wait is
+ * unbounded. */
+void momms_debug_withhold_load(void);
+/* Per-launch timing of the dominant kernel (no counterpart in the paper; measurement only):
+ * with max_launches > 0 every later emulated single product of this handle records a CUDA
+ * event pair on its stream around its slice- or residue-product launch(es), for up to
+ * max_launches products (further ones are not timed); 0 switches it off.  The events are
+ * created here, never in the product calls.  Returns -2 for max_launches < 0. */
+int momms_set_kernel_timing(momms_handle_t handle, int max_launches);
+/* Sum of the recorded launch durations in milliseconds and their number since the last
+ * read (waits for the last recorded event), then starts counting again.  Returns -2 / -3
+ * for a NULL total_ms / launches. */
+int momms_kernel_timing(momms_handle_t handle, double* total_ms, int64_t* launches);
 const char* momms_status_string(int status);
 
 /* -------------------------------------------------------------- workspace */
@@ -416,9 +436,13 @@ int momms_gemm_host(momms_handle_t handle, int64_t m, int64_t n, int64_t k, doub
  *   - Every call shares the array, which keeps the previous call's contents:
  *     calls that overlap on the GPU (other streams, other host threads on the same
  *     device) race on it.  Issue them in order on one stream.
- *   - slices must be given (1..16).  A problem whose scratch does not fit returns
- *     MOMMS_ERR_WORKSPACE before anything is enqueued; m = 0 or n = 0 is a no-op;
- *     k = 0 or alpha = 0 returns MOMMS_ERR_UNSUPPORTED (use momms_gemm_ex).
+ *   - slices must be given (1..16).  A problem whose scratch does not fit, or with m,
+ *     n or k above 2^30, returns MOMMS_ERR_WORKSPACE before anything is enqueued;
+ *     m = 0 or n = 0 is a no-op; k = 0 or alpha = 0 returns MOMMS_ERR_UNSUPPORTED
+ *     (use momms_gemm_ex).
+ *   - The return value covers the enqueueing only.  A bounded device wait that runs
+ *     out writes MOMMS_ERR_TIMEOUT into the array's status word (C is then not
+ *     valid); momms_noalloc_status() reports and clears it.
  *   - Arguments: op_a 1, op_b 2, m 3, n 4, k 5, slices 6, alpha 7, A 8, lda 9,
  *     B 10, ldb 11, beta 12, C 13, ldc 14, stream 15 (negative return = index). */
 int momms_gemm_emulated_noalloc(int op_a, int op_b, int64_t m, int64_t n, int64_t k, int slices,
@@ -426,6 +450,12 @@ int momms_gemm_emulated_noalloc(int op_a, int op_b, int64_t m, int64_t n, int64_
                                 int64_t ldb, double beta, double* C, int64_t ldc,
                                 momms_stream_t stream);
 size_t momms_noalloc_scratch_bytes(void);
+/* Status of the allocation-free calls on the current device: waits for `stream`
+ * (all calls enqueued on it before this one), then stores in *status MOMMS_OK, or
+ * MOMMS_ERR_TIMEOUT if a bounded device wait of one of them ran out since the last
+ * read, and clears the word.  Allocates nothing.  Returns -2 for status = NULL,
+ * MOMMS_ERR_CUDA if the copy or the synchronisation fails. */
+int momms_noalloc_status(momms_stream_t stream, int* status);
 
 /* ---------------------------------------------------------------- tuning */
 /* Time the candidate plans (mode x member x slices) for the size buckets of the

@@ -8,18 +8,26 @@ C ABI, so the product is issued as C^T = B^T A^T.
 """
 from __future__ import annotations
 
+import threading
+
 import torch
 
 from . import momms as M
 
-_handles = {}
+_local = threading.local()
 
 
 def _handle(mode):
-    h = _handles.get(mode)
+    """The handle of this thread for (current device, mode): a handle holds per-call state (report,
+    workspace, status word) and belongs to one thread and one device."""
+    key = (torch.cuda.current_device(), mode)
+    handles = getattr(_local, "handles", None)
+    if handles is None:
+        handles = _local.handles = {}
+    h = handles.get(key)
     if h is None:
         h = M.Handle(mode=mode)
-        _handles[mode] = h
+        handles[key] = h
     return h
 
 

@@ -91,6 +91,10 @@ struct momms_handle_s {
     // the B operand's scale and split run on a second stream beside A's (fork / join events)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // per-launch timing of the dominant product launch (momms_set_kernel_timing): an event pair
+    // recorded on the launching stream around each slice- / residue-product launch
+    std::vector<cudaEvent_t> kev;  // 2 per launch: before, after
+    size_t kev_used = 0;           // pairs recorded since the last read
 };
 
 namespace {
@@ -295,6 +299,26 @@ int join_aux(momms_handle_t h, cudaStream_t s) {
     return MOMMS_OK;
 }
 
+// Event pair around one product launch when kernel timing is on and a pair is left (else no-op).
+struct KernelTimer {
+    momms_handle_t h;
+    cudaStream_t s;
+    cudaEvent_t* pair = nullptr;
+    KernelTimer(momms_handle_t h_, cudaStream_t s_) : h(h_), s(s_) {
+        if (2 * (h->kev_used + 1) <= h->kev.size()) {
+            pair = &h->kev[2 * h->kev_used];
+            if (cudaEventRecord(pair[0], s) != cudaSuccess) {
+                cudaGetLastError();
+                pair = nullptr;
+            }
+        }
+    }
+    void done() {
+        if (pair && cudaEventRecord(pair[1], s) == cudaSuccess) ++h->kev_used;
+        pair = nullptr;
+    }
+};
+
 // tri = 1 / 2: the symmetric rank-k update C := alpha op(A) op(A)^T + beta C on the lower / upper
 // triangle (m = n, B = A with opb the other transposition of A): one scale and residue split
 // serve both operands, the residue products visit the tiles that meet the triangle and the
@@ -456,9 +480,11 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
                 return MOMMS_ERR_CUDA;
         }
     }
+    KernelTimer timer(h, s);
     ce = momms::launch_emu_slice_gemm(a, &passes, s);
     if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
     if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+    timer.done();
     launches += used_launches;
     if (mod && !fuse) {
         // C from the residues of the product (Chinese remainder theorem), scaled, alpha / beta
@@ -876,6 +902,8 @@ int momms_destroy(momms_handle_t h) {
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    for (cudaEvent_t e : h->kev)
+        if (e) cudaEventDestroy(e);
     h->magic = 0;
     delete h;
     return MOMMS_OK;
@@ -899,6 +927,46 @@ int momms_set_slices(momms_handle_t h, int slices) {
     if (!valid(h)) return MOMMS_ERR_HANDLE;
     if (slices < 0 || slices > MOMMS_MAX_SLICES) return -2;
     h->slices = slices;
+    return MOMMS_OK;
+}
+
+void momms_debug_withhold_load(void) { momms::emu_debug_withhold_load(); }
+
+int momms_set_kernel_timing(momms_handle_t h, int max_launches) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (max_launches < 0) return -2;
+    const size_t want = 2 * static_cast<size_t>(max_launches);
+    while (h->kev.size() < want) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return MOMMS_ERR_CUDA;
+        }
+        h->kev.push_back(e);
+    }
+    while (h->kev.size() > want) {
+        cudaEventDestroy(h->kev.back());
+        h->kev.pop_back();
+    }
+    h->kev_used = 0;
+    return MOMMS_OK;
+}
+
+int momms_kernel_timing(momms_handle_t h, double* total_ms, int64_t* launches) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (!total_ms) return -2;
+    if (!launches) return -3;
+    double t = 0.0;
+    for (size_t i = 0; i < h->kev_used; ++i) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(h->kev[2 * i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, h->kev[2 * i], h->kev[2 * i + 1]) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        t += ms;
+    }
+    *total_ms = t;
+    *launches = static_cast<int64_t>(h->kev_used);
+    h->kev_used = 0;
     return MOMMS_OK;
 }
 

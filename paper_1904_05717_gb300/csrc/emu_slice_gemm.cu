@@ -129,6 +129,10 @@ struct Params {
     // zero are skipped per unit.  1: op(A) lower (k < (tm + 1) BM), 2: op(A) upper (k >= tm BM),
     // 3: op(B) lower (k >= tn BN), 4: op(B) upper (k < (tn + 1) BN); 0: every slab.
     int kcap;
+    // Test hook of the timeout path (momms_debug_withhold_load): CTA 0's producer announces its
+    // first stage but issues no copy into it, so the MMA thread's bounded wait on that stage runs
+    // out -- the abort, drain and status path runs without any fault.
+    int withhold;
     int crt_L;                // limbs of the reconstruction arithmetic (3: P < 2^96, else 4)
     int crt_bits;             // integer width of the operands
     int* done;                // per tile: moduli whose residues are stored
@@ -856,6 +860,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             int last_phase[STAGES];
             for (int i = 0; i < STAGES; ++i) last_phase[i] = -1;
             bool ok = true;
+            bool withhold = p.withhold != 0 && blockIdx.x == 0;
             for (int it = 0; ok; ++it) {
                 int tm, tn, prob, part, lm = 0;
                 if (!tile_of<TAIL, MOD>(p, it, &prob, &tm, &tn, &part, &lm)) break;
@@ -880,8 +885,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                             // A slice s rows [tm*BM, +BM), B slice d-s rows [tn*BN, +BN) (MOD: the
                             // residue planes of one modulus); rows past the end of a plane are
                             // zero-filled by the copy engine
-                            tma_load_3d(sa, mapA, &full[stage], x, tm * BM, plane_a);
-                            tma_load_3d(sa + A_TILE, mapB, &full[stage], x, tn * BN, plane_b);
+                            if (!withhold) {
+                                tma_load_3d(sa, mapA, &full[stage], x, tm * BM, plane_a);
+                                tma_load_3d(sa + A_TILE, mapB, &full[stage], x, tn * BN, plane_b);
+                            }
+                            withhold = false;  // (test hook: only the first stage stays empty)
                             last_phase[stage] = static_cast<int>(phase);
                             if (++stage == STAGES) {
                                 stage = 0;
@@ -1080,6 +1088,9 @@ namespace emu {
 // Tail split of a single-problem launch.  With a round-robin member the last round holds only
 // tiles % ctas tiles; cutting each into `parts` k ranges (parts = ctas / that count, at most the
 // slabs of the shortest pass) lets parts x as many CTAs share that round.
+// Armed by momms_debug_withhold_load(); the next slice-product launch takes it (Params::withhold).
+static std::atomic<int> g_withhold{0};
+
 struct TailPlan {
     int full_rounds = 0, tiles = 0, parts = 0;
     size_t sums_bytes = 0;
@@ -1126,8 +1137,8 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     if (!emu_make_digit_map(&mapA, a.Ad, a.k_pad, a.m_pad, a.S, BM)) return cudaErrorInvalidValue;
     if (!emu_make_digit_map(&mapB, a.Bd, a.k_pad, a.n_pad, a.S, BN)) return cudaErrorInvalidValue;
 
-    static std::atomic<bool> attr_set{false};  // idempotent; atomic for concurrent first calls
-    if (!attr_set) {
+    static PerDeviceFlag attr_set;  // idempotent; per device, atomic for concurrent first calls
+    if (!attr_set.done()) {
         cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(C_::SMEM_BYTES));
@@ -1138,7 +1149,7 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
             e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C_::SMEM_BYTES));
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.mark();
     }
     const bool mod = a.crt != nullptr;
     const int64_t kslabs = (a.k + BK - 1) / BK;
@@ -1183,6 +1194,7 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         if (a.used_ctas) *a.used_ctas = static_cast<int>(ctas);
         if (a.used_group) *a.used_group = p.group;
         p.table = nullptr;
+        p.withhold = g_withhold.exchange(0);
         p.qscratch = static_cast<long long*>(a.scratch);
         p.scratch = reinterpret_cast<double*>(static_cast<char*>(a.scratch) + half);
         p.status = a.status;
@@ -1232,6 +1244,7 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         ++nlaunch;
+        p.withhold = 0;  // the test hook acts on the first launch only
         if (tp.parts) {
             // tail launch: one CTA per k part of every tile of the last, partial round ...
             slice_gemm_kernel<BN, true><<<static_cast<unsigned>(tp.tiles * tp.parts), THREADS, C_::SMEM_BYTES,
@@ -1260,18 +1273,19 @@ static cudaError_t launch_bn_batched(const EmuBatchProblem* table, int count, in
     if (ctas > total_tiles) ctas = total_tiles;
     const size_t half = static_cast<size_t>(ctas) * BN * BM * sizeof(double);
     if (scratch_bytes < 2 * half) return cudaErrorInvalidValue;
-    static std::atomic<bool> attr_set{false};  // idempotent; atomic for concurrent first calls
-    if (!attr_set) {
+    static PerDeviceFlag attr_set;  // idempotent; per device, atomic for concurrent first calls
+    if (!attr_set.done()) {
         cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(C_::SMEM_BYTES));
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.mark();
     }
     Params p{};
     p.table = table;
     p.count = count;
     p.total_tiles = total_tiles;
+    p.withhold = g_withhold.exchange(0);
     p.qscratch = static_cast<long long*>(scratch);
     p.scratch = reinterpret_cast<double*>(static_cast<char*>(scratch) + half);
     p.status = status;
@@ -1291,18 +1305,19 @@ static cudaError_t launch_bn_batched_mod(const EmuBatchProblem* table, int count
     if (ctas > total_units) ctas = total_units;
     const size_t half = static_cast<size_t>(ctas) * BN * BM * sizeof(double);
     if (scratch_bytes < 2 * half) return cudaErrorInvalidValue;
-    static std::atomic<bool> attr_set{false};  // idempotent; atomic for concurrent first calls
-    if (!attr_set) {
+    static PerDeviceFlag attr_set;  // idempotent; per device, atomic for concurrent first calls
+    if (!attr_set.done()) {
         cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(C_::SMEM_BYTES));
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.mark();
     }
     Params p{};
     p.table = table;
     p.count = count;
     p.total_tiles = total_units;
+    p.withhold = g_withhold.exchange(0);
     p.qscratch = static_cast<long long*>(scratch);
     p.scratch = reinterpret_cast<double*>(static_cast<char*>(scratch) + half);
     p.status = status;
@@ -1335,15 +1350,28 @@ cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int 
     return emu::launch_bn_batched<192>(dev_table, count, total_tiles, scratch, scratch_bytes, status, stream);
 }
 
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return dev;
+}
+
 int device_sm_count() {
-    // initialised once, thread-safely, on the first call's current device
-    static const int sms = [] {
-        int dev = 0, n = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        return n > 0 ? n : 1;
-    }();
-    return sms;
+    // looked up once per device ordinal, thread-safely (a racing first call stores the same value)
+    static std::atomic<int> sms[kMaxDevices] = {};
+    const int dev = current_device();
+    if (dev >= 0 && dev < kMaxDevices) {
+        const int v = sms[dev].load(std::memory_order_relaxed);
+        if (v > 0) return v;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) cudaGetLastError();
+    n = n > 0 ? n : 1;
+    if (dev >= 0 && dev < kMaxDevices) sms[dev].store(n, std::memory_order_relaxed);
+    return n;
 }
 
 size_t emu_scratch_bytes(int num_sms) { return emu_scratch_bytes_for_ctas(num_sms); }
@@ -1456,6 +1484,8 @@ int emu_default_group(int64_t ctas, int tiles_m, int tiles_n) {
     cache[key] = best;
     return best;
 }
+
+void emu_debug_withhold_load() { emu::g_withhold.store(1); }
 
 cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_t stream) {
     using namespace emu;

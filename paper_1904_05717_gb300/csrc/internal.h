@@ -226,6 +226,8 @@ int emu_pick_bn(int64_t m, int64_t n, int64_t k, int requested, int units_per_ti
 // Default C2 group of the slice-product kernel for `ctas` persistent CTAs (tile rows of the
 // block of C one wave covers; fewest operand rows read per unit of k over all waves).
 int emu_default_group(int64_t ctas, int tiles_m, int tiles_n);
+// Arms the timeout test hook: the next slice-product launch leaves one stage of CTA 0 empty.
+void emu_debug_withhold_load();
 // Launches the slice-product kernel once per k pass; *passes receives the count.
 cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_t stream);
 size_t emu_scratch_bytes(int num_sms);
@@ -240,7 +242,25 @@ int64_t emu_max_k_per_pass(int S, int beta);
 // Products per FP32 accumulation chunk (every partial sum below 2^24), in 64-wide slabs.
 int emu_chunk_slabs(int beta);
 
+// SM count of the current device (looked up once per device ordinal).
 int device_sm_count();
+
+// Kernel attributes (the dynamic shared-memory limit) belong to a device's context, so the
+// "already set" flags of the launchers are kept per device ordinal.  done() / mark() act on the
+// current device; ordinals beyond kMaxDevices are never marked (the attribute is set every call).
+constexpr int kMaxDevices = 64;
+int current_device();
+struct PerDeviceFlag {
+    std::atomic<bool> set[kMaxDevices] = {};
+    bool done() const {
+        const int d = current_device();
+        return d >= 0 && d < kMaxDevices && set[d].load(std::memory_order_acquire);
+    }
+    void mark() {
+        const int d = current_device();
+        if (d >= 0 && d < kMaxDevices) set[d].store(true, std::memory_order_release);
+    }
+};
 
 // ------------------------------------------------------------------ probes
 cudaError_t probe_peak(int kind, double* tflops, cudaStream_t stream);

@@ -19,6 +19,9 @@
 //   * Problems whose scratch does not fit are rejected with MOMMS_ERR_WORKSPACE
 //     before anything is enqueued; the slice count must be given (1..16) because the
 //     data-driven choice needs a host readback.
+//   * A call only enqueues work.  Whether its bounded device waits all finished in time is
+//     recorded in a status word inside the array; momms_noalloc_status() waits for the
+//     stream, returns that word and clears it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,6 +35,7 @@ namespace {
 
 constexpr size_t kNoAllocBytes = size_t(64) << 20;
 constexpr int kNoAllocMaxCtas = 64;  // FP64 recombination blocks kept in the array
+constexpr size_t kStatusOffset = 0;  // the device status word: zero-initialised at load, 0 = no timeout
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -40,6 +44,16 @@ std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Largest m, n or k the carve-up below accepts: the int32 tile and slab arithmetic of the kernels,
+// and every region's byte count stays far inside 64-bit arithmetic.
+constexpr int64_t kNoAllocMaxDim = int64_t(1) << 30;
+
+// a * b * c * d bytes, or SIZE_MAX when the product exceeds the array (no 64-bit wrap-around).
+size_t region_bytes(uint64_t a, uint64_t b, uint64_t c, uint64_t d = 1) {
+    const unsigned __int128 v = static_cast<unsigned __int128>(a) * b * c * d;
+    return v > kNoAllocBytes ? SIZE_MAX : static_cast<size_t>(v);
+}
 
 // Device address of the array on the current device (looked up once per device).
 int scratch_address(void** out) {
@@ -83,6 +97,7 @@ extern "C" int momms_gemm_emulated_noalloc(int op_a, int op_b, int64_t m, int64_
     if (ldc < std::max<int64_t>(1, m)) return -14;
     if (m == 0 || n == 0) return MOMMS_OK;
     if (!work) return MOMMS_ERR_UNSUPPORTED;  // C := beta*C needs no product: use momms_gemm_ex
+    if (m > kNoAllocMaxDim || n > kNoAllocMaxDim || k > kNoAllocMaxDim) return MOMMS_ERR_WORKSPACE;
 
     constexpr int beta_bits = 7;
     const int64_t k_pad = (k + momms::kEmuBK - 1) / momms::kEmuBK * momms::kEmuBK;
@@ -90,15 +105,23 @@ extern "C" int momms_gemm_emulated_noalloc(int op_a, int op_b, int64_t m, int64_
                           ((n + momms::kEmuBNMax - 1) / momms::kEmuBNMax);
     const int ctas = static_cast<int>(std::min<int64_t>(
         {static_cast<int64_t>(momms::device_sm_count()), tiles, static_cast<int64_t>(kNoAllocMaxCtas)}));
-    // carve the array: status word, exponents, flags, digit slices, recombination blocks
-    size_t o = 0;
-    const size_t off_status = o;  o += 256;
+    // carve the array: status word, exponents, flags, digit slices, recombination blocks (each
+    // region's size checked against the array before it is added: no sum can wrap)
+    const size_t digits_a = region_bytes(2, static_cast<uint64_t>(slices), static_cast<uint64_t>(m),
+                                         static_cast<uint64_t>(k_pad));
+    const size_t digits_b = region_bytes(2, static_cast<uint64_t>(slices), static_cast<uint64_t>(n),
+                                         static_cast<uint64_t>(k_pad));
+    if (digits_a == SIZE_MAX || digits_b == SIZE_MAX) return MOMMS_ERR_WORKSPACE;
+    size_t o = kStatusOffset + 256;  // the status word leads the array
     const size_t off_e = o;       o += up256(sizeof(int32_t) * m);
     const size_t off_ef = o;      o += up256(static_cast<size_t>(m));
     const size_t off_f = o;       o += up256(sizeof(int32_t) * n);
     const size_t off_ff = o;      o += up256(static_cast<size_t>(n));
-    const size_t off_Ad = o;      o += up256(size_t(2) * slices * m * k_pad);
-    const size_t off_Bd = o;      o += up256(size_t(2) * slices * n * k_pad);
+    if (o > kNoAllocBytes) return MOMMS_ERR_WORKSPACE;
+    const size_t off_Ad = o;      o += up256(digits_a);
+    if (o > kNoAllocBytes) return MOMMS_ERR_WORKSPACE;
+    const size_t off_Bd = o;      o += up256(digits_b);
+    if (o > kNoAllocBytes) return MOMMS_ERR_WORKSPACE;
     const size_t off_R = o;
     const size_t r_bytes = momms::emu_scratch_bytes_for_ctas(ctas);
     o += up256(r_bytes);
@@ -109,13 +132,14 @@ extern "C" int momms_gemm_emulated_noalloc(int op_a, int op_b, int64_t m, int64_
     if (rc) return rc;
     char* w = static_cast<char*>(base);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    int32_t* status = reinterpret_cast<int32_t*>(w + off_status);
+    int32_t* status = reinterpret_cast<int32_t*>(w + kStatusOffset);
     int32_t* e = reinterpret_cast<int32_t*>(w + off_e);
     uint8_t* ef = reinterpret_cast<uint8_t*>(w + off_ef);
     int32_t* f = reinterpret_cast<int32_t*>(w + off_f);
     uint8_t* ff = reinterpret_cast<uint8_t*>(w + off_ff);
-    // the status word must start at zero; every other region is fully written before it is read
-    if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return MOMMS_ERR_CUDA;
+    // The status word is not cleared here: a timeout of an earlier call stays visible until
+    // momms_noalloc_status() reads and clears it.  Every other region is fully written before it
+    // is read.
     if (momms::launch_emu_scale(0, op_a, m, k, A, lda, e, ef, nullptr, s) != cudaSuccess) return MOMMS_ERR_CUDA;
     if (momms::launch_emu_scale(1, op_b, n, k, B, ldb, f, ff, nullptr, s) != cudaSuccess) return MOMMS_ERR_CUDA;
     if (momms::launch_emu_split(0, op_a, m, k, A, lda, e, ef, slices, beta_bits, w + off_Ad, m, k_pad, s) !=
@@ -136,4 +160,25 @@ extern "C" int momms_gemm_emulated_noalloc(int op_a, int op_b, int64_t m, int64_
     cudaError_t ce = momms::launch_emu_slice_gemm(a, &passes, s);
     if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
     return ce == cudaSuccess ? MOMMS_OK : MOMMS_ERR_CUDA;
+}
+
+extern "C" int momms_noalloc_status(momms_stream_t stream, int* status) {
+    if (!status) return -2;
+    *status = MOMMS_OK;
+    void* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int32_t* word = reinterpret_cast<int32_t*>(static_cast<char*>(base) + kStatusOffset);
+    int32_t v = 0;
+    // the copy waits for every call enqueued on `stream` before it; the clear follows it in order
+    if (cudaMemcpyAsync(&v, word, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    if (v != 0) {
+        if (cudaMemsetAsync(word, 0, sizeof(int32_t), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        *status = v == MOMMS_ERR_TIMEOUT ? MOMMS_ERR_TIMEOUT : MOMMS_ERR_CUDA;
+    }
+    return MOMMS_OK;
 }

@@ -74,12 +74,12 @@ constexpr int kCopyThreads = 1024, kCopySmem = 120 * 1024;
 cudaError_t stream_copy(void* dst, const void* src, size_t bytes, int ctas, int repeats,
                         cudaStream_t stream) {
     if (bytes == 0 || repeats == 0) return cudaSuccess;
-    static std::atomic<bool> attr_set{false};  // idempotent; atomic for concurrent first calls
-    if (!attr_set) {
+    static PerDeviceFlag attr_set;  // idempotent; per device, atomic for concurrent first calls
+    if (!attr_set.done()) {
         cudaError_t e = cudaFuncSetAttribute(probe::copy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kCopySmem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.mark();
     }
     const int sms = device_sm_count();
     const int grid = (ctas <= 0 || ctas > sms) ? sms : ctas;

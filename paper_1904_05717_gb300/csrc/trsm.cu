@@ -86,12 +86,12 @@ cudaError_t launch_tri_inverse(int64_t t, const double* A, int64_t lda, int uplo
     const int64_t blocks = (t + kTrsmNb - 1) / kTrsmNb;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     constexpr size_t smem = 2 * sizeof(double) * kTrsmNb * (kTrsmNb + 1) / 2;
-    static std::atomic<bool> attr_set{false};  // idempotent; atomic for concurrent first calls
-    if (!attr_set) {
+    static PerDeviceFlag attr_set;  // idempotent; per device, atomic for concurrent first calls
+    if (!attr_set.done()) {
         const cudaError_t e =
             cudaFuncSetAttribute(tri_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.mark();
     }
     tri_inverse_kernel<<<static_cast<unsigned>(blocks), kTrsmNb, smem, stream>>>(t, A, lda, uplo, unit, W);
     return cudaGetLastError();

@@ -102,6 +102,10 @@ _SIGS = {
     "momms_gemm_emulated_noalloc": ([_I32, _I32, _I64, _I64, _I64, _I32, _DBL, _VP, _I64, _VP, _I64, _DBL, _VP,
                                      _I64, _VP], _I32),
     "momms_noalloc_scratch_bytes": ([], _SZ),
+    "momms_noalloc_status": ([_VP, ctypes.POINTER(_I32)], _I32),
+    "momms_debug_withhold_load": ([], None),
+    "momms_set_kernel_timing": ([_VP, _I32], _I32),
+    "momms_kernel_timing": ([_VP, ctypes.POINTER(_DBL), ctypes.POINTER(_I64)], _I32),
     "momms_member_tile": ([_I32, _I32, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
                           _I32),
     "momms_tri_tile": ([_I32, _I32, _I64, _I64, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64)],
@@ -266,6 +270,18 @@ def momms_noalloc_scratch_bytes():
     return int(lib().momms_noalloc_scratch_bytes())
 
 
+def momms_debug_withhold_load():
+    """Test hook: the next slice-product launch leaves one stage empty, so its bounded wait runs out."""
+    lib().momms_debug_withhold_load()
+
+
+def momms_noalloc_status(stream=None):
+    """(return code, status word) of the allocation-free calls on the current device; clears the word."""
+    st = _I32(0)
+    rc = lib().momms_noalloc_status(_stream(stream), ctypes.byref(st))
+    return int(rc), int(st.value)
+
+
 def momms_probe_peak(kind, stream=None):
     out = _DBL(0.0)
     check(lib().momms_probe_peak(kind, ctypes.byref(out), _stream(stream)), "momms_probe_peak")
@@ -335,6 +351,15 @@ class Handle:
 
     def device_status(self, stream=None):
         return lib().momms_check_device_status(self.ptr, _stream(stream))
+
+    def set_kernel_timing(self, max_launches):
+        check(lib().momms_set_kernel_timing(self.ptr, max_launches), "momms_set_kernel_timing")
+
+    def kernel_timing(self):
+        """(total ms, launches) of the product launches timed since the last read."""
+        t, c = _DBL(0.0), _I64(0)
+        check(lib().momms_kernel_timing(self.ptr, ctypes.byref(t), ctypes.byref(c)), "momms_kernel_timing")
+        return float(t.value), int(c.value)
 
     def workspace_size(self, m, n, k, op_a=OP_N, op_b=OP_N):
         out = _SZ(0)

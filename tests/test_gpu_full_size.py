@@ -76,6 +76,25 @@ def test_square_8192_auto_as_benchmarked():
     assert np.array_equal(C[np.ix_(rs, cs)], Co)
 
 
+def test_square_16384_auto_as_benchmarked():
+    # the largest square of the shape sweep (bench --size 16384): AUTO plan as timed; 26 sampled rows
+    # and columns against the oracle, Freivalds on all of C, sampled elements bit for bit against the
+    # definition of the modular result
+    n = 16384
+    A = syn.matrix("uniform", n, n, syn.workload_seed(1, "A"))
+    B = syn.matrix("uniform", n, n, syn.workload_seed(1, "B"))
+    C0 = syn.matrix("uniform", n, n, syn.workload_seed(1, "C"))
+    C, rep = run(A, B, C0, M.MODE_AUTO)
+    assert rep["mode"] == M.MODE_EMULATED and rep["moduli"] > 0
+    assert sample_ratio(A, B, C0, C, 1.0, 1.0) <= 1.0
+    assert freivalds_ok(A, B, C0, C, 1.0, 1.0)
+    rs = np.array([0, 127, 128, 9000, 16383])
+    cs = np.array([0, 191, 192, 12345, 16383])
+    Co, _ = oracle.modular_dgemm(np.asfortranarray(A[rs, :]), np.asfortranarray(B[:, cs]), rep["operand_bits"],
+                                 np.asfortranarray(C0[np.ix_(rs, cs)]), 1.0, 1.0)
+    assert np.array_equal(C[np.ix_(rs, cs)], Co)
+
+
 def test_square_8192_slices():
     n = 8192
     A = syn.matrix("uniform", n, n, syn.workload_seed(1, "A"))
