@@ -78,6 +78,10 @@ def parse():
     p.add_argument("--slices", type=int, default=0, help="emulated slice count (0 = from the data)")
     p.add_argument("--group", type=int, default=0, help="C2 raster group in tile rows (0 = library default)")
     p.add_argument("--ctas", type=int, default=0, help="grid cap of the product launch (0 = library default)")
+    p.add_argument("--cta-pairs", default="auto", choices=["auto", "off", "on"],
+                   help="residue products on CTA pairs (momms_set_cta_pairs)")
+    p.add_argument("--plan", default="device", choices=["device", "host"],
+                   help="where the data-driven slice count is chosen (momms_set_plan_on_device)")
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--native-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -446,6 +450,8 @@ def main():
     h = M.Handle(mode=mode, member=member, slices=args.slices, scheme=SCHEMES[args.scheme])
     h.set_raster_group(args.group)
     h.set_max_ctas(args.ctas)
+    h.set_cta_pairs({"auto": 0, "off": 1, "on": 2}[args.cta_pairs])
+    h.set_plan_on_device(1 if args.plan == "device" else 0)
 
     def step():
         M.check(M.momms_gemm_ex(h, 0, 0, m, n, k, 1.0, dA.ptr, dA.ld, dB.ptr, dB.ld, 1.0, dC.ptr, dC.ld, stream),
@@ -507,7 +513,9 @@ def main():
                                                  int(rep["member"]), res.data_ptr(), scratch.data_ptr(), nbytes,
                                                  st.data_ptr(), stream), "residue gemm")
             products = n_mod
-            kernel = (f"momms::emu::slice_gemm_kernel<{int(rep['tile_n'])}, 0, 1, 0> (tcgen05 kind::f16; modular "
+            kernel = ("momms::emu::residue_pair_kernel (tcgen05.mma.cta_group::2 kind::f16, 256 x 192 tiles on CTA "
+                      "pairs; modular encoding: one residue product per modulus)" if rep["cta_pairs"] else
+                      f"momms::emu::slice_gemm_kernel<{int(rep['tile_n'])}, 0, 1> (tcgen05 kind::f16; modular "
                       f"encoding: one residue product per modulus)")
             capture = NCU_RESIDUE_CAPTURE
         else:
@@ -681,6 +689,7 @@ def main():
                        "encoding": ("moduli" if n_mod else "slices") if emulated else None,
                        "member": M.MEMBER_NAMES.get(int(rep["member"]), "auto"),
                        "raster_group": int(rep["group"]), "ctas": int(rep["ctas"]),
+                       "cta_pairs": int(rep["cta_pairs"]), "plan": args.plan,
                        "l2": "operands exceed L2 (126 MB) at the default size: no flush between steps",
                        "replicas": world},
             "roofline": roof,

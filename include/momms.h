@@ -105,6 +105,7 @@ typedef struct {
     int moduli;          /* emulated, modular encoding: N moduli (0: digit slices)   */
     int operand_bits;    /* emulated: integer width of the operands (7 S for slices) */
     int crt_fused;       /* moduli: 1 when the residue product rebuilt C itself       */
+    int cta_pairs;       /* moduli: 1 when the residue products ran on CTA pairs      */
 } momms_report_t;
 
 /* ---------------------------------------------------------------- handles */
@@ -146,6 +147,23 @@ int momms_set_scheme(momms_handle_t handle, int scheme);
  * products wait behind them -- 11.9 against 10.4 ms per 8192^3 step).  Returns -2 for other
  * values. */
 int momms_set_crt_fusion(momms_handle_t handle, int mode);
+/* Where a product with the data-driven slice count (slices = 0, EMULATED or AUTO mode) makes its
+ * choices.  1 (default) = on the device: a one-thread kernel after the scaling pass turns the
+ * measured spreads into S, the operand width and the encoding, and every later kernel of the
+ * product reads that plan when it starts (the kernels of the encoding not chosen return at once),
+ * so the call only enqueues work and can be captured in a CUDA graph once its workspace exists;
+ * the report's slices / moduli / operand_bits / est_err_ratio are fetched from the device when
+ * momms_get_last_report is called.  0 = on the host: the spreads are read back (the call waits
+ * for them) and only the chosen encoding's kernels are launched.  Both give the same plan and the
+ * same C.  Triangular updates (momms_syrk) always choose on the host.  Returns -2 for other values. */
+int momms_set_plan_on_device(momms_handle_t handle, int on);
+/* CTA pairs for the modular encoding's residue products (192-wide tiles, no triangle or k-range
+ * skipping): two CTAs of a cluster share each MMA (tcgen05.mma.cta_group::2, M = 256) on a
+ * 256 x 192 tile, each staging its own 128 rows of A and 96 rows of B.  Per MMA flop a CTA's shared
+ * memory is written and read 30 % less than with one CTA per 128 x 192 tile, and L2 sends 30 %
+ * fewer operand bytes.  Both CTAs load only their own tiles (no shared loads).  Results are
+ * bit-identical either way.  0 = automatic, 1 = off, 2 = on.  Returns -2 for other values. */
+int momms_set_cta_pairs(momms_handle_t handle, int mode);
 /* Caps the grid of the single-product launches of this handle at `ctas` CTAs that each
  * loop over their share of the member's tiles (0 = default: one CTA per SM for the
  * emulated slice products, one CTA per tile for the native kernel).  Fewer CTAs lower
@@ -168,6 +186,9 @@ int momms_set_raster_group(momms_handle_t handle, int group);
  * (small products: more SMs at work), else 192.  Results are bit-identical either way.
  * Single-product calls only.  Returns -2 for other values. */
 int momms_set_tile_n(momms_handle_t handle, int tile_n);
+/* What the handle's last call used.  When that call chose its slice count on the device
+ * (momms_set_plan_on_device), the plan is copied back from the device here, which waits for the
+ * work already enqueued; a replayed CUDA graph of such a call updates it again. */
 int momms_get_last_report(momms_handle_t handle, momms_report_t* report);
 /* Device status word of the handle (0 = fine, MOMMS_ERR_TIMEOUT after a capped
  * wait expired).  Synchronises `stream` first.  Clears the word. */

@@ -25,6 +25,9 @@ namespace {
 constexpr int kHandleMagic = 0x4D4F4D53;  // "MOMS"
 constexpr int kDigitBits = 7;             // beta: 7-bit digits, FP32 chunk of 1024 products
 constexpr int kAutoSliceMax = 14;         // workspace sized for this many slices in AUTO
+// Whether the residue product runs on CTA pairs (one MMA over two SMs) when the handle says AUTO.
+constexpr bool kCtaPairsAuto = false;
+bool pairs_on(int mode) { return mode == 2 || (mode == 0 && kCtaPairsAuto); }
 
 struct Plan {
     int mode;
@@ -58,12 +61,19 @@ struct momms_handle_s {
     int group = 0;                  // C2 raster group in tile rows (0 = default)
     int scheme = MOMMS_SCHEME_AUTO; // integer encoding of the emulated product
     int crt_fusion = 0;             // 0 auto, 1 separate reconstruction launch, 2 fused
+    int cta_pairs = 0;              // 0 auto, 1 off, 2 on: residue products on CTA pairs (cta_group::2)
     void* user_ws = nullptr;
     size_t user_ws_bytes = 0;
     void* own_ws = nullptr;
     size_t own_ws_bytes = 0;
     int32_t* status = nullptr;  // device word
     int* spread_dev = nullptr;  // device pair of spread values (AUTO slice rule)
+    bool plan_mode = true;               // data-driven S chosen on the device (else: host readback)
+    momms::EmuPlan* plan_dev = nullptr;  // device plan of the last data-driven product
+    bool report_pending = false;         // the report's S / moduli / width are still in plan_dev
+    int64_t ntab_k = -1;                 // contraction length and scheme the plan table was built for
+    int ntab_scheme = -1;
+    momms::EmuPlanTable ntab{};
     int* spread_host = nullptr; // pinned
     cudaEvent_t spread_ready = nullptr;
     int last_auto_slices = 6;   // speculative slice count for the next AUTO call
@@ -100,6 +110,11 @@ struct momms_handle_s {
 namespace {
 
 bool valid(momms_handle_t h) { return h && h->magic == kHandleMagic; }
+
+void reset_report(momms_handle_t h) {
+    h->report = momms_report_t{};
+    h->report_pending = false;
+}
 
 int cuda_fail(cudaError_t e) {
     if (e == cudaSuccess) return MOMMS_OK;
@@ -231,11 +246,17 @@ int scale_c(int64_t m, int64_t n, double beta, double* C, int64_t ldc, cudaStrea
 // uniform, normal and (u - 0.5) exp(phi g) inputs (phi = 1, 2, 4) at k = 64..16384
 // and hold every case there at least 10x inside the bound; the result is clamped
 // to [3, 14].
-int slices_from_spread(double spread_a, double spread_b, int64_t k, int beta, double* bits_out) {
+// The k-dependent part of the rule: bits = rule_c0(k) + 1.25 (s_A + s_B).  The device plan kernel
+// evaluates the same expression with the same IEEE operations in the same order.
+double rule_c0(int64_t k) {
     const double L = std::log2(static_cast<double>(std::max<int64_t>(k, 1)));
-    const double bits = 55.25 + 1.25 * (spread_a + spread_b) - 1.5 * L + 1.5 * std::max(0.0, 12.0 - L);
+    return 55.25 - 1.5 * L + 1.5 * std::max(0.0, 12.0 - L);
+}
+
+int slices_from_spread(double spread_a, double spread_b, int64_t k, int beta, double* bits_out) {
+    const double bits = rule_c0(k) + 1.25 * (spread_a + spread_b);
     if (bits_out) *bits_out = bits;
-    int S = static_cast<int>(std::ceil(bits / beta));
+    int S = static_cast<int>(std::ceil(bits / static_cast<double>(beta)));
     return std::min(std::max(S, 3), kAutoSliceMax);
 }
 
@@ -271,7 +292,7 @@ int run_native(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t
                                               member, h->max_ctas, h->group, s, &ctas, &group);
     if (e == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return MOMMS_ERR_CUDA;
-    h->report = momms_report_t{};
+    reset_report(h);
     h->report.ctas = ctas;
     h->report.group = group;
     h->report.mode = MOMMS_MODE_NATIVE;
@@ -328,10 +349,176 @@ struct KernelTimer {
 // modular encoding's residue products skip each tile's zero k range (EmuGemmArgs::kcap).
 constexpr int kSlicesChosen = 1;
 
+// Reconstruction constants of every moduli count (built once per handle).
+const momms::CrtReconSet& crt_set(momms_handle_t h) {
+    if (!h->crt_set) {
+        h->crt_set.reset(new momms::CrtReconSet{});
+        for (int nm = 1; nm <= momms::kCrtMaxModuli; ++nm) {
+            momms::CrtConsts cn;
+            momms::crt_consts(nm, 0, &cn, &h->crt_set->by_n[nm]);
+        }
+    }
+    return *h->crt_set;
+}
+
+// The plan table of the device plan kernel for contraction length k: the rule's constant and the
+// moduli count of every operand width (cached per handle for the last k and scheme).
+const momms::EmuPlanTable& plan_table(momms_handle_t h, int64_t k, int n_alloc) {
+    if (h->ntab_k != k || h->ntab_scheme != h->scheme || h->ntab.n_alloc != n_alloc) {
+        momms::EmuPlanTable& t = h->ntab;
+        t = momms::EmuPlanTable{};
+        t.c0 = rule_c0(k);
+        t.smax = kAutoSliceMax;
+        t.n_alloc = n_alloc;
+        t.scheme_moduli = h->scheme == MOMMS_SCHEME_MODULI;
+        t.tri = 0;
+        for (int w = 1; w <= momms::kPlanMaxBits && n_alloc > 0; ++w) {
+            momms::CrtConsts c;
+            momms::CrtRecon r;
+            t.ntab[w] = momms::crt_plan(w, k, &c, &r) ? static_cast<uint8_t>(c.N) : 0;
+        }
+        h->ntab_k = k;
+        h->ntab_scheme = h->scheme;
+    }
+    return h->ntab;
+}
+
+// The data-driven product with every choice made on the device: scale and spreads, the plan kernel
+// (S, operand width, moduli or slices), then both encodings' splits and products and the
+// reconstruction, each reading the plan at launch time and returning at once when the plan chose
+// the other encoding.  Nothing is read back, so the call only enqueues work (and can be captured
+// in a CUDA graph once the workspace exists).  The report's slice count, moduli and width are
+// fetched from the plan when the report is asked for.
+int run_emulated_planned(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
+                         const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                         int64_t ldc, int member, cudaStream_t s, int kcap) {
+    const int bb = h->digit_bits;
+    const int S_alloc = kAutoSliceMax;
+    const int N_alloc = k <= momms::crt_max_k() ? moduli_reserved(h->scheme, 0, k) : 0;  // one exact pass
+    EmuLayout L = emu_layout(m, n, k, S_alloc, h->max_ctas, N_alloc);
+    if (std::max(L.m_pad, L.n_pad) > (int64_t(1) << 30)) return MOMMS_ERR_UNSUPPORTED;
+    void* ws = nullptr;
+    int rc = ensure_workspace(h, L.total, &ws);
+    if (rc) return rc;
+    rc = ensure_aux(h);
+    if (rc) return rc;
+    char* w = static_cast<char*>(ws);
+    int32_t* e = reinterpret_cast<int32_t*>(w + L.off_e);
+    uint8_t* ef = reinterpret_cast<uint8_t*>(w + L.off_ef);
+    float* l1a = reinterpret_cast<float*>(w + L.off_l1a);
+    int32_t* f = reinterpret_cast<int32_t*>(w + L.off_f);
+    uint8_t* ff = reinterpret_cast<uint8_t*>(w + L.off_ff);
+    float* l1b = reinterpret_cast<float*>(w + L.off_l1b);
+    void* Ad = w + L.off_Ad;
+    void* Bd = w + L.off_Bd;
+    uint8_t* res = reinterpret_cast<uint8_t*>(w + L.off_res);
+    const momms::EmuPlanTable& table = plan_table(h, k, N_alloc);
+    const momms::CrtReconSet& set = crt_set(h);
+    cudaStream_t sb = h->aux;
+    int64_t launches = 0;
+    auto fork = [&]() {
+        return cudaEventRecord(h->ev_fork, s) == cudaSuccess && cudaStreamWaitEvent(sb, h->ev_fork, 0) == cudaSuccess;
+    };
+    // statistics of A on the caller's stream, of B on the second stream, then the plan
+    if (cudaMemsetAsync(h->spread_dev, 0, 2 * sizeof(int), s) != cudaSuccess || !fork()) return MOMMS_ERR_CUDA;
+    if (momms::launch_emu_scale(0, opa, m, k, A, lda, e, ef, l1a, s) != cudaSuccess ||
+        momms::launch_emu_scale(1, opb, n, k, B, ldb, f, ff, l1b, sb) != cudaSuccess ||
+        momms::launch_emu_spread(m, k, e, ef, l1a, h->spread_dev, s) != cudaSuccess ||
+        momms::launch_emu_spread(n, k, f, ff, l1b, h->spread_dev + 1, sb) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    launches += momms::emu_scale_kernel_count(0, opa) + momms::emu_scale_kernel_count(1, opb) + 2;
+    rc = join_aux(h, s);
+    if (rc) return rc;
+    if (momms::launch_emu_plan(h->spread_dev, table, h->plan_dev, s) != cudaSuccess) return MOMMS_ERR_CUDA;
+    launches += 1;
+    // both encodings' operand passes (the one the plan did not choose returns at once)
+    if (!fork()) return MOMMS_ERR_CUDA;
+    momms::CrtConsts call;
+    momms::CrtRecon rall;
+    momms::crt_consts(momms::kCrtMaxModuli, 56, &call, &rall);  // every modulus; N and width from the plan
+    if (N_alloc > 0) {
+        if (momms::launch_emu_residues(0, opa, m, k, A, lda, e, ef, call, Ad, L.m_pad, L.k_pad, s, h->plan_dev) !=
+                cudaSuccess ||
+            momms::launch_emu_residues(1, opb, n, k, B, ldb, f, ff, call, Bd, L.n_pad, L.k_pad, sb, h->plan_dev) !=
+                cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        launches += 2;
+    }
+    if (momms::launch_emu_split(0, opa, m, k, A, lda, e, ef, S_alloc, bb, Ad, L.m_pad, L.k_pad, s, 0, h->plan_dev) !=
+            cudaSuccess ||
+        momms::launch_emu_split(1, opb, n, k, B, ldb, f, ff, S_alloc, bb, Bd, L.n_pad, L.k_pad, sb, 0, h->plan_dev) !=
+            cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    launches += 2;
+    rc = join_aux(h, s);
+    if (rc) return rc;
+    momms::EmuGemmArgs a{};
+    a.m = m; a.n = n; a.k = k; a.beta = bb;
+    a.Ad = Ad; a.Bd = Bd; a.m_pad = L.m_pad; a.n_pad = L.n_pad; a.k_pad = L.k_pad;
+    a.e = e; a.ef = ef; a.f = f; a.ff = ff;
+    a.alpha = alpha; a.beta_c = beta; a.C = C; a.ldc = ldc;
+    a.member = member; a.group = h->group;
+    a.scratch = w + L.off_scratch; a.scratch_bytes = L.scratch_bytes;
+    a.status = h->status; a.max_ctas = h->max_ctas; a.tile_n = h->tile_n;
+    a.plan = h->plan_dev;
+    int passes = 0, used_ctas = 0, used_group = 0, used_launches = 0, used_pairs = 0;
+    a.used_ctas = &used_ctas; a.used_group = &used_group; a.used_launches = &used_launches;
+    a.used_pairs = &used_pairs;
+    // the digit encoding's products (nothing to do when the plan chose moduli) ...
+    momms::EmuGemmArgs as = a;
+    as.S = S_alloc;
+    cudaError_t ce;
+    {
+        std::unique_ptr<KernelTimer> timer;  // (with moduli possible, the modular launch below is the one timed)
+        if (N_alloc == 0) timer.reset(new KernelTimer(h, s));
+        ce = momms::launch_emu_slice_gemm(as, &passes, s);
+        if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        if (timer) timer->done();
+        launches += used_launches;
+    }
+    // ... and the modular encoding's residue products and reconstruction (nothing when it chose slices)
+    if (N_alloc > 0) {
+        momms::EmuGemmArgs am = a;
+        am.S = momms::kCrtMaxModuli;
+        am.crt = &call;
+        am.res = res;
+        am.kcap = kcap;
+        am.cta_pairs = pairs_on(h->cta_pairs) ? 1 : 0;
+        int mpasses = 0;
+        KernelTimer timer(h, s);
+        ce = momms::launch_emu_slice_gemm(am, &mpasses, s);
+        if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
+        if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+        timer.done();
+        launches += used_launches;
+        if (momms::launch_crt_reconstruct_plan(m, n, res, set, h->plan_dev, e, ef, f, ff, alpha, beta, C, ldc, s) !=
+            cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        launches += 1;
+    }
+    reset_report(h);
+    h->report.ctas = used_ctas;
+    h->report.group = used_group;
+    h->report.mode = MOMMS_MODE_EMULATED;
+    h->report.member = member;
+    h->report.digit_bits = bb;
+    h->report.k_passes = passes;
+    h->report.tile_m = momms::kEmuBM;
+    h->report.tile_n = momms::emu_pick_bn(m, n, k, h->tile_n, N_alloc > 0 ? N_alloc : 1);
+    h->report.launches = launches;
+    h->report.cta_pairs = used_pairs;
+    h->report_pending = true;  // slices, moduli, operand_bits and est_err_ratio come from the plan
+    return MOMMS_OK;
+}
+
 int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64_t k, double alpha,
                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                  int64_t ldc, int member, int S, cudaStream_t s, int tri = 0, int kcap = 0) {
     const int bb = h->digit_bits;
+    h->report_pending = false;
+    if (S == 0 && !tri && bb == kDigitBits && h->plan_mode)
+        return run_emulated_planned(h, opa, opb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, member, s, kcap);
     if (tri && (m != n || A != B || opa == opb)) return MOMMS_ERR_UNSUPPORTED;
     if (S > MOMMS_MAX_SLICES) return MOMMS_ERR_UNSUPPORTED;
     const int S_alloc = S > 0 ? S : kAutoSliceMax;
@@ -457,13 +644,15 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     a.member = member; a.group = h->group;
     a.scratch = scratch; a.scratch_bytes = L.scratch_bytes;
     a.status = h->status; a.max_ctas = h->max_ctas; a.tile_n = h->tile_n;
-    int passes = 0, used_ctas = 0, used_group = 0, used_launches = 0;
+    int passes = 0, used_ctas = 0, used_group = 0, used_launches = 0, used_pairs = 0;
     a.used_ctas = &used_ctas; a.used_group = &used_group; a.used_launches = &used_launches;
+    a.used_pairs = &used_pairs;
     // the reconstruction inside the residue product's epilogue (the last modulus of each tile) only
     // on request: measured slower than the separate launch (8192^3: 11.9 against 10.4 ms per step --
     // twelve drain warps per SM rebuild C at a fraction of the separate kernel's rate and stall the
     // products behind them)
     const bool fuse = mod && h->crt_fusion == 2 && !tri;
+    a.cta_pairs = pairs_on(h->cta_pairs) ? 1 : 0;
     if (mod) {
         a.crt = &cc;
         a.res = res;
@@ -492,7 +681,7 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
         launches += 1;
     }
-    h->report = momms_report_t{};
+    reset_report(h);
     h->report.ctas = used_ctas;
     h->report.group = used_group;
     h->report.mode = MOMMS_MODE_EMULATED;
@@ -507,6 +696,7 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
     h->report.moduli = mod ? cc.N : 0;
     h->report.operand_bits = mod ? mbits : bb * S;
     h->report.crt_fused = fuse ? 1 : 0;
+    h->report.cta_pairs = used_pairs;
     return MOMMS_OK;
 }
 
@@ -762,23 +952,16 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
             scratch_bytes, h->status, s);
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
         // C of the modular problems by the Chinese remainder theorem (the constants by moduli count)
-        if (!h->crt_set) {
-            h->crt_set.reset(new momms::CrtReconSet{});
-            for (int nm = 1; nm <= momms::kCrtMaxModuli; ++nm) {
-                momms::CrtConsts cn;
-                momms::crt_consts(nm, 0, &cn, &h->crt_set->by_n[nm]);
-            }
-        }
         ce = momms::launch_crt_reconstruct_batched(reinterpret_cast<const momms::CrtBatchProblem*>(tb + off_mod[3]),
                                                    reinterpret_cast<const int2*>(tb + off_mod[4]),
-                                                   (int)crt_items.size(), *h->crt_set, s);
+                                                   (int)crt_items.size(), crt_set(h), s);
         if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
         launches += 2;
     }
     int smax = 0;
     for (int i = 0; i < count; ++i)
         if (!mod[i]) smax = std::max(smax, S[i]);
-    h->report = momms_report_t{};
+    reset_report(h);
     h->report.mode = MOMMS_MODE_EMULATED;
     h->report.member = MOMMS_MEMBER_AUTO;
     h->report.slices = smax;
@@ -795,11 +978,11 @@ int gemm_dispatch(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int6
                   const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                   int64_t ldc, cudaStream_t s) {
     if (m == 0 || n == 0) {
-        h->report = momms_report_t{};
+        reset_report(h);
         return MOMMS_OK;
     }
     if (k == 0 || alpha == 0.0) {
-        h->report = momms_report_t{};
+        reset_report(h);
         h->report.launches = beta == 1.0 ? 0 : 1;
         return scale_c(m, n, beta, C, ldc, s);
     }
@@ -862,17 +1045,18 @@ int momms_create(momms_handle_t* handle) {
     *handle = nullptr;
     momms_handle_t h = new (std::nothrow) momms_handle_s();
     if (!h) return MOMMS_ERR_ALLOC;
-    if (cudaMalloc(&h->status, 64) != cudaSuccess) {
+    if (cudaMalloc(&h->status, 128) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return MOMMS_ERR_ALLOC;
     }
     h->spread_dev = reinterpret_cast<int*>(reinterpret_cast<char*>(h->status) + 16);
+    h->plan_dev = reinterpret_cast<momms::EmuPlan*>(reinterpret_cast<char*>(h->status) + 64);
     if (cudaEventCreateWithFlags(&h->spread_ready, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         h->spread_ready = nullptr;
     }
-    if (cudaMemset(h->status, 0, 64) != cudaSuccess ||
+    if (cudaMemset(h->status, 0, 128) != cudaSuccess ||
         cudaMallocHost(&h->spread_host, 2 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->status);
@@ -970,6 +1154,20 @@ int momms_kernel_timing(momms_handle_t h, double* total_ms, int64_t* launches) {
     return MOMMS_OK;
 }
 
+int momms_set_plan_on_device(momms_handle_t h, int on) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (on != 0 && on != 1) return -2;
+    h->plan_mode = on != 0;
+    return MOMMS_OK;
+}
+
+int momms_set_cta_pairs(momms_handle_t h, int mode) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (mode < 0 || mode > 2) return -2;
+    h->cta_pairs = mode;
+    return MOMMS_OK;
+}
+
 int momms_set_crt_fusion(momms_handle_t h, int mode) {
     if (!valid(h)) return MOMMS_ERR_HANDLE;
     if (mode < 0 || mode > 2) return -2;
@@ -1008,6 +1206,15 @@ int momms_set_raster_group(momms_handle_t h, int group) {
 int momms_get_last_report(momms_handle_t h, momms_report_t* r) {
     if (!valid(h)) return MOMMS_ERR_HANDLE;
     if (!r) return -2;
+    if (h->report_pending) {
+        // the last product chose its slice count on the device: its plan holds what it used
+        momms::EmuPlan pl{};
+        if (cudaMemcpy(&pl, h->plan_dev, sizeof(pl), cudaMemcpyDeviceToHost) != cudaSuccess) return MOMMS_ERR_CUDA;
+        h->report.slices = pl.S;
+        h->report.moduli = pl.N;
+        h->report.operand_bits = pl.bits;
+        h->report.est_err_ratio = pl.est;  // (kept pending: a graph replay updates the plan again)
+    }
     *r = h->report;
     return MOMMS_OK;
 }
@@ -1167,7 +1374,7 @@ int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const 
             idx.push_back(i);
         }
         if (idx.empty()) {
-            h->report = momms_report_t{};
+            reset_report(h);
             h->report.launches = launches;
             return MOMMS_OK;
         }
@@ -1203,7 +1410,7 @@ int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const 
         probs.push_back(p);
     }
     if (probs.empty()) {
-        h->report = momms_report_t{};
+        reset_report(h);
         h->report.launches = scale_only;
         return MOMMS_OK;
     }
@@ -1233,7 +1440,7 @@ int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const 
     }
     cudaError_t e = momms::launch_native_batched(h->dev_probs, static_cast<int>(probs.size()), tiles, s);
     if (e != cudaSuccess) return MOMMS_ERR_CUDA;
-    h->report = momms_report_t{};
+    reset_report(h);
     h->report.mode = MOMMS_MODE_NATIVE;
     h->report.member = MOMMS_MEMBER_C2;
     h->report.tile_m = momms::kNativeBM;
@@ -1397,6 +1604,7 @@ int momms_emu_residue_gemm(int64_t m, int64_t n, int64_t k, int bits, const void
     a.scratch = scratch; a.scratch_bytes = scratch_bytes; a.status = status; a.max_ctas = 0; a.tile_n = 0;
     a.crt = &c;
     a.res = res;
+    a.cta_pairs = pairs_on(0) ? 1 : 0;
     int passes = 0;
     cudaError_t ce = momms::launch_emu_slice_gemm(a, &passes, reinterpret_cast<cudaStream_t>(stream));
     if (ce == cudaErrorInvalidValue) return MOMMS_ERR_UNSUPPORTED;
@@ -1659,7 +1867,7 @@ int run_syrk_emulated(momms_handle_t h, int uplo, int trans, int64_t n, int64_t 
         launches += 1;
         off += sizeof(momms::EmuBatchProblem) * static_cast<size_t>(tiles_m);
     }
-    h->report = momms_report_t{};
+    reset_report(h);
     h->report.mode = MOMMS_MODE_EMULATED;
     h->report.member = MOMMS_MEMBER_AUTO;
     h->report.slices = S;
@@ -1688,7 +1896,7 @@ int momms_syrk(momms_handle_t h, int uplo, int trans, int64_t n, int64_t k, doub
     if (n > (int64_t(1) << 30) || k > (int64_t(1) << 30)) return MOMMS_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int tri = uplo == MOMMS_LOWER ? 1 : 2;
-    h->report = momms_report_t{};
+    reset_report(h);
     if (n == 0) return MOMMS_OK;
     if (!product) {
         h->report.launches = beta == 1.0 ? 0 : 1;
@@ -1758,7 +1966,7 @@ int momms_trmm(momms_handle_t h, int side, int uplo, int trans, int diag, int64_
     if (m > 0 && n > 0 && alpha != 0.0 && !A) return -9;
     if (m > 0 && n > 0 && !B) return -11;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    h->report = momms_report_t{};
+    reset_report(h);
     if (m == 0 || n == 0) return MOMMS_OK;
     if (alpha == 0.0) {
         h->report.launches = 1;
@@ -1978,7 +2186,7 @@ int momms_trsm(momms_handle_t h, int side, int uplo, int trans, int diag, int64_
     if (m > 0 && n > 0 && alpha != 0.0 && !A) return -9;
     if (m > 0 && n > 0 && !B) return -11;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    h->report = momms_report_t{};
+    reset_report(h);
     if (m == 0 || n == 0) return MOMMS_OK;
     if (alpha == 0.0) {
         h->report.launches = 1;

@@ -51,18 +51,16 @@ uint32_t inverse_mod(uint32_t a, uint32_t p) {  // a^-1 mod p (gcd(a, p) = 1)
 // C) reads and writes C as two double2.  L = 3 when P < 2^96, else 4.  The modulus loop keeps
 // few registers live, so that many warps hide the load latency.
 template <int V, bool CV, int L>
-__global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
-                                                  const __grid_constant__ CrtRecon r,
-                                                  const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
-                                                  const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
-                                                  double alpha, double beta, double* __restrict__ C, int64_t ldc,
-                                                  int tri) {
+__device__ __forceinline__ void crt_columns(int64_t m, int64_t n, const uint8_t* __restrict__ res, const CrtRecon& r,
+                                            int bits, const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
+                                            const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
+                                            double alpha, double beta, double* __restrict__ C, int64_t ldc, int tri) {
     const int64_t mn = m * n;
     const int64_t groups = m / V;
     const bool unit_alpha = alpha == 1.0, beta_zero = beta == 0.0;
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
-        const int Ej = f[j] - 2 * r.bits;
+        const int Ej = f[j] - 2 * bits;
         const bool fj = ff[j] != 0;
         // a triangle (m = n): rows i >= j (lower) or i <= j (upper) of column j; the groups of V
         // rows that hold the diagonal element are written element by element
@@ -129,6 +127,33 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
     }
 }
 
+template <int V, bool CV, int L>
+__global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
+                                                  const __grid_constant__ CrtRecon r,
+                                                  const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
+                                                  const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
+                                                  double alpha, double beta, double* __restrict__ C, int64_t ldc,
+                                                  int tri) {
+    crt_columns<V, CV, L>(m, n, res, r, r.bits, e, ef, f, ff, alpha, beta, C, ldc, tri);
+}
+
+// The same with the moduli count and the operand width from the device plan (the constants of
+// every count in `set`); returns at once when the plan chose digit slices.
+template <int V, bool CV>
+__global__ void __launch_bounds__(256) crt_plan_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
+                                                       const __grid_constant__ CrtReconSet set,
+                                                       const EmuPlan* __restrict__ plan,
+                                                       const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
+                                                       const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
+                                                       double alpha, double beta, double* __restrict__ C,
+                                                       int64_t ldc) {
+    const int N = plan->N;
+    if (N < 1 || N > kCrtMaxModuli) return;
+    const CrtRecon& r = set.by_n[N];
+    if (r.Pw[3] == 0) crt_columns<V, CV, 3>(m, n, res, r, plan->bits, e, ef, f, ff, alpha, beta, C, ldc, 0);
+    else crt_columns<V, CV, 4>(m, n, res, r, plan->bits, e, ef, f, ff, alpha, beta, C, ldc, 0);
+}
+
 // One column of one problem of a batch: the warp's lanes take its rows 32 apart, one element
 // each (byte loads, 32 consecutive bytes per warp and modulus), the arithmetic of crt_kernel.
 template <int L>
@@ -170,6 +195,30 @@ cudaError_t launch_crt_reconstruct_batched(const CrtBatchProblem* probs, const i
                                            const CrtReconSet& set, cudaStream_t stream) {
     if (n_items <= 0) return cudaSuccess;
     crt_batch_kernel<<<static_cast<unsigned>(n_items), 256, 0, stream>>>(probs, items, set);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crt_reconstruct_plan(int64_t m, int64_t n, const uint8_t* res, const CrtReconSet& set,
+                                        const EmuPlan* plan, const int32_t* e, const uint8_t* ef, const int32_t* f,
+                                        const uint8_t* ff, double alpha, double beta, double* C, int64_t ldc,
+                                        cudaStream_t stream) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    const bool vec = m % 4 == 0 && reinterpret_cast<uintptr_t>(res) % 4 == 0;
+    const bool cvec = vec && ldc % 2 == 0 && reinterpret_cast<uintptr_t>(C) % 16 == 0;
+    const int64_t groups = vec ? m / 4 : m;
+    int64_t bx = (groups + 255) / 256;
+    if (bx > 64) bx = 64;
+    const int64_t want = static_cast<int64_t>(device_sm_count()) * 16;
+    int64_t by = (want + bx - 1) / bx;
+    if (by > n) by = n;
+    if (by > 65535) by = 65535;
+    const dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(by));
+    if (cvec)
+        crt_plan_kernel<4, true><<<grid, 256, 0, stream>>>(m, n, res, set, plan, e, ef, f, ff, alpha, beta, C, ldc);
+    else if (vec)
+        crt_plan_kernel<4, false><<<grid, 256, 0, stream>>>(m, n, res, set, plan, e, ef, f, ff, alpha, beta, C, ldc);
+    else
+        crt_plan_kernel<1, false><<<grid, 256, 0, stream>>>(m, n, res, set, plan, e, ef, f, ff, alpha, beta, C, ldc);
     return cudaGetLastError();
 }
 

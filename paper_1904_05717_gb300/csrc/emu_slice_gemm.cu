@@ -133,6 +133,12 @@ struct Params {
     // first stage but issues no copy into it, so the MMA thread's bounded wait on that stage runs
     // out -- the abort, drain and status path runs without any fault.
     int withhold;
+    // Device plan (single problem, AUTO slice count): plan_kind 1 = this is the modular launch (N
+    // moduli from the plan, nothing to do when it chose slices), 2 = the digit launch (S from the
+    // plan and its group ends from group_end_by_s, nothing to do when it chose moduli); 0 = none.
+    const EmuPlan* plan;
+    int plan_kind;
+    uint32_t group_end_by_s[17];
     int crt_L;                // limbs of the reconstruction arithmetic (3: P < 2^96, else 4)
     int crt_bits;             // integer width of the operands
     int* done;                // per tile: moduli whose residues are stored
@@ -143,6 +149,14 @@ struct Params {
     uint32_t modmagic[kCrtMaxModuli];  // floor(2^32 / p) + 1
     uint32_t modoff[kCrtMaxModuli];    // p ceil(2^31 / p): makes any int32 sum a uint32 of equal residue
 };
+
+// S of the single problem (moduli for the modular launch): the launch's, or the device plan's (0
+// when the plan chose the other encoding).
+MOMMS_DEV int one_S(const Params& p) {
+    if (p.plan_kind == 0) return p.one.S;
+    const int N = p.plan->N;
+    return p.plan_kind == 1 ? N : (N != 0 ? 0 : p.plan->S);
+}
 
 // The it-th tile of this CTA: its problem (-1 = the single problem of p.one) and tile
 // coordinates.  A single problem uses the member's tile order; a batch walks the
@@ -181,7 +195,7 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
         // digit pair), only the last round is partial, and with group_tiles = the grid a full
         // group keeps every modulus of a tile on one CTA.
         const int64_t tiles = p.tri ? p.tri_tiles : static_cast<int64_t>(p.tiles_m) * p.tiles_n;
-        const int64_t N = p.one.S;
+        const int64_t N = one_S(p);
         const int64_t u = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
         if (u >= tiles * N) return false;
         const int64_t GT = p.group_tiles;
@@ -209,6 +223,7 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
     }
     if (p.table == nullptr) {
         *prob = -1;
+        if (p.plan_kind != 0 && one_S(p) == 0) return false;  // the plan chose the modular encoding
         if (p.tail_parts >= 2 && it >= p.full_rounds) return false;  // the rest is the tail launch's
         return member_tile(p.member, p.group, blockIdx.x, gridDim.x, it, p.tiles_m, p.tiles_n, tm, tn);
     }
@@ -236,8 +251,9 @@ struct TileInts {
 MOMMS_DEV TileInts tile_ints(const Params& p, int prob, int part) {
     TileInts t;
     if (prob < 0) {
-        t.S = p.one.S; t.beta = p.one.beta; t.chunk_slabs = p.one.chunk_slabs;
-        t.slab0 = p.one.slab0; t.nslab = p.one.nslab; t.group_end = p.one.group_end;
+        t.S = one_S(p); t.beta = p.one.beta; t.chunk_slabs = p.one.chunk_slabs;
+        t.slab0 = p.one.slab0; t.nslab = p.one.nslab;
+        t.group_end = p.plan_kind != 0 ? p.group_end_by_s[t.S < 17 ? t.S : 16] : p.one.group_end;
         if (part >= 0) {  // this unit's share of the pass's k slabs (every part gets at least one)
             const int lo = part * t.nslab / p.tail_parts, hi = (part + 1) * t.nslab / p.tail_parts;
             t.slab0 += lo;
@@ -657,11 +673,13 @@ MOMMS_DEV void stage_columns(const Params& p, int prob, int tn, int beta, int* c
 // Drains the accumulator chunks of one diagonal (`units` k slabs, `chunk_slabs` per chunk) into
 // int32 sums: the first CR of the thread's columns in `acc`, the other CT in TMEM at `tsum`.
 // `tacc` is the thread's first accumulator column in buffer 0 (buffer 1 is 256 columns on).
+// `remote_empty` (CTA pairs): the shared::cluster address of the pair leader's acc_empty[0], on
+// which the peer's warps arrive instead of their own (0: this CTA's acc_empty).
 // Returns false if a bounded wait gave up.
 template <int CR, int CT>
 MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, uint64_t* acc_empty, uint32_t& abuf,
                               uint32_t (&aphase)[2], volatile int* abort_flag, uint32_t tacc, uint32_t tsum,
-                              int lane, int32_t (&acc)[CR]) {
+                              int lane, int32_t (&acc)[CR], uint32_t remote_empty = 0) {
 #pragma unroll
     for (int c = 0; c < CR; ++c) acc[c] = 0;
     bool first = true;
@@ -699,7 +717,10 @@ MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, ui
         tmem_st_wait();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[abuf]);
+        if (lane == 0) {
+            if (remote_empty) mbar_arrive_cluster(remote_empty + 8u * abuf);
+            else mbar_arrive(&acc_empty[abuf]);
+        }
         aphase[abuf] ^= 1u;
         abuf ^= 1u;
         u += cnt;
@@ -1042,6 +1063,238 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------- residue product on CTA pairs
+// The modular encoding's residue product with the tensor cores of two SMs per MMA
+// (tcgen05.mma.cta_group::2, M = 256): a cluster of two CTAs takes a 256 x 192 tile of one
+// modulus; each CTA stages its own 128 rows of A and its own 96 of the tile's 192 B rows, so per
+// MMA flop a CTA's shared memory is written by TMA and read by the tensor core 30 % less than with
+// one CTA per 128 x 192 tile (28 instead of 40 KB per 64-deep slab), and L2 sends 30 % fewer bytes
+// per flop.  The even CTA (leader) issues the MMAs; each CTA receives its 128 rows of the
+// accumulator in its own tensor memory and drains, reduces and stores them as in slice_gemm_kernel.
+//
+// Barriers.  Each CTA's producer fills its own stage and completes its own full barrier; the
+// peer's warp 1 forwards each completed stage to the leader's full barrier (count 2: the leader's
+// own arrival plus the forward), so the leader's MMA thread waits on one barrier for both halves.
+// The leader's commits release the stage (empty) and hand over the accumulator (acc_full) in both
+// CTAs; both CTAs' drain warps arrive on the leader's acc_empty.  All waits are bounded; a CTA that
+// gives up raises its abort flag, the other one's waits then run out too, and both wait for their
+// own copies (and the leader for its MMAs) before the closing cluster barrier frees tensor memory.
+namespace pairk {
+constexpr int BN = kEmuBNMax;                       // 192 columns per pair tile
+constexpr int BNH = BN / 2;                         // B rows staged per CTA
+constexpr uint32_t B_HALF = BNH * BK * 2;           // 12 KB
+constexpr uint32_t STAGE = A_TILE + B_HALF;         // 28 KB
+constexpr int STAGES = 7;
+constexpr size_t SMEM_BYTES = 1024 + static_cast<size_t>(STAGES) * STAGE + 256 + 5 * BN;
+constexpr uint32_t IDESC = idesc_f16_f32(2 * BM, BN);
+static_assert(STAGE % 1024 == 0, "stage bases stay 1024-byte aligned for the 128-B swizzle");
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
+
+// Unit `it` of this pair: modulus lm of pair tile (tm2, tn); p.tiles_m counts pair rows.
+MOMMS_DEV bool unit_of(const Params& p, int it, int* lm, int* tm2, int* tn) {
+    const int64_t ncl = gridDim.x >> 1, cl = blockIdx.x >> 1;
+    const int64_t tiles = static_cast<int64_t>(p.tiles_m) * p.tiles_n;
+    const int64_t u = cl + static_cast<int64_t>(it) * ncl;
+    if (u >= tiles * one_S(p)) return false;
+    *lm = static_cast<int>(u / tiles);
+    const int64_t t = u - *lm * tiles;
+    const int member = p.member == kMemberA1 ? kMemberA2 : p.member;
+    return member_tile(member, p.group, t % ncl, ncl, t / ncl, p.tiles_m, p.tiles_n, tm2, tn);
+}
+}  // namespace pairk
+
+__global__ void __launch_bounds__(THREADS, 1)
+    residue_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ Params p) {
+    using namespace pairk;
+    using C_ = Cfg<BN>;
+    constexpr int CR = C_::CR, CT = C_::CT, CW = C_::CW;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+    uint64_t* full = bars;                        // STAGES
+    uint64_t* empty = bars + STAGES;              // STAGES
+    uint64_t* acc_full = bars + 2 * STAGES;       // 2
+    uint64_t* acc_empty = bars + 2 * STAGES + 2;  // 2 (the leader's count both CTAs' drain warps)
+    uint64_t* drain = bars + 2 * STAGES + 4;      // 1
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = rank == 0;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&full[i], leader ? 2 : 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 2 * EPI_WARPS);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_mbarrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(tmem_slot, TMEM_COLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // both CTAs' barriers are initialised before any remote arrive or commit
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer (both CTAs)
+        if (lane == 0) {
+            prefetch_tensormap(&tmA);
+            prefetch_tensormap(&tmB);
+            uint32_t stage = 0, phase = 0;
+            int last_phase[STAGES];
+            for (int i = 0; i < STAGES; ++i) last_phase[i] = -1;
+            bool ok = true;
+            bool withhold = p.withhold != 0 && blockIdx.x == 0;
+            const int nslab = p.one.nslab, slab0 = p.one.slab0;
+            for (int it = 0; ok; ++it) {
+                int lm, tm2, tn;
+                if (!unit_of(p, it, &lm, &tm2, &tn)) break;
+                for (int j = 0; j < nslab; ++j) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* sa = smem + stage * STAGE;
+                    mbar_arrive_expect_tx(&full[stage], STAGE);
+                    const int x = (slab0 + j) * BK;
+                    // this CTA's 128 rows of A and 96 rows of B (rows past a plane's end read as zero)
+                    if (!withhold) {
+                        tma_load_3d(sa, &tmA, &full[stage], x, (2 * tm2 + static_cast<int>(rank)) * BM, lm);
+                        tma_load_3d(sa + A_TILE, &tmB, &full[stage], x, tn * BN + static_cast<int>(rank) * BNH, lm);
+                    }
+                    withhold = false;  // (test hook: only the first stage stays empty)
+                    last_phase[stage] = static_cast<int>(phase);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                for (int i = 0; i < STAGES; ++i)
+                    if (last_phase[i] >= 0) mbar_wait_drain(&full[i], static_cast<uint32_t>(last_phase[i]));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            // -------------------------------------------------------- MMA issuer (leader)
+            const uint32_t peer_empty = cluster_addr(empty, 1);
+            const uint32_t peer_acc_full = cluster_addr(acc_full, 1);
+            uint32_t stage = 0, phase = 0, abuf = 0;
+            uint32_t aphase[2] = {0u, 0u};
+            bool ok = true, issued = false;
+            const int nslab = p.one.nslab, chunk = p.one.chunk_slabs;
+            for (int it = 0; ok; ++it) {
+                int lm, tm2, tn;
+                if (!unit_of(p, it, &lm, &tm2, &tn)) break;
+                for (int u = 0; u < nslab && ok;) {
+                    const int cnt = min(chunk, nslab - u);
+                    if (!mbar_wait(&acc_empty[abuf], aphase[abuf] ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tmem_base + abuf * 256u;
+                    for (int c = 0; c < cnt; ++c) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(smem + stage * STAGE);
+                        const uint64_t da = smem_desc_k_sw128(sa);
+                        const uint64_t db = smem_desc_k_sw128(sa + A_TILE);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            umma_f16_ss_pair(dt, da + 2ull * kk, db + 2ull * kk, IDESC,
+                                             static_cast<uint32_t>((c | kk) != 0));
+                        issued = true;
+                        umma_commit_pair(smem_u32(&empty[stage]));
+                        umma_commit_pair(peer_empty + 8u * stage);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    umma_commit_pair(smem_u32(&acc_full[abuf]));
+                    umma_commit_pair(peer_acc_full + 8u * abuf);
+                    aphase[abuf] ^= 1u;
+                    abuf ^= 1u;
+                    u += cnt;
+                }
+            }
+            if (!ok && issued) {
+                umma_commit_pair(smem_u32(drain));
+                mbar_wait_drain(drain, 0);
+            }
+        } else if (lane == 0) {
+            // -------------------------------------------------------- stage forwarder (peer)
+            // every stage of this CTA that completes is announced on the leader's full barrier
+            const uint32_t leader_full = cluster_addr(full, 0);
+            uint32_t stage = 0, phase = 0;
+            bool ok = true;
+            const int nslab = p.one.nslab;
+            for (int it = 0; ok; ++it) {
+                int lm, tm2, tn;
+                if (!unit_of(p, it, &lm, &tm2, &tn)) break;
+                for (int j = 0; j < nslab; ++j) {
+                    if (!mbar_wait(&full[stage], phase, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(leader_full + 8u * stage);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp >= CTRL_WARPS) {
+        // ------------------------------------------------------------ drain + residues (both CTAs)
+        const int quad = warp & 3;
+        const int third = (warp - CTRL_WARPS) >> 2;
+        const int rloc = quad * 32 + lane;
+        const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+        const uint32_t tsum = tmem_base + lane_off + (third < 2 ? 192u + 32u * third : 448u);
+        const uint32_t remote_empty = leader ? 0u : cluster_addr(acc_empty, 0);
+        uint32_t abuf = 0;
+        uint32_t aphase[2] = {0u, 0u};
+        for (int it = 0;; ++it) {
+            int lm, tm2, tn;
+            if (!unit_of(p, it, &lm, &tm2, &tn)) break;
+            int32_t acc[CR];
+            if (!drain_diagonal<CR, CT>(p.one.nslab, p.one.chunk_slabs, acc_full, acc_empty, abuf, aphase,
+                                        abort_flag, tmem_base + lane_off + third * CW, tsum, lane, acc, remote_empty))
+                break;
+            store_residues<BN, CR, CT>(p, -1, 2 * tm2 + static_cast<int>(rank), tn, lm, third, rloc, acc, tsum);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // no CTA leaves while its peer may still arrive on its barriers or MMAs write its TMEM
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(p.status, kStatusTimeout);
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, TMEM_COLS);
+    }
+}
+
 // ------------------------------------------------------------------ host side
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
 
@@ -1158,7 +1411,9 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
     if (kslabs <= 0 || pass_slabs <= 0) return cudaErrorInvalidValue;
     if (mod && (a.res == nullptr || a.crt->N != a.S || kslabs * BK > crt_max_k())) return cudaErrorInvalidValue;
     const int member = a.member == kMemberAuto ? kMemberC2 : a.member;
-    TailPlan tp = BN == kEmuBNMax && !mod ? tail_plan(tiles, ctas, kslabs, pass_slabs, a.S, member) : TailPlan{};
+    // (with a device plan the digit launch keeps whole tiles: the tail split is planned for one S)
+    TailPlan tp = BN == kEmuBNMax && !mod && !a.plan ? tail_plan(tiles, ctas, kslabs, pass_slabs, a.S, member)
+                                                     : TailPlan{};
     if (tp.parts && a.scratch_bytes < 2 * half + tp.sums_bytes) tp = TailPlan{};  // whole tiles
     char* tail_base = static_cast<char*>(a.scratch) + 2 * half;
     int npass = 0, nlaunch = 0;
@@ -1195,6 +1450,13 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         if (a.used_group) *a.used_group = p.group;
         p.table = nullptr;
         p.withhold = g_withhold.exchange(0);
+        if (a.plan) {
+            // S or N from the device plan; the pass above was sized for the largest the plan may pick
+            p.plan = a.plan;
+            p.plan_kind = mod ? 1 : 2;
+            for (int q = 1; q <= 16; ++q)
+                p.group_end_by_s[q] = emu_group_ends(q, a.beta, p.one.nslab * static_cast<int64_t>(BK));
+        }
         p.qscratch = static_cast<long long*>(a.scratch);
         p.scratch = reinterpret_cast<double*>(static_cast<char*>(a.scratch) + half);
         p.status = a.status;
@@ -1231,9 +1493,68 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
             }
             if (a.kcap < 0 || a.kcap > 4) return cudaErrorInvalidValue;
             p.kcap = a.kcap;
-            slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(
-                mapA, mapB, p);
-            cudaError_t e = cudaGetLastError();
+            cudaError_t e;
+            const int64_t pair_rows = (tiles_m + 1) / 2;
+            if (BN == kEmuBNMax && a.cta_pairs && !a.crt_fuse && !a.tri && !a.kcap && tiles_m >= 2 && ctas >= 4) {
+                // CTA pairs over 256 x 192 tiles: B staged as two 96-row halves, one per CTA
+                CUtensorMap mapBh;
+                if (!emu_make_digit_map(&mapBh, a.Bd, a.k_pad, a.n_pad, a.S, pairk::BNH)) return cudaErrorInvalidValue;
+                static PerDeviceFlag pair_attr;
+                if (!pair_attr.done()) {
+                    e = cudaFuncSetAttribute(residue_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(pairk::SMEM_BYTES));
+                    if (e != cudaSuccess) return e;
+                    pair_attr.mark();
+                }
+                // as many pairs as can be resident at once (a GPC with an odd SM count leaves one SM out)
+                static std::atomic<int> resident[kMaxDevices] = {};
+                const int dev = current_device();
+                int max_cl = dev >= 0 && dev < kMaxDevices ? resident[dev].load() : 0;
+                if (max_cl <= 0) {
+                    cudaLaunchConfig_t q{};
+                    q.gridDim = dim3(static_cast<unsigned>(2 * (sms / 2)));
+                    q.blockDim = dim3(THREADS);
+                    q.dynamicSmemBytes = pairk::SMEM_BYTES;
+                    cudaLaunchAttribute qa[1];
+                    qa[0].id = cudaLaunchAttributeClusterDimension;
+                    qa[0].val.clusterDim.x = 2;
+                    qa[0].val.clusterDim.y = 1;
+                    qa[0].val.clusterDim.z = 1;
+                    q.attrs = qa;
+                    q.numAttrs = 1;
+                    if (cudaOccupancyMaxActiveClusters(&max_cl, residue_pair_kernel, &q) != cudaSuccess || max_cl <= 0) {
+                        cudaGetLastError();
+                        max_cl = sms / 2;
+                    }
+                    if (dev >= 0 && dev < kMaxDevices) resident[dev].store(max_cl);
+                }
+                const int64_t ncl = std::min<int64_t>({ctas / 2, static_cast<int64_t>(max_cl),
+                                                       pair_rows * tiles_n * a.crt->N});
+                p.tiles_m = static_cast<int>(pair_rows);
+                p.group = a.group > 0 ? a.group : emu_default_group(ncl, static_cast<int>(pair_rows),
+                                                                     static_cast<int>(tiles_n));
+                p.group_tiles = static_cast<int>(pair_rows * tiles_n);
+                if (a.used_ctas) *a.used_ctas = static_cast<int>(2 * ncl);
+                if (a.used_group) *a.used_group = p.group;
+                if (a.used_pairs) *a.used_pairs = 1;
+                cudaLaunchConfig_t cfg{};
+                cfg.gridDim = dim3(static_cast<unsigned>(2 * ncl));
+                cfg.blockDim = dim3(THREADS);
+                cfg.dynamicSmemBytes = pairk::SMEM_BYTES;
+                cfg.stream = stream;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = 2;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                e = cudaLaunchKernelEx(&cfg, residue_pair_kernel, mapA, mapBh, p);
+            } else {
+                slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(
+                    mapA, mapB, p);
+                e = cudaGetLastError();
+            }
             if (e != cudaSuccess) return e;
             ++nlaunch;
             ++npass;

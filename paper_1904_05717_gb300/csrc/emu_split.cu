@@ -140,6 +140,30 @@ __global__ void spread_kernel(int64_t rows, int64_t inner, const int32_t* __rest
     if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(out, v);
 }
 
+// The device plan of one product (EmuPlanTable): the slice-count rule on the spreads, then the
+// encoding.  Every quantity is formed by the same IEEE operations, in the same order, as the host
+// form of the rule, so both give the same S and width for the same spreads.
+__global__ void plan_kernel(const int* __restrict__ spreads, const __grid_constant__ EmuPlanTable t, EmuPlan* out) {
+    if (threadIdx.x != 0) return;
+    const double sa = spreads[0] / 16.0;
+    const double sb = t.tri ? sa : spreads[1] / 16.0;
+    const double bits = t.c0 + 1.25 * (sa + sb);
+    int S = static_cast<int>(ceil(bits / 7.0));
+    S = S < 3 ? 3 : (S > t.smax ? t.smax : S);
+    const int cb = static_cast<int>(ceil(bits));
+    int w = cb > 7 * S - 6 ? cb : 7 * S - 6;
+    w = w < 7 * S ? w : 7 * S;
+    const int N = w <= kPlanMaxBits ? t.ntab[w] : 0;
+    const bool mod = N > 0 && N <= t.n_alloc && (t.scheme_moduli || N + 2 <= S * (S + 1) / 2);
+    EmuPlan p;
+    p.S = S;
+    p.bits = mod ? w : 7 * S;
+    p.N = mod ? N : 0;
+    p.pad = 0;
+    p.est = 0.1 * exp2(bits - static_cast<double>(p.bits));  // the rule keeps a 10x margin
+    *out = p;
+}
+
 // Decompose x into (integer significand, binary exponent e2, sign); zero / non-finite -> mag 0.
 __device__ __forceinline__ void decompose(double x, unsigned long long* mag, int* e2, bool* neg) {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
@@ -365,7 +389,18 @@ __global__ void split_inner_contig(const double* __restrict__ X, int64_t ld, int
                                    int64_t inner, const int32_t* __restrict__ exps,
                                    const uint8_t* __restrict__ flags, int S, int beta,
                                    __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad,
-                                   int s_first, const __grid_constant__ CrtConsts crt) {
+                                   int s_first, const __grid_constant__ CrtConsts crt, const EmuPlan* plan) {
+    int nres = crt.N, rbits = crt.bits;
+    if (plan) {  // the device plan decides the encoding, S or (N, width)
+        const int pn = plan->N;
+        if (RES ? pn == 0 : pn != 0) return;
+        if (RES) {
+            nres = pn;
+            rbits = plan->bits;
+        } else {
+            S = plan->S;
+        }
+    }
     const int64_t octs = inner_pad / 8;
     const int64_t total = rows_pad * octs;
     const int64_t plane = rows_pad * inner_pad;
@@ -378,7 +413,7 @@ __global__ void split_inner_contig(const double* __restrict__ X, int64_t ld, int
 #pragma unroll
         for (int t = 0; t < 8; ++t) x[t] = (valid && q + t < inner) ? X[q + t + r * ld] : 0.0;
         if constexpr (RES)
-            write_residues<8>(x, valid, valid ? exps[r] : 0, crt, digits, plane, r * inner_pad + q, crt.N, crt.bits);
+            write_residues<8>(x, valid, valid ? exps[r] : 0, crt, digits, plane, r * inner_pad + q, nres, rbits);
         else
             write_digits8(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
     }
@@ -396,8 +431,19 @@ __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int6
                                   int64_t inner, const int32_t* __restrict__ exps,
                                   const uint8_t* __restrict__ flags, int S, int beta,
                                   __half* __restrict__ digits, int64_t rows_pad, int64_t inner_pad,
-                                  int s_first, const __grid_constant__ CrtConsts crt) {
+                                  int s_first, const __grid_constant__ CrtConsts crt, const EmuPlan* plan) {
     __shared__ double tile[TT][TT];  // [q][r ^ swz(q)]
+    int nres = crt.N, rbits = crt.bits;
+    if (plan) {  // the device plan decides the encoding, S or (N, width)
+        const int pn = plan->N;
+        if (RES ? pn == 0 : pn != 0) return;
+        if (RES) {
+            nres = pn;
+            rbits = plan->bits;
+        } else {
+            S = plan->S;
+        }
+    }
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TT;
     const int64_t q0 = static_cast<int64_t>(blockIdx.y) * TT;
     const int tid = threadIdx.x;  // 256 threads
@@ -417,7 +463,7 @@ __global__ void split_rows_contig(const double* __restrict__ X, int64_t ld, int6
 #pragma unroll
         for (int t = 0; t < 4; ++t) x[t] = tile[qg + t][rr ^ swz(qg + t)];
         if constexpr (RES)
-            write_residues<4>(x, valid, valid ? exps[r] : 0, crt, digits, plane, r * inner_pad + q, crt.N, crt.bits);
+            write_residues<4>(x, valid, valid ? exps[r] : 0, crt, digits, plane, r * inner_pad + q, nres, rbits);
         else
             write_digits4(x, valid, valid ? exps[r] : 0, S, beta, digits, plane, r * inner_pad + q, s_first);
     }
@@ -632,6 +678,11 @@ cudaError_t launch_emu_scale(int which, int op, int64_t rows, int64_t inner, con
     return cudaGetLastError();
 }
 
+cudaError_t launch_emu_plan(const int* spreads, const EmuPlanTable& t, EmuPlan* out, cudaStream_t stream) {
+    split::plan_kernel<<<1, 32, 0, stream>>>(spreads, t, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_emu_spread(int64_t rows, int64_t inner, const int32_t* exps, const uint8_t* flags,
                               const float* l1, int* out, cudaStream_t stream) {
     if (rows <= 0) return cudaSuccess;
@@ -642,7 +693,7 @@ cudaError_t launch_emu_spread(int64_t rows, int64_t inner, const int32_t* exps, 
 cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, const double* X,
                              int64_t ldx, const int32_t* exps, const uint8_t* flags, int S, int beta,
                              void* digits, int64_t rows_pad, int64_t inner_pad, cudaStream_t stream,
-                             int s_first) {
+                             int s_first, const EmuPlan* plan) {
     using namespace split;
     if (rows_pad <= 0 || inner_pad <= 0) return cudaSuccess;
     if (S < 1 || beta < 1 || beta > 10 || inner_pad % 8 || s_first < 0) return cudaErrorInvalidValue;
@@ -653,7 +704,7 @@ cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, con
         dim3 grid(static_cast<unsigned>((rows_pad + TT - 1) / TT), static_cast<unsigned>((inner_pad + TT - 1) / TT));
         if (grid.y > 65535) return cudaErrorInvalidValue;
         split_rows_contig<false><<<grid, 256, 0, stream>>>(X, ldx, rows, inner, exps, flags, S, beta, dg,
-                                                           rows_pad, inner_pad, s_first, CrtConsts{});
+                                                           rows_pad, inner_pad, s_first, CrtConsts{}, plan);
         return cudaGetLastError();
     }
     const int64_t total = rows_pad * (inner_pad / 8);
@@ -661,13 +712,13 @@ cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, con
     const int64_t cap = static_cast<int64_t>(device_sm_count()) * 32;
     if (blocks > cap) blocks = cap;
     split_inner_contig<false><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
-        X, ldx, rows, inner, exps, flags, S, beta, dg, rows_pad, inner_pad, s_first, CrtConsts{});
+        X, ldx, rows, inner, exps, flags, S, beta, dg, rows_pad, inner_pad, s_first, CrtConsts{}, plan);
     return cudaGetLastError();
 }
 
 cudaError_t launch_emu_residues(int which, int op, int64_t rows, int64_t inner, const double* X, int64_t ldx,
                                 const int32_t* exps, const uint8_t* flags, const CrtConsts& c, void* planes,
-                                int64_t rows_pad, int64_t inner_pad, cudaStream_t stream) {
+                                int64_t rows_pad, int64_t inner_pad, cudaStream_t stream, const EmuPlan* plan) {
     using namespace split;
     if (rows_pad <= 0 || inner_pad <= 0) return cudaSuccess;
     if (c.N < 1 || c.N > kCrtMaxModuli || c.bits < 1 || c.bits > 56 || inner_pad % 8) return cudaErrorInvalidValue;
@@ -677,7 +728,7 @@ cudaError_t launch_emu_residues(int which, int op, int64_t rows, int64_t inner, 
         dim3 grid(static_cast<unsigned>((rows_pad + TT - 1) / TT), static_cast<unsigned>((inner_pad + TT - 1) / TT));
         if (grid.y > 65535) return cudaErrorInvalidValue;
         split_rows_contig<true><<<grid, 256, 0, stream>>>(X, ldx, rows, inner, exps, flags, c.N, 7, dg, rows_pad,
-                                                          inner_pad, 0, c);
+                                                          inner_pad, 0, c, plan);
         return cudaGetLastError();
     }
     const int64_t total = rows_pad * (inner_pad / 8);
@@ -685,7 +736,7 @@ cudaError_t launch_emu_residues(int which, int op, int64_t rows, int64_t inner, 
     const int64_t cap = static_cast<int64_t>(device_sm_count()) * 32;
     if (blocks > cap) blocks = cap;
     split_inner_contig<true><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
-        X, ldx, rows, inner, exps, flags, c.N, 7, dg, rows_pad, inner_pad, 0, c);
+        X, ldx, rows, inner, exps, flags, c.N, 7, dg, rows_pad, inner_pad, 0, c, plan);
     return cudaGetLastError();
 }
 

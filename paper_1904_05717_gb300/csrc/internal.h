@@ -46,12 +46,36 @@ inline int emu_scale_kernel_count(int which, int op) { return ((which == 0) == (
 // atomicMax into *out of ceil(16 * max_r log2(2^e_r * inner / l1_r)).
 cudaError_t launch_emu_spread(int64_t rows, int64_t inner, const int32_t* exps, const uint8_t* flags,
                               const float* l1, int* out, cudaStream_t stream);
+// The plan of one emulated product when the data decide it (AUTO slice count), chosen on the
+// device so that no call waits for a readback: written by launch_emu_plan after the spreads,
+// read at launch time by the split, product and reconstruction kernels of that product.
+struct EmuPlan {
+    int S;        // digit slices of the width rule (the digit encoding's S)
+    int bits;     // operand width: the modular encoding's, or 7 S for digit slices
+    int N;        // moduli; 0 = the digit encoding serves the product
+    int pad;
+    double est;   // estimated max error / bound (the rule's margin)
+};
+// Largest operand width whose moduli count the plan kernel looks up.
+constexpr int kPlanMaxBits = 16 * 7;
+// One thread: spreads[0..1] (ceil(16 x spread) of op(A) rows, op(B) columns; `tri`: op(B) is
+// op(A)^T and spreads[1] is not read) -> rule bits = c0 + 1.25 (s_A + s_B) with c0 the k-dependent
+// part of the rule, S = ceil(bits / 7) in [3, smax], the modular width min(7 S, max(ceil(bits),
+// 7 S - 6)), its moduli count ntab[width] (0: none) and the encoding: moduli when ntab gives N,
+// N <= n_alloc and (scheme_moduli or N + 2 <= S (S + 1) / 2).
+struct EmuPlanTable {
+    double c0;
+    int smax, n_alloc, scheme_moduli, tri;
+    uint8_t ntab[kPlanMaxBits + 1];
+};
+cudaError_t launch_emu_plan(const int* spreads, const EmuPlanTable& t, EmuPlan* out, cudaStream_t stream);
 // Truncation digits (fp16, integer valued), layout [S][rows_pad][inner_pad].  Only the
 // slices s_first .. S-1 (0-based) are written; a slice's digits do not depend on S.
+// plan (optional): S comes from the device plan, and nothing is written when it chose moduli.
 cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, const double* X,
                              int64_t ldx, const int32_t* exps, const uint8_t* flags, int S,
                              int beta, void* digits, int64_t rows_pad, int64_t inner_pad,
-                             cudaStream_t stream, int s_first = 0);
+                             cudaStream_t stream, int s_first = 0, const EmuPlan* plan = nullptr);
 
 // ----------------------------------------------- emulated FP64, modular (CRT) encoding
 // The operands are truncated to integers of `bits` bits (the first bits/7 digits of the slice
@@ -82,14 +106,24 @@ void crt_consts(int N, int bits, CrtConsts* c, CrtRecon* r);
 // Largest k one modular product keeps exact in int32 (k * 127^2 < 2^31), a multiple of 64.
 int64_t crt_max_k();
 // Residues of the integer operand, layout [N][rows_pad][inner_pad] fp16 (as the digit slices).
+// plan (optional): N and the width come from the device plan (c then holds all kCrtMaxModuli
+// moduli), and nothing is written when it chose digit slices.
 cudaError_t launch_emu_residues(int which, int op, int64_t rows, int64_t inner, const double* X, int64_t ldx,
                                 const int32_t* exps, const uint8_t* flags, const CrtConsts& c, void* planes,
-                                int64_t rows_pad, int64_t inner_pad, cudaStream_t stream);
+                                int64_t rows_pad, int64_t inner_pad, cudaStream_t stream,
+                                const EmuPlan* plan = nullptr);
 // C from the residue planes of the product ([N][n][m] bytes, residue in [0, p_l)); tri = 1 / 2
 // (m = n): only the lower / upper triangle of C is read from the residues and written.
 cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, const CrtRecon& r, const int32_t* e,
                                    const uint8_t* ef, const int32_t* f, const uint8_t* ff, double alpha,
                                    double beta, double* C, int64_t ldc, cudaStream_t stream, int tri = 0);
+struct CrtReconSet;
+// The same with the moduli count and width from the device plan (constants of every count in
+// `set`); nothing is written when the plan chose digit slices.
+cudaError_t launch_crt_reconstruct_plan(int64_t m, int64_t n, const uint8_t* res, const CrtReconSet& set,
+                                        const EmuPlan* plan, const int32_t* e, const uint8_t* ef, const int32_t* f,
+                                        const uint8_t* ff, double alpha, double beta, double* C, int64_t ldc,
+                                        cudaStream_t stream);
 
 // ----------------------------------------------- triangular solve (leaf step)
 constexpr int kTrsmNb = 64;       // order of the blocks inverted by substitution
@@ -133,6 +167,13 @@ struct EmuGemmArgs {
                            // lower / upper triangle of C
     int kcap;              // modular: a triangular operand, its zero k range skipped per tile (1 op(A)
                            // lower, 2 op(A) upper, 3 op(B) lower, 4 op(B) upper; 0 none)
+    int cta_pairs;         // modular, 192-wide tiles: the residue product on CTA pairs (one MMA over two
+                           // SMs, 256 x 192 pair tiles) where the problem allows it
+    // Device plan (AUTO slice count): S (digit slices) or N (moduli, with `crt` holding all moduli)
+    // is read at launch time; the launch does nothing when the plan chose the other encoding.  The
+    // pass structure is that of S (or N) as given here, the largest the plan can pick.
+    const EmuPlan* plan;
+    int* used_pairs;       // optional out: 1 when the residue product ran on CTA pairs
 };
 constexpr int kEmuBM = 128, kEmuBK = 64, kEmuBNMax = 192;
 

@@ -50,7 +50,8 @@ class Report(ctypes.Structure):
                 ("tile_n", ctypes.c_int), ("ctas", ctypes.c_int), ("group", ctypes.c_int),
                 ("launches", ctypes.c_int64), ("est_err_ratio", ctypes.c_double),
                 ("ooc_block", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
-                ("moduli", ctypes.c_int), ("operand_bits", ctypes.c_int), ("crt_fused", ctypes.c_int)]
+                ("moduli", ctypes.c_int), ("operand_bits", ctypes.c_int), ("crt_fused", ctypes.c_int),
+                ("cta_pairs", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -70,6 +71,8 @@ _SIGS = {
     "momms_set_raster_group": ([_VP, _I32], _I32),
     "momms_set_tile_n": ([_VP, _I32], _I32),
     "momms_set_scheme": ([_VP, _I32], _I32),
+    "momms_set_plan_on_device": ([_VP, _I32], _I32),
+    "momms_set_cta_pairs": ([_VP, _I32], _I32),
     "momms_set_crt_fusion": ([_VP, _I32], _I32),
     "momms_trsm": ([_VP, _I32, _I32, _I32, _I32, _I64, _I64, _DBL, _VP, _I64, _VP, _I64, _VP], _I32),
     "momms_crt_moduli": ([_I32, _I64, _VP, _VP], _I32),
@@ -339,6 +342,12 @@ class Handle:
 
     def set_scheme(self, scheme):
         check(lib().momms_set_scheme(self.ptr, scheme), "momms_set_scheme")
+
+    def set_plan_on_device(self, on):
+        check(lib().momms_set_plan_on_device(self.ptr, on), "momms_set_plan_on_device")
+
+    def set_cta_pairs(self, mode):
+        check(lib().momms_set_cta_pairs(self.ptr, mode), "momms_set_cta_pairs")
 
     def set_crt_fusion(self, mode):
         check(lib().momms_set_crt_fusion(self.ptr, mode), "momms_set_crt_fusion")

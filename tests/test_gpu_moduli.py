@@ -52,11 +52,12 @@ def test_residue_split_bitwise(which, op, bits, k):
     assert not np.any(got[:, rows:, :]) and not np.any(got[:, :, inner:])
 
 
-def modular(A, B, C0, alpha, beta, S=0, opa=0, opb=0, scheme=M.SCHEME_MODULI, tile_n=0, ctas=0, fusion=0):
+def modular(A, B, C0, alpha, beta, S=0, opa=0, opb=0, scheme=M.SCHEME_MODULI, tile_n=0, ctas=0, fusion=0, pairs=0):
     h = M.Handle(mode=M.MODE_EMULATED, slices=S, scheme=scheme)
     h.set_tile_n(tile_n)
     h.set_max_ctas(ctas)
     h.set_crt_fusion(fusion)
+    h.set_cta_pairs(pairs)
     dA = M.DeviceMatrix.from_numpy(A)
     dB = M.DeviceMatrix.from_numpy(B)
     dC = M.DeviceMatrix.from_numpy(C0)
@@ -315,6 +316,57 @@ def test_fused_reconstruction_bitwise_equal_to_separate(m, n, k):
     assert np.array_equal(Cf, Cs)
     Cref, N = reference(A, B, C0, -1.25, 0.5)
     assert max_ratio(Cf, Cref, k, 1.25, 0.5, N, C0) <= 1.0
+
+
+@pytest.mark.parametrize("m,n,k,opa,opb,ctas", [(300, 1000, 520, 0, 0, 0), (200, 700, 300, 1, 0, 0),
+                                                (2000, 900, 1100, 0, 1, 0), (1024, 1152, 640, 1, 1, 0),
+                                                (700, 450, 2000, 0, 0, 6)])
+def test_cta_pairs_bitwise_identical(m, n, k, opa, opb, ctas):
+    # the residue product on CTA pairs (one MMA over two SMs, 256 x 192 tiles, each CTA staging
+    # its own rows of A and half of B) against single CTAs: ragged pair rows (the second half of the
+    # last pair row past m: zero operands, nothing stored), one pair row, transposes, a capped grid
+    A = syn.matrix("phi", k if opa else m, m if opa else k, 431, phi=1.0)
+    B = syn.matrix("phi", n if opb else k, k if opb else n, 432, phi=1.0)
+    C0 = syn.matrix("uniform", m, n, 433)
+    C1, r1 = modular(A, B, C0, 1.5, -0.5, 6, opa, opb, tile_n=192, ctas=ctas, pairs=1)
+    C2, r2 = modular(A, B, C0, 1.5, -0.5, 6, opa, opb, tile_n=192, ctas=ctas, pairs=2)
+    assert r1["moduli"] > 0 and r2["moduli"] == r1["moduli"]
+    assert r2["ctas"] % 2 == 0
+    assert np.array_equal(C1, C2)
+    # sampled elements at the pair tile's seams bit for bit against the definition of the result
+    rs = np.unique([0, 127, 128, min(255, m - 1), min(256, m - 1), m - 1])
+    cs = np.unique([0, 95, 96, min(191, n - 1), min(192, n - 1), n - 1])
+    As = np.asfortranarray(A[:, rs] if opa else A[rs, :])
+    Bs = np.asfortranarray(B[cs, :] if opb else B[:, cs])
+    Co, _ = oracle.modular_dgemm(As, Bs, 42, np.asfortranarray(C0[np.ix_(rs, cs)]), 1.5, -0.5, bool(opa), bool(opb))
+    assert np.array_equal(C2[np.ix_(rs, cs)], Co)
+
+
+def test_cta_pairs_timeout_path():
+    # the timeout test hook on the pair kernel: the leader of the first pair leaves a stage empty,
+    # both CTAs' bounded waits run out, the status reads MOMMS_ERR_TIMEOUT, the next call is exact
+    m, n, k = 600, 800, 512
+    A = syn.matrix("uniform", m, k, 441)
+    B = syn.matrix("uniform", k, n, 442)
+    C0 = syn.matrix("uniform", m, n, 443)
+    h = M.Handle(mode=M.MODE_EMULATED, slices=6, scheme=M.SCHEME_MODULI)
+    h.set_tile_n(192)
+    h.set_cta_pairs(2)
+    dA, dB = M.DeviceMatrix.from_numpy(A), M.DeviceMatrix.from_numpy(B)
+    M.momms_debug_withhold_load()
+    dC = M.DeviceMatrix.from_numpy(C0)
+    M.gemm(dA, dB, dC, 1.0, 1.0, handle=h)
+    assert h.device_status() == M.MOMMS_ERR_TIMEOUT
+    dC = M.DeviceMatrix.from_numpy(C0)
+    M.gemm(dA, dB, dC, 1.0, 1.0, handle=h)
+    assert h.device_status() == M.MOMMS_OK
+    rs, cs = np.array([0, 255, 256, 599]), np.array([0, 96, 191, 192, 799])
+    Co, _ = oracle.modular_dgemm(np.asfortranarray(A[rs, :]), np.asfortranarray(B[:, cs]), 42,
+                                 np.asfortranarray(C0[np.ix_(rs, cs)]), 1.0, 1.0)
+    assert np.array_equal(dC.to_numpy()[np.ix_(rs, cs)], Co)
+    Cref, N = reference(A, B, C0, 1.0, 1.0)
+    assert max_ratio(dC.to_numpy(), Cref, k, 1.0, 1.0, N, C0) <= 1.0
+    h.close()
 
 
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (3, 5, 70), (129, 1, 300), (1, 300, 64)])

@@ -24,7 +24,7 @@ def inputs(m, n, k, seed):
     return A, B, C0
 
 
-@pytest.mark.parametrize("scheme,slices", [(M.SCHEME_MODULI, 6), (M.SCHEME_SLICES, 6), (M.SCHEME_AUTO, 0)])
+@pytest.mark.parametrize("scheme,slices", [(M.SCHEME_MODULI, 6), (M.SCHEME_SLICES, 8), (M.SCHEME_AUTO, 0)])
 def test_withheld_stage_times_out_and_the_next_product_is_correct(scheme, slices):
     m, n, k = 700, 900, 640
     A, B, C0 = inputs(m, n, k, 5100)
