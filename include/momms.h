@@ -479,15 +479,46 @@ size_t momms_noalloc_scratch_bytes(void);
 int momms_noalloc_status(momms_stream_t stream, int* status);
 
 /* ---------------------------------------------------------------- tuning */
-/* Time the candidate plans (mode x member x slices) for the size buckets of the
- * given shapes (count triples m[i], n[i], k[i]) on `stream`, keep the fastest
- * that meets the accuracy rule, and persist the plan table to `path` (a small
- * text file; NULL = do not persist).  A readable file is loaded first. */
+/* A plan: what runs the products of one size bucket (ceil log2 of m, n, k, and the two
+ * transpositions).  The paper's point that different members win under different shapes and
+ * bandwidths (Sec. 2.3, Sec. 5.4, Fig. 11) made operational: the tuner times the candidates
+ * on the device and keeps the fastest.  Zero in tile_n / scheme / cta_pairs means the
+ * library's own rule; a handle setting that is not automatic overrides the plan's. */
+typedef struct {
+    int tuned;      /* 1: from momms_tune / a plan file; 0: the built-in default       */
+    int mode;       /* MOMMS_MODE_NATIVE or MOMMS_MODE_EMULATED                         */
+    int member;     /* MOMMS_MEMBER_C2 .. A1                                            */
+    int slices;     /* 0 = data-driven                                                  */
+    int tile_n;     /* emulated tile width: 0 = automatic, 96 or 192                    */
+    int scheme;     /* MOMMS_SCHEME_AUTO / SLICES / MODULI                              */
+    int cta_pairs;  /* 0 = automatic, 1 = off, 2 = on (momms_set_cta_pairs)             */
+} momms_plan_t;
+/* Time the candidate plans for the size buckets of the given shapes (count triples
+ * m[i], n[i], k[i]; op_a[i] / op_b[i] the transpositions, NULL = all N) on `stream`, on
+ * uniform[-1,1] data with the data-driven slice count: the native engine, and for the
+ * emulated engine every member (C2, A2, B2, A1) x tile width (192, 96) x encoding (digit
+ * slices, moduli), moduli on 192-wide tiles with and without CTA pairs.  Each candidate
+ * runs once untimed, then at least three timed calls and at least 20 ms of them (CUDA
+ * events on `stream`, mean).  The fastest becomes the bucket's plan; buckets that already
+ * have one are skipped.  The plan table is persisted to `path` (a small text file; NULL =
+ * do not persist); a readable file is loaded first.  With the environment variable
+ * MOMMS_TUNE_LOG set to a path, every candidate's time is appended there as a text line.
+ * Single products (momms_gemm, momms_gemm_ex and the calls built on them) use the plan of
+ * their bucket; batched calls take each problem's mode and encoding from its bucket's plan.
+ * Returns -3 / -4 for a bad count or NULL size arrays, -7 for a bad transposition. */
+int momms_tune_ex(momms_handle_t handle, const char* path, int64_t count, const int64_t* m,
+                  const int64_t* n, const int64_t* k, const int* op_a, const int* op_b,
+                  momms_stream_t stream);
+/* momms_tune_ex with every transposition N. */
 int momms_tune(momms_handle_t handle, const char* path, int64_t count, const int64_t* m,
                const int64_t* n, const int64_t* k, momms_stream_t stream);
 /* Load a plan table written by momms_tune (a missing or mismatching file is
  * ignored and reported as MOMMS_ERR_IO). */
 int momms_load_plans(momms_handle_t handle, const char* path);
+/* The plan the handle holds for the bucket of (op_a, op_b, m, n, k): tuned, or the built-in
+ * default (tuned = 0).  Returns -2 .. -7 for a bad argument (index). */
+int momms_get_plan(momms_handle_t handle, int op_a, int op_b, int64_t m, int64_t n, int64_t k,
+                   momms_plan_t* plan);
 
 /* ------------------------------------------------------- schedule query */
 /* The member's tile order (host side, no GPU needed): the i-th tile taken by CTA `cta`

@@ -29,20 +29,28 @@ constexpr int kAutoSliceMax = 14;         // workspace sized for this many slice
 constexpr bool kCtaPairsAuto = false;
 bool pairs_on(int mode) { return mode == 2 || (mode == 0 && kCtaPairsAuto); }
 
+// What runs one product of a size bucket: the engine, the member (tile order), the slice count,
+// and for the emulated engine the tile width, the integer encoding and the CTA pairs.  Zero in the
+// last four means "the library's rule" (the handle's own setting takes precedence when it is not
+// automatic).
 struct Plan {
     int mode;
     int member;
     int slices;  // 0 = data-driven rule
+    int tile_n;  // 0 = automatic, 96, 192
+    int scheme;  // MOMMS_SCHEME_AUTO / SLICES / MODULI
+    int pairs;   // 0 = automatic, 1 = off, 2 = on
 };
 
-// size bucket = (ceil log2 m, ceil log2 n, ceil log2 k)
+// size bucket = (ceil log2 m, ceil log2 n, ceil log2 k) and the two transpositions
 inline int lg2c(int64_t x) {
     int b = 0;
     while ((int64_t(1) << b) < x && b < 62) ++b;
     return b;
 }
-inline uint32_t bucket_key(int64_t m, int64_t n, int64_t k) {
-    return static_cast<uint32_t>(lg2c(m) | (lg2c(n) << 8) | (lg2c(k) << 16));
+inline uint32_t bucket_key(int64_t m, int64_t n, int64_t k, int opa = MOMMS_OP_N, int opb = MOMMS_OP_N) {
+    return static_cast<uint32_t>(lg2c(m) | (lg2c(n) << 8) | (lg2c(k) << 16) | ((opa & 1) << 24) |
+                                 ((opb & 1) << 25));
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -274,9 +282,9 @@ Plan default_plan(int64_t m, int64_t n, int64_t k) {
     return p;
 }
 
-Plan pick_plan(momms_handle_t h, int64_t m, int64_t n, int64_t k) {
+Plan pick_plan(momms_handle_t h, int64_t m, int64_t n, int64_t k, int opa = MOMMS_OP_N, int opb = MOMMS_OP_N) {
     Plan p = default_plan(m, n, k);
-    auto it = h->plans.find(bucket_key(m, n, k));
+    auto it = h->plans.find(bucket_key(m, n, k, opa, opb));
     if (it != h->plans.end()) p = it->second;
     if (h->mode != MOMMS_MODE_AUTO) p.mode = h->mode;
     if (h->member != MOMMS_MEMBER_AUTO) p.member = h->member;
@@ -705,7 +713,8 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
 // slice count nothing is read back, and a repeated call with the same problems only re-enqueues
 // the five kernels (tables are uploaded only when they change), so it can be graph-captured.
 // With the data-driven slice count the per-problem spreads are read back once per call.
-int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, const int64_t* m, const int64_t* n,
+int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, const std::vector<int>& scheme_of,
+                         const int64_t* m, const int64_t* n,
                          const int64_t* k, const double* alpha, const double* const* A, const int64_t* lda,
                          const double* const* B, const int64_t* ldb, const double* beta, double* const* C,
                          const int64_t* ldc, cudaStream_t s) {
@@ -830,8 +839,10 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
         momms::CrtRecon cr;
         const int w = auto_s ? std::min(bb * S[i], std::max(static_cast<int>(std::ceil(rule_bits[i])), bb * S[i] - bb + 1))
                              : bb * S[i];
-        mod[i] = S[i] <= MOMMS_MAX_SLICES && use_moduli(h->scheme, w, S[i], bb, k[idx[i]], &cc, &cr);
-        if (mod[i] && h->scheme == MOMMS_SCHEME_AUTO) {
+        // the handle's encoding, or where it is AUTO the problem's plan's
+        const int sch = h->scheme == MOMMS_SCHEME_AUTO ? scheme_of[i] : h->scheme;
+        mod[i] = S[i] <= MOMMS_MAX_SLICES && use_moduli(sch, w, S[i], bb, k[idx[i]], &cc, &cr);
+        if (mod[i] && sch == MOMMS_SCHEME_AUTO) {
             const double kk = static_cast<double>(k[idx[i]]);
             mod[i] = cc.N * (kk + 850.0) <= 0.9 * (S[i] * (S[i] + 1) / 2) * kk;
         }
@@ -986,10 +997,20 @@ int gemm_dispatch(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int6
         h->report.launches = beta == 1.0 ? 0 : 1;
         return scale_c(m, n, beta, C, ldc, s);
     }
-    const Plan p = pick_plan(h, m, n, k);
+    const Plan p = pick_plan(h, m, n, k, opa, opb);
     const int member = p.member == MOMMS_MEMBER_AUTO ? MOMMS_MEMBER_C2 : p.member;
-    if (p.mode == MOMMS_MODE_EMULATED)
-        return run_emulated(h, opa, opb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, member, p.slices, s);
+    if (p.mode == MOMMS_MODE_EMULATED) {
+        // the plan's tile width, encoding and CTA pairs where the handle leaves them automatic
+        const int tile_n = h->tile_n, scheme = h->scheme, pairs = h->cta_pairs;
+        if (tile_n == 0) h->tile_n = p.tile_n;
+        if (scheme == MOMMS_SCHEME_AUTO) h->scheme = p.scheme;
+        if (pairs == 0) h->cta_pairs = p.pairs;
+        const int rc = run_emulated(h, opa, opb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, member, p.slices, s);
+        h->tile_n = tile_n;
+        h->scheme = scheme;
+        h->cta_pairs = pairs;
+        return rc;
+    }
     return run_native(h, opa, opb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, member, s);
 }
 
@@ -1253,7 +1274,7 @@ int momms_workspace_size(momms_handle_t h, int op_a, int op_b, int64_t m, int64_
     if (n < 0) return -5;
     if (k < 0) return -6;
     if (!bytes) return -7;
-    const Plan p = pick_plan(h, m, n, k);
+    const Plan p = pick_plan(h, m, n, k, op_a, op_b);
     if (p.mode == MOMMS_MODE_NATIVE || m == 0 || n == 0 || k == 0) {
         *bytes = 0;
         return MOMMS_OK;
@@ -1356,97 +1377,101 @@ int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const 
         if (m[i] > INT32_MAX / 2 || n[i] > INT32_MAX / 2 || k[i] > INT32_MAX / 2) return MOMMS_ERR_UNSUPPORTED;
         total_flops += 2.0 * static_cast<double>(m[i]) * static_cast<double>(n[i]) * static_cast<double>(k[i]);
     }
-    // AUTO: the emulated pipeline (five launches for the whole batch) once the batch's work
-    // amortises them, as for a single product of that many flops
-    const bool emulated = h->mode == MOMMS_MODE_EMULATED || (h->mode == MOMMS_MODE_AUTO && total_flops >= 2.0e9);
-    if (emulated) {
-        // problems with work go to one batched pipeline; the rest only scale C
-        std::vector<int64_t> idx;
-        int64_t launches = 0;
-        for (int64_t i = 0; i < count; ++i) {
-            if (m[i] == 0 || n[i] == 0) continue;
-            if (k[i] == 0 || alpha[i] == 0.0) {
-                int rc = scale_c(m[i], n[i], beta[i], C[i], ldc[i], s);
-                if (rc) return rc;
-                ++launches;
-                continue;
-            }
-            idx.push_back(i);
-        }
-        if (idx.empty()) {
-            reset_report(h);
-            h->report.launches = launches;
-            return MOMMS_OK;
-        }
-        if (idx.size() > (size_t(1) << 24)) return MOMMS_ERR_UNSUPPORTED;
-        int rc = run_emulated_batched(h, idx, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
-        if (rc) return rc;
-        h->report.launches += launches;
-        return MOMMS_OK;
-    }
-    // native: one persistent launch over a device tile table
-    std::vector<BatchProblem> probs;
-    probs.reserve(static_cast<size_t>(count));
-    int64_t tiles = 0;
-    int64_t scale_only = 0;
+    // The engine of each problem: the tuned plan of its size bucket where the handle holds one
+    // (AUTO mode), else the call's rule -- the emulated pipeline (five launches for the whole batch)
+    // once the batch's work amortises them, as for a single product of that many flops.  A plan's
+    // encoding also applies per problem when the handle's scheme is AUTO.
+    const bool call_emulated =
+        h->mode == MOMMS_MODE_EMULATED || (h->mode == MOMMS_MODE_AUTO && total_flops >= 2.0e9);
+    std::vector<int64_t> emu_idx, nat_idx;
+    std::vector<int> emu_scheme;
+    int64_t launches = 0;
     for (int64_t i = 0; i < count; ++i) {
         if (m[i] == 0 || n[i] == 0) continue;
-        if (k[i] == 0 || alpha[i] == 0.0) {
+        if (k[i] == 0 || alpha[i] == 0.0) {  // C := beta C only
             int rc = scale_c(m[i], n[i], beta[i], C[i], ldc[i], s);
             if (rc) return rc;
-            ++scale_only;
+            ++launches;
             continue;
         }
-        BatchProblem p{};
-        p.A = A[i]; p.B = B[i]; p.C = C[i];
-        p.lda = lda[i]; p.ldb = ldb[i]; p.ldc = ldc[i];
-        p.m = static_cast<int32_t>(m[i]); p.n = static_cast<int32_t>(n[i]); p.k = static_cast<int32_t>(k[i]);
-        const int64_t tm = (m[i] + momms::kNativeBM - 1) / momms::kNativeBM;
-        const int64_t tn = (n[i] + momms::kNativeBN - 1) / momms::kNativeBN;
-        p.tiles_n = static_cast<int32_t>(tn);
-        p.tile0 = tiles;
-        p.alpha = alpha[i]; p.beta = beta[i];
-        tiles += tm * tn;
-        probs.push_back(p);
-    }
-    if (probs.empty()) {
-        reset_report(h);
-        h->report.launches = scale_only;
-        return MOMMS_OK;
-    }
-    const size_t bytes = probs.size() * sizeof(BatchProblem);
-    const bool same_table = h->host_probs.size() == probs.size() && h->dev_probs &&
-                            std::memcmp(h->host_probs.data(), probs.data(), bytes) == 0;
-    if (!same_table) {
-        if (h->dev_probs_cap < bytes) {
-            if (h->dev_probs) {
-                cudaDeviceSynchronize();
-                cudaFree(h->dev_probs);
-                h->dev_probs = nullptr;
-                h->dev_probs_cap = 0;
-            }
-            if (cudaMalloc(&h->dev_probs, bytes) != cudaSuccess) {
-                cudaGetLastError();
-                return MOMMS_ERR_ALLOC;
-            }
-            h->dev_probs_cap = bytes;
+        bool emu = call_emulated;
+        int sch = MOMMS_SCHEME_AUTO;
+        auto it = h->plans.find(bucket_key(m[i], n[i], k[i]));
+        if (it != h->plans.end()) {
+            if (h->mode == MOMMS_MODE_AUTO) emu = it->second.mode == MOMMS_MODE_EMULATED;
+            sch = it->second.scheme;
         }
-        // A pageable-memory copy: it has completed when the call returns.  An identical
-        // table is not uploaded again, so a call repeated with the same problems enqueues
-        // only the kernel and can be captured in a CUDA graph after one eager call.
-        if (cudaMemcpyAsync(h->dev_probs, probs.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
-            return MOMMS_ERR_CUDA;
-        h->host_probs = probs;
+        if (emu) {
+            emu_idx.push_back(i);
+            emu_scheme.push_back(sch);
+        } else {
+            nat_idx.push_back(i);
+        }
     }
-    cudaError_t e = momms::launch_native_batched(h->dev_probs, static_cast<int>(probs.size()), tiles, s);
-    if (e != cudaSuccess) return MOMMS_ERR_CUDA;
+    if (emu_idx.size() > (size_t(1) << 24)) return MOMMS_ERR_UNSUPPORTED;
+    momms_report_t rep{};
+    if (!emu_idx.empty()) {
+        int rc = run_emulated_batched(h, emu_idx, emu_scheme, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+        if (rc) return rc;
+        rep = h->report;
+        launches += h->report.launches;
+    }
+    if (!nat_idx.empty()) {
+        // native: one persistent launch over a device tile table
+        std::vector<BatchProblem> probs;
+        probs.reserve(nat_idx.size());
+        int64_t tiles = 0;
+        for (int64_t i : nat_idx) {
+            BatchProblem p{};
+            p.A = A[i]; p.B = B[i]; p.C = C[i];
+            p.lda = lda[i]; p.ldb = ldb[i]; p.ldc = ldc[i];
+            p.m = static_cast<int32_t>(m[i]); p.n = static_cast<int32_t>(n[i]); p.k = static_cast<int32_t>(k[i]);
+            const int64_t tm = (m[i] + momms::kNativeBM - 1) / momms::kNativeBM;
+            const int64_t tn = (n[i] + momms::kNativeBN - 1) / momms::kNativeBN;
+            p.tiles_n = static_cast<int32_t>(tn);
+            p.tile0 = tiles;
+            p.alpha = alpha[i]; p.beta = beta[i];
+            tiles += tm * tn;
+            probs.push_back(p);
+        }
+        const size_t bytes = probs.size() * sizeof(BatchProblem);
+        const bool same_table = h->host_probs.size() == probs.size() && h->dev_probs &&
+                                std::memcmp(h->host_probs.data(), probs.data(), bytes) == 0;
+        if (!same_table) {
+            if (h->dev_probs_cap < bytes) {
+                if (h->dev_probs) {
+                    cudaDeviceSynchronize();
+                    cudaFree(h->dev_probs);
+                    h->dev_probs = nullptr;
+                    h->dev_probs_cap = 0;
+                }
+                if (cudaMalloc(&h->dev_probs, bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    return MOMMS_ERR_ALLOC;
+                }
+                h->dev_probs_cap = bytes;
+            }
+            // A pageable-memory copy: it has completed when the call returns.  An identical
+            // table is not uploaded again, so a call repeated with the same problems enqueues
+            // only the kernel and can be captured in a CUDA graph after one eager call.
+            if (cudaMemcpyAsync(h->dev_probs, probs.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return MOMMS_ERR_CUDA;
+            h->host_probs = probs;
+        }
+        cudaError_t e = momms::launch_native_batched(h->dev_probs, static_cast<int>(probs.size()), tiles, s);
+        if (e != cudaSuccess) return MOMMS_ERR_CUDA;
+        launches += 1;
+        if (emu_idx.empty()) {
+            rep.mode = MOMMS_MODE_NATIVE;
+            rep.member = MOMMS_MEMBER_C2;
+            rep.tile_m = momms::kNativeBM;
+            rep.tile_n = momms::kNativeBN;
+            rep.k_passes = 1;
+        }
+    }
     reset_report(h);
-    h->report.mode = MOMMS_MODE_NATIVE;
-    h->report.member = MOMMS_MEMBER_C2;
-    h->report.tile_m = momms::kNativeBM;
-    h->report.tile_n = momms::kNativeBN;
-    h->report.k_passes = 1;
-    h->report.launches = 1 + scale_only;
+    h->report = rep;
+    h->report.launches = launches;
     return MOMMS_OK;
 }
 
@@ -1639,7 +1664,7 @@ static std::string plan_header() {
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, dev);
     char buf[sizeof(prop.name) + 64];  // the device name (up to 255 characters) and the numbers fit
-    std::snprintf(buf, sizeof(buf), "momms-plan v1 %s sms=%d l2=%d", prop.name, prop.multiProcessorCount,
+    std::snprintf(buf, sizeof(buf), "momms-plan v2 %s sms=%d l2=%d", prop.name, prop.multiProcessorCount,
                   prop.l2CacheSize);
     for (char* c = buf; *c; ++c)
         if (*c == '\n') *c = ' ';
@@ -1664,12 +1689,15 @@ int momms_load_plans(momms_handle_t h, const char* path) {
     }
     std::map<uint32_t, Plan> plans;
     unsigned key;
-    int mode, member, slices;
-    while (std::fscanf(fp, "%u %d %d %d", &key, &mode, &member, &slices) == 4) {
+    int mode, member, slices, tile_n, scheme, pairs;
+    while (std::fscanf(fp, "%u %d %d %d %d %d %d", &key, &mode, &member, &slices, &tile_n, &scheme, &pairs) == 7) {
         if (mode < MOMMS_MODE_NATIVE || mode > MOMMS_MODE_EMULATED) continue;
         if (member < MOMMS_MEMBER_C2 || member > MOMMS_MEMBER_A1) continue;
         if (slices < 0 || slices > MOMMS_MAX_SLICES) continue;
-        plans[key] = Plan{mode, member, slices};
+        if (tile_n != 0 && tile_n != 96 && tile_n != 192) continue;
+        if (scheme < MOMMS_SCHEME_AUTO || scheme > MOMMS_SCHEME_MODULI) continue;
+        if (pairs < 0 || pairs > 2) continue;
+        plans[key] = Plan{mode, member, slices, tile_n, scheme, pairs};
     }
     std::fclose(fp);
     for (auto& kv : plans) h->plans[kv.first] = kv.second;
@@ -1682,7 +1710,8 @@ static int save_plans(momms_handle_t h, const char* path) {
     if (!fp) return MOMMS_ERR_IO;
     std::fprintf(fp, "%s\n", plan_header().c_str());
     for (auto& kv : h->plans)
-        std::fprintf(fp, "%u %d %d %d\n", kv.first, kv.second.mode, kv.second.member, kv.second.slices);
+        std::fprintf(fp, "%u %d %d %d %d %d %d\n", kv.first, kv.second.mode, kv.second.member, kv.second.slices,
+                     kv.second.tile_n, kv.second.scheme, kv.second.pairs);
     std::fclose(fp);
     if (std::rename(tmp.c_str(), path) != 0) return MOMMS_ERR_IO;
     return MOMMS_OK;
@@ -1699,57 +1728,95 @@ __global__ void fill_uniform_kernel(double* x, int64_t n, uint64_t seed) {
     }
 }
 
-int momms_tune(momms_handle_t h, const char* path, int64_t count, const int64_t* m, const int64_t* n,
-               const int64_t* k, momms_stream_t stream) {
+// The candidate plans of one bucket: the native engine (its members time the same: the FP64 pipe
+// bounds it), and for the emulated engine every member x tile width x encoding, with CTA pairs on
+// and off where they apply (moduli, 192-wide tiles).  The slice count stays data-driven.
+static std::vector<Plan> tune_candidates(int64_t k) {
+    std::vector<Plan> c = {{MOMMS_MODE_NATIVE, MOMMS_MEMBER_C2, 0, 0, MOMMS_SCHEME_AUTO, 0}};
+    for (int mem = MOMMS_MEMBER_C2; mem <= MOMMS_MEMBER_A1; ++mem)
+        for (int tn : {192, 96})
+            for (int sch : {MOMMS_SCHEME_SLICES, MOMMS_SCHEME_MODULI}) {
+                if (sch == MOMMS_SCHEME_MODULI && k > momms::crt_max_k()) continue;
+                if (sch == MOMMS_SCHEME_MODULI && tn == 192) {
+                    c.push_back({MOMMS_MODE_EMULATED, mem, 0, tn, sch, 1});
+                    c.push_back({MOMMS_MODE_EMULATED, mem, 0, tn, sch, 2});
+                } else {
+                    c.push_back({MOMMS_MODE_EMULATED, mem, 0, tn, sch, 1});
+                }
+            }
+    return c;
+}
+
+int momms_tune_ex(momms_handle_t h, const char* path, int64_t count, const int64_t* m, const int64_t* n,
+                  const int64_t* k, const int* op_a, const int* op_b, momms_stream_t stream) {
     if (!valid(h)) return MOMMS_ERR_HANDLE;
     if (count < 0) return -3;
     if (count > 0 && (!m || !n || !k)) return -4;
+    for (int64_t i = 0; i < count; ++i)
+        if ((op_a && op_a[i] != MOMMS_OP_N && op_a[i] != MOMMS_OP_T) ||
+            (op_b && op_b[i] != MOMMS_OP_N && op_b[i] != MOMMS_OP_T))
+            return -7;
     if (path) momms_load_plans(h, path);  // a missing or stale file is simply re-tuned
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int saved_mode = h->mode, saved_member = h->member, saved_slices = h->slices;
+    const int saved_tile = h->tile_n, saved_scheme = h->scheme, saved_pairs = h->cta_pairs;
+    FILE* log = nullptr;
+    if (const char* lp = std::getenv("MOMMS_TUNE_LOG")) log = std::fopen(lp, "a");
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int status = MOMMS_OK;
     for (int64_t i = 0; i < count && status == MOMMS_OK; ++i) {
         if (m[i] <= 0 || n[i] <= 0 || k[i] <= 0) continue;
-        const uint32_t key = bucket_key(m[i], n[i], k[i]);
+        const int oa = op_a ? op_a[i] : MOMMS_OP_N, ob = op_b ? op_b[i] : MOMMS_OP_N;
+        const uint32_t key = bucket_key(m[i], n[i], k[i], oa, ob);
         if (h->plans.count(key)) continue;
+        // op(A) is m x k, op(B) k x n; stored with the leading dimension of their stored rows
+        const int64_t ra = oa == MOMMS_OP_N ? m[i] : k[i], ca = oa == MOMMS_OP_N ? k[i] : m[i];
+        const int64_t rb = ob == MOMMS_OP_N ? k[i] : n[i], cb = ob == MOMMS_OP_N ? n[i] : k[i];
         double *A = nullptr, *B = nullptr, *C = nullptr;
-        if (cudaMalloc(&A, sizeof(double) * m[i] * k[i]) != cudaSuccess ||
-            cudaMalloc(&B, sizeof(double) * k[i] * n[i]) != cudaSuccess ||
+        if (cudaMalloc(&A, sizeof(double) * ra * ca) != cudaSuccess ||
+            cudaMalloc(&B, sizeof(double) * rb * cb) != cudaSuccess ||
             cudaMalloc(&C, sizeof(double) * m[i] * n[i]) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(A); cudaFree(B); cudaFree(C);
             status = MOMMS_ERR_ALLOC;
             break;
         }
-        fill_uniform_kernel<<<1024, 256, 0, s>>>(A, m[i] * k[i], 1);
-        fill_uniform_kernel<<<1024, 256, 0, s>>>(B, k[i] * n[i], 2);
-        Plan best{MOMMS_MODE_NATIVE, MOMMS_MEMBER_C2, 0};
-        float best_ms = 1e30f;
-        // candidate plans: native (member does not matter for a compute-bound FP64 pipe)
-        // and emulated with each member; the slice count stays data-driven (0).
-        std::vector<Plan> cands = {{MOMMS_MODE_NATIVE, MOMMS_MEMBER_C2, 0}};
-        for (int mem = MOMMS_MEMBER_C2; mem <= MOMMS_MEMBER_A1; ++mem) cands.push_back({MOMMS_MODE_EMULATED, mem, 0});
-        // the slice count for timing: the rule's choice for this data (uniform inputs)
-        h->mode = MOMMS_MODE_EMULATED; h->member = MOMMS_MEMBER_C2; h->slices = 0;
-        int rc0 = gemm_dispatch(h, 0, 0, m[i], n[i], k[i], 1.0, A, m[i], B, k[i], 0.0, C, m[i], s);
-        const int S_rule = rc0 == MOMMS_OK ? h->report.slices : 8;
-        for (const Plan& c : cands) {
-            h->mode = c.mode; h->member = c.member; h->slices = c.mode == MOMMS_MODE_EMULATED ? S_rule : 0;
-            int rc = gemm_dispatch(h, 0, 0, m[i], n[i], k[i], 1.0, A, m[i], B, k[i], 0.0, C, m[i], s);  // warm-up
+        fill_uniform_kernel<<<1024, 256, 0, s>>>(A, ra * ca, 1);
+        fill_uniform_kernel<<<1024, 256, 0, s>>>(B, rb * cb, 2);
+        Plan best{MOMMS_MODE_NATIVE, MOMMS_MEMBER_C2, 0, 0, MOMMS_SCHEME_AUTO, 0};
+        double best_ms = 1e300;
+        for (const Plan& c : tune_candidates(k[i])) {
+            h->mode = c.mode; h->member = c.member; h->slices = 0;
+            h->tile_n = c.tile_n; h->scheme = c.scheme; h->cta_pairs = c.pairs;
+            auto call = [&]() {
+                return gemm_dispatch(h, oa, ob, m[i], n[i], k[i], 1.0, A, ra, B, rb, 0.0, C, m[i], s);
+            };
+            int rc = call();  // warm-up (workspace, kernel attributes)
             if (rc) continue;
-            cudaEventRecord(e0, s);
-            const int reps = 2;
-            for (int r = 0; r < reps && rc == MOMMS_OK; ++r)
-                rc = gemm_dispatch(h, 0, 0, m[i], n[i], k[i], 1.0, A, m[i], B, k[i], 0.0, C, m[i], s);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rc == MOMMS_OK && ms < best_ms) {
-                best_ms = ms;
+            // at least three timed calls and at least 20 ms of them (at most 50 calls)
+            int reps = 0;
+            float total = 0.f;
+            while (rc == MOMMS_OK && reps < 50 && (reps < 3 || total < 20.f)) {
+                cudaEventRecord(e0, s);
+                rc = call();
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                total += ms;
+                ++reps;
+            }
+            if (rc != MOMMS_OK) continue;
+            const double per = total / reps;
+            if (log)
+                std::fprintf(log, "m=%lld n=%lld k=%lld opa=%d opb=%d mode=%d member=%d tile_n=%d scheme=%d pairs=%d "
+                                  "ms=%.4f reps=%d\n",
+                             static_cast<long long>(m[i]), static_cast<long long>(n[i]), static_cast<long long>(k[i]),
+                             oa, ob, c.mode, c.member, c.tile_n, c.scheme, c.pairs, per, reps);
+            if (per < best_ms) {
+                best_ms = per;
                 best = c;
             }
         }
@@ -1758,10 +1825,37 @@ int momms_tune(momms_handle_t h, const char* path, int64_t count, const int64_t*
         cudaFree(A); cudaFree(B); cudaFree(C);
     }
     h->mode = saved_mode; h->member = saved_member; h->slices = saved_slices;
+    h->tile_n = saved_tile; h->scheme = saved_scheme; h->cta_pairs = saved_pairs;
+    if (log) std::fclose(log);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (status == MOMMS_OK && path) status = save_plans(h, path);
     return status;
+}
+
+int momms_tune(momms_handle_t h, const char* path, int64_t count, const int64_t* m, const int64_t* n,
+               const int64_t* k, momms_stream_t stream) {
+    return momms_tune_ex(h, path, count, m, n, k, nullptr, nullptr, stream);
+}
+
+int momms_get_plan(momms_handle_t h, int op_a, int op_b, int64_t m, int64_t n, int64_t k, momms_plan_t* plan) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (op_a != MOMMS_OP_N && op_a != MOMMS_OP_T) return -2;
+    if (op_b != MOMMS_OP_N && op_b != MOMMS_OP_T) return -3;
+    if (m < 1) return -4;
+    if (n < 1) return -5;
+    if (k < 1) return -6;
+    if (!plan) return -7;
+    auto it = h->plans.find(bucket_key(m, n, k, op_a, op_b));
+    const Plan p = it != h->plans.end() ? it->second : default_plan(m, n, k);
+    plan->tuned = it != h->plans.end() ? 1 : 0;
+    plan->mode = p.mode;
+    plan->member = p.member;
+    plan->slices = p.slices;
+    plan->tile_n = p.tile_n;
+    plan->scheme = p.scheme;
+    plan->cta_pairs = p.pairs;
+    return MOMMS_OK;
 }
 
 // ------------------------------------------------------------------ symmetric rank-k update

@@ -57,6 +57,11 @@ class Report(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class PlanT(ctypes.Structure):
+    _fields_ = [("tuned", ctypes.c_int), ("mode", ctypes.c_int), ("member", ctypes.c_int), ("slices", ctypes.c_int),
+                ("tile_n", ctypes.c_int), ("scheme", ctypes.c_int), ("cta_pairs", ctypes.c_int)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -100,6 +105,8 @@ _SIGS = {
     "momms_emu_scratch_bytes_for": ([_I64, _I64, _I64, _I32], _SZ),
     "momms_tune": ([_VP, ctypes.c_char_p, _I64, _VP, _VP, _VP, _VP], _I32),
     "momms_load_plans": ([_VP, ctypes.c_char_p], _I32),
+    "momms_tune_ex": ([_VP, ctypes.c_char_p, _I64, _VP, _VP, _VP, _VP, _VP, _VP], _I32),
+    "momms_get_plan": ([_VP, _I32, _I32, _I64, _I64, _I64, _VP], _I32),
     "momms_probe_peak": ([_I32, ctypes.POINTER(_DBL), _VP], _I32),
     "momms_stream_copy": ([_VP, _VP, _SZ, _I32, _I32, _VP], _I32),
     "momms_gemm_emulated_noalloc": ([_I32, _I32, _I64, _I64, _I64, _I32, _DBL, _VP, _I64, _VP, _I64, _DBL, _VP,
@@ -380,11 +387,21 @@ class Handle:
         check(lib().momms_set_workspace(self.ptr, _VP(ptr), nbytes), "momms_set_workspace")
 
     def tune(self, shapes, path=None, stream=None):
+        """shapes: (m, n, k) or (m, n, k, op_a, op_b) tuples."""
         m = np.ascontiguousarray([s[0] for s in shapes], dtype=np.int64)
         n = np.ascontiguousarray([s[1] for s in shapes], dtype=np.int64)
         k = np.ascontiguousarray([s[2] for s in shapes], dtype=np.int64)
-        check(lib().momms_tune(self.ptr, path.encode() if path else None, len(shapes), _VP(m.ctypes.data),
-                               _VP(n.ctypes.data), _VP(k.ctypes.data), _stream(stream)), "momms_tune")
+        oa = np.ascontiguousarray([s[3] if len(s) > 3 else OP_N for s in shapes], dtype=np.int32)
+        ob = np.ascontiguousarray([s[4] if len(s) > 4 else OP_N for s in shapes], dtype=np.int32)
+        check(lib().momms_tune_ex(self.ptr, path.encode() if path else None, len(shapes), _VP(m.ctypes.data),
+                                  _VP(n.ctypes.data), _VP(k.ctypes.data), _VP(oa.ctypes.data), _VP(ob.ctypes.data),
+                                  _stream(stream)), "momms_tune_ex")
+
+    def plan(self, m, n, k, op_a=OP_N, op_b=OP_N):
+        """The plan of the bucket of (op_a, op_b, m, n, k) as a dict (tuned = 0: the built-in default)."""
+        p = PlanT()
+        check(lib().momms_get_plan(self.ptr, op_a, op_b, m, n, k, ctypes.byref(p)), "momms_get_plan")
+        return {f: getattr(p, f) for f, _ in PlanT._fields_}
 
     def load_plans(self, path):
         return lib().momms_load_plans(self.ptr, path.encode())
