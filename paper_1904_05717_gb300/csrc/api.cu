@@ -473,6 +473,7 @@ int run_emulated_planned(momms_handle_t h, int opa, int opb, int64_t m, int64_t 
     a.used_ctas = &used_ctas; a.used_group = &used_group; a.used_launches = &used_launches;
     a.used_pairs = &used_pairs;
     // the digit encoding's products (nothing to do when the plan chose moduli) ...
+    a.withhold = momms::emu_debug_take_withhold();  // (test hook: whichever launch the plan runs)
     momms::EmuGemmArgs as = a;
     as.S = S_alloc;
     cudaError_t ce;
@@ -525,7 +526,8 @@ int run_emulated(momms_handle_t h, int opa, int opb, int64_t m, int64_t n, int64
                  int64_t ldc, int member, int S, cudaStream_t s, int tri = 0, int kcap = 0) {
     const int bb = h->digit_bits;
     h->report_pending = false;
-    if (S == 0 && !tri && bb == kDigitBits && h->plan_mode)
+    // (the fused reconstruction needs the moduli count at launch: it keeps the host plan)
+    if (S == 0 && !tri && bb == kDigitBits && h->plan_mode && h->crt_fusion != 2)
         return run_emulated_planned(h, opa, opb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, member, s, kcap);
     if (tri && (m != n || A != B || opa == opb)) return MOMMS_ERR_UNSUPPORTED;
     if (S > MOMMS_MAX_SLICES) return MOMMS_ERR_UNSUPPORTED;

@@ -1449,7 +1449,7 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         if (a.used_ctas) *a.used_ctas = static_cast<int>(ctas);
         if (a.used_group) *a.used_group = p.group;
         p.table = nullptr;
-        p.withhold = g_withhold.exchange(0);
+        p.withhold = a.withhold > 0 ? 1 : g_withhold.exchange(0);
         if (a.plan) {
             // S or N from the device plan; the pass above was sized for the largest the plan may pick
             p.plan = a.plan;
@@ -1807,6 +1807,7 @@ int emu_default_group(int64_t ctas, int tiles_m, int tiles_n) {
 }
 
 void emu_debug_withhold_load() { emu::g_withhold.store(1); }
+int emu_debug_take_withhold() { return emu::g_withhold.exchange(0); }
 
 cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_t stream) {
     using namespace emu;

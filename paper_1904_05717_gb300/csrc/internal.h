@@ -174,6 +174,7 @@ struct EmuGemmArgs {
     // pass structure is that of S (or N) as given here, the largest the plan can pick.
     const EmuPlan* plan;
     int* used_pairs;       // optional out: 1 when the residue product ran on CTA pairs
+    int withhold;          // 1: the timeout test hook for this launch (else the armed process flag)
 };
 constexpr int kEmuBM = 128, kEmuBK = 64, kEmuBNMax = 192;
 
@@ -269,6 +270,9 @@ int emu_pick_bn(int64_t m, int64_t n, int64_t k, int requested, int units_per_ti
 int emu_default_group(int64_t ctas, int tiles_m, int tiles_n);
 // Arms the timeout test hook: the next slice-product launch leaves one stage of CTA 0 empty.
 void emu_debug_withhold_load();
+// Takes (and clears) the armed test hook: a call that enqueues several product launches of which
+// the device plan picks one hands it to each of them.
+int emu_debug_take_withhold();
 // Launches the slice-product kernel once per k pass; *passes receives the count.
 cudaError_t launch_emu_slice_gemm(const EmuGemmArgs& a, int* passes, cudaStream_t stream);
 size_t emu_scratch_bytes(int num_sms);

@@ -51,7 +51,7 @@ def test_withheld_stage_in_a_batched_call():
     # the batched residue-product launch takes the hook too; the call after it is correct
     sizes = [(130, 200, 300), (64, 64, 64), (257, 100, 513)]
     probs = [inputs(m, n, k, 5200 + 10 * i) for i, (m, n, k) in enumerate(sizes)]
-    h = M.Handle(mode=M.MODE_EMULATED, slices=6, scheme=M.SCHEME_MODULI)
+    h = M.Handle(mode=M.MODE_EMULATED, slices=8, scheme=M.SCHEME_MODULI)
     dA = [M.DeviceMatrix.from_numpy(A) for A, _, _ in probs]
     dB = [M.DeviceMatrix.from_numpy(B) for _, B, _ in probs]
     for attempt in range(2):
