@@ -106,6 +106,7 @@ typedef struct {
     int operand_bits;    /* emulated: integer width of the operands (7 S for slices) */
     int crt_fused;       /* moduli: 1 when the residue product rebuilt C itself       */
     int cta_pairs;       /* moduli: 1 when the residue products ran on CTA pairs      */
+    int ooc_resident;    /* momms_gemm_host: 0 Resident C, 1 Resident A at HBM level  */
 } momms_report_t;
 
 /* ---------------------------------------------------------------- handles */
@@ -438,6 +439,17 @@ int momms_gemm_host(momms_handle_t handle, int64_t m, int64_t n, int64_t k, doub
                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                     double* C, int64_t ldc, size_t device_bytes, int64_t block,
                     momms_stream_t stream);
+
+/* The member of momms_gemm_host at the HBM level, which with the handle's member inside each
+ * block product (momms_set_member: the L2 level) and the accumulator tile (registers / TMEM)
+ * makes a four-level member in the paper's naming (Sec. 3.2, Fig. 8's C4A2C0): host memory ->
+ * HBM -> L2 -> SM.  0 = Resident C (default): a b x b block of C stays in HBM, A and B stream
+ * along k (Sec. 2.2.1).  1 = Resident A: a b x b block of A stays in HBM while the blocks of B and
+ * C of its block row stream through (Sec. 2.2.2): host<->device words A m k, B k n ceil(m/b),
+ * C read m n (ceil(k/b) - 1 + [beta != 0]) and written m n ceil(k/b) -- better than Resident C
+ * when k <= b and n is large (a rank-k update: A crosses the link once instead of ceil(n/b)
+ * times).  Returns -2 for other values. */
+int momms_set_host_resident(momms_handle_t handle, int resident);
 
 /* ------------------------------------------------ allocation-free variant */
 /* The emulated product (scale, split and slice-product kernels of EMULATED mode)

@@ -70,6 +70,7 @@ struct momms_handle_s {
     int scheme = MOMMS_SCHEME_AUTO; // integer encoding of the emulated product
     int crt_fusion = 0;             // 0 auto, 1 separate reconstruction launch, 2 fused
     int cta_pairs = 0;              // 0 auto, 1 off, 2 on: residue products on CTA pairs (cta_group::2)
+    int host_resident = 0;          // momms_gemm_host: 0 = Resident C, 1 = Resident A at the HBM level
     void* user_ws = nullptr;
     size_t user_ws_bytes = 0;
     void* own_ws = nullptr;
@@ -1174,6 +1175,13 @@ int momms_kernel_timing(momms_handle_t h, double* total_ms, int64_t* launches) {
     *total_ms = t;
     *launches = static_cast<int64_t>(h->kev_used);
     h->kev_used = 0;
+    return MOMMS_OK;
+}
+
+int momms_set_host_resident(momms_handle_t h, int resident) {
+    if (!valid(h)) return MOMMS_ERR_HANDLE;
+    if (resident != 0 && resident != 1) return -2;
+    h->host_resident = resident;
     return MOMMS_OK;
 }
 
@@ -2425,60 +2433,122 @@ int momms_gemm_host(momms_handle_t h, int64_t m, int64_t n, int64_t k, double al
         return MOMMS_ERR_CUDA;
     const bool kzero = (k == 0 || alpha == 0.0);
     int64_t step = 0, cblk = 0, h2d = 0, d2h = 0, launches = 0;
-    for (int64_t jc = 0; jc < n; jc += b) {
-        const int64_t nb = std::min(b, n - jc);
-        for (int64_t ic = 0; ic < m; ic += b, ++cblk) {
+    auto note = [&](const momms_report_t& r) {
+        launches += r.launches;
+        total.mode = r.mode;
+        total.member = r.member;
+        total.slices = std::max(total.slices, r.slices);
+        total.digit_bits = r.digit_bits;
+        total.k_passes = std::max(total.k_passes, r.k_passes);
+        total.tile_m = r.tile_m;
+        total.tile_n = r.tile_n;
+        total.ctas = r.ctas;
+        total.group = r.group;
+        total.est_err_ratio = std::max(total.est_err_ratio, r.est_err_ratio);
+        total.moduli = std::max(total.moduli, r.moduli);
+        total.operand_bits = std::max(total.operand_bits, r.operand_bits);
+        total.cta_pairs = r.cta_pairs;
+    };
+    if (h->host_resident == 1 && !kzero) {
+        // Resident A at the HBM level (Sec. 2.2.2): a b x b block of A stays on the device while the
+        // b x b blocks of B and C of its block row stream through; A is read once, B ceil(m/b) times,
+        // C read ceil(k/b) - 1 (+1 when beta != 0) times and written ceil(k/b) times.  B and C share a
+        // buffer slot (they change together); A has its own pair of slots.
+        const int64_t nbn = (n + b - 1) / b;
+        for (int64_t ic = 0; ic < m; ic += b) {
             const int64_t mb = std::min(b, m - ic);
-            const int cs = static_cast<int>(cblk & 1);
-            double* hC = C + ic + jc * ldc;
-            const bool read_c = beta != 0.0;
-            if (cudaStreamWaitEvent(h->ooc_in, c_free[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
-            if (read_c) {
-                if (copy_block(Cb[cs], b, hC, ldc, mb, nb, cudaMemcpyHostToDevice, h->ooc_in) != cudaSuccess)
-                    return MOMMS_ERR_CUDA;
-                h2d += mb * nb * 8;
-            }
-            if (cudaEventRecord(c_ready[cs], h->ooc_in) != cudaSuccess) return MOMMS_ERR_CUDA;
-            if (cudaStreamWaitEvent(s, c_ready[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
-            if (kzero) {
-                rc = scale_c(mb, nb, beta, Cb[cs], b, s);
-                if (rc) return rc;
-                launches += beta == 1.0 ? 0 : 1;
-            }
-            for (int64_t pc = 0; !kzero && pc < k; pc += b, ++step) {
+            for (int64_t pc = 0; pc < k; pc += b, ++step) {
                 const int64_t kb = std::min(b, k - pc);
                 const int as = static_cast<int>(step & 1);
-                if (cudaStreamWaitEvent(h->ooc_in, ab_free[as], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
-                if (copy_block(Ab[as], b, A + ic + pc * lda, lda, mb, kb, cudaMemcpyHostToDevice, h->ooc_in) !=
+                if (cudaStreamWaitEvent(h->ooc_in, ab_free[as], 0) != cudaSuccess ||
+                    copy_block(Ab[as], b, A + ic + pc * lda, lda, mb, kb, cudaMemcpyHostToDevice, h->ooc_in) !=
                         cudaSuccess ||
-                    copy_block(Bb[as], b, B + pc + jc * ldb, ldb, kb, nb, cudaMemcpyHostToDevice, h->ooc_in) !=
-                        cudaSuccess)
+                    cudaEventRecord(ab_ready[as], h->ooc_in) != cudaSuccess ||
+                    cudaStreamWaitEvent(s, ab_ready[as], 0) != cudaSuccess)
                     return MOMMS_ERR_CUDA;
-                h2d += (mb * kb + kb * nb) * 8;
-                if (cudaEventRecord(ab_ready[as], h->ooc_in) != cudaSuccess) return MOMMS_ERR_CUDA;
-                if (cudaStreamWaitEvent(s, ab_ready[as], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
-                rc = gemm_dispatch(h, MOMMS_OP_N, MOMMS_OP_N, mb, nb, kb, alpha, Ab[as], b, Bb[as], b,
-                                   pc == 0 ? beta : 1.0, Cb[cs], b, s);
-                if (rc) return rc;
-                launches += h->report.launches;
-                total.mode = h->report.mode;
-                total.member = h->report.member;
-                total.slices = std::max(total.slices, h->report.slices);
-                total.digit_bits = h->report.digit_bits;
-                total.k_passes = std::max(total.k_passes, h->report.k_passes);
-                total.tile_m = h->report.tile_m;
-                total.tile_n = h->report.tile_n;
-                total.ctas = h->report.ctas;
-                total.group = h->report.group;
-                total.est_err_ratio = std::max(total.est_err_ratio, h->report.est_err_ratio);
+                h2d += mb * kb * 8;
+                for (int64_t jc = 0; jc < n; jc += b, ++cblk) {
+                    const int64_t nb = std::min(b, n - jc);
+                    const int cs = static_cast<int>(cblk & 1);
+                    double* hC = C + ic + jc * ldc;
+                    const bool read_c = pc > 0 || beta != 0.0;
+                    // the slot's last copy-out is done (copy-outs complete in order, so with two or more
+                    // block columns that includes this C block's previous k step; with one, wait for it)
+                    if (cudaStreamWaitEvent(h->ooc_in, c_free[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+                    if (nbn == 1 && cudaStreamWaitEvent(h->ooc_in, c_free[1 - cs], 0) != cudaSuccess)
+                        return MOMMS_ERR_CUDA;
+                    if (copy_block(Bb[cs], b, B + pc + jc * ldb, ldb, kb, nb, cudaMemcpyHostToDevice, h->ooc_in) !=
+                        cudaSuccess)
+                        return MOMMS_ERR_CUDA;
+                    h2d += kb * nb * 8;
+                    if (read_c) {
+                        if (copy_block(Cb[cs], b, hC, ldc, mb, nb, cudaMemcpyHostToDevice, h->ooc_in) != cudaSuccess)
+                            return MOMMS_ERR_CUDA;
+                        h2d += mb * nb * 8;
+                    }
+                    if (cudaEventRecord(c_ready[cs], h->ooc_in) != cudaSuccess ||
+                        cudaStreamWaitEvent(s, c_ready[cs], 0) != cudaSuccess)
+                        return MOMMS_ERR_CUDA;
+                    rc = gemm_dispatch(h, MOMMS_OP_N, MOMMS_OP_N, mb, nb, kb, alpha, Ab[as], b, Bb[cs], b,
+                                       pc == 0 ? beta : 1.0, Cb[cs], b, s);
+                    if (rc) return rc;
+                    note(h->report);  // (a device-planned product's S and moduli stay pending: no readback here)
+                    if (cudaEventRecord(c_done[cs], s) != cudaSuccess ||
+                        cudaStreamWaitEvent(h->ooc_out, c_done[cs], 0) != cudaSuccess ||
+                        copy_block(hC, ldc, Cb[cs], b, mb, nb, cudaMemcpyDeviceToHost, h->ooc_out) != cudaSuccess ||
+                        cudaEventRecord(c_free[cs], h->ooc_out) != cudaSuccess)
+                        return MOMMS_ERR_CUDA;
+                    d2h += mb * nb * 8;
+                }
                 if (cudaEventRecord(ab_free[as], s) != cudaSuccess) return MOMMS_ERR_CUDA;
             }
-            if (cudaEventRecord(c_done[cs], s) != cudaSuccess) return MOMMS_ERR_CUDA;
-            if (cudaStreamWaitEvent(h->ooc_out, c_done[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
-            if (copy_block(hC, ldc, Cb[cs], b, mb, nb, cudaMemcpyDeviceToHost, h->ooc_out) != cudaSuccess)
-                return MOMMS_ERR_CUDA;
-            d2h += mb * nb * 8;
-            if (cudaEventRecord(c_free[cs], h->ooc_out) != cudaSuccess) return MOMMS_ERR_CUDA;
+        }
+    } else {
+        for (int64_t jc = 0; jc < n; jc += b) {
+            const int64_t nb = std::min(b, n - jc);
+            for (int64_t ic = 0; ic < m; ic += b, ++cblk) {
+                const int64_t mb = std::min(b, m - ic);
+                const int cs = static_cast<int>(cblk & 1);
+                double* hC = C + ic + jc * ldc;
+                const bool read_c = beta != 0.0;
+                if (cudaStreamWaitEvent(h->ooc_in, c_free[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+                if (read_c) {
+                    if (copy_block(Cb[cs], b, hC, ldc, mb, nb, cudaMemcpyHostToDevice, h->ooc_in) != cudaSuccess)
+                        return MOMMS_ERR_CUDA;
+                    h2d += mb * nb * 8;
+                }
+                if (cudaEventRecord(c_ready[cs], h->ooc_in) != cudaSuccess) return MOMMS_ERR_CUDA;
+                if (cudaStreamWaitEvent(s, c_ready[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+                if (kzero) {
+                    rc = scale_c(mb, nb, beta, Cb[cs], b, s);
+                    if (rc) return rc;
+                    launches += beta == 1.0 ? 0 : 1;
+                }
+                for (int64_t pc = 0; !kzero && pc < k; pc += b, ++step) {
+                    const int64_t kb = std::min(b, k - pc);
+                    const int as = static_cast<int>(step & 1);
+                    if (cudaStreamWaitEvent(h->ooc_in, ab_free[as], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+                    if (copy_block(Ab[as], b, A + ic + pc * lda, lda, mb, kb, cudaMemcpyHostToDevice, h->ooc_in) !=
+                            cudaSuccess ||
+                        copy_block(Bb[as], b, B + pc + jc * ldb, ldb, kb, nb, cudaMemcpyHostToDevice, h->ooc_in) !=
+                            cudaSuccess)
+                        return MOMMS_ERR_CUDA;
+                    h2d += (mb * kb + kb * nb) * 8;
+                    if (cudaEventRecord(ab_ready[as], h->ooc_in) != cudaSuccess) return MOMMS_ERR_CUDA;
+                    if (cudaStreamWaitEvent(s, ab_ready[as], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+                    rc = gemm_dispatch(h, MOMMS_OP_N, MOMMS_OP_N, mb, nb, kb, alpha, Ab[as], b, Bb[as], b,
+                                       pc == 0 ? beta : 1.0, Cb[cs], b, s);
+                    if (rc) return rc;
+                    note(h->report);  // (a device-planned product's S and moduli stay pending: no readback here)
+                    if (cudaEventRecord(ab_free[as], s) != cudaSuccess) return MOMMS_ERR_CUDA;
+                }
+                if (cudaEventRecord(c_done[cs], s) != cudaSuccess) return MOMMS_ERR_CUDA;
+                if (cudaStreamWaitEvent(h->ooc_out, c_done[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
+                if (copy_block(hC, ldc, Cb[cs], b, mb, nb, cudaMemcpyDeviceToHost, h->ooc_out) != cudaSuccess)
+                    return MOMMS_ERR_CUDA;
+                d2h += mb * nb * 8;
+                if (cudaEventRecord(c_free[cs], h->ooc_out) != cudaSuccess) return MOMMS_ERR_CUDA;
+            }
         }
     }
     // the caller's stream completes only after the last block is back in host memory
@@ -2486,6 +2556,7 @@ int momms_gemm_host(momms_handle_t h, int64_t m, int64_t n, int64_t k, double al
         if (cudaStreamWaitEvent(s, c_free[cs], 0) != cudaSuccess) return MOMMS_ERR_CUDA;
     total.launches = launches;
     total.ooc_block = b;
+    total.ooc_resident = h->host_resident == 1 && !kzero ? 1 : 0;
     total.h2d_bytes = h2d;
     total.d2h_bytes = d2h;
     h->report = total;

@@ -51,7 +51,7 @@ class Report(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("est_err_ratio", ctypes.c_double),
                 ("ooc_block", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("moduli", ctypes.c_int), ("operand_bits", ctypes.c_int), ("crt_fused", ctypes.c_int),
-                ("cta_pairs", ctypes.c_int)]
+                ("cta_pairs", ctypes.c_int), ("ooc_resident", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -77,6 +77,7 @@ _SIGS = {
     "momms_set_tile_n": ([_VP, _I32], _I32),
     "momms_set_scheme": ([_VP, _I32], _I32),
     "momms_set_plan_on_device": ([_VP, _I32], _I32),
+    "momms_set_host_resident": ([_VP, _I32], _I32),
     "momms_set_cta_pairs": ([_VP, _I32], _I32),
     "momms_set_crt_fusion": ([_VP, _I32], _I32),
     "momms_trsm": ([_VP, _I32, _I32, _I32, _I32, _I64, _I64, _DBL, _VP, _I64, _VP, _I64, _VP], _I32),
@@ -349,6 +350,9 @@ class Handle:
 
     def set_scheme(self, scheme):
         check(lib().momms_set_scheme(self.ptr, scheme), "momms_set_scheme")
+
+    def set_host_resident(self, resident):
+        check(lib().momms_set_host_resident(self.ptr, resident), "momms_set_host_resident")
 
     def set_plan_on_device(self, on):
         check(lib().momms_set_plan_on_device(self.ptr, on), "momms_set_plan_on_device")

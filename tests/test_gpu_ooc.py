@@ -90,3 +90,33 @@ def test_host_product_block_from_budget_and_argument_errors():
     assert M.momms_gemm_host(h, m, n, k, 1.0, 1 << 40, m, 1 << 41, k, 1.0, 1 << 42, m, 0, 300) == -14
     assert M.momms_gemm_host(h, m, n, k, 1.0, 1 << 40, m - 1, 1 << 41, k, 1.0, 1 << 42, m, 0, 256) == -7
     h.close()
+
+
+@pytest.mark.parametrize("shape", [(700, 530, 900), (600, 1100, 256), (300, 200, 700)])
+@pytest.mark.parametrize("member", [M.MEMBER_C2, M.MEMBER_A1])
+@pytest.mark.parametrize("beta", [1.0, 0.0])
+def test_four_level_members_resident_a_and_c_at_the_hbm_level(shape, member, beta):
+    # the four-level composition: the HBM-level member (Resident C or Resident A over host memory)
+    # times the L2-level member of each block product (C2 blocked, or A1: L2 not blocked for, the
+    # paper's skipped level, Sec. 4.3).  Host<->device bytes equal the closed forms of the
+    # HBM-level member exactly, the report names both members, and C meets the bound
+    m, n, k = shape
+    b = 256
+    A = syn.matrix("uniform", m, k, 931)
+    B = syn.matrix("uniform", k, n, 932)
+    C0 = syn.matrix("uniform", m, n, 933) if beta else np.full((m, n), np.nan, order="F")
+    for resident in (0, 1):
+        h = M.Handle(mode=M.MODE_EMULATED, member=member)
+        h.set_host_resident(resident)
+        C, rep = run_host(h, A, B, C0, 1.0, beta, block=b)
+        assert h.device_status() == M.MOMMS_OK
+        Cref, N = reference(A, B, C0 if beta else None, 1.0, beta)
+        assert max_ratio(C, Cref, k, 1.0, beta, N, C0 if beta else None) <= 1.0
+        if resident:
+            w = I.resident_a_words(m, n, k, b, b, c_read=beta != 0.0)
+        else:
+            w = I.resident_c_words(m, n, k, b, b, c_read=beta != 0.0)
+        h2d = 8 * (w["a_reads"] + w["b_reads"] + w["c_reads"])
+        assert (rep["ooc_resident"], rep["h2d_bytes"], rep["d2h_bytes"]) == (resident, h2d, 8 * w["c_writes"])
+        assert rep["member"] == member
+        h.close()
