@@ -70,6 +70,9 @@ def parse():
                         "trsm / trmm: lower triangular A size x size, B size x size (momms_trsm / momms_trmm, "
                         "B restored from a copy each step); syrk: C lower += A A^T, A size x size")
     p.add_argument("--block", type=int, default=0, help="momms_gemm_host block size (0 = from the budget)")
+    p.add_argument("--host-resident", default="c", choices=["c", "a"],
+                   help="momms_gemm_host member at the HBM level: Resident C or Resident A")
+    p.add_argument("--host-k", type=int, default=0, help="k of the host shape (0 = size)")
     p.add_argument("--scheme", default="auto", choices=["auto", "slices", "moduli"],
                    help="integer encoding of the emulated product (momms_set_scheme)")
     p.add_argument("--device-gb", type=float, default=0.0, help="momms_gemm_host device budget (0 = half free)")
@@ -309,18 +312,23 @@ def run_side_workload(args):
     M.lib(build_if_missing=True)
     stream = torch.cuda.current_stream()
     mode = {"auto": M.MODE_AUTO, "native": M.MODE_NATIVE, "emulated": M.MODE_EMULATED}[args.mode]
-    h = M.Handle(mode=mode, slices=args.slices, scheme=SCHEMES[args.scheme])
+    member = {"auto": M.MEMBER_AUTO, "C2": M.MEMBER_C2, "A2": M.MEMBER_A2, "B2": M.MEMBER_B2,
+              "A1": M.MEMBER_A1}[args.member]
+    h = M.Handle(mode=mode, member=member, slices=args.slices, scheme=SCHEMES[args.scheme])
+    h.set_host_resident(1 if args.host_resident == "a" else 0)
     keep = []
     io = {}
     if args.shape == "host":
-        m = n = k = args.size
+        m = n = args.size
+        k = args.host_k or args.size
         hosts = [torch.from_numpy(np.ascontiguousarray(syn.matrix("uniform", r, c, syn.workload_seed(1, nm)).T)).pin_memory()
                  for r, c, nm in ((m, k, "A"), (k, n, "B"), (m, n, "C"))]
         keep.append(hosts)
         hA, hB, hC = (t.data_ptr() for t in hosts)
         flops = 2.0 * m * n * k
-        workload = (f"square FP64 GEMM C := A*B + C, m=n=k={m}, A, B, C in pinned host memory, uniform[-1,1] "
-                    f"(seeded SplitMix64); out-of-core product, Resident C at the HBM level")
+        workload = (f"FP64 GEMM C := A*B + C, m=n={m} k={k}, A, B, C in pinned host memory, uniform[-1,1] "
+                    f"(seeded SplitMix64); out-of-core product, Resident {args.host_resident.upper()} at the HBM "
+                    f"level, member {args.member} inside each block")
 
         def step():
             M.check(M.momms_gemm_host(h, m, n, k, 1.0, hA, m, hB, k, 1.0, hC, m, int(args.device_gb * 2 ** 30),

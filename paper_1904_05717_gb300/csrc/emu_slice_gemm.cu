@@ -679,13 +679,15 @@ MOMMS_DEV void stage_columns(const Params& p, int prob, int tn, int beta, int* c
 template <int CR, int CT>
 MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, uint64_t* acc_empty, uint32_t& abuf,
                               uint32_t (&aphase)[2], volatile int* abort_flag, uint32_t tacc, uint32_t tsum,
-                              int lane, int32_t (&acc)[CR], uint32_t remote_empty = 0) {
+                              int lane, int32_t (&acc)[CR], uint32_t remote_empty = 0, bool remote_full = false) {
 #pragma unroll
     for (int c = 0; c < CR; ++c) acc[c] = 0;
     bool first = true;
     for (int u = 0; u < units;) {
         const int cnt = min(chunk_slabs, units - u);
-        if (!mbar_wait(&acc_full[abuf], aphase[abuf], abort_flag)) return false;
+        const bool ready = remote_full ? mbar_wait_cluster(&acc_full[abuf], aphase[abuf], abort_flag)
+                                       : mbar_wait(&acc_full[abuf], aphase[abuf], abort_flag);
+        if (!ready) return false;
         tc_fence_after();
         const uint32_t taddr = tacc + abuf * 256u;
 #pragma unroll
@@ -1164,7 +1166,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 int lm, tm2, tn;
                 if (!unit_of(p, it, &lm, &tm2, &tn)) break;
                 for (int j = 0; j < nslab; ++j) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+                    // the peer's stages are released by the leader's commits
+                    const bool freed = leader ? mbar_wait(&empty[stage], phase ^ 1u, abort_flag)
+                                              : mbar_wait_cluster(&empty[stage], phase ^ 1u, abort_flag);
+                    if (!freed) {
                         ok = false;
                         break;
                     }
@@ -1203,14 +1208,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!unit_of(p, it, &lm, &tm2, &tn)) break;
                 for (int u = 0; u < nslab && ok;) {
                     const int cnt = min(chunk, nslab - u);
-                    if (!mbar_wait(&acc_empty[abuf], aphase[abuf] ^ 1u, abort_flag)) {
+                    if (!mbar_wait_cluster(&acc_empty[abuf], aphase[abuf] ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t dt = tmem_base + abuf * 256u;
                     for (int c = 0; c < cnt; ++c) {
-                        if (!mbar_wait(&full[stage], phase, abort_flag)) {
+                        if (!mbar_wait_cluster(&full[stage], phase, abort_flag)) {
                             ok = false;
                             break;
                         }
@@ -1279,7 +1284,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!unit_of(p, it, &lm, &tm2, &tn)) break;
             int32_t acc[CR];
             if (!drain_diagonal<CR, CT>(p.one.nslab, p.one.chunk_slabs, acc_full, acc_empty, abuf, aphase,
-                                        abort_flag, tmem_base + lane_off + third * CW, tsum, lane, acc, remote_empty))
+                                        abort_flag, tmem_base + lane_off + third * CW, tsum, lane, acc, remote_empty,
+                                        !leader))
                 break;
             store_residues<BN, CR, CT>(p, -1, 2 * tm2 + static_cast<int>(rank), tn, lm, third, rloc, acc, tsum);
         }

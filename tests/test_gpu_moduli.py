@@ -52,8 +52,10 @@ def test_residue_split_bitwise(which, op, bits, k):
     assert not np.any(got[:, rows:, :]) and not np.any(got[:, :, inner:])
 
 
-def modular(A, B, C0, alpha, beta, S=0, opa=0, opb=0, scheme=M.SCHEME_MODULI, tile_n=0, ctas=0, fusion=0, pairs=0):
+def modular(A, B, C0, alpha, beta, S=0, opa=0, opb=0, scheme=M.SCHEME_MODULI, tile_n=0, ctas=0, fusion=0, pairs=0,
+            plan_on_device=1):
     h = M.Handle(mode=M.MODE_EMULATED, slices=S, scheme=scheme)
+    h.set_plan_on_device(plan_on_device)
     h.set_tile_n(tile_n)
     h.set_max_ctas(ctas)
     h.set_crt_fusion(fusion)
@@ -309,7 +311,8 @@ def test_fused_reconstruction_bitwise_equal_to_separate(m, n, k):
     B = syn.matrix("normal", k, n, 402)
     C0 = syn.matrix("uniform", m, n, 403)
     # data-driven width (S = 0): the bound holds; both runs take the same width from the same data
-    Cs, rs = modular(A, B, C0, -1.25, 0.5, 0, fusion=0)
+    # (the fused form chooses its width on the host: compare launch counts with the host plan)
+    Cs, rs = modular(A, B, C0, -1.25, 0.5, 0, fusion=0, plan_on_device=0)
     Cf, rf = modular(A, B, C0, -1.25, 0.5, 0, fusion=2)
     assert rs["moduli"] > 0 and rs["crt_fused"] == 0
     assert rf["crt_fused"] == 1 and rf["launches"] == rs["launches"] - 1
