@@ -747,6 +747,7 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
         q.m = static_cast<int32_t>(m[p]); q.n = static_cast<int32_t>(n[p]); q.k = static_cast<int32_t>(k[p]);
         q.k_pad = static_cast<int32_t>(round_up(k[p], momms::kEmuBK));
         q.S = h->slices; q.beta = bb;
+        q.enc = -1;  // encodings chosen on the host: every split launch takes the problems given to it
         q.e = reinterpret_cast<int32_t*>(mb + off_e[i]);
         q.ef = reinterpret_cast<uint8_t*>(mb + off_ef[i]);
         q.f = reinterpret_cast<int32_t*>(mb + off_f[i]);
@@ -985,6 +986,192 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
     h->report.tile_m = momms::kEmuBM;
     h->report.tile_n = momms::kEmuBNMax;
     h->report.launches = launches;
+    return MOMMS_OK;
+}
+
+// Batched emulated products with the data-driven slice count chosen on the device: one scale pass,
+// the batched plan kernel (each problem's S, width and encoding, and the unit layout of both product
+// launches, written into the device tables), then both encodings' split passes, both persistent
+// product launches (each walking only the problems and units the plan gave it; their totals are
+// read on the device) and the reconstruction.  Nothing is read back: the call only enqueues work,
+// and a repeated call with the same problems uploads nothing, so it can be captured in a CUDA graph.
+int run_emulated_batched_planned(momms_handle_t h, const std::vector<int64_t>& idx, const std::vector<int>& scheme_of,
+                                 const int64_t* m, const int64_t* n, const int64_t* k, const double* alpha,
+                                 const double* const* A, const int64_t* lda, const double* const* B,
+                                 const int64_t* ldb, const double* beta, double* const* C, const int64_t* ldc,
+                                 cudaStream_t s) {
+    const int count = static_cast<int>(idx.size());
+    const int bb = h->digit_bits;
+    constexpr int kPlanes = momms::kCrtMaxModuli;  // room for the most moduli and for S <= kAutoSliceMax
+    static_assert(kAutoSliceMax <= kPlanes, "digit planes fit the reserved planes");
+    // ---- per-problem statistics (exponents, flags; the spreads first)
+    std::vector<size_t> off_e(count), off_ef(count), off_f(count), off_ff(count);
+    size_t meta = align256(sizeof(int32_t) * 2 * static_cast<size_t>(count));
+    for (int i = 0; i < count; ++i) {
+        const int64_t p = idx[i];
+        off_e[i] = meta;  meta += align256(sizeof(int32_t) * m[p]);
+        off_ef[i] = meta; meta += align256(static_cast<size_t>(m[p]));
+        off_f[i] = meta;  meta += align256(sizeof(int32_t) * n[p]);
+        off_ff[i] = meta; meta += align256(static_cast<size_t>(n[p]));
+    }
+    int rc = grow_device(&h->batch_meta, &h->batch_meta_cap, meta);
+    if (rc) return rc;
+    char* mb = static_cast<char*>(h->batch_meta);
+    int32_t* spreads = reinterpret_cast<int32_t*>(mb);
+    // ---- workspace: every problem's planes (kPlanes per operand) and product residues, then scratch
+    std::vector<size_t> off_ad(count), off_bd(count), off_res(count);
+    size_t ws_bytes = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t p = idx[i];
+        const int64_t k_pad = round_up(k[p], momms::kEmuBK);
+        off_ad[i] = ws_bytes; ws_bytes += align256(size_t(2) * kPlanes * m[p] * k_pad);
+        off_bd[i] = ws_bytes; ws_bytes += align256(size_t(2) * kPlanes * n[p] * k_pad);
+        off_res[i] = ws_bytes; ws_bytes += align256(static_cast<size_t>(kPlanes) * m[p] * n[p]);
+    }
+    const size_t off_scratch = ws_bytes;
+    const size_t scratch_bytes = momms::emu_scratch_bytes(momms::device_sm_count());
+    ws_bytes += align256(scratch_bytes);
+    void* ws = nullptr;
+    rc = ensure_workspace(h, ws_bytes, &ws);
+    if (rc) return rc;
+    char* w = static_cast<char*>(ws);
+    // ---- the host-side parts of the tables (the plan kernel fills in S, widths, encodings and offsets)
+    std::vector<momms::EmuBatchPrep> prep(count);
+    std::vector<momms::EmuBatchProblem> gs(count), gm(count);
+    std::vector<momms::CrtBatchProblem> cp(count);
+    std::vector<int2> sa_items, sb_items, pa_items, pb_items, crt_items;
+    int64_t tiles_all = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t p = idx[i];
+        momms::EmuBatchPrep& q = prep[i];
+        q.A = A[p]; q.B = B[p]; q.lda = lda[p]; q.ldb = ldb[p];
+        q.m = static_cast<int32_t>(m[p]); q.n = static_cast<int32_t>(n[p]); q.k = static_cast<int32_t>(k[p]);
+        q.k_pad = static_cast<int32_t>(round_up(k[p], momms::kEmuBK));
+        q.S = kPlanes; q.beta = bb; q.bits = 0; q.enc = 0;
+        q.scheme = h->scheme == MOMMS_SCHEME_AUTO ? scheme_of[i] : h->scheme;
+        q.c0 = rule_c0(k[p]);
+        q.e = reinterpret_cast<int32_t*>(mb + off_e[i]);
+        q.ef = reinterpret_cast<uint8_t*>(mb + off_ef[i]);
+        q.f = reinterpret_cast<int32_t*>(mb + off_f[i]);
+        q.ff = reinterpret_cast<uint8_t*>(mb + off_ff[i]);
+        q.spread = spreads + 2 * i;
+        q.Ad = w + off_ad[i];
+        q.Bd = w + off_bd[i];
+        for (int64_t b = 0; b < momms::emu_batch_scale_a_blocks(m[p]); ++b) sa_items.push_back(make_int2(i, (int)b));
+        for (int64_t b = 0; b < momms::emu_batch_scale_b_blocks(n[p]); ++b) sb_items.push_back(make_int2(i, (int)b));
+        for (int64_t b = 0; b < momms::emu_batch_split_a_blocks(m[p], q.k_pad); ++b) pa_items.push_back(make_int2(i, (int)b));
+        for (int64_t b = 0; b < momms::emu_batch_split_b_blocks(n[p], q.k_pad); ++b) pb_items.push_back(make_int2(i, (int)b));
+        for (int64_t b = 0; b < momms::crt_batch_blocks(n[p]); ++b) crt_items.push_back(make_int2(i, (int)b));
+        momms::EmuBatchProblem g;
+        std::memset(&g, 0, sizeof(g));
+        if (!momms::emu_make_digit_map(&g.mapA, q.Ad, q.k_pad, q.m, kPlanes, momms::kEmuBM) ||
+            !momms::emu_make_digit_map(&g.mapB, q.Bd, q.k_pad, q.n, kPlanes, momms::kEmuBNMax))
+            return MOMMS_ERR_UNSUPPORTED;
+        g.e = q.e; g.ef = q.ef; g.f = q.f; g.ff = q.ff;
+        g.C = C[p]; g.ldc = ldc[p]; g.alpha = alpha[p]; g.beta_c = beta[p];
+        g.m = q.m; g.n = q.n; g.beta = bb;
+        g.nslab = q.k_pad / momms::kEmuBK;
+        g.chunk_slabs = momms::emu_chunk_slabs(bb);
+        g.tiles_n = static_cast<int32_t>((q.n + momms::kEmuBNMax - 1) / momms::kEmuBNMax);
+        tiles_all += ((q.m + momms::kEmuBM - 1) / momms::kEmuBM) * g.tiles_n;
+        gs[i] = g;
+        g.res = reinterpret_cast<uint8_t*>(w + off_res[i]);
+        gm[i] = g;
+        cp[i] = momms::CrtBatchProblem{g.res, q.e, q.ef, q.f, q.ff, g.C, g.ldc, g.alpha, g.beta_c, q.m, q.n, 0, 0};
+    }
+    if (sa_items.size() > INT32_MAX || pa_items.size() > INT32_MAX || pb_items.size() > INT32_MAX ||
+        crt_items.size() > INT32_MAX)
+        return MOMMS_ERR_UNSUPPORTED;
+    // ---- one device block: [prep][sa][sb][pa][pb][gs][gm][crt][crt items][totals]
+    std::vector<char> buf;
+    auto put = [&](const void* src, size_t bytes) {
+        size_t o = align256(buf.size());
+        buf.resize(o + bytes);
+        if (bytes) std::memcpy(buf.data() + o, src, bytes);
+        return o;
+    };
+    const size_t o_prep = put(prep.data(), sizeof(momms::EmuBatchPrep) * count);
+    const size_t o_sa = put(sa_items.data(), sizeof(int2) * sa_items.size());
+    const size_t o_sb = put(sb_items.data(), sizeof(int2) * sb_items.size());
+    const size_t o_pa = put(pa_items.data(), sizeof(int2) * pa_items.size());
+    const size_t o_pb = put(pb_items.data(), sizeof(int2) * pb_items.size());
+    const size_t o_gs = put(gs.data(), sizeof(momms::EmuBatchProblem) * count);
+    const size_t o_gm = put(gm.data(), sizeof(momms::EmuBatchProblem) * count);
+    const size_t o_cp = put(cp.data(), sizeof(momms::CrtBatchProblem) * count);
+    const size_t o_ci = put(crt_items.data(), sizeof(int2) * crt_items.size());
+    const int64_t zeros[2] = {0, 0};
+    const size_t o_tot = put(zeros, sizeof(zeros));
+    const bool same = buf.size() == h->host_tables.size() && h->batch_tables &&
+                      std::memcmp(buf.data(), h->host_tables.data(), buf.size()) == 0;
+    if (!same) {
+        rc = grow_device(&h->batch_tables, &h->batch_tables_cap, buf.size());
+        if (rc) return rc;
+        if (cudaMemcpyAsync(h->batch_tables, buf.data(), buf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return MOMMS_ERR_CUDA;
+        h->host_tables.swap(buf);
+    }
+    char* tb = static_cast<char*>(h->batch_tables);
+    auto* dprep = reinterpret_cast<momms::EmuBatchPrep*>(tb + o_prep);
+    auto items = [&](size_t o) { return reinterpret_cast<const int2*>(tb + o); };
+    auto* totals = reinterpret_cast<int64_t*>(tb + o_tot);
+    // ---- the launches
+    int64_t launches = 0;
+    if (cudaMemsetAsync(spreads, 0, sizeof(int32_t) * 2 * count, s) != cudaSuccess ||
+        momms::launch_emu_batch_scale(dprep, items(o_sa), (int)sa_items.size(), items(o_sb), (int)sb_items.size(), s) !=
+            cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    launches += 2;
+    momms::EmuBatchPlanArgs pa{};
+    pa.prep = dprep;
+    pa.slices = reinterpret_cast<momms::EmuBatchProblem*>(tb + o_gs);
+    pa.moduli = reinterpret_cast<momms::EmuBatchProblem*>(tb + o_gm);
+    pa.crt = reinterpret_cast<momms::CrtBatchProblem*>(tb + o_cp);
+    pa.count = count;
+    pa.smax = kAutoSliceMax;
+    pa.totals = totals;
+    pa.summary = h->plan_dev;
+    const momms::CrtReconSet& set = crt_set(h);
+    for (int c = 1; c <= momms::kCrtMaxModuli; ++c) {
+        const uint32_t* Pw = set.by_n[c].Pw;
+        pa.P[c][0] = static_cast<uint64_t>(Pw[0]) | (static_cast<uint64_t>(Pw[1]) << 32);
+        pa.P[c][1] = static_cast<uint64_t>(Pw[2]) | (static_cast<uint64_t>(Pw[3]) << 32);
+    }
+    if (momms::launch_emu_batch_plan(pa, s) != cudaSuccess) return MOMMS_ERR_CUDA;
+    launches += 1;
+    momms::CrtConsts c16;
+    momms::CrtRecon r16;
+    momms::crt_consts(momms::kCrtMaxModuli, 0, &c16, &r16);  // the moduli; each problem takes a prefix
+    if (momms::launch_emu_batch_split(dprep, items(o_pa), (int)pa_items.size(), items(o_pb), (int)pb_items.size(), s) !=
+            cudaSuccess ||
+        momms::launch_emu_batch_residues(dprep, items(o_pa), (int)pa_items.size(), items(o_pb), (int)pb_items.size(),
+                                         c16, s) != cudaSuccess)
+        return MOMMS_ERR_CUDA;
+    launches += 4;
+    const int wh = momms::emu_debug_take_withhold();  // (test hook: one of the two product launches works)
+    if (wh) momms::emu_debug_withhold_load();
+    cudaError_t ce = momms::launch_emu_slice_gemm_batched(reinterpret_cast<const momms::EmuBatchProblem*>(tb + o_gs),
+                                                          count, tiles_all, w + off_scratch, scratch_bytes, h->status,
+                                                          s, totals);
+    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+    if (wh) momms::emu_debug_withhold_load();
+    ce = momms::launch_emu_residue_gemm_batched(reinterpret_cast<const momms::EmuBatchProblem*>(tb + o_gm), count,
+                                                tiles_all * momms::kCrtMaxModuli, c16, w + off_scratch, scratch_bytes,
+                                                h->status, s, totals + 1);
+    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+    momms::emu_debug_take_withhold();
+    ce = momms::launch_crt_reconstruct_batched(reinterpret_cast<const momms::CrtBatchProblem*>(tb + o_cp),
+                                               items(o_ci), (int)crt_items.size(), set, s);
+    if (ce != cudaSuccess) return MOMMS_ERR_CUDA;
+    launches += 3;
+    reset_report(h);
+    h->report.mode = MOMMS_MODE_EMULATED;
+    h->report.member = MOMMS_MEMBER_AUTO;
+    h->report.digit_bits = bb;
+    h->report.k_passes = 1;
+    h->report.tile_m = momms::kEmuBM;
+    h->report.tile_n = momms::kEmuBNMax;
+    h->report.launches = launches;
+    h->report_pending = true;  // the largest S / moduli / width of the call, from the plan kernel
     return MOMMS_OK;
 }
 
@@ -1421,7 +1608,14 @@ int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const 
     if (emu_idx.size() > (size_t(1) << 24)) return MOMMS_ERR_UNSUPPORTED;
     momms_report_t rep{};
     if (!emu_idx.empty()) {
-        int rc = run_emulated_batched(h, emu_idx, emu_scheme, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+        // the data-driven slice count is planned on the device unless the handle says otherwise (or a
+        // problem's k exceeds what the largest planned slice count keeps exact in one pass)
+        bool planned = h->slices <= 0 && h->plan_mode && h->digit_bits == kDigitBits;
+        for (int64_t i : emu_idx)
+            if (k[i] > momms::emu_max_k_per_pass(kAutoSliceMax, kDigitBits)) planned = false;
+        int rc = planned ? run_emulated_batched_planned(h, emu_idx, emu_scheme, m, n, k, alpha, A, lda, B, ldb, beta,
+                                                        C, ldc, s)
+                         : run_emulated_batched(h, emu_idx, emu_scheme, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
         if (rc) return rc;
         rep = h->report;
         launches += h->report.launches;

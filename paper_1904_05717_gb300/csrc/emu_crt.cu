@@ -222,10 +222,7 @@ cudaError_t launch_crt_reconstruct_plan(int64_t m, int64_t n, const uint8_t* res
     return cudaGetLastError();
 }
 
-int64_t crt_max_k() {
-    int64_t k = ((1ll << 31) - 1) / (127ll * 127ll);
-    return k - k % 64;
-}
+int64_t crt_max_k() { return kCrtMaxK; }
 
 bool crt_plan(int bits, int64_t k, CrtConsts* c, CrtRecon* r) {
     if (bits < 1 || bits > 56 || k < 1 || k > crt_max_k()) return false;

@@ -101,6 +101,7 @@ struct Params {
     const EmuBatchProblem* table;  // batched: one entry per problem, ordered by tile0
     int count;
     int64_t total_tiles;
+    const int64_t* total_dev;      // batched with a device plan: the total, written by the plan kernel
     double* scratch;          // FP64 partial recombination R, one BN x BM block per CTA
     long long* qscratch;      // int64 exact group sums Q, one BN x BM block per CTA
     int32_t* status;
@@ -170,7 +171,7 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
             // a batch: the units of each problem (its tiles times its moduli) follow one another,
             // modulus-major inside the problem; tile0 is the problem's first unit
             const int64_t u = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
-            if (u >= p.total_tiles) return false;
+            if (u >= (p.total_dev ? *p.total_dev : p.total_tiles)) return false;
             int lo = 0, hi = p.count - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -228,7 +229,7 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
         return member_tile(p.member, p.group, blockIdx.x, gridDim.x, it, p.tiles_m, p.tiles_n, tm, tn);
     }
     const int64_t t = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
-    if (t >= p.total_tiles) return false;
+    if (t >= (p.total_dev ? *p.total_dev : p.total_tiles)) return false;
     int lo = 0, hi = p.count - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -1594,10 +1595,11 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
 
 template <int BN>
 static cudaError_t launch_bn_batched(const EmuBatchProblem* table, int count, int64_t total_tiles, void* scratch,
-                                     size_t scratch_bytes, int32_t* status, cudaStream_t stream) {
+                                     size_t scratch_bytes, int32_t* status, cudaStream_t stream,
+                                     const int64_t* total_dev) {
     using C_ = Cfg<BN>;
     int64_t ctas = device_sm_count();
-    if (ctas > total_tiles) ctas = total_tiles;
+    if (ctas > total_tiles) ctas = total_tiles;  // (with total_dev: an upper bound of the total)
     const size_t half = static_cast<size_t>(ctas) * BN * BM * sizeof(double);
     if (scratch_bytes < 2 * half) return cudaErrorInvalidValue;
     static PerDeviceFlag attr_set;  // idempotent; per device, atomic for concurrent first calls
@@ -1612,6 +1614,7 @@ static cudaError_t launch_bn_batched(const EmuBatchProblem* table, int count, in
     p.table = table;
     p.count = count;
     p.total_tiles = total_tiles;
+    p.total_dev = total_dev;
     p.withhold = g_withhold.exchange(0);
     p.qscratch = static_cast<long long*>(scratch);
     p.scratch = reinterpret_cast<double*>(static_cast<char*>(scratch) + half);
@@ -1626,7 +1629,7 @@ static cudaError_t launch_bn_batched(const EmuBatchProblem* table, int count, in
 template <int BN>
 static cudaError_t launch_bn_batched_mod(const EmuBatchProblem* table, int count, int64_t total_units,
                                          const CrtConsts& c, void* scratch, size_t scratch_bytes, int32_t* status,
-                                         cudaStream_t stream) {
+                                         cudaStream_t stream, const int64_t* total_dev) {
     using C_ = Cfg<BN>;
     int64_t ctas = device_sm_count();
     if (ctas > total_units) ctas = total_units;
@@ -1644,6 +1647,7 @@ static cudaError_t launch_bn_batched_mod(const EmuBatchProblem* table, int count
     p.table = table;
     p.count = count;
     p.total_tiles = total_units;
+    p.total_dev = total_dev;
     p.withhold = g_withhold.exchange(0);
     p.qscratch = static_cast<long long*>(scratch);
     p.scratch = reinterpret_cast<double*>(static_cast<char*>(scratch) + half);
@@ -1664,17 +1668,19 @@ static cudaError_t launch_bn_batched_mod(const EmuBatchProblem* table, int count
 
 cudaError_t launch_emu_residue_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_units,
                                             const CrtConsts& c, void* scratch, size_t scratch_bytes,
-                                            int32_t* status, cudaStream_t stream) {
+                                            int32_t* status, cudaStream_t stream, const int64_t* total_dev) {
     if (count <= 0 || total_units <= 0) return cudaSuccess;
     if (c.N < 1 || c.N > kCrtMaxModuli) return cudaErrorInvalidValue;
-    return emu::launch_bn_batched_mod<192>(dev_table, count, total_units, c, scratch, scratch_bytes, status, stream);
+    return emu::launch_bn_batched_mod<192>(dev_table, count, total_units, c, scratch, scratch_bytes, status, stream,
+                                           total_dev);
 }
 
 cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_tiles,
                                           void* scratch, size_t scratch_bytes, int32_t* status,
-                                          cudaStream_t stream) {
+                                          cudaStream_t stream, const int64_t* total_dev) {
     if (count <= 0 || total_tiles <= 0) return cudaSuccess;
-    return emu::launch_bn_batched<192>(dev_table, count, total_tiles, scratch, scratch_bytes, status, stream);
+    return emu::launch_bn_batched<192>(dev_table, count, total_tiles, scratch, scratch_bytes, status, stream,
+                                       total_dev);
 }
 
 int current_device() {
@@ -1720,33 +1726,6 @@ size_t emu_scratch_bytes_tail(int64_t m, int64_t n, int64_t k, int S, int max_ct
 size_t emu_scratch_bytes_for_ctas(int ctas) {
     // FP64 partial sums R and int64 group sums Q, one 128 x 192 block each per CTA
     return 2 * static_cast<size_t>(ctas) * kEmuBNMax * emu::BM * sizeof(double);
-}
-
-uint32_t emu_group_ends(int S, int beta, int64_t k_pass) {
-    // Diagonal d sums (d - 1) pair products over k_pass, each |digit product| <= (2^beta - 1)^2:
-    // |P_d| <= (d - 1) (2^beta - 1)^2 k_pass.  Walking from the least significant diagonal,
-    // a group [lo, hi] holds Q = sum_{d=lo}^{hi} P_d 2^(beta (hi - d)); a group is closed
-    // before the bound on |Q| would reach 2^63.
-    const unsigned __int128 limit = static_cast<unsigned __int128>(1) << 63;
-    const unsigned __int128 dmax = static_cast<unsigned __int128>((1ll << beta) - 1);
-    uint32_t mask = 0;
-    unsigned __int128 acc = 0;
-    int j = 0;
-    for (int d = S + 1; d >= 2; --d) {
-        const unsigned __int128 pb =
-            static_cast<unsigned __int128>(d - 1) * dmax * dmax * static_cast<unsigned __int128>(k_pass);
-        bool fits = (j == 0);
-        if (j > 0 && beta * j < 64) fits = acc + (pb << (beta * j)) < limit;
-        if (!fits) {
-            mask |= 1u << (d + 1);  // diagonal d + 1 closed the previous group
-            acc = 0;
-            j = 0;
-        }
-        acc += pb << (beta * j);
-        ++j;
-    }
-    mask |= 1u << 2;  // the most significant diagonal always closes the last group
-    return mask;
 }
 
 int64_t emu_max_k_per_pass(int S, int beta) {

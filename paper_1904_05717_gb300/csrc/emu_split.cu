@@ -164,6 +164,82 @@ __global__ void plan_kernel(const int* __restrict__ spreads, const __grid_consta
     *out = p;
 }
 
+// The batched device plan (EmuBatchPlanArgs), one block: per problem (threads in parallel) the
+// rule of plan_kernel on its spreads and, for its width w, the fewest moduli whose product exceeds
+// 4 k (2^w - 1)^2 (exact 128-bit arithmetic, as the host's choice of moduli); moduli when the
+// problem's rule takes them (SLICES: never; MODULI: whenever they cover the width; AUTO: when they
+// save two or more products and their per-element passes are paid for, N (k + 850) <= 0.9
+// S (S + 1) / 2 k); then thread 0 lays the units of both launches out problem by problem.
+__global__ void batch_plan_kernel(const __grid_constant__ EmuBatchPlanArgs a) {
+    using u128 = unsigned __int128;
+    __shared__ int smax_s, nmax_s, bmax_s;
+    if (threadIdx.x == 0) {
+        smax_s = 0;
+        nmax_s = 0;
+        bmax_s = 0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.count; i += blockDim.x) {
+        EmuBatchPrep& q = a.prep[i];
+        const double sa = q.spread[0] / 16.0, sb = q.spread[1] / 16.0;
+        const double bits = q.c0 + 1.25 * (sa + sb);
+        int S = static_cast<int>(ceil(bits / 7.0));
+        S = S < 3 ? 3 : (S > a.smax ? a.smax : S);
+        const int cb = static_cast<int>(ceil(bits));
+        int w = cb > 7 * S - 6 ? cb : 7 * S - 6;
+        w = w < 7 * S ? w : 7 * S;
+        int N = 0;
+        const bool range = q.scheme != 1 && w <= 56 && static_cast<int64_t>(q.k_pad) <= kCrtMaxK;
+        if (range) {
+            const u128 v = (static_cast<u128>(1) << w) - 1;
+            const u128 need = static_cast<u128>(4) * static_cast<u128>(q.k) * v * v;
+            for (int c = 1; c <= kCrtMaxModuli && N == 0; ++c) {
+                const u128 P = (static_cast<u128>(a.P[c][1]) << 64) | a.P[c][0];
+                if (P > need) N = c;
+            }
+        }
+        const int pairs = S * (S + 1) / 2;
+        const double kk = static_cast<double>(q.k);
+        bool mod = N > 0;
+        if (mod && q.scheme == 0)  // AUTO
+            mod = N + 2 <= pairs && N * (kk + 850.0) <= 0.9 * pairs * kk;
+        q.enc = mod ? 1 : 0;
+        q.S = mod ? N : S;
+        q.bits = mod ? w : 7 * S;
+        a.slices[i].S = S;
+        a.slices[i].group_end = emu_group_ends(S, 7, q.k_pad);
+        a.moduli[i].S = mod ? N : 0;
+        a.crt[i].N = mod ? N : 0;
+        a.crt[i].bits = w;
+        if (mod) {
+            atomicMax(&nmax_s, N);
+            atomicMax(&bmax_s, w);
+        } else {
+            atomicMax(&smax_s, S);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    int64_t ts = 0, tm = 0;
+    for (int i = 0; i < a.count; ++i) {
+        const EmuBatchPrep& q = a.prep[i];
+        const int64_t tiles = static_cast<int64_t>((q.m + kEmuBM - 1) / kEmuBM) * a.slices[i].tiles_n;
+        a.slices[i].tile0 = ts;
+        a.moduli[i].tile0 = tm;
+        if (q.enc) tm += tiles * q.S;
+        else ts += tiles;
+    }
+    a.totals[0] = ts;
+    a.totals[1] = tm;
+    EmuPlan sm;
+    sm.S = smax_s;
+    sm.N = nmax_s;
+    sm.bits = bmax_s > 7 * smax_s ? bmax_s : 7 * smax_s;
+    sm.pad = 0;
+    sm.est = 0.0;
+    *a.summary = sm;
+}
+
 // Decompose x into (integer significand, binary exponent e2, sign); zero / non-finite -> mag 0.
 __device__ __forceinline__ void decompose(double x, unsigned long long* mag, int* e2, bool* neg) {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
@@ -562,6 +638,7 @@ __global__ void batch_split_a(const EmuBatchPrep* __restrict__ probs, const int2
     __shared__ double tile[TT][TT];  // [q][r ^ swz(q)]
     const int2 it = items[blockIdx.x];
     const EmuBatchPrep& pr = probs[it.x];
+    if (pr.enc >= 0 && pr.enc != (RES ? 1 : 0)) return;  // the device plan put it on the other encoding
     const int64_t qtiles = pr.k_pad / TT;
     const int64_t r0 = (it.y / qtiles) * TT;
     const int64_t q0 = (it.y % qtiles) * TT;
@@ -595,6 +672,7 @@ __global__ void batch_split_b(const EmuBatchPrep* __restrict__ probs, const int2
                               const __grid_constant__ CrtConsts c) {
     const int2 it = items[blockIdx.x];
     const EmuBatchPrep& pr = probs[it.x];
+    if (pr.enc >= 0 && pr.enc != (RES ? 1 : 0)) return;  // the device plan put it on the other encoding
     const int64_t quads = pr.k_pad / 4;
     const int64_t idx = static_cast<int64_t>(it.y) * 256 + threadIdx.x;
     if (idx >= static_cast<int64_t>(pr.n) * quads) return;
@@ -675,6 +753,12 @@ cudaError_t launch_emu_scale(int which, int op, int64_t rows, int64_t inner, con
     }
     const int64_t blocks = (rows + 7) / 8;
     scale_inner_contig<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(X, ldx, rows, inner, exps, flags, l1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emu_batch_plan(const EmuBatchPlanArgs& a, cudaStream_t stream) {
+    if (a.count <= 0) return cudaSuccess;
+    split::batch_plan_kernel<<<1, 1024, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

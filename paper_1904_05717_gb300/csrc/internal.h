@@ -84,6 +84,8 @@ cudaError_t launch_emu_split(int which, int op, int64_t rows, int64_t inner, con
 // modulus -- and rebuilt by the Chinese remainder theorem; C := alpha 2^(e + f - 2 bits) A^B^
 // + beta C.  N products instead of the S(S+1)/2 of the slice encoding.
 constexpr int kCrtMaxModuli = 16;
+// Largest k one modular product keeps exact in int32: k 127^2 < 2^31, rounded down to a multiple of 64.
+constexpr int64_t kCrtMaxK = (((int64_t(1) << 31) - 1) / (127 * 127)) / 64 * 64;
 struct CrtConsts {                 // residue split and slice-product epilogue
     int N;                         // moduli in use
     int bits;                      // integer width of the operands (7 x slices)
@@ -213,7 +215,28 @@ struct EmuBatchPrep {
     void* Bd;          // S slices [S][n][k_pad] fp16
     int32_t* spread;   // 2 values (A, B): ceil(16 x spread) by atomicMax, or null
     int32_t bits;      // modular batch: operand width, the S planes being residues of S moduli
+    int32_t enc;       // device plan: 0 = digit slices, 1 = moduli (the split of the other encoding
+                       // skips the problem); -1 = no plan (every split launch takes it)
+    int32_t scheme;    // device plan: the problem's encoding rule (MOMMS_SCHEME_*)
+    double c0;         // device plan: the k-dependent constant of the slice-count rule
 };
+struct CrtBatchProblem;
+// The batched device plan: per problem the slice-count rule on its spreads, its encoding and the
+// fields of the four tables that depend on them (split passes, both product launches'
+// tables with their unit offsets, the reconstruction table), the two launches' unit totals, and
+// the largest S / moduli / width of the call as a summary plan.
+struct EmuBatchPlanArgs {
+    EmuBatchPrep* prep;
+    EmuBatchProblem* slices;   // digit-slice launch table (every problem; 0 tiles when on moduli)
+    EmuBatchProblem* moduli;   // residue-product launch table (every problem; 0 units when on slices)
+    CrtBatchProblem* crt;      // reconstruction table (N = 0 when on slices)
+    int count;
+    int smax;                  // largest slice count of the rule
+    int64_t* totals;           // [0] digit-slice tiles, [1] residue units
+    EmuPlan* summary;
+    uint64_t P[17][2];         // product of the first N moduli (low, high 64 bits), N = 0..16
+};
+cudaError_t launch_emu_batch_plan(const EmuBatchPlanArgs& a, cudaStream_t stream);
 // Work items are (problem, block) pairs; the block's meaning depends on the pass:
 //   scale A: 256 rows   scale B: 8 columns   split A: a 64 x 64 (row, k) tile   split B: 1024 digits.
 cudaError_t launch_emu_batch_scale(const EmuBatchPrep* probs, const int2* items_a, int n_a, const int2* items_b,
@@ -240,7 +263,7 @@ bool emu_make_digit_map(CUtensorMap* map, const void* base, int64_t k_pad, int64
 // problem and modulus-major inside a problem; each problem's moduli are the first S of c.
 cudaError_t launch_emu_residue_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_units,
                                             const CrtConsts& c, void* scratch, size_t scratch_bytes,
-                                            int32_t* status, cudaStream_t stream);
+                                            int32_t* status, cudaStream_t stream, const int64_t* total_dev = nullptr);
 // Reconstruction of a batch of modular products: work items (problem, block of 8 columns), a warp
 // per column.  The reconstruction constants depend only on the number of moduli.
 struct CrtBatchProblem {
@@ -262,7 +285,7 @@ cudaError_t launch_crt_reconstruct_batched(const CrtBatchProblem* probs, const i
                                            const CrtReconSet& set, cudaStream_t stream);
 cudaError_t launch_emu_slice_gemm_batched(const EmuBatchProblem* dev_table, int count, int64_t total_tiles,
                                           void* scratch, size_t scratch_bytes, int32_t* status,
-                                          cudaStream_t stream);
+                                          cudaStream_t stream, const int64_t* total_dev = nullptr);
 // The CTA tile width used for n columns (tile_n request 0 = automatic).
 int emu_pick_bn(int64_t m, int64_t n, int64_t k, int requested, int units_per_tile = 1);
 // Default C2 group of the slice-product kernel for `ctas` persistent CTAs (tile rows of the
@@ -281,7 +304,32 @@ size_t emu_scratch_bytes(int num_sms);
 size_t emu_scratch_bytes_tail(int64_t m, int64_t n, int64_t k, int S, int max_ctas, int beta);
 size_t emu_scratch_bytes_for_ctas(int ctas);
 // Bit d set: diagonal d is the most significant of an exact int64 group (S, beta, k per pass).
-uint32_t emu_group_ends(int S, int beta, int64_t k_pass);
+// Diagonal d sums (d - 1) pair products over k_pass, each |digit product| <= (2^beta - 1)^2:
+// |P_d| <= (d - 1) (2^beta - 1)^2 k_pass.  Walking from the least significant diagonal, a group
+// [lo, hi] holds Q = sum_{d=lo}^{hi} P_d 2^(beta (hi - d)); a group is closed before the bound on
+// |Q| would reach 2^63.  (Host and device: the batched device plan evaluates it per problem.)
+__host__ __device__ inline uint32_t emu_group_ends(int S, int beta, int64_t k_pass) {
+    const unsigned __int128 limit = static_cast<unsigned __int128>(1) << 63;
+    const unsigned __int128 dmax = static_cast<unsigned __int128>((1ll << beta) - 1);
+    uint32_t mask = 0;
+    unsigned __int128 acc = 0;
+    int j = 0;
+    for (int d = S + 1; d >= 2; --d) {
+        const unsigned __int128 pb =
+            static_cast<unsigned __int128>(d - 1) * dmax * dmax * static_cast<unsigned __int128>(k_pass);
+        bool fits = (j == 0);
+        if (j > 0 && beta * j < 64) fits = acc + (pb << (beta * j)) < limit;
+        if (!fits) {
+            mask |= 1u << (d + 1);  // diagonal d + 1 closed the previous group
+            acc = 0;
+            j = 0;
+        }
+        acc += pb << (beta * j);
+        ++j;
+    }
+    mask |= 1u << 2;  // the most significant diagonal always closes the last group
+    return mask;
+}
 // Largest k one pass may cover so that every diagonal sum stays below 2^31.
 int64_t emu_max_k_per_pass(int S, int beta);
 // Products per FP32 accumulation chunk (every partial sum below 2^24), in 64-wide slabs.

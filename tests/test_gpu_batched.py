@@ -270,3 +270,80 @@ def test_batched_mixed_encodings_within_the_bound():
     assert rep["slices"] > 0 and rep["moduli"] > 0 and rep["launches"] == 9
     assert check_all(probs, dev) <= 1.0
     h.close()
+
+
+def test_batched_auto_device_plan_equals_host_plan_and_replays_from_a_graph():
+    # AUTO batched call with the slice count of every problem chosen on the device (nothing read
+    # back): bit for bit the host plan's result, within the bound against the oracle, and the same
+    # call captured in a CUDA graph replays it exactly
+    import torch
+    probs = make_problems(200, 32, 1024, 8000)
+    hd = M.Handle(mode=M.MODE_EMULATED)
+    hh = M.Handle(mode=M.MODE_EMULATED)
+    hh.set_plan_on_device(0)
+    dev_d, args_d = run_batched(hd, probs, 1.0, 1.0)
+    dev_h, _ = run_batched(hh, probs, 1.0, 1.0)
+    torch.cuda.synchronize()
+    assert hd.device_status() == M.MOMMS_OK and hh.device_status() == M.MOMMS_OK
+    rd, rh = hd.report(), hh.report()
+    assert (rd["slices"], rd["moduli"]) == (rh["slices"], rh["moduli"])
+    for a, b in zip(dev_d, dev_h):
+        assert np.array_equal(a[2].to_numpy(), b[2].to_numpy())
+    assert check_all(probs, dev_d, 1.0, 1.0) <= 1.0
+    eager = [d[2].to_numpy() for d in dev_d]
+    for d, p in zip(dev_d, probs):
+        d[2].storage.copy_(torch.from_numpy(np.ascontiguousarray(p[5].T)))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        M.check(M.momms_gemm_batched(hd, stream=s, **args_d), "capture")
+    g.replay()
+    torch.cuda.synchronize()
+    assert hd.device_status() == M.MOMMS_OK
+    for d, e in zip(dev_d, eager):
+        assert np.array_equal(d[2].to_numpy(), e)
+
+
+def test_batched_2000_auto_graph_capture():
+    # the batched workload (2000 problems, m, n, k log-uniform in [32, 2048]) in AUTO mode captured in
+    # a CUDA graph after one eager call: the replay equals the eager result bit for bit; every 20th
+    # problem against the oracle
+    import torch
+    count = 2000
+    sizes = syn.log_uniform_sizes(syn.workload_seed(4, "A"), count, 32, 2048)
+    h = M.Handle()
+    dev, hosts = [], []
+    for i, (m, n, k) in enumerate(sizes):
+        m, n, k = int(m), int(n), int(k)
+        A = syn.matrix("uniform", m, k, 100000 + 3 * i)
+        B = syn.matrix("uniform", k, n, 100001 + 3 * i)
+        C = syn.matrix("uniform", m, n, 100002 + 3 * i)
+        dev.append((M.DeviceMatrix.from_numpy(A), M.DeviceMatrix.from_numpy(B), M.DeviceMatrix.from_numpy(C)))
+        hosts.append((m, n, k, A, B, C) if i % 20 == 0 else (None, None, None, None, None, C))
+    args = dict(m=[int(s_[0]) for s_ in sizes], n=[int(s_[1]) for s_ in sizes], k=[int(s_[2]) for s_ in sizes],
+                alpha=[1.0] * count, A=[d[0].ptr for d in dev], lda=[d[0].ld for d in dev],
+                B=[d[1].ptr for d in dev], ldb=[d[1].ld for d in dev], beta=[1.0] * count,
+                C=[d[2].ptr for d in dev], ldc=[d[2].ld for d in dev])
+    M.check(M.momms_gemm_batched(h, **args), "eager")
+    torch.cuda.synchronize()
+    assert h.device_status() == M.MOMMS_OK
+    assert h.report()["mode"] == M.MODE_EMULATED
+    eager = [d[2].to_numpy() for d in dev]
+    for d, hst in zip(dev, hosts):
+        d[2].storage.copy_(torch.from_numpy(np.ascontiguousarray(hst[5].T)))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        M.check(M.momms_gemm_batched(h, stream=s, **args), "capture")
+    g.replay()
+    torch.cuda.synchronize()
+    assert h.device_status() == M.MOMMS_OK
+    worst = 0.0
+    for d, e, hst in zip(dev, eager, hosts):
+        got = d[2].to_numpy()
+        assert np.array_equal(got, e)
+        if hst[0] is not None:
+            m, n, k, A, B, C = hst
+            Cref = oracle.dgemm(A, B, C.copy(order="F"), 1.0, 1.0)
+            worst = max(worst, max_ratio(got, Cref, k, 1.0, 1.0, oracle.dgemm_abs(A, B), C))
+    assert worst <= 1.0
