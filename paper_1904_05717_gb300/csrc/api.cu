@@ -1607,6 +1607,7 @@ int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const 
     }
     if (emu_idx.size() > (size_t(1) << 24)) return MOMMS_ERR_UNSUPPORTED;
     momms_report_t rep{};
+    bool pending = false;  // the emulated part planned on the device: its S / moduli come from the plan
     if (!emu_idx.empty()) {
         // the data-driven slice count is planned on the device unless the handle says otherwise (or a
         // problem's k exceeds what the largest planned slice count keeps exact in one pass)
@@ -1618,6 +1619,7 @@ int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const 
                          : run_emulated_batched(h, emu_idx, emu_scheme, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
         if (rc) return rc;
         rep = h->report;
+        pending = h->report_pending;
         launches += h->report.launches;
     }
     if (!nat_idx.empty()) {
@@ -1676,6 +1678,7 @@ int momms_gemm_batched(momms_handle_t h, int64_t count, const int64_t* m, const 
     reset_report(h);
     h->report = rep;
     h->report.launches = launches;
+    h->report_pending = pending;
     return MOMMS_OK;
 }
 
