@@ -135,7 +135,6 @@ struct Params {
     // first stage but issues no copy into it, so the MMA thread's bounded wait on that stage runs
     // out -- the abort, drain and status path runs without any fault.
     int withhold;
-    int poll;                 // hot waits of the producer and the MMA thread polled (test_wait)
     // Device plan (single problem, AUTO slice count): plan_kind 1 = this is the modular launch (N
     // moduli from the plan, nothing to do when it chose slices), 2 = the digit launch (S from the
     // plan and its group ends from group_end_by_s, nothing to do when it chose moduli); 0 = none.
@@ -901,8 +900,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const int plane_a = MOD ? lm : s - 1;
                         const int plane_b = MOD ? plane_a : d - s - 1;
                         for (int j = 0; j < pr.nslab; ++j) {
-                            if (!(p.poll ? mbar_wait_poll(&empty[stage], phase ^ 1u, abort_flag)
-                                         : mbar_wait(&empty[stage], phase ^ 1u, abort_flag))) {
+                            if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
                                 ok = false;
                                 break;
                             }
@@ -949,16 +947,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const int units = (MOD ? 1 : d - 1) * pr.nslab;
                     for (int u = 0; u < units && ok;) {
                         const int cnt = min(pr.chunk_slabs, units - u);
-                        if (!(p.poll ? mbar_wait_poll(&acc_empty[abuf], aphase[abuf] ^ 1u, abort_flag)
-                                     : mbar_wait(&acc_empty[abuf], aphase[abuf] ^ 1u, abort_flag))) {
+                        if (!mbar_wait(&acc_empty[abuf], aphase[abuf] ^ 1u, abort_flag)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
                         const uint32_t dt = tmem_base + abuf * 256u;
                         for (int c = 0; c < cnt; ++c) {
-                            if (!(p.poll ? mbar_wait_poll(&full[stage], phase, abort_flag)
-                                         : mbar_wait(&full[stage], phase, abort_flag))) {
+                            if (!mbar_wait(&full[stage], phase, abort_flag)) {
                                 ok = false;
                                 break;
                             }
@@ -1462,10 +1458,6 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         if (a.used_group) *a.used_group = p.group;
         p.table = nullptr;
         p.withhold = a.withhold > 0 ? 1 : g_withhold.exchange(0);
-        {
-            const char* ev = std::getenv("MOMMS_POLL_WAITS");  // measurement switch (both forms are exact)
-            p.poll = ev && ev[0] == '1';
-        }
         if (a.plan) {
             // S or N from the device plan; the pass above was sized for the largest the plan may pick
             p.plan = a.plan;
@@ -1558,19 +1550,13 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
                 cfg.blockDim = dim3(THREADS);
                 cfg.dynamicSmemBytes = pairk::SMEM_BYTES;
                 cfg.stream = stream;
-                cudaLaunchAttribute attr[2];
+                cudaLaunchAttribute attr[1];
                 attr[0].id = cudaLaunchAttributeClusterDimension;
                 attr[0].val.clusterDim.x = 2;
                 attr[0].val.clusterDim.y = 1;
                 attr[0].val.clusterDim.z = 1;
-                attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
-                attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicySpread;
-                {
-                    const char* ev = std::getenv("MOMMS_PAIR_POLICY");  // measurement switch
-                    if (ev && ev[0] == 'l') attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
-                }
                 cfg.attrs = attr;
-                cfg.numAttrs = 2;
+                cfg.numAttrs = 1;
                 e = cudaLaunchKernelEx(&cfg, residue_pair_kernel, mapA, mapBh, p);
             } else {
                 slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(

@@ -77,33 +77,6 @@ MOMMS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
     }
 }
 
-// The same wait polled with test_wait (the thread is never suspended between checks).
-MOMMS_DEV bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-MOMMS_DEV bool mbar_wait_poll(uint64_t* bar, uint32_t parity, volatile int* abort) {
-    if (mbar_test_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_test_wait(bar, parity)) return true;
-        if ((it & 255u) == 0) {
-            if (*abort) return false;
-            if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
-                *abort = 1;
-                return false;
-            }
-        }
-    }
-}
-
 // A barrier whose phase another CTA of the cluster completes (a remote arrive or commit): polled
 // with test_wait at cluster scope (acquire.cluster pairs with the remote release), never
 // suspending the thread; bounded like mbar_wait.
