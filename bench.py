@@ -579,6 +579,12 @@ def main():
                 "launch_ms_alone": alone_ms}
         if stale:
             roof["traffic_last_capture"] = traffic
+        # what the product's MMA instruction alone reaches (operands resident in shared memory, no
+        # loads or drains): tcgen05 kind::f16 M 128 x N 192 on every SM (momms_probe_peak kind 2)
+        try:
+            roof["instruction_probe_tflops"] = M.momms_probe_peak(2, stream)
+        except Exception:
+            roof["instruction_probe_tflops"] = None
         del Ad, Bd, scratch
 
     # ---- native FP64 DMMA path on the same inputs (the other half of the metric)

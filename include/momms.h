@@ -550,9 +550,12 @@ int momms_member_tile(int member, int group, int64_t cta, int64_t ctas, int64_t 
 int momms_tri_tile(int uplo, int tile_n, int64_t n, int64_t t, int* tm, int* tn, int64_t* count);
 
 /* ------------------------------------------------------- microbenchmarks */
-/* Peak probes used as roofline denominators: kind 0 = FP64 DMMA, 1 = FP64 DFMA,
- * 2 = fp16 tcgen05 (kind::f16, FP32 accumulate).  Writes the achieved rate in
- * TFLOP/s to *tflops.  Synchronous. */
+/* Peak probes used as roofline denominators: kind 0 = FP64 DMMA, 1 = FP64 DFMA; the
+ * tcgen05 kind::f16 (FP32 accumulate) instruction shapes of the product kernels issued back
+ * to back from operands resident in shared memory: 2 = M 128 x N 192 on one CTA per SM,
+ * 3 = M 128 x N 256, 4 = M 256 x N 192 on CTA pairs (cta_group::2), 5 = M 256 x N 256 on CTA
+ * pairs.  Writes the achieved rate in TFLOP/s (0 if a bounded wait ran out) to *tflops.
+ * Synchronous. */
 int momms_probe_peak(int kind, double* tflops, momms_stream_t stream);
 /* Copies `bytes` of device memory from src to dst, `repeats` times over, on `ctas` SMs
  * (one CTA of 1024 threads per SM; 0 = every SM), asynchronously on `stream`, with

@@ -2789,7 +2789,7 @@ int momms_tri_tile(int uplo, int tile_n, int64_t n, int64_t t, int* tm, int* tn,
 }
 
 int momms_probe_peak(int kind, double* tflops, momms_stream_t stream) {
-    if (kind < 0 || kind > 2) return -1;
+    if (kind < 0 || kind > 5) return -1;
     if (!tflops) return -2;
     cudaError_t e = momms::probe_peak(kind, tflops, reinterpret_cast<cudaStream_t>(stream));
     if (e == cudaErrorNotSupported) return MOMMS_ERR_UNSUPPORTED;
