@@ -1180,8 +1180,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const int x = (slab0 + j) * BK;
                     // this CTA's 128 rows of A and 96 rows of B (rows past a plane's end read as zero)
                     if (!withhold) {
-                        tma_load_3d(sa, &tmA, &full[stage], x, (2 * tm2 + static_cast<int>(rank)) * BM, lm);
-                        tma_load_3d(sa + A_TILE, &tmB, &full[stage], x, tn * BN + static_cast<int>(rank) * BNH, lm);
+                        tma_load_3d_cta(sa, &tmA, &full[stage], x, (2 * tm2 + static_cast<int>(rank)) * BM, lm);
+                        tma_load_3d_cta(sa + A_TILE, &tmB, &full[stage], x, tn * BN + static_cast<int>(rank) * BNH,
+                                        lm);
                     }
                     withhold = false;  // (test hook: only the first stage stays empty)
                     last_phase[stage] = static_cast<int>(phase);
