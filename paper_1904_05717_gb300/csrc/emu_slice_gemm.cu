@@ -150,7 +150,6 @@ struct Params {
     uint32_t modp[kCrtMaxModuli];
     uint32_t modmagic[kCrtMaxModuli];  // floor(2^32 / p) + 1
     uint32_t modoff[kCrtMaxModuli];    // p ceil(2^31 / p): makes any int32 sum a uint32 of equal residue
-    float modinvf[kCrtMaxModuli];      // 1 / p rounded to FP32 (the epilogue's quotient estimates)
 };
 
 // S of the single problem (moduli for the modular launch): the launch's, or the device plan's (0
@@ -529,89 +528,6 @@ MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, 
             const uint32_t r = residue_of(static_cast<int32_t>(t[j]), pl, mg, off);
             if (row_ok && c < ncols) dst[c * cstep] = static_cast<uint8_t>(r);
         }
-    }
-}
-
-// ---------------------------------------------------------------- the modular epilogue in FP32
-// A modular unit's accumulator chunks are reduced modulo p as they are drained, in FP32 arithmetic
-// that stays exact: a chunk value x is an integer with |x| <= 1024 127^2 < 2^24 (exact in FP32);
-// q = rint(x / p) is estimated as rint(x * fl(1/p)) -- within one of the true quotient, the
-// estimate's error being below 0.02 for |x| < 2^24, p >= 193 -- through the add-and-subtract of
-// 1.5 2^23 (exact rounding to an integer for |t| < 2^22); r = fma(-q, p, x) is the exact integer
-// x - q p (representable, so the fused operation returns it unrounded), |r| <= 1.5 p; the running
-// sum of r over the chunks stays below 2^24 (at most 130 chunks).  The sum is congruent to the
-// unit's int32 dot product modulo p, so the residue stored at the end -- the sum reduced into
-// [0, p) the same way and read out of the float's low mantissa bits -- is the same byte as the
-// integer path's (residue_of).  No float-to-int conversions: those run on a narrow pipe (16 per
-// clock per SM) and bounded the epilogue of short units.
-MOMMS_DEV float rint_small(float t) {
-    return (t + 12582912.0f) - 12582912.0f;  // round to nearest integer, |t| < 2^22
-}
-MOMMS_DEV float mod_reduce_step(float x, float pf, float inv_p) {
-    const float q = rint_small(x * inv_p);
-    return fmaf(-q, pf, x);
-}
-
-// Drains the chunks of one modular unit (`units` k slabs) into `acc` (the thread's CW columns, a
-// value congruent to each column's dot product modulo p).  Returns false if a bounded wait gave up.
-template <int CW>
-MOMMS_DEV bool drain_residue_unit(int units, int chunk_slabs, uint64_t* acc_full, uint64_t* acc_empty,
-                                  uint32_t& abuf, uint32_t (&aphase)[2], volatile int* abort_flag, uint32_t tacc,
-                                  int lane, float pf, float inv_p, float (&acc)[CW], uint32_t remote_empty = 0,
-                                  bool remote_full = false) {
-#pragma unroll
-    for (int c = 0; c < CW; ++c) acc[c] = 0.f;
-    for (int u = 0; u < units;) {
-        const int cnt = min(chunk_slabs, units - u);
-        const bool ready = remote_full ? mbar_wait_cluster(&acc_full[abuf], aphase[abuf], abort_flag)
-                                       : mbar_wait(&acc_full[abuf], aphase[abuf], abort_flag);
-        if (!ready) return false;
-        tc_fence_after();
-        const uint32_t taddr = tacc + abuf * 256u;
-#pragma unroll
-        for (int q = 0; q < CW / 32; ++q) {
-            uint32_t r[32];
-            tmem_ld_32x32b_x32(taddr + q * 32, r);
-            tmem_ld_wait(r);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc[q * 32 + j] += mod_reduce_step(__uint_as_float(r[j]), pf, inv_p);
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-            if (remote_empty) mbar_arrive_cluster(remote_empty + 8u * abuf);
-            else mbar_arrive(&acc_empty[abuf]);
-        }
-        aphase[abuf] ^= 1u;
-        abuf ^= 1u;
-        u += cnt;
-    }
-    return true;
-}
-
-// The residues of the thread's CW columns (acc from drain_residue_unit) reduced into [0, p) and
-// stored as bytes at res[l][col][row], as store_residues does.
-template <int BN, int CW>
-MOMMS_DEV void store_residue_bytes(const Params& p, int prob, int tm, int tn, int l, int third, int rloc,
-                                   const float (&acc)[CW], float pf, float inv_p) {
-    const int row = tm * BM + rloc;
-    const int col0 = tn * BN + third * CW;
-    const int m = prob < 0 ? p.one.m : p.table[prob].m;
-    const int n = prob < 0 ? p.one.n : p.table[prob].n;
-    uint8_t* res = prob < 0 ? p.res : p.table[prob].res;
-    const bool row_ok = row < m;
-    uint8_t* dst = res + static_cast<size_t>(l) * m * n + static_cast<size_t>(col0) * m + row;
-    const size_t cstep = static_cast<size_t>(m);
-    const int ncols = min(CW, n - col0);
-#pragma unroll
-    for (int c = 0; c < CW; ++c) {
-        float r = mod_reduce_step(acc[c], pf, inv_p);  // |r| <= 1.5 p
-        r = r < 0.f ? r + pf : r;
-        r = r < 0.f ? r + pf : r;
-        r = r >= pf ? r - pf : r;
-        r = r >= pf ? r - pf : r;
-        const uint8_t b = static_cast<uint8_t>(__float_as_uint(r + 8388608.0f) & 0xFFu);  // r in [0, 255]
-        if (row_ok && c < ncols) dst[c * cstep] = b;
     }
 }
 
@@ -1113,22 +1029,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                     stage_columns<BN>(p, prob, tn, p.crt_bits, colexp, colflag);
                     prefetch_residues<BN>(p, tm, tn, lm, third, quad, lane);
                 }
-                if constexpr (MOD) {
-                    if (!final_unit) {
-                        // the unit's residues reduced in FP32 as the chunks are drained (no conversions)
-                        const float pf = static_cast<float>(p.modp[lm]), inv_p = p.modinvf[lm];
-                        float racc[CW];
-                        if (!drain_residue_unit<CW>(pr.nslab, pr.chunk_slabs, acc_full, acc_empty, abuf, aphase,
-                                                    abort_flag, tmem_base + lane_off + third * CW, lane, pf, inv_p,
-                                                    racc)) {
-                            ok = false;
-                            break;
-                        }
-                        store_residue_bytes<BN, CW>(p, prob, tm, tn, lm, third, rloc, racc, pf, inv_p);
-                        if (p.crt_fused) signal_tile(p, tile);
-                        continue;
-                    }
-                }
                 for (int d = MOD ? 2 : pr.S + 1; d >= 2; --d) {
                     int32_t acc[CR];
                     if (!drain_diagonal<CR, CT>((MOD ? 1 : d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty,
@@ -1138,7 +1038,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         break;
                     }
                     if constexpr (MOD) {
-                        if (wait_tile(p, tile, pr.S - 1, abort_flag, wait_ok)) {  // the fused last modulus
+                        if (!final_unit) {
+                            store_residues<BN, CR, CT>(p, prob, tm, tn, lm, third, rloc, acc, tsum);
+                            if (p.crt_fused) signal_tile(p, tile);
+                        } else if (wait_tile(p, tile, pr.S - 1, abort_flag, wait_ok)) {
                             if (p.crt_L == 3)
                                 crt_final<BN, CR, CT, 3>(p, tm, tn, lm, third, rloc, acc, tsum, colexp, colflag);
                             else
@@ -1383,13 +1286,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int it = 0;; ++it) {
             int lm, tm2, tn;
             if (!unit_of(p, it, &lm, &tm2, &tn)) break;
-            const float pf = static_cast<float>(p.modp[lm]), inv_p = p.modinvf[lm];
-            float racc[CW];
-            if (!drain_residue_unit<CW>(p.one.nslab, p.one.chunk_slabs, acc_full, acc_empty, abuf, aphase, abort_flag,
-                                        tmem_base + lane_off + third * CW, lane, pf, inv_p, racc, remote_empty,
+            int32_t acc[CR];
+            if (!drain_diagonal<CR, CT>(p.one.nslab, p.one.chunk_slabs, acc_full, acc_empty, abuf, aphase,
+                                        abort_flag, tmem_base + lane_off + third * CW, tsum, lane, acc, remote_empty,
                                         !leader))
                 break;
-            store_residue_bytes<BN, CW>(p, -1, 2 * tm2 + static_cast<int>(rank), tn, lm, third, rloc, racc, pf, inv_p);
+            store_residues<BN, CR, CT>(p, -1, 2 * tm2 + static_cast<int>(rank), tn, lm, third, rloc, acc, tsum);
         }
     }
 
@@ -1593,7 +1495,6 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
                 p.modp[l] = pl;
                 p.modmagic[l] = a.crt->magic[l];
                 p.modoff[l] = static_cast<uint32_t>(pl * (((1ull << 31) + pl - 1) / pl));
-                p.modinvf[l] = static_cast<float>(1.0 / pl);
             }
             if (a.tri) {
                 p.tri = a.tri;
@@ -1759,7 +1660,6 @@ static cudaError_t launch_bn_batched_mod(const EmuBatchProblem* table, int count
         p.modp[l] = pl;
         p.modmagic[l] = c.magic[l];
         p.modoff[l] = static_cast<uint32_t>(pl * (((1ull << 31) + pl - 1) / pl));
-        p.modinvf[l] = static_cast<float>(1.0 / pl);
     }
     CUtensorMap unused{};
     slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(unused, unused,
