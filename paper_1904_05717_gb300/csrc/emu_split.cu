@@ -219,18 +219,49 @@ __global__ void batch_plan_kernel(const __grid_constant__ EmuBatchPlanArgs a) {
         }
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    int64_t ts = 0, tm = 0;
-    for (int i = 0; i < a.count; ++i) {
-        const EmuBatchPrep& q = a.prep[i];
-        const int64_t tiles = static_cast<int64_t>((q.m + kEmuBM - 1) / kEmuBM) * a.slices[i].tiles_n;
-        a.slices[i].tile0 = ts;
-        a.moduli[i].tile0 = tm;
-        if (q.enc) tm += tiles * q.S;
-        else ts += tiles;
+    // unit offsets of both launches, problem by problem: a block-wide exclusive scan per chunk of
+    // blockDim.x problems (two running totals carried from chunk to chunk)
+    __shared__ long long scan_s[1024], scan_m[1024];
+    __shared__ long long carry_s, carry_m;
+    if (threadIdx.x == 0) {
+        carry_s = 0;
+        carry_m = 0;
     }
-    a.totals[0] = ts;
-    a.totals[1] = tm;
+    __syncthreads();
+    for (int c0 = 0; c0 < a.count; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        long long us = 0, um = 0;
+        if (i < a.count) {
+            const EmuBatchPrep& q = a.prep[i];
+            const long long tiles = static_cast<long long>((q.m + kEmuBM - 1) / kEmuBM) * a.slices[i].tiles_n;
+            if (q.enc) um = tiles * q.S;
+            else us = tiles;
+        }
+        scan_s[threadIdx.x] = us;
+        scan_m[threadIdx.x] = um;
+        __syncthreads();
+        for (int off = 1; off < static_cast<int>(blockDim.x); off <<= 1) {  // inclusive Hillis-Steele scan
+            const long long vs = threadIdx.x >= off ? scan_s[threadIdx.x - off] : 0;
+            const long long vm = threadIdx.x >= off ? scan_m[threadIdx.x - off] : 0;
+            __syncthreads();
+            scan_s[threadIdx.x] += vs;
+            scan_m[threadIdx.x] += vm;
+            __syncthreads();
+        }
+        if (i < a.count) {
+            a.slices[i].tile0 = carry_s + scan_s[threadIdx.x] - us;
+            a.moduli[i].tile0 = carry_m + scan_m[threadIdx.x] - um;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            carry_s += scan_s[blockDim.x - 1];
+            carry_m += scan_m[blockDim.x - 1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    a.totals[0] = carry_s;
+    a.totals[1] = carry_m;
     EmuPlan sm;
     sm.S = smax_s;
     sm.N = nmax_s;
