@@ -16,7 +16,12 @@
  *     scratch are DEVICE pointers owned by the caller.  The library never frees
  *     them and never uses them after the work enqueued by the call has finished.
  *   - Every call is asynchronous on `stream` (0 = the legacy default stream);
- *     results are ready when the stream reaches the enqueued work.
+ *     results are ready when the stream reaches the enqueued work.  The
+ *     data-driven slice count is chosen on the device (momms_set_plan_on_device),
+ *     so the product calls do not wait for the GPU; the exceptions are the
+ *     first call that sizes a workspace (it may allocate), momms_syrk with the
+ *     data-driven slice count (it reads the spread back), and the calls that say
+ *     they synchronise (status, report, probes, tuning).
  *   - Return value: MOMMS_OK (0), a negative number -i when argument i
  *     (1-based, in the order of the prototype) is invalid, or one of the
  *     positive MOMMS_ERR_* codes.  Nothing is enqueued when a call fails.
@@ -410,7 +415,7 @@ int momms_trmm(momms_handle_t handle, int side, int uplo, int trans, int diag, i
  * block) and are joined pairwise by batched products.  The error is that of the
  * GEMMs plus the inverses' (well-conditioned diagonal blocks: a small multiple of
  * 2^-53 (|op(A)| |X|) componentwise).  Device pointers, asynchronous on `stream` (the
- * data-driven slice count of the emulated GEMMs reads back a spread per GEMM).  Errors:
+ * emulated GEMMs choose their slice counts on the device).  Errors:
  * BLAS-style negative index (side -2, uplo -3, trans -4, diag -5, m -6, n -7, A -9,
  * lda -10, B -11, ldb -12), MOMMS_ERR_*. */
 int momms_trsm(momms_handle_t handle, int side, int uplo, int trans, int diag, int64_t m, int64_t n,
