@@ -83,6 +83,8 @@ def parse():
     p.add_argument("--slices", type=int, default=0, help="emulated slice count (0 = from the data)")
     p.add_argument("--group", type=int, default=0, help="C2 raster group in tile rows (0 = library default)")
     p.add_argument("--ctas", type=int, default=0, help="grid cap of the product launch (0 = library default)")
+    p.add_argument("--tile-n", type=int, default=0, choices=[0, 96, 192],
+                   help="emulated tile width (momms_set_tile_n; 0 = automatic)")
     p.add_argument("--cta-pairs", default="auto", choices=["auto", "off", "on"],
                    help="residue products on CTA pairs (momms_set_cta_pairs)")
     p.add_argument("--plan", default="device", choices=["device", "host"],
@@ -461,6 +463,7 @@ def main():
     h.set_raster_group(args.group)
     h.set_max_ctas(args.ctas)
     h.set_cta_pairs({"auto": 0, "off": 1, "on": 2}[args.cta_pairs])
+    h.set_tile_n(args.tile_n)
     h.set_plan_on_device(1 if args.plan == "device" else 0)
 
     def step():
