@@ -296,7 +296,7 @@ struct RecombineCtx {
     uint64_t keep;     // L2 policy of the scratch accesses (evict last)
     uint32_t tsum;     // TMEM address of the int32 sums of the last CT columns
     int sh;            // beta * (position of d in its group)
-    double gscale;     // 2^-(beta * position)
+    int gsh;           // -beta * position: R is 2^gsh times the group's fold
     double rb;         // 2^-beta
     bool gfirst;       // d is the least significant diagonal of its group
     bool rfirst;       // no earlier group has produced R yet
@@ -311,11 +311,15 @@ struct FinalCtx {
     double* cp;              // &C[row, first column of the thread]
     int64_t ldc;
     double alpha, beta_c, qnan;
+    bool unit_alpha, beta_zero;  // alpha == 1, beta_c == 0, decided once per tile
 };
 enum { kMid = 0, kGroupEnd = 1, kLast = 2 };
 constexpr int BM_ = kEmuBM;
 
-// 8 columns [c0, c0 + 8): exact int64 group sum, FP64 fold at the group end, C at the end.
+// 8 columns [c0, c0 + 8): exact int64 group sum, FP64 fold at the group end, C at the end.  The
+// FP64 pipe is this epilogue's bottleneck, so every power-of-two scaling is an exponent-field add
+// (mul_pow2) and alpha = 1 multiplies nothing: per element the conversion and the fold at a group
+// end, the conversion, the fold and beta_c's multiply-add at the end.
 template <int MODE, bool QT = false>
 MOMMS_DEV void recombine8(const RecombineCtx& rc, const int32_t (&pv)[8], int c0, const FinalCtx* fc) {
     long long qv[8];
@@ -354,15 +358,18 @@ MOMMS_DEV void recombine8(const RecombineCtx& rc, const int32_t (&pv)[8], int c0
             }
         } else {
             const double x = static_cast<double>(v);
-            const double r = (rc.rfirst ? x : fma(rv[j], rc.rb, x)) * rc.gscale;
+            const double f = rc.rfirst ? x : fma(rv[j], rc.rb, x);  // exact but for this rounding
             if (MODE == kGroupEnd) {
-                st_l2_hint(rc.R + (c0 + j) * BM_, r, rc.keep);
+                st_l2_hint(rc.R + (c0 + j) * BM_, mul_pow2(f, rc.gsh), rc.keep);
             } else if (fc->row_ok && c0 + j < fc->ncols &&
                        (fc->tri == 0 || (fc->tri == 1 ? c0 + j <= fc->lim : c0 + j >= fc->lim))) {
-                const double y = (fc->eflag || fc->colflag[c0 + j]) ? fc->qnan
-                                                                    : scale_pow2(r, fc->ei + fc->colexp[c0 + j]);
+                // f 2^gsh is exact (no partial sum comes near the subnormal range), so one scaling by
+                // 2^(gsh + e_i + f_j - 2 beta) rounds as the two would
+                double y = (fc->eflag || fc->colflag[c0 + j]) ? fc->qnan
+                                                              : mul_pow2(f, rc.gsh + fc->ei + fc->colexp[c0 + j]);
+                if (!fc->unit_alpha) y *= fc->alpha;
                 double* cp = fc->cp + static_cast<int64_t>(c0 + j) * fc->ldc;
-                *cp = (fc->beta_c == 0.0) ? fc->alpha * y : fma(fc->beta_c, *cp, fc->alpha * y);
+                *cp = fc->beta_zero ? y : fma(fc->beta_c, *cp, y);
             }
         }
     }
@@ -422,7 +429,7 @@ MOMMS_DEV void recombine_diagonal(const Params& p, int prob, int tm, int tn, int
     constexpr int CW = BN / 3;
     const bool gfirst = (gj == 0);
     const bool gend = (pr.group_end >> d) & 1u;
-    const RecombineCtx rc{Q, R, tsum, keep, tsum, pr.beta * gj, pow2_normal(-pr.beta * gj), rb, gfirst, rfirst};
+    const RecombineCtx rc{Q, R, tsum, keep, tsum, pr.beta * gj, -pr.beta * gj, rb, gfirst, rfirst};
     if (!gend) {
         recombine<kMid, CR, CT>(rc, acc, nullptr);
     } else if (d != 2) {
@@ -447,6 +454,8 @@ MOMMS_DEV void recombine_diagonal(const Params& p, int prob, int tm, int tn, int
         fc.alpha = bp ? bp->alpha : one.alpha;
         fc.beta_c = bp ? bp->beta_c : one.beta_c;
         fc.qnan = qnan;
+        fc.unit_alpha = fc.alpha == 1.0;
+        fc.beta_zero = fc.beta_c == 0.0;
         recombine<kLast, CR, CT>(rc, acc, &fc);
     }
     if (gend) {
@@ -790,7 +799,6 @@ __global__ void __launch_bounds__(256) tail_fixup_kernel(const __grid_constant__
         const bool gfirst = (gj == 0);
         const bool gend = (one.group_end >> d) & 1u;
         const int sh = beta * gj;
-        const double gscale = pow2_normal(-beta * gj);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const long long p64 = static_cast<long long>(pv[j]);
@@ -799,7 +807,7 @@ __global__ void __launch_bounds__(256) tail_fixup_kernel(const __grid_constant__
                 q[j] = v;
             } else {
                 const double x = static_cast<double>(v);
-                r[j] = (rfirst ? x : fma(r[j], rb, x)) * gscale;
+                r[j] = mul_pow2(rfirst ? x : fma(r[j], rb, x), -beta * gj);
             }
         }
         if (gend) {
@@ -814,13 +822,15 @@ __global__ void __launch_bounds__(256) tail_fixup_kernel(const __grid_constant__
     const int ei = one.e[row];
     const bool eflag = one.ef[row] != 0;
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    const bool unit_alpha = one.alpha == 1.0, beta_zero = one.beta_c == 0.0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int col = tn * kEmuBNMax + cg * 8 + j;
         if (col >= one.n) break;
-        const double y = (eflag || one.ff[col]) ? qnan : scale_pow2(r[j], ei + (one.f[col] - 2 * beta));
+        double y = (eflag || one.ff[col]) ? qnan : mul_pow2(r[j], ei + (one.f[col] - 2 * beta));
+        if (!unit_alpha) y *= one.alpha;
         double* cp = one.C + row + static_cast<int64_t>(col) * one.ldc;
-        *cp = (one.beta_c == 0.0) ? one.alpha * y : fma(one.beta_c, *cp, one.alpha * y);
+        *cp = beta_zero ? y : fma(one.beta_c, *cp, y);
     }
 }
 

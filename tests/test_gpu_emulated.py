@@ -154,6 +154,22 @@ def test_emulated_single_group_bitwise_vs_oracle_emulation(S):
     assert np.array_equal(C, Co)
 
 
+@pytest.mark.parametrize("scale", [-510, -520, 512])
+def test_emulated_rounding_at_the_ends_of_the_exponent_range(scale):
+    # products scaled into the subnormal range (the 53-bit rounding, then the subnormal grid, as the
+    # oracle does it) and beyond the largest double (infinities): one exact group, so bit for bit
+    m, n, k, S = 130, 200, 120, 6
+    A = syn.matrix("phi", m, k, 53, phi=1.0) * 2.0 ** scale
+    B = syn.matrix("phi", k, n, 54, phi=1.0) * 2.0 ** scale
+    Co, _ = oracle.emulated_dgemm(A, B, S, BETA)
+    C, _, _ = emulated(A, B, F(np.zeros((m, n))), 1.0, 0.0, S)
+    if scale < 0:  # -510: normal and subnormal results mixed, -520: all subnormal
+        assert np.any((Co != 0) & (np.abs(Co) < np.finfo(np.float64).tiny))
+    else:
+        assert np.any(np.isinf(Co)) and np.any(np.isfinite(Co))
+    assert np.array_equal(C, Co)
+
+
 @pytest.mark.parametrize("opa,opb", [(1, 0), (0, 1), (1, 1)])
 def test_emulated_transposes(opa, opb):
     m, n, k = 140, 260, 150
