@@ -38,6 +38,8 @@ uint32_t inverse_mod(uint32_t a, uint32_t p) {  // a^-1 mod p (gcd(a, p) = 1)
     return static_cast<uint32_t>(t);
 }
 
+constexpr int kGroup = 8;  // moduli whose residues one thread loads at once
+
 // C from the residue bytes res[l][j][i] (m n per modulus).  Per element, with S = sum_l c_l w_l
 // (so S = Z mod P, and S / P = q + Z / P with |Z / P| <= 1/4 by the choice of moduli):
 //   q  = round(sum_l c_l F_l / 2^19), F_l = round(2^19 w_l / P): one 32-bit multiply-add per
@@ -77,21 +79,33 @@ __device__ __forceinline__ void crt_columns(int64_t m, int64_t n, const uint8_t*
                 for (int q = 0; q < L; ++q) s[t][q] = 0;
             }
             const uint8_t* src = res + j * m + i0;
-            for (int l = 0; l < r.N; ++l) {
-                uint32_t word[V > 4 ? 2 : 1];
-                if constexpr (V == 8) {
-                    const uint2 w2 = __ldcs(reinterpret_cast<const uint2*>(src + l * mn));
-                    word[0] = w2.x;
-                    word[1] = w2.y;
-                } else if constexpr (V == 4) {
-                    word[0] = __ldcs(reinterpret_cast<const unsigned int*>(src + l * mn));
-                } else {
-                    word[0] = src[l * mn];
-                }
-                const uint32_t fl = r.frac[l];
+            // the moduli eight at a time: their loads in flight together (one load per modulus
+            // in turn left every modulus a full memory latency)
+            for (int l0 = 0; l0 < r.N; l0 += kGroup) {
+                uint32_t word[kGroup][V > 4 ? 2 : 1];
 #pragma unroll
-                for (int t = 0; t < V; ++t)
-                    crt_accumulate<L>(s[t], qs[t], (word[t >> 2] >> (8 * (t & 3))) & 0xFFu, r.w[l], fl);
+                for (int q = 0; q < kGroup; ++q) {
+                    const int l = l0 + q;
+                    if constexpr (V == 8) {
+                        uint2 w2 = make_uint2(0u, 0u);
+                        if (l < r.N) w2 = __ldcs(reinterpret_cast<const uint2*>(src + l * mn));
+                        word[q][0] = w2.x;
+                        word[q][V > 4 ? 1 : 0] = w2.y;
+                    } else if constexpr (V == 4) {
+                        word[q][0] = l < r.N ? __ldcs(reinterpret_cast<const unsigned int*>(src + l * mn)) : 0u;
+                    } else {
+                        word[q][0] = l < r.N ? src[l * mn] : 0u;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q) {
+                    const int l = l0 + q;
+                    if (l >= r.N) break;
+                    const uint32_t fl = r.frac[l];
+#pragma unroll
+                    for (int t = 0; t < V; ++t)
+                        crt_accumulate<L>(s[t], qs[t], (word[q][t >> 2] >> (8 * (t & 3))) & 0xFFu, r.w[l], fl);
+                }
             }
             double y[V];
 #pragma unroll
@@ -169,7 +183,16 @@ __device__ __forceinline__ void crt_batch_column(const CrtBatchProblem& pr, cons
 #pragma unroll
         for (int q = 0; q < L; ++q) s[q] = 0;
         const uint8_t* src = pr.res + j * m + i;
-        for (int l = 0; l < r.N; ++l) crt_accumulate<L>(s, qs, src[l * mn], r.w[l], r.frac[l]);
+        for (int l0 = 0; l0 < r.N; l0 += kGroup) {  // kGroup loads in flight at a time, as in crt_columns
+            uint32_t c[kGroup];
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) c[q] = l0 + q < r.N ? src[(l0 + q) * mn] : 0u;
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) {
+                if (l0 + q >= r.N) break;
+                crt_accumulate<L>(s, qs, c[q], r.w[l0 + q], r.frac[l0 + q]);
+            }
+        }
         double y = (fj || pr.ef[i] != 0) ? qnan : crt_value<L>(s, qs, r.Pw, pr.e[i] + Ej);
         if (!unit_alpha) y *= pr.alpha;
         double* cp = pr.C + i + j * pr.ldc;
