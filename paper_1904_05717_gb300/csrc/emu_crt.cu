@@ -38,7 +38,13 @@ uint32_t inverse_mod(uint32_t a, uint32_t p) {  // a^-1 mod p (gcd(a, p) = 1)
     return static_cast<uint32_t>(t);
 }
 
-constexpr int kGroup = 8;  // moduli whose residues one thread loads at once
+
+// Moduli whose residues one thread loads at once (kGroup of crt_columns): eight in the plan kernel
+// (measured: the rank-k 16384^2 x 256 call 0.8 ms faster than one at a time, 8192^3 0.1 ms), one in
+// the kernel of the host-planned moduli count (SYRK n = k = 8192, a triangle: 0.2 ms slower with
+// four or eight -- 80 registers against 60).
+constexpr int kGroupPlan = 8, kGroupFixed = 1;
+constexpr int kGroup = 8;  // (the batched reconstruction)
 
 // C from the residue bytes res[l][j][i] (m n per modulus).  Per element, with S = sum_l c_l w_l
 // (so S = Z mod P, and S / P = q + Z / P with |Z / P| <= 1/4 by the choice of moduli):
@@ -52,7 +58,7 @@ constexpr int kGroup = 8;  // moduli whose residues one thread loads at once
 // consecutive rows and loads one 32-bit word per modulus, and with CV (16-byte aligned pairs of
 // C) reads and writes C as two double2.  L = 3 when P < 2^96, else 4.  The modulus loop keeps
 // few registers live, so that many warps hide the load latency.
-template <int V, bool CV, int L>
+template <int V, bool CV, int L, int kGroup>
 __device__ __forceinline__ void crt_columns(int64_t m, int64_t n, const uint8_t* __restrict__ res, const CrtRecon& r,
                                             int bits, const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
                                             const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
                                                   const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
                                                   double alpha, double beta, double* __restrict__ C, int64_t ldc,
                                                   int tri) {
-    crt_columns<V, CV, L>(m, n, res, r, r.bits, e, ef, f, ff, alpha, beta, C, ldc, tri);
+    crt_columns<V, CV, L, kGroupFixed>(m, n, res, r, r.bits, e, ef, f, ff, alpha, beta, C, ldc, tri);
 }
 
 // The same with the moduli count and the operand width from the device plan (the constants of
@@ -164,8 +170,8 @@ __global__ void __launch_bounds__(256) crt_plan_kernel(int64_t m, int64_t n, con
     const int N = plan->N;
     if (N < 1 || N > kCrtMaxModuli) return;
     const CrtRecon& r = set.by_n[N];
-    if (r.Pw[3] == 0) crt_columns<V, CV, 3>(m, n, res, r, plan->bits, e, ef, f, ff, alpha, beta, C, ldc, 0);
-    else crt_columns<V, CV, 4>(m, n, res, r, plan->bits, e, ef, f, ff, alpha, beta, C, ldc, 0);
+    if (r.Pw[3] == 0) crt_columns<V, CV, 3, kGroupPlan>(m, n, res, r, plan->bits, e, ef, f, ff, alpha, beta, C, ldc, 0);
+    else crt_columns<V, CV, 4, kGroupPlan>(m, n, res, r, plan->bits, e, ef, f, ff, alpha, beta, C, ldc, 0);
 }
 
 // One column of one problem of a batch: the warp's lanes take its rows 32 apart, one element
