@@ -39,11 +39,10 @@ uint32_t inverse_mod(uint32_t a, uint32_t p) {  // a^-1 mod p (gcd(a, p) = 1)
 }
 
 
-// Moduli whose residues one thread loads at once (kGroup of crt_columns): eight in the plan kernel
-// (measured: the rank-k 16384^2 x 256 call 0.8 ms faster than one at a time, 8192^3 0.1 ms), one in
-// the kernel of the host-planned moduli count (SYRK n = k = 8192, a triangle: 0.2 ms slower with
-// four or eight -- 80 registers against 60).
-constexpr int kGroupPlan = 8, kGroupFixed = 1;
+// Moduli whose residues one thread loads at once (kGroup of crt_columns): eight (measured: the
+// rank-k 16384^2 x 256 call 0.8 ms faster than one at a time, 8192^3 0.1 ms), but one for a
+// triangle (SYRK n = k = 8192: 0.2 ms slower with four or eight -- 80 registers against 60).
+constexpr int kGroupPlan = 8;
 constexpr int kGroup = 8;  // (the batched reconstruction)
 
 // C from the residue bytes res[l][j][i] (m n per modulus).  Per element, with S = sum_l c_l w_l
@@ -147,14 +146,14 @@ __device__ __forceinline__ void crt_columns(int64_t m, int64_t n, const uint8_t*
     }
 }
 
-template <int V, bool CV, int L>
+template <int V, bool CV, int L, int G>
 __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
                                                   const __grid_constant__ CrtRecon r,
                                                   const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
                                                   const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
                                                   double alpha, double beta, double* __restrict__ C, int64_t ldc,
                                                   int tri) {
-    crt_columns<V, CV, L, kGroupFixed>(m, n, res, r, r.bits, e, ef, f, ff, alpha, beta, C, ldc, tri);
+    crt_columns<V, CV, L, G>(m, n, res, r, r.bits, e, ef, f, ff, alpha, beta, C, ldc, tri);
 }
 
 // The same with the moduli count and the operand width from the device plan (the constants of
@@ -316,8 +315,11 @@ cudaError_t launch_crt_reconstruct(int64_t m, int64_t n, const uint8_t* res, con
     if (by > n) by = n;
     if (by > 65535) by = 65535;
     const dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(by));
-#define MOMMS_CRT_LAUNCH(V, CV, L) \
-    crt_kernel<V, CV, L><<<grid, 256, 0, stream>>>(m, n, res, r, e, ef, f, ff, alpha, beta, C, ldc, tri)
+#define MOMMS_CRT_LAUNCH(V, CV, L)                                                                    \
+    do {                                                                                              \
+        if (tri) crt_kernel<V, CV, L, 1><<<grid, 256, 0, stream>>>(m, n, res, r, e, ef, f, ff, alpha, beta, C, ldc, tri); \
+        else crt_kernel<V, CV, L, kGroupPlan><<<grid, 256, 0, stream>>>(m, n, res, r, e, ef, f, ff, alpha, beta, C, ldc, tri); \
+    } while (0)
     if (cvec) {
         if (three) MOMMS_CRT_LAUNCH(4, true, 3);
         else MOMMS_CRT_LAUNCH(4, true, 4);
