@@ -503,11 +503,24 @@ MOMMS_DEV uint32_t residue_of(int32_t x, uint32_t p, uint32_t magic, uint32_t of
     return static_cast<uint32_t>(r);
 }
 
+// Four columns' bytes of one row (column c in byte c) transposed across the four lanes of each
+// group (rows 4g .. 4g + 3 of the warp): lane q of the group returns column q's bytes of the
+// group's four rows, row 4g + t in byte t.
+MOMMS_DEV uint32_t transpose4x4_bytes(uint32_t w, int lane) {
+    const uint32_t o1 = __shfl_xor_sync(0xffffffffu, w, 1);
+    const uint32_t t1 = (lane & 1) ? __byte_perm(w, o1, 0x3715) : __byte_perm(w, o1, 0x6240);
+    const uint32_t o2 = __shfl_xor_sync(0xffffffffu, t1, 2);
+    return (lane & 2) ? __byte_perm(t1, o2, 0x3276) : __byte_perm(t1, o2, 0x5410);
+}
+
 // The modular epilogue of modulus l: the thread's int32 sums (CR in `acc`, CT in TMEM at
-// `tsum`) reduced into [0, p) and stored as bytes at res[l][col][row] (a warp's 32 rows: one
-// 32-byte sector per column; 16-byte strided bytes per element instead made the residue
-// product 30 % slower).  The TMEM reads are warp-wide, so every lane takes them before the
-// bounds checks.
+// `tsum`) reduced into [0, p) and stored as bytes at res[l][col][row].  With m a multiple of 4
+// (and res 4-byte aligned) every four columns of the four rows of a lane group are transposed
+// across the group and stored as one 32-bit word per lane: a quarter of the store instructions,
+// 4 x 32 contiguous bytes each (one byte store per element and column measured 1.2 of the 5.2 us
+// a rank-k unit of 128 x 192 x 256 takes).  Else one byte per element (a warp's 32 rows: one
+// 32-byte sector per column).  The TMEM reads and the shuffles are warp-wide, so every lane takes
+// them before the bounds checks.
 template <int BN, int CR, int CT>
 MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, int third, int rloc,
                               const int32_t (&acc)[CR], uint32_t tsum) {
@@ -518,9 +531,40 @@ MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, 
     const int n = prob < 0 ? p.one.n : p.table[prob].n;
     uint8_t* res = prob < 0 ? p.res : p.table[prob].res;
     const bool row_ok = row < m;
-    uint8_t* dst = res + static_cast<size_t>(l) * m * n + static_cast<size_t>(col0) * m + row;
     const size_t cstep = static_cast<size_t>(m);
     const int ncols = min(BN / 3, n - col0);
+    const int lane = static_cast<int>(threadIdx.x & 31);
+    if ((m & 3) == 0 && (reinterpret_cast<uintptr_t>(res) & 3) == 0) {
+        // word store: lane 4g + q writes column 4j + q of rows 4g .. 4g + 3 (all inside m or none)
+        uint8_t* base = res + static_cast<size_t>(l) * m * n + static_cast<size_t>(col0) * m + (row & ~3);
+        const int cq = lane & 3;
+#pragma unroll
+        for (int c = 0; c < CR; c += 4) {
+            const uint32_t w = residue_of(acc[c], pl, mg, off) | (residue_of(acc[c + 1], pl, mg, off) << 8) |
+                               (residue_of(acc[c + 2], pl, mg, off) << 16) |
+                               (residue_of(acc[c + 3], pl, mg, off) << 24);
+            const uint32_t x = transpose4x4_bytes(w, lane);
+            if (row_ok && c + cq < ncols) *reinterpret_cast<uint32_t*>(base + (c + cq) * cstep) = x;
+        }
+#pragma unroll
+        for (int q = 0; q < CT / 16; ++q) {
+            uint32_t t[16];
+            tmem_ld_32x32b_x16(tsum + q * 16, t);
+            tmem_ld_wait(t);
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+                const int c = CR + q * 16 + j;
+                const uint32_t w = residue_of(static_cast<int32_t>(t[j]), pl, mg, off) |
+                                   (residue_of(static_cast<int32_t>(t[j + 1]), pl, mg, off) << 8) |
+                                   (residue_of(static_cast<int32_t>(t[j + 2]), pl, mg, off) << 16) |
+                                   (residue_of(static_cast<int32_t>(t[j + 3]), pl, mg, off) << 24);
+                const uint32_t x = transpose4x4_bytes(w, lane);
+                if (row_ok && c + cq < ncols) *reinterpret_cast<uint32_t*>(base + (c + cq) * cstep) = x;
+            }
+        }
+        return;
+    }
+    uint8_t* dst = res + static_cast<size_t>(l) * m * n + static_cast<size_t>(col0) * m + row;
 #pragma unroll
     for (int c = 0; c < CR; ++c) {
         const uint32_t r = residue_of(acc[c], pl, mg, off);
