@@ -150,6 +150,13 @@ struct Params {
     uint32_t modp[kCrtMaxModuli];
     uint32_t modmagic[kCrtMaxModuli];  // floor(2^32 / p) + 1
     uint32_t modoff[kCrtMaxModuli];    // p ceil(2^31 / p): makes any int32 sum a uint32 of equal residue
+    // 32-bit unit decoding (u32dec: every unit index of a single problem below 2^31): the
+    // launch-invariant divisors of tile_of, as multiply-high divisions -- every warp role decodes
+    // every unit, and 64-bit division routines cost those warps microseconds per small-k unit.
+    int u32dec;
+    FastDiv fd_n[17];         // moduli counts 1..16 (the count may come from the device plan)
+    FastDiv fd_gt, fd_gt_last;  // group_tiles, and the tiles of the last (partial) group
+    TileDiv tdv;              // the member order's divisors
 };
 
 // S of the single problem (moduli for the modular launch): the launch's, or the device plan's (0
@@ -196,6 +203,23 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
         // modulus by modulus.  A wave covers one modulus of a block of tiles (the L2 footprint of a
         // digit pair), only the last round is partial, and with group_tiles = the grid a full
         // group keeps every modulus of a tile on one CTA.
+        if (p.u32dec && !p.tri) {  // the same order in 32-bit arithmetic
+            const uint32_t tiles = static_cast<uint32_t>(p.tiles_m) * static_cast<uint32_t>(p.tiles_n);
+            const int N = one_S(p);
+            const uint32_t u = blockIdx.x + static_cast<uint32_t>(it) * gridDim.x;
+            if (N < 1 || N > 16 || u >= tiles * static_cast<uint32_t>(N)) return false;
+            const uint32_t g = fdiv(fdiv(u, p.fd_gt), p.fd_n[N]);  // floor(u / (GT N))
+            const uint32_t first = g * p.fd_gt.d;
+            const FastDiv& gt = tiles - first < p.fd_gt.d ? p.fd_gt_last : p.fd_gt;
+            const uint32_t r = u - first * static_cast<uint32_t>(N);
+            const uint32_t l = fdiv(r, gt);
+            const uint32_t t = first + (r - l * gt.d);
+            *prob = -1;
+            *lmod = static_cast<int>(l);
+            if (tile) *tile = t;
+            member_tile_fast(p.member == kMemberA1 ? kMemberA2 : p.member, p.tdv, t, p.tiles_m, tm, tn);
+            return true;
+        }
         const int64_t tiles = p.tri ? p.tri_tiles : static_cast<int64_t>(p.tiles_m) * p.tiles_n;
         const int64_t N = one_S(p);
         const int64_t u = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
@@ -227,6 +251,12 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
         *prob = -1;
         if (p.plan_kind != 0 && one_S(p) == 0) return false;  // the plan chose the modular encoding
         if (p.tail_parts >= 2 && it >= p.full_rounds) return false;  // the rest is the tail launch's
+        if (p.u32dec && p.member != kMemberA1) {
+            const uint32_t t = blockIdx.x + static_cast<uint32_t>(it) * gridDim.x;
+            if (t >= static_cast<uint32_t>(p.tiles_m) * static_cast<uint32_t>(p.tiles_n)) return false;
+            member_tile_fast(p.member, p.tdv, t, p.tiles_m, tm, tn);
+            return true;
+        }
         return member_tile(p.member, p.group, blockIdx.x, gridDim.x, it, p.tiles_m, p.tiles_n, tm, tn);
     }
     const int64_t t = static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(it) * gridDim.x;
@@ -1513,6 +1543,12 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
         if (a.used_ctas) *a.used_ctas = static_cast<int>(ctas);
         if (a.used_group) *a.used_group = p.group;
         p.table = nullptr;
+        // unit indices below 2^31 (blockIdx + it ctas stays below tiles N + ctas): 32-bit decoding
+        if (tiles_m * tiles_n * kCrtMaxModuli + ctas < (int64_t(1) << 31)) {
+            p.u32dec = 1;
+            for (int q = 1; q <= 16; ++q) p.fd_n[q] = make_fastdiv(static_cast<uint32_t>(q));
+            p.tdv = make_tilediv(p.group, static_cast<int>(tiles_m), static_cast<int>(tiles_n));
+        }
         p.withhold = a.withhold > 0 ? 1 : g_withhold.exchange(0);
         if (a.plan) {
             // S or N from the device plan; the pass above was sized for the largest the plan may pick
@@ -1532,6 +1568,9 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
             // four consecutive waves still share a modulus (groups of one wave's tiles lost that reuse:
             // 8.3 -> 10.9 ms at 8192^3)
             p.group_tiles = a.crt_fuse ? static_cast<int>(std::min<int64_t>(tiles, 4 * ctas)) : static_cast<int>(tiles);
+            p.fd_gt = make_fastdiv(static_cast<uint32_t>(p.group_tiles));
+            p.fd_gt_last = make_fastdiv(static_cast<uint32_t>(tiles % p.group_tiles == 0 ? p.group_tiles
+                                                                                        : tiles % p.group_tiles));
             if (a.crt_fuse) {
                 if (a.done == nullptr || a.crt_fuse->N != a.crt->N) return cudaErrorInvalidValue;
                 p.crt_fused = 1;

@@ -19,6 +19,77 @@ namespace momms {
 
 enum : int { kMemberAuto = 0, kMemberC2 = 1, kMemberA2 = 2, kMemberB2 = 3, kMemberA1 = 4 };
 
+// Division of 32-bit unsigned integers by a divisor d >= 1 fixed for a launch, as a multiply-high,
+// two shifts and two adds instead of a division routine (the method of Granlund and Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, Sec. 4: the multiplier is
+// 2^32 + m, one bit too wide for a register, so the quotient is t + (n - t) / 2 shifted, t being
+// the high word of m n).  With l = ceil(log2 d): m = floor(2^32 (2^l - d) / d) + 1, and
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) for every 32-bit n.
+struct FastDiv {
+    uint32_t d, m, s1, s2;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f{};
+    if (d == 0) d = 1;  // (never used with d = 0; keeps the quotient defined)
+    int l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    f.d = d;
+    f.m = static_cast<uint32_t>(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    f.s1 = l < 1 ? static_cast<uint32_t>(l) : 1u;
+    f.s2 = l > 1 ? static_cast<uint32_t>(l - 1) : 0u;
+    return f;
+}
+__host__ __device__ inline uint32_t fdiv(uint32_t n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(f.m, n);
+#else
+    const uint32_t t = static_cast<uint32_t>((static_cast<uint64_t>(f.m) * n) >> 32);
+#endif
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// The launch-invariant divisors of a member's tile order (member_tile_fast).
+struct TileDiv {
+    FastDiv tn, tm;         // tiles_n, tiles_m
+    FastDiv gsize;          // C2: G tiles_n
+    FastDiv gm, gm_last;    // C2: G, and the tile rows of the last (partial) row group
+    int G;
+};
+inline TileDiv make_tilediv(int group, int tiles_m, int tiles_n) {
+    TileDiv t{};
+    t.G = group < 1 ? 1 : group;
+    t.tn = make_fastdiv(static_cast<uint32_t>(tiles_n));
+    t.tm = make_fastdiv(static_cast<uint32_t>(tiles_m));
+    t.gsize = make_fastdiv(static_cast<uint32_t>(t.G) * static_cast<uint32_t>(tiles_n));
+    t.gm = make_fastdiv(static_cast<uint32_t>(t.G));
+    const int rest = tiles_m % t.G;
+    t.gm_last = make_fastdiv(static_cast<uint32_t>(rest == 0 ? t.G : rest));
+    return t;
+}
+
+// Tile t (< tiles_m tiles_n < 2^31) of the A2, B2 and C2 orders as member_tile places it, with
+// the divisions by invariant divisors.
+__host__ __device__ inline void member_tile_fast(int member, const TileDiv& dv, uint32_t t, int tiles_m, int* tm,
+                                                 int* tn) {
+    if (member == kMemberA2) {
+        const uint32_t q = fdiv(t, dv.tn);
+        *tm = static_cast<int>(q);
+        *tn = static_cast<int>(t - q * dv.tn.d);
+    } else if (member == kMemberB2) {
+        const uint32_t q = fdiv(t, dv.tm);
+        *tn = static_cast<int>(q);
+        *tm = static_cast<int>(t - q * dv.tm.d);
+    } else {
+        const uint32_t g = fdiv(t, dv.gsize);
+        const uint32_t first_m = g * static_cast<uint32_t>(dv.G);
+        const FastDiv& gm = static_cast<uint32_t>(tiles_m) - first_m < static_cast<uint32_t>(dv.G) ? dv.gm_last : dv.gm;
+        const uint32_t r = t - g * dv.gsize.d;
+        const uint32_t q = fdiv(r, gm);
+        *tm = static_cast<int>(first_m + (r - q * gm.d));
+        *tn = static_cast<int>(q);
+    }
+}
+
 // Maps the i-th tile taken by CTA `cta` (of `ctas`) to tile coordinates.
 // Returns false when the CTA has no i-th tile.
 __host__ __device__ inline bool member_tile(int member, int group, int64_t cta, int64_t ctas,
