@@ -146,8 +146,14 @@ __device__ __forceinline__ void crt_columns(int64_t m, int64_t n, const uint8_t*
     }
 }
 
+// Four blocks of 256 threads resident per SM (at most 64 registers a thread): the kernel is bound
+// by the issue of its wide multiply-adds and by load latency, and two resident blocks (98
+// registers) left it short of warps -- rank-k 16384^2 with 15 moduli 4.80 -> 4.05 ms, 8192^2 with
+// 12 moduli 1.04 -> 0.79 ms, the same bits (a few bytes of spills cost less than the lost warps).
+constexpr int kCrtMinBlocks = 4;
+
 template <int V, bool CV, int L, int G>
-__global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
+__global__ void __launch_bounds__(256, kCrtMinBlocks) crt_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
                                                   const __grid_constant__ CrtRecon r,
                                                   const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
                                                   const int32_t* __restrict__ f, const uint8_t* __restrict__ ff,
@@ -159,7 +165,7 @@ __global__ void __launch_bounds__(256) crt_kernel(int64_t m, int64_t n, const ui
 // The same with the moduli count and the operand width from the device plan (the constants of
 // every count in `set`); returns at once when the plan chose digit slices.
 template <int V, bool CV>
-__global__ void __launch_bounds__(256) crt_plan_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
+__global__ void __launch_bounds__(256, kCrtMinBlocks) crt_plan_kernel(int64_t m, int64_t n, const uint8_t* __restrict__ res,
                                                        const __grid_constant__ CrtReconSet set,
                                                        const EmuPlan* __restrict__ plan,
                                                        const int32_t* __restrict__ e, const uint8_t* __restrict__ ef,
@@ -205,7 +211,7 @@ __device__ __forceinline__ void crt_batch_column(const CrtBatchProblem& pr, cons
     }
 }
 
-__global__ void __launch_bounds__(256) crt_batch_kernel(const CrtBatchProblem* __restrict__ probs,
+__global__ void __launch_bounds__(256, kCrtMinBlocks) crt_batch_kernel(const CrtBatchProblem* __restrict__ probs,
                                                         const int2* __restrict__ items,
                                                         const __grid_constant__ CrtReconSet set) {
     const int2 it = items[blockIdx.x];
