@@ -467,8 +467,8 @@ __device__ __forceinline__ void write_residues(const double (&x)[NE], bool valid
         for (int i = 0; i < NE; ++i) {
             const uint32_t t = a2[i] * k32 + a1[i] * k16 + a0[i];  // < 2^32 for bits <= 56
             const uint32_t q = __umulhi(t, mg);                    // floor(t / p) or one more
-            int r = static_cast<int>(t - q * pl);                  // in [-p, p)
-            if (r < 0) r += static_cast<int>(pl);
+            const int r = static_cast<int>(t - q * pl);            // in [-p, p), r = t mod p
+            // the signed residue in (-p, p], then one step of p into [lo, hi] (no step to [0, p) first)
             int v = neg[i] ? -r : r;
             if (v > hi) v -= static_cast<int>(pl);
             else if (v < lo) v += static_cast<int>(pl);
