@@ -291,6 +291,11 @@ void crt_consts(int N, int bits, CrtConsts* c, CrtRecon* r) {
         c->magic[l] = static_cast<uint32_t>((1ull << 32) / p + 1);
         c->c16[l] = static_cast<uint32_t>((1ull << 16) % p);
         c->c32[l] = static_cast<uint32_t>((1ull << 32) % p);
+        for (int j = 0; j < 3; ++j) c->kf[l][j] = static_cast<float>((1ull << (14 * (j + 1))) % p);
+        c->pf[l] = static_cast<float>(p);
+        c->invf[l] = 1.0f / static_cast<float>(p);
+        c->lof[l] = -static_cast<float>(p / 2);
+        c->hif[l] = static_cast<float>((p - 1) / 2);
         const u128 Ml = P / p;
         const uint32_t inv = inverse_mod(static_cast<uint32_t>(Ml % p), p);
         const u128 w = Ml * inv;  // < P

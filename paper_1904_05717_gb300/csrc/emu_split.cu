@@ -438,42 +438,44 @@ __device__ __forceinline__ void write_digits8(const double (&x)[8], bool valid_r
 }
 
 // Residues of the integer operand A^ = trunc(|x| 2^(bits - e)) sign(x) modulo each p_l, in the
-// symmetric range [-floor(p/2), floor((p-1)/2)] (|r| <= 127: exact in fp16, products < 2^14 as
-// for the digits).  A^ is the top `bits` bits of the 128-bit fraction (the first bits/7
-// digits); its residue comes from 16-bit pieces, a0 + 2^16 a1 + 2^32 a2, with 2^16 and 2^32
-// reduced mod p beforehand, and one multiply-high quotient.
+// symmetric range [lo, hi] = [-floor(p/2), floor((p-1)/2)] (|r| <= 127: exact in fp16, products
+// < 2^14 as for the digits).  A^ is the top `bits` bits of the 128-bit fraction (the first bits/7
+// digits), cut into four 14-bit pieces a_j, signed, held as FP32 integers; per modulus, in exact
+// FP32 arithmetic (the FP32 pipes issue twice the integer multiply-adds' rate):
+//   t = a_0 + a_1 (2^14 mod p) + a_2 (2^28 mod p) + a_3 (2^42 mod p)   (|t| < 2^24: exact),
+//   q = the integer nearest t (1/p)_FP32   (within 1/193 of t / p: one rounding of 1.5 2^23 + t/p),
+//   r = t - q p   (exact; |r| < p/2 + 2, r = A^ mod p), one step of p into [lo, hi],
+// and the fp16 code of 1536 + r is the low half of the FP32 bits of (1.5 2^23 + 0x6600) + r.
 template <int NE>
 __device__ __forceinline__ void write_residues(const double (&x)[NE], bool valid_row, int e, const CrtConsts& c,
                                                __half* __restrict__ planes, int64_t plane, int64_t off,
                                                int N, int bits) {
-    uint32_t a0[NE], a1[NE], a2[NE];
-    bool neg[NE];
+    float a[NE][4];
 #pragma unroll
     for (int i = 0; i < NE; ++i) {
         unsigned long long fh, fl;
         uint32_t sg;
         fraction128(x[i], valid_row, e, &fh, &fl, &sg);
-        const unsigned long long A = fh >> (64 - bits);
-        a0[i] = static_cast<uint32_t>(A & 0xFFFFu);
-        a1[i] = static_cast<uint32_t>((A >> 16) & 0xFFFFu);
-        a2[i] = static_cast<uint32_t>(A >> 32);
-        neg[i] = sg != 0;
+        const unsigned long long A = fh >> (64 - bits);  // < 2^56
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            // 2^23 + piece is an FP32 integer with the piece in its low bits; subtracting 2^23 is exact
+            const float v = __uint_as_float(0x4B000000u | static_cast<uint32_t>((A >> (14 * j)) & 0x3FFFu)) - 8388608.0f;
+            a[i][j] = sg ? -v : v;
+        }
     }
     for (int l = 0; l < N; ++l) {
-        const uint32_t pl = c.p[l], mg = c.magic[l], k16 = c.c16[l], k32 = c.c32[l];
-        const int hi = static_cast<int>((pl - 1) / 2), lo = -static_cast<int>(pl / 2);
+        const float k1 = c.kf[l][0], k2 = c.kf[l][1], k3 = c.kf[l][2];
+        const float pf = c.pf[l], inv = c.invf[l], lo = c.lof[l], hi = c.hif[l];
         uint32_t h[NE];
 #pragma unroll
         for (int i = 0; i < NE; ++i) {
-            const uint32_t t = a2[i] * k32 + a1[i] * k16 + a0[i];  // < 2^32 for bits <= 56
-            const uint32_t q = __umulhi(t, mg);                    // floor(t / p) or one more
-            const int r = static_cast<int>(t - q * pl);            // in [-p, p), r = t mod p
-            // the signed residue in (-p, p], then one step of p into [lo, hi] (no step to [0, p) first)
-            int v = neg[i] ? -r : r;
-            if (v > hi) v -= static_cast<int>(pl);
-            else if (v < lo) v += static_cast<int>(pl);
-            // fp16 bits of 1536 + v: in [1024, 2048) the fp16 integers are consecutive codes
-            h[i] = static_cast<uint32_t>(0x6600 + v);
+            const float t = fmaf(a[i][3], k3, fmaf(a[i][2], k2, fmaf(a[i][1], k1, a[i][0])));
+            const float q = fmaf(t, inv, 12582912.0f) - 12582912.0f;
+            float r = fmaf(-q, pf, t);
+            r = r > hi ? r - pf : (r < lo ? r + pf : r);
+            // fp16 bits of 1536 + r: in [1024, 2048) the fp16 integers are consecutive codes
+            h[i] = __float_as_uint(r + 12609024.0f) & 0xFFFFu;
         }
         uint32_t w[NE / 2];
         const __half2 bias = __half2half2(__ushort_as_half(0x6600));  // 1536

@@ -93,6 +93,10 @@ struct CrtConsts {                 // residue split and slice-product epilogue
     uint32_t magic[kCrtMaxModuli]; // floor(2^32 / p) + 1: exact quotients of a < 2^26
     uint32_t c16[kCrtMaxModuli];   // 2^16 mod p
     uint32_t c32[kCrtMaxModuli];   // 2^32 mod p
+    // the residue split's FP32 arithmetic: 2^14, 2^28, 2^42 mod p; p; 1 / p rounded to FP32; the
+    // centred range [lo, hi] = [-floor(p / 2), floor((p - 1) / 2)]
+    float kf[kCrtMaxModuli][3];
+    float pf[kCrtMaxModuli], invf[kCrtMaxModuli], lof[kCrtMaxModuli], hif[kCrtMaxModuli];
 };
 struct CrtRecon {                  // reconstruction
     int N, bits;
