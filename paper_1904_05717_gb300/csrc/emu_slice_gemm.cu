@@ -79,6 +79,18 @@ struct Cfg {
     static_assert(STAGE % 1024 == 0, "stage bases stay 1024-byte aligned for the 128-B swizzle");
 };
 
+// The residue product of short k with each CTA's A tile kept in shared memory (AK): units of
+// one modulus walk along a tile row, so consecutive units of a CTA share their A tile; it is
+// loaded once per (modulus, tile row) into a region of AK_SLABS slabs, and only B streams
+// through the ring (24 KB stages instead of 40).
+constexpr int AK_SLABS = 4;                               // k <= 256
+constexpr uint32_t AK_REGION = AK_SLABS * A_TILE;         // 64 KB
+constexpr uint32_t AK_STAGE = kEmuBNMax * BK * 2;         // 24 KB: one B slab
+constexpr int AK_STAGES = 6;
+constexpr size_t AK_SMEM_BYTES = 1024 + AK_REGION + static_cast<size_t>(AK_STAGES) * AK_STAGE + 256 + 5 * kEmuBNMax;
+static_assert(AK_SMEM_BYTES <= SMEM_BUDGET + 1024, "kept-A residue product fits one CTA's shared memory");
+static_assert(AK_STAGE % 1024 == 0 && AK_REGION % 1024 == 0, "1024-byte aligned slabs for the 128-B swizzle");
+
 // The per-problem quantities every role needs for one tile.
 struct Prob {
     int m, n;
@@ -154,6 +166,11 @@ struct Params {
     // launch-invariant divisors of tile_of, as multiply-high divisions -- every warp role decodes
     // every unit, and 64-bit division routines cost those warps microseconds per small-k unit.
     int u32dec;
+    // Kept-A order (akeep): CTA b takes the tiles [floor(b T / C), floor((b + 1) T / C)) of every
+    // modulus in turn, row-major (T tiles, C CTAs); fd_ctas divides by C, fd_len and fd_len1 by the
+    // two strip lengths floor(T / C) and floor(T / C) + 1.
+    int akeep;
+    FastDiv fd_ctas, fd_len, fd_len1;
     FastDiv fd_n[17];         // moduli counts 1..16 (the count may come from the device plan)
     FastDiv fd_gt, fd_gt_last;  // group_tiles, and the tiles of the last (partial) group
     TileDiv tdv;              // the member order's divisors
@@ -203,6 +220,24 @@ MOMMS_DEV bool tile_of(const Params& p, int it, int* prob, int* tm, int* tn, int
         // modulus by modulus.  A wave covers one modulus of a block of tiles (the L2 footprint of a
         // digit pair), only the last round is partial, and with group_tiles = the grid a full
         // group keeps every modulus of a tile on one CTA.
+        if (p.akeep) {  // kept-A order: this CTA's strip of tiles, modulus after modulus
+            const uint32_t tiles = static_cast<uint32_t>(p.tiles_m) * static_cast<uint32_t>(p.tiles_n);
+            const int N = one_S(p);
+            const uint32_t start = fdiv(blockIdx.x * tiles, p.fd_ctas);
+            const uint32_t len = fdiv((blockIdx.x + 1) * tiles, p.fd_ctas) - start;
+            if (N < 1 || N > 16 || len == 0) return false;
+            const FastDiv& fl = len == p.fd_len.d ? p.fd_len : p.fd_len1;  // the strip's length
+            const uint32_t l = fdiv(static_cast<uint32_t>(it), fl);
+            if (l >= static_cast<uint32_t>(N)) return false;
+            const uint32_t t = start + (static_cast<uint32_t>(it) - l * fl.d);
+            const uint32_t q = fdiv(t, p.tdv.tn);
+            *prob = -1;
+            *lmod = static_cast<int>(l);
+            *tm = static_cast<int>(q);
+            *tn = static_cast<int>(t - q * p.tdv.tn.d);
+            if (tile) *tile = t;
+            return true;
+        }
         if (p.u32dec && !p.tri) {  // the same order in 32-bit arithmetic
             const uint32_t tiles = static_cast<uint32_t>(p.tiles_m) * static_cast<uint32_t>(p.tiles_n);
             const int N = one_S(p);
@@ -761,7 +796,17 @@ MOMMS_DEV void stage_columns(const Params& p, int prob, int tn, int beta, int* c
 // `remote_empty` (CTA pairs): the shared::cluster address of the pair leader's acc_empty[0], on
 // which the peer's warps arrive instead of their own (0: this CTA's acc_empty).
 // Returns false if a bounded wait gave up.
-template <int CR, int CT>
+// FP32 accumulator value x (an exact integer) as int32.  SMALL (|x| < 2^22, e.g. residue products
+// of k <= 256: |x| <= 256 127^2): 1.5 2^23 + x lies in [2^23, 2^24), where FP32 holds every
+// integer, so its bits minus those of 1.5 2^23 are x -- an FP32 add and an integer add instead of a
+// float-to-int conversion, whose pipe takes 16 lanes per clock per SM.
+template <bool SMALL>
+MOMMS_DEV int32_t acc_int(uint32_t bits) {
+    if constexpr (SMALL) return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
+    else return __float2int_rn(__uint_as_float(bits));
+}
+
+template <int CR, int CT, bool SMALL = false>
 MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, uint64_t* acc_empty, uint32_t& abuf,
                               uint32_t (&aphase)[2], volatile int* abort_flag, uint32_t tacc, uint32_t tsum,
                               int lane, int32_t (&acc)[CR], uint32_t remote_empty = 0, bool remote_full = false) {
@@ -781,7 +826,7 @@ MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, ui
             tmem_ld_32x32b_x16(taddr + q * 16, r);
             tmem_ld_wait(r);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[q * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
+            for (int j = 0; j < 16; ++j) acc[q * 16 + j] += acc_int<SMALL>(r[j]);
         }
 #pragma unroll
         for (int q = 0; q < CT / 16; ++q) {
@@ -791,13 +836,13 @@ MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, ui
             uint32_t t[16];
             if (first) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) t[j] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[j])));
+                for (int j = 0; j < 16; ++j) t[j] = static_cast<uint32_t>(acc_int<SMALL>(r[j]));
             } else {
                 tmem_ld_32x32b_x16(tsum + q * 16, t);
                 tmem_ld_wait(t);
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
-                    t[j] = static_cast<uint32_t>(static_cast<int32_t>(t[j]) + __float2int_rn(__uint_as_float(r[j])));
+                    t[j] = static_cast<uint32_t>(static_cast<int32_t>(t[j]) + acc_int<SMALL>(r[j]));
             }
             tmem_st_32x32b_x16(tsum + q * 16, t);
         }
@@ -910,27 +955,36 @@ __global__ void __launch_bounds__(256) tail_fixup_kernel(const __grid_constant__
 
 // MOD: the modular encoding -- a unit is one modulus l of one tile (p.one.S moduli), one pair
 // (residue plane l of A, plane l of B), and its epilogue stores residues instead of recombining.
-template <int BN, bool TAIL, bool MOD = false>
+// AK: the kept-A residue product (MOD, BN = kEmuBNMax, k <= AK_SLABS slabs): the A region holds
+// the unit's A slabs, loaded once per (modulus, tile row) of the CTA's strip (a_full / a_empty),
+// and the ring stages hold B slabs only.
+template <int BN, bool TAIL, bool MOD = false, bool AK = false>
 __global__ void __launch_bounds__(THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, const __grid_constant__ Params p) {
     using C_ = Cfg<BN>;
-    constexpr int STAGES = C_::STAGES;
-    constexpr uint32_t STAGE = C_::STAGE;
+    static_assert(!AK || (MOD && !TAIL && BN == kEmuBNMax), "kept A: residue products of wide tiles");
+    constexpr int STAGES = AK ? AK_STAGES : C_::STAGES;
+    constexpr uint32_t STAGE = AK ? AK_STAGE : C_::STAGE;
+    constexpr uint32_t RING = AK ? AK_REGION : 0;   // the ring's offset (the A region before it)
+    constexpr uint32_t B_OFF = AK ? 0 : A_TILE;     // B slab inside a stage
     constexpr int CW = C_::CW;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+    uint8_t* ring = smem + RING;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + STAGES * STAGE);
     uint64_t* full = bars;                        // STAGES
     uint64_t* empty = bars + STAGES;              // STAGES
     uint64_t* acc_full = bars + 2 * STAGES;       // 2
     uint64_t* acc_empty = bars + 2 * STAGES + 2;  // 2
     uint64_t* drain = bars + 2 * STAGES + 4;      // 1
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+    uint64_t* a_full = bars + 2 * STAGES + 5;     // 1 (AK)
+    uint64_t* a_empty = bars + 2 * STAGES + 6;    // 1 (AK)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 7);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* wait_ok = reinterpret_cast<volatile int*>(tmem_slot + 2);  // fused reconstruction
-    int* colexp = reinterpret_cast<int*>(smem + STAGES * STAGE + 256);   // BN column exponents
+    int* colexp = reinterpret_cast<int*>(ring + STAGES * STAGE + 256);   // BN column exponents
     uint8_t* colflag = reinterpret_cast<uint8_t*>(colexp + BN);          // BN column flags
 
     const int warp = threadIdx.x >> 5;
@@ -946,6 +1000,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&acc_empty[i], EPI_WARPS);
         }
         mbar_init(drain, 1);
+        mbar_init(a_full, 1);
+        mbar_init(a_empty, 1);
         *abort_flag = 0;
         fence_mbarrier_init();
     }
@@ -970,6 +1026,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int i = 0; i < STAGES; ++i) last_phase[i] = -1;
             bool ok = true;
             bool withhold = p.withhold != 0 && blockIdx.x == 0;
+            int ag = -1, a_lm = -1, a_tm = -1;  // AK: group of units sharing the A region
+            int a_armed = -1;                   // AK: the last group whose A loads were issued
             for (int it = 0; ok; ++it) {
                 int tm, tn, prob, part, lm = 0;
                 if (!tile_of<TAIL, MOD>(p, it, &prob, &tm, &tn, &part, &lm)) break;
@@ -977,6 +1035,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if constexpr (MOD) apply_kcap<BN>(p, tm, tn, pr);
                 const CUtensorMap* mapA = prob < 0 ? &tmA : &p.table[prob].mapA;
                 const CUtensorMap* mapB = prob < 0 ? &tmB : &p.table[prob].mapB;
+                if constexpr (AK) {
+                    if (lm != a_lm || tm != a_tm) {
+                        // a new (modulus, tile row): once the MMAs of the last group are done with the
+                        // region, load this unit's A slabs into it
+                        ++ag;
+                        if (!mbar_wait(a_empty, static_cast<uint32_t>(ag & 1) ^ 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(a_full, static_cast<uint32_t>(pr.nslab) * A_TILE);
+                        for (int j = 0; j < pr.nslab; ++j)
+                            tma_load_3d(smem + j * A_TILE, mapA, a_full, (pr.slab0 + j) * BK, tm * BM, lm);
+                        a_armed = ag;
+                        a_lm = lm;
+                        a_tm = tm;
+                    }
+                }
 
                 for (int d = MOD ? 2 : pr.S + 1; d >= 2 && ok; --d) {
                     const int npairs = MOD ? 1 : d - 1;
@@ -988,15 +1063,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 ok = false;
                                 break;
                             }
-                            uint8_t* sa = smem + stage * STAGE;
+                            uint8_t* sa = ring + stage * STAGE;
                             mbar_arrive_expect_tx(&full[stage], STAGE);
                             const int x = (pr.slab0 + j) * BK;
                             // A slice s rows [tm*BM, +BM), B slice d-s rows [tn*BN, +BN) (MOD: the
                             // residue planes of one modulus); rows past the end of a plane are
-                            // zero-filled by the copy engine
+                            // zero-filled by the copy engine (AK: B only, A is in its region)
                             if (!withhold) {
-                                tma_load_3d(sa, mapA, &full[stage], x, tm * BM, plane_a);
-                                tma_load_3d(sa + A_TILE, mapB, &full[stage], x, tn * BN, plane_b);
+                                if constexpr (!AK) tma_load_3d(sa, mapA, &full[stage], x, tm * BM, plane_a);
+                                tma_load_3d(sa + B_OFF, mapB, &full[stage], x, tn * BN, plane_b);
                             }
                             withhold = false;  // (test hook: only the first stage stays empty)
                             last_phase[stage] = static_cast<int>(phase);
@@ -1012,6 +1087,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 // let every issued copy land before the CTA's shared memory goes away
                 for (int i = 0; i < STAGES; ++i)
                     if (last_phase[i] >= 0) mbar_wait_drain(&full[i], static_cast<uint32_t>(last_phase[i]));
+                // (AK: and the A loads of the last group that issued any)
+                if (AK && a_armed >= 0) mbar_wait_drain(a_full, static_cast<uint32_t>(a_armed & 1));
             }
         }
     } else if (warp == 1) {
@@ -1022,11 +1099,26 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t aphase[2] = {0u, 0u};
             bool ok = true;
             bool issued = false;
+            int ag = -1, a_lm = -1, a_tm = -1;  // AK: as the producer's
             for (int it = 0; ok; ++it) {
                 int tm, tn, prob, part, lm = 0;
                 if (!tile_of<TAIL, MOD>(p, it, &prob, &tm, &tn, &part, &lm)) break;
                 TileInts pr = tile_ints(p, prob, part);
                 if constexpr (MOD) apply_kcap<BN>(p, tm, tn, pr);
+                if constexpr (AK) {
+                    if (lm != a_lm || tm != a_tm) {
+                        ++ag;
+                        // the A region goes back to the producer once every MMA issued so far is done
+                        if (ag > 0) umma_commit(a_empty);
+                        if (!mbar_wait(a_full, static_cast<uint32_t>(ag & 1), abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        a_lm = lm;
+                        a_tm = tm;
+                    }
+                }
                 for (int d = MOD ? 2 : pr.S + 1; d >= 2 && ok; --d) {
                     const int units = (MOD ? 1 : d - 1) * pr.nslab;
                     for (int u = 0; u < units && ok;) {
@@ -1043,9 +1135,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 break;
                             }
                             tc_fence_after();
-                            const uint32_t sa = smem_u32(smem + stage * STAGE);
-                            const uint64_t da = smem_desc_k_sw128(sa);
-                            const uint64_t db = smem_desc_k_sw128(sa + A_TILE);
+                            const uint32_t sa = smem_u32(ring + stage * STAGE);
+                            const uint64_t da = smem_desc_k_sw128(AK ? smem_u32(smem + (u + c) * A_TILE) : sa);
+                            const uint64_t db = smem_desc_k_sw128(sa + B_OFF);
 #pragma unroll
                             for (int kk = 0; kk < BK / 16; ++kk)
                                 umma_f16_ss(dt, da + 2ull * kk, db + 2ull * kk, C_::IDESC,
@@ -1115,9 +1207,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 for (int d = MOD ? 2 : pr.S + 1; d >= 2; --d) {
                     int32_t acc[CR];
-                    if (!drain_diagonal<CR, CT>((MOD ? 1 : d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty,
-                                                abuf, aphase, abort_flag, tmem_base + lane_off + third * CW, tsum,
-                                                lane, acc)) {
+                    // (AK: k <= 256, every residue-product sum below 2^22 in magnitude)
+                    if (!drain_diagonal<CR, CT, AK>((MOD ? 1 : d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty,
+                                                    abuf, aphase, abort_flag, tmem_base + lane_off + third * CW, tsum,
+                                                    lane, acc)) {
                         ok = false;
                         break;
                     }
@@ -1654,9 +1747,35 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
                 cfg.numAttrs = 1;
                 e = cudaLaunchKernelEx(&cfg, residue_pair_kernel, mapA, mapBh, p);
             } else {
-                slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(
-                    mapA, mapB, p);
-                e = cudaGetLastError();
+                bool kept = false;
+                if constexpr (BN == kEmuBNMax) {
+                    if (!a.crt_fuse && !a.tri && !a.kcap && p.u32dec && p.one.nslab <= AK_SLABS && tiles >= ctas &&
+                        ctas * tiles < (int64_t(1) << 32)) {
+                        // short k: the kept-A order and kernel (each CTA loads its A tile once per tile
+                        // row of its strip and modulus)
+                        static PerDeviceFlag ak_attr;
+                        if (!ak_attr.done()) {
+                            e = cudaFuncSetAttribute(slice_gemm_kernel<BN, false, true, true>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     static_cast<int>(AK_SMEM_BYTES));
+                            if (e != cudaSuccess) return e;
+                            ak_attr.mark();
+                        }
+                        p.akeep = 1;
+                        p.fd_ctas = make_fastdiv(static_cast<uint32_t>(ctas));
+                        p.fd_len = make_fastdiv(static_cast<uint32_t>(tiles / ctas));
+                        p.fd_len1 = make_fastdiv(static_cast<uint32_t>(tiles / ctas + 1));
+                        slice_gemm_kernel<BN, false, true, true>
+                            <<<static_cast<unsigned>(ctas), THREADS, AK_SMEM_BYTES, stream>>>(mapA, mapB, p);
+                        e = cudaGetLastError();
+                        kept = true;
+                    }
+                }
+                if (!kept) {
+                    slice_gemm_kernel<BN, false, true><<<static_cast<unsigned>(ctas), THREADS, C_::SMEM_BYTES, stream>>>(
+                        mapA, mapB, p);
+                    e = cudaGetLastError();
+                }
             }
             if (e != cudaSuccess) return e;
             ++nlaunch;

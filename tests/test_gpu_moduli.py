@@ -399,3 +399,41 @@ def test_modular_odd_leading_dimension_bitwise():
     Co, _ = oracle.modular_dgemm(A, B, 42, C0.copy(order="F"), 1.0, 1.0)
     assert np.array_equal(dC.to_numpy(), Co)
     assert np.all(np.isnan(dC.padding_numpy()))          # the row of padding is never written
+
+
+@pytest.mark.parametrize("m,n,k,opa,opb", [(300, 500, 130, 0, 0), (260, 620, 64, 1, 0), (390, 400, 256, 0, 1),
+                                           (200, 900, 200, 1, 1)])
+def test_kept_a_short_k_bitwise(m, n, k, opa, opb):
+    # k <= 256: each CTA keeps its A tile in shared memory over a strip of tiles (at least as many
+    # tiles as CTAs); a grid of 5 CTAs over 6-15 tiles gives strips that end inside and at the end
+    # of a tile row, several moduli per strip; 40 CTAs (more than the tiles) take the ring kernel
+    A = syn.matrix("phi", k if opa else m, m if opa else k, 451, phi=1.0)
+    B = syn.matrix("phi", n if opb else k, k if opb else n, 452, phi=1.0)
+    C0 = syn.matrix("uniform", m, n, 453)
+    Ck, rk = modular(A, B, C0, -1.5, 0.5, 6, opa, opb, tile_n=192, ctas=5)
+    Cr, rr = modular(A, B, C0, -1.5, 0.5, 6, opa, opb, tile_n=192, ctas=40)
+    assert rk["moduli"] > 0 and rk["ctas"] == 5 and rr["ctas"] > 5
+    assert np.array_equal(Ck, Cr)
+    # rows and columns at the tile seams bit for bit against the definition of the result
+    rs = np.unique([0, 1, 127, 128, 129, min(255, m - 1), min(256, m - 1), m - 1])
+    cs = np.unique([0, 1, 191, 192, 193, min(383, n - 1), min(384, n - 1), n - 1])
+    As = np.asfortranarray(A[:, rs] if opa else A[rs, :])
+    Bs = np.asfortranarray(B[cs, :] if opb else B[:, cs])
+    Co, _ = oracle.modular_dgemm(As, Bs, 42, np.asfortranarray(C0[np.ix_(rs, cs)]), -1.5, 0.5, bool(opa), bool(opb))
+    assert np.array_equal(Ck[np.ix_(rs, cs)], Co)
+
+
+def test_kept_a_full_grid_bitwise_at_tile_seams():
+    # every SM's CTA on the kept-A kernel: 17 x 9 = 153 tiles (at least one per CTA), ragged m, n
+    # and k (4 slabs, the last partial); elements at the tile seams bit for bit against the definition
+    m, n, k = 2085, 1700, 200
+    A = syn.matrix("phi", m, k, 461, phi=1.0)
+    B = syn.matrix("phi", k, n, 462, phi=1.0)
+    C0 = syn.matrix("uniform", m, n, 463)
+    C, rep = modular(A, B, C0, 1.0, 1.0, 6, tile_n=192)
+    assert rep["moduli"] > 0
+    rs = np.unique([0, 127, 128, 1023, 1024, 2047, 2048, m - 1])
+    cs = np.unique([0, 191, 192, 767, 768, 1535, 1536, n - 1])
+    Co, _ = oracle.modular_dgemm(np.asfortranarray(A[rs, :]), np.asfortranarray(B[:, cs]), 42,
+                                 np.asfortranarray(C0[np.ix_(rs, cs)]), 1.0, 1.0)
+    assert np.array_equal(C[np.ix_(rs, cs)], Co)
