@@ -162,6 +162,8 @@ struct Params {
     uint32_t modp[kCrtMaxModuli];
     uint32_t modmagic[kCrtMaxModuli];  // floor(2^32 / p) + 1
     uint32_t modoff[kCrtMaxModuli];    // p ceil(2^31 / p): makes any int32 sum a uint32 of equal residue
+    uint32_t modmagic_up[kCrtMaxModuli];  // ceil(2^32 / p): exact floor quotients of u < 2^24
+    uint32_t modoff22[kCrtMaxModuli];     // p ceil(2^22 / p): makes a sum |x| < 2^22 a u < 2^24
     // 32-bit unit decoding (u32dec: every unit index of a single problem below 2^31): the
     // launch-invariant divisors of tile_of, as multiply-high divisions -- every warp role decodes
     // every unit, and 64-bit division routines cost those warps microseconds per small-k unit.
@@ -568,6 +570,14 @@ MOMMS_DEV uint32_t residue_of(int32_t x, uint32_t p, uint32_t magic, uint32_t of
     return static_cast<uint32_t>(r);
 }
 
+// x mod p in [0, p) for |x| < 2^22 (the residue-product sums of k <= 256): u = x + p ceil(2^22 / p)
+// lies in [0, 2^24), where the multiply-high by ceil(2^32 / p) is the exact floor of u / p (its
+// excess, below u 2^-32 < 2^-8, stays under 1/p for p < 256) -- no correction step.
+MOMMS_DEV uint32_t residue_small(int32_t x, uint32_t p, uint32_t magic_up, uint32_t off22) {
+    const uint32_t u = static_cast<uint32_t>(x) + off22;
+    return u - __umulhi(u, magic_up) * p;
+}
+
 // Four columns' bytes of one row (column c in byte c) transposed across the four lanes of each
 // group (rows 4g .. 4g + 3 of the warp): lane q of the group returns column q's bytes of the
 // group's four rows, row 4g + t in byte t.
@@ -586,12 +596,15 @@ MOMMS_DEV uint32_t transpose4x4_bytes(uint32_t w, int lane) {
 // a rank-k unit of 128 x 192 x 256 takes).  Else one byte per element (a warp's 32 rows: one
 // 32-byte sector per column).  The TMEM reads and the shuffles are warp-wide, so every lane takes
 // them before the bounds checks.
-template <int BN, int CR, int CT>
+template <int BN, int CR, int CT, bool SMALL = false>
 MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, int third, int rloc,
                               const int32_t (&acc)[CR], uint32_t tsum) {
     const int row = tm * BM + rloc;
     const int col0 = tn * BN + third * (BN / 3);
-    const uint32_t pl = p.modp[l], mg = p.modmagic[l], off = p.modoff[l];
+    // SMALL: every sum below 2^22 in magnitude (k <= 256), the exact-floor residue
+    const uint32_t pl = p.modp[l], mg = SMALL ? p.modmagic_up[l] : p.modmagic[l],
+                   off = SMALL ? p.modoff22[l] : p.modoff[l];
+    auto residue = [&](int32_t v) { return SMALL ? residue_small(v, pl, mg, off) : residue_of(v, pl, mg, off); };
     const int m = prob < 0 ? p.one.m : p.table[prob].m;
     const int n = prob < 0 ? p.one.n : p.table[prob].n;
     uint8_t* res = prob < 0 ? p.res : p.table[prob].res;
@@ -605,9 +618,9 @@ MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, 
         const int cq = lane & 3;
 #pragma unroll
         for (int c = 0; c < CR; c += 4) {
-            const uint32_t w = residue_of(acc[c], pl, mg, off) | (residue_of(acc[c + 1], pl, mg, off) << 8) |
-                               (residue_of(acc[c + 2], pl, mg, off) << 16) |
-                               (residue_of(acc[c + 3], pl, mg, off) << 24);
+            const uint32_t w = residue(acc[c]) | (residue(acc[c + 1]) << 8) |
+                               (residue(acc[c + 2]) << 16) |
+                               (residue(acc[c + 3]) << 24);
             const uint32_t x = transpose4x4_bytes(w, lane);
             if (row_ok && c + cq < ncols) *reinterpret_cast<uint32_t*>(base + (c + cq) * cstep) = x;
         }
@@ -619,10 +632,10 @@ MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, 
 #pragma unroll
             for (int j = 0; j < 16; j += 4) {
                 const int c = CR + q * 16 + j;
-                const uint32_t w = residue_of(static_cast<int32_t>(t[j]), pl, mg, off) |
-                                   (residue_of(static_cast<int32_t>(t[j + 1]), pl, mg, off) << 8) |
-                                   (residue_of(static_cast<int32_t>(t[j + 2]), pl, mg, off) << 16) |
-                                   (residue_of(static_cast<int32_t>(t[j + 3]), pl, mg, off) << 24);
+                const uint32_t w = residue(static_cast<int32_t>(t[j])) |
+                                   (residue(static_cast<int32_t>(t[j + 1])) << 8) |
+                                   (residue(static_cast<int32_t>(t[j + 2])) << 16) |
+                                   (residue(static_cast<int32_t>(t[j + 3])) << 24);
                 const uint32_t x = transpose4x4_bytes(w, lane);
                 if (row_ok && c + cq < ncols) *reinterpret_cast<uint32_t*>(base + (c + cq) * cstep) = x;
             }
@@ -632,7 +645,7 @@ MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, 
     uint8_t* dst = res + static_cast<size_t>(l) * m * n + static_cast<size_t>(col0) * m + row;
 #pragma unroll
     for (int c = 0; c < CR; ++c) {
-        const uint32_t r = residue_of(acc[c], pl, mg, off);
+        const uint32_t r = residue(acc[c]);
         if (row_ok && c < ncols) dst[c * cstep] = static_cast<uint8_t>(r);
     }
 #pragma unroll
@@ -643,7 +656,7 @@ MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, 
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int c = CR + q * 16 + j;
-            const uint32_t r = residue_of(static_cast<int32_t>(t[j]), pl, mg, off);
+            const uint32_t r = residue(static_cast<int32_t>(t[j]));
             if (row_ok && c < ncols) dst[c * cstep] = static_cast<uint8_t>(r);
         }
     }
@@ -1216,7 +1229,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     if constexpr (MOD) {
                         if (!final_unit) {
-                            store_residues<BN, CR, CT>(p, prob, tm, tn, lm, third, rloc, acc, tsum);
+                            store_residues<BN, CR, CT, AK>(p, prob, tm, tn, lm, third, rloc, acc, tsum);
                             if (p.crt_fused) signal_tile(p, tile);
                         } else if (wait_tile(p, tile, pr.S - 1, abort_flag, wait_ok)) {
                             if (p.crt_L == 3)
@@ -1681,6 +1694,8 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
                 p.modp[l] = pl;
                 p.modmagic[l] = a.crt->magic[l];
                 p.modoff[l] = static_cast<uint32_t>(pl * (((1ull << 31) + pl - 1) / pl));
+                p.modmagic_up[l] = static_cast<uint32_t>(((1ull << 32) + pl - 1) / pl);
+                p.modoff22[l] = static_cast<uint32_t>(pl * (((1ull << 22) + pl - 1) / pl));
             }
             if (a.tri) {
                 p.tri = a.tri;
