@@ -581,11 +581,19 @@ MOMMS_DEV uint32_t residue_small(int32_t x, uint32_t p, uint32_t magic_up, uint3
 // Four columns' bytes of one row (column c in byte c) transposed across the four lanes of each
 // group (rows 4g .. 4g + 3 of the warp): lane q of the group returns column q's bytes of the
 // group's four rows, row 4g + t in byte t.
-MOMMS_DEV uint32_t transpose4x4_bytes(uint32_t w, int lane) {
+// The two byte-permute selectors of a lane (one per exchange step), taken once per call site:
+// each step is then one shuffle and one permute with a register selector.
+struct Transpose4Sel {
+    uint32_t s1, s2;
+};
+MOMMS_DEV Transpose4Sel transpose4_sel(int lane) {
+    return Transpose4Sel{(lane & 1) ? 0x3715u : 0x6240u, (lane & 2) ? 0x3276u : 0x5410u};
+}
+MOMMS_DEV uint32_t transpose4x4_bytes(uint32_t w, const Transpose4Sel& sel) {
     const uint32_t o1 = __shfl_xor_sync(0xffffffffu, w, 1);
-    const uint32_t t1 = (lane & 1) ? __byte_perm(w, o1, 0x3715) : __byte_perm(w, o1, 0x6240);
+    const uint32_t t1 = __byte_perm(w, o1, sel.s1);
     const uint32_t o2 = __shfl_xor_sync(0xffffffffu, t1, 2);
-    return (lane & 2) ? __byte_perm(t1, o2, 0x3276) : __byte_perm(t1, o2, 0x5410);
+    return __byte_perm(t1, o2, sel.s2);
 }
 
 // The modular epilogue of modulus l: the thread's int32 sums (CR in `acc`, CT in TMEM at
@@ -616,12 +624,13 @@ MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, 
         // word store: lane 4g + q writes column 4j + q of rows 4g .. 4g + 3 (all inside m or none)
         uint8_t* base = res + static_cast<size_t>(l) * m * n + static_cast<size_t>(col0) * m + (row & ~3);
         const int cq = lane & 3;
+        const Transpose4Sel tsel = transpose4_sel(lane);
 #pragma unroll
         for (int c = 0; c < CR; c += 4) {
             const uint32_t w = residue(acc[c]) | (residue(acc[c + 1]) << 8) |
                                (residue(acc[c + 2]) << 16) |
                                (residue(acc[c + 3]) << 24);
-            const uint32_t x = transpose4x4_bytes(w, lane);
+            const uint32_t x = transpose4x4_bytes(w, tsel);
             if (row_ok && c + cq < ncols) *reinterpret_cast<uint32_t*>(base + (c + cq) * cstep) = x;
         }
 #pragma unroll
@@ -636,7 +645,7 @@ MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, 
                                    (residue(static_cast<int32_t>(t[j + 1])) << 8) |
                                    (residue(static_cast<int32_t>(t[j + 2])) << 16) |
                                    (residue(static_cast<int32_t>(t[j + 3])) << 24);
-                const uint32_t x = transpose4x4_bytes(w, lane);
+                const uint32_t x = transpose4x4_bytes(w, tsel);
                 if (row_ok && c + cq < ncols) *reinterpret_cast<uint32_t*>(base + (c + cq) * cstep) = x;
             }
         }
