@@ -883,6 +883,64 @@ MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, ui
     return true;
 }
 
+// The kept-A kernel's unit (one chunk: every k <= 256 sum is an FP32 integer below 2^22 in
+// magnitude) from the accumulator straight to its residues: 16 of the thread's columns per
+// tensor-memory load, the next load in flight while the current 16 are reduced (exact floors,
+// residue_small, on 1.5 2^23 + x), packed, transposed across each group of four lanes and stored
+// four rows to a word.  The accumulator goes back to the MMA thread once its last load has landed
+// (no int32 sums staged in tensor memory, one exposed load latency per unit).  Requires m % 4 == 0.
+template <int BN>
+MOMMS_DEV bool drain_store_small(const Params& p, int tm, int tn, int l, int third, int rloc, int lane,
+                                 uint64_t* acc_full, uint64_t* acc_empty, uint32_t& abuf, uint32_t (&aphase)[2],
+                                 volatile int* abort_flag, uint32_t tacc) {
+    constexpr int CW = BN / 3;
+    constexpr int G = CW / 16;
+    if (!mbar_wait(&acc_full[abuf], aphase[abuf], abort_flag)) return false;
+    tc_fence_after();
+    const uint32_t taddr = tacc + abuf * 256u;
+    const int row = tm * BM + rloc;
+    const int col0 = tn * BN + third * CW;
+    const int m = p.one.m, n = p.one.n;
+    const uint32_t pl = p.modp[l], mg = p.modmagic_up[l];
+    const uint32_t off = p.modoff22[l] - 0x4B400000u;  // bits of 1.5 2^23 + x, plus off: x + p ceil(2^22 / p)
+    const bool row_ok = row < m;
+    const size_t cstep = static_cast<size_t>(m);
+    const int ncols = min(CW, n - col0);
+    uint8_t* base = p.res + static_cast<size_t>(l) * m * n + static_cast<size_t>(col0) * m + (row & ~3);
+    const int cq = lane & 3;
+    const Transpose4Sel tsel = transpose4_sel(lane);
+    uint32_t r[2][16];
+    tmem_ld_32x32b_x16(taddr, r[0]);
+    tmem_ld_wait(r[0]);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (g + 1 < G) tmem_ld_32x32b_x16(taddr + (g + 1) * 16, r[(g + 1) & 1]);
+#pragma unroll
+        for (int c = 0; c < 16; c += 4) {
+            uint32_t w = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t u = __float_as_uint(__uint_as_float(r[g & 1][c + j]) + 12582912.0f) + off;
+                w |= (u - __umulhi(u, mg) * pl) << (8 * j);
+            }
+            const uint32_t x = transpose4x4_bytes(w, tsel);
+            const int cc = g * 16 + c + cq;
+            if (row_ok && cc < ncols) *reinterpret_cast<uint32_t*>(base + cc * cstep) = x;
+        }
+        if (g + 1 < G) {
+            tmem_ld_wait(r[(g + 1) & 1]);
+            if (g + 2 == G) {  // every load has landed: the accumulator is free
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[abuf]);
+            }
+        }
+    }
+    aphase[abuf] ^= 1u;
+    abuf ^= 1u;
+    return true;
+}
+
 // A drain warp's share of a k part of a split tail tile (always the CTA's last unit): drain
 // every diagonal and store its int32 sums for the fix-up launch (tail_fixup_kernel), which
 // adds the parts and recombines once all of them are done.
@@ -1227,31 +1285,39 @@ __global__ void __launch_bounds__(THREADS, 1)
                     stage_columns<BN>(p, prob, tn, p.crt_bits, colexp, colflag);
                     prefetch_residues<BN>(p, tm, tn, lm, third, quad, lane);
                 }
-                for (int d = MOD ? 2 : pr.S + 1; d >= 2; --d) {
-                    int32_t acc[CR];
-                    // (AK: k <= 256, every residue-product sum below 2^22 in magnitude)
-                    if (!drain_diagonal<CR, CT, AK>((MOD ? 1 : d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty,
-                                                    abuf, aphase, abort_flag, tmem_base + lane_off + third * CW, tsum,
-                                                    lane, acc)) {
+                if constexpr (AK) {
+                    if (!drain_store_small<BN>(p, tm, tn, lm, third, rloc, lane, acc_full, acc_empty, abuf, aphase,
+                                               abort_flag, tmem_base + lane_off + third * CW)) {
                         ok = false;
                         break;
                     }
-                    if constexpr (MOD) {
-                        if (!final_unit) {
-                            store_residues<BN, CR, CT, AK>(p, prob, tm, tn, lm, third, rloc, acc, tsum);
-                            if (p.crt_fused) signal_tile(p, tile);
-                        } else if (wait_tile(p, tile, pr.S - 1, abort_flag, wait_ok)) {
-                            if (p.crt_L == 3)
-                                crt_final<BN, CR, CT, 3>(p, tm, tn, lm, third, rloc, acc, tsum, colexp, colflag);
-                            else
-                                crt_final<BN, CR, CT, 4>(p, tm, tn, lm, third, rloc, acc, tsum, colexp, colflag);
-                        } else {
+                } else {
+                    for (int d = MOD ? 2 : pr.S + 1; d >= 2; --d) {
+                        int32_t acc[CR];
+                        // (AK: k <= 256, every residue-product sum below 2^22 in magnitude)
+                        if (!drain_diagonal<CR, CT, AK>((MOD ? 1 : d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty,
+                                                        abuf, aphase, abort_flag, tmem_base + lane_off + third * CW, tsum,
+                                                        lane, acc)) {
                             ok = false;
                             break;
                         }
-                    } else
-                        recombine_diagonal<BN, CR, CT>(p, prob, tm, tn, d, pr, Q, R, keep, tsum, rb, third, rloc,
-                                                       colexp, colflag, qnan, acc, gj, rfirst);
+                        if constexpr (MOD) {
+                            if (!final_unit) {
+                                store_residues<BN, CR, CT, AK>(p, prob, tm, tn, lm, third, rloc, acc, tsum);
+                                if (p.crt_fused) signal_tile(p, tile);
+                            } else if (wait_tile(p, tile, pr.S - 1, abort_flag, wait_ok)) {
+                                if (p.crt_L == 3)
+                                    crt_final<BN, CR, CT, 3>(p, tm, tn, lm, third, rloc, acc, tsum, colexp, colflag);
+                                else
+                                    crt_final<BN, CR, CT, 4>(p, tm, tn, lm, third, rloc, acc, tsum, colexp, colflag);
+                            } else {
+                                ok = false;
+                                break;
+                            }
+                        } else
+                            recombine_diagonal<BN, CR, CT>(p, prob, tm, tn, d, pr, Q, R, keep, tsum, rb, third, rloc,
+                                                           colexp, colflag, qnan, acc, gj, rfirst);
+                    }
                 }
             }
         }
@@ -1773,7 +1839,9 @@ static cudaError_t launch_bn(const EmuGemmArgs& a, int* passes, cudaStream_t str
             } else {
                 bool kept = false;
                 if constexpr (BN == kEmuBNMax) {
+                    // (the fused drain stores four rows to a word: m a multiple of 4)
                     if (!a.crt_fuse && !a.tri && !a.kcap && p.u32dec && p.one.nslab <= AK_SLABS && tiles >= ctas &&
+                        a.m % 4 == 0 && (reinterpret_cast<uintptr_t>(a.res) & 3) == 0 &&
                         ctas * tiles < (int64_t(1) << 32)) {
                         // short k: the kept-A order and kernel (each CTA loads its A tile once per tile
                         // row of its strip and modulus)

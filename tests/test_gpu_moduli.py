@@ -401,12 +401,13 @@ def test_modular_odd_leading_dimension_bitwise():
     assert np.all(np.isnan(dC.padding_numpy()))          # the row of padding is never written
 
 
-@pytest.mark.parametrize("m,n,k,opa,opb", [(300, 500, 130, 0, 0), (260, 620, 64, 1, 0), (390, 400, 256, 0, 1),
-                                           (200, 900, 200, 1, 1)])
+@pytest.mark.parametrize("m,n,k,opa,opb", [(300, 500, 130, 0, 0), (260, 620, 64, 1, 0), (388, 400, 256, 0, 1),
+                                           (200, 900, 200, 1, 1), (390, 400, 256, 0, 0)])
 def test_kept_a_short_k_bitwise(m, n, k, opa, opb):
     # k <= 256: each CTA keeps its A tile in shared memory over a strip of tiles (at least as many
-    # tiles as CTAs); a grid of 5 CTAs over 6-15 tiles gives strips that end inside and at the end
-    # of a tile row, several moduli per strip; 40 CTAs (more than the tiles) take the ring kernel
+    # tiles as CTAs, m a multiple of 4) and stores its residues straight from the accumulator; a
+    # grid of 5 CTAs over 6-15 tiles gives strips that end inside and at the end of a tile row,
+    # several moduli per strip; 40 CTAs (more than the tiles) and m = 390 take the ring kernel
     A = syn.matrix("phi", k if opa else m, m if opa else k, 451, phi=1.0)
     B = syn.matrix("phi", n if opb else k, k if opb else n, 452, phi=1.0)
     C0 = syn.matrix("uniform", m, n, 453)
@@ -426,7 +427,7 @@ def test_kept_a_short_k_bitwise(m, n, k, opa, opb):
 def test_kept_a_full_grid_bitwise_at_tile_seams():
     # every SM's CTA on the kept-A kernel: 17 x 9 = 153 tiles (at least one per CTA), ragged m, n
     # and k (4 slabs, the last partial); elements at the tile seams bit for bit against the definition
-    m, n, k = 2085, 1700, 200
+    m, n, k = 2084, 1700, 200
     A = syn.matrix("phi", m, k, 461, phi=1.0)
     B = syn.matrix("phi", k, n, 462, phi=1.0)
     C0 = syn.matrix("uniform", m, n, 463)
