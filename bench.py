@@ -46,9 +46,9 @@ NCU_SLICE_CAPTURE = {"dram_bytes": (27.75e9 + 0.706e9 + 0.087e9) + (1.93e9 + 0.0
                      "source": "ncu DRAM counters of the 8192^3 slice-product call, scaled by tensor flops for "
                                "other sizes; taken before the kernel's current version"}
 # The same for the residue-product launch of the modular encoding (m=n=k=8192, 12 moduli): the
-# launch of a timed step of this bench (ncu dram__bytes_read.sum 9.721 GB, dram__bytes_write.sum
-# 0.801 GB; one-pass metrics, the same command run without ncu first).
-NCU_RESIDUE_CAPTURE = {"dram_bytes": 9.7207e9 + 0.8010e9,
+# launch of a timed step of this bench (ncu dram__bytes_read.sum 8.929 GB, dram__bytes_write.sum
+# 0.802 GB; one-pass metrics, the same command run without ncu first).
+NCU_RESIDUE_CAPTURE = {"dram_bytes": 8.9286e9 + 0.8018e9,
                        "tensor_flops": 12 * 2.0 * 8192 ** 3,
                        "current": True,
                        "source": "ncu DRAM counters (read + write) of the 8192^3 residue-product launch (12 moduli) "
