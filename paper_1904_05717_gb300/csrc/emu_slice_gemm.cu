@@ -570,11 +570,14 @@ MOMMS_DEV uint32_t residue_of(int32_t x, uint32_t p, uint32_t magic, uint32_t of
     return static_cast<uint32_t>(r);
 }
 
-// x mod p in [0, p) for |x| < 2^22 (the residue-product sums of k <= 256): u = x + p ceil(2^22 / p)
-// lies in [0, 2^24), where the multiply-high by ceil(2^32 / p) is the exact floor of u / p (its
-// excess, below u 2^-32 < 2^-8, stays under 1/p for p < 256) -- no correction step.
-MOMMS_DEV uint32_t residue_small(int32_t x, uint32_t p, uint32_t magic_up, uint32_t off22) {
-    const uint32_t u = static_cast<uint32_t>(x) + off22;
+// x mod p in [0, p) from the FP32 bits of an accumulator sum x, an integer with |x| < 2^22 (the
+// residue-product sums of k <= 256).  1.5 2^23 + x lies in [2^23, 2^24), where FP32 holds every
+// integer, so its bits are 0x4B400000 + x (an FP32 add instead of a float-to-int conversion,
+// whose pipe takes 16 lanes per clock per SM); off = p ceil(2^22 / p) - 0x4B400000 turns them into
+// u = x + p ceil(2^22 / p) in [0, 2^24), where the multiply-high by ceil(2^32 / p) is the exact
+// floor of u / p (its excess, below u 2^-32 < 2^-8, stays under 1/p for p < 256): no correction.
+MOMMS_DEV uint32_t residue_small_bits(uint32_t bits, uint32_t p, uint32_t magic_up, uint32_t off) {
+    const uint32_t u = __float_as_uint(__uint_as_float(bits) + 12582912.0f) + off;
     return u - __umulhi(u, magic_up) * p;
 }
 
@@ -604,15 +607,13 @@ MOMMS_DEV uint32_t transpose4x4_bytes(uint32_t w, const Transpose4Sel& sel) {
 // a rank-k unit of 128 x 192 x 256 takes).  Else one byte per element (a warp's 32 rows: one
 // 32-byte sector per column).  The TMEM reads and the shuffles are warp-wide, so every lane takes
 // them before the bounds checks.
-template <int BN, int CR, int CT, bool SMALL = false>
+template <int BN, int CR, int CT>
 MOMMS_DEV void store_residues(const Params& p, int prob, int tm, int tn, int l, int third, int rloc,
                               const int32_t (&acc)[CR], uint32_t tsum) {
     const int row = tm * BM + rloc;
     const int col0 = tn * BN + third * (BN / 3);
-    // SMALL: every sum below 2^22 in magnitude (k <= 256), the exact-floor residue
-    const uint32_t pl = p.modp[l], mg = SMALL ? p.modmagic_up[l] : p.modmagic[l],
-                   off = SMALL ? p.modoff22[l] : p.modoff[l];
-    auto residue = [&](int32_t v) { return SMALL ? residue_small(v, pl, mg, off) : residue_of(v, pl, mg, off); };
+    const uint32_t pl = p.modp[l], mg = p.modmagic[l], off = p.modoff[l];
+    auto residue = [&](int32_t v) { return residue_of(v, pl, mg, off); };
     const int m = prob < 0 ? p.one.m : p.table[prob].m;
     const int n = prob < 0 ? p.one.n : p.table[prob].n;
     uint8_t* res = prob < 0 ? p.res : p.table[prob].res;
@@ -818,17 +819,7 @@ MOMMS_DEV void stage_columns(const Params& p, int prob, int tn, int beta, int* c
 // `remote_empty` (CTA pairs): the shared::cluster address of the pair leader's acc_empty[0], on
 // which the peer's warps arrive instead of their own (0: this CTA's acc_empty).
 // Returns false if a bounded wait gave up.
-// FP32 accumulator value x (an exact integer) as int32.  SMALL (|x| < 2^22, e.g. residue products
-// of k <= 256: |x| <= 256 127^2): 1.5 2^23 + x lies in [2^23, 2^24), where FP32 holds every
-// integer, so its bits minus those of 1.5 2^23 are x -- an FP32 add and an integer add instead of a
-// float-to-int conversion, whose pipe takes 16 lanes per clock per SM.
-template <bool SMALL>
-MOMMS_DEV int32_t acc_int(uint32_t bits) {
-    if constexpr (SMALL) return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
-    else return __float2int_rn(__uint_as_float(bits));
-}
-
-template <int CR, int CT, bool SMALL = false>
+template <int CR, int CT>
 MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, uint64_t* acc_empty, uint32_t& abuf,
                               uint32_t (&aphase)[2], volatile int* abort_flag, uint32_t tacc, uint32_t tsum,
                               int lane, int32_t (&acc)[CR], uint32_t remote_empty = 0, bool remote_full = false) {
@@ -848,7 +839,7 @@ MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, ui
             tmem_ld_32x32b_x16(taddr + q * 16, r);
             tmem_ld_wait(r);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[q * 16 + j] += acc_int<SMALL>(r[j]);
+            for (int j = 0; j < 16; ++j) acc[q * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
         }
 #pragma unroll
         for (int q = 0; q < CT / 16; ++q) {
@@ -858,13 +849,13 @@ MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, ui
             uint32_t t[16];
             if (first) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) t[j] = static_cast<uint32_t>(acc_int<SMALL>(r[j]));
+                for (int j = 0; j < 16; ++j) t[j] = static_cast<uint32_t>(__float2int_rn(__uint_as_float(r[j])));
             } else {
                 tmem_ld_32x32b_x16(tsum + q * 16, t);
                 tmem_ld_wait(t);
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
-                    t[j] = static_cast<uint32_t>(static_cast<int32_t>(t[j]) + acc_int<SMALL>(r[j]));
+                    t[j] = static_cast<uint32_t>(static_cast<int32_t>(t[j]) + __float2int_rn(__uint_as_float(r[j])));
             }
             tmem_st_32x32b_x16(tsum + q * 16, t);
         }
@@ -885,8 +876,8 @@ MOMMS_DEV bool drain_diagonal(int units, int chunk_slabs, uint64_t* acc_full, ui
 
 // The kept-A kernel's unit (one chunk: every k <= 256 sum is an FP32 integer below 2^22 in
 // magnitude) from the accumulator straight to its residues: 16 of the thread's columns per
-// tensor-memory load, the next load in flight while the current 16 are reduced (exact floors,
-// residue_small, on 1.5 2^23 + x), packed, transposed across each group of four lanes and stored
+// tensor-memory load, the next load in flight while the current 16 are reduced
+// (residue_small_bits), packed, transposed across each group of four lanes and stored
 // four rows to a word.  The accumulator goes back to the MMA thread once its last load has landed
 // (no int32 sums staged in tensor memory, one exposed load latency per unit).  Requires m % 4 == 0.
 template <int BN>
@@ -902,7 +893,7 @@ MOMMS_DEV bool drain_store_small(const Params& p, int tm, int tn, int l, int thi
     const int col0 = tn * BN + third * CW;
     const int m = p.one.m, n = p.one.n;
     const uint32_t pl = p.modp[l], mg = p.modmagic_up[l];
-    const uint32_t off = p.modoff22[l] - 0x4B400000u;  // bits of 1.5 2^23 + x, plus off: x + p ceil(2^22 / p)
+    const uint32_t off = p.modoff22[l] - 0x4B400000u;  // residue_small_bits' offset
     const bool row_ok = row < m;
     const size_t cstep = static_cast<size_t>(m);
     const int ncols = min(CW, n - col0);
@@ -919,10 +910,7 @@ MOMMS_DEV bool drain_store_small(const Params& p, int tm, int tn, int l, int thi
         for (int c = 0; c < 16; c += 4) {
             uint32_t w = 0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t u = __float_as_uint(__uint_as_float(r[g & 1][c + j]) + 12582912.0f) + off;
-                w |= (u - __umulhi(u, mg) * pl) << (8 * j);
-            }
+            for (int j = 0; j < 4; ++j) w |= residue_small_bits(r[g & 1][c + j], pl, mg, off) << (8 * j);
             const uint32_t x = transpose4x4_bytes(w, tsel);
             const int cc = g * 16 + c + cq;
             if (row_ok && cc < ncols) *reinterpret_cast<uint32_t*>(base + cc * cstep) = x;
@@ -1294,16 +1282,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                 } else {
                     for (int d = MOD ? 2 : pr.S + 1; d >= 2; --d) {
                         int32_t acc[CR];
-                        // (AK: k <= 256, every residue-product sum below 2^22 in magnitude)
-                        if (!drain_diagonal<CR, CT, AK>((MOD ? 1 : d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty,
-                                                        abuf, aphase, abort_flag, tmem_base + lane_off + third * CW, tsum,
-                                                        lane, acc)) {
+                        if (!drain_diagonal<CR, CT>((MOD ? 1 : d - 1) * pr.nslab, pr.chunk_slabs, acc_full, acc_empty,
+                                                    abuf, aphase, abort_flag, tmem_base + lane_off + third * CW, tsum,
+                                                    lane, acc)) {
                             ok = false;
                             break;
                         }
                         if constexpr (MOD) {
                             if (!final_unit) {
-                                store_residues<BN, CR, CT, AK>(p, prob, tm, tn, lm, third, rloc, acc, tsum);
+                                store_residues<BN, CR, CT>(p, prob, tm, tn, lm, third, rloc, acc, tsum);
                                 if (p.crt_fused) signal_tile(p, tile);
                             } else if (wait_tile(p, tile, pr.S - 1, abort_flag, wait_ok)) {
                                 if (p.crt_L == 3)
