@@ -832,10 +832,12 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
     }
     // ---- encoding per problem: the modular one where the single-problem rule takes it (the
     // operand width of the slice rule, moduli when they save two or more products) and, in AUTO,
-    // where its per-element costs that do not shrink with k are covered: the reconstruction of one
-    // element costs about what 850 k-steps of one residue product cost (measured: 1.08 ps per
-    // element and modulus against 1.27 fs per multiply-add step on the tensor cores), so moduli
-    // are taken when N (k + 850) <= 0.9 S (S + 1) / 2 k; digit slices otherwise
+    // where its per-element costs that do not shrink with k are covered: the reconstruction and
+    // residue split of one element cost about what 650 k-steps of one residue product cost, so
+    // moduli are taken when N (k + 650) <= 0.9 S (S + 1) / 2 k; digit slices otherwise (850 when
+    // the reconstruction took 1.08 ps per element and modulus against 1.27 fs per tensor
+    // multiply-add step; on the 2000-problem workload 850 / 650 / 450 then measured 37.8 / 37.1 /
+    // 37.1 ms per call with the faster reconstruction and split)
     std::vector<char> mod(count, 0);
     std::vector<int> planes(count), mbits(count, 0);
     for (int i = 0; i < count; ++i) {
@@ -848,7 +850,7 @@ int run_emulated_batched(momms_handle_t h, const std::vector<int64_t>& idx, cons
         mod[i] = S[i] <= MOMMS_MAX_SLICES && use_moduli(sch, w, S[i], bb, k[idx[i]], &cc, &cr);
         if (mod[i] && sch == MOMMS_SCHEME_AUTO) {
             const double kk = static_cast<double>(k[idx[i]]);
-            mod[i] = cc.N * (kk + 850.0) <= 0.9 * (S[i] * (S[i] + 1) / 2) * kk;
+            mod[i] = cc.N * (kk + 650.0) <= 0.9 * (S[i] * (S[i] + 1) / 2) * kk;
         }
         if (mod[i]) {
             planes[i] = cc.N;

@@ -168,8 +168,8 @@ __global__ void plan_kernel(const int* __restrict__ spreads, const __grid_consta
 // rule of plan_kernel on its spreads and, for its width w, the fewest moduli whose product exceeds
 // 4 k (2^w - 1)^2 (exact 128-bit arithmetic, as the host's choice of moduli); moduli when the
 // problem's rule takes them (SLICES: never; MODULI: whenever they cover the width; AUTO: when they
-// save two or more products and their per-element passes are paid for, N (k + 850) <= 0.9
-// S (S + 1) / 2 k); then thread 0 lays the units of both launches out problem by problem.
+// save two or more products and their per-element passes are paid for, N (k + 650) <= 0.9
+// S (S + 1) / 2 k, as the host rule); then the units of both launches are laid out problem by problem.
 __global__ void batch_plan_kernel(const __grid_constant__ EmuBatchPlanArgs a) {
     using u128 = unsigned __int128;
     __shared__ int smax_s, nmax_s, bmax_s;
@@ -202,7 +202,7 @@ __global__ void batch_plan_kernel(const __grid_constant__ EmuBatchPlanArgs a) {
         const double kk = static_cast<double>(q.k);
         bool mod = N > 0;
         if (mod && q.scheme == 0)  // AUTO
-            mod = N + 2 <= pairs && N * (kk + 850.0) <= 0.9 * pairs * kk;
+            mod = N + 2 <= pairs && N * (kk + 650.0) <= 0.9 * pairs * kk;
         q.enc = mod ? 1 : 0;
         q.S = mod ? N : S;
         q.bits = mod ? w : 7 * S;
