@@ -84,10 +84,10 @@ typedef enum { MOMMS_MODE_AUTO = 0, MOMMS_MODE_NATIVE = 1, MOMMS_MODE_EMULATED =
  *   B2  mirror of A2: a block of columns of B stays in L2 (like B3A2C0).
  *   A1  plain row-major raster: each CTA keeps its A tile and walks n
  *       (Goto-like A2C0: the L2 level is not designed for, Sec. 4.3).
- * Residue products (modular encoding) with k <= 256, at least one tile per CTA, m a
- * multiple of 4 and no triangle take A1's order whatever the member, with the A tile
- * held in shared memory over each CTA's strip of tiles (the report keeps the member the
- * handle asked for). */
+ * Residue products (modular encoding) with k <= 256, at least one tile per CTA and m a
+ * multiple of 4 -- not SYRK's triangle, TRMM's skipped k ranges or the fused
+ * reconstruction -- take A1's order whatever the member, with the A tile held in shared
+ * memory over each CTA's strip of tiles (the report keeps the member the handle asked for). */
 typedef enum {
     MOMMS_MEMBER_AUTO = 0,
     MOMMS_MEMBER_C2 = 1,
