@@ -177,6 +177,32 @@ def emulated_l2_to_sm_bytes(m: int, n: int, k: int, S: int, bm: int = 128, bn: i
     return pairs * tiles_m * tiles_n * (bm + bn) * k_pad * 2
 
 
+def kept_a_l2_to_sm_bytes(m: int, n: int, k: int, N: int, ctas: int = 152, bm: int = 128, bn: int = 192):
+    """L2 -> SM bytes of the short-k residue product (k <= 256) with the A tile kept in shared
+    memory: CTA b takes the tiles [floor(b T / C), floor((b + 1) T / C)) row-major, modulus after
+    modulus; it loads an A tile (bm rows of the modulus's plane) when its unit's (modulus, tile
+    row) differs from the last one's, and every unit's B tile (bn rows).  The units are walked in
+    the kernel's order (`ring` = the same units with A and B per unit, the ring kernel's bytes)."""
+    tiles_m, tiles_n = cdiv(m, bm), cdiv(n, bn)
+    T = tiles_m * tiles_n
+    k_pad = cdiv(k, 64) * 64
+    a_loads = units = 0
+    for b in range(ctas):
+        start, end = (b * T) // ctas, ((b + 1) * T) // ctas
+        last = None
+        for l in range(N):
+            for t in range(start, end):
+                key = (l, t // tiles_n)
+                if key != last:
+                    a_loads += 1
+                    last = key
+                units += 1
+    a = a_loads * bm * k_pad * 2
+    bb = units * bn * k_pad * 2
+    return {"a": a, "b": bb, "total": a + bb, "a_loads": a_loads, "units": units,
+            "ring": units * (bm + bn) * k_pad * 2}
+
+
 def paper_member_intensity(name: str, M_words: int | None = None):
     """Flops per byte of the paper's CPU members at their published blocksizes (large m=n=k)."""
     L = 10 ** 7

@@ -78,3 +78,27 @@ def test_modular_model_is_the_slice_model_with_moduli_for_pairs():
         s = I.emulated_dram_bytes(member, m, n, k, S=4)
         r = I.modular_dram_bytes(member, m, n, k, N=10)
         assert r["planes"] == s["digits"] and r["residues"] == 10 * m * n
+
+
+@pytest.mark.parametrize("m,n,N,ctas", [(16384, 16384, 15, 152), (300, 500, 11, 5), (2084, 1700, 12, 152),
+                                        (128, 192, 3, 1)])
+def test_kept_a_bytes_against_the_strips(m, n, N, ctas):
+    # every unit's B tile once; an A tile per modulus and distinct tile row of each CTA's strip
+    # (a strip of consecutive row-major tiles spans last_row - first_row + 1 tile rows)
+    k = 256
+    r = I.kept_a_l2_to_sm_bytes(m, n, k, N, ctas)
+    tiles_m, tiles_n = -(-m // 128), -(-n // 192)
+    T = tiles_m * tiles_n
+    rows = 0
+    for b in range(ctas):
+        s, e = b * T // ctas, (b + 1) * T // ctas
+        if e > s:
+            rows += (e - 1) // tiles_n - s // tiles_n + 1
+    assert r["units"] == N * T
+    assert r["a_loads"] == N * rows
+    assert r["b"] == N * T * 192 * k * 2 and r["a"] == N * rows * 128 * k * 2
+    assert r["total"] <= r["ring"]  # equal when every strip holds one tile per modulus
+    if (m, n) == (16384, 16384):
+        # the rank-k launch: 96 KB of B per unit, A about once per modulus and CTA strip row
+        assert r["b"] == 15 * 11008 * 96 * 1024
+        assert r["a"] / r["ring"] < 0.02
